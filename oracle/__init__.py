@@ -1,0 +1,151 @@
+"""Python face of the FP64 CPU oracle (``oracle.c``).
+
+TEST INFRASTRUCTURE, NOT THE PRODUCT.  Only ``tests/``, ``__graft_entry__.smoke``
+and the CPU-baseline leg of ``bench.py`` import this package.  It never imports
+the CUDA package and the CUDA package never imports it; the two share only the
+seeded input generator ``meshgen``.
+
+``build()`` compiles ``oracle.c`` with gcc into ``oracle/_build/liboracle.so``.
+Every function here is argument marshalling around one C routine; the
+arithmetic, its citations and its readings of the paper are in ``oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_p = ctypes.c_void_p
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C, -O2, no fast-math) if it is missing or stale."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    stale = (not os.path.exists(_LIB_PATH)) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)
+    if force or stale:
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        L.oracle_ke_dense.argtypes = [_int, _p, ctypes.c_double, _p]
+        L.oracle_ke_dense.restype = _int
+        L.oracle_ke_packed.argtypes = [_int, _i64, _p, _p, _p, _p, _p]
+        L.oracle_ke_packed.restype = _i64
+        L.oracle_triplets.argtypes = [_int, _i64, _p, _p, _p, _p, _p, _p, _p]
+        L.oracle_triplets.restype = _i64
+        L.oracle_compress.argtypes = [_i64, _i64, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]
+        L.oracle_compress.restype = _i64
+        L.oracle_vjp.argtypes = [_int, _i64, _p, _p, _p, _p, _p, _p]
+        L.oracle_vjp.restype = None
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _inputs(X, E, c):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    E = np.ascontiguousarray(E, dtype=np.int32)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    return X, E, c
+
+
+def npairs(npe: int) -> int:
+    return npe * (npe + 1) // 2
+
+
+def ke_dense(npe: int, xe, c: float) -> np.ndarray:
+    """Full npe x npe element matrix of one element with node coordinates xe [npe, 3]."""
+    xe = np.ascontiguousarray(xe, dtype=np.float64).reshape(npe, 3)
+    ke = np.zeros((npe, npe))
+    lib().oracle_ke_dense(npe, _ptr(xe), float(c), _ptr(ke))
+    return ke
+
+
+def ke_packed(npe: int, X, E, c):
+    """Packed lower k_e [n_elems, npe(npe+1)/2] (p = a(a+1)/2 + b), the Cauchy-Schwarz
+    scales sqrt(k_aa k_bb) of each entry, and the number of elements with det J <= 0."""
+    X, E, c = _inputs(X, E, c)
+    n = E.shape[0]
+    ke = np.zeros((n, npairs(npe)))
+    cs = np.zeros((n, npairs(npe)))
+    bad = lib().oracle_ke_packed(npe, n, _ptr(E), _ptr(X), _ptr(c), _ptr(ke), _ptr(cs))
+    return ke, cs, int(bad)
+
+
+def triplets(npe: int, X, E, c):
+    """Algorithm 1's triplet arrays (rows, cols, vals) plus per-triplet scales."""
+    X, E, c = _inputs(X, E, c)
+    nt = E.shape[0] * npairs(npe)
+    rows = np.zeros(nt, np.int64)
+    cols = np.zeros(nt, np.int32)
+    vals = np.zeros(nt)
+    cs = np.zeros(nt)
+    bad = lib().oracle_triplets(npe, E.shape[0], _ptr(E), _ptr(X), _ptr(c), _ptr(rows),
+                                _ptr(cols), _ptr(vals), _ptr(cs))
+    return rows, cols, vals, cs, int(bad)
+
+
+def compress(n_nodes: int, rows, cols, vals, cs):
+    """The sparse conversion: lower CSR with per-entry sums of |val| and of scales,
+    and the CSR slot of every triplet."""
+    nt = rows.shape[0]
+    rowptr = np.zeros(n_nodes + 1, np.int64)
+    col = np.zeros(max(nt, 1), np.int32)
+    val = np.zeros(max(nt, 1))
+    ab = np.zeros(max(nt, 1))
+    sc = np.zeros(max(nt, 1))
+    slot = np.zeros(max(nt, 1), np.int64)
+    nnz = lib().oracle_compress(nt, n_nodes, _ptr(rows), _ptr(cols), _ptr(vals), _ptr(cs),
+                                _ptr(rowptr), _ptr(col), _ptr(val), _ptr(ab), _ptr(sc), _ptr(slot))
+    return dict(rowptr=rowptr, col=col[:nnz].copy(), vals=val[:nnz].copy(), abs=ab[:nnz].copy(),
+                cs=sc[:nnz].copy(), slot=slot[:nt].copy(), nnz=int(nnz))
+
+
+def build_K(npe: int, X, E, c):
+    """Algorithm 1 end to end: global lower-triangular CSR K in FP64.
+
+    Returns a dict with rowptr, col, vals, abs (sum of |contribution|), cs (sum of
+    Cauchy-Schwarz scales), slot (CSR position of each packed (e, p)), nnz, and
+    n_bad (elements with a non-positive Jacobian determinant)."""
+    X, E, c = _inputs(X, E, c)
+    rows, cols, vals, cs, bad = triplets(npe, X, E, c)
+    out = compress(X.shape[0], rows, cols, vals, cs)
+    out["n_bad"] = bad
+    return out
+
+
+def vjp(npe: int, X, E, c, S):
+    """Gradient of L = sum_(e,p) S[e,p] k_e[p] with respect to X [n_nodes, 3] and c [n_elems]."""
+    X, E, c = _inputs(X, E, c)
+    S = np.ascontiguousarray(S, dtype=np.float64).reshape(E.shape[0], npairs(npe))
+    dX = np.zeros_like(X)
+    dc = np.zeros(E.shape[0])
+    lib().oracle_vjp(npe, E.shape[0], _ptr(E), _ptr(X), _ptr(c), _ptr(S), _ptr(dX), _ptr(dc))
+    return dX, dc
+
+
+def vjp_from_G(npe: int, X, E, c, G, slot):
+    """Gradient of L = sum over stored entries G_ij K_ij (Section 3's lower storage,
+    each packed pair counted once) given the CSR slot map from ``build_K``."""
+    S = np.asarray(G)[np.asarray(slot)]
+    return vjp(npe, X, E, c, S)
