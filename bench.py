@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark of the global stiffness-matrix build (integrate + assemble).
+
+Workload: the 1M-brick mesh -- a 100^3 grid of 8-node trilinear bricks on the
+unit cube (1,030,301 nodes), interior nodes jittered by +-0.25 h, random node and
+element numbering, c_e ~ lognormal(0, 1), 2x2x2 Gauss (seeded synthetic data).
+A step is one numeric build of the lower-CSR values of K with the pattern
+cached (the symbolic phase is timed separately as the cold build).
+
+`value` is elements/s of the mixed-precision build (FP32 with FP64 Jacobians for
+distorted elements), inputs resident in HBM, L2 flushed before every step.
+The FP64 build, the cold build and the end-to-end build through the host-buffer
+C-ABI call are reported beside it.  Multi-GPU runs are independent replicas.
+"""
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "1M-hex8: 100^3 unit-cube bricks, jitter 0.25h, permuted, c~lognormal(0,1), 2x2x2 Gauss"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=100, help="grid cells per axis (100 = the 1M-brick workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def init_dist(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        return dist
+    return None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, v):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, v):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.05)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons, n = [], None, set(), 0
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            n += 1
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": n}
+
+
+# ------------------------------------------------------------------ helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1501_04784_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, workload_key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kernel, {}).get(workload_key)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def algorithmic_bytes(n_nodes, n_elems, npe, nnz, xsize, csize, vsize):
+    # coordinates + connectivity + c_e read, CSR values written
+    return n_nodes * 3 * xsize + n_elems * npe * 4 + n_elems * csize + nnz * vsize
+
+
+def cpu_baseline(m, target_s=12.0):
+    """The FP64 oracle (Algorithm 1 as written, single thread) on a bounded sample
+    of the workload's elements: whole passes over growing prefixes until ~target_s."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    n = 4096
+    spent = 0.0
+    while True:
+        t0 = time.perf_counter()
+        oracle.build_K(m.npe, m.X, m.E[:n], m.c[:n])
+        dt = time.perf_counter() - t0
+        spent += dt
+        if spent + 2.5 * dt > target_s or n >= m.n_elems:
+            break
+        n = min(2 * n, m.n_elems)
+    return {"value": n / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n} of {m.n_elems} elements of the workload: element loop + stable sort/reduce to CSR, FP64, 1 thread"}
+
+
+# --------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import meshgen
+    from paper_1501_04784_gb300 import _build, fem
+
+    rank, world, local = dist_env()
+    dist = init_dist(world)
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        _build.build()
+    barrier(dist)
+
+    m = meshgen.config_mesh(1, nx=args.n)
+    E = torch.from_numpy(m.E).cuda()
+    X64 = torch.from_numpy(m.X).cuda()
+    c64 = torch.from_numpy(m.c).cuda()
+    Xf, cf = X64.float(), c64.float()
+    stream = torch.cuda.current_stream()
+
+    # cold build: handle creation (validation + locality order) + symbolic + first numeric build
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mesh = fem.Mesh(E, m.n_nodes, X=X64)
+    nnz = mesh.pattern()
+    vals = torch.empty(nnz, dtype=torch.float32, device="cuda")
+    mesh.build_K(Xf, cf, "mixed", out=vals)
+    torch.cuda.synchronize()
+    cold_s = time.perf_counter() - t0
+    info = mesh.info()
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    def timed(prec, X, c, out, steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            mesh.build_K(X, c, prec, out=out)
+            b.record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    for _ in range(args.warmup):
+        mesh.build_K(Xf, cf, "mixed", out=vals)
+    torch.cuda.synchronize()
+
+    clk = Clocks(local) if rank == 0 else None
+    barrier(dist)
+    torch.cuda.synchronize()
+    fem.launch_count(reset=True)
+    ms = timed("mixed", Xf, cf, vals, args.steps)
+    launches = fem.launch_count()
+    torch.cuda.synchronize()
+    barrier(dist)
+    clocks = clk.stop() if clk else None
+
+    total_s = sum(ms) / 1e3
+    max_total = max_over_ranks(dist, total_s)
+    elems_all = sum_over_ranks(dist, float(m.n_elems * args.steps))
+    value = elems_all / max_total
+    ms_step = statistics.mean(ms)
+
+    # FP64 build beside it
+    vals64 = torch.empty(nnz, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        mesh.build_K(X64, c64, "fp64", out=vals64)
+    steps64 = max(3, min(args.steps, 20))
+    ms64 = timed("fp64", X64, c64, vals64, steps64)
+    fp64_eps = m.n_elems / (statistics.mean(ms64) / 1e3)
+
+    # end to end through the host-buffer C-ABI call (pinned inputs and outputs)
+    e2e = None
+    if not args.no_e2e:
+        Xh = Xf.cpu().pin_memory()
+        ch = cf.cpu().pin_memory()
+        vh = torch.empty(nnz, dtype=torch.float32).pin_memory()
+        for _ in range(3):
+            mesh.build_K_host(Xh, ch, "mixed", out=vh)
+        ne = max(3, min(args.steps, 30))
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            mesh.build_K_host(Xh, ch, "mixed", out=vh)
+        dt = (time.perf_counter() - t0) / ne
+        e2e = {"value": m.n_elems / dt, "unit": "elements/s", "h2d_bytes_per_step": Xh.nbytes + ch.nbytes,
+               "d2h_bytes_per_step": nnz * 4}
+
+    peak, peak_kind = measured_peaks()
+    alg = algorithmic_bytes(m.n_nodes, m.n_elems, 8, nnz, 4, 4, 4)
+    alg64 = algorithmic_bytes(m.n_nodes, m.n_elems, 8, nnz, 8, 8, 8)
+    achieved = alg / (ms_step / 1e3) / 1e9
+    wkey = f"hex8_n{args.n}_mixed"
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": profiled_traffic("k_patch", wkey),
+            "peak_source": peak_kind, "kernel": "k_patch (fused integrate + assemble)",
+            "algorithmic_bytes_per_launch": alg}
+
+    if rank == 0:
+        out = {
+            "metric": "global-K build elements/s (integrate+assemble), % HBM roofline, mixed vs FP64",
+            "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (f64 Jacobians of distorted elements)", "data": "synthetic (seeded)",
+            "config": {"workload": WORKLOAD if args.n == 100 else f"{args.n}^3 bricks", "n_elems": m.n_elems,
+                       "n_nodes": m.n_nodes, "nnz": nnz, "precision": "mixed", "pattern": "cached",
+                       "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before every step"},
+            "hbm_frac": round(achieved / peak, 4),
+            "fp64": {"value": fp64_eps, "unit": "elements/s", "ms_per_step": statistics.mean(ms64),
+                     "hbm_frac": round(alg64 / (statistics.mean(ms64) / 1e3) / 1e9 / peak, 4),
+                     "mixed_speedup": value / world / fp64_eps},
+            "cold_build": {"value": m.n_elems / cold_s, "unit": "elements/s", "seconds": cold_s,
+                           "includes": "validation, locality order, pattern, plan, first numeric build"},
+            "plan": {k: info[k] for k in ("n_patches", "closure_elems", "n_colors", "plan_bytes")},
+            "roofline": roof, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(m)
+        print(json.dumps(out))
+    mesh.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# -------------------------------------------------------- reference arm
+def run_reference(args):
+    """The oracle (the plain FP64 CPU program of Algorithm 1) on the host cores,
+    each step one bounded slice of the same workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import meshgen
+    import oracle
+    oracle.build()
+    m = meshgen.config_mesh(1, nx=args.n)
+    per_step = 8192
+    off = 0
+
+    def step():
+        nonlocal off
+        lo = off % max(1, m.n_elems - per_step)
+        oracle.build_K(m.npe, m.X, m.E[lo:lo + per_step], m.c[lo:lo + per_step])
+        off += per_step
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    print(json.dumps({
+        "impl": "reference", "metric": "global-K build elements/s (integrate+assemble), % HBM roofline, mixed vs FP64",
+        "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded)",
+        "config": {"workload": WORKLOAD if args.n == 100 else f"{args.n}^3 bricks", "precision": "fp64 oracle"},
+        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} consecutive elements of the workload per step (rotating)"},
+        "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

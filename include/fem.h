@@ -1,0 +1,207 @@
+/*
+ * fem.h -- C ABI of libfem: global stiffness-matrix construction for the 3D
+ * Poisson equation on one GB300 (sm_103a).
+ *
+ * The operation (Ramirez-Gil, Tsuzuki, Montealegre-Rubio, "Global finite element
+ * matrix construction based on a CPU-GPU implementation"):
+ *   given node coordinates C, element connectivity E and a per-element
+ *   coefficient MP = c_e (Section 3), build K = sum_e k_e (Eq. 6) with
+ *   k_e = c_e * integral B^T B dOmega (Eq. 7), evaluated on the reference element
+ *   (Eq. 8) by Gauss quadrature (Eq. 9): 2x2x2 points for the 8-node brick, the
+ *   exact 1-point rule for the 4-node tetrahedron.  Only the lower triangle is
+ *   computed and stored (Section 3: 36 of the 64 entries of a brick's k_e), and
+ *   the result is a lower-triangular CSR matrix (the paper's CSC of the upper
+ *   triangle has the same arrays).
+ *
+ * Conventions shared by every call
+ *   - Pointers named X, c, E, ke, vals, rowptr, col, G, dX, dc are DEVICE
+ *     pointers unless the function name ends in _host.  The caller owns them.
+ *   - X is [n_nodes][3] row-major; E is [n_elems][npe] int32 row-major
+ *     (npe = 8 or 4); c is [n_elems].  Brick node order: nodes 0-3 on the face
+ *     t = -1 counter-clockwise from (-1,-1,-1), nodes 4-7 the same on t = +1.
+ *   - Packed lower k_e: [n_elems][npe(npe+1)/2], entry p = a(a+1)/2 + b, b <= a.
+ *     The local pair (a, b) lands at global (max(E[a], E[b]), min(E[a], E[b])).
+ *   - CSR: rowptr [n_nodes + 1] int64, col [nnz] int32 ascending within a row
+ *     (the diagonal is the last entry of each row), vals [nnz].
+ *   - Precision.  FEM_FP64: X, c, ke and vals are double; all arithmetic FP64.
+ *     FEM_MIXED: X and c are float or double (x_dtype, c_dtype); ke and vals are
+ *     float; element arithmetic FP32 with FP32 accumulation, except the
+ *     Jacobian determinant and inverse of elements whose distortion indicator
+ *     exceeds fem_options.distortion_threshold (FP64) and the summation of
+ *     entries that receive more than fem_options.valence_threshold
+ *     contributions (FP64, rounded once).
+ *   - Every call is ordered on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and returns without waiting, except where stated.  Asynchronous
+ *     CUDA errors surface at the next call on the mesh or at fem_sync.
+ *   - Every call returns a status; nothing throws across this boundary.  A
+ *     one-line detail of the last failure on the calling thread is available
+ *     from fem_last_error().
+ *   - Values are deterministic: the order in which contributions are summed
+ *     into each entry is fixed by the mesh's cached plan, so repeated builds of
+ *     the same inputs are bitwise identical.
+ */
+#ifndef FEM_H
+#define FEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fem_mesh_s *fem_mesh; /* opaque, library-owned */
+
+typedef enum {
+    FEM_OK = 0,
+    FEM_ERR_ARG = 1,         /* null or misaligned pointer, bad size, bad enum value */
+    FEM_ERR_INDEX = 2,       /* a node id in E outside [0, n_nodes) */
+    FEM_ERR_DEGENERATE = 3,  /* a node repeated within one element */
+    FEM_ERR_OOM = 4,         /* a device allocation failed */
+    FEM_ERR_BUDGET = 5,      /* the memory budget cannot hold the smallest unit of work */
+    FEM_ERR_CUDA = 6,        /* a CUDA runtime call or kernel failed */
+    FEM_ERR_TIMEOUT = 7,     /* a bounded device-side wait gave up */
+    FEM_ERR_STATE = 8,       /* call out of order, e.g. values before the pattern */
+    FEM_ERR_UNSUPPORTED = 9  /* mesh outside the supported range (see fem_last_error) */
+} fem_status;
+
+typedef enum { FEM_TET4 = 4, FEM_HEX8 = 8 } fem_elem;
+typedef enum { FEM_FP64 = 0, FEM_MIXED = 1 } fem_prec;
+typedef enum { FEM_F32 = 0, FEM_F64 = 1 } fem_dtype;
+
+typedef struct {
+    size_t mem_budget_bytes;     /* cap on library-owned device memory; 0 = no cap */
+    double distortion_threshold; /* mixed mode; brick: max_q detJ / min_q detJ, tet:
+                                    longest edge / shortest altitude.  Default 3 / 10. */
+    int valence_threshold;       /* mixed mode: entries with more contributions than
+                                    this are summed in FP64.  Default 8. */
+    int patch_entries;           /* lower-CSR entries owned by one thread block (0 = default) */
+    int block_threads;           /* threads per block of the patch kernels (0 = default) */
+    int blocks_per_sm;           /* resident blocks per SM for the patch kernels (0 = default) */
+    int locality_order;          /* 1 = order nodes along a Morton curve of X (default); 0 = by id */
+    int reserved[8];
+} fem_options;
+
+typedef struct {
+    int64_t n_nodes, n_elems, nnz;
+    int64_t n_patches;           /* thread-block work units of the numeric kernels */
+    int64_t closure_elems;       /* sum over patches of the elements each one integrates */
+    int64_t max_patch_entries, max_patch_cnodes, max_patch_elems;
+    int32_t n_colors;            /* colours of the in-block accumulation order */
+    int32_t max_row_len;
+    size_t plan_bytes;           /* device bytes held by the cached pattern and plan */
+    size_t budget_bytes;         /* the budget in force (0 = none) */
+    int32_t n_groups;            /* patch groups the numeric build runs in under the budget */
+    int32_t reserved[7];
+} fem_info;
+
+/* Default options (see the field comments). */
+void fem_options_default(fem_options *opt);
+
+/* Human-readable name of a status code (static storage). */
+const char *fem_status_str(fem_status s);
+
+/* Detail of the last failure on the calling thread (static thread-local storage). */
+const char *fem_last_error(void);
+
+/*
+ * Create a mesh handle: validates E (Section 3's connectivity array) and caches
+ * nothing else yet.  E must stay valid and unchanged until fem_mesh_destroy.
+ * X (optional, may be NULL) is read once to order nodes along a space-filling
+ * curve, which only changes locality; it is not retained.
+ * Blocks until validation is done.  Errors: FEM_ERR_ARG (null E, sizes <= 0,
+ * n_nodes >= 2^31, bad type), FEM_ERR_INDEX, FEM_ERR_DEGENERATE, FEM_ERR_OOM.
+ */
+fem_status fem_mesh_create(fem_mesh *out, fem_elem type, int64_t n_nodes, int64_t n_elems,
+                           const int32_t *E, const void *X, fem_dtype x_dtype,
+                           const fem_options *opt, void *stream);
+
+/* Release the handle and everything it owns.  NULL is ignored. */
+void fem_mesh_destroy(fem_mesh m);
+
+/*
+ * Symbolic phase (Algorithm 1's Mapping plus the structure of the sparse
+ * conversion): build and cache the lower-CSR pattern of K -- every node pair
+ * that shares an element, explicit zeros included -- and the per-block plan of
+ * the numeric kernels.  Writes nnz to *nnz_out.  Idempotent.  Blocks (reads nnz
+ * back).  Errors: FEM_ERR_OOM, FEM_ERR_BUDGET, FEM_ERR_UNSUPPORTED (a row with
+ * more than 255 entries, more than 128 colours), FEM_ERR_CUDA.
+ */
+fem_status fem_pattern(fem_mesh m, int64_t *nnz_out, void *stream);
+
+/* Copy the cached pattern into caller arrays rowptr [n_nodes+1], col [nnz]
+ * (device).  FEM_ERR_STATE before fem_pattern. */
+fem_status fem_get_pattern(fem_mesh m, int64_t *rowptr, int32_t *col, void *stream);
+
+/* Library-owned device pointers of the cached pattern (valid until destroy). */
+fem_status fem_pattern_ptrs(fem_mesh m, const int64_t **rowptr, const int32_t **col);
+
+/*
+ * Numerical integration (Algorithm 2, Eqs. 7-9): packed lower k_e of every
+ * element into ke_out [n_elems][36|10] (double for FEM_FP64, float for
+ * FEM_MIXED).  Needs no pattern.
+ */
+fem_status fem_integrate_local(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype,
+                               const void *c, fem_dtype c_dtype, void *ke_out, void *stream);
+
+/*
+ * Assembly (Section 3: triplet-to-compressed conversion, Eq. 6): sum the packed
+ * element matrices ke [n_elems][36|10] into vals [nnz] of the cached pattern.
+ * Every entry is written (no need to clear vals).  FEM_ERR_STATE before
+ * fem_pattern.
+ */
+fem_status fem_assemble_csr(fem_mesh m, fem_prec p, const void *ke, void *vals, void *stream);
+
+/*
+ * Integration and assembly fused: vals [nnz] of K for coordinates X and
+ * coefficients c, with the pattern cached.  No element matrix goes through
+ * device memory in FEM_MIXED; in FEM_FP64 the library may stage element
+ * matrices in its own memory when that is faster (within the budget).
+ * FEM_ERR_STATE before fem_pattern.
+ */
+fem_status fem_build_K(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c,
+                       fem_dtype c_dtype, void *vals, void *stream);
+
+/*
+ * fem_build_K with HOST inputs and outputs (page-locked memory gives full
+ * copy bandwidth; pageable memory works but is slower): copies X and c to
+ * library-owned device buffers, builds, copies vals back.  Blocks until vals
+ * is on the host.
+ */
+fem_status fem_build_K_host(fem_mesh m, fem_prec p, const void *X_host, fem_dtype x_dtype,
+                            const void *c_host, fem_dtype c_dtype, void *vals_host, void *stream);
+
+/*
+ * Backward pass: for L = sum over stored entries of G_ij K_ij (each packed pair
+ * (a, b) of an element counted once), write dX [n_nodes][3] = dL/dX and
+ * dc [n_elems] = dL/dc, recomputing J and B (nothing is kept from the forward
+ * pass).  FEM_FP64: G, X, c, dX, dc double.  FEM_MIXED: G float, X and c per
+ * dtype, dX and dc float; arithmetic FP32.  Every output entry is written.
+ */
+fem_status fem_vjp(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c,
+                   fem_dtype c_dtype, const void *G, void *dX, void *dc, void *stream);
+
+/*
+ * Batched build of n meshes (each with its pattern cached) in one persistent
+ * launch, replayed from a CUDA graph when the same mesh set is built again.
+ * X[i], c[i], vals[i] are host arrays of n device pointers; all meshes share
+ * p, x_dtype and c_dtype.
+ */
+fem_status fem_build_K_batched(const fem_mesh *meshes, int n, fem_prec p, const void *const *X,
+                               fem_dtype x_dtype, const void *const *c, fem_dtype c_dtype,
+                               void *const *vals, void *stream);
+
+/* Wait for the mesh's work on `stream` and report any asynchronous error. */
+fem_status fem_sync(fem_mesh m, void *stream);
+
+/* Sizes and plan statistics of the mesh (after fem_pattern for the plan fields). */
+fem_status fem_mesh_info(fem_mesh m, fem_info *info);
+
+/* Number of kernel launches the library issued since the last reset (for
+ * benchmarks that count the work inside a timed region). */
+int64_t fem_launch_count(int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEM_H */

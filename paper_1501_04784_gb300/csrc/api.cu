@@ -1,0 +1,380 @@
+// api.cu -- the C ABI declared in include/fem.h: argument checks, the mesh
+// handle's lifecycle, and dispatch to the symbolic and numeric kernels.
+#include <cstring>
+#include <new>
+
+#include "mesh.cuh"
+#include "numeric.cuh"
+
+namespace fem {
+int64_t launch_count(int reset);
+fem_status launch_vjp(fem_mesh m, bool mixed, const void *X, fem_dtype xd, const void *c, fem_dtype cd,
+                      const void *G, void *dX, void *dc, cudaStream_t s);
+fem_status launch_batched(const fem_mesh *ms, int n, bool mixed, const void *const *X, fem_dtype xd,
+                          const void *const *c, fem_dtype cd, void *const *vals, cudaStream_t s);
+}  // namespace fem
+
+using namespace fem;
+
+static cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+static bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+static size_t dsize(fem_dtype d) { return d == FEM_F64 ? 8 : 4; }
+
+static float default_threshold(const fem_mesh m) {
+    if (m->opt.distortion_threshold > 0) return (float)m->opt.distortion_threshold;
+    return m->npe == 8 ? 2.5f : 10.0f;
+}
+
+static fem_status check_dtype(fem_dtype d, const char *what) {
+    if (d != FEM_F32 && d != FEM_F64) {
+        set_error("%s: dtype must be FEM_F32 or FEM_F64", what);
+        return FEM_ERR_ARG;
+    }
+    return FEM_OK;
+}
+
+// Inputs of a numeric call: FP64 mode takes double X and c; mixed takes either.
+static fem_status check_inputs(fem_mesh m, fem_prec p, const void *X, fem_dtype xd, const void *c, fem_dtype cd) {
+    if (!m) {
+        set_error("null mesh");
+        return FEM_ERR_ARG;
+    }
+    if (p != FEM_FP64 && p != FEM_MIXED) {
+        set_error("precision must be FEM_FP64 or FEM_MIXED");
+        return FEM_ERR_ARG;
+    }
+    FEM_TRY(check_dtype(xd, "x_dtype"));
+    FEM_TRY(check_dtype(cd, "c_dtype"));
+    if (p == FEM_FP64 && (xd != FEM_F64 || cd != FEM_F64)) {
+        set_error("FEM_FP64 needs double X and c");
+        return FEM_ERR_ARG;
+    }
+    if (!X || !c) {
+        set_error("null X or c");
+        return FEM_ERR_ARG;
+    }
+    if (!aligned(X, dsize(xd)) || !aligned(c, dsize(cd))) {
+        set_error("X or c is not aligned to its element size");
+        return FEM_ERR_ARG;
+    }
+    return FEM_OK;
+}
+
+extern "C" {
+
+void fem_options_default(fem_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->mem_budget_bytes = 0;
+    opt->distortion_threshold = 0.0;  // 0 = per element type: brick 2.5, tetrahedron 10
+    opt->valence_threshold = 8;
+    opt->patch_entries = 0;
+    opt->block_threads = 0;
+    opt->blocks_per_sm = 0;
+    opt->locality_order = 1;
+}
+
+const char *fem_status_str(fem_status s) {
+    switch (s) {
+        case FEM_OK: return "FEM_OK";
+        case FEM_ERR_ARG: return "FEM_ERR_ARG";
+        case FEM_ERR_INDEX: return "FEM_ERR_INDEX";
+        case FEM_ERR_DEGENERATE: return "FEM_ERR_DEGENERATE";
+        case FEM_ERR_OOM: return "FEM_ERR_OOM";
+        case FEM_ERR_BUDGET: return "FEM_ERR_BUDGET";
+        case FEM_ERR_CUDA: return "FEM_ERR_CUDA";
+        case FEM_ERR_TIMEOUT: return "FEM_ERR_TIMEOUT";
+        case FEM_ERR_STATE: return "FEM_ERR_STATE";
+        case FEM_ERR_UNSUPPORTED: return "FEM_ERR_UNSUPPORTED";
+    }
+    return "FEM_ERR_UNKNOWN";
+}
+
+const char *fem_last_error(void);  // defined in primitives.cu
+
+fem_status fem_mesh_create(fem_mesh *out, fem_elem type, int64_t n_nodes, int64_t n_elems, const int32_t *E,
+                           const void *X, fem_dtype x_dtype, const fem_options *opt, void *stream) {
+    if (!out) {
+        set_error("null output handle");
+        return FEM_ERR_ARG;
+    }
+    *out = nullptr;
+    if (type != FEM_HEX8 && type != FEM_TET4) {
+        set_error("element type must be FEM_HEX8 or FEM_TET4");
+        return FEM_ERR_ARG;
+    }
+    if (n_nodes <= 0 || n_elems <= 0 || n_nodes >= (1ll << 31) || n_elems >= (1ll << 31)) {
+        set_error("sizes must be in [1, 2^31)");
+        return FEM_ERR_ARG;
+    }
+    if (!E || !aligned(E, 16)) {
+        set_error("E must be a non-null device pointer aligned to 16 bytes");
+        return FEM_ERR_ARG;
+    }
+    if (X) {
+        FEM_TRY(check_dtype(x_dtype, "x_dtype"));
+        if (!aligned(X, dsize(x_dtype))) {
+            set_error("X is not aligned to its element size");
+            return FEM_ERR_ARG;
+        }
+    }
+    fem_mesh m = new (std::nothrow) fem_mesh_s();
+    if (!m) {
+        set_error("host allocation failed");
+        return FEM_ERR_OOM;
+    }
+    m->type = type;
+    m->npe = (int)type;
+    m->np = m->npe * (m->npe + 1) / 2;
+    m->n_nodes = n_nodes;
+    m->n_elems = n_elems;
+    m->E = E;
+    if (opt) m->opt = *opt; else fem_options_default(&m->opt);
+    if (m->opt.valence_threshold <= 0) m->opt.valence_threshold = 8;
+    m->arena.budget = m->opt.mem_budget_bytes;
+    cudaStream_t s = as_stream(stream);
+    fem_status st = validate_connectivity(m, s);
+    if (st == FEM_OK) st = build_locality_order(m, X, x_dtype, s);
+    if (st == FEM_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_status(e, "fem_mesh_create");
+    }
+    if (st != FEM_OK) {
+        delete m;
+        return st;
+    }
+    *out = m;
+    return FEM_OK;
+}
+
+void fem_mesh_destroy(fem_mesh m) {
+    if (!m) return;
+    cudaDeviceSynchronize();
+    delete m;
+}
+
+fem_status fem_pattern(fem_mesh m, int64_t *nnz_out, void *stream) {
+    if (!m) {
+        set_error("null mesh");
+        return FEM_ERR_ARG;
+    }
+    if (!m->has_pattern) {
+        cudaStream_t s = as_stream(stream);
+        fem_status st = build_pattern_and_plan(m, s);
+        if (st == FEM_OK) {
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) st = cuda_status(e, "fem_pattern");
+        }
+        if (st != FEM_OK) {
+            m->has_pattern = false;
+            return st;
+        }
+    }
+    if (nnz_out) *nnz_out = m->nnz;
+    return FEM_OK;
+}
+
+fem_status fem_get_pattern(fem_mesh m, int64_t *rowptr, int32_t *col, void *stream) {
+    if (!m) {
+        set_error("null mesh");
+        return FEM_ERR_ARG;
+    }
+    if (!m->has_pattern) {
+        set_error("fem_get_pattern before fem_pattern");
+        return FEM_ERR_STATE;
+    }
+    cudaStream_t s = as_stream(stream);
+    if (rowptr)
+        FEM_CUDA(cudaMemcpyAsync(rowptr, m->rowptr.ptr, (m->n_nodes + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    if (col && m->nnz)
+        FEM_CUDA(cudaMemcpyAsync(col, m->col.ptr, m->nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    return FEM_OK;
+}
+
+fem_status fem_pattern_ptrs(fem_mesh m, const int64_t **rowptr, const int32_t **col) {
+    if (!m) {
+        set_error("null mesh");
+        return FEM_ERR_ARG;
+    }
+    if (!m->has_pattern) {
+        set_error("fem_pattern_ptrs before fem_pattern");
+        return FEM_ERR_STATE;
+    }
+    if (rowptr) *rowptr = m->rowptr.ptr;
+    if (col) *col = m->col.ptr;
+    return FEM_OK;
+}
+
+fem_status fem_integrate_local(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c,
+                               fem_dtype c_dtype, void *ke_out, void *stream) {
+    FEM_TRY(check_inputs(m, p, X, x_dtype, c, c_dtype));
+    if (!ke_out || !aligned(ke_out, p == FEM_FP64 ? 8 : 4)) {
+        set_error("ke_out must be a non-null aligned device pointer");
+        return FEM_ERR_ARG;
+    }
+    IntegrateArgs a{m->npe, p == FEM_MIXED, x_dtype, c_dtype, m->E, m->n_elems, X, c, ke_out,
+                    default_threshold(m), nullptr};
+    return launch_integrate(a, as_stream(stream));
+}
+
+static PatchArgs patch_args(fem_mesh m, fem_prec p, bool fused) {
+    PatchArgs a{};
+    a.plan = &m->plan;
+    a.npe = m->npe;
+    a.mixed = p == FEM_MIXED;
+    a.fused = fused;
+    a.thr = default_threshold(m);
+    a.p0 = 0;
+    a.p1 = m->plan.n_patches;
+    a.threads = m->opt.block_threads > 0 ? m->opt.block_threads : 256;
+    if (a.threads > PATCH_MAX_THREADS) a.threads = PATCH_MAX_THREADS;
+    a.threads = (a.threads + 31) / 32 * 32;
+    a.blocks_per_sm = m->opt.blocks_per_sm;
+    return a;
+}
+
+fem_status fem_assemble_csr(fem_mesh m, fem_prec p, const void *ke, void *vals, void *stream) {
+    if (!m) {
+        set_error("null mesh");
+        return FEM_ERR_ARG;
+    }
+    if (!m->has_pattern) {
+        set_error("fem_assemble_csr before fem_pattern");
+        return FEM_ERR_STATE;
+    }
+    if (p != FEM_FP64 && p != FEM_MIXED) {
+        set_error("precision must be FEM_FP64 or FEM_MIXED");
+        return FEM_ERR_ARG;
+    }
+    const size_t w = p == FEM_FP64 ? 8 : 4;
+    if (!ke || !vals || !aligned(ke, w) || !aligned(vals, w)) {
+        set_error("ke and vals must be non-null aligned device pointers");
+        return FEM_ERR_ARG;
+    }
+    PatchArgs a = patch_args(m, p, false);
+    a.xd = FEM_F32;
+    a.cd = FEM_F32;
+    a.ke = ke;
+    a.vals = vals;
+    return launch_patch(a, as_stream(stream));
+}
+
+fem_status fem_build_K(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c, fem_dtype c_dtype,
+                       void *vals, void *stream) {
+    FEM_TRY(check_inputs(m, p, X, x_dtype, c, c_dtype));
+    if (!m->has_pattern) {
+        set_error("fem_build_K before fem_pattern");
+        return FEM_ERR_STATE;
+    }
+    if (!vals || !aligned(vals, p == FEM_FP64 ? 8 : 4)) {
+        set_error("vals must be a non-null aligned device pointer");
+        return FEM_ERR_ARG;
+    }
+    PatchArgs a = patch_args(m, p, true);
+    a.xd = x_dtype;
+    a.cd = c_dtype;
+    a.X = X;
+    a.c = c;
+    a.vals = vals;
+    return launch_patch(a, as_stream(stream));
+}
+
+fem_status fem_build_K_host(fem_mesh m, fem_prec p, const void *X_host, fem_dtype x_dtype, const void *c_host,
+                            fem_dtype c_dtype, void *vals_host, void *stream) {
+    FEM_TRY(check_inputs(m, p, X_host, x_dtype, c_host, c_dtype));
+    if (!m->has_pattern) {
+        set_error("fem_build_K_host before fem_pattern");
+        return FEM_ERR_STATE;
+    }
+    if (!vals_host) {
+        set_error("null vals");
+        return FEM_ERR_ARG;
+    }
+    const size_t xb = (size_t)m->n_nodes * 3 * dsize(x_dtype);
+    const size_t cb = (size_t)m->n_elems * dsize(c_dtype);
+    const size_t vb = (size_t)m->nnz * (p == FEM_FP64 ? 8 : 4);
+    const size_t xo = 0, co = (xb + 255) / 256 * 256, vo = co + (cb + 255) / 256 * 256;
+    const size_t total = vo + vb;
+    if (m->host_stage.n < total) FEM_TRY(m->host_stage.alloc(m->arena, total, "host staging"));
+    unsigned char *base = m->host_stage.ptr;
+    cudaStream_t s = as_stream(stream);
+    FEM_CUDA(cudaMemcpyAsync(base + xo, X_host, xb, cudaMemcpyHostToDevice, s));
+    FEM_CUDA(cudaMemcpyAsync(base + co, c_host, cb, cudaMemcpyHostToDevice, s));
+    FEM_TRY(fem_build_K(m, p, base + xo, x_dtype, base + co, c_dtype, base + vo, stream));
+    FEM_CUDA(cudaMemcpyAsync(vals_host, base + vo, vb, cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    return FEM_OK;
+}
+
+fem_status fem_vjp(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c, fem_dtype c_dtype,
+                   const void *G, void *dX, void *dc, void *stream) {
+    FEM_TRY(check_inputs(m, p, X, x_dtype, c, c_dtype));
+    if (!m->has_pattern) {
+        set_error("fem_vjp before fem_pattern");
+        return FEM_ERR_STATE;
+    }
+    const size_t w = p == FEM_FP64 ? 8 : 4;
+    if (!G || !dX || !dc || !aligned(G, w) || !aligned(dX, w) || !aligned(dc, w)) {
+        set_error("G, dX and dc must be non-null aligned device pointers");
+        return FEM_ERR_ARG;
+    }
+    return launch_vjp(m, p == FEM_MIXED, X, x_dtype, c, c_dtype, G, dX, dc, as_stream(stream));
+}
+
+fem_status fem_build_K_batched(const fem_mesh *meshes, int n, fem_prec p, const void *const *X, fem_dtype x_dtype,
+                               const void *const *c, fem_dtype c_dtype, void *const *vals, void *stream) {
+    if (!meshes || n < 0 || (n > 0 && (!X || !c || !vals))) {
+        set_error("bad batch arguments");
+        return FEM_ERR_ARG;
+    }
+    for (int i = 0; i < n; ++i) {
+        FEM_TRY(check_inputs(meshes[i], p, X[i], x_dtype, c[i], c_dtype));
+        if (!meshes[i]->has_pattern) {
+            set_error("mesh %d of the batch has no pattern", i);
+            return FEM_ERR_STATE;
+        }
+        if (!vals[i]) {
+            set_error("null vals for mesh %d", i);
+            return FEM_ERR_ARG;
+        }
+    }
+    if (n == 0) return FEM_OK;
+    return launch_batched(meshes, n, p == FEM_MIXED, X, x_dtype, c, c_dtype, vals, as_stream(stream));
+}
+
+fem_status fem_sync(fem_mesh m, void *stream) {
+    (void)m;
+    cudaError_t e = cudaStreamSynchronize(as_stream(stream));
+    if (e != cudaSuccess) return cuda_status(e, "fem_sync");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e, "fem_sync");
+    return FEM_OK;
+}
+
+fem_status fem_mesh_info(fem_mesh m, fem_info *info) {
+    if (!m || !info) {
+        set_error("null argument");
+        return FEM_ERR_ARG;
+    }
+    std::memset(info, 0, sizeof(*info));
+    info->n_nodes = m->n_nodes;
+    info->n_elems = m->n_elems;
+    info->nnz = m->nnz;
+    info->n_patches = m->plan.n_patches;
+    info->closure_elems = m->plan.total_celems;
+    info->max_patch_entries = m->plan.max_acc;
+    info->max_patch_cnodes = m->plan.max_cnodes;
+    info->max_patch_elems = m->plan.max_celems;
+    info->n_colors = m->plan.n_colors;
+    info->max_row_len = m->max_row_len;
+    info->plan_bytes = m->plan.bytes() + m->rowptr.bytes() + m->col.bytes() + m->inc_ptr.bytes() + m->inc_elem.bytes();
+    info->budget_bytes = m->arena.budget;
+    info->n_groups = m->n_groups;
+    return FEM_OK;
+}
+
+int64_t fem_launch_count(int reset) { return launch_count(reset); }
+
+}  // extern "C"

@@ -1,0 +1,351 @@
+// numeric.cu -- the numeric kernels.
+//
+// k_integrate: Algorithm 2's kernel re-designed for sm_103a -- one thread per
+//   element forms the packed lower k_e (Eqs. 7-9); the block stages its
+//   elements' k_e in shared memory and writes them to HBM in one coalesced
+//   stream.
+// k_patch: integration fused with assembly (Eq. 6).  One block per patch of
+//   owned rows (see mesh.cuh): node coordinates of the patch's closure are
+//   gathered once into shared memory, every closure element is integrated by one
+//   thread, its entries that fall in owned rows are added into shared-memory
+//   accumulators colour by colour, and each owned row is written to HBM once.
+//   The same kernel assembles given element matrices when FUSED is false.
+#include "element.cuh"
+#include "mesh.cuh"
+#include "numeric.cuh"
+
+namespace fem {
+
+template <int NPE>
+struct ElemTraits;
+template <>
+struct ElemTraits<8> {
+    static constexpr int NP = 36;
+};
+template <>
+struct ElemTraits<4> {
+    static constexpr int NP = 10;
+};
+
+template <int NPE>
+__device__ __forceinline__ void load_ids(const int32_t *__restrict__ E, int64_t e, int32_t (&g)[NPE]) {
+    if constexpr (NPE == 8) {
+        const int4 *p = reinterpret_cast<const int4 *>(E + e * 8);
+        const int4 a = __ldg(p), b = __ldg(p + 1);
+        g[0] = a.x; g[1] = a.y; g[2] = a.z; g[3] = a.w;
+        g[4] = b.x; g[5] = b.y; g[6] = b.z; g[7] = b.w;
+    } else {
+        const int4 a = __ldg(reinterpret_cast<const int4 *>(E + e * 4));
+        g[0] = a.x; g[1] = a.y; g[2] = a.z; g[3] = a.w;
+    }
+}
+
+template <int NPE>
+__device__ __forceinline__ void load_lnodes(const uint16_t *__restrict__ L, int64_t i, uint16_t (&ln)[NPE]) {
+    if constexpr (NPE == 8) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(L + i * 8));
+        ln[0] = v.x & 0xffff; ln[1] = v.x >> 16; ln[2] = v.y & 0xffff; ln[3] = v.y >> 16;
+        ln[4] = v.z & 0xffff; ln[5] = v.z >> 16; ln[6] = v.w & 0xffff; ln[7] = v.w >> 16;
+    } else {
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(L + i * 4));
+        ln[0] = v.x & 0xffff; ln[1] = v.x >> 16; ln[2] = v.y & 0xffff; ln[3] = v.y >> 16;
+    }
+}
+
+// Element matrix in the arithmetic of the precision mode.  FP64: everything in
+// double.  MIXED: float, FP64 Jacobians for distorted elements.
+template <int NPE, typename AccT, typename S, bool MIXED>
+__device__ __forceinline__ bool element_matrix(const S (*xc)[3], double ce, float thr,
+                                               AccT (&k)[ElemTraits<NPE>::NP]) {
+    if constexpr (MIXED) {
+        if constexpr (NPE == 8) return brick_ke_mixed<S>(xc, (float)ce, thr, k);
+        else return tet_ke_mixed<S>(xc, (float)ce, thr, k);
+    } else {
+        if constexpr (NPE == 8) brick_ke<double, S>(xc, ce, k);
+        else tet_ke<double, S>(xc, ce, k);
+        return false;
+    }
+}
+
+// ------------------------------------------------------------- k_integrate
+static constexpr int INT_THREADS = 128;
+
+template <int NPE, typename T, typename S, typename CT, bool MIXED>
+__global__ void __launch_bounds__(INT_THREADS) k_integrate(const int32_t *__restrict__ E, int64_t nel,
+                                                           const S *__restrict__ X, const CT *__restrict__ c,
+                                                           T *__restrict__ ke_out, float thr,
+                                                           unsigned long long *nflag) {
+    constexpr int NP = ElemTraits<NPE>::NP;
+    constexpr int LD = NP + 1;  // odd stride: conflict-free staging
+    extern __shared__ __align__(16) unsigned char int_smem[];
+    T *st = reinterpret_cast<T *>(int_smem);
+    unsigned flagged_total = 0;
+    for (int64_t e0 = (int64_t)blockIdx.x * INT_THREADS; e0 < nel; e0 += (int64_t)gridDim.x * INT_THREADS) {
+        const int64_t e = e0 + threadIdx.x;
+        bool fl = false;
+        if (e < nel) {
+            int32_t g[NPE];
+            load_ids<NPE>(E, e, g);
+            S xc[NPE][3];
+#pragma unroll
+            for (int a = 0; a < NPE; ++a) {
+                xc[a][0] = __ldg(X + 3 * (int64_t)g[a] + 0);
+                xc[a][1] = __ldg(X + 3 * (int64_t)g[a] + 1);
+                xc[a][2] = __ldg(X + 3 * (int64_t)g[a] + 2);
+            }
+            T k[NP];
+            fl = element_matrix<NPE, T, S, MIXED>(xc, (double)__ldg(c + e), thr, k);
+#pragma unroll
+            for (int p = 0; p < NP; ++p) st[threadIdx.x * LD + p] = k[p];
+        }
+        flagged_total += __syncthreads_count(fl);
+        const int nb = (int)min((int64_t)INT_THREADS, nel - e0);
+        T *out = ke_out + e0 * NP;
+        for (int idx = threadIdx.x; idx < nb * NP; idx += INT_THREADS) out[idx] = st[(idx / NP) * LD + idx % NP];
+        __syncthreads();
+    }
+    if (nflag && threadIdx.x == 0 && flagged_total) atomicAdd(nflag, (unsigned long long)flagged_total);
+}
+
+// ------------------------------------------------------------------ k_patch
+template <int NPE, typename AccT, typename S, typename CT, bool FUSED, bool MIXED>
+__global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch(PlanView pv, const S *__restrict__ X,
+                                                             const CT *__restrict__ c, const AccT *__restrict__ ke,
+                                                             AccT *__restrict__ vals, float thr, int64_t p0,
+                                                             int64_t p1, PatchSmem L) {
+    constexpr int NP = ElemTraits<NPE>::NP;
+    extern __shared__ __align__(16) unsigned char patch_smem[];
+    AccT *acc = reinterpret_cast<AccT *>(patch_smem + L.acc);
+    double *hv = reinterpret_cast<double *>(patch_smem + L.hv);
+    S(*xs)[3] = reinterpret_cast<S(*)[3]>(patch_smem + L.xs);
+    int32_t *cown = reinterpret_cast<int32_t *>(patch_smem + L.cown);
+    int32_t *roff = reinterpret_cast<int32_t *>(patch_smem + L.roff);
+    uint8_t *hvf = patch_smem + L.hvf;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+
+    for (int64_t p = p0 + blockIdx.x; p < p1; p += gridDim.x) {
+        const int64_t nb = pv.patch_node_ptr[p];
+        const int nown = (int)(pv.patch_node_ptr[p + 1] - nb);
+        const int64_t cb = pv.patch_cnode_ptr[p];
+        const int ncn = (int)(pv.patch_cnode_ptr[p + 1] - cb);
+        const int64_t eb = pv.patch_elem_ptr[p];
+        const int nel = (int)(pv.patch_elem_ptr[p + 1] - eb);
+        const int nacc = pv.patch_acc[p];
+
+        for (int j = tid; j < ncn; j += nthr) {
+            cown[j] = pv.cnode_own[cb + j];
+            if constexpr (FUSED) {
+                const int64_t g = pv.cnode_gid[cb + j];
+                xs[j][0] = __ldg(X + 3 * g + 0);
+                xs[j][1] = __ldg(X + 3 * g + 1);
+                xs[j][2] = __ldg(X + 3 * g + 2);
+            }
+        }
+        for (int k = tid; k < nown; k += nthr) {
+            roff[k] = pv.own_acc[nb + k];
+            if constexpr (MIXED) {
+                hv[k] = 0.0;
+                hvf[k] = pv.own_hv[nb + k];
+            }
+        }
+        if (tid == 0) roff[nown] = nacc;
+        for (int i = tid; i < nacc; i += nthr) acc[i] = AccT(0);
+        __syncthreads();
+
+        for (int base = 0; base < nel; base += nthr) {
+            const int i = base + tid;
+            const bool act = i < nel;
+            const int64_t ci = eb + i;
+            AccT kv[NP];
+            uint16_t ln[NPE];
+            int mycol = -1;
+            if (act) {
+                load_lnodes<NPE>(pv.celem_lnode, ci, ln);
+                mycol = pv.celem_color[ci];
+                const int64_t e = pv.celem_id[ci];
+                if constexpr (FUSED) {
+                    S xc[NPE][3];
+#pragma unroll
+                    for (int a = 0; a < NPE; ++a) {
+                        xc[a][0] = xs[ln[a]][0];
+                        xc[a][1] = xs[ln[a]][1];
+                        xc[a][2] = xs[ln[a]][2];
+                    }
+                    element_matrix<NPE, AccT, S, MIXED>(xc, (double)__ldg(c + e), thr, kv);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) kv[q] = __ldg(ke + e * NP + q);
+                }
+            }
+            const int last = min(base + nthr, nel) - 1;
+            const int c0 = pv.celem_color[eb + base], c1 = pv.celem_color[eb + last];
+            for (int cc = c0; cc <= c1; ++cc) {
+                if (mycol == cc) {
+                    uint8_t pos[NP];
+                    const uint32_t *pw = reinterpret_cast<const uint32_t *>(pv.celem_pos + ci * ((NP + 3) / 4 * 4));
+#pragma unroll
+                    for (int w = 0; w < (NP + 3) / 4; ++w) {
+                        const uint32_t v = __ldg(pw + w);
+#pragma unroll
+                        for (int b = 0; b < 4; ++b)
+                            if (4 * w + b < NP) pos[4 * w + b] = (uint8_t)(v >> (8 * b));
+                    }
+#pragma unroll
+                    for (int a = 0; a < NPE; ++a) {
+#pragma unroll
+                        for (int b = 0; b <= a; ++b) {
+                            const int q = a * (a + 1) / 2 + b;
+                            const int rl = ln[a] > ln[b] ? ln[a] : ln[b];
+                            const int o = cown[rl];
+                            if (o >= 0) {
+                                if (MIXED && a == b && hvf[o]) hv[o] += (double)kv[q];
+                                else acc[roff[o] + pos[q]] += kv[q];
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+
+        // each owned row to HBM once (one warp per row)
+        for (int k = warp; k < nown; k += nwarps) {
+            const int64_t rp = pv.own_rowptr[nb + k];
+            const int o0 = roff[k], len = roff[k + 1] - o0;
+            const bool h = MIXED && hvf[k];
+            for (int j = lane; j < len; j += 32) {
+                AccT v = acc[o0 + j];
+                if (h && j == len - 1) v = (AccT)hv[k];
+                vals[rp + j] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename F>
+static fem_status set_smem(F *f, size_t bytes) {
+    FEM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return FEM_OK;
+}
+
+template <int NPE, typename T, typename S, typename CT, bool MIXED>
+static fem_status launch_integrate_t(const int32_t *E, int64_t nel, const void *X, const void *c, void *ke, float thr,
+                                     unsigned long long *nflag, cudaStream_t s) {
+    constexpr int NP = ElemTraits<NPE>::NP;
+    const size_t smem = (size_t)INT_THREADS * (NP + 1) * sizeof(T);
+    auto f = k_integrate<NPE, T, S, CT, MIXED>;
+    FEM_TRY(set_smem(f, smem));
+    int per_sm = 0;
+    FEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, INT_THREADS, smem));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t tiles = cdiv(nel, INT_THREADS);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms() * per_sm));
+    f<<<grid, INT_THREADS, smem, s>>>(E, nel, (const S *)X, (const CT *)c, (T *)ke, thr, nflag);
+    FEM_LAUNCHED("k_integrate");
+    return FEM_OK;
+}
+
+fem_status launch_integrate(const IntegrateArgs &a, cudaStream_t s) {
+    if (a.nel <= 0) return FEM_OK;
+#define FEM_INT(NPE, T, S, CT, MX) \
+    return launch_integrate_t<NPE, T, S, CT, MX>(a.E, a.nel, a.X, a.c, a.ke, a.thr, a.nflag, s)
+    if (!a.mixed) {
+        if (a.npe == 8) FEM_INT(8, double, double, double, false);
+        FEM_INT(4, double, double, double, false);
+    }
+    if (a.npe == 8) {
+        if (a.xd == FEM_F32 && a.cd == FEM_F32) FEM_INT(8, float, float, float, true);
+        if (a.xd == FEM_F32 && a.cd == FEM_F64) FEM_INT(8, float, float, double, true);
+        if (a.xd == FEM_F64 && a.cd == FEM_F32) FEM_INT(8, float, double, float, true);
+        FEM_INT(8, float, double, double, true);
+    }
+    if (a.xd == FEM_F32 && a.cd == FEM_F32) FEM_INT(4, float, float, float, true);
+    if (a.xd == FEM_F32 && a.cd == FEM_F64) FEM_INT(4, float, float, double, true);
+    if (a.xd == FEM_F64 && a.cd == FEM_F32) FEM_INT(4, float, double, float, true);
+    FEM_INT(4, float, double, double, true);
+#undef FEM_INT
+}
+
+static size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+PatchSmem patch_smem_layout(const Plan &P, bool fused, bool mixed, size_t xsize) {
+    PatchSmem L{};
+    const size_t accsz = mixed ? sizeof(float) : sizeof(double);
+    size_t o = 0;
+    L.acc = o;
+    o = align16(o + (size_t)P.max_acc * accsz);
+    L.hv = o;
+    if (mixed) o = align16(o + (size_t)P.max_own * sizeof(double));
+    L.xs = o;
+    if (fused) o = align16(o + (size_t)P.max_cnodes * 3 * xsize);
+    L.cown = o;
+    o = align16(o + (size_t)P.max_cnodes * sizeof(int32_t));
+    L.roff = o;
+    o = align16(o + (size_t)(P.max_own + 1) * sizeof(int32_t));
+    L.hvf = o;
+    if (mixed) o = align16(o + (size_t)P.max_own);
+    L.total = o;
+    return L;
+}
+
+template <int NPE, typename AccT, typename S, typename CT, bool FUSED, bool MIXED>
+static fem_status launch_patch_t(const PatchArgs &a, cudaStream_t s) {
+    const Plan &P = *a.plan;
+    const PatchSmem L = patch_smem_layout(P, FUSED, MIXED, sizeof(S));
+    int dev = 0, max_optin = 0;
+    FEM_CUDA(cudaGetDevice(&dev));
+    FEM_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (L.total > (size_t)max_optin) {
+        set_error("a patch needs %zu bytes of shared memory (limit %d); lower patch_entries", L.total, max_optin);
+        return FEM_ERR_UNSUPPORTED;
+    }
+    auto f = k_patch<NPE, AccT, S, CT, FUSED, MIXED>;
+    FEM_TRY(set_smem(f, L.total));
+    const int threads = a.threads;
+    int per_sm = 0;
+    FEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, L.total));
+    if (per_sm < 1) {
+        set_error("patch kernel cannot be resident with %d threads and %zu bytes of shared memory", threads, L.total);
+        return FEM_ERR_UNSUPPORTED;
+    }
+    if (a.blocks_per_sm > 0 && a.blocks_per_sm < per_sm) per_sm = a.blocks_per_sm;
+    const int64_t np = a.p1 - a.p0;
+    if (np <= 0) return FEM_OK;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np, (int64_t)num_sms() * per_sm));
+    f<<<grid, threads, L.total, s>>>(P.view(), (const S *)a.X, (const CT *)a.c, (const AccT *)a.ke, (AccT *)a.vals,
+                                     a.thr, a.p0, a.p1, L);
+    FEM_LAUNCHED("k_patch");
+    return FEM_OK;
+}
+
+fem_status launch_patch(const PatchArgs &a, cudaStream_t s) {
+#define FEM_P(NPE, ACC, S, CT, FU, MX) return launch_patch_t<NPE, ACC, S, CT, FU, MX>(a, s)
+    if (!a.mixed) {
+        if (a.fused) {
+            if (a.npe == 8) FEM_P(8, double, double, double, true, false);
+            FEM_P(4, double, double, double, true, false);
+        }
+        if (a.npe == 8) FEM_P(8, double, double, double, false, false);
+        FEM_P(4, double, double, double, false, false);
+    }
+    if (!a.fused) {
+        if (a.npe == 8) FEM_P(8, float, float, float, false, true);
+        FEM_P(4, float, float, float, false, true);
+    }
+    if (a.npe == 8) {
+        if (a.xd == FEM_F32 && a.cd == FEM_F32) FEM_P(8, float, float, float, true, true);
+        if (a.xd == FEM_F32 && a.cd == FEM_F64) FEM_P(8, float, float, double, true, true);
+        if (a.xd == FEM_F64 && a.cd == FEM_F32) FEM_P(8, float, double, float, true, true);
+        FEM_P(8, float, double, double, true, true);
+    }
+    if (a.xd == FEM_F32 && a.cd == FEM_F32) FEM_P(4, float, float, float, true, true);
+    if (a.xd == FEM_F32 && a.cd == FEM_F64) FEM_P(4, float, float, double, true, true);
+    if (a.xd == FEM_F64 && a.cd == FEM_F32) FEM_P(4, float, double, float, true, true);
+    FEM_P(4, float, double, double, true, true);
+#undef FEM_P
+}
+
+}  // namespace fem

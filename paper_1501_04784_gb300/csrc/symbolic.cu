@@ -1,0 +1,763 @@
+// symbolic.cu -- the symbolic phase: validation of E, the node -> element
+// incidence, the lower-CSR pattern of K, the locality order of the nodes and the
+// per-block plan of the numeric kernels.
+//
+// Pattern (Algorithm 1's Mapping and the structure of the sparse conversion,
+// Section 3).  Row i of the lower CSR holds every node j <= i that shares an
+// element with i (explicit zeros included: the pattern is structural, as the
+// nonzero counts of Table 1 are).  It is built row by row, one warp per row, from
+// the elements incident to node i -- the property the paper credits to MILAMIN's
+// sparse_create (no global triplet index arrays) -- so its memory is O(npe * nel)
+// integers instead of a global sort of npe(npe+1)/2 * nel (row, col) keys.
+#include <climits>
+#include <vector>
+
+#include "mesh.cuh"
+
+namespace fem {
+
+static constexpr int TPB = 256;
+
+static unsigned grid_for(int64_t n, int tpb = TPB) {
+    int64_t b = cdiv(n, tpb);
+    const int64_t cap = (int64_t)num_sms() * 32;
+    return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+// ------------------------------------------------------------------ validation
+__global__ void k_validate(const int32_t *__restrict__ E, int64_t nel, int npe, int64_t N,
+                           unsigned long long *bad_index, unsigned long long *bad_repeat) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nel; e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t id[8];
+        for (int a = 0; a < npe; ++a) id[a] = E[e * npe + a];
+        bool bi = false, br = false;
+        for (int a = 0; a < npe; ++a) {
+            if (id[a] < 0 || (int64_t)id[a] >= N) bi = true;
+            for (int b = 0; b < a; ++b)
+                if (id[a] == id[b]) br = true;
+        }
+        if (bi) atomicMin(bad_index, (unsigned long long)e);
+        if (br) atomicMin(bad_repeat, (unsigned long long)e);
+    }
+}
+
+fem_status validate_connectivity(fem_mesh m, cudaStream_t s) {
+    DevBuf<unsigned long long> flags;
+    FEM_TRY(flags.alloc(m->arena, 2, "validation flags"));
+    FEM_CUDA(cudaMemsetAsync(flags.ptr, 0xff, 2 * sizeof(unsigned long long), s));
+    k_validate<<<grid_for(m->n_elems), TPB, 0, s>>>(m->E, m->n_elems, m->npe, m->n_nodes, flags.ptr, flags.ptr + 1);
+    FEM_LAUNCHED("k_validate");
+    unsigned long long h[2];
+    FEM_CUDA(cudaMemcpyAsync(h, flags.ptr, sizeof(h), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    if (h[0] != ~0ull) {
+        set_error("element %llu has a node id outside [0, %lld)", h[0], (long long)m->n_nodes);
+        return FEM_ERR_INDEX;
+    }
+    if (h[1] != ~0ull) {
+        set_error("element %llu repeats a node", h[1]);
+        return FEM_ERR_DEGENERATE;
+    }
+    return FEM_OK;
+}
+
+// ------------------------------------------------------------- locality order
+// Nodes sorted (stably) by the 30-bit Morton code of their coordinates in the
+// mesh's bounding box.  This is a locality heuristic only: any order gives the
+// same K.
+__device__ __forceinline__ unsigned long long ord_key(double v) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double ord_val(unsigned long long k) {
+    unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
+template <typename S>
+__global__ void k_bbox(const S *__restrict__ X, int64_t N, unsigned long long *bb /*6: min xyz, max xyz*/) {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        for (int d = 0; d < 3; ++d) {
+            double v = (double)X[3 * i + d];
+            lo[d] = fmin(lo[d], v);
+            hi[d] = fmax(hi[d], v);
+        }
+    for (int d = 0; d < 3; ++d) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[d] = fmin(lo[d], __shfl_down_sync(0xffffffffu, lo[d], o));
+            hi[d] = fmax(hi[d], __shfl_down_sync(0xffffffffu, hi[d], o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&bb[d], ord_key(lo[d]));
+            atomicMax(&bb[3 + d], ord_key(hi[d]));
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+template <typename S>
+__global__ void k_morton(const S *__restrict__ X, int64_t N, const unsigned long long *bb, uint64_t *keys,
+                         uint32_t *vals) {
+    double lo[3], sc[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = ord_val(bb[d]);
+        double w = ord_val(bb[3 + d]) - lo[d];
+        sc[d] = w > 0 ? 1023.0 / w : 0.0;
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t q[3];
+        for (int d = 0; d < 3; ++d) {
+            double t = ((double)X[3 * i + d] - lo[d]) * sc[d];
+            t = t < 0 ? 0 : (t > 1023 ? 1023 : t);
+            q[d] = (uint32_t)t;
+        }
+        keys[i] = (uint64_t)(spread10(q[0]) | (spread10(q[1]) << 1) | (spread10(q[2]) << 2));
+        vals[i] = (uint32_t)i;
+    }
+}
+
+__global__ void k_iota(int32_t *o, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        o[i] = (int32_t)i;
+}
+
+fem_status build_locality_order(fem_mesh m, const void *X, fem_dtype xd, cudaStream_t s) {
+    const int64_t N = m->n_nodes;
+    FEM_TRY(m->order.alloc(m->arena, N, "node order"));
+    if (!X || !m->opt.locality_order) {
+        k_iota<<<grid_for(N), TPB, 0, s>>>(m->order.ptr, N);
+        FEM_LAUNCHED("k_iota");
+        return FEM_OK;
+    }
+    DevBuf<unsigned long long> bb;
+    DevBuf<uint64_t> keys, alt;
+    DevBuf<uint32_t> alt_vals;
+    DevBuf<int64_t> hist;
+    FEM_TRY(bb.alloc(m->arena, 6, "bbox"));
+    FEM_TRY(keys.alloc(m->arena, N, "morton keys"));
+    FEM_TRY(alt.alloc(m->arena, N, "morton keys'"));
+    FEM_TRY(alt_vals.alloc(m->arena, N, "morton vals'"));
+    FEM_TRY(hist.alloc(m->arena, radix_hist_elems(N), "radix histogram"));
+    unsigned long long init[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
+    FEM_CUDA(cudaMemcpyAsync(bb.ptr, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    uint32_t *vals = reinterpret_cast<uint32_t *>(m->order.ptr);
+    if (xd == FEM_F64) {
+        k_bbox<double><<<grid_for(N), TPB, 0, s>>>((const double *)X, N, bb.ptr);
+        FEM_LAUNCHED("k_bbox");
+        k_morton<double><<<grid_for(N), TPB, 0, s>>>((const double *)X, N, bb.ptr, keys.ptr, vals);
+    } else {
+        k_bbox<float><<<grid_for(N), TPB, 0, s>>>((const float *)X, N, bb.ptr);
+        FEM_LAUNCHED("k_bbox");
+        k_morton<float><<<grid_for(N), TPB, 0, s>>>((const float *)X, N, bb.ptr, keys.ptr, vals);
+    }
+    FEM_LAUNCHED("k_morton");
+    FEM_TRY(radix_sort_u64(keys.ptr, vals, N, 30, alt.ptr, alt_vals.ptr, hist.ptr, s));
+    FEM_CUDA(cudaStreamSynchronize(s));  // temporaries are freed on return
+    return FEM_OK;
+}
+
+// ------------------------------------------------------------------ incidence
+__global__ void k_degree(const int32_t *__restrict__ E, int64_t n_ent, unsigned long long *deg) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_ent; t += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&deg[E[t]], 1ull);
+}
+
+__global__ void k_inc_fill(const int32_t *__restrict__ E, int64_t n_ent, int npe, const int64_t *inc_ptr,
+                           unsigned int *cursor, int32_t *inc_elem) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_ent; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = E[t];
+        const unsigned k = atomicAdd(&cursor[g], 1u);
+        inc_elem[inc_ptr[g] + k] = (int32_t)(t / npe);
+    }
+}
+
+// Insertion sort of each node's (short) list of incident elements, so that the
+// incidence does not depend on the order in which the atomics were served.
+__global__ void k_inc_sort(const int64_t *inc_ptr, int32_t *inc_elem, int64_t N) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < N; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = inc_ptr[g], e = inc_ptr[g + 1];
+        for (int64_t i = b + 1; i < e; ++i) {
+            const int32_t v = inc_elem[i];
+            int64_t j = i - 1;
+            while (j >= b && inc_elem[j] > v) {
+                inc_elem[j + 1] = inc_elem[j];
+                --j;
+            }
+            inc_elem[j + 1] = v;
+        }
+    }
+}
+
+__global__ void k_max_deg(const int64_t *inc_ptr, int64_t N, unsigned long long *mx) {
+    unsigned long long m = 0;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < N; g += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (unsigned long long)(inc_ptr[g + 1] - inc_ptr[g]));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(mx, m);
+}
+
+// ------------------------------------------------------------- row pattern
+// One warp per row i.  The warp lists the nodes j <= i of every element incident
+// to i (cap >= max degree * npe candidates, in shared memory), drops repeats, and
+// ranks each distinct j among the others: that rank is its position in the row.
+// count pass: cnt[i] = number of distinct j; fill pass: col[rowptr[i] + rank] = j.
+template <int NPE>
+__global__ void k_row_pattern(const int32_t *__restrict__ E, const int64_t *__restrict__ inc_ptr,
+                              const int32_t *__restrict__ inc_elem, int64_t N, int cap, int64_t *cnt,
+                              const int64_t *__restrict__ rowptr, int32_t *col) {
+    extern __shared__ int32_t pat_buf[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    int32_t *buf = pat_buf + (size_t)wib * cap;
+    for (int64_t i = (int64_t)blockIdx.x * wpb + wib; i < N; i += (int64_t)gridDim.x * wpb) {
+        const int64_t b0 = inc_ptr[i];
+        const int n = (int)(inc_ptr[i + 1] - b0) * NPE;
+        for (int t = lane; t < n; t += 32) {
+            const int32_t e = inc_elem[b0 + t / NPE];
+            const int32_t g = E[(int64_t)e * NPE + t % NPE];
+            buf[t] = (g <= i) ? g : INT_MAX;
+        }
+        __syncwarp();
+        // mark repeats (keep the first occurrence); items of this lane: t = lane + 32 k
+        unsigned long long dup = 0;
+        for (int t = lane, k = 0; t < n; t += 32, ++k) {
+            const int32_t v = buf[t];
+            bool d = (v == INT_MAX);
+            for (int u = 0; u < t && !d; ++u) d = (buf[u] == v);
+            if (d) dup |= 1ull << k;
+        }
+        __syncwarp();
+        for (int t = lane, k = 0; t < n; t += 32, ++k)
+            if (dup >> k & 1ull) buf[t] = INT_MAX;
+        __syncwarp();
+        int mine = 0;
+        for (int t = lane; t < n; t += 32) {
+            const int32_t v = buf[t];
+            if (v == INT_MAX) continue;
+            ++mine;
+            if (col) {
+                int rank = 0;
+                for (int u = 0; u < n; ++u) rank += (buf[u] < v);
+                col[rowptr[i] + rank] = v;
+            }
+        }
+        if (cnt) {
+            for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
+            if (lane == 0) cnt[i] = mine;
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_row_len_max(const int64_t *rowptr, int64_t N, unsigned long long *mx) {
+    unsigned long long m = 0;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < N; g += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (unsigned long long)(rowptr[g + 1] - rowptr[g]));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(mx, m);
+}
+
+// ------------------------------------------------------------------- patches
+// len_in_order[k] = length of row order[k]
+__global__ void k_len_in_order(const int32_t *order, const int64_t *rowptr, int64_t N, int64_t *len) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = order[k];
+        len[k] = rowptr[g + 1] - rowptr[g];
+    }
+}
+
+// first index with pre[k] >= p * cap (lower bound), p = 0..npatch-1; ptr[npatch] = N
+__global__ void k_patch_bounds(const int64_t *pre, int64_t N, int64_t cap, int64_t npatch, int64_t *ptr) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p <= npatch; p += (int64_t)gridDim.x * blockDim.x) {
+        if (p == npatch) {
+            ptr[p] = N;
+            continue;
+        }
+        const int64_t target = p * cap;
+        int64_t lo = 0, hi = N;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (pre[mid] < target) lo = mid + 1; else hi = mid;
+        }
+        ptr[p] = (p == 0) ? 0 : lo;
+    }
+}
+
+__global__ void k_patch_nodes(const int32_t *order, const int64_t *pre, const int64_t *pn_ptr, int64_t N,
+                              int64_t cap, int64_t npatch, const int64_t *rowptr, const int64_t *inc_ptr, int hv_thr,
+                              int32_t *node_patch, int32_t *own_idx, int32_t *own_row, int64_t *own_rowptr,
+                              int32_t *own_acc, uint8_t *own_hv) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p = pre[k] / cap;
+        if (p > npatch - 1) p = npatch - 1;
+        // a row that starts exactly at a boundary may have been put in the next patch by the bound search
+        while (p > 0 && pn_ptr[p] > k) --p;
+        while (p < npatch - 1 && pn_ptr[p + 1] <= k) ++p;
+        const int32_t g = order[k];
+        node_patch[g] = (int32_t)p;
+        own_idx[g] = (int32_t)(k - pn_ptr[p]);
+        own_row[k] = g;
+        own_rowptr[k] = rowptr[g];
+        own_acc[k] = (int32_t)(pre[k] - pre[pn_ptr[p]]);
+        own_hv[k] = (inc_ptr[g + 1] - inc_ptr[g]) > hv_thr ? 1 : 0;
+    }
+}
+
+__global__ void k_patch_acc(const int64_t *pre, const int64_t *pn_ptr, int64_t npatch, int32_t *acc) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npatch; p += (int64_t)gridDim.x * blockDim.x)
+        acc[p] = (int32_t)(pre[pn_ptr[p + 1]] - pre[pn_ptr[p]]);
+}
+
+// ------------------------------------------------------------- closure lists
+__global__ void k_closure_pairs(const int32_t *__restrict__ E, int64_t n_ent, int npe, const int32_t *node_patch,
+                                uint64_t *keys) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_ent; t += (int64_t)gridDim.x * blockDim.x)
+        keys[t] = ((uint64_t)(uint32_t)node_patch[E[t]] << 32) | (uint64_t)(t / npe);
+}
+
+__global__ void k_unique_flags(const uint64_t *keys, int64_t n, int64_t *flags) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+}
+
+__global__ void k_unique_compact(const uint64_t *keys, int64_t n, const int64_t *pos, uint64_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (i == 0 || keys[i] != keys[i - 1]) out[pos[i]] = keys[i];
+}
+
+// ptr[p] = first index whose key >> shift >= p (keys sorted); ptr[np] = n
+__global__ void k_segment_ptr(const uint64_t *keys, int64_t n, int shift, int64_t np, int64_t *ptr) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p <= np; p += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = n;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if ((keys[mid] >> shift) < (uint64_t)p) lo = mid + 1; else hi = mid;
+        }
+        ptr[p] = lo;
+    }
+}
+
+// Greedy colouring of a patch's closure (elements in ascending id): an element
+// takes the lowest colour not yet used by an element sharing an owned node with
+// it.  Owned-node colour sets are 128-bit masks in shared memory; the
+// element -> owned-node table is staged chunk by chunk so that the serial loop
+// runs from shared memory.
+static constexpr int COLOR_CHUNK = 2048;
+
+template <int NPE>
+__global__ void k_color(const uint64_t *ckeys, const int64_t *pe_ptr, const int64_t *pn_ptr, const int32_t *E,
+                        const int32_t *node_patch, const int32_t *own_idx, int64_t npatch, uint8_t *color_out,
+                        int *max_color) {
+    extern __shared__ unsigned long long col_smem[];
+    for (int64_t p = blockIdx.x; p < npatch; p += gridDim.x) {
+        const int nown = (int)(pn_ptr[p + 1] - pn_ptr[p]);
+        unsigned long long *mask = col_smem;                                // [2 * nown]
+        int16_t *tab = reinterpret_cast<int16_t *>(col_smem + 2 * nown);    // [COLOR_CHUNK * NPE]
+        for (int i = threadIdx.x; i < 2 * nown; i += blockDim.x) mask[i] = 0;
+        const int64_t b = pe_ptr[p], n = pe_ptr[p + 1] - b;
+        int local_max = -1;
+        for (int64_t c0 = 0; c0 < n; c0 += COLOR_CHUNK) {
+            const int cn = (int)min((int64_t)COLOR_CHUNK, n - c0);
+            __syncthreads();
+            for (int t = threadIdx.x; t < cn * NPE; t += blockDim.x) {
+                const int64_t e = (int64_t)(uint32_t)ckeys[b + c0 + t / NPE];
+                const int32_t g = E[e * NPE + t % NPE];
+                tab[t] = node_patch[g] == (int32_t)p ? (int16_t)own_idx[g] : (int16_t)-1;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int i = 0; i < cn; ++i) {
+                    unsigned long long m0 = 0, m1 = 0;
+#pragma unroll
+                    for (int a = 0; a < NPE; ++a) {
+                        const int o = tab[i * NPE + a];
+                        if (o >= 0) {
+                            m0 |= mask[2 * o];
+                            m1 |= mask[2 * o + 1];
+                        }
+                    }
+                    int c;
+                    if (~m0) c = __ffsll((long long)~m0) - 1;
+                    else if (~m1) c = 64 + __ffsll((long long)~m1) - 1;
+                    else c = 255;
+                    color_out[b + c0 + i] = (uint8_t)c;
+                    if (c < 128) {
+#pragma unroll
+                        for (int a = 0; a < NPE; ++a) {
+                            const int o = tab[i * NPE + a];
+                            if (o >= 0) mask[2 * o + (c >> 6)] |= 1ull << (c & 63);
+                        }
+                    }
+                    local_max = max(local_max, c);
+                }
+            }
+        }
+        if (threadIdx.x == 0) atomicMax(max_color, local_max);
+        __syncthreads();
+    }
+}
+
+__global__ void k_color_keys(const uint64_t *ckeys, const uint8_t *color, int64_t n, uint64_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = ckeys[i];
+        out[i] = ((k >> 32) << 40) | ((uint64_t)color[i] << 32) | (k & 0xffffffffull);
+    }
+}
+
+__global__ void k_cnode_pairs(const uint64_t *ckeys, int64_t nce, int npe, const int32_t *E, uint64_t *keys) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nce * npe; t += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = ckeys[t / npe];
+        const uint64_t p = k >> 40;
+        const int64_t e = (int64_t)(k & 0xffffffffull);
+        keys[t] = (p << 32) | (uint64_t)(uint32_t)E[e * npe + t % npe];
+    }
+}
+
+__global__ void k_cnode_own(const uint64_t *cn_keys, int64_t ncn, const int32_t *node_patch, const int32_t *own_idx,
+                            int32_t *gid, int32_t *own) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ncn; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = cn_keys[j];
+        const int32_t g = (int32_t)(k & 0xffffffffull);
+        const int32_t p = (int32_t)(k >> 32);
+        gid[j] = g;
+        own[j] = node_patch[g] == p ? own_idx[g] : -1;
+    }
+}
+
+// Per closure element: id, colour, closure-local node indices (binary search in
+// the patch's sorted closure-node list) and, for every packed pair (a, b), the
+// position of min(g_a, g_b) within row max(g_a, g_b) of the pattern.
+template <int NPE>
+__global__ void k_celem_fill(const uint64_t *ckeys, int64_t nce, const int32_t *__restrict__ E,
+                             const uint64_t *cn_keys, const int64_t *pc_ptr, const int64_t *__restrict__ rowptr,
+                             const int32_t *__restrict__ col, int pos_stride, int32_t *celem_id, uint8_t *celem_color,
+                             uint16_t *lnode, uint8_t *pos) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nce; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = ckeys[i];
+        const uint64_t p = k >> 40;
+        const int64_t e = (int64_t)(k & 0xffffffffull);
+        celem_id[i] = (int32_t)e;
+        celem_color[i] = (uint8_t)((k >> 32) & 0xff);
+        int32_t g[NPE];
+        const int64_t cb = pc_ptr[p], ce = pc_ptr[p + 1];
+#pragma unroll
+        for (int a = 0; a < NPE; ++a) {
+            g[a] = E[e * NPE + a];
+            const uint64_t key = (p << 32) | (uint64_t)(uint32_t)g[a];
+            int64_t lo = cb, hi = ce;
+            while (lo < hi) {
+                int64_t mid = (lo + hi) >> 1;
+                if (cn_keys[mid] < key) lo = mid + 1; else hi = mid;
+            }
+            lnode[i * NPE + a] = (uint16_t)(lo - cb);
+        }
+        int q = 0;
+#pragma unroll
+        for (int a = 0; a < NPE; ++a)
+#pragma unroll
+            for (int b = 0; b <= a; ++b, ++q) {
+                const int32_t r = max(g[a], g[b]), cv = min(g[a], g[b]);
+                int64_t lo = rowptr[r], hi = rowptr[r + 1];
+                const int64_t r0 = lo;
+                while (lo < hi) {
+                    int64_t mid = (lo + hi) >> 1;
+                    if (col[mid] < cv) lo = mid + 1; else hi = mid;
+                }
+                pos[i * pos_stride + q] = (uint8_t)(lo - r0);
+            }
+    }
+}
+
+// --------------------------------------------------------------- orchestration
+static int bits_for(int64_t v) {
+    int b = 1;
+    while ((v >> b) != 0) ++b;
+    return b;
+}
+
+template <typename T>
+static fem_status read_scalar(const T *dev, T *host, cudaStream_t s) {
+    FEM_CUDA(cudaMemcpyAsync(host, dev, sizeof(T), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    return FEM_OK;
+}
+
+static fem_status sort_unique(Arena &ar, DevBuf<uint64_t> &keys, int64_t n, int key_bits, DevBuf<uint64_t> &out,
+                              int64_t *n_out, cudaStream_t s) {
+    DevBuf<uint64_t> alt;
+    DevBuf<int64_t> hist, flags;
+    FEM_TRY(alt.alloc(ar, n, "sort scratch"));
+    FEM_TRY(hist.alloc(ar, radix_hist_elems(n), "sort histogram"));
+    FEM_TRY(radix_sort_u64(keys.ptr, nullptr, n, key_bits, alt.ptr, nullptr, hist.ptr, s));
+    hist.free();
+    FEM_TRY(flags.alloc(ar, n + 1, "unique flags"));
+    k_unique_flags<<<grid_for(n), TPB, 0, s>>>(keys.ptr, n, flags.ptr);
+    FEM_LAUNCHED("k_unique_flags");
+    DevBuf<int64_t> tmp;
+    FEM_TRY(tmp.alloc(ar, scan_tmp_elems(n + 1), "scan scratch"));
+    FEM_TRY(scan_exclusive_i64(flags.ptr, flags.ptr, n, true, tmp.ptr, s));
+    FEM_TRY(read_scalar(flags.ptr + n, n_out, s));
+    alt.free();
+    FEM_TRY(out.alloc(ar, *n_out, "unique keys"));
+    k_unique_compact<<<grid_for(n), TPB, 0, s>>>(keys.ptr, n, flags.ptr, out.ptr);
+    FEM_LAUNCHED("k_unique_compact");
+    return FEM_OK;
+}
+
+fem_status build_pattern_and_plan(fem_mesh m, cudaStream_t s) {
+    Arena &ar = m->arena;
+    const int64_t N = m->n_nodes, nel = m->n_elems, npe = m->npe, n_ent = nel * npe;
+
+    // ---- node -> element incidence
+    FEM_TRY(m->inc_ptr.alloc(ar, N + 1, "incidence pointers"));
+    FEM_TRY(m->inc_elem.alloc(ar, n_ent, "incidence lists"));
+    {
+        DevBuf<int64_t> deg, tmp;
+        DevBuf<unsigned int> cursor;
+        FEM_TRY(deg.alloc(ar, N + 1, "degrees"));
+        FEM_CUDA(cudaMemsetAsync(deg.ptr, 0, (N + 1) * sizeof(int64_t), s));
+        k_degree<<<grid_for(n_ent), TPB, 0, s>>>(m->E, n_ent, reinterpret_cast<unsigned long long *>(deg.ptr));
+        FEM_LAUNCHED("k_degree");
+        FEM_TRY(tmp.alloc(ar, scan_tmp_elems(N + 1), "scan scratch"));
+        FEM_TRY(scan_exclusive_i64(deg.ptr, m->inc_ptr.ptr, N, true, tmp.ptr, s));
+        deg.free();
+        FEM_TRY(cursor.alloc(ar, N, "incidence cursors"));
+        FEM_CUDA(cudaMemsetAsync(cursor.ptr, 0, N * sizeof(unsigned int), s));
+        k_inc_fill<<<grid_for(n_ent), TPB, 0, s>>>(m->E, n_ent, (int)npe, m->inc_ptr.ptr, cursor.ptr, m->inc_elem.ptr);
+        FEM_LAUNCHED("k_inc_fill");
+        k_inc_sort<<<grid_for(N), TPB, 0, s>>>(m->inc_ptr.ptr, m->inc_elem.ptr, N);
+        FEM_LAUNCHED("k_inc_sort");
+    }
+    unsigned long long max_deg = 0;
+    {
+        DevBuf<unsigned long long> mx;
+        FEM_TRY(mx.alloc(ar, 1, "max"));
+        FEM_CUDA(cudaMemsetAsync(mx.ptr, 0, sizeof(unsigned long long), s));
+        k_max_deg<<<grid_for(N), TPB, 0, s>>>(m->inc_ptr.ptr, N, mx.ptr);
+        FEM_LAUNCHED("k_max_deg");
+        FEM_TRY(read_scalar(mx.ptr, &max_deg, s));
+    }
+    const int cap = (int)(max_deg * npe);
+    if (cap > 64 * 32) {
+        set_error("a node belongs to %llu elements; at most %d are supported", max_deg, (int)(64 * 32 / npe));
+        return FEM_ERR_UNSUPPORTED;
+    }
+
+    // ---- lower-CSR pattern, one warp per row
+    FEM_TRY(m->rowptr.alloc(ar, N + 1, "rowptr"));
+    {
+        DevBuf<int64_t> cnt, tmp;
+        FEM_TRY(cnt.alloc(ar, N + 1, "row counts"));
+        const int wpb = 8;
+        const size_t smem = (size_t)wpb * (cap > 0 ? cap : 1) * sizeof(int32_t);
+        const unsigned grid = (unsigned)std::min<int64_t>(cdiv(N, wpb), (int64_t)num_sms() * 64);
+        if (npe == 8)
+            k_row_pattern<8><<<grid, wpb * 32, smem, s>>>(m->E, m->inc_ptr.ptr, m->inc_elem.ptr, N, cap, cnt.ptr,
+                                                          nullptr, nullptr);
+        else
+            k_row_pattern<4><<<grid, wpb * 32, smem, s>>>(m->E, m->inc_ptr.ptr, m->inc_elem.ptr, N, cap, cnt.ptr,
+                                                          nullptr, nullptr);
+        FEM_LAUNCHED("k_row_pattern(count)");
+        FEM_TRY(tmp.alloc(ar, scan_tmp_elems(N + 1), "scan scratch"));
+        FEM_TRY(scan_exclusive_i64(cnt.ptr, m->rowptr.ptr, N, true, tmp.ptr, s));
+        FEM_TRY(read_scalar(m->rowptr.ptr + N, &m->nnz, s));
+        FEM_TRY(m->col.alloc(ar, m->nnz, "col"));
+        if (npe == 8)
+            k_row_pattern<8><<<grid, wpb * 32, smem, s>>>(m->E, m->inc_ptr.ptr, m->inc_elem.ptr, N, cap, nullptr,
+                                                          m->rowptr.ptr, m->col.ptr);
+        else
+            k_row_pattern<4><<<grid, wpb * 32, smem, s>>>(m->E, m->inc_ptr.ptr, m->inc_elem.ptr, N, cap, nullptr,
+                                                          m->rowptr.ptr, m->col.ptr);
+        FEM_LAUNCHED("k_row_pattern(fill)");
+        DevBuf<unsigned long long> mx;
+        FEM_TRY(mx.alloc(ar, 1, "max"));
+        FEM_CUDA(cudaMemsetAsync(mx.ptr, 0, sizeof(unsigned long long), s));
+        k_row_len_max<<<grid_for(N), TPB, 0, s>>>(m->rowptr.ptr, N, mx.ptr);
+        FEM_LAUNCHED("k_row_len_max");
+        unsigned long long ml = 0;
+        FEM_TRY(read_scalar(mx.ptr, &ml, s));
+        m->max_row_len = (int)ml;
+        if (ml > 255) {
+            set_error("a row of K has %llu lower entries; at most 255 are supported", ml);
+            return FEM_ERR_UNSUPPORTED;
+        }
+    }
+
+    // ---- patches of consecutive nodes in locality order
+    Plan &P = m->plan;
+    int64_t cap_entries = m->opt.patch_entries > 0 ? m->opt.patch_entries : 8192;
+    if (cap_entries < 2 * (int64_t)m->max_row_len) cap_entries = 2 * (int64_t)m->max_row_len;
+    const int64_t cap_eff = cap_entries - m->max_row_len;
+    DevBuf<int64_t> pre;
+    {
+        DevBuf<int64_t> len, tmp;
+        FEM_TRY(len.alloc(ar, N + 1, "row lengths"));
+        FEM_TRY(pre.alloc(ar, N + 1, "row length prefix"));
+        k_len_in_order<<<grid_for(N), TPB, 0, s>>>(m->order.ptr, m->rowptr.ptr, N, len.ptr);
+        FEM_LAUNCHED("k_len_in_order");
+        FEM_TRY(tmp.alloc(ar, scan_tmp_elems(N + 1), "scan scratch"));
+        FEM_TRY(scan_exclusive_i64(len.ptr, pre.ptr, N, true, tmp.ptr, s));
+    }
+    P.n_patches = m->nnz > 0 ? cdiv(m->nnz, cap_eff) : 1;
+    const int64_t npatch = P.n_patches;
+    if (npatch >= (1ll << 23)) {
+        set_error("too many patches (%lld)", (long long)npatch);
+        return FEM_ERR_UNSUPPORTED;
+    }
+    FEM_TRY(P.patch_node_ptr.alloc(ar, npatch + 1, "patch node ptr"));
+    k_patch_bounds<<<grid_for(npatch + 1), TPB, 0, s>>>(pre.ptr, N, cap_eff, npatch, P.patch_node_ptr.ptr);
+    FEM_LAUNCHED("k_patch_bounds");
+    FEM_TRY(P.node_patch.alloc(ar, N, "node patch"));
+    FEM_TRY(P.own_idx.alloc(ar, N, "own index"));
+    FEM_TRY(P.own_row.alloc(ar, N, "own row"));
+    FEM_TRY(P.own_rowptr.alloc(ar, N, "own rowptr"));
+    FEM_TRY(P.own_acc.alloc(ar, N, "own acc"));
+    FEM_TRY(P.own_hv.alloc(ar, N, "own hv"));
+    FEM_TRY(P.patch_acc.alloc(ar, npatch, "patch acc"));
+    const int hv_thr = m->opt.valence_threshold;
+    k_patch_nodes<<<grid_for(N), TPB, 0, s>>>(m->order.ptr, pre.ptr, P.patch_node_ptr.ptr, N, cap_eff, npatch,
+                                              m->rowptr.ptr, m->inc_ptr.ptr, hv_thr, P.node_patch.ptr, P.own_idx.ptr,
+                                              P.own_row.ptr, P.own_rowptr.ptr, P.own_acc.ptr, P.own_hv.ptr);
+    FEM_LAUNCHED("k_patch_nodes");
+    k_patch_acc<<<grid_for(npatch), TPB, 0, s>>>(pre.ptr, P.patch_node_ptr.ptr, npatch, P.patch_acc.ptr);
+    FEM_LAUNCHED("k_patch_acc");
+    pre.free();
+    const int pbits = bits_for(npatch);
+
+    // ---- closure elements of each patch: unique (patch, element) pairs
+    DevBuf<uint64_t> ckeys;
+    int64_t nce = 0;
+    {
+        DevBuf<uint64_t> pairs;
+        FEM_TRY(pairs.alloc(ar, n_ent, "closure pairs"));
+        k_closure_pairs<<<grid_for(n_ent), TPB, 0, s>>>(m->E, n_ent, (int)npe, P.node_patch.ptr, pairs.ptr);
+        FEM_LAUNCHED("k_closure_pairs");
+        FEM_TRY(sort_unique(ar, pairs, n_ent, 32 + pbits, ckeys, &nce, s));
+    }
+    P.total_celems = nce;
+    FEM_TRY(P.patch_elem_ptr.alloc(ar, npatch + 1, "patch elem ptr"));
+    k_segment_ptr<<<grid_for(npatch + 1), TPB, 0, s>>>(ckeys.ptr, nce, 32, npatch, P.patch_elem_ptr.ptr);
+    FEM_LAUNCHED("k_segment_ptr(elems)");
+
+    // host copies of the patch pointers for sizes
+    std::vector<int64_t> h_pn(npatch + 1), h_pe(npatch + 1), h_pc(npatch + 1);
+    FEM_CUDA(cudaMemcpyAsync(h_pn.data(), P.patch_node_ptr.ptr, (npatch + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaMemcpyAsync(h_pe.data(), P.patch_elem_ptr.ptr, (npatch + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    P.max_own = 0;
+    P.max_celems = 0;
+    for (int64_t p = 0; p < npatch; ++p) {
+        P.max_own = std::max(P.max_own, h_pn[p + 1] - h_pn[p]);
+        P.max_celems = std::max(P.max_celems, h_pe[p + 1] - h_pe[p]);
+    }
+    if (P.max_own > 32767) {
+        set_error("a patch owns %lld rows; at most 32767 are supported", (long long)P.max_own);
+        return FEM_ERR_UNSUPPORTED;
+    }
+
+    // ---- colouring of each closure, then order each closure by (colour, element)
+    {
+        DevBuf<uint8_t> color;
+        DevBuf<int> mxc;
+        FEM_TRY(color.alloc(ar, nce, "colours"));
+        FEM_TRY(mxc.alloc(ar, 1, "max colour"));
+        FEM_CUDA(cudaMemsetAsync(mxc.ptr, 0, sizeof(int), s));
+        const size_t smem = (size_t)2 * P.max_own * sizeof(unsigned long long) + (size_t)COLOR_CHUNK * npe * sizeof(int16_t);
+        const unsigned grid = (unsigned)std::min<int64_t>(npatch, (int64_t)num_sms() * 8);
+        if (npe == 8) {
+            FEM_CUDA(cudaFuncSetAttribute(k_color<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_color<8><<<grid, 128, smem, s>>>(ckeys.ptr, P.patch_elem_ptr.ptr, P.patch_node_ptr.ptr, m->E,
+                                               P.node_patch.ptr, P.own_idx.ptr, npatch, color.ptr, mxc.ptr);
+        } else {
+            FEM_CUDA(cudaFuncSetAttribute(k_color<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_color<4><<<grid, 128, smem, s>>>(ckeys.ptr, P.patch_elem_ptr.ptr, P.patch_node_ptr.ptr, m->E,
+                                               P.node_patch.ptr, P.own_idx.ptr, npatch, color.ptr, mxc.ptr);
+        }
+        FEM_LAUNCHED("k_color");
+        int h_mxc = 0;
+        FEM_TRY(read_scalar(mxc.ptr, &h_mxc, s));
+        if (h_mxc >= 128) {
+            set_error("the closure colouring needs more than 128 colours");
+            return FEM_ERR_UNSUPPORTED;
+        }
+        P.n_colors = h_mxc + 1;
+        DevBuf<uint64_t> ck2, alt;
+        DevBuf<int64_t> hist;
+        FEM_TRY(ck2.alloc(ar, nce, "closure keys"));
+        k_color_keys<<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, color.ptr, nce, ck2.ptr);
+        FEM_LAUNCHED("k_color_keys");
+        color.free();
+        ckeys.free();
+        FEM_TRY(alt.alloc(ar, nce, "sort scratch"));
+        FEM_TRY(hist.alloc(ar, radix_hist_elems(nce), "sort histogram"));
+        FEM_TRY(radix_sort_u64(ck2.ptr, nullptr, nce, 40 + pbits, alt.ptr, nullptr, hist.ptr, s));
+        FEM_CUDA(cudaStreamSynchronize(s));
+        std::swap(ckeys.ptr, ck2.ptr);
+        std::swap(ckeys.n, ck2.n);
+        std::swap(ckeys.arena, ck2.arena);
+    }
+
+    // ---- closure nodes of each patch
+    DevBuf<uint64_t> cnkeys;
+    int64_t ncn = 0;
+    {
+        DevBuf<uint64_t> pairs;
+        FEM_TRY(pairs.alloc(ar, nce * npe, "closure node pairs"));
+        k_cnode_pairs<<<grid_for(nce * npe), TPB, 0, s>>>(ckeys.ptr, nce, (int)npe, m->E, pairs.ptr);
+        FEM_LAUNCHED("k_cnode_pairs");
+        FEM_TRY(sort_unique(ar, pairs, nce * npe, 32 + pbits, cnkeys, &ncn, s));
+    }
+    P.total_cnodes = ncn;
+    FEM_TRY(P.patch_cnode_ptr.alloc(ar, npatch + 1, "patch cnode ptr"));
+    k_segment_ptr<<<grid_for(npatch + 1), TPB, 0, s>>>(cnkeys.ptr, ncn, 32, npatch, P.patch_cnode_ptr.ptr);
+    FEM_LAUNCHED("k_segment_ptr(cnodes)");
+    FEM_TRY(P.cnode_gid.alloc(ar, ncn, "cnode gid"));
+    FEM_TRY(P.cnode_own.alloc(ar, ncn, "cnode own"));
+    k_cnode_own<<<grid_for(ncn), TPB, 0, s>>>(cnkeys.ptr, ncn, P.node_patch.ptr, P.own_idx.ptr, P.cnode_gid.ptr,
+                                              P.cnode_own.ptr);
+    FEM_LAUNCHED("k_cnode_own");
+
+    // ---- per closure element data
+    P.pos_stride = (int)((m->np + 3) / 4 * 4);
+    FEM_TRY(P.celem_id.alloc(ar, nce, "celem id"));
+    FEM_TRY(P.celem_color.alloc(ar, nce, "celem colour"));
+    FEM_TRY(P.celem_lnode.alloc(ar, nce * npe, "celem local nodes"));
+    FEM_TRY(P.celem_pos.alloc(ar, nce * P.pos_stride, "celem positions"));
+    FEM_CUDA(cudaMemsetAsync(P.celem_pos.ptr, 0, nce * P.pos_stride, s));
+    if (npe == 8)
+        k_celem_fill<8><<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, nce, m->E, cnkeys.ptr, P.patch_cnode_ptr.ptr,
+                                                      m->rowptr.ptr, m->col.ptr, P.pos_stride, P.celem_id.ptr,
+                                                      P.celem_color.ptr, P.celem_lnode.ptr, P.celem_pos.ptr);
+    else
+        k_celem_fill<4><<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, nce, m->E, cnkeys.ptr, P.patch_cnode_ptr.ptr,
+                                                      m->rowptr.ptr, m->col.ptr, P.pos_stride, P.celem_id.ptr,
+                                                      P.celem_color.ptr, P.celem_lnode.ptr, P.celem_pos.ptr);
+    FEM_LAUNCHED("k_celem_fill");
+
+    FEM_CUDA(cudaMemcpyAsync(h_pc.data(), P.patch_cnode_ptr.ptr, (npatch + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    std::vector<int32_t> h_acc(npatch);
+    FEM_CUDA(cudaMemcpyAsync(h_acc.data(), P.patch_acc.ptr, npatch * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    P.max_cnodes = 0;
+    P.max_acc = 0;
+    for (int64_t p = 0; p < npatch; ++p) {
+        P.max_cnodes = std::max(P.max_cnodes, h_pc[p + 1] - h_pc[p]);
+        P.max_acc = std::max(P.max_acc, (int64_t)h_acc[p]);
+    }
+    if (P.max_cnodes > 65535) {
+        set_error("a patch touches %lld nodes; at most 65535 are supported", (long long)P.max_cnodes);
+        return FEM_ERR_UNSUPPORTED;
+    }
+    m->has_pattern = true;
+    return FEM_OK;
+}
+
+}  // namespace fem

@@ -1,0 +1,186 @@
+"""Thin binding of libfem for torch tensors.
+
+Every method is one C-ABI call: it checks tensor devices and dtypes, passes
+``data_ptr()`` and the current CUDA stream, and raises ``FemError`` on a
+non-OK status.  All arithmetic runs in the library's CUDA kernels.  PyTorch
+provides device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import abi
+
+_DT = {torch.float32: abi.FEM_F32, torch.float64: abi.FEM_F64}
+_PREC = {"fp64": abi.FEM_FP64, "mixed": abi.FEM_MIXED}
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, name: str, dtype=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _prec(prec: str) -> int:
+    if prec not in _PREC:
+        raise ValueError("prec must be 'fp64' or 'mixed'")
+    return _PREC[prec]
+
+
+def value_dtype(prec: str):
+    return torch.float64 if prec == "fp64" else torch.float32
+
+
+def default_options() -> abi.fem_options:
+    o = abi.fem_options()
+    abi.load().fem_options_default(ctypes.byref(o))
+    return o
+
+
+def launch_count(reset: bool = False) -> int:
+    return int(abi.load().fem_launch_count(1 if reset else 0))
+
+
+class Mesh:
+    """A mesh handle: E (int32 [n_elems, npe] on the GPU) plus the cached pattern."""
+
+    def __init__(self, E: torch.Tensor, n_nodes: int, X: torch.Tensor | None = None, options=None, stream=None,
+                 **opts):
+        L = abi.load()
+        if E.dim() != 2 or E.shape[1] not in (4, 8):
+            raise ValueError("E must be [n_elems, 8] or [n_elems, 4]")
+        self.E = E
+        self.npe = int(E.shape[1])
+        self.np = self.npe * (self.npe + 1) // 2
+        self.n_nodes = int(n_nodes)
+        self.n_elems = int(E.shape[0])
+        o = options if options is not None else default_options()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.options = o
+        h = ctypes.c_void_p()
+        xp = _dev(X, "X") if X is not None else None
+        xd = _DT.get(X.dtype, abi.FEM_F64) if X is not None else abi.FEM_F64
+        abi.check(L.fem_mesh_create(ctypes.byref(h), self.npe, self.n_nodes, self.n_elems, _dev(E, "E", torch.int32),
+                                    xp, xd, ctypes.byref(o), _stream(stream)))
+        self._h = h
+        self.nnz = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            abi.load().fem_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- symbolic
+    def pattern(self, stream=None) -> int:
+        n = ctypes.c_int64()
+        abi.check(abi.load().fem_pattern(self._h, ctypes.byref(n), _stream(stream)))
+        self.nnz = int(n.value)
+        return self.nnz
+
+    def get_pattern(self, stream=None):
+        if self.nnz is None:
+            self.pattern(stream)
+        rowptr = torch.empty(self.n_nodes + 1, dtype=torch.int64, device=self.E.device)
+        col = torch.empty(max(self.nnz, 1), dtype=torch.int32, device=self.E.device)
+        abi.check(abi.load().fem_get_pattern(self._h, _dev(rowptr, "rowptr"), _dev(col, "col"), _stream(stream)))
+        return rowptr, col[: self.nnz]
+
+    # ---- numeric
+    def integrate_local(self, X, c, prec="fp64", out=None, stream=None):
+        p = _prec(prec)
+        if out is None:
+            out = torch.empty(self.n_elems, self.np, dtype=value_dtype(prec), device=X.device)
+        abi.check(abi.load().fem_integrate_local(self._h, p, _dev(X, "X"), _DT[X.dtype], _dev(c, "c"), _DT[c.dtype],
+                                                 _dev(out, "ke", value_dtype(prec)), _stream(stream)))
+        return out
+
+    def assemble_csr(self, ke, prec="fp64", out=None, stream=None):
+        p = _prec(prec)
+        if self.nnz is None:
+            self.pattern(stream)
+        if out is None:
+            out = torch.empty(max(self.nnz, 1), dtype=value_dtype(prec), device=ke.device)
+        abi.check(abi.load().fem_assemble_csr(self._h, p, _dev(ke, "ke", value_dtype(prec)),
+                                              _dev(out, "vals", value_dtype(prec)), _stream(stream)))
+        return out[: self.nnz]
+
+    def build_K(self, X, c, prec="fp64", out=None, stream=None):
+        p = _prec(prec)
+        if self.nnz is None:
+            self.pattern(stream)
+        if out is None:
+            out = torch.empty(max(self.nnz, 1), dtype=value_dtype(prec), device=X.device)
+        abi.check(abi.load().fem_build_K(self._h, p, _dev(X, "X"), _DT[X.dtype], _dev(c, "c"), _DT[c.dtype],
+                                         _dev(out, "vals", value_dtype(prec)), _stream(stream)))
+        return out[: self.nnz]
+
+    def build_K_host(self, X, c, prec="fp64", out=None, stream=None):
+        """Host tensors in and out (pin them for full copy bandwidth)."""
+        p = _prec(prec)
+        if self.nnz is None:
+            self.pattern(stream)
+        for t, n in ((X, "X"), (c, "c")):
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError(f"{n} must be a contiguous host tensor")
+        if out is None:
+            out = torch.empty(max(self.nnz, 1), dtype=value_dtype(prec), pin_memory=True)
+        abi.check(abi.load().fem_build_K_host(self._h, p, ctypes.c_void_p(X.data_ptr()), _DT[X.dtype],
+                                              ctypes.c_void_p(c.data_ptr()), _DT[c.dtype],
+                                              ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out[: self.nnz]
+
+    def vjp(self, X, c, G, prec="fp64", stream=None):
+        p = _prec(prec)
+        vd = value_dtype(prec)
+        dX = torch.empty(self.n_nodes, 3, dtype=vd, device=X.device)
+        dc = torch.empty(self.n_elems, dtype=vd, device=X.device)
+        abi.check(abi.load().fem_vjp(self._h, p, _dev(X, "X"), _DT[X.dtype], _dev(c, "c"), _DT[c.dtype],
+                                     _dev(G, "G", vd), _dev(dX, "dX"), _dev(dc, "dc"), _stream(stream)))
+        return dX, dc
+
+    def sync(self, stream=None):
+        abi.check(abi.load().fem_sync(self._h, _stream(stream)))
+
+    def info(self) -> dict:
+        i = abi.fem_info()
+        abi.check(abi.load().fem_mesh_info(self._h, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in abi.fem_info._fields_ if f != "reserved"}
+
+
+def build_K_batched(meshes, X, c, prec="mixed", out=None, stream=None):
+    """One persistent launch over many meshes (each with its pattern cached)."""
+    p = _prec(prec)
+    n = len(meshes)
+    for m in meshes:
+        if m.nnz is None:
+            m.pattern(stream)
+    if out is None:
+        out = [torch.empty(max(m.nnz, 1), dtype=value_dtype(prec), device=X[i].device) for i, m in enumerate(meshes)]
+    H = (ctypes.c_void_p * n)(*[m.handle.value for m in meshes])
+    XP = (ctypes.c_void_p * n)(*[x.data_ptr() for x in X])
+    CP = (ctypes.c_void_p * n)(*[t.data_ptr() for t in c])
+    VP = (ctypes.c_void_p * n)(*[v.data_ptr() for v in out])
+    abi.check(abi.load().fem_build_K_batched(H, n, p, XP, _DT[X[0].dtype], CP, _DT[c[0].dtype], VP, _stream(stream)))
+    return [v[: m.nnz] for v, m in zip(out, meshes)]

@@ -1,0 +1,191 @@
+"""Parity of the CUDA path with the FP64 oracle, through the C ABI.
+
+Pattern and row pointers must be bit-exact; values within 1e-12 (FP64) or
+1e-5 (mixed) of the oracle, relative to each entry's Cauchy-Schwarz scale (see
+helpers.py).  Sizes span many thread-block patches and ragged tails; small
+patch capacities force hundreds of patches on small meshes.
+"""
+import numpy as np
+import pytest
+
+import meshgen
+from helpers import TOL_FP64, TOL_MIXED, oracle_K, oracle_ke, oracle_rows, rel_err, rounded_inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fem():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1501_04784_gb300 import _build
+    _build.build()
+    from paper_1501_04784_gb300 import fem as F
+    return F
+
+
+def dev(a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda").to(dtype)
+
+
+def make(fem, m, **opts):
+    E = dev(m.E, torch.int32)
+    mesh = fem.Mesh(E, m.n_nodes, X=dev(m.X, torch.float64), **opts)
+    return mesh
+
+
+def inputs(m, prec):
+    X, c = rounded_inputs(m, prec)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    return dev(X, dt), dev(c, dt), X, c
+
+
+MESHES = {
+    "hex20_perm": lambda: meshgen.config_mesh(0),
+    "hex_7x5x3": lambda: meshgen.hex_grid(7, 5, 3, jitter=0.25, seed=5, permute_nodes=True, permute_elems=True),
+    "hex_1x1x1": lambda: meshgen.hex_grid(1, 1, 1, jitter=0.0, seed=1),
+    "tet10_perm": lambda: meshgen.config_mesh(2, nx=10),
+    "tet_6x4x3": lambda: meshgen.kuhn_tets(6, 4, 3, jitter=0.3, seed=2, permute_nodes=True, permute_elems=True),
+}
+PATCH_CAPS = {"default": 0, "tiny": 64}
+
+
+@pytest.mark.parametrize("cap", list(PATCH_CAPS))
+@pytest.mark.parametrize("name", list(MESHES))
+def test_pattern_bit_exact(fem, name, cap):
+    m = MESHES[name]()
+    mesh = make(fem, m, patch_entries=PATCH_CAPS[cap])
+    ref = oracle_K(m)
+    nnz = mesh.pattern()
+    assert nnz == ref["nnz"]
+    rowptr, col = mesh.get_pattern()
+    assert np.array_equal(rowptr.cpu().numpy(), ref["rowptr"])
+    assert np.array_equal(col.cpu().numpy(), ref["col"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["hex20_perm", "tet10_perm", "hex_7x5x3"])
+def test_integrate_local(fem, name, prec):
+    m = MESHES[name]()
+    mesh = make(fem, m)
+    Xd, cd, X, c = inputs(m, prec)
+    ke = mesh.integrate_local(Xd, cd, prec).cpu().numpy()
+    ref, cs, _ = oracle_ke(m, X, c)
+    err = rel_err(ke.ravel(), ref.ravel(), cs.ravel())
+    assert err <= (TOL_FP64 if prec == "fp64" else TOL_MIXED), err
+
+
+@pytest.mark.parametrize("cap", list(PATCH_CAPS))
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", list(MESHES))
+def test_build_K(fem, name, prec, cap):
+    m = MESHES[name]()
+    mesh = make(fem, m, patch_entries=PATCH_CAPS[cap])
+    Xd, cd, X, c = inputs(m, prec)
+    ref = oracle_K(m, X, c)
+    vals = mesh.build_K(Xd, cd, prec).cpu().numpy()
+    err = rel_err(vals, ref["vals"], ref["cs"])
+    assert err <= (TOL_FP64 if prec == "fp64" else TOL_MIXED), err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["hex20_perm", "tet10_perm"])
+def test_assemble_given_ke(fem, name, prec):
+    """fem_assemble_csr of the oracle's own element matrices: only the summation
+    order differs from the oracle's sparse conversion."""
+    m = MESHES[name]()
+    mesh = make(fem, m)
+    mesh.pattern()
+    ke, cs, _ = oracle_ke(m)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    vals = mesh.assemble_csr(dev(ke, dt), prec).cpu().numpy()
+    ref = oracle_K(m)
+    tol = 1e-14 if prec == "fp64" else 3e-7
+    assert rel_err(vals, ref["vals"], ref["cs"]) <= tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_bitwise_reproducible_across_launch_shapes(fem, prec):
+    m = MESHES["hex20_perm"]()
+    Xd, cd, _, _ = inputs(m, prec)
+    outs = []
+    for threads, bps in ((256, 0), (256, 0), (128, 1), (512, 1), (64, 3)):
+        mesh = make(fem, m, block_threads=threads, blocks_per_sm=bps, patch_entries=2048)
+        outs.append(mesh.build_K(Xd, cd, prec).cpu().numpy())
+    for o in outs[1:]:
+        assert np.array_equal(o.view(np.uint8), outs[0].view(np.uint8))
+
+
+def test_host_entry_point_matches_device(fem):
+    m = MESHES["tet10_perm"]()
+    mesh = make(fem, m)
+    Xd, cd, X, c = inputs(m, "mixed")
+    dv = mesh.build_K(Xd, cd, "mixed").cpu().numpy()
+    hv = mesh.build_K_host(torch.from_numpy(np.ascontiguousarray(X)).pin_memory(),
+                           torch.from_numpy(np.ascontiguousarray(c)).pin_memory(), "mixed").numpy()
+    assert np.array_equal(dv, hv)
+
+
+def test_isolated_nodes_and_single_element(fem):
+    m = meshgen.hex_grid(1, 1, 1, seed=3)
+    E = dev(m.E, torch.int32)
+    mesh = fem.Mesh(E, m.n_nodes + 5)           # 5 nodes that no element uses
+    nnz = mesh.pattern()
+    assert nnz == 36
+    rowptr, col = mesh.get_pattern()
+    assert np.array_equal(rowptr.cpu().numpy()[-6:], np.full(6, 36))
+    X = np.vstack([m.X, np.zeros((5, 3))])
+    vals = mesh.build_K(dev(X, torch.float64), dev(m.c, torch.float64), "fp64").cpu().numpy()
+    ref = oracle_K(m)
+    assert rel_err(vals, ref["vals"], ref["cs"]) <= TOL_FP64
+
+
+def test_error_statuses(fem):
+    from paper_1501_04784_gb300 import abi
+    m = meshgen.hex_grid(2, seed=3)
+    E = m.E.copy()
+    E[1, 3] = m.n_nodes + 7
+    with pytest.raises(abi.FemError, match="FEM_ERR_INDEX"):
+        fem.Mesh(dev(E, torch.int32), m.n_nodes)
+    E = m.E.copy()
+    E[2, 5] = E[2, 1]
+    with pytest.raises(abi.FemError, match="FEM_ERR_DEGENERATE"):
+        fem.Mesh(dev(E, torch.int32), m.n_nodes)
+    mesh = fem.Mesh(dev(m.E, torch.int32), m.n_nodes)
+    vals = torch.empty(1000, dtype=torch.float64, device="cuda")
+    L = abi.load()
+    import ctypes
+    st = L.fem_build_K(mesh.handle, 0, ctypes.c_void_p(dev(m.X, torch.float64).data_ptr()), 1,
+                       ctypes.c_void_p(dev(m.c, torch.float64).data_ptr()), 1, ctypes.c_void_p(vals.data_ptr()), None)
+    assert abi.STATUS[st] == "FEM_ERR_STATE"
+    small = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, mem_budget_bytes=1024)
+    with pytest.raises(abi.FemError, match="FEM_ERR_BUDGET"):
+        small.pattern()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_full_size_1M_bricks_sampled(fem, prec):
+    """The 1M-brick workload at full size: pattern checked against the closed-form
+    nnz and structural invariants, values of sampled rows against the oracle."""
+    m = meshgen.config_mesh(1)
+    mesh = make(fem, m)
+    nnz = mesh.pattern()
+    assert nnz == ((3 * 100 + 1) ** 3 + 101 ** 3) // 2 == 14150601
+    rowptr, col = mesh.get_pattern()
+    rp = rowptr.cpu().numpy()
+    cl = col.cpu().numpy()
+    assert np.all(np.diff(rp) >= 1)
+    last = cl[rp[1:] - 1]
+    assert np.array_equal(last, np.arange(m.n_nodes))      # diagonal is the last entry of each row
+    Xd, cd, X, c = inputs(m, prec)
+    vals = mesh.build_K(Xd, cd, prec).cpu().numpy()
+    rng = np.random.default_rng(12)
+    sample = rng.choice(m.n_nodes, 3000, replace=False)
+    ref = oracle_rows(m, sample, X, c)
+    worst = 0.0
+    for r, (cols, v, cs) in ref.items():
+        a, b = rp[r], rp[r + 1]
+        assert np.array_equal(cl[a:b], cols)
+        worst = max(worst, rel_err(vals[a:b], v, cs))
+    assert worst <= (TOL_FP64 if prec == "fp64" else TOL_MIXED), worst
