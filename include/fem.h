@@ -72,7 +72,8 @@ typedef enum { FEM_F32 = 0, FEM_F64 = 1 } fem_dtype;
 typedef struct {
     size_t mem_budget_bytes;     /* cap on library-owned device memory; 0 = no cap */
     double distortion_threshold; /* mixed mode; brick: max_q detJ / min_q detJ, tet:
-                                    longest edge / shortest altitude.  Default 3 / 10. */
+                                    longest edge / shortest altitude.  0 = default
+                                    (brick 4, tetrahedron 10). */
     int valence_threshold;       /* mixed mode: entries with more contributions than
                                     this are summed in FP64.  Default 8. */
     int patch_entries;           /* lower-CSR entries owned by one thread block (0 = default) */

@@ -24,7 +24,7 @@ static size_t dsize(fem_dtype d) { return d == FEM_F64 ? 8 : 4; }
 
 static float default_threshold(const fem_mesh m) {
     if (m->opt.distortion_threshold > 0) return (float)m->opt.distortion_threshold;
-    return m->npe == 8 ? 2.5f : 10.0f;
+    return m->npe == 8 ? 4.0f : 10.0f;
 }
 
 static fem_status check_dtype(fem_dtype d, const char *what) {
@@ -68,7 +68,7 @@ void fem_options_default(fem_options *opt) {
     if (!opt) return;
     std::memset(opt, 0, sizeof(*opt));
     opt->mem_budget_bytes = 0;
-    opt->distortion_threshold = 0.0;  // 0 = per element type: brick 2.5, tetrahedron 10
+    opt->distortion_threshold = 0.0;  // 0 = per element type: brick 4, tetrahedron 10
     opt->valence_threshold = 8;
     opt->patch_entries = 0;
     opt->block_threads = 0;

@@ -56,6 +56,11 @@ template <typename T>
 __device__ __forceinline__ T dot3(const Vec3<T> &a, const Vec3<T> &b) {
     return a.x * b.x + a.y * b.y + a.z * b.z;
 }
+// Correctly rounded reciprocal (IEEE round-to-nearest), without the general
+// division routine.
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
 template <typename T>
 __device__ __forceinline__ Vec3<T> lerp2(T wa, const Vec3<T> &a, T wb, const Vec3<T> &b) {
     return {wa * a.x + wb * b.x, wa * a.y + wb * b.y, wa * a.z + wb * b.z};
@@ -117,7 +122,7 @@ __device__ __forceinline__ void brick_M(const Vec3<T> (&row)[3][2][2], T (&M)[8]
                 const Vec3<T> C0 = cross3(S, U), C1 = cross3(U, R), C2 = cross3(R, S);
                 const T d = dot3(R, C0);
                 det[q] = d;
-                const T inv = T(1) / (d < T(0) ? -d : d);
+                const T inv = rcp_rn(d < T(0) ? -d : d);
                 M[q][0] = dot3(C0, C0) * inv;
                 M[q][1] = dot3(C1, C1) * inv;
                 M[q][2] = dot3(C2, C2) * inv;
@@ -305,77 +310,85 @@ __device__ __forceinline__ bool brick_ke_mixed(const S (*xc)[3], float c, float 
 }
 
 // ---------------------------------------------------------------- tetrahedron
-// Rows of J are the edge vectors x_i - x_0 (i = 1..3); the gradient of
-// lambda_i is cof row i-1 over det J; k = c |det J|/6 B^T B with B the matrix
-// of barycentric gradients.  M = cof cof^T / (6 |det J|).
+// Rows of J are the edge vectors x_i - x_0 (i = 1..3).  The gradient of the
+// barycentric function lambda_a is F_a / det J, where F_a is twice the area
+// vector of the face opposite node a: F_1, F_2, F_3 are the cofactor rows
+// (R1 x R2, R2 x R0, R0 x R1) and F_0 = (x3 - x1) x (x2 - x1) = -(F_1 + F_2 + F_3).
+// Hence k_ab = c |det J|/6 grad(lambda_a).grad(lambda_b) = c F_a.F_b / (6 |det J|).
+// F_0 is formed from its own coordinate differences rather than as -(F_1+F_2+F_3),
+// so no entry is a cancelling sum (the FP32 error stays relative to the element).
 template <typename T>
-__device__ __forceinline__ void tet_from_rows(const Vec3<T> &R0, const Vec3<T> &R1, const Vec3<T> &R2, T c,
-                                              T (&k)[10]) {
-    const Vec3<T> C0 = cross3(R1, R2), C1 = cross3(R2, R0), C2 = cross3(R0, R1);
-    const T d = dot3(R0, C0);
-    const T inv = c / (T(6) * (d < T(0) ? -d : d));
-    const T m00 = dot3(C0, C0) * inv, m11 = dot3(C1, C1) * inv, m22 = dot3(C2, C2) * inv;
-    const T m01 = dot3(C0, C1) * inv, m02 = dot3(C0, C2) * inv, m12 = dot3(C1, C2) * inv;
-    const T s0 = m00 + m01 + m02, s1 = m01 + m11 + m12, s2 = m02 + m12 + m22;
-    k[0] = s0 + s1 + s2;  // (0,0)
-    k[1] = -s0;           // (1,0)
-    k[2] = m00;           // (1,1)
-    k[3] = -s1;           // (2,0)
-    k[4] = m01;           // (2,1)
-    k[5] = m11;           // (2,2)
-    k[6] = -s2;           // (3,0)
-    k[7] = m02;           // (3,1)
-    k[8] = m12;           // (3,2)
-    k[9] = m22;           // (3,3)
-}
+struct TetGeom {
+    Vec3<T> R0, R1, R2, D1, D2;  // x1-x0, x2-x0, x3-x0, x2-x1, x3-x1
+};
 
 template <typename T, typename S>
-__device__ __forceinline__ void tet_rows(const S (*xc)[3], Vec3<T> &R0, Vec3<T> &R1, Vec3<T> &R2) {
-    R0 = {T(xc[1][0] - xc[0][0]), T(xc[1][1] - xc[0][1]), T(xc[1][2] - xc[0][2])};
-    R1 = {T(xc[2][0] - xc[0][0]), T(xc[2][1] - xc[0][1]), T(xc[2][2] - xc[0][2])};
-    R2 = {T(xc[3][0] - xc[0][0]), T(xc[3][1] - xc[0][1]), T(xc[3][2] - xc[0][2])};
+__device__ __forceinline__ void tet_geom(const S (*xc)[3], TetGeom<T> &g) {
+    auto d = [&](int i, int j) {
+        return Vec3<T>{T(xc[i][0] - xc[j][0]), T(xc[i][1] - xc[j][1]), T(xc[i][2] - xc[j][2])};
+    };
+    g.R0 = d(1, 0);
+    g.R1 = d(2, 0);
+    g.R2 = d(3, 0);
+    g.D1 = d(2, 1);
+    g.D2 = d(3, 1);
+}
+
+template <typename T>
+__device__ __forceinline__ void tet_faces(const TetGeom<T> &g, Vec3<T> (&F)[4], T &det) {
+    F[1] = cross3(g.R1, g.R2);
+    F[2] = cross3(g.R2, g.R0);
+    F[3] = cross3(g.R0, g.R1);
+    F[0] = cross3(g.D2, g.D1);
+    det = dot3(g.R0, F[1]);
+}
+
+template <typename T>
+__device__ __forceinline__ void tet_from_faces(const Vec3<T> (&F)[4], T det, T c, T (&k)[10]) {
+    const T s = c * rcp_rn(T(6) * (det < T(0) ? -det : det));
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b <= a; ++b) k[a * (a + 1) / 2 + b] = dot3(F[a], F[b]) * s;
 }
 
 template <typename T, typename S>
 __device__ __forceinline__ void tet_ke(const S (*xc)[3], T c, T (&k)[10]) {
-    Vec3<T> R0, R1, R2;
-    tet_rows<T, S>(xc, R0, R1, R2);
-    tet_from_rows(R0, R1, R2, c, k);
+    TetGeom<T> g;
+    tet_geom<T, S>(xc, g);
+    Vec3<T> F[4];
+    T det;
+    tet_faces(g, F, det);
+    tet_from_faces(F, det, c, k);
 }
 
 // Mixed precision tetrahedron: the aspect ratio (longest edge over shortest
-// altitude = L_max |cof|_max / |det J|, |cof|_max the largest face-area vector
-// times 2) is evaluated in FP32; above `thr` the determinant and inverse are
-// recomputed in FP64.  Returns true when the FP64 path was taken.
+// altitude = L_max |F|_max / |det J|) is evaluated in FP32; above `thr` the
+// face vectors and the determinant are recomputed in FP64 from the coordinate
+// differences and rounded once.  Returns true when the FP64 path was taken.
 template <typename S>
 __device__ __forceinline__ bool tet_ke_mixed(const S (*xc)[3], float c, float thr, float (&k)[10]) {
-    Vec3<float> R0, R1, R2;
-    tet_rows<float, S>(xc, R0, R1, R2);
-    const Vec3<float> C0 = cross3(R1, R2), C1 = cross3(R2, R0), C2 = cross3(R0, R1);
-    const Vec3<float> C3 = {C0.x + C1.x + C2.x, C0.y + C1.y + C2.y, C0.z + C1.z + C2.z};
-    const float d = dot3(R0, C0);
-    const Vec3<float> E3 = {R1.x - R0.x, R1.y - R0.y, R1.z - R0.z};
-    const Vec3<float> E4 = {R2.x - R0.x, R2.y - R0.y, R2.z - R0.z};
-    const Vec3<float> E5 = {R2.x - R1.x, R2.y - R1.y, R2.z - R1.z};
-    const float L2 = fmaxf(fmaxf(fmaxf(dot3(R0, R0), dot3(R1, R1)), fmaxf(dot3(R2, R2), dot3(E3, E3))),
-                           fmaxf(dot3(E4, E4), dot3(E5, E5)));
-    const float A2 = fmaxf(fmaxf(dot3(C0, C0), dot3(C1, C1)), fmaxf(dot3(C2, C2), dot3(C3, C3)));
-    const bool flagged = !(L2 * A2 <= thr * thr * d * d);
+    TetGeom<float> g;
+    tet_geom<float, S>(xc, g);
+    Vec3<float> F[4];
+    float det;
+    tet_faces(g, F, det);
+    const Vec3<float> E5 = {g.R2.x - g.R1.x, g.R2.y - g.R1.y, g.R2.z - g.R1.z};
+    const float L2 = fmaxf(fmaxf(fmaxf(dot3(g.R0, g.R0), dot3(g.R1, g.R1)), fmaxf(dot3(g.R2, g.R2), dot3(g.D1, g.D1))),
+                           fmaxf(dot3(g.D2, g.D2), dot3(E5, E5)));
+    const float A2 = fmaxf(fmaxf(dot3(F[0], F[0]), dot3(F[1], F[1])), fmaxf(dot3(F[2], F[2]), dot3(F[3], F[3])));
+    const bool flagged = !(L2 * A2 <= thr * thr * det * det);
     if (flagged) {
-        Vec3<double> D0, D1, D2;
-        tet_rows<double, S>(xc, D0, D1, D2);
-        double kd[10];
-        tet_from_rows(D0, D1, D2, (double)c, kd);
+        TetGeom<double> gd;
+        tet_geom<double, S>(xc, gd);
+        Vec3<double> Fd[4];
+        double dd;
+        tet_faces(gd, Fd, dd);
 #pragma unroll
-        for (int i = 0; i < 10; ++i) k[i] = (float)kd[i];
-    } else {
-        const float inv = c / (6.f * fabsf(d));
-        const float m00 = dot3(C0, C0) * inv, m11 = dot3(C1, C1) * inv, m22 = dot3(C2, C2) * inv;
-        const float m01 = dot3(C0, C1) * inv, m02 = dot3(C0, C2) * inv, m12 = dot3(C1, C2) * inv;
-        const float s0 = m00 + m01 + m02, s1 = m01 + m11 + m12, s2 = m02 + m12 + m22;
-        k[0] = s0 + s1 + s2; k[1] = -s0; k[2] = m00; k[3] = -s1; k[4] = m01;
-        k[5] = m11; k[6] = -s2; k[7] = m02; k[8] = m12; k[9] = m22;
+        for (int a = 0; a < 4; ++a) F[a] = {(float)Fd[a].x, (float)Fd[a].y, (float)Fd[a].z};
+        det = (float)dd;
     }
+    tet_from_faces(F, det, c, k);
     return flagged;
 }
 

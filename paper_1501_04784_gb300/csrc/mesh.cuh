@@ -29,6 +29,7 @@ struct PlanView {
     const uint8_t *celem_color;      // [total celems]
     const uint16_t *celem_lnode;     // [total celems * npe] closure-local node index
     const uint8_t *celem_pos;        // [total celems * pos_stride] position of the entry in its row
+    const int32_t *own_row;          // [n_nodes] global id of each owned row, in patch order
     int64_t n_patches;
 };
 
@@ -45,7 +46,7 @@ struct Plan {
         return PlanView{patch_node_ptr.ptr, patch_elem_ptr.ptr, patch_cnode_ptr.ptr, patch_acc.ptr,
                         own_acc.ptr,        own_rowptr.ptr,     own_hv.ptr,          cnode_gid.ptr,
                         cnode_own.ptr,      celem_id.ptr,       celem_color.ptr,     celem_lnode.ptr,
-                        celem_pos.ptr,      n_patches};
+                        celem_pos.ptr,      own_row.ptr,        n_patches};
     }
     size_t bytes() const {
         return patch_node_ptr.bytes() + patch_elem_ptr.bytes() + patch_cnode_ptr.bytes() + own_rowptr.bytes() +

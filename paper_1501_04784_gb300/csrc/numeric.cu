@@ -107,6 +107,80 @@ __global__ void __launch_bounds__(INT_THREADS) k_integrate(const int32_t *__rest
     if (nflag && threadIdx.x == 0 && flagged_total) atomicAdd(nflag, (unsigned long long)flagged_total);
 }
 
+// Adds the owned entries of one element's packed k_e into the block's
+// accumulators.  Row bases are looked up once per node, then the accumulator
+// reads of a group of entries are issued together before their writes, so a
+// group costs one shared-memory round trip instead of one per entry.  All
+// entries of one element are distinct, so the reads of a group do not alias
+// its writes.
+__host__ __device__ constexpr int tri_row(int q) {
+    int a = 0;
+    while ((a + 1) * (a + 2) / 2 <= q) ++a;
+    return a;
+}
+
+template <int NPE, typename AccT, bool MIXED>
+__device__ __forceinline__ void scatter_element(const uint8_t *__restrict__ posp, const uint16_t (&ln)[NPE],
+                                                const int32_t *cown, const int32_t *roff, const uint8_t *hvf,
+                                                double *hv, AccT *acc, const AccT (&kv)[NPE * (NPE + 1) / 2]) {
+    constexpr int NP = NPE * (NPE + 1) / 2;
+    constexpr int NW = (NP + 3) / 4;
+    uint32_t pw[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) pw[w] = __ldg(reinterpret_cast<const uint32_t *>(posp) + w);
+    int own[NPE], rbase[NPE];
+#pragma unroll
+    for (int a = 0; a < NPE; ++a) own[a] = cown[ln[a]];
+#pragma unroll
+    for (int a = 0; a < NPE; ++a) rbase[a] = own[a] >= 0 ? roff[own[a]] : -1;
+    // entry q of the packed lower triangle is the pair (a, b) = (pa(q), pb(q))
+    auto entry_index = [&](int q, int a, int b) {
+        const int base = ln[a] > ln[b] ? rbase[a] : rbase[b];
+        const int pos = (pw[q >> 2] >> (8 * (q & 3))) & 0xff;
+        return base >= 0 ? base + pos : -1;
+    };
+    if constexpr (MIXED) {
+        // diagonal entries of high-valence rows are summed in FP64 instead
+#pragma unroll
+        for (int a = 0; a < NPE; ++a) {
+            const int q = a * (a + 1) / 2 + a;
+            if (rbase[a] >= 0 && hvf[own[a]]) {
+                hv[own[a]] += (double)kv[q];
+                rbase[a] = -2 - rbase[a];  // keep off-diagonals, mark the diagonal
+            }
+        }
+    }
+    constexpr int G = 12;
+#pragma unroll
+    for (int g0 = 0; g0 < NP; g0 += G) {
+        int idx[G];
+        AccT old[G];
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            const int q = g0 + j;
+            if (q < NP) {
+                const int a = tri_row(q), b = q - a * (a + 1) / 2;
+                if (MIXED && a == b) idx[j] = rbase[a] >= 0 ? entry_index(q, a, b) : -1;
+                else {
+                    const int ra = rbase[a] < -1 ? -2 - rbase[a] : rbase[a];
+                    const int rb = rbase[b] < -1 ? -2 - rbase[b] : rbase[b];
+                    const int base = ln[a] > ln[b] ? ra : rb;
+                    const int pos = (pw[q >> 2] >> (8 * (q & 3))) & 0xff;
+                    idx[j] = base >= 0 ? base + pos : -1;
+                }
+            } else {
+                idx[j] = -1;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < G; ++j)
+            if (idx[j] >= 0) old[j] = acc[idx[j]];
+#pragma unroll
+        for (int j = 0; j < G; ++j)
+            if (idx[j] >= 0) acc[idx[j]] = old[j] + kv[g0 + j < NP ? g0 + j : 0];
+    }
+}
+
 // ------------------------------------------------------------------ k_patch
 template <int NPE, typename AccT, typename S, typename CT, bool FUSED, bool MIXED>
 __global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch(PlanView pv, const S *__restrict__ X,
@@ -124,6 +198,9 @@ __global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch(PlanView pv, const 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
 
+    int64_t *rps = reinterpret_cast<int64_t *>(patch_smem + L.rps);
+    int32_t *gid = reinterpret_cast<int32_t *>(patch_smem + L.gid);
+
     for (int64_t p = p0 + blockIdx.x; p < p1; p += gridDim.x) {
         const int64_t nb = pv.patch_node_ptr[p];
         const int nown = (int)(pv.patch_node_ptr[p + 1] - nb);
@@ -133,17 +210,14 @@ __global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch(PlanView pv, const 
         const int nel = (int)(pv.patch_elem_ptr[p + 1] - eb);
         const int nacc = pv.patch_acc[p];
 
+        // Prologue, stage 1: every contiguous per-patch array, independent loads.
         for (int j = tid; j < ncn; j += nthr) {
             cown[j] = pv.cnode_own[cb + j];
-            if constexpr (FUSED) {
-                const int64_t g = pv.cnode_gid[cb + j];
-                xs[j][0] = __ldg(X + 3 * g + 0);
-                xs[j][1] = __ldg(X + 3 * g + 1);
-                xs[j][2] = __ldg(X + 3 * g + 2);
-            }
+            if constexpr (FUSED) gid[j] = pv.cnode_gid[cb + j];
         }
         for (int k = tid; k < nown; k += nthr) {
             roff[k] = pv.own_acc[nb + k];
+            rps[k] = pv.own_rowptr[nb + k];
             if constexpr (MIXED) {
                 hv[k] = 0.0;
                 hvf[k] = pv.own_hv[nb + k];
@@ -152,7 +226,28 @@ __global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch(PlanView pv, const 
         if (tid == 0) roff[nown] = nacc;
         for (int i = tid; i < nacc; i += nthr) acc[i] = AccT(0);
         __syncthreads();
+        // Prologue, stage 2: gathers through the staged indices (node coordinates,
+        // coefficients), unrolled so that several loads are in flight per thread.
+        if constexpr (FUSED) {
+#pragma unroll 4
+            for (int j = tid; j < ncn; j += nthr) {
+                const int64_t g = gid[j];
+                xs[j][0] = __ldg(X + 3 * g + 0);
+                xs[j][1] = __ldg(X + 3 * g + 1);
+                xs[j][2] = __ldg(X + 3 * g + 2);
+            }
+        }
+        __syncthreads();
 
+        // Coefficients come through a two-stage register pipeline: element ids two
+        // batches ahead, c one batch ahead, so the dependent loads overlap compute.
+        int32_t eid_n2 = -1;
+        CT c_n1 = CT(0);
+        if constexpr (FUSED) {
+            const int32_t e0 = tid < nel ? pv.celem_id[eb + tid] : -1;
+            c_n1 = e0 >= 0 ? __ldg(c + e0) : CT(0);
+            eid_n2 = tid + nthr < nel ? pv.celem_id[eb + tid + nthr] : -1;
+        }
         for (int base = 0; base < nel; base += nthr) {
             const int i = base + tid;
             const bool act = i < nel;
@@ -160,10 +255,16 @@ __global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch(PlanView pv, const 
             AccT kv[NP];
             uint16_t ln[NPE];
             int mycol = -1;
+            CT ce = CT(0);
+            if constexpr (FUSED) {
+                ce = c_n1;
+                c_n1 = eid_n2 >= 0 ? __ldg(c + eid_n2) : CT(0);
+                const int i2 = i + 2 * nthr;
+                eid_n2 = i2 < nel ? pv.celem_id[eb + i2] : -1;
+            }
             if (act) {
                 load_lnodes<NPE>(pv.celem_lnode, ci, ln);
                 mycol = pv.celem_color[ci];
-                const int64_t e = pv.celem_id[ci];
                 if constexpr (FUSED) {
                     S xc[NPE][3];
 #pragma unroll
@@ -172,8 +273,9 @@ __global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch(PlanView pv, const 
                         xc[a][1] = xs[ln[a]][1];
                         xc[a][2] = xs[ln[a]][2];
                     }
-                    element_matrix<NPE, AccT, S, MIXED>(xc, (double)__ldg(c + e), thr, kv);
+                    element_matrix<NPE, AccT, S, MIXED>(xc, (double)ce, thr, kv);
                 } else {
+                    const int64_t e = pv.celem_id[ci];
 #pragma unroll
                     for (int q = 0; q < NP; ++q) kv[q] = __ldg(ke + e * NP + q);
                 }
@@ -181,37 +283,15 @@ __global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch(PlanView pv, const 
             const int last = min(base + nthr, nel) - 1;
             const int c0 = pv.celem_color[eb + base], c1 = pv.celem_color[eb + last];
             for (int cc = c0; cc <= c1; ++cc) {
-                if (mycol == cc) {
-                    uint8_t pos[NP];
-                    const uint32_t *pw = reinterpret_cast<const uint32_t *>(pv.celem_pos + ci * ((NP + 3) / 4 * 4));
-#pragma unroll
-                    for (int w = 0; w < (NP + 3) / 4; ++w) {
-                        const uint32_t v = __ldg(pw + w);
-#pragma unroll
-                        for (int b = 0; b < 4; ++b)
-                            if (4 * w + b < NP) pos[4 * w + b] = (uint8_t)(v >> (8 * b));
-                    }
-#pragma unroll
-                    for (int a = 0; a < NPE; ++a) {
-#pragma unroll
-                        for (int b = 0; b <= a; ++b) {
-                            const int q = a * (a + 1) / 2 + b;
-                            const int rl = ln[a] > ln[b] ? ln[a] : ln[b];
-                            const int o = cown[rl];
-                            if (o >= 0) {
-                                if (MIXED && a == b && hvf[o]) hv[o] += (double)kv[q];
-                                else acc[roff[o] + pos[q]] += kv[q];
-                            }
-                        }
-                    }
-                }
+                if (mycol == cc) scatter_element<NPE, AccT, MIXED>(pv.celem_pos + ci * ((NP + 3) / 4 * 4), ln, cown, roff,
+                                                                    hvf, hv, acc, kv);
                 __syncthreads();
             }
         }
 
         // each owned row to HBM once (one warp per row)
         for (int k = warp; k < nown; k += nwarps) {
-            const int64_t rp = pv.own_rowptr[nb + k];
+            const int64_t rp = rps[k];
             const int o0 = roff[k], len = roff[k + 1] - o0;
             const bool h = MIXED && hvf[k];
             for (int j = lane; j < len; j += 32) {
@@ -271,7 +351,7 @@ fem_status launch_integrate(const IntegrateArgs &a, cudaStream_t s) {
 
 static size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-PatchSmem patch_smem_layout(const Plan &P, bool fused, bool mixed, size_t xsize) {
+PatchSmem patch_smem_layout(const Plan &P, bool fused, bool mixed, size_t xsize, size_t csize) {
     PatchSmem L{};
     const size_t accsz = mixed ? sizeof(float) : sizeof(double);
     size_t o = 0;
@@ -287,6 +367,12 @@ PatchSmem patch_smem_layout(const Plan &P, bool fused, bool mixed, size_t xsize)
     o = align16(o + (size_t)(P.max_own + 1) * sizeof(int32_t));
     L.hvf = o;
     if (mixed) o = align16(o + (size_t)P.max_own);
+    L.rps = o;
+    o = align16(o + (size_t)P.max_own * sizeof(int64_t));
+    L.gid = o;
+    if (fused) o = align16(o + (size_t)P.max_cnodes * sizeof(int32_t));
+    L.eid = L.cvs = o;
+    (void)csize;
     L.total = o;
     return L;
 }
@@ -294,7 +380,7 @@ PatchSmem patch_smem_layout(const Plan &P, bool fused, bool mixed, size_t xsize)
 template <int NPE, typename AccT, typename S, typename CT, bool FUSED, bool MIXED>
 static fem_status launch_patch_t(const PatchArgs &a, cudaStream_t s) {
     const Plan &P = *a.plan;
-    const PatchSmem L = patch_smem_layout(P, FUSED, MIXED, sizeof(S));
+    const PatchSmem L = patch_smem_layout(P, FUSED, MIXED, sizeof(S), sizeof(CT));
     int dev = 0, max_optin = 0;
     FEM_CUDA(cudaGetDevice(&dev));
     FEM_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));

@@ -9,7 +9,7 @@ static constexpr int PATCH_MAX_THREADS = 512;
 
 // byte offsets of the patch kernel's shared-memory arrays
 struct PatchSmem {
-    size_t acc, hv, xs, cown, roff, hvf, total;
+    size_t acc, hv, xs, cown, roff, hvf, rps, gid, eid, cvs, total;
 };
 
 struct IntegrateArgs {
@@ -38,6 +38,6 @@ struct PatchArgs {
 
 fem_status launch_integrate(const IntegrateArgs &a, cudaStream_t s);
 fem_status launch_patch(const PatchArgs &a, cudaStream_t s);
-PatchSmem patch_smem_layout(const Plan &P, bool fused, bool mixed, size_t xsize);
+PatchSmem patch_smem_layout(const Plan &P, bool fused, bool mixed, size_t xsize, size_t csize);
 
 }  // namespace fem

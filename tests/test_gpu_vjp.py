@@ -1,0 +1,101 @@
+"""Backward pass: the GPU vector-Jacobian product against the oracle's
+complex-step gradient, and against central finite differences of the GPU build
+on the 10^3 sub-mesh of the large streamed workload."""
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+from helpers import rounded_inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fem():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1501_04784_gb300 import _build
+    _build.build()
+    from paper_1501_04784_gb300 import fem as F
+    return F
+
+
+def dev(a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda").to(dtype)
+
+
+CASES = {
+    "hex_4x3x3": lambda: meshgen.hex_grid(4, 3, 3, jitter=0.25, seed=31, permute_nodes=True, permute_elems=True),
+    "tet_3x3x2": lambda: meshgen.kuhn_tets(3, 3, 2, jitter=0.25, seed=32, permute_nodes=True, permute_elems=True),
+    "hex20_perm": lambda: meshgen.config_mesh(0),
+}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_vjp_matches_oracle_gradient(fem, name, prec):
+    m = CASES[name]()
+    X, c = rounded_inputs(m, prec)
+    ref = oracle.build_K(m.npe, X.astype(np.float64), m.E, c.astype(np.float64))
+    G = np.random.default_rng(4).standard_normal(ref["nnz"])
+    if prec == "mixed":
+        G = G.astype(np.float32)
+    dX_ref, dc_ref = oracle.vjp_from_G(m.npe, X.astype(np.float64), m.E, c.astype(np.float64),
+                                       G.astype(np.float64), ref["slot"])
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    mesh = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), patch_entries=512)
+    mesh.pattern()
+    dX, dc = mesh.vjp(dev(X, dt), dev(c, dt), dev(G, dt), prec)
+    dX, dc = dX.cpu().numpy().astype(np.float64), dc.cpu().numpy().astype(np.float64)
+    tol = 1e-11 if prec == "fp64" else 2e-4
+    assert np.abs(dX - dX_ref).max() <= tol * np.abs(dX_ref).max()
+    assert np.abs(dc - dc_ref).max() <= tol * np.abs(dc_ref).max()
+
+
+def test_vjp_bitwise_reproducible(fem):
+    m = CASES["hex20_perm"]()
+    mesh = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64))
+    nnz = mesh.pattern()
+    G = dev(np.random.default_rng(5).standard_normal(nnz), torch.float64)
+    X, c = dev(m.X, torch.float64), dev(m.c, torch.float64)
+    a = mesh.vjp(X, c, G, "fp64")
+    b = mesh.vjp(X, c, G, "fp64")
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+def test_autograd_central_differences_10cube(fem):
+    """The large workload's recipe (jitter 0.2h, c ~ lognormal(0, 0.5)) on its
+    10^3 sub-mesh: torch.autograd through BuildK against central differences of
+    the GPU build itself, for sampled coordinates and coefficients (FP64)."""
+    from paper_1501_04784_gb300.autograd import build_K
+    m = meshgen.config_mesh(4, nx=10)
+    mesh = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64))
+    nnz = mesh.pattern()
+    G = dev(np.random.default_rng(6).standard_normal(nnz), torch.float64)
+    X = dev(m.X, torch.float64).requires_grad_(True)
+    c = dev(m.c, torch.float64).requires_grad_(True)
+    L = (build_K(mesh, X, c, "fp64") * G).sum()
+    L.backward()
+    rng = np.random.default_rng(7)
+    h = 1e-6
+
+    def Lval(Xv, cv):
+        return float((mesh.build_K(Xv, cv, "fp64") * G).sum())
+
+    Xd, cd = X.detach(), c.detach()
+    for _ in range(25):
+        i, j = int(rng.integers(m.n_nodes)), int(rng.integers(3))
+        Xp, Xm = Xd.clone(), Xd.clone()
+        Xp[i, j] += h
+        Xm[i, j] -= h
+        fd = (Lval(Xp, cd) - Lval(Xm, cd)) / (2 * h)
+        assert abs(fd - float(X.grad[i, j])) <= 1e-6 * (abs(fd) + 1e-3)
+    for _ in range(25):
+        e = int(rng.integers(m.n_elems))
+        cp, cm = cd.clone(), cd.clone()
+        cp[e] += h
+        cm[e] -= h
+        fd = (Lval(Xd, cp) - Lval(Xd, cm)) / (2 * h)
+        assert abs(fd - float(c.grad[e])) <= 1e-6 * (abs(fd) + 1e-3)
