@@ -27,9 +27,9 @@
  *     FEM_MIXED: X and c are float or double (x_dtype, c_dtype); ke and vals are
  *     float; element arithmetic FP32 with FP32 accumulation, except the
  *     Jacobian determinant and inverse of elements whose distortion indicator
- *     exceeds fem_options.distortion_threshold (FP64) and the summation of
- *     entries that receive more than fem_options.valence_threshold
- *     contributions (FP64, rounded once).
+ *     exceeds fem_options.distortion_threshold (FP64 determinant) and the
+ *     summation of entries that receive more than fem_options.valence_threshold
+ *     contributions (FP64-accurate, rounded once; see fem_options.fp64_sums).
  *   - Every call is ordered on `stream` (a cudaStream_t; NULL = legacy default
  *     stream) and returns without waiting, except where stated.  Asynchronous
  *     CUDA errors surface at the next call on the mesh or at fem_sync.
@@ -80,6 +80,9 @@ typedef struct {
     int block_threads;           /* threads per block of the patch kernels (0 = default) */
     int blocks_per_sm;           /* resident blocks per SM for the patch kernels (0 = default) */
     int locality_order;          /* 1 = order nodes along a Morton curve of X (default); 0 = by id */
+    int fp64_sums;               /* mixed mode, high-valence entries: 0 (default) = error-free
+                                    FP32 pair summation (TwoSum, accurate to ~2^-48 like an
+                                    FP64 sum, rounded once); 1 = FP64 adds */
     int reserved[8];
 } fem_options;
 

@@ -232,6 +232,7 @@ static PatchArgs patch_args(fem_mesh m, fem_prec p, bool fused) {
     if (a.threads > PATCH_MAX_THREADS) a.threads = PATCH_MAX_THREADS;
     a.threads = (a.threads + 31) / 32 * 32;
     a.blocks_per_sm = m->opt.blocks_per_sm;
+    a.fp64_sums = m->opt.fp64_sums != 0;
     return a;
 }
 

@@ -56,10 +56,30 @@ template <typename T>
 __device__ __forceinline__ T dot3(const Vec3<T> &a, const Vec3<T> &b) {
     return a.x * b.x + a.y * b.y + a.z * b.z;
 }
-// Correctly rounded reciprocal (IEEE round-to-nearest), without the general
-// division routine.
-__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+// Reciprocals.  FP32: the hardware approximation (rcp.approx) refined by one
+// Newton-Raphson step r' = r + r (1 - x r), about 1 ulp, FP32 pipe only.  (The
+// correctly rounded FP32 reciprocal and any conversion to double use the FP64
+// pipe, which on this part runs at 1/64 of the FP32 rate.)  FP64: the correctly
+// rounded double reciprocal.
+__device__ __forceinline__ float rcp_rn(float x) {
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    const float e = fmaf(-x, r, 1.0f);
+    return fmaf(r, e, r);
+}
 __device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
+// a*b - c*d with a single rounding error (Kahan's FMA-based 2x2 determinant):
+// w = c*d is rounded, its rounding error is recovered exactly by an FMA.
+__device__ __forceinline__ float det2(float a, float b, float c, float d) {
+    const float w = c * d;
+    const float err = fmaf(-c, d, w);
+    const float f = fmaf(a, b, -w);
+    return f + err;
+}
+__device__ __forceinline__ Vec3<float> cross3_accurate(const Vec3<float> &a, const Vec3<float> &b) {
+    return {det2(a.y, b.z, a.z, b.y), det2(a.z, b.x, a.x, b.z), det2(a.x, b.y, a.y, b.x)};
+}
 
 template <typename T>
 __device__ __forceinline__ Vec3<T> lerp2(T wa, const Vec3<T> &a, T wb, const Vec3<T> &b) {
@@ -379,14 +399,18 @@ __device__ __forceinline__ bool tet_ke_mixed(const S (*xc)[3], float c, float th
     const float A2 = fmaxf(fmaxf(dot3(F[0], F[0]), dot3(F[1], F[1])), fmaxf(dot3(F[2], F[2]), dot3(F[3], F[3])));
     const bool flagged = !(L2 * A2 <= thr * thr * det * det);
     if (flagged) {
-        TetGeom<double> gd;
-        tet_geom<double, S>(xc, gd);
-        Vec3<double> Fd[4];
-        double dd;
-        tet_faces(gd, Fd, dd);
-#pragma unroll
-        for (int a = 0; a < 4; ++a) F[a] = {(float)Fd[a].x, (float)Fd[a].y, (float)Fd[a].z};
-        det = (float)dd;
+        // Distorted: cofactors (face vectors) with one rounding each, and the
+        // Jacobian determinant in FP64 from exact FP64 products of the FP32 edge
+        // vectors (a product of two floats is exact in double).
+        F[1] = cross3_accurate(g.R1, g.R2);
+        F[2] = cross3_accurate(g.R2, g.R0);
+        F[3] = cross3_accurate(g.R0, g.R1);
+        F[0] = cross3_accurate(g.D2, g.D1);
+        const double r1y = g.R1.y, r1z = g.R1.z, r1x = g.R1.x, r2x = g.R2.x, r2y = g.R2.y, r2z = g.R2.z;
+        const double m0 = fma(r1y, r2z, -(r1z * r2y));
+        const double m1 = fma(r1z, r2x, -(r1x * r2z));
+        const double m2 = fma(r1x, r2y, -(r1y * r2x));
+        det = (float)fma((double)g.R0.x, m0, fma((double)g.R0.y, m1, (double)g.R0.z * m2));
     }
     tet_from_faces(F, det, c, k);
     return flagged;

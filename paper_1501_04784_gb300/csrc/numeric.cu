@@ -54,17 +54,26 @@ __device__ __forceinline__ void load_lnodes(const uint16_t *__restrict__ L, int6
 
 // Element matrix in the arithmetic of the precision mode.  FP64: everything in
 // double.  MIXED: float, FP64 Jacobians for distorted elements.
-template <int NPE, typename AccT, typename S, bool MIXED>
-__device__ __forceinline__ bool element_matrix(const S (*xc)[3], double ce, float thr,
+template <int NPE, typename AccT, typename S, bool MIXED, typename CT>
+__device__ __forceinline__ bool element_matrix(const S (*xc)[3], CT ce, float thr,
                                                AccT (&k)[ElemTraits<NPE>::NP]) {
     if constexpr (MIXED) {
-        if constexpr (NPE == 8) return brick_ke_mixed<S>(xc, (float)ce, thr, k);
-        else return tet_ke_mixed<S>(xc, (float)ce, thr, k);
+        if constexpr (NPE == 8) return brick_ke_mixed<S>(xc, static_cast<float>(ce), thr, k);
+        else return tet_ke_mixed<S>(xc, static_cast<float>(ce), thr, k);
     } else {
-        if constexpr (NPE == 8) brick_ke<double, S>(xc, ce, k);
-        else tet_ke<double, S>(xc, ce, k);
+        if constexpr (NPE == 8) brick_ke<double, S>(xc, static_cast<double>(ce), k);
+        else tet_ke<double, S>(xc, static_cast<double>(ce), k);
         return false;
     }
+}
+
+// Knuth's TwoSum: s + err == a + b exactly (round-to-nearest, no reassociation).
+__device__ __forceinline__ void two_sum_acc(float2 &acc, float x) {
+    const float s = acc.x + x;
+    const float bp = s - acc.x;
+    const float err = (acc.x - (s - bp)) + (x - bp);
+    acc.x = s;
+    acc.y += err;
 }
 
 // ------------------------------------------------------------- k_integrate
@@ -94,7 +103,7 @@ __global__ void __launch_bounds__(INT_THREADS) k_integrate(const int32_t *__rest
                 xc[a][2] = __ldg(X + 3 * (int64_t)g[a] + 2);
             }
             T k[NP];
-            fl = element_matrix<NPE, T, S, MIXED>(xc, (double)__ldg(c + e), thr, k);
+            fl = element_matrix<NPE, T, S, MIXED>(xc, __ldg(c + e), thr, k);
 #pragma unroll
             for (int p = 0; p < NP; ++p) st[threadIdx.x * LD + p] = k[p];
         }
@@ -122,7 +131,8 @@ __host__ __device__ constexpr int tri_row(int q) {
 template <int NPE, typename AccT, bool MIXED>
 __device__ __forceinline__ void scatter_element(const uint8_t *__restrict__ posp, const uint16_t (&ln)[NPE],
                                                 const int32_t *cown, const int32_t *roff, const uint8_t *hvf,
-                                                double *hv, AccT *acc, const AccT (&kv)[NPE * (NPE + 1) / 2]) {
+                                                void *hv, bool fp64_sums, AccT *acc,
+                                                const AccT (&kv)[NPE * (NPE + 1) / 2]) {
     constexpr int NP = NPE * (NPE + 1) / 2;
     constexpr int NW = (NP + 3) / 4;
     uint32_t pw[NW];
@@ -145,7 +155,8 @@ __device__ __forceinline__ void scatter_element(const uint8_t *__restrict__ posp
         for (int a = 0; a < NPE; ++a) {
             const int q = a * (a + 1) / 2 + a;
             if (rbase[a] >= 0 && hvf[own[a]]) {
-                hv[own[a]] += (double)kv[q];
+                if (fp64_sums) static_cast<double *>(hv)[own[a]] += (double)kv[q];
+                else two_sum_acc(static_cast<float2 *>(hv)[own[a]], (float)kv[q]);
                 rbase[a] = -2 - rbase[a];  // keep off-diagonals, mark the diagonal
             }
         }
@@ -186,7 +197,7 @@ template <int NPE, typename AccT, typename S, typename CT, bool FUSED, bool MIXE
 __global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch(PlanView pv, const S *__restrict__ X,
                                                              const CT *__restrict__ c, const AccT *__restrict__ ke,
                                                              AccT *__restrict__ vals, float thr, int64_t p0,
-                                                             int64_t p1, PatchSmem L) {
+                                                             int64_t p1, PatchSmem L, bool fp64_sums) {
     constexpr int NP = ElemTraits<NPE>::NP;
     extern __shared__ __align__(16) unsigned char patch_smem[];
     AccT *acc = reinterpret_cast<AccT *>(patch_smem + L.acc);
@@ -219,7 +230,7 @@ __global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch(PlanView pv, const 
             roff[k] = pv.own_acc[nb + k];
             rps[k] = pv.own_rowptr[nb + k];
             if constexpr (MIXED) {
-                hv[k] = 0.0;
+                hv[k] = 0.0;  // also clears the (hi, lo) float pair
                 hvf[k] = pv.own_hv[nb + k];
             }
         }
@@ -273,7 +284,7 @@ __global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch(PlanView pv, const 
                         xc[a][1] = xs[ln[a]][1];
                         xc[a][2] = xs[ln[a]][2];
                     }
-                    element_matrix<NPE, AccT, S, MIXED>(xc, (double)ce, thr, kv);
+                    element_matrix<NPE, AccT, S, MIXED>(xc, ce, thr, kv);
                 } else {
                     const int64_t e = pv.celem_id[ci];
 #pragma unroll
@@ -283,8 +294,9 @@ __global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch(PlanView pv, const 
             const int last = min(base + nthr, nel) - 1;
             const int c0 = pv.celem_color[eb + base], c1 = pv.celem_color[eb + last];
             for (int cc = c0; cc <= c1; ++cc) {
-                if (mycol == cc) scatter_element<NPE, AccT, MIXED>(pv.celem_pos + ci * ((NP + 3) / 4 * 4), ln, cown, roff,
-                                                                    hvf, hv, acc, kv);
+                if (mycol == cc)
+                    scatter_element<NPE, AccT, MIXED>(pv.celem_pos + ci * ((NP + 3) / 4 * 4), ln, cown, roff, hvf, hv,
+                                                      fp64_sums, acc, kv);
                 __syncthreads();
             }
         }
@@ -296,7 +308,13 @@ __global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch(PlanView pv, const 
             const bool h = MIXED && hvf[k];
             for (int j = lane; j < len; j += 32) {
                 AccT v = acc[o0 + j];
-                if (h && j == len - 1) v = (AccT)hv[k];
+                if (h && j == len - 1) {
+                    if (fp64_sums) v = (AccT)hv[k];
+                    else {
+                        const float2 pr = reinterpret_cast<const float2 *>(hv)[k];
+                        v = (AccT)(pr.x + pr.y);  // the pair rounded once
+                    }
+                }
                 vals[rp + j] = v;
             }
         }
@@ -402,7 +420,7 @@ static fem_status launch_patch_t(const PatchArgs &a, cudaStream_t s) {
     if (np <= 0) return FEM_OK;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np, (int64_t)num_sms() * per_sm));
     f<<<grid, threads, L.total, s>>>(P.view(), (const S *)a.X, (const CT *)a.c, (const AccT *)a.ke, (AccT *)a.vals,
-                                     a.thr, a.p0, a.p1, L);
+                                     a.thr, a.p0, a.p1, L, a.fp64_sums);
     FEM_LAUNCHED("k_patch");
     return FEM_OK;
 }

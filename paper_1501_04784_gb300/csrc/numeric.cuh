@@ -34,6 +34,7 @@ struct PatchArgs {
     float thr;
     int64_t p0, p1;
     int threads, blocks_per_sm;
+    bool fp64_sums;  // high-valence sums with FP64 adds instead of FP32 TwoSum pairs
 };
 
 fem_status launch_integrate(const IntegrateArgs &a, cudaStream_t s);

@@ -189,3 +189,20 @@ def test_full_size_1M_bricks_sampled(fem, prec):
         assert np.array_equal(cl[a:b], cols)
         worst = max(worst, rel_err(vals[a:b], v, cs))
     assert worst <= (TOL_FP64 if prec == "fp64" else TOL_MIXED), worst
+
+
+@pytest.mark.parametrize("fp64_sums", [0, 1])
+def test_high_valence_summation_modes(fem, fp64_sums):
+    """Tet diagonals (up to 24 contributions) are summed FP64-accurately either by
+    FP32 TwoSum pairs (default) or by FP64 adds; both round once to FP32."""
+    m = MESHES["tet10_perm"]()
+    mesh = make(fem, m, fp64_sums=fp64_sums)
+    Xd, cd, X, c = inputs(m, "mixed")
+    ref = oracle_K(m, X, c)
+    vals = mesh.build_K(Xd, cd, "mixed").cpu().numpy()
+    assert rel_err(vals, ref["vals"], ref["cs"]) <= TOL_MIXED
+    rp = ref["rowptr"]
+    diag = rp[1:] - 1
+    # the diagonal sum itself: within a few FP32 roundings of the exact sum
+    d_err = np.abs(vals[diag].astype(np.float64) - ref["vals"][diag]) / ref["cs"][diag]
+    assert d_err.max() <= 4e-7
