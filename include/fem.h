@@ -205,6 +205,37 @@ fem_status fem_mesh_info(fem_mesh m, fem_info *info);
  * benchmarks that count the work inside a timed region). */
 int64_t fem_launch_count(int reset);
 
+/*
+ * Allocation-free variant of the symbolic phase (the paper has no counterpart:
+ * it exists for callers that cannot allocate device memory -- code under an
+ * external memory manager that owns the device heap, plugins that may only
+ * touch the buffers they are handed, or callers that must keep allocation and
+ * its implicit synchronisation out of their stream).
+ *
+ * Computes the same lower-CSR pattern as fem_pattern (bit-identical rowptr and
+ * col) for E [n_elems][npe] (device, 16-byte aligned) into rowptr [n_nodes + 1]
+ * (device) and col [col_capacity] (device), and writes nnz to *nnz_out (host).
+ * It needs no mesh handle and calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Its working memory is one static device array of
+ * FEM_NOALLOC_SCRATCH_BYTES (16 MiB) inside the library, which every GPU that
+ * loads the library holds until the process exits; the scratch needed is about
+ * 24 * n_nodes + 4 * npe * n_elems bytes (about 300,000 bricks).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - Every call shares the array and leaves its contents behind; each call
+ *     clears what must start at zero.  Calls that overlap on the GPU (other
+ *     streams, other host threads) race on the array: serialise them.
+ *   - Blocks the calling thread (reads sizes back).
+ * Errors: FEM_ERR_ARG (bad sizes or pointers; col_capacity < nnz, in which
+ * case *nnz_out still receives nnz), FEM_ERR_BUDGET (mesh larger than the
+ * scratch), FEM_ERR_INDEX, FEM_ERR_DEGENERATE, FEM_ERR_UNSUPPORTED, FEM_ERR_CUDA.
+ */
+#define FEM_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+fem_status fem_pattern_noalloc(fem_elem type, int64_t n_nodes, int64_t n_elems, const int32_t *E,
+                               int64_t *rowptr, int32_t *col, int64_t col_capacity, int64_t *nnz_out,
+                               void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,7 +39,7 @@ class fem_info(ctypes.Structure):
 EXPORTS = ["fem_options_default", "fem_status_str", "fem_last_error", "fem_mesh_create", "fem_mesh_destroy",
            "fem_pattern", "fem_get_pattern", "fem_pattern_ptrs", "fem_integrate_local", "fem_assemble_csr",
            "fem_build_K", "fem_build_K_host", "fem_vjp", "fem_build_K_batched", "fem_sync", "fem_mesh_info",
-           "fem_launch_count"]
+           "fem_launch_count", "fem_pattern_noalloc"]
 
 _lib = None
 
@@ -96,6 +96,8 @@ def load(build_if_missing: bool = False):
     L.fem_mesh_info.restype = S
     L.fem_launch_count.argtypes = [INT]
     L.fem_launch_count.restype = I64
+    L.fem_pattern_noalloc.argtypes = [INT, I64, I64, P, P, P, I64, ctypes.POINTER(I64), P]
+    L.fem_pattern_noalloc.restype = S
     _lib = L
     return L
 

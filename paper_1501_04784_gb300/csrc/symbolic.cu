@@ -761,3 +761,51 @@ fem_status build_pattern_and_plan(fem_mesh m, cudaStream_t s) {
 }
 
 }  // namespace fem
+
+// ------------------------------------------------ pattern over caller scratch
+// The steps of the row-wise pattern above, run over scratch memory the caller
+// provides (used by the allocation-free entry point; the mesh-handle path
+// allocates its own).  Scratch layout and sizes: see noalloc.cu.
+namespace fem {
+
+fem_status pattern_steps_validate(const int32_t *E, int64_t nel, int npe, int64_t N, unsigned long long *flags,
+                                  cudaStream_t s) {
+    FEM_CUDA(cudaMemsetAsync(flags, 0xff, 2 * sizeof(unsigned long long), s));
+    k_validate<<<grid_for(nel), TPB, 0, s>>>(E, nel, npe, N, flags, flags + 1);
+    FEM_LAUNCHED("k_validate");
+    return FEM_OK;
+}
+
+fem_status pattern_steps_incidence(const int32_t *E, int64_t nel, int npe, int64_t N, int64_t *deg, int64_t *inc_ptr,
+                                   unsigned int *cursor, int32_t *inc_elem, int64_t *scan_tmp,
+                                   unsigned long long *mx, cudaStream_t s) {
+    const int64_t n_ent = nel * npe;
+    FEM_CUDA(cudaMemsetAsync(deg, 0, (N + 1) * sizeof(int64_t), s));
+    FEM_CUDA(cudaMemsetAsync(cursor, 0, N * sizeof(unsigned int), s));
+    FEM_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
+    k_degree<<<grid_for(n_ent), TPB, 0, s>>>(E, n_ent, reinterpret_cast<unsigned long long *>(deg));
+    FEM_LAUNCHED("k_degree");
+    FEM_TRY(scan_exclusive_i64(deg, inc_ptr, N, true, scan_tmp, s));
+    k_inc_fill<<<grid_for(n_ent), TPB, 0, s>>>(E, n_ent, npe, inc_ptr, cursor, inc_elem);
+    FEM_LAUNCHED("k_inc_fill");
+    k_inc_sort<<<grid_for(N), TPB, 0, s>>>(inc_ptr, inc_elem, N);
+    FEM_LAUNCHED("k_inc_sort");
+    k_max_deg<<<grid_for(N), TPB, 0, s>>>(inc_ptr, N, mx);
+    FEM_LAUNCHED("k_max_deg");
+    return FEM_OK;
+}
+
+fem_status pattern_steps_rows(const int32_t *E, int npe, int64_t N, const int64_t *inc_ptr, const int32_t *inc_elem,
+                              int cap, int64_t *cnt, const int64_t *rowptr, int32_t *col, cudaStream_t s) {
+    const int wpb = 8;
+    const size_t smem = (size_t)wpb * (cap > 0 ? cap : 1) * sizeof(int32_t);
+    const unsigned grid = (unsigned)std::min<int64_t>(cdiv(N, wpb), (int64_t)num_sms() * 64);
+    if (npe == 8)
+        k_row_pattern<8><<<grid, wpb * 32, smem, s>>>(E, inc_ptr, inc_elem, N, cap, cnt, rowptr, col);
+    else
+        k_row_pattern<4><<<grid, wpb * 32, smem, s>>>(E, inc_ptr, inc_elem, N, cap, cnt, rowptr, col);
+    FEM_LAUNCHED("k_row_pattern");
+    return FEM_OK;
+}
+
+}  // namespace fem
