@@ -195,6 +195,29 @@ fem_status fem_build_K_batched(const fem_mesh *meshes, int n, fem_prec p, const 
                                fem_dtype x_dtype, const void *const *c, fem_dtype c_dtype,
                                void *const *vals, void *stream);
 
+/* Launch shape the batched build of exactly these meshes was tuned to (after a
+ * first fem_build_K_batched call on them).  FEM_ERR_STATE otherwise. */
+fem_status fem_batched_config(const fem_mesh *meshes, int n, fem_prec p, int *block_threads, int *blocks_per_sm,
+                              int *grid);
+
+typedef struct {
+    int patch_entries;  /* chosen assembly tile: lower-CSR entries per thread block */
+    int block_threads;  /* chosen threads per block (elements integrated per batch) */
+    float ms;           /* time of one fem_build_K with the chosen configuration */
+    int tried;          /* candidate configurations timed */
+    int reserved[4];
+} fem_tuning;
+
+/*
+ * Tuner: rebuilds the mesh's plan for each candidate patch size (the assembly
+ * tile) and times fem_build_K for each candidate block size on the given inputs
+ * (vals is overwritten); the mesh keeps the fastest configuration.  Gauss-point
+ * unrolling is not a candidate: the sum-factorised brick couples all 8 points.
+ * Blocks.  FEM_ERR_STATE before fem_pattern.
+ */
+fem_status fem_autotune(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c, fem_dtype c_dtype,
+                        void *vals, void *stream, fem_tuning *out);
+
 /* Wait for the mesh's work on `stream` and report any asynchronous error. */
 fem_status fem_sync(fem_mesh m, void *stream);
 

@@ -36,10 +36,15 @@ class fem_info(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 7)]
 
 
+class fem_tuning(ctypes.Structure):
+    _fields_ = [("patch_entries", ctypes.c_int), ("block_threads", ctypes.c_int), ("ms", ctypes.c_float),
+                ("tried", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+
+
 EXPORTS = ["fem_options_default", "fem_status_str", "fem_last_error", "fem_mesh_create", "fem_mesh_destroy",
            "fem_pattern", "fem_get_pattern", "fem_pattern_ptrs", "fem_integrate_local", "fem_assemble_csr",
            "fem_build_K", "fem_build_K_host", "fem_vjp", "fem_build_K_batched", "fem_sync", "fem_mesh_info",
-           "fem_launch_count", "fem_pattern_noalloc"]
+           "fem_launch_count", "fem_pattern_noalloc", "fem_batched_config", "fem_autotune"]
 
 _lib = None
 
@@ -98,6 +103,11 @@ def load(build_if_missing: bool = False):
     L.fem_launch_count.restype = I64
     L.fem_pattern_noalloc.argtypes = [INT, I64, I64, P, P, P, I64, ctypes.POINTER(I64), P]
     L.fem_pattern_noalloc.restype = S
+    L.fem_batched_config.argtypes = [ctypes.POINTER(P), INT, INT, ctypes.POINTER(INT), ctypes.POINTER(INT),
+                                     ctypes.POINTER(INT)]
+    L.fem_batched_config.restype = S
+    L.fem_autotune.argtypes = [P, INT, P, INT, P, INT, P, P, ctypes.POINTER(fem_tuning)]
+    L.fem_autotune.restype = S
     _lib = L
     return L
 

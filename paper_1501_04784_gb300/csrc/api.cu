@@ -12,6 +12,8 @@ fem_status launch_vjp(fem_mesh m, bool mixed, const void *X, fem_dtype xd, const
                       const void *G, void *dX, void *dc, cudaStream_t s);
 fem_status launch_batched(const fem_mesh *ms, int n, bool mixed, const void *const *X, fem_dtype xd,
                           const void *const *c, fem_dtype cd, void *const *vals, cudaStream_t s);
+fem_status batched_query(const fem_mesh *ms, int n, bool mixed, int *threads, int *blocks_per_sm, int *grid);
+void batch_forget(fem_mesh m);
 }  // namespace fem
 
 using namespace fem;
@@ -152,6 +154,7 @@ fem_status fem_mesh_create(fem_mesh *out, fem_elem type, int64_t n_nodes, int64_
 void fem_mesh_destroy(fem_mesh m) {
     if (!m) return;
     cudaDeviceSynchronize();
+    batch_forget(m);
     delete m;
 }
 
@@ -222,6 +225,7 @@ fem_status fem_integrate_local(fem_mesh m, fem_prec p, const void *X, fem_dtype 
 static PatchArgs patch_args(fem_mesh m, fem_prec p, bool fused) {
     PatchArgs a{};
     a.plan = &m->plan;
+    a.closure = nullptr;
     a.npe = m->npe;
     a.mixed = p == FEM_MIXED;
     a.fused = fused;
@@ -259,7 +263,11 @@ fem_status fem_assemble_csr(fem_mesh m, fem_prec p, const void *ke, void *vals, 
     a.cd = FEM_F32;
     a.ke = ke;
     a.vals = vals;
-    return launch_patch(a, as_stream(stream));
+    cudaStream_t s = as_stream(stream);
+    return for_each_group(m, s, [&](const Closure &cl) {
+        a.closure = &cl;
+        return launch_patch(a, s);
+    });
 }
 
 fem_status fem_build_K(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c, fem_dtype c_dtype,
@@ -279,7 +287,11 @@ fem_status fem_build_K(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype,
     a.X = X;
     a.c = c;
     a.vals = vals;
-    return launch_patch(a, as_stream(stream));
+    cudaStream_t s = as_stream(stream);
+    return for_each_group(m, s, [&](const Closure &cl) {
+        a.closure = &cl;
+        return launch_patch(a, s);
+    });
 }
 
 fem_status fem_build_K_host(fem_mesh m, fem_prec p, const void *X_host, fem_dtype x_dtype, const void *c_host,
@@ -342,7 +354,91 @@ fem_status fem_build_K_batched(const fem_mesh *meshes, int n, fem_prec p, const 
         }
     }
     if (n == 0) return FEM_OK;
+    for (int i = 0; i < n; ++i)
+        if (meshes[i]->plan.chunked) {
+            set_error("mesh %d of the batch is planned in groups under its memory budget", i);
+            return FEM_ERR_UNSUPPORTED;
+        }
     return launch_batched(meshes, n, p == FEM_MIXED, X, x_dtype, c, c_dtype, vals, as_stream(stream));
+}
+
+fem_status fem_batched_config(const fem_mesh *meshes, int n, fem_prec p, int *block_threads, int *blocks_per_sm,
+                              int *grid) {
+    if (!meshes || n <= 0) {
+        set_error("bad batch arguments");
+        return FEM_ERR_ARG;
+    }
+    return batched_query(meshes, n, p == FEM_MIXED, block_threads, blocks_per_sm, grid);
+}
+
+// Tuner of the assembly tile (patch size) and of the threads per block: the
+// plan is rebuilt for each candidate patch size and every candidate is timed on
+// the caller's inputs; the mesh keeps the fastest.
+fem_status fem_autotune(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c, fem_dtype c_dtype,
+                        void *vals, void *stream, fem_tuning *out) {
+    FEM_TRY(check_inputs(m, p, X, x_dtype, c, c_dtype));
+    if (!m->has_pattern) {
+        set_error("fem_autotune before fem_pattern");
+        return FEM_ERR_STATE;
+    }
+    if (!vals) {
+        set_error("null vals");
+        return FEM_ERR_ARG;
+    }
+    cudaStream_t s = as_stream(stream);
+    const fem_options keep = m->opt;
+    static const int entries[] = {4096, 6144, 8192, 12288, 16384};
+    static const int threads[] = {128, 256, 512};
+    float best = 1e30f;
+    int best_e = 0, best_t = 0, tried = 0;
+    cudaEvent_t e0, e1;
+    FEM_CUDA(cudaEventCreate(&e0));
+    FEM_CUDA(cudaEventCreate(&e1));
+    for (int pe : entries) {
+        m->opt = keep;
+        m->opt.patch_entries = pe;
+        if (build_plan(m, s) != FEM_OK) continue;
+        for (int t : threads) {
+            m->opt.block_threads = t;
+            m->opt.blocks_per_sm = 0;
+            if (fem_build_K(m, p, X, x_dtype, c, c_dtype, vals, stream) != FEM_OK) continue;
+            float tot = 0.f;
+            for (int r = 0; r < 3; ++r) {
+                FEM_CUDA(cudaEventRecord(e0, s));
+                FEM_TRY(fem_build_K(m, p, X, x_dtype, c, c_dtype, vals, stream));
+                FEM_CUDA(cudaEventRecord(e1, s));
+                FEM_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                FEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                tot += ms;
+            }
+            ++tried;
+            if (tot < best) {
+                best = tot;
+                best_e = pe;
+                best_t = t;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    m->opt = keep;
+    if (!tried) {
+        FEM_TRY(build_plan(m, s));
+        set_error("no candidate configuration ran");
+        return FEM_ERR_UNSUPPORTED;
+    }
+    m->opt.patch_entries = best_e;
+    m->opt.block_threads = best_t;
+    FEM_TRY(build_plan(m, s));
+    if (out) {
+        std::memset(out, 0, sizeof(*out));
+        out->patch_entries = best_e;
+        out->block_threads = best_t;
+        out->ms = best / 3.f;
+        out->tried = tried;
+    }
+    return FEM_OK;
 }
 
 fem_status fem_sync(fem_mesh m, void *stream) {

@@ -11,6 +11,8 @@
 // the result is bitwise reproducible without atomics.
 #pragma once
 
+#include <functional>
+
 #include "common.cuh"
 
 namespace fem {
@@ -33,26 +35,58 @@ struct PlanView {
     int64_t n_patches;
 };
 
-struct Plan {
-    int64_t n_patches = 0, total_cnodes = 0, total_celems = 0;
-    int64_t max_acc = 0, max_cnodes = 0, max_own = 0, max_celems = 0;
+// Closure data of a range of patches [p0, p1): the elements each patch
+// integrates and the nodes they touch.  Patch indices inside are relative to p0.
+struct Closure {
+    int64_t p0 = 0, p1 = 0, total_cnodes = 0, total_celems = 0;
+    int64_t max_cnodes = 0, max_celems = 0;
     int n_colors = 0;
-    int pos_stride = 0;
-    DevBuf<int64_t> patch_node_ptr, patch_elem_ptr, patch_cnode_ptr, own_rowptr;
-    DevBuf<int32_t> patch_acc, own_acc, cnode_gid, cnode_own, celem_id, own_row, node_patch, own_idx;
-    DevBuf<uint8_t> own_hv, celem_color, celem_pos;
+    DevBuf<int64_t> patch_elem_ptr, patch_cnode_ptr;
+    DevBuf<int32_t> cnode_gid, cnode_own, celem_id;
+    DevBuf<uint8_t> celem_color, celem_pos;
     DevBuf<uint16_t> celem_lnode;
-    PlanView view() const {
-        return PlanView{patch_node_ptr.ptr, patch_elem_ptr.ptr, patch_cnode_ptr.ptr, patch_acc.ptr,
-                        own_acc.ptr,        own_rowptr.ptr,     own_hv.ptr,          cnode_gid.ptr,
-                        cnode_own.ptr,      celem_id.ptr,       celem_color.ptr,     celem_lnode.ptr,
-                        celem_pos.ptr,      own_row.ptr,        n_patches};
+    void reset() {
+        patch_elem_ptr.free(); patch_cnode_ptr.free(); cnode_gid.free(); cnode_own.free(); celem_id.free();
+        celem_color.free(); celem_pos.free(); celem_lnode.free();
+        p0 = p1 = total_cnodes = total_celems = max_cnodes = max_celems = 0;
+        n_colors = 0;
     }
     size_t bytes() const {
-        return patch_node_ptr.bytes() + patch_elem_ptr.bytes() + patch_cnode_ptr.bytes() + own_rowptr.bytes() +
-               patch_acc.bytes() + own_acc.bytes() + cnode_gid.bytes() + cnode_own.bytes() + celem_id.bytes() +
-               own_row.bytes() + node_patch.bytes() + own_idx.bytes() + own_hv.bytes() + celem_color.bytes() +
-               celem_pos.bytes() + celem_lnode.bytes();
+        return patch_elem_ptr.bytes() + patch_cnode_ptr.bytes() + cnode_gid.bytes() + cnode_own.bytes() +
+               celem_id.bytes() + celem_color.bytes() + celem_pos.bytes() + celem_lnode.bytes();
+    }
+};
+
+struct Plan {
+    int64_t n_patches = 0;
+    int64_t max_acc = 0, max_own = 0;
+    int pos_stride = 0;
+    DevBuf<int64_t> patch_node_ptr, own_rowptr;
+    DevBuf<int32_t> patch_acc, own_acc, own_row, node_patch, own_idx;
+    DevBuf<uint8_t> own_hv;
+    Closure full;          // closure of every patch, when it fits the memory budget
+    bool chunked = false;  // closures built per patch group at each numeric call
+    // aggregate statistics (over all groups when chunked)
+    int64_t total_cnodes = 0, total_celems = 0, max_cnodes = 0, max_celems = 0;
+    int n_colors = 0;
+    PlanView view(const Closure &cl) const {
+        return PlanView{patch_node_ptr.ptr + cl.p0, cl.patch_elem_ptr.ptr, cl.patch_cnode_ptr.ptr,
+                        patch_acc.ptr + cl.p0,    own_acc.ptr,           own_rowptr.ptr,
+                        own_hv.ptr,               cl.cnode_gid.ptr,      cl.cnode_own.ptr,
+                        cl.celem_id.ptr,          cl.celem_color.ptr,    cl.celem_lnode.ptr,
+                        cl.celem_pos.ptr,         own_row.ptr,           cl.p1 - cl.p0};
+    }
+    PlanView view() const { return view(full); }
+    void reset() {
+        patch_node_ptr.free(); own_rowptr.free(); patch_acc.free(); own_acc.free(); own_row.free();
+        node_patch.free(); own_idx.free(); own_hv.free(); full.reset();
+        n_patches = max_acc = max_own = total_cnodes = total_celems = max_cnodes = max_celems = 0;
+        n_colors = 0;
+        chunked = false;
+    }
+    size_t bytes() const {
+        return patch_node_ptr.bytes() + own_rowptr.bytes() + patch_acc.bytes() + own_acc.bytes() + own_row.bytes() +
+               node_patch.bytes() + own_idx.bytes() + own_hv.bytes() + full.bytes();
     }
 };
 
@@ -77,10 +111,18 @@ struct fem_mesh_s {
     // staging for the _host entry point
     fem::DevBuf<unsigned char> host_stage;
     int n_groups = 1;
+    int64_t group_patches = 0;  // patches per group when the closures are built per group
 };
 
 namespace fem {
 fem_status build_locality_order(fem_mesh m, const void *X, fem_dtype xd, cudaStream_t s);
 fem_status validate_connectivity(fem_mesh m, cudaStream_t s);
 fem_status build_pattern_and_plan(fem_mesh m, cudaStream_t s);
+void batch_forget(fem_mesh m);  // drops cached batched launches that use m's plan
+fem_status build_pattern(fem_mesh m, cudaStream_t s);
+fem_status build_plan(fem_mesh m, cudaStream_t s);
+fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaStream_t s);
+// Runs fn over the closure of every patch group (one group covering all patches
+// unless the plan is chunked under the memory budget).
+fem_status for_each_group(fem_mesh m, cudaStream_t s, const std::function<fem_status(const Closure &)> &fn);
 }  // namespace fem

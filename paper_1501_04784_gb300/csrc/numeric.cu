@@ -193,11 +193,12 @@ __device__ __forceinline__ void scatter_element(const uint8_t *__restrict__ posp
 }
 
 // ------------------------------------------------------------------ k_patch
+// One patch: owned rows' accumulators in shared memory, the closure integrated
+// batch by batch and added colour by colour, each owned row written once.
 template <int NPE, typename AccT, typename S, typename CT, bool FUSED, bool MIXED>
-__global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch(PlanView pv, const S *__restrict__ X,
-                                                             const CT *__restrict__ c, const AccT *__restrict__ ke,
-                                                             AccT *__restrict__ vals, float thr, int64_t p0,
-                                                             int64_t p1, PatchSmem L, bool fp64_sums) {
+__device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restrict__ X, const CT *__restrict__ c,
+                                           const AccT *__restrict__ ke, AccT *__restrict__ vals, float thr,
+                                           int64_t p, const PatchSmem &L, bool fp64_sums) {
     constexpr int NP = ElemTraits<NPE>::NP;
     extern __shared__ __align__(16) unsigned char patch_smem[];
     AccT *acc = reinterpret_cast<AccT *>(patch_smem + L.acc);
@@ -208,11 +209,9 @@ __global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch(PlanView pv, const 
     uint8_t *hvf = patch_smem + L.hvf;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
-
     int64_t *rps = reinterpret_cast<int64_t *>(patch_smem + L.rps);
     int32_t *gid = reinterpret_cast<int32_t *>(patch_smem + L.gid);
-
-    for (int64_t p = p0 + blockIdx.x; p < p1; p += gridDim.x) {
+    {
         const int64_t nb = pv.patch_node_ptr[p];
         const int nown = (int)(pv.patch_node_ptr[p + 1] - nb);
         const int64_t cb = pv.patch_cnode_ptr[p];
@@ -322,6 +321,34 @@ __global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch(PlanView pv, const 
     }
 }
 
+template <int NPE, typename AccT, typename S, typename CT, bool FUSED, bool MIXED>
+__global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch(PlanView pv, const S *__restrict__ X,
+                                                             const CT *__restrict__ c, const AccT *__restrict__ ke,
+                                                             AccT *__restrict__ vals, float thr, int64_t p0,
+                                                             int64_t p1, PatchSmem L, bool fp64_sums) {
+    for (int64_t p = p0 + blockIdx.x; p < p1; p += gridDim.x)
+        patch_body<NPE, AccT, S, CT, FUSED, MIXED>(pv, X, c, ke, vals, thr, p, L, fp64_sums);
+}
+
+// Persistent kernel over the patches of many meshes: work item w is patch
+// w - prefix[m] of mesh m, prefix[m] <= w < prefix[m + 1].
+template <int NPE, typename AccT, typename S, typename CT, bool MIXED>
+__global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch_batched(const BatchItem *__restrict__ items,
+                                                                     const int64_t *__restrict__ prefix, int n,
+                                                                     PatchSmem L, bool fp64_sums) {
+    const int64_t total = prefix[n];
+    for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+        int lo = 0, hi = n;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (prefix[mid] <= w) lo = mid; else hi = mid;
+        }
+        const BatchItem &it = items[lo];
+        patch_body<NPE, AccT, S, CT, true, MIXED>(it.pv, (const S *)it.X, (const CT *)it.c, nullptr,
+                                                   (AccT *)it.vals, it.thr, w - prefix[lo], L, fp64_sums);
+    }
+}
+
 // ------------------------------------------------------------------ launchers
 template <typename F>
 static fem_status set_smem(F *f, size_t bytes) {
@@ -369,7 +396,7 @@ fem_status launch_integrate(const IntegrateArgs &a, cudaStream_t s) {
 
 static size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-PatchSmem patch_smem_layout(const Plan &P, bool fused, bool mixed, size_t xsize, size_t csize) {
+PatchSmem patch_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsize, size_t csize) {
     PatchSmem L{};
     const size_t accsz = mixed ? sizeof(float) : sizeof(double);
     size_t o = 0;
@@ -398,7 +425,10 @@ PatchSmem patch_smem_layout(const Plan &P, bool fused, bool mixed, size_t xsize,
 template <int NPE, typename AccT, typename S, typename CT, bool FUSED, bool MIXED>
 static fem_status launch_patch_t(const PatchArgs &a, cudaStream_t s) {
     const Plan &P = *a.plan;
-    const PatchSmem L = patch_smem_layout(P, FUSED, MIXED, sizeof(S), sizeof(CT));
+    const Closure &cl = a.closure ? *a.closure : P.full;
+    PlanMax pm;
+    pm.add(P);
+    const PatchSmem L = patch_smem_layout(pm, FUSED, MIXED, sizeof(S), sizeof(CT));
     int dev = 0, max_optin = 0;
     FEM_CUDA(cudaGetDevice(&dev));
     FEM_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -416,11 +446,11 @@ static fem_status launch_patch_t(const PatchArgs &a, cudaStream_t s) {
         return FEM_ERR_UNSUPPORTED;
     }
     if (a.blocks_per_sm > 0 && a.blocks_per_sm < per_sm) per_sm = a.blocks_per_sm;
-    const int64_t np = a.p1 - a.p0;
+    const int64_t np = cl.p1 - cl.p0;
     if (np <= 0) return FEM_OK;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np, (int64_t)num_sms() * per_sm));
-    f<<<grid, threads, L.total, s>>>(P.view(), (const S *)a.X, (const CT *)a.c, (const AccT *)a.ke, (AccT *)a.vals,
-                                     a.thr, a.p0, a.p1, L, a.fp64_sums);
+    f<<<grid, threads, L.total, s>>>(P.view(cl), (const S *)a.X, (const CT *)a.c, (const AccT *)a.ke, (AccT *)a.vals,
+                                     a.thr, 0, np, L, a.fp64_sums);
     FEM_LAUNCHED("k_patch");
     return FEM_OK;
 }
@@ -450,6 +480,55 @@ fem_status launch_patch(const PatchArgs &a, cudaStream_t s) {
     if (a.xd == FEM_F64 && a.cd == FEM_F32) FEM_P(4, float, double, float, true, true);
     FEM_P(4, float, double, double, true, true);
 #undef FEM_P
+}
+
+template <int NPE, typename AccT, bool MIXED>
+static fem_status batched_config_t(const PlanMax &pm, int threads, int blocks_per_sm, BatchLaunch *out) {
+    using T = AccT;
+    const PatchSmem L = patch_smem_layout(pm, true, MIXED, sizeof(T), sizeof(T));
+    int dev = 0, max_optin = 0;
+    FEM_CUDA(cudaGetDevice(&dev));
+    FEM_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (L.total > (size_t)max_optin) {
+        set_error("a patch of the batch needs %zu bytes of shared memory (limit %d)", L.total, max_optin);
+        return FEM_ERR_UNSUPPORTED;
+    }
+    auto f = k_patch_batched<NPE, AccT, T, T, MIXED>;
+    FEM_TRY(set_smem(f, L.total));
+    int per_sm = 0;
+    FEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, L.total));
+    if (per_sm < 1) {
+        set_error("batched kernel cannot be resident with %d threads", threads);
+        return FEM_ERR_UNSUPPORTED;
+    }
+    if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
+    out->L = L;
+    out->threads = threads;
+    out->grid = num_sms() * per_sm;
+    return FEM_OK;
+}
+
+fem_status batched_config(int npe, bool mixed, const PlanMax &pm, int threads, int blocks_per_sm, BatchLaunch *out) {
+    out->npe = npe;
+    out->mixed = mixed;
+    if (mixed) return npe == 8 ? batched_config_t<8, float, true>(pm, threads, blocks_per_sm, out)
+                               : batched_config_t<4, float, true>(pm, threads, blocks_per_sm, out);
+    return npe == 8 ? batched_config_t<8, double, false>(pm, threads, blocks_per_sm, out)
+                    : batched_config_t<4, double, false>(pm, threads, blocks_per_sm, out);
+}
+
+fem_status launch_batched_kernel(const BatchLaunch &bl, cudaStream_t s) {
+#define FEM_B(NPE, T, MX)                                                                                   \
+    k_patch_batched<NPE, T, T, T, MX><<<bl.grid, bl.threads, bl.L.total, s>>>(bl.items, bl.prefix, bl.n, bl.L, \
+                                                                               bl.fp64_sums)
+    if (bl.mixed) {
+        if (bl.npe == 8) FEM_B(8, float, true); else FEM_B(4, float, true);
+    } else {
+        if (bl.npe == 8) FEM_B(8, double, false); else FEM_B(4, double, false);
+    }
+#undef FEM_B
+    FEM_LAUNCHED("k_patch_batched");
+    return FEM_OK;
 }
 
 }  // namespace fem

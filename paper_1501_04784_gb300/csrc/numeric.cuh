@@ -1,6 +1,8 @@
 // numeric.cuh -- launch interfaces of the numeric kernels.
 #pragma once
 
+#include <algorithm>
+
 #include "mesh.cuh"
 
 namespace fem {
@@ -26,6 +28,7 @@ struct IntegrateArgs {
 
 struct PatchArgs {
     const Plan *plan;
+    const Closure *closure;  // the patch group to run (its p0..p1)
     int npe;
     bool mixed, fused;
     fem_dtype xd, cd;
@@ -37,8 +40,42 @@ struct PatchArgs {
     bool fp64_sums;  // high-valence sums with FP64 adds instead of FP32 TwoSum pairs
 };
 
+// Largest per-patch sizes over the plans a launch covers (sizes shared memory).
+struct PlanMax {
+    int64_t max_acc = 0, max_own = 0, max_cnodes = 0;
+    void add(const Plan &P) {
+        max_acc = std::max(max_acc, P.max_acc);
+        max_own = std::max(max_own, P.max_own);
+        max_cnodes = std::max(max_cnodes, P.max_cnodes);
+    }
+};
+
+// One mesh of a batched build.
+struct BatchItem {
+    PlanView pv;
+    const void *X, *c;
+    void *vals;
+    float thr;
+    int pad;
+};
+
+struct BatchLaunch {
+    int npe = 8;
+    bool mixed = true, fp64_sums = false;
+    const BatchItem *items = nullptr;
+    const int64_t *prefix = nullptr;
+    int n = 0;
+    PatchSmem L{};
+    int threads = 256, grid = 1;
+};
+
+// Shared memory, residency and grid of the batched kernel for `threads` threads
+// and at most `blocks_per_sm` blocks per SM (0 = as many as fit).
+fem_status batched_config(int npe, bool mixed, const PlanMax &pm, int threads, int blocks_per_sm, BatchLaunch *out);
+fem_status launch_batched_kernel(const BatchLaunch &bl, cudaStream_t s);
+
 fem_status launch_integrate(const IntegrateArgs &a, cudaStream_t s);
 fem_status launch_patch(const PatchArgs &a, cudaStream_t s);
-PatchSmem patch_smem_layout(const Plan &P, bool fused, bool mixed, size_t xsize, size_t csize);
+PatchSmem patch_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsize, size_t csize);
 
 }  // namespace fem

@@ -10,6 +10,7 @@
 // sparse_create (no global triplet index arrays) -- so its memory is O(npe * nel)
 // integers instead of a global sort of npe(npe+1)/2 * nel (row, col) keys.
 #include <climits>
+#include <functional>
 #include <vector>
 
 #include "mesh.cuh"
@@ -317,12 +318,6 @@ __global__ void k_patch_acc(const int64_t *pre, const int64_t *pn_ptr, int64_t n
 }
 
 // ------------------------------------------------------------- closure lists
-__global__ void k_closure_pairs(const int32_t *__restrict__ E, int64_t n_ent, int npe, const int32_t *node_patch,
-                                uint64_t *keys) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_ent; t += (int64_t)gridDim.x * blockDim.x)
-        keys[t] = ((uint64_t)(uint32_t)node_patch[E[t]] << 32) | (uint64_t)(t / npe);
-}
-
 __global__ void k_unique_flags(const uint64_t *keys, int64_t n, int64_t *flags) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
@@ -354,8 +349,8 @@ static constexpr int COLOR_CHUNK = 2048;
 
 template <int NPE>
 __global__ void k_color(const uint64_t *ckeys, const int64_t *pe_ptr, const int64_t *pn_ptr, const int32_t *E,
-                        const int32_t *node_patch, const int32_t *own_idx, int64_t npatch, uint8_t *color_out,
-                        int *max_color) {
+                        const int32_t *node_patch, const int32_t *own_idx, int64_t npatch, int64_t p0,
+                        uint8_t *color_out, int *max_color) {
     extern __shared__ unsigned long long col_smem[];
     for (int64_t p = blockIdx.x; p < npatch; p += gridDim.x) {
         const int nown = (int)(pn_ptr[p + 1] - pn_ptr[p]);
@@ -370,7 +365,7 @@ __global__ void k_color(const uint64_t *ckeys, const int64_t *pe_ptr, const int6
             for (int t = threadIdx.x; t < cn * NPE; t += blockDim.x) {
                 const int64_t e = (int64_t)(uint32_t)ckeys[b + c0 + t / NPE];
                 const int32_t g = E[e * NPE + t % NPE];
-                tab[t] = node_patch[g] == (int32_t)p ? (int16_t)own_idx[g] : (int16_t)-1;
+                tab[t] = node_patch[g] == (int32_t)(p0 + p) ? (int16_t)own_idx[g] : (int16_t)-1;
             }
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -421,12 +416,12 @@ __global__ void k_cnode_pairs(const uint64_t *ckeys, int64_t nce, int npe, const
     }
 }
 
-__global__ void k_cnode_own(const uint64_t *cn_keys, int64_t ncn, const int32_t *node_patch, const int32_t *own_idx,
-                            int32_t *gid, int32_t *own) {
+__global__ void k_cnode_own(const uint64_t *cn_keys, int64_t ncn, int64_t p0, const int32_t *node_patch,
+                            const int32_t *own_idx, int32_t *gid, int32_t *own) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ncn; j += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t k = cn_keys[j];
         const int32_t g = (int32_t)(k & 0xffffffffull);
-        const int32_t p = (int32_t)(k >> 32);
+        const int32_t p = (int32_t)(p0 + (int64_t)(k >> 32));
         gid[j] = g;
         own[j] = node_patch[g] == p ? own_idx[g] : -1;
     }
@@ -512,9 +507,9 @@ static fem_status sort_unique(Arena &ar, DevBuf<uint64_t> &keys, int64_t n, int 
     return FEM_OK;
 }
 
-fem_status build_pattern_and_plan(fem_mesh m, cudaStream_t s) {
+fem_status build_pattern(fem_mesh m, cudaStream_t s) {
     Arena &ar = m->arena;
-    const int64_t N = m->n_nodes, nel = m->n_elems, npe = m->npe, n_ent = nel * npe;
+    const int64_t N = m->n_nodes, npe = m->npe, n_ent = m->n_elems * npe;
 
     // ---- node -> element incidence
     FEM_TRY(m->inc_ptr.alloc(ar, N + 1, "incidence pointers"));
@@ -591,77 +586,74 @@ fem_status build_pattern_and_plan(fem_mesh m, cudaStream_t s) {
         }
     }
 
-    // ---- patches of consecutive nodes in locality order
+    return FEM_OK;
+}
+
+// Closure pairs of patches [p0, p1) from the node -> element incidence: for every
+// owned node of the range and every element incident to it, the key
+// ((patch - p0) << 32) | element.
+__global__ void k_range_degree(const int32_t *own_row, const int64_t *inc_ptr, int64_t k0, int64_t nk, int64_t *deg) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nk; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = own_row[k0 + k];
+        deg[k] = inc_ptr[g + 1] - inc_ptr[g];
+    }
+}
+
+__global__ void k_range_pairs(const int32_t *own_row, const int32_t *node_patch, const int64_t *inc_ptr,
+                              const int32_t *inc_elem, int64_t k0, int64_t nk, int64_t p0, const int64_t *off,
+                              uint64_t *keys) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nk; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = own_row[k0 + k];
+        const uint64_t pl = (uint64_t)(node_patch[g] - p0);
+        int64_t o = off[k];
+        for (int64_t t = inc_ptr[g]; t < inc_ptr[g + 1]; ++t, ++o) keys[o] = (pl << 32) | (uint64_t)(uint32_t)inc_elem[t];
+    }
+}
+
+fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaStream_t s) {
+    Arena &ar = m->arena;
     Plan &P = m->plan;
-    int64_t cap_entries = m->opt.patch_entries > 0 ? m->opt.patch_entries : 8192;
-    if (cap_entries < 2 * (int64_t)m->max_row_len) cap_entries = 2 * (int64_t)m->max_row_len;
-    const int64_t cap_eff = cap_entries - m->max_row_len;
-    DevBuf<int64_t> pre;
-    {
-        DevBuf<int64_t> len, tmp;
-        FEM_TRY(len.alloc(ar, N + 1, "row lengths"));
-        FEM_TRY(pre.alloc(ar, N + 1, "row length prefix"));
-        k_len_in_order<<<grid_for(N), TPB, 0, s>>>(m->order.ptr, m->rowptr.ptr, N, len.ptr);
-        FEM_LAUNCHED("k_len_in_order");
-        FEM_TRY(tmp.alloc(ar, scan_tmp_elems(N + 1), "scan scratch"));
-        FEM_TRY(scan_exclusive_i64(len.ptr, pre.ptr, N, true, tmp.ptr, s));
-    }
-    P.n_patches = m->nnz > 0 ? cdiv(m->nnz, cap_eff) : 1;
-    const int64_t npatch = P.n_patches;
-    if (npatch >= (1ll << 23)) {
-        set_error("too many patches (%lld)", (long long)npatch);
-        return FEM_ERR_UNSUPPORTED;
-    }
-    FEM_TRY(P.patch_node_ptr.alloc(ar, npatch + 1, "patch node ptr"));
-    k_patch_bounds<<<grid_for(npatch + 1), TPB, 0, s>>>(pre.ptr, N, cap_eff, npatch, P.patch_node_ptr.ptr);
-    FEM_LAUNCHED("k_patch_bounds");
-    FEM_TRY(P.node_patch.alloc(ar, N, "node patch"));
-    FEM_TRY(P.own_idx.alloc(ar, N, "own index"));
-    FEM_TRY(P.own_row.alloc(ar, N, "own row"));
-    FEM_TRY(P.own_rowptr.alloc(ar, N, "own rowptr"));
-    FEM_TRY(P.own_acc.alloc(ar, N, "own acc"));
-    FEM_TRY(P.own_hv.alloc(ar, N, "own hv"));
-    FEM_TRY(P.patch_acc.alloc(ar, npatch, "patch acc"));
-    const int hv_thr = m->opt.valence_threshold;
-    k_patch_nodes<<<grid_for(N), TPB, 0, s>>>(m->order.ptr, pre.ptr, P.patch_node_ptr.ptr, N, cap_eff, npatch,
-                                              m->rowptr.ptr, m->inc_ptr.ptr, hv_thr, P.node_patch.ptr, P.own_idx.ptr,
-                                              P.own_row.ptr, P.own_rowptr.ptr, P.own_acc.ptr, P.own_hv.ptr);
-    FEM_LAUNCHED("k_patch_nodes");
-    k_patch_acc<<<grid_for(npatch), TPB, 0, s>>>(pre.ptr, P.patch_node_ptr.ptr, npatch, P.patch_acc.ptr);
-    FEM_LAUNCHED("k_patch_acc");
-    pre.free();
-    const int pbits = bits_for(npatch);
+    const int64_t npe = m->npe;
+    const int64_t np_ = p1 - p0;
+    cl.reset();
+    cl.p0 = p0;
+    cl.p1 = p1;
+    std::vector<int64_t> h_pn(np_ + 1);
+    FEM_CUDA(cudaMemcpyAsync(h_pn.data(), P.patch_node_ptr.ptr + p0, (np_ + 1) * sizeof(int64_t),
+                             cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    const int64_t k0 = h_pn[0], nk = h_pn[np_] - h_pn[0];
+    const int pbits = bits_for(np_);
 
     // ---- closure elements of each patch: unique (patch, element) pairs
     DevBuf<uint64_t> ckeys;
     int64_t nce = 0;
     {
+        DevBuf<int64_t> deg, tmp;
+        FEM_TRY(deg.alloc(ar, nk + 1, "closure degrees"));
+        k_range_degree<<<grid_for(nk), TPB, 0, s>>>(P.own_row.ptr, m->inc_ptr.ptr, k0, nk, deg.ptr);
+        FEM_LAUNCHED("k_range_degree");
+        FEM_TRY(tmp.alloc(ar, scan_tmp_elems(nk + 1), "scan scratch"));
+        FEM_TRY(scan_exclusive_i64(deg.ptr, deg.ptr, nk, true, tmp.ptr, s));
+        int64_t npairs = 0;
+        FEM_TRY(read_scalar(deg.ptr + nk, &npairs, s));
         DevBuf<uint64_t> pairs;
-        FEM_TRY(pairs.alloc(ar, n_ent, "closure pairs"));
-        k_closure_pairs<<<grid_for(n_ent), TPB, 0, s>>>(m->E, n_ent, (int)npe, P.node_patch.ptr, pairs.ptr);
-        FEM_LAUNCHED("k_closure_pairs");
-        FEM_TRY(sort_unique(ar, pairs, n_ent, 32 + pbits, ckeys, &nce, s));
+        FEM_TRY(pairs.alloc(ar, npairs, "closure pairs"));
+        k_range_pairs<<<grid_for(nk), TPB, 0, s>>>(P.own_row.ptr, P.node_patch.ptr, m->inc_ptr.ptr, m->inc_elem.ptr,
+                                                   k0, nk, p0, deg.ptr, pairs.ptr);
+        FEM_LAUNCHED("k_range_pairs");
+        deg.free();
+        tmp.free();
+        FEM_TRY(sort_unique(ar, pairs, npairs, 32 + pbits, ckeys, &nce, s));
     }
-    P.total_celems = nce;
-    FEM_TRY(P.patch_elem_ptr.alloc(ar, npatch + 1, "patch elem ptr"));
-    k_segment_ptr<<<grid_for(npatch + 1), TPB, 0, s>>>(ckeys.ptr, nce, 32, npatch, P.patch_elem_ptr.ptr);
+    cl.total_celems = nce;
+    FEM_TRY(cl.patch_elem_ptr.alloc(ar, np_ + 1, "patch elem ptr"));
+    k_segment_ptr<<<grid_for(np_ + 1), TPB, 0, s>>>(ckeys.ptr, nce, 32, np_, cl.patch_elem_ptr.ptr);
     FEM_LAUNCHED("k_segment_ptr(elems)");
-
-    // host copies of the patch pointers for sizes
-    std::vector<int64_t> h_pn(npatch + 1), h_pe(npatch + 1), h_pc(npatch + 1);
-    FEM_CUDA(cudaMemcpyAsync(h_pn.data(), P.patch_node_ptr.ptr, (npatch + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    FEM_CUDA(cudaMemcpyAsync(h_pe.data(), P.patch_elem_ptr.ptr, (npatch + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    std::vector<int64_t> h_pe(np_ + 1), h_pc(np_ + 1);
+    FEM_CUDA(cudaMemcpyAsync(h_pe.data(), cl.patch_elem_ptr.ptr, (np_ + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     FEM_CUDA(cudaStreamSynchronize(s));
-    P.max_own = 0;
-    P.max_celems = 0;
-    for (int64_t p = 0; p < npatch; ++p) {
-        P.max_own = std::max(P.max_own, h_pn[p + 1] - h_pn[p]);
-        P.max_celems = std::max(P.max_celems, h_pe[p + 1] - h_pe[p]);
-    }
-    if (P.max_own > 32767) {
-        set_error("a patch owns %lld rows; at most 32767 are supported", (long long)P.max_own);
-        return FEM_ERR_UNSUPPORTED;
-    }
+    for (int64_t p = 0; p < np_; ++p) cl.max_celems = std::max(cl.max_celems, h_pe[p + 1] - h_pe[p]);
 
     // ---- colouring of each closure, then order each closure by (colour, element)
     {
@@ -671,15 +663,15 @@ fem_status build_pattern_and_plan(fem_mesh m, cudaStream_t s) {
         FEM_TRY(mxc.alloc(ar, 1, "max colour"));
         FEM_CUDA(cudaMemsetAsync(mxc.ptr, 0, sizeof(int), s));
         const size_t smem = (size_t)2 * P.max_own * sizeof(unsigned long long) + (size_t)COLOR_CHUNK * npe * sizeof(int16_t);
-        const unsigned grid = (unsigned)std::min<int64_t>(npatch, (int64_t)num_sms() * 8);
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np_, (int64_t)num_sms() * 8));
         if (npe == 8) {
             FEM_CUDA(cudaFuncSetAttribute(k_color<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_color<8><<<grid, 128, smem, s>>>(ckeys.ptr, P.patch_elem_ptr.ptr, P.patch_node_ptr.ptr, m->E,
-                                               P.node_patch.ptr, P.own_idx.ptr, npatch, color.ptr, mxc.ptr);
+            k_color<8><<<grid, 128, smem, s>>>(ckeys.ptr, cl.patch_elem_ptr.ptr, P.patch_node_ptr.ptr + p0, m->E,
+                                               P.node_patch.ptr, P.own_idx.ptr, np_, p0, color.ptr, mxc.ptr);
         } else {
             FEM_CUDA(cudaFuncSetAttribute(k_color<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_color<4><<<grid, 128, smem, s>>>(ckeys.ptr, P.patch_elem_ptr.ptr, P.patch_node_ptr.ptr, m->E,
-                                               P.node_patch.ptr, P.own_idx.ptr, npatch, color.ptr, mxc.ptr);
+            k_color<4><<<grid, 128, smem, s>>>(ckeys.ptr, cl.patch_elem_ptr.ptr, P.patch_node_ptr.ptr + p0, m->E,
+                                               P.node_patch.ptr, P.own_idx.ptr, np_, p0, color.ptr, mxc.ptr);
         }
         FEM_LAUNCHED("k_color");
         int h_mxc = 0;
@@ -688,12 +680,13 @@ fem_status build_pattern_and_plan(fem_mesh m, cudaStream_t s) {
             set_error("the closure colouring needs more than 128 colours");
             return FEM_ERR_UNSUPPORTED;
         }
-        P.n_colors = h_mxc + 1;
+        cl.n_colors = h_mxc + 1;
         DevBuf<uint64_t> ck2, alt;
         DevBuf<int64_t> hist;
         FEM_TRY(ck2.alloc(ar, nce, "closure keys"));
         k_color_keys<<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, color.ptr, nce, ck2.ptr);
         FEM_LAUNCHED("k_color_keys");
+        FEM_CUDA(cudaStreamSynchronize(s));
         color.free();
         ckeys.free();
         FEM_TRY(alt.alloc(ar, nce, "sort scratch"));
@@ -715,47 +708,186 @@ fem_status build_pattern_and_plan(fem_mesh m, cudaStream_t s) {
         FEM_LAUNCHED("k_cnode_pairs");
         FEM_TRY(sort_unique(ar, pairs, nce * npe, 32 + pbits, cnkeys, &ncn, s));
     }
-    P.total_cnodes = ncn;
-    FEM_TRY(P.patch_cnode_ptr.alloc(ar, npatch + 1, "patch cnode ptr"));
-    k_segment_ptr<<<grid_for(npatch + 1), TPB, 0, s>>>(cnkeys.ptr, ncn, 32, npatch, P.patch_cnode_ptr.ptr);
+    cl.total_cnodes = ncn;
+    FEM_TRY(cl.patch_cnode_ptr.alloc(ar, np_ + 1, "patch cnode ptr"));
+    k_segment_ptr<<<grid_for(np_ + 1), TPB, 0, s>>>(cnkeys.ptr, ncn, 32, np_, cl.patch_cnode_ptr.ptr);
     FEM_LAUNCHED("k_segment_ptr(cnodes)");
-    FEM_TRY(P.cnode_gid.alloc(ar, ncn, "cnode gid"));
-    FEM_TRY(P.cnode_own.alloc(ar, ncn, "cnode own"));
-    k_cnode_own<<<grid_for(ncn), TPB, 0, s>>>(cnkeys.ptr, ncn, P.node_patch.ptr, P.own_idx.ptr, P.cnode_gid.ptr,
-                                              P.cnode_own.ptr);
+    FEM_TRY(cl.cnode_gid.alloc(ar, ncn, "cnode gid"));
+    FEM_TRY(cl.cnode_own.alloc(ar, ncn, "cnode own"));
+    k_cnode_own<<<grid_for(ncn), TPB, 0, s>>>(cnkeys.ptr, ncn, p0, P.node_patch.ptr, P.own_idx.ptr, cl.cnode_gid.ptr,
+                                              cl.cnode_own.ptr);
     FEM_LAUNCHED("k_cnode_own");
 
     // ---- per closure element data
-    P.pos_stride = (int)((m->np + 3) / 4 * 4);
-    FEM_TRY(P.celem_id.alloc(ar, nce, "celem id"));
-    FEM_TRY(P.celem_color.alloc(ar, nce, "celem colour"));
-    FEM_TRY(P.celem_lnode.alloc(ar, nce * npe, "celem local nodes"));
-    FEM_TRY(P.celem_pos.alloc(ar, nce * P.pos_stride, "celem positions"));
-    FEM_CUDA(cudaMemsetAsync(P.celem_pos.ptr, 0, nce * P.pos_stride, s));
+    FEM_TRY(cl.celem_id.alloc(ar, nce, "celem id"));
+    FEM_TRY(cl.celem_color.alloc(ar, nce, "celem colour"));
+    FEM_TRY(cl.celem_lnode.alloc(ar, nce * npe, "celem local nodes"));
+    FEM_TRY(cl.celem_pos.alloc(ar, nce * P.pos_stride, "celem positions"));
+    FEM_CUDA(cudaMemsetAsync(cl.celem_pos.ptr, 0, nce * P.pos_stride, s));
     if (npe == 8)
-        k_celem_fill<8><<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, nce, m->E, cnkeys.ptr, P.patch_cnode_ptr.ptr,
-                                                      m->rowptr.ptr, m->col.ptr, P.pos_stride, P.celem_id.ptr,
-                                                      P.celem_color.ptr, P.celem_lnode.ptr, P.celem_pos.ptr);
+        k_celem_fill<8><<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, nce, m->E, cnkeys.ptr, cl.patch_cnode_ptr.ptr,
+                                                      m->rowptr.ptr, m->col.ptr, P.pos_stride, cl.celem_id.ptr,
+                                                      cl.celem_color.ptr, cl.celem_lnode.ptr, cl.celem_pos.ptr);
     else
-        k_celem_fill<4><<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, nce, m->E, cnkeys.ptr, P.patch_cnode_ptr.ptr,
-                                                      m->rowptr.ptr, m->col.ptr, P.pos_stride, P.celem_id.ptr,
-                                                      P.celem_color.ptr, P.celem_lnode.ptr, P.celem_pos.ptr);
+        k_celem_fill<4><<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, nce, m->E, cnkeys.ptr, cl.patch_cnode_ptr.ptr,
+                                                      m->rowptr.ptr, m->col.ptr, P.pos_stride, cl.celem_id.ptr,
+                                                      cl.celem_color.ptr, cl.celem_lnode.ptr, cl.celem_pos.ptr);
     FEM_LAUNCHED("k_celem_fill");
-
-    FEM_CUDA(cudaMemcpyAsync(h_pc.data(), P.patch_cnode_ptr.ptr, (npatch + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    std::vector<int32_t> h_acc(npatch);
-    FEM_CUDA(cudaMemcpyAsync(h_acc.data(), P.patch_acc.ptr, npatch * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaMemcpyAsync(h_pc.data(), cl.patch_cnode_ptr.ptr, (np_ + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     FEM_CUDA(cudaStreamSynchronize(s));
-    P.max_cnodes = 0;
-    P.max_acc = 0;
-    for (int64_t p = 0; p < npatch; ++p) {
-        P.max_cnodes = std::max(P.max_cnodes, h_pc[p + 1] - h_pc[p]);
-        P.max_acc = std::max(P.max_acc, (int64_t)h_acc[p]);
-    }
-    if (P.max_cnodes > 65535) {
-        set_error("a patch touches %lld nodes; at most 65535 are supported", (long long)P.max_cnodes);
+    for (int64_t p = 0; p < np_; ++p) cl.max_cnodes = std::max(cl.max_cnodes, h_pc[p + 1] - h_pc[p]);
+    if (cl.max_cnodes > 65535) {
+        set_error("a patch touches %lld nodes; at most 65535 are supported", (long long)cl.max_cnodes);
         return FEM_ERR_UNSUPPORTED;
     }
+    return FEM_OK;
+}
+
+// Patch groups under the memory budget (Eq. 10: the work is split into
+// GPU_g = ceil(required / available) groups run one after the other).  A group
+// of G patches is tried, halved while its closure does not fit, and every group
+// is built once here to record the sizes the kernels' shared memory needs; the
+// numeric calls rebuild each group's closure, run it and free it.
+static fem_status closure_range(fem_mesh m, int64_t p0, int64_t p1, cudaStream_t s,
+                                const std::function<fem_status(const Closure &)> &fn, int *groups) {
+    Closure cl;
+    fem_status st = build_closure(m, p0, p1, cl, s);
+    if (st == FEM_ERR_BUDGET && p1 - p0 > 1) {
+        cl.reset();
+        cudaGetLastError();
+        const int64_t mid = p0 + (p1 - p0) / 2;
+        FEM_TRY(closure_range(m, p0, mid, s, fn, groups));
+        return closure_range(m, mid, p1, s, fn, groups);
+    }
+    FEM_TRY(st);
+    ++*groups;
+    FEM_TRY(fn(cl));
+    FEM_CUDA(cudaStreamSynchronize(s));  // the closure's buffers are freed on return
+    return FEM_OK;
+}
+
+fem_status for_each_group(fem_mesh m, cudaStream_t s, const std::function<fem_status(const Closure &)> &fn) {
+    Plan &P = m->plan;
+    if (!P.chunked) return fn(P.full);
+    int groups = 0;
+    for (int64_t p0 = 0; p0 < P.n_patches; p0 += m->group_patches)
+        FEM_TRY(closure_range(m, p0, std::min(P.n_patches, p0 + m->group_patches), s, fn, &groups));
+    m->n_groups = groups;
+    return FEM_OK;
+}
+
+static fem_status plan_groups(fem_mesh m, cudaStream_t s) {
+    Plan &P = m->plan;
+    int64_t G = std::max<int64_t>(1, P.n_patches / 2);
+    for (;;) {
+        Closure cl;
+        fem_status st = build_closure(m, 0, std::min(G, P.n_patches), cl, s);
+        if (st == FEM_OK) break;
+        cl.reset();
+        cudaGetLastError();
+        if (st != FEM_ERR_BUDGET) return st;
+        if (G == 1) {
+            set_error("the memory budget cannot hold the closure of one patch; raise it or lower patch_entries");
+            return FEM_ERR_BUDGET;
+        }
+        G = std::max<int64_t>(1, G / 2);
+    }
+    m->group_patches = G;
+    P.total_cnodes = P.total_celems = P.max_cnodes = P.max_celems = 0;
+    P.n_colors = 0;
+    return for_each_group(m, s, [&](const Closure &cl) {
+        P.total_cnodes += cl.total_cnodes;
+        P.total_celems += cl.total_celems;
+        P.max_cnodes = std::max(P.max_cnodes, cl.max_cnodes);
+        P.max_celems = std::max(P.max_celems, cl.max_celems);
+        P.n_colors = std::max(P.n_colors, cl.n_colors);
+        return FEM_OK;
+    });
+}
+
+// Global part of the plan (patches of consecutive nodes in locality order, the
+// owned-row tables), then the closures of all patches at once if the memory
+// budget holds them, else closures are built per patch group by each numeric call.
+fem_status build_plan(fem_mesh m, cudaStream_t s) {
+    Arena &ar = m->arena;
+    const int64_t N = m->n_nodes;
+    Plan &P = m->plan;
+    batch_forget(m);  // cached batched launches were sized for the old plan
+    P.reset();
+    int64_t cap_entries = m->opt.patch_entries > 0 ? m->opt.patch_entries : 8192;
+    if (cap_entries < 2 * (int64_t)m->max_row_len) cap_entries = 2 * (int64_t)m->max_row_len;
+    const int64_t cap_eff = cap_entries - m->max_row_len;
+    DevBuf<int64_t> pre;
+    {
+        DevBuf<int64_t> len, tmp;
+        FEM_TRY(len.alloc(ar, N + 1, "row lengths"));
+        FEM_TRY(pre.alloc(ar, N + 1, "row length prefix"));
+        k_len_in_order<<<grid_for(N), TPB, 0, s>>>(m->order.ptr, m->rowptr.ptr, N, len.ptr);
+        FEM_LAUNCHED("k_len_in_order");
+        FEM_TRY(tmp.alloc(ar, scan_tmp_elems(N + 1), "scan scratch"));
+        FEM_TRY(scan_exclusive_i64(len.ptr, pre.ptr, N, true, tmp.ptr, s));
+        FEM_CUDA(cudaStreamSynchronize(s));
+    }
+    P.n_patches = m->nnz > 0 ? cdiv(m->nnz, cap_eff) : 1;
+    const int64_t npatch = P.n_patches;
+    if (npatch >= (1ll << 23)) {
+        set_error("too many patches (%lld)", (long long)npatch);
+        return FEM_ERR_UNSUPPORTED;
+    }
+    P.pos_stride = (int)((m->np + 3) / 4 * 4);
+    FEM_TRY(P.patch_node_ptr.alloc(ar, npatch + 1, "patch node ptr"));
+    k_patch_bounds<<<grid_for(npatch + 1), TPB, 0, s>>>(pre.ptr, N, cap_eff, npatch, P.patch_node_ptr.ptr);
+    FEM_LAUNCHED("k_patch_bounds");
+    FEM_TRY(P.node_patch.alloc(ar, N, "node patch"));
+    FEM_TRY(P.own_idx.alloc(ar, N, "own index"));
+    FEM_TRY(P.own_row.alloc(ar, N, "own row"));
+    FEM_TRY(P.own_rowptr.alloc(ar, N, "own rowptr"));
+    FEM_TRY(P.own_acc.alloc(ar, N, "own acc"));
+    FEM_TRY(P.own_hv.alloc(ar, N, "own hv"));
+    FEM_TRY(P.patch_acc.alloc(ar, npatch, "patch acc"));
+    const int hv_thr = m->opt.valence_threshold;
+    k_patch_nodes<<<grid_for(N), TPB, 0, s>>>(m->order.ptr, pre.ptr, P.patch_node_ptr.ptr, N, cap_eff, npatch,
+                                              m->rowptr.ptr, m->inc_ptr.ptr, hv_thr, P.node_patch.ptr, P.own_idx.ptr,
+                                              P.own_row.ptr, P.own_rowptr.ptr, P.own_acc.ptr, P.own_hv.ptr);
+    FEM_LAUNCHED("k_patch_nodes");
+    k_patch_acc<<<grid_for(npatch), TPB, 0, s>>>(pre.ptr, P.patch_node_ptr.ptr, npatch, P.patch_acc.ptr);
+    FEM_LAUNCHED("k_patch_acc");
+    std::vector<int64_t> h_pn(npatch + 1);
+    std::vector<int32_t> h_acc(npatch);
+    FEM_CUDA(cudaMemcpyAsync(h_pn.data(), P.patch_node_ptr.ptr, (npatch + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaMemcpyAsync(h_acc.data(), P.patch_acc.ptr, npatch * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    pre.free();
+    for (int64_t p = 0; p < npatch; ++p) {
+        P.max_own = std::max(P.max_own, h_pn[p + 1] - h_pn[p]);
+        P.max_acc = std::max(P.max_acc, (int64_t)h_acc[p]);
+    }
+    if (P.max_own > 32767) {
+        set_error("a patch owns %lld rows; at most 32767 are supported", (long long)P.max_own);
+        return FEM_ERR_UNSUPPORTED;
+    }
+
+    // closures of all patches, unless the budget refuses them
+    fem_status st = build_closure(m, 0, npatch, P.full, s);
+    if (st == FEM_ERR_BUDGET) {
+        P.full.reset();
+        cudaGetLastError();
+        P.chunked = true;
+        return plan_groups(m, s);
+    }
+    FEM_TRY(st);
+    P.total_cnodes = P.full.total_cnodes;
+    P.total_celems = P.full.total_celems;
+    P.max_cnodes = P.full.max_cnodes;
+    P.max_celems = P.full.max_celems;
+    P.n_colors = P.full.n_colors;
+    m->n_groups = 1;
+    return FEM_OK;
+}
+
+fem_status build_pattern_and_plan(fem_mesh m, cudaStream_t s) {
+    FEM_TRY(build_pattern(m, s));
+    FEM_TRY(build_plan(m, s));
     m->has_pattern = true;
     return FEM_OK;
 }

@@ -293,8 +293,8 @@ __global__ void __launch_bounds__(256) k_vjp(PlanView pv, const int64_t *__restr
 static size_t a16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 template <int NPE, typename T, typename S, typename CT>
-static fem_status launch_vjp_t(fem_mesh m, const void *X, const void *c, const void *G, void *dX, void *dc,
-                               cudaStream_t s) {
+static fem_status launch_vjp_t(fem_mesh m, const Closure &cl, const void *X, const void *c, const void *G, void *dX,
+                               void *dc, cudaStream_t s) {
     const Plan &P = m->plan;
     VjpSmem L{};
     size_t o = 0;
@@ -315,16 +315,18 @@ static fem_status launch_vjp_t(fem_mesh m, const void *X, const void *c, const v
         set_error("backward kernel cannot be resident with %zu bytes of shared memory", L.total);
         return FEM_ERR_UNSUPPORTED;
     }
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(P.n_patches, (int64_t)num_sms() * per_sm));
-    f<<<grid, 256, L.total, s>>>(P.view(), m->rowptr.ptr, (const S *)X, (const CT *)c, (const T *)G, (T *)dX,
+    const int64_t np = cl.p1 - cl.p0;
+    if (np <= 0) return FEM_OK;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np, (int64_t)num_sms() * per_sm));
+    f<<<grid, 256, L.total, s>>>(P.view(cl), m->rowptr.ptr, (const S *)X, (const CT *)c, (const T *)G, (T *)dX,
                                  (T *)dc, L);
     FEM_LAUNCHED("k_vjp");
     return FEM_OK;
 }
 
-fem_status launch_vjp(fem_mesh m, bool mixed, const void *X, fem_dtype xd, const void *c, fem_dtype cd,
-                      const void *G, void *dX, void *dc, cudaStream_t s) {
-#define FEM_V(NPE, T, S, CT) return launch_vjp_t<NPE, T, S, CT>(m, X, c, G, dX, dc, s)
+static fem_status launch_vjp_group(fem_mesh m, const Closure &cl, bool mixed, const void *X, fem_dtype xd,
+                                   const void *c, fem_dtype cd, const void *G, void *dX, void *dc, cudaStream_t s) {
+#define FEM_V(NPE, T, S, CT) return launch_vjp_t<NPE, T, S, CT>(m, cl, X, c, G, dX, dc, s)
     if (!mixed) {
         if (m->npe == 8) FEM_V(8, double, double, double);
         FEM_V(4, double, double, double);
@@ -340,6 +342,13 @@ fem_status launch_vjp(fem_mesh m, bool mixed, const void *X, fem_dtype xd, const
     if (xd == FEM_F64 && cd == FEM_F32) FEM_V(4, float, double, float);
     FEM_V(4, float, double, double);
 #undef FEM_V
+}
+
+fem_status launch_vjp(fem_mesh m, bool mixed, const void *X, fem_dtype xd, const void *c, fem_dtype cd,
+                      const void *G, void *dX, void *dc, cudaStream_t s) {
+    return for_each_group(m, s, [&](const Closure &cl) {
+        return launch_vjp_group(m, cl, mixed, X, xd, c, cd, G, dX, dc, s);
+    });
 }
 
 }  // namespace fem

@@ -160,6 +160,16 @@ class Mesh:
                                      _dev(G, "G", vd), _dev(dX, "dX"), _dev(dc, "dc"), _stream(stream)))
         return dX, dc
 
+    def autotune(self, X, c, prec="mixed", stream=None) -> dict:
+        """Pick the patch size and block size by timing fem_build_K (overwrites a scratch vals)."""
+        if self.nnz is None:
+            self.pattern(stream)
+        vals = torch.empty(max(self.nnz, 1), dtype=value_dtype(prec), device=X.device)
+        t = abi.fem_tuning()
+        abi.check(abi.load().fem_autotune(self._h, _prec(prec), _dev(X, "X"), _DT[X.dtype], _dev(c, "c"),
+                                          _DT[c.dtype], _dev(vals, "vals"), _stream(stream), ctypes.byref(t)))
+        return dict(patch_entries=t.patch_entries, block_threads=t.block_threads, ms=t.ms, tried=t.tried)
+
     def sync(self, stream=None):
         abi.check(abi.load().fem_sync(self._h, _stream(stream)))
 
@@ -167,6 +177,15 @@ class Mesh:
         i = abi.fem_info()
         abi.check(abi.load().fem_mesh_info(self._h, ctypes.byref(i)))
         return {f: getattr(i, f) for f, _ in abi.fem_info._fields_ if f != "reserved"}
+
+
+def batched_config(meshes, prec="mixed") -> dict:
+    """Launch shape the batched build of these meshes was tuned to."""
+    n = len(meshes)
+    H = (ctypes.c_void_p * n)(*[m.handle.value for m in meshes])
+    t, b, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    abi.check(abi.load().fem_batched_config(H, n, _prec(prec), ctypes.byref(t), ctypes.byref(b), ctypes.byref(g)))
+    return dict(block_threads=t.value, blocks_per_sm=b.value, grid=g.value)
 
 
 def build_K_batched(meshes, X, c, prec="mixed", out=None, stream=None):
