@@ -129,15 +129,12 @@ __host__ __device__ constexpr int tri_row(int q) {
 }
 
 template <int NPE, typename AccT, bool MIXED>
-__device__ __forceinline__ void scatter_element(const uint8_t *__restrict__ posp, const uint16_t (&ln)[NPE],
+__device__ __forceinline__ void scatter_element(const uint32_t (&pw)[(NPE * (NPE + 1) / 2 + 3) / 4],
+                                                const uint16_t (&ln)[NPE],
                                                 const int32_t *cown, const int32_t *roff, const uint8_t *hvf,
                                                 void *hv, bool fp64_sums, AccT *acc,
                                                 const AccT (&kv)[NPE * (NPE + 1) / 2]) {
     constexpr int NP = NPE * (NPE + 1) / 2;
-    constexpr int NW = (NP + 3) / 4;
-    uint32_t pw[NW];
-#pragma unroll
-    for (int w = 0; w < NW; ++w) pw[w] = __ldg(reinterpret_cast<const uint32_t *>(posp) + w);
     int own[NPE], rbase[NPE];
 #pragma unroll
     for (int a = 0; a < NPE; ++a) own[a] = cown[ln[a]];
@@ -264,6 +261,7 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
             const int64_t ci = eb + i;
             AccT kv[NP];
             uint16_t ln[NPE];
+            uint32_t pw[(NP + 3) / 4];
             int mycol = -1;
             CT ce = CT(0);
             if constexpr (FUSED) {
@@ -289,13 +287,17 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
 #pragma unroll
                     for (int q = 0; q < NP; ++q) kv[q] = __ldg(ke + e * NP + q);
                 }
+                // in-row positions before the colour phases, so that no phase waits
+                // on its own global load (one exposed latency per batch)
+                const uint32_t *pp = reinterpret_cast<const uint32_t *>(pv.celem_pos + ci * ((NP + 3) / 4 * 4));
+#pragma unroll
+                for (int w = 0; w < (NP + 3) / 4; ++w) pw[w] = __ldg(pp + w);
             }
             const int last = min(base + nthr, nel) - 1;
             const int c0 = pv.celem_color[eb + base], c1 = pv.celem_color[eb + last];
             for (int cc = c0; cc <= c1; ++cc) {
                 if (mycol == cc)
-                    scatter_element<NPE, AccT, MIXED>(pv.celem_pos + ci * ((NP + 3) / 4 * 4), ln, cown, roff, hvf, hv,
-                                                      fp64_sums, acc, kv);
+                    scatter_element<NPE, AccT, MIXED>(pw, ln, cown, roff, hvf, hv, fp64_sums, acc, kv);
                 __syncthreads();
             }
         }

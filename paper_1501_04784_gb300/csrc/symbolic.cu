@@ -400,6 +400,33 @@ __global__ void k_color(const uint64_t *ckeys, const int64_t *pe_ptr, const int6
     }
 }
 
+// Colouring order: closure elements grouped by patch, then by the smallest
+// patch-local index of their owned nodes (owned nodes follow the Morton order),
+// so the greedy colouring sweeps each patch in space; key = (patch << 15) | that
+// index, payload = the entry's position.
+template <int NPE>
+__global__ void k_sweep_keys(const uint64_t *ckeys, int64_t nce, const int32_t *__restrict__ E,
+                             const int32_t *node_patch, const int32_t *own_idx, int64_t p0, uint64_t *keys,
+                             uint32_t *vals) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nce; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = ckeys[i];
+        const int64_t pl = (int64_t)(k >> 32), e = (int64_t)(k & 0xffffffffull);
+        int mo = 32767;
+#pragma unroll
+        for (int a = 0; a < NPE; ++a) {
+            const int32_t g = E[e * NPE + a];
+            if (node_patch[g] == (int32_t)(p0 + pl)) mo = min(mo, own_idx[g]);
+        }
+        keys[i] = ((uint64_t)pl << 15) | (uint64_t)mo;
+        vals[i] = (uint32_t)i;
+    }
+}
+
+__global__ void k_gather_u64(const uint64_t *in, const uint32_t *perm, int64_t n, uint64_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[perm[i]];
+}
+
 __global__ void k_color_keys(const uint64_t *ckeys, const uint8_t *color, int64_t n, uint64_t *out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t k = ckeys[i];
@@ -655,7 +682,32 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
     FEM_CUDA(cudaStreamSynchronize(s));
     for (int64_t p = 0; p < np_; ++p) cl.max_celems = std::max(cl.max_celems, h_pe[p + 1] - h_pe[p]);
 
-    // ---- colouring of each closure, then order each closure by (colour, element)
+    // ---- colouring of each closure (in sweep order), then order each closure by (colour, element)
+    {
+        DevBuf<uint64_t> skeys, salt, swept;
+        DevBuf<uint32_t> sperm, spalt;
+        DevBuf<int64_t> shist;
+        FEM_TRY(skeys.alloc(ar, nce, "sweep keys"));
+        FEM_TRY(sperm.alloc(ar, nce, "sweep order"));
+        if (npe == 8)
+            k_sweep_keys<8><<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, nce, m->E, P.node_patch.ptr, P.own_idx.ptr, p0,
+                                                          skeys.ptr, sperm.ptr);
+        else
+            k_sweep_keys<4><<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, nce, m->E, P.node_patch.ptr, P.own_idx.ptr, p0,
+                                                          skeys.ptr, sperm.ptr);
+        FEM_LAUNCHED("k_sweep_keys");
+        FEM_TRY(salt.alloc(ar, nce, "sort scratch"));
+        FEM_TRY(spalt.alloc(ar, nce, "sort scratch"));
+        FEM_TRY(shist.alloc(ar, radix_hist_elems(nce), "sort histogram"));
+        FEM_TRY(radix_sort_u64(skeys.ptr, sperm.ptr, nce, 15 + pbits, salt.ptr, spalt.ptr, shist.ptr, s));
+        FEM_TRY(swept.alloc(ar, nce, "closure keys (sweep order)"));
+        k_gather_u64<<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, sperm.ptr, nce, swept.ptr);
+        FEM_LAUNCHED("k_gather_u64");
+        FEM_CUDA(cudaStreamSynchronize(s));
+        std::swap(ckeys.ptr, swept.ptr);
+        std::swap(ckeys.n, swept.n);
+        std::swap(ckeys.arena, swept.arena);
+    }
     {
         DevBuf<uint8_t> color;
         DevBuf<int> mxc;
