@@ -83,6 +83,9 @@ typedef struct {
     int fp64_sums;               /* mixed mode, high-valence entries: 0 (default) = error-free
                                     FP32 pair summation (TwoSum, accurate to ~2^-48 like an
                                     FP64 sum, rounded once); 1 = FP64 adds */
+    int fp64_fused;              /* FEM_FP64 builds: 0 (default) = integrate each element once
+                                    into library memory, then assemble; 1 = recompute element
+                                    matrices inside the assembly (no staging memory) */
     int reserved[8];
 } fem_options;
 
@@ -157,10 +160,12 @@ fem_status fem_integrate_local(fem_mesh m, fem_prec p, const void *X, fem_dtype 
 fem_status fem_assemble_csr(fem_mesh m, fem_prec p, const void *ke, void *vals, void *stream);
 
 /*
- * Integration and assembly fused: vals [nnz] of K for coordinates X and
- * coefficients c, with the pattern cached.  No element matrix goes through
- * device memory in FEM_MIXED; in FEM_FP64 the library may stage element
- * matrices in its own memory when that is faster (within the budget).
+ * Integration and assembly: vals [nnz] of K for coordinates X and
+ * coefficients c, with the pattern cached.  FEM_MIXED fuses both (no element
+ * matrix goes through device memory).  FEM_FP64 integrates each element once
+ * into library memory (n_elems * 36|10 doubles, within the budget) and then
+ * assembles, unless fem_options.fp64_fused is set or the budget refuses the
+ * buffer, in which case it fuses too.
  * FEM_ERR_STATE before fem_pattern.
  */
 fem_status fem_build_K(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c,

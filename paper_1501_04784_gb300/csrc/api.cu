@@ -281,13 +281,34 @@ fem_status fem_build_K(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype,
         set_error("vals must be a non-null aligned device pointer");
         return FEM_ERR_ARG;
     }
+    cudaStream_t s = as_stream(stream);
+    if (p == FEM_FP64 && !m->plan.chunked && m->opt.fp64_fused == 0) {
+        // integrate once into library memory, then assemble (falls back to the
+        // fused kernel if the budget refuses the buffer)
+        const size_t n = (size_t)m->n_elems * m->np;
+        fem_status st = m->ke64.n >= n ? FEM_OK : m->ke64.alloc(m->arena, n, "FP64 element matrices");
+        if (st == FEM_OK) {
+            IntegrateArgs ia{m->npe, false, x_dtype, c_dtype, m->E, m->n_elems, X, c, m->ke64.ptr,
+                             default_threshold(m), nullptr};
+            FEM_TRY(launch_integrate(ia, s));
+            PatchArgs a = patch_args(m, p, false);
+            a.xd = FEM_F64;
+            a.cd = FEM_F64;
+            a.ke = m->ke64.ptr;
+            a.vals = vals;
+            return for_each_group(m, s, [&](const Closure &cl) {
+                a.closure = &cl;
+                return launch_patch(a, s);
+            });
+        }
+        if (st != FEM_ERR_BUDGET) return st;
+    }
     PatchArgs a = patch_args(m, p, true);
     a.xd = x_dtype;
     a.cd = c_dtype;
     a.X = X;
     a.c = c;
     a.vals = vals;
-    cudaStream_t s = as_stream(stream);
     return for_each_group(m, s, [&](const Closure &cl) {
         a.closure = &cl;
         return launch_patch(a, s);

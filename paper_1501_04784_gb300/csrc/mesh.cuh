@@ -110,6 +110,10 @@ struct fem_mesh_s {
     fem::Plan plan;
     // staging for the _host entry point
     fem::DevBuf<unsigned char> host_stage;
+    // FP64 element matrices staged between integration and assembly (the FP64
+    // pipe is the bound there, so integrating each element once beats recomputing
+    // it in every closure that contains it)
+    fem::DevBuf<double> ke64;
     int n_groups = 1;
     int64_t group_patches = 0;  // patches per group when the closures are built per group
 };

@@ -255,6 +255,14 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
             c_n1 = e0 >= 0 ? __ldg(c + e0) : CT(0);
             eid_n2 = tid + nthr < nel ? pv.celem_id[eb + tid + nthr] : -1;
         }
+        // tets (short integration): closure-local node indices and colours of the
+        // next batch are loaded one batch ahead as well; bricks load them in place
+        uint16_t ln_n[NPE];
+        int col_n = -1;
+        if (NPE == 4 && tid < nel) {
+            load_lnodes<NPE>(pv.celem_lnode, eb + tid, ln_n);
+            col_n = pv.celem_color[eb + tid];
+        }
         for (int base = 0; base < nel; base += nthr) {
             const int i = base + tid;
             const bool act = i < nel;
@@ -263,6 +271,18 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
             uint16_t ln[NPE];
             uint32_t pw[(NP + 3) / 4];
             int mycol = -1;
+            if constexpr (NPE == 4) {
+#pragma unroll
+                for (int a = 0; a < NPE; ++a) ln[a] = ln_n[a];
+                if (act) mycol = col_n;
+                if (i + nthr < nel) {
+                    load_lnodes<NPE>(pv.celem_lnode, ci + nthr, ln_n);
+                    col_n = pv.celem_color[ci + nthr];
+                }
+            } else if (act) {
+                load_lnodes<NPE>(pv.celem_lnode, ci, ln);
+                mycol = pv.celem_color[ci];
+            }
             CT ce = CT(0);
             if constexpr (FUSED) {
                 ce = c_n1;
@@ -271,8 +291,6 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
                 eid_n2 = i2 < nel ? pv.celem_id[eb + i2] : -1;
             }
             if (act) {
-                load_lnodes<NPE>(pv.celem_lnode, ci, ln);
-                mycol = pv.celem_color[ci];
                 if constexpr (FUSED) {
                     S xc[NPE][3];
 #pragma unroll

@@ -75,11 +75,12 @@ def test_budget_groups_bitwise_equal(fem, prec):
     m = meshgen.hex_grid(24, jitter=0.2, seed=77, permute_nodes=True, permute_elems=True)
     dt = torch.float32 if prec == "mixed" else torch.float64
     X, c = dev(m.X, dt), dev(m.c, dt)
-    free = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), patch_entries=1024)
+    # FP64 builds fuse here on both sides, so the two differ only in the grouping
+    free = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), patch_entries=1024, fp64_fused=1)
     ref = free.build_K(X, c, prec)
     need = free.info()["plan_bytes"]
     tight = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), patch_entries=1024,
-                     mem_budget_bytes=int(need * 0.75))
+                     mem_budget_bytes=int(need * 0.75), fp64_fused=1)
     got = tight.build_K(X, c, prec)
     info = tight.info()
     assert info["n_groups"] > 1
@@ -89,6 +90,19 @@ def test_budget_groups_bitwise_equal(fem, prec):
     a = free.vjp(X, c, G, prec)
     b = tight.vjp(X, c, G, prec)
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+def test_fp64_staged_and_fused_agree(fem):
+    """FEM_FP64 integrates once into staged element matrices by default; the fused
+    form recomputes them per closure.  Both match the oracle to FP64 tolerance."""
+    m = meshgen.config_mesh(0)
+    X, c = dev(m.X, torch.float64), dev(m.c, torch.float64)
+    staged = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=X).build_K(X, c, "fp64").cpu().numpy()
+    fused = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=X, fp64_fused=1).build_K(X, c, "fp64").cpu().numpy()
+    ref = oracle_K(m)
+    assert rel_err(staged, ref["vals"], ref["cs"]) <= TOL_FP64
+    assert rel_err(fused, ref["vals"], ref["cs"]) <= TOL_FP64
+    assert np.abs(staged - fused).max() <= 1e-14 * np.abs(ref["cs"]).max()
 
 
 def test_budget_too_small_for_one_patch(fem):
