@@ -38,6 +38,12 @@ def parse():
     ap.add_argument("--n", type=int, default=100, help="grid cells per axis (100 = the 1M-brick workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--once", choices=["mixed", "fp64"], default=None,
+                    help="profiling mode: build K twice in this precision and exit (no timing, no JSON)")
+    ap.add_argument("--workload", choices=["hex", "tet"], default="hex",
+                    help="--once only: the 1M-brick workload or the 3.07M-tet workload")
+    ap.add_argument("--patch-entries", type=int, default=0, help="--once only: plan patch size (0 = default)")
+    ap.add_argument("--block-threads", type=int, default=0, help="--once only: threads per block (0 = default)")
     return ap.parse_args()
 
 
@@ -365,9 +371,31 @@ def run_reference(args):
     }))
 
 
+def run_once(args):
+    """Two builds of one workload, for a profiler to capture the second one."""
+    import torch
+
+    import meshgen
+    from paper_1501_04784_gb300 import _build, fem
+    _build.build()
+    m = meshgen.config_mesh(1 if args.workload == "hex" else 2)
+    E = torch.from_numpy(m.E).cuda()
+    X64, c64 = torch.from_numpy(m.X).cuda(), torch.from_numpy(m.c).cuda()
+    mesh = fem.Mesh(E, m.n_nodes, X=X64, patch_entries=args.patch_entries, block_threads=args.block_threads)
+    nnz = mesh.pattern()
+    X, c = (X64.float(), c64.float()) if args.once == "mixed" else (X64, c64)
+    v = torch.empty(nnz, dtype=X.dtype, device="cuda")
+    for _ in range(2):
+        mesh.build_K(X, c, args.once, out=v)
+    torch.cuda.synchronize()
+    print(f"built {args.workload} {args.once}: nnz {nnz}, patches {mesh.info()['n_patches']}")
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.once:
+        run_once(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

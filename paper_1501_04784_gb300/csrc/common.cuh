@@ -10,7 +10,7 @@
 #include <cstdio>
 #include <string>
 
-#include "../../include/fem.h"
+#include "fem.h"  // include/ is on the include path
 
 namespace fem {
 
