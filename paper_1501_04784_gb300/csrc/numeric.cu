@@ -217,31 +217,76 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
         const int nel = (int)(pv.patch_elem_ptr[p + 1] - eb);
         const int nacc = pv.patch_acc[p];
 
-        // Prologue, stage 1: every contiguous per-patch array, independent loads.
-        for (int j = tid; j < ncn; j += nthr) {
-            cown[j] = pv.cnode_own[cb + j];
-            if constexpr (FUSED) gid[j] = pv.cnode_gid[cb + j];
+        // Prologue, stage 1: the patch's contiguous plan arrays.  Loads go out in
+        // chunks of CH per thread before their shared-memory stores, so each
+        // thread has CH global loads in flight instead of one per round trip.
+        constexpr int CH = 8;
+        for (int j0 = 0; j0 < ncn; j0 += CH * nthr) {
+            int32_t vo[CH], vg[CH];
+#pragma unroll
+            for (int k = 0; k < CH; ++k) {
+                const int j = j0 + k * nthr + tid;
+                vo[k] = j < ncn ? pv.cnode_own[cb + j] : 0;
+                vg[k] = (FUSED && j < ncn) ? pv.cnode_gid[cb + j] : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < CH; ++k) {
+                const int j = j0 + k * nthr + tid;
+                if (j < ncn) {
+                    cown[j] = vo[k];
+                    if constexpr (FUSED) gid[j] = vg[k];
+                }
+            }
         }
-        for (int k = tid; k < nown; k += nthr) {
-            roff[k] = pv.own_acc[nb + k];
-            rps[k] = pv.own_rowptr[nb + k];
-            if constexpr (MIXED) {
-                hv[k] = 0.0;  // also clears the (hi, lo) float pair
-                hvf[k] = pv.own_hv[nb + k];
+        for (int k0 = 0; k0 < nown; k0 += CH * nthr) {
+            int32_t vr[CH];
+            int64_t vp[CH];
+            uint8_t vh[CH];
+#pragma unroll
+            for (int k = 0; k < CH; ++k) {
+                const int kk = k0 + k * nthr + tid;
+                vr[k] = kk < nown ? pv.own_acc[nb + kk] : 0;
+                vp[k] = kk < nown ? pv.own_rowptr[nb + kk] : 0;
+                vh[k] = (MIXED && kk < nown) ? pv.own_hv[nb + kk] : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < CH; ++k) {
+                const int kk = k0 + k * nthr + tid;
+                if (kk < nown) {
+                    roff[kk] = vr[k];
+                    rps[kk] = vp[k];
+                    if constexpr (MIXED) {
+                        hv[kk] = 0.0;  // also clears the (hi, lo) float pair
+                        hvf[kk] = vh[k];
+                    }
+                }
             }
         }
         if (tid == 0) roff[nown] = nacc;
         for (int i = tid; i < nacc; i += nthr) acc[i] = AccT(0);
         __syncthreads();
-        // Prologue, stage 2: gathers through the staged indices (node coordinates,
-        // coefficients), unrolled so that several loads are in flight per thread.
+        // Prologue, stage 2: node coordinates of the closure, gathered through the
+        // staged ids, CH nodes (3 CH loads) in flight per thread.
         if constexpr (FUSED) {
-#pragma unroll 4
-            for (int j = tid; j < ncn; j += nthr) {
-                const int64_t g = gid[j];
-                xs[j][0] = __ldg(X + 3 * g + 0);
-                xs[j][1] = __ldg(X + 3 * g + 1);
-                xs[j][2] = __ldg(X + 3 * g + 2);
+            for (int j0 = 0; j0 < ncn; j0 += CH * nthr) {
+                S v[CH][3];
+#pragma unroll
+                for (int k = 0; k < CH; ++k) {
+                    const int j = j0 + k * nthr + tid;
+                    const int64_t g = j < ncn ? gid[j] : 0;
+                    v[k][0] = j < ncn ? __ldg(X + 3 * g + 0) : S(0);
+                    v[k][1] = j < ncn ? __ldg(X + 3 * g + 1) : S(0);
+                    v[k][2] = j < ncn ? __ldg(X + 3 * g + 2) : S(0);
+                }
+#pragma unroll
+                for (int k = 0; k < CH; ++k) {
+                    const int j = j0 + k * nthr + tid;
+                    if (j < ncn) {
+                        xs[j][0] = v[k][0];
+                        xs[j][1] = v[k][1];
+                        xs[j][2] = v[k][2];
+                    }
+                }
             }
         }
         __syncthreads();
@@ -320,21 +365,34 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
             }
         }
 
-        // each owned row to HBM once (one warp per row)
-        for (int k = warp; k < nown; k += nwarps) {
-            const int64_t rp = rps[k];
-            const int o0 = roff[k], len = roff[k + 1] - o0;
-            const bool h = MIXED && hvf[k];
-            for (int j = lane; j < len; j += 32) {
-                AccT v = acc[o0 + j];
-                if (h && j == len - 1) {
-                    if (fp64_sums) v = (AccT)hv[k];
-                    else {
-                        const float2 pr = reinterpret_cast<const float2 *>(hv)[k];
-                        v = (AccT)(pr.x + pr.y);  // the pair rounded once
+        // each owned row to HBM once: a warp takes RW rows per iteration, their
+        // bounds read together, so RW rows' shared-memory reads are in flight
+        constexpr int RW = 4;
+        for (int k0 = warp; k0 < nown; k0 += nwarps * RW) {
+            int o0[RW], len[RW];
+            int64_t rp[RW];
+#pragma unroll
+            for (int r = 0; r < RW; ++r) {
+                const int k = k0 + r * nwarps;
+                o0[r] = k < nown ? roff[k] : 0;
+                len[r] = k < nown ? roff[k + 1] - o0[r] : 0;
+                rp[r] = k < nown ? rps[k] : 0;
+            }
+#pragma unroll
+            for (int r = 0; r < RW; ++r) {
+                const int k = k0 + r * nwarps;
+                const bool h = MIXED && k < nown && hvf[k];
+                for (int j = lane; j < len[r]; j += 32) {
+                    AccT v = acc[o0[r] + j];
+                    if (h && j == len[r] - 1) {
+                        if (fp64_sums) v = (AccT)hv[k];
+                        else {
+                            const float2 pr = reinterpret_cast<const float2 *>(hv)[k];
+                            v = (AccT)(pr.x + pr.y);  // the pair rounded once
+                        }
                     }
+                    vals[rp[r] + j] = v;
                 }
-                vals[rp + j] = v;
             }
         }
         __syncthreads();
