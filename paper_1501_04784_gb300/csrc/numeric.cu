@@ -365,35 +365,28 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
             }
         }
 
-        // each owned row to HBM once: a warp takes RW rows per iteration, their
-        // bounds read together, so RW rows' shared-memory reads are in flight
-        constexpr int RW = 4;
-        for (int k0 = warp; k0 < nown; k0 += nwarps * RW) {
-            int o0[RW], len[RW];
-            int64_t rp[RW];
-#pragma unroll
-            for (int r = 0; r < RW; ++r) {
-                const int k = k0 + r * nwarps;
-                o0[r] = k < nown ? roff[k] : 0;
-                len[r] = k < nown ? roff[k + 1] - o0[r] : 0;
-                rp[r] = k < nown ? rps[k] : 0;
-            }
-#pragma unroll
-            for (int r = 0; r < RW; ++r) {
-                const int k = k0 + r * nwarps;
-                const bool h = MIXED && k < nown && hvf[k];
-                for (int j = lane; j < len[r]; j += 32) {
-                    AccT v = acc[o0[r] + j];
-                    if (h && j == len[r] - 1) {
-                        if (fp64_sums) v = (AccT)hv[k];
-                        else {
-                            const float2 pr = reinterpret_cast<const float2 *>(hv)[k];
-                            v = (AccT)(pr.x + pr.y);  // the pair rounded once
-                        }
-                    }
-                    vals[rp[r] + j] = v;
+        // each owned row to HBM once: a group of 2^wg_shift lanes (about one row
+        // length) stores one row, so a warp writes 32 >> wg_shift rows per step,
+        // each as one contiguous segment
+        const int gsh = L.wg_shift, gsz = 1 << gsh;
+        const int rows_step = nwarps << (5 - gsh);
+        for (int k = (warp << (5 - gsh)) + (lane >> gsh); k < nown; k += rows_step) {
+            const int o0 = roff[k], len = roff[k + 1] - o0;
+            AccT *dst = vals + rps[k];
+            const AccT *src = acc + o0;
+            // the diagonal (last entry of a lower row) of a high-valence row comes
+            // from its FP64-accurate sum instead
+            int jd = -1;
+            AccT vd = AccT(0);
+            if (MIXED && hvf[k]) {
+                jd = len - 1;
+                if (fp64_sums) vd = (AccT)hv[k];
+                else {
+                    const float2 pr = reinterpret_cast<const float2 *>(hv)[k];
+                    vd = (AccT)(pr.x + pr.y);  // the pair rounded once
                 }
             }
+            for (int j = lane & (gsz - 1); j < len; j += gsz) dst[j] = j == jd ? vd : src[j];
         }
         __syncthreads();
     }
@@ -496,6 +489,11 @@ PatchSmem patch_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsi
     if (fused) o = align16(o + (size_t)P.max_cnodes * sizeof(int32_t));
     L.eid = L.cvs = o;
     (void)csize;
+    // lanes per row in the write-out: the power of two at or above the mean
+    // owned-row length of the largest patch, between 4 and 32
+    const int64_t mean_row = P.max_own > 0 ? (P.max_acc + P.max_own - 1) / P.max_own : 1;
+    L.wg_shift = 2;
+    while (L.wg_shift < 5 && (int64_t(1) << L.wg_shift) < mean_row) ++L.wg_shift;
     L.total = o;
     return L;
 }

@@ -12,6 +12,7 @@ static constexpr int PATCH_MAX_THREADS = 512;
 // byte offsets of the patch kernel's shared-memory arrays
 struct PatchSmem {
     size_t acc, hv, xs, cown, roff, hvf, rps, gid, eid, cvs, total;
+    int wg_shift;  // log2 of the lanes that store one owned row
 };
 
 struct IntegrateArgs {
