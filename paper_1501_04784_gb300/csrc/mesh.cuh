@@ -33,7 +33,17 @@ struct PlanView {
     const uint8_t *celem_pos;        // [total celems * pos_stride] position of the entry in its row
     const int32_t *own_row;          // [n_nodes] global id of each owned row, in patch order
     int64_t n_patches;
+    // [NP/2 words][total celems] (word-major, so a warp's loads of one word are
+    // contiguous): two 16-bit targets per word, entry q in the low half when q is
+    // even.  A target is the entry's offset in the patch's accumulators, 0xFFFF
+    // when its row is not owned by the patch, or 0x8000 | k for the diagonal of
+    // owned row k when that row's diagonal is summed FP64-accurately.
+    const uint32_t *celem_aidx;
+    int64_t aidx_n;                  // total celems (the word stride)
 };
+
+// Packed targets of celem_aidx.
+static constexpr uint32_t AIDX_NONE = 0xFFFFu, AIDX_HV = 0x8000u;
 
 // Closure data of a range of patches [p0, p1): the elements each patch
 // integrates and the nodes they touch.  Patch indices inside are relative to p0.
@@ -45,15 +55,16 @@ struct Closure {
     DevBuf<int32_t> cnode_gid, cnode_own, celem_id;
     DevBuf<uint8_t> celem_color, celem_pos;
     DevBuf<uint16_t> celem_lnode;
+    DevBuf<uint32_t> celem_aidx;
     void reset() {
         patch_elem_ptr.free(); patch_cnode_ptr.free(); cnode_gid.free(); cnode_own.free(); celem_id.free();
-        celem_color.free(); celem_pos.free(); celem_lnode.free();
+        celem_color.free(); celem_pos.free(); celem_lnode.free(); celem_aidx.free();
         p0 = p1 = total_cnodes = total_celems = max_cnodes = max_celems = 0;
         n_colors = 0;
     }
     size_t bytes() const {
         return patch_elem_ptr.bytes() + patch_cnode_ptr.bytes() + cnode_gid.bytes() + cnode_own.bytes() +
-               celem_id.bytes() + celem_color.bytes() + celem_pos.bytes() + celem_lnode.bytes();
+               celem_id.bytes() + celem_color.bytes() + celem_pos.bytes() + celem_lnode.bytes() + celem_aidx.bytes();
     }
 };
 
@@ -70,11 +81,25 @@ struct Plan {
     int64_t total_cnodes = 0, total_celems = 0, max_cnodes = 0, max_celems = 0;
     int n_colors = 0;
     PlanView view(const Closure &cl) const {
-        return PlanView{patch_node_ptr.ptr + cl.p0, cl.patch_elem_ptr.ptr, cl.patch_cnode_ptr.ptr,
-                        patch_acc.ptr + cl.p0,    own_acc.ptr,           own_rowptr.ptr,
-                        own_hv.ptr,               cl.cnode_gid.ptr,      cl.cnode_own.ptr,
-                        cl.celem_id.ptr,          cl.celem_color.ptr,    cl.celem_lnode.ptr,
-                        cl.celem_pos.ptr,         own_row.ptr,           cl.p1 - cl.p0};
+        PlanView v{};
+        v.patch_node_ptr = patch_node_ptr.ptr + cl.p0;
+        v.patch_elem_ptr = cl.patch_elem_ptr.ptr;
+        v.patch_cnode_ptr = cl.patch_cnode_ptr.ptr;
+        v.patch_acc = patch_acc.ptr + cl.p0;
+        v.own_acc = own_acc.ptr;
+        v.own_rowptr = own_rowptr.ptr;
+        v.own_hv = own_hv.ptr;
+        v.cnode_gid = cl.cnode_gid.ptr;
+        v.cnode_own = cl.cnode_own.ptr;
+        v.celem_id = cl.celem_id.ptr;
+        v.celem_color = cl.celem_color.ptr;
+        v.celem_lnode = cl.celem_lnode.ptr;
+        v.celem_pos = cl.celem_pos.ptr;
+        v.own_row = own_row.ptr;
+        v.n_patches = cl.p1 - cl.p0;
+        v.celem_aidx = cl.celem_aidx.ptr;
+        v.aidx_n = cl.total_celems;
+        return v;
     }
     PlanView view() const { return view(full); }
     void reset() {

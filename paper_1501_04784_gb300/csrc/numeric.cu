@@ -117,11 +117,11 @@ __global__ void __launch_bounds__(INT_THREADS) k_integrate(const int32_t *__rest
 }
 
 // Adds the owned entries of one element's packed k_e into the block's
-// accumulators.  Row bases are looked up once per node, then the accumulator
-// reads of a group of entries are issued together before their writes, so a
-// group costs one shared-memory round trip instead of one per entry.  All
-// entries of one element are distinct, so the reads of a group do not alias
-// its writes.
+// accumulators.  Each entry's target comes precomputed from the plan (two 16-bit
+// targets per word, see PlanView::celem_aidx).  The accumulator reads of a group
+// of entries are issued together before their writes, so a group costs one
+// shared-memory round trip instead of one per entry; all entries of one element
+// are distinct, so the reads of a group do not alias its writes.
 __host__ __device__ constexpr int tri_row(int q) {
     int a = 0;
     while ((a + 1) * (a + 2) / 2 <= q) ++a;
@@ -129,57 +129,40 @@ __host__ __device__ constexpr int tri_row(int q) {
 }
 
 template <int NPE, typename AccT, bool MIXED>
-__device__ __forceinline__ void scatter_element(const uint32_t (&pw)[(NPE * (NPE + 1) / 2 + 3) / 4],
-                                                const uint16_t (&ln)[NPE],
-                                                const int32_t *cown, const int32_t *roff, const uint8_t *hvf,
+__device__ __forceinline__ void scatter_element(const uint32_t (&aw)[NPE * (NPE + 1) / 4], const int32_t *roff,
                                                 void *hv, bool fp64_sums, AccT *acc,
                                                 const AccT (&kv)[NPE * (NPE + 1) / 2]) {
     constexpr int NP = NPE * (NPE + 1) / 2;
-    int own[NPE], rbase[NPE];
-#pragma unroll
-    for (int a = 0; a < NPE; ++a) own[a] = cown[ln[a]];
-#pragma unroll
-    for (int a = 0; a < NPE; ++a) rbase[a] = own[a] >= 0 ? roff[own[a]] : -1;
-    // entry q of the packed lower triangle is the pair (a, b) = (pa(q), pb(q))
-    auto entry_index = [&](int q, int a, int b) {
-        const int base = ln[a] > ln[b] ? rbase[a] : rbase[b];
-        const int pos = (pw[q >> 2] >> (8 * (q & 3))) & 0xff;
-        return base >= 0 ? base + pos : -1;
-    };
-    if constexpr (MIXED) {
-        // diagonal entries of high-valence rows are summed in FP64 instead
-#pragma unroll
-        for (int a = 0; a < NPE; ++a) {
-            const int q = a * (a + 1) / 2 + a;
-            if (rbase[a] >= 0 && hvf[own[a]]) {
-                if (fp64_sums) static_cast<double *>(hv)[own[a]] += (double)kv[q];
-                else two_sum_acc(static_cast<float2 *>(hv)[own[a]], (float)kv[q]);
-                rbase[a] = -2 - rbase[a];  // keep off-diagonals, mark the diagonal
-            }
-        }
-    }
     constexpr int G = 12;
 #pragma unroll
     for (int g0 = 0; g0 < NP; g0 += G) {
         int idx[G];
-        AccT old[G];
 #pragma unroll
         for (int j = 0; j < G; ++j) {
             const int q = g0 + j;
+            idx[j] = -1;
             if (q < NP) {
-                const int a = tri_row(q), b = q - a * (a + 1) / 2;
-                if (MIXED && a == b) idx[j] = rbase[a] >= 0 ? entry_index(q, a, b) : -1;
-                else {
-                    const int ra = rbase[a] < -1 ? -2 - rbase[a] : rbase[a];
-                    const int rb = rbase[b] < -1 ? -2 - rbase[b] : rbase[b];
-                    const int base = ln[a] > ln[b] ? ra : rb;
-                    const int pos = (pw[q >> 2] >> (8 * (q & 3))) & 0xff;
-                    idx[j] = base >= 0 ? base + pos : -1;
+                const uint32_t t = (aw[q >> 1] >> (16 * (q & 1))) & 0xffffu;
+                const int a = tri_row(q);
+                if (q == a * (a + 1) / 2 + a) {
+                    // a diagonal: owned entry, FP64-accurate diagonal, or not owned
+                    if (t < AIDX_HV) {
+                        idx[j] = (int)t;
+                    } else if (t != AIDX_NONE) {
+                        const int k = (int)(t & 0x7fffu);
+                        if constexpr (MIXED) {
+                            if (fp64_sums) static_cast<double *>(hv)[k] += (double)kv[q];
+                            else two_sum_acc(static_cast<float2 *>(hv)[k], (float)kv[q]);
+                        } else {
+                            idx[j] = roff[k + 1] - 1;  // the diagonal closes a lower row
+                        }
+                    }
+                } else {
+                    idx[j] = t < AIDX_HV ? (int)t : -1;
                 }
-            } else {
-                idx[j] = -1;
             }
         }
+        AccT old[G];
 #pragma unroll
         for (int j = 0; j < G; ++j)
             if (idx[j] >= 0) old[j] = acc[idx[j]];
@@ -201,7 +184,6 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
     AccT *acc = reinterpret_cast<AccT *>(patch_smem + L.acc);
     double *hv = reinterpret_cast<double *>(patch_smem + L.hv);
     S(*xs)[3] = reinterpret_cast<S(*)[3]>(patch_smem + L.xs);
-    int32_t *cown = reinterpret_cast<int32_t *>(patch_smem + L.cown);
     int32_t *roff = reinterpret_cast<int32_t *>(patch_smem + L.roff);
     uint8_t *hvf = patch_smem + L.hvf;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -221,20 +203,18 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
         // chunks of CH per thread before their shared-memory stores, so each
         // thread has CH global loads in flight instead of one per round trip.
         constexpr int CH = 8;
-        for (int j0 = 0; j0 < ncn; j0 += CH * nthr) {
-            int32_t vo[CH], vg[CH];
+        if constexpr (FUSED) {
+            for (int j0 = 0; j0 < ncn; j0 += CH * nthr) {
+                int32_t vg[CH];
 #pragma unroll
-            for (int k = 0; k < CH; ++k) {
-                const int j = j0 + k * nthr + tid;
-                vo[k] = j < ncn ? pv.cnode_own[cb + j] : 0;
-                vg[k] = (FUSED && j < ncn) ? pv.cnode_gid[cb + j] : 0;
-            }
+                for (int k = 0; k < CH; ++k) {
+                    const int j = j0 + k * nthr + tid;
+                    vg[k] = j < ncn ? pv.cnode_gid[cb + j] : 0;
+                }
 #pragma unroll
-            for (int k = 0; k < CH; ++k) {
-                const int j = j0 + k * nthr + tid;
-                if (j < ncn) {
-                    cown[j] = vo[k];
-                    if constexpr (FUSED) gid[j] = vg[k];
+                for (int k = 0; k < CH; ++k) {
+                    const int j = j0 + k * nthr + tid;
+                    if (j < ncn) gid[j] = vg[k];
                 }
             }
         }
@@ -314,7 +294,7 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
             const int64_t ci = eb + i;
             AccT kv[NP];
             uint16_t ln[NPE];
-            uint32_t pw[(NP + 3) / 4];
+            uint32_t aw[NP / 2];
             int mycol = -1;
             if constexpr (NPE == 4) {
 #pragma unroll
@@ -350,17 +330,16 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
 #pragma unroll
                     for (int q = 0; q < NP; ++q) kv[q] = __ldg(ke + e * NP + q);
                 }
-                // in-row positions before the colour phases, so that no phase waits
-                // on its own global load (one exposed latency per batch)
-                const uint32_t *pp = reinterpret_cast<const uint32_t *>(pv.celem_pos + ci * ((NP + 3) / 4 * 4));
+                // accumulator targets before the colour phases, so that no phase
+                // waits on its own global load (one exposed latency per batch)
 #pragma unroll
-                for (int w = 0; w < (NP + 3) / 4; ++w) pw[w] = __ldg(pp + w);
+                for (int w = 0; w < NP / 2; ++w) aw[w] = __ldg(pv.celem_aidx + w * pv.aidx_n + ci);
             }
             const int last = min(base + nthr, nel) - 1;
             const int c0 = pv.celem_color[eb + base], c1 = pv.celem_color[eb + last];
             for (int cc = c0; cc <= c1; ++cc) {
                 if (mycol == cc)
-                    scatter_element<NPE, AccT, MIXED>(pw, ln, cown, roff, hvf, hv, fp64_sums, acc, kv);
+                    scatter_element<NPE, AccT, MIXED>(aw, roff, hv, fp64_sums, acc, kv);
                 __syncthreads();
             }
         }
@@ -477,8 +456,7 @@ PatchSmem patch_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsi
     if (mixed) o = align16(o + (size_t)P.max_own * sizeof(double));
     L.xs = o;
     if (fused) o = align16(o + (size_t)P.max_cnodes * 3 * xsize);
-    L.cown = o;
-    o = align16(o + (size_t)P.max_cnodes * sizeof(int32_t));
+    L.cown = o;  // unused: accumulator targets come from the plan
     L.roff = o;
     o = align16(o + (size_t)(P.max_own + 1) * sizeof(int32_t));
     L.hvf = o;

@@ -456,12 +456,20 @@ __global__ void k_cnode_own(const uint64_t *cn_keys, int64_t ncn, int64_t p0, co
 
 // Per closure element: id, colour, closure-local node indices (binary search in
 // the patch's sorted closure-node list) and, for every packed pair (a, b), the
-// position of min(g_a, g_b) within row max(g_a, g_b) of the pattern.
+// position of min(g_a, g_b) within row max(g_a, g_b) of the pattern, plus the
+// pair's target in the patch's accumulators (celem_aidx, see PlanView).
+struct OwnTables {
+    const int32_t *node_patch, *own_idx, *own_acc;
+    const int64_t *patch_node_ptr;  // global patch index
+    const uint8_t *own_hv;
+    int64_t p0;
+};
+
 template <int NPE>
 __global__ void k_celem_fill(const uint64_t *ckeys, int64_t nce, const int32_t *__restrict__ E,
                              const uint64_t *cn_keys, const int64_t *pc_ptr, const int64_t *__restrict__ rowptr,
-                             const int32_t *__restrict__ col, int pos_stride, int32_t *celem_id, uint8_t *celem_color,
-                             uint16_t *lnode, uint8_t *pos) {
+                             const int32_t *__restrict__ col, int pos_stride, OwnTables ot, int32_t *celem_id,
+                             uint8_t *celem_color, uint16_t *lnode, uint8_t *pos, uint16_t *aidx) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nce; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t k = ckeys[i];
         const uint64_t p = k >> 40;
@@ -481,6 +489,8 @@ __global__ void k_celem_fill(const uint64_t *ckeys, int64_t nce, const int32_t *
             }
             lnode[i * NPE + a] = (uint16_t)(lo - cb);
         }
+        const int64_t gp = ot.p0 + (int64_t)p;
+        const int64_t nb = ot.patch_node_ptr[gp];
         int q = 0;
 #pragma unroll
         for (int a = 0; a < NPE; ++a)
@@ -494,6 +504,14 @@ __global__ void k_celem_fill(const uint64_t *ckeys, int64_t nce, const int32_t *
                     if (col[mid] < cv) lo = mid + 1; else hi = mid;
                 }
                 pos[i * pos_stride + q] = (uint8_t)(lo - r0);
+                uint32_t t = AIDX_NONE;
+                if (ot.node_patch[r] == gp) {
+                    const int32_t kr = ot.own_idx[r];
+                    if (a == b && ot.own_hv[nb + kr]) t = AIDX_HV | (uint32_t)kr;
+                    else t = (uint32_t)(ot.own_acc[nb + kr] + (lo - r0));
+                }
+                // word q/2 of element i, low half for even q
+                aidx[((int64_t)(q >> 1) * nce + i) * 2 + (q & 1)] = (uint16_t)t;
             }
     }
 }
@@ -776,14 +794,17 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
     FEM_TRY(cl.celem_lnode.alloc(ar, nce * npe, "celem local nodes"));
     FEM_TRY(cl.celem_pos.alloc(ar, nce * P.pos_stride, "celem positions"));
     FEM_CUDA(cudaMemsetAsync(cl.celem_pos.ptr, 0, nce * P.pos_stride, s));
+    FEM_TRY(cl.celem_aidx.alloc(ar, nce * (m->np / 2), "celem accumulator targets"));
+    const OwnTables ot{P.node_patch.ptr, P.own_idx.ptr, P.own_acc.ptr, P.patch_node_ptr.ptr, P.own_hv.ptr, p0};
+    uint16_t *aidx16 = reinterpret_cast<uint16_t *>(cl.celem_aidx.ptr);
     if (npe == 8)
         k_celem_fill<8><<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, nce, m->E, cnkeys.ptr, cl.patch_cnode_ptr.ptr,
-                                                      m->rowptr.ptr, m->col.ptr, P.pos_stride, cl.celem_id.ptr,
-                                                      cl.celem_color.ptr, cl.celem_lnode.ptr, cl.celem_pos.ptr);
+                                                      m->rowptr.ptr, m->col.ptr, P.pos_stride, ot, cl.celem_id.ptr,
+                                                      cl.celem_color.ptr, cl.celem_lnode.ptr, cl.celem_pos.ptr, aidx16);
     else
         k_celem_fill<4><<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, nce, m->E, cnkeys.ptr, cl.patch_cnode_ptr.ptr,
-                                                      m->rowptr.ptr, m->col.ptr, P.pos_stride, cl.celem_id.ptr,
-                                                      cl.celem_color.ptr, cl.celem_lnode.ptr, cl.celem_pos.ptr);
+                                                      m->rowptr.ptr, m->col.ptr, P.pos_stride, ot, cl.celem_id.ptr,
+                                                      cl.celem_color.ptr, cl.celem_lnode.ptr, cl.celem_pos.ptr, aidx16);
     FEM_LAUNCHED("k_celem_fill");
     FEM_CUDA(cudaMemcpyAsync(h_pc.data(), cl.patch_cnode_ptr.ptr, (np_ + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     FEM_CUDA(cudaStreamSynchronize(s));
@@ -914,8 +935,9 @@ fem_status build_plan(fem_mesh m, cudaStream_t s) {
         P.max_own = std::max(P.max_own, h_pn[p + 1] - h_pn[p]);
         P.max_acc = std::max(P.max_acc, (int64_t)h_acc[p]);
     }
-    if (P.max_own > 32767) {
-        set_error("a patch owns %lld rows; at most 32767 are supported", (long long)P.max_own);
+    if (P.max_own > 32767 || P.max_acc > 32767) {
+        set_error("a patch owns %lld rows and %lld entries; at most 32767 of each are supported",
+                  (long long)P.max_own, (long long)P.max_acc);
         return FEM_ERR_UNSUPPORTED;
     }
 
