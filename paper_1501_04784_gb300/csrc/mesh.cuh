@@ -72,6 +72,7 @@ struct Plan {
     int64_t n_patches = 0;
     int64_t max_acc = 0, max_own = 0;
     int pos_stride = 0;
+    bool any_hv = false;  // some row's diagonal is summed FP64-accurately (mixed)
     DevBuf<int64_t> patch_node_ptr, own_rowptr;
     DevBuf<int32_t> patch_acc, own_acc, own_row, node_patch, own_idx;
     DevBuf<uint8_t> own_hv;
@@ -108,6 +109,7 @@ struct Plan {
         n_patches = max_acc = max_own = total_cnodes = total_celems = max_cnodes = max_celems = 0;
         n_colors = 0;
         chunked = false;
+        any_hv = false;
     }
     size_t bytes() const {
         return patch_node_ptr.bytes() + own_rowptr.bytes() + patch_acc.bytes() + own_acc.bytes() + own_row.bytes() +
@@ -128,6 +130,7 @@ struct fem_mesh_s {
     bool has_pattern = false;
     int64_t nnz = 0;
     int max_row_len = 0;
+    int64_t max_deg = 0;  // most elements incident to one node
     fem::DevBuf<int64_t> rowptr;
     fem::DevBuf<int32_t> col;
     fem::DevBuf<int64_t> inc_ptr;  // node -> incident elements (kept for the backward pass)

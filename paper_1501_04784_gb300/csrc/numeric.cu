@@ -236,14 +236,20 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
                     roff[kk] = vr[k];
                     rps[kk] = vp[k];
                     if constexpr (MIXED) {
-                        hv[kk] = 0.0;  // also clears the (hi, lo) float pair
+                        if (L.hv_on) hv[kk] = 0.0;  // also clears the (hi, lo) float pair
                         hvf[kk] = vh[k];
                     }
                 }
             }
         }
         if (tid == 0) roff[nown] = nacc;
-        for (int i = tid; i < nacc; i += nthr) acc[i] = AccT(0);
+        {
+            // accumulators cleared with 16-byte stores (acc starts the layout)
+            constexpr int V = 16 / sizeof(AccT);
+            float4 *a4 = reinterpret_cast<float4 *>(acc);
+            for (int i = tid; i < nacc / V; i += nthr) a4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = nacc / V * V + tid; i < nacc; i += nthr) acc[i] = AccT(0);
+        }
         __syncthreads();
         // Prologue, stage 2: node coordinates of the closure, gathered through the
         // staged ids, CH nodes (3 CH loads) in flight per thread.
@@ -453,7 +459,8 @@ PatchSmem patch_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsi
     L.acc = o;
     o = align16(o + (size_t)P.max_acc * accsz);
     L.hv = o;
-    if (mixed) o = align16(o + (size_t)P.max_own * sizeof(double));
+    L.hv_on = mixed && P.any_hv;
+    if (L.hv_on) o = align16(o + (size_t)P.max_own * sizeof(double));
     L.xs = o;
     if (fused) o = align16(o + (size_t)P.max_cnodes * 3 * xsize);
     L.cown = o;  // unused: accumulator targets come from the plan
@@ -467,11 +474,10 @@ PatchSmem patch_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsi
     if (fused) o = align16(o + (size_t)P.max_cnodes * sizeof(int32_t));
     L.eid = L.cvs = o;
     (void)csize;
-    // lanes per row in the write-out: the power of two at or above the mean
-    // owned-row length of the largest patch, between 4 and 32
-    const int64_t mean_row = P.max_own > 0 ? (P.max_acc + P.max_own - 1) / P.max_own : 1;
+    // lanes per row in the write-out: 4, so that a warp's per-row bookkeeping
+    // covers 8 rows at once (faster than one lane group per mean row length for
+    // rows of 8 to 14 entries)
     L.wg_shift = 2;
-    while (L.wg_shift < 5 && (int64_t(1) << L.wg_shift) < mean_row) ++L.wg_shift;
     L.total = o;
     return L;
 }

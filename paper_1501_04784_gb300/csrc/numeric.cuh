@@ -13,6 +13,7 @@ static constexpr int PATCH_MAX_THREADS = 512;
 struct PatchSmem {
     size_t acc, hv, xs, cown, roff, hvf, rps, gid, eid, cvs, total;
     int wg_shift;  // log2 of the lanes that store one owned row
+    int hv_on;     // the hv region exists (some owned row has an FP64-accurate diagonal)
 };
 
 struct IntegrateArgs {
@@ -44,7 +45,9 @@ struct PatchArgs {
 // Largest per-patch sizes over the plans a launch covers (sizes shared memory).
 struct PlanMax {
     int64_t max_acc = 0, max_own = 0, max_cnodes = 0;
+    bool any_hv = false;
     void add(const Plan &P) {
+        any_hv = any_hv || P.any_hv;
         max_acc = std::max(max_acc, P.max_acc);
         max_own = std::max(max_own, P.max_own);
         max_cnodes = std::max(max_cnodes, P.max_cnodes);

@@ -585,6 +585,7 @@ fem_status build_pattern(fem_mesh m, cudaStream_t s) {
         FEM_LAUNCHED("k_max_deg");
         FEM_TRY(read_scalar(mx.ptr, &max_deg, s));
     }
+    m->max_deg = (int64_t)max_deg;
     const int cap = (int)(max_deg * npe);
     if (cap > 64 * 32) {
         set_error("a node belongs to %llu elements; at most %d are supported", max_deg, (int)(64 * 32 / npe));
@@ -919,6 +920,7 @@ fem_status build_plan(fem_mesh m, cudaStream_t s) {
     FEM_TRY(P.own_hv.alloc(ar, N, "own hv"));
     FEM_TRY(P.patch_acc.alloc(ar, npatch, "patch acc"));
     const int hv_thr = m->opt.valence_threshold;
+    P.any_hv = m->max_deg > hv_thr;
     k_patch_nodes<<<grid_for(N), TPB, 0, s>>>(m->order.ptr, pre.ptr, P.patch_node_ptr.ptr, N, cap_eff, npatch,
                                               m->rowptr.ptr, m->inc_ptr.ptr, hv_thr, P.node_patch.ptr, P.own_idx.ptr,
                                               P.own_row.ptr, P.own_rowptr.ptr, P.own_acc.ptr, P.own_hv.ptr);
