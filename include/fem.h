@@ -86,7 +86,11 @@ typedef struct {
     int fp64_fused;              /* FEM_FP64 builds: 0 (default) = integrate each element once
                                     into library memory, then assemble; 1 = recompute element
                                     matrices inside the assembly (no staging memory) */
-    int reserved[8];
+    int fp64_dets;               /* mixed mode, distorted tetrahedra: 0 (default) = Jacobian
+                                    determinant in double-single FP32 arithmetic (accurate to
+                                    ~2^-46 of its terms, FP64-grade for the float result);
+                                    1 = FP64 arithmetic */
+    int reserved[7];
 } fem_options;
 
 typedef struct {

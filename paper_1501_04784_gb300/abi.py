@@ -24,7 +24,8 @@ class fem_options(ctypes.Structure):
                 ("valence_threshold", ctypes.c_int), ("patch_entries", ctypes.c_int),
                 ("block_threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("locality_order", ctypes.c_int), ("fp64_sums", ctypes.c_int),
-                ("fp64_fused", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("fp64_fused", ctypes.c_int), ("fp64_dets", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
 
 
 class fem_info(ctypes.Structure):

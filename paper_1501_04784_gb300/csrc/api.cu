@@ -218,7 +218,7 @@ fem_status fem_integrate_local(fem_mesh m, fem_prec p, const void *X, fem_dtype 
         return FEM_ERR_ARG;
     }
     IntegrateArgs a{m->npe, p == FEM_MIXED, x_dtype, c_dtype, m->E, m->n_elems, X, c, ke_out,
-                    default_threshold(m), nullptr};
+                    default_threshold(m), nullptr, m->opt.fp64_dets != 0};
     return launch_integrate(a, as_stream(stream));
 }
 
@@ -236,7 +236,7 @@ static PatchArgs patch_args(fem_mesh m, fem_prec p, bool fused) {
     if (a.threads > PATCH_MAX_THREADS) a.threads = PATCH_MAX_THREADS;
     a.threads = (a.threads + 31) / 32 * 32;
     a.blocks_per_sm = m->opt.blocks_per_sm;
-    a.fp64_sums = m->opt.fp64_sums != 0;
+    a.fp64_mode = fp64_mode(m->opt);
     return a;
 }
 

@@ -81,6 +81,69 @@ __device__ __forceinline__ Vec3<float> cross3_accurate(const Vec3<float> &a, con
     return {det2(a.y, b.z, a.z, b.y), det2(a.z, b.x, a.x, b.z), det2(a.x, b.y, a.y, b.x)};
 }
 
+// Error-free transformations: Knuth's TwoSum (a + b = s + e exactly) and the FMA
+// form of Dekker's product (a * b = p + e exactly).
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod_f(float a, float b, float &p, float &e) {
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+
+// x - y split into a float pair (h, l) with h + l == x - y: exactly for float
+// inputs (TwoSum), to ~2^-48 relative for double inputs.
+__device__ __forceinline__ void diff_ds(float x, float y, float &h, float &l) { two_sum_f(x, -y, h, l); }
+__device__ __forceinline__ void diff_ds(double x, double y, float &h, float &l) {
+    const double d = x - y;
+    h = (float)d;
+    l = (float)(d - (double)h);
+}
+
+// Jacobian determinant of a tetrahedron, det [x1 - x0; x2 - x0; x3 - x0], in
+// double-single arithmetic: the edge vectors are formed exactly as float pairs,
+// each product of pairs is split exactly (the FMA form of Dekker's product) with
+// its cross terms added, each 2x2 minor and the final dot product are summed with
+// TwoSum.  The result, rounded once to float, is accurate to a few units of
+// 2^-46 times the sum of the magnitudes of the determinant's terms: what an FP64
+// evaluation from the same coordinates gives a float result, in FP32 arithmetic.
+template <typename S>
+__device__ __forceinline__ float det3_ds(const S (*xc)[3]) {
+    float h[3][3], l[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) diff_ds(xc[i + 1][k], xc[0][k], h[i][k], l[i][k]);
+    // product of pairs (ah + al)(bh + bl) as (p, e), dropping al * bl
+    auto mul = [](float ah, float al, float bh, float bl, float &p, float &e) {
+        two_prod_f(ah, bh, p, e);
+        e = fmaf(ah, bl, fmaf(al, bh, e));
+    };
+    // minors of rows 1, 2 (the cofactors of row 0) as unevaluated pairs (s, t)
+    float s[3], t[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int u = (k + 1) % 3, v = (k + 2) % 3;
+        float p, ep, q, eq, es;
+        mul(h[1][u], l[1][u], h[2][v], l[2][v], p, ep);
+        mul(h[1][v], l[1][v], h[2][u], l[2][u], q, eq);
+        two_sum_f(p, -q, s[k], es);
+        t[k] = es + (ep - eq);
+    }
+    float P[3], E[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        two_prod_f(h[0][k], s[k], P[k], E[k]);
+        E[k] = fmaf(h[0][k], t[k], fmaf(l[0][k], s[k], E[k]));
+    }
+    float a, e1, b, e2;
+    two_sum_f(P[0], P[1], a, e1);
+    two_sum_f(a, P[2], b, e2);
+    return b + ((e1 + e2) + (E[0] + E[1] + E[2]));
+}
+
 template <typename T>
 __device__ __forceinline__ Vec3<T> lerp2(T wa, const Vec3<T> &a, T wb, const Vec3<T> &b) {
     return {wa * a.x + wb * b.x, wa * a.y + wb * b.y, wa * a.z + wb * b.z};
@@ -384,10 +447,12 @@ __device__ __forceinline__ void tet_ke(const S (*xc)[3], T c, T (&k)[10]) {
 
 // Mixed precision tetrahedron: the aspect ratio (longest edge over shortest
 // altitude = L_max |F|_max / |det J|) is evaluated in FP32; above `thr` the
-// face vectors and the determinant are recomputed in FP64 from the coordinate
-// differences and rounded once.  Returns true when the FP64 path was taken.
+// face vectors are recomputed with one rounding each and the determinant to
+// FP64 accuracy -- in double-single FP32 arithmetic (det3_ds) by default, or in
+// FP64 arithmetic when fp64_det is set -- and rounded once.  Returns true when
+// the accurate path was taken.
 template <typename S>
-__device__ __forceinline__ bool tet_ke_mixed(const S (*xc)[3], float c, float thr, float (&k)[10]) {
+__device__ __forceinline__ bool tet_ke_mixed(const S (*xc)[3], float c, float thr, bool fp64_det, float (&k)[10]) {
     TetGeom<float> g;
     tet_geom<float, S>(xc, g);
     Vec3<float> F[4];
@@ -400,17 +465,28 @@ __device__ __forceinline__ bool tet_ke_mixed(const S (*xc)[3], float c, float th
     const bool flagged = !(L2 * A2 <= thr * thr * det * det);
     if (flagged) {
         // Distorted: cofactors (face vectors) with one rounding each, and the
-        // Jacobian determinant in FP64 from exact FP64 products of the FP32 edge
-        // vectors (a product of two floats is exact in double).
+        // Jacobian determinant to FP64 accuracy.  The double-single form keeps
+        // the work off the FP64 pipe (1/64 of the FP32 rate on this part), where
+        // a warp with one distorted lane would otherwise stall all 32.
         F[1] = cross3_accurate(g.R1, g.R2);
         F[2] = cross3_accurate(g.R2, g.R0);
         F[3] = cross3_accurate(g.R0, g.R1);
         F[0] = cross3_accurate(g.D2, g.D1);
-        const double r1y = g.R1.y, r1z = g.R1.z, r1x = g.R1.x, r2x = g.R2.x, r2y = g.R2.y, r2z = g.R2.z;
-        const double m0 = fma(r1y, r2z, -(r1z * r2y));
-        const double m1 = fma(r1z, r2x, -(r1x * r2z));
-        const double m2 = fma(r1x, r2y, -(r1y * r2x));
-        det = (float)fma((double)g.R0.x, m0, fma((double)g.R0.y, m1, (double)g.R0.z * m2));
+        if (fp64_det) {
+            // FP64 from the coordinates: the edge vectors are exact in double
+            // (differences of floats), the products of two of them too
+            double r[3][3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) r[i][k] = (double)xc[i + 1][k] - (double)xc[0][k];
+            const double m0 = fma(r[1][1], r[2][2], -(r[1][2] * r[2][1]));
+            const double m1 = fma(r[1][2], r[2][0], -(r[1][0] * r[2][2]));
+            const double m2 = fma(r[1][0], r[2][1], -(r[1][1] * r[2][0]));
+            det = (float)fma(r[0][0], m0, fma(r[0][1], m1, r[0][2] * m2));
+        } else {
+            det = det3_ds<S>(xc);
+        }
     }
     tet_from_faces(F, det, c, k);
     return flagged;

@@ -16,6 +16,9 @@ struct PatchSmem {
     int hv_on;     // the hv region exists (some owned row has an FP64-accurate diagonal)
 };
 
+// Bits of the FP64 mode of the mixed kernels (fem_options.fp64_sums, fp64_dets).
+static constexpr unsigned FP64_SUMS = 1u, FP64_DETS = 2u;
+
 struct IntegrateArgs {
     int npe;
     bool mixed;
@@ -26,6 +29,7 @@ struct IntegrateArgs {
     void *ke;
     float thr;
     unsigned long long *nflag;
+    bool fp64_det = false;  // distorted tetrahedra: FP64 determinant instead of double-single
 };
 
 struct PatchArgs {
@@ -39,7 +43,8 @@ struct PatchArgs {
     float thr;
     int64_t p0, p1;
     int threads, blocks_per_sm;
-    bool fp64_sums;  // high-valence sums with FP64 adds instead of FP32 TwoSum pairs
+    unsigned fp64_mode;  // FP64_SUMS: high-valence sums with FP64 adds instead of FP32 TwoSum pairs;
+                         // FP64_DETS: distorted tetrahedra's determinant in FP64 arithmetic
 };
 
 // Largest per-patch sizes over the plans a launch covers (sizes shared memory).
@@ -65,7 +70,8 @@ struct BatchItem {
 
 struct BatchLaunch {
     int npe = 8;
-    bool mixed = true, fp64_sums = false;
+    bool mixed = true;
+    unsigned fp64_mode = 0;
     const BatchItem *items = nullptr;
     const int64_t *prefix = nullptr;
     int n = 0;
@@ -79,6 +85,10 @@ fem_status batched_config(int npe, bool mixed, const PlanMax &pm, int threads, i
 fem_status launch_batched_kernel(const BatchLaunch &bl, cudaStream_t s);
 
 fem_status launch_integrate(const IntegrateArgs &a, cudaStream_t s);
+
+inline unsigned fp64_mode(const fem_options &o) {
+    return (o.fp64_sums ? FP64_SUMS : 0u) | (o.fp64_dets ? FP64_DETS : 0u);
+}
 fem_status launch_patch(const PatchArgs &a, cudaStream_t s);
 PatchSmem patch_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsize, size_t csize);
 

@@ -191,6 +191,45 @@ def test_full_size_1M_bricks_sampled(fem, prec):
     assert worst <= (TOL_FP64 if prec == "fp64" else TOL_MIXED), worst
 
 
+def sliver_tets(n=64, lift=1e-4, seed=7):
+    """n separate slivers: a unit right triangle and a fourth node `lift` above a
+    point inside it, each randomly rotated and shifted, so that the Jacobian
+    determinant is a heavily cancelling sum of products of the FP32 edge
+    vectors (a plain FP32 evaluation is off by ~1e-4 relative)."""
+    rng = np.random.default_rng(seed)
+    P = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0.3, 0.3, lift]], float)
+    X, E = [], []
+    for t in range(n):
+        Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        X.append(P @ Q.T + rng.normal(size=3))
+        E.append([4 * t, 4 * t + 1, 4 * t + 2, 4 * t + 3])
+    return meshgen.Mesh(X=np.vstack(X), E=np.asarray(E, np.int32), c=rng.lognormal(0, 0.5, n), npe=4,
+                        shape=(n, 1, 1))
+
+
+@pytest.mark.parametrize("fp64_dets", [0, 1])
+def test_distorted_tet_determinant_modes(fem, fp64_dets):
+    """Distorted tetrahedra take an FP64-accurate determinant, in double-single
+    FP32 arithmetic (default) or in FP64: slivers far beyond a plain FP32
+    determinant's reach still meet the mixed tolerance, element by element and
+    assembled, and so does the 80^3-cell tetrahedron recipe at 10^3 cells."""
+    m = sliver_tets()
+    mesh = make(fem, m, fp64_dets=fp64_dets)
+    Xd, cd, X, c = inputs(m, "mixed")
+    ke = mesh.integrate_local(Xd, cd, "mixed").cpu().numpy()
+    ref, cs, _ = oracle_ke(m, X, c)
+    assert rel_err(ke.ravel(), ref.ravel(), cs.ravel()) <= TOL_MIXED
+    refK = oracle_K(m, X, c)
+    vals = mesh.build_K(Xd, cd, "mixed").cpu().numpy()
+    assert rel_err(vals, refK["vals"], refK["cs"]) <= TOL_MIXED
+    m = MESHES["tet10_perm"]()
+    mesh = make(fem, m, fp64_dets=fp64_dets)
+    Xd, cd, X, c = inputs(m, "mixed")
+    refK = oracle_K(m, X, c)
+    vals = mesh.build_K(Xd, cd, "mixed").cpu().numpy()
+    assert rel_err(vals, refK["vals"], refK["cs"]) <= TOL_MIXED
+
+
 @pytest.mark.parametrize("fp64_sums", [0, 1])
 def test_high_valence_summation_modes(fem, fp64_sums):
     """Tet diagonals (up to 24 contributions) are summed FP64-accurately either by
