@@ -35,15 +35,18 @@ struct PlanView {
     int64_t n_patches;
     // [NP/2 words][total celems] (word-major, so a warp's loads of one word are
     // contiguous): two 16-bit targets per word, entry q in the low half when q is
-    // even.  A target is the entry's offset in the patch's accumulators, 0xFFFF
-    // when its row is not owned by the patch, or 0x8000 | k for the diagonal of
-    // owned row k when that row's diagonal is summed FP64-accurately.
+    // even.  A target is the entry's offset in the patch's accumulators; for a
+    // pair whose row the patch does not own, one of 32 scratch accumulators past
+    // the largest patch's (max_acc + the element's lane in its batch), added to
+    // and never read; 0x8000 | k for the diagonal of owned row k when that row's
+    // diagonal is summed FP64-accurately.
     const uint32_t *celem_aidx;
     int64_t aidx_n;                  // total celems (the word stride)
 };
 
-// Packed targets of celem_aidx.
-static constexpr uint32_t AIDX_NONE = 0xFFFFu, AIDX_HV = 0x8000u;
+// Marker bit of celem_aidx's FP64-accurate diagonals; scratch accumulators per block.
+static constexpr uint32_t AIDX_HV = 0x8000u;
+static constexpr int ACC_SCRATCH = 32;
 
 // Closure data of a range of patches [p0, p1): the elements each patch
 // integrates and the nodes they touch.  Patch indices inside are relative to p0.

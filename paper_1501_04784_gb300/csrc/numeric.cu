@@ -144,21 +144,17 @@ __device__ __forceinline__ void scatter_element(const uint32_t (&aw)[NPE * (NPE 
             if (q < NP) {
                 const uint32_t t = (aw[q >> 1] >> (16 * (q & 1))) & 0xffffu;
                 const int a = tri_row(q);
-                if (q == a * (a + 1) / 2 + a) {
-                    // a diagonal: owned entry, FP64-accurate diagonal, or not owned
-                    if (t < AIDX_HV) {
-                        idx[j] = (int)t;
-                    } else if (t != AIDX_NONE) {
-                        const int k = (int)(t & 0x7fffu);
-                        if constexpr (MIXED) {
-                            if (fp64_sums) static_cast<double *>(hv)[k] += (double)kv[q];
-                            else two_sum_acc(static_cast<float2 *>(hv)[k], (float)kv[q]);
-                        } else {
-                            idx[j] = roff[k + 1] - 1;  // the diagonal closes a lower row
-                        }
+                if (q == a * (a + 1) / 2 + a && t >= AIDX_HV) {
+                    // a diagonal summed FP64-accurately
+                    const int k = (int)(t & 0x7fffu);
+                    if constexpr (MIXED) {
+                        if (fp64_sums) static_cast<double *>(hv)[k] += (double)kv[q];
+                        else two_sum_acc(static_cast<float2 *>(hv)[k], (float)kv[q]);
+                    } else {
+                        idx[j] = roff[k + 1] - 1;  // the diagonal closes a lower row
                     }
                 } else {
-                    idx[j] = t < AIDX_HV ? (int)t : -1;
+                    idx[j] = (int)t;  // owned entry, or the lane's scratch slot
                 }
             }
         }
@@ -458,7 +454,7 @@ PatchSmem patch_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsi
     const size_t accsz = mixed ? sizeof(float) : sizeof(double);
     size_t o = 0;
     L.acc = o;
-    o = align16(o + (size_t)P.max_acc * accsz);
+    o = align16(o + (size_t)(P.max_acc + ACC_SCRATCH) * accsz);
     L.hv = o;
     L.hv_on = mixed && P.any_hv;
     if (L.hv_on) o = align16(o + (size_t)P.max_own * sizeof(double));

@@ -462,7 +462,9 @@ struct OwnTables {
     const int32_t *node_patch, *own_idx, *own_acc;
     const int64_t *patch_node_ptr;  // global patch index
     const uint8_t *own_hv;
+    const int64_t *pe_ptr;          // closure-element range of each patch of the closure
     int64_t p0;
+    int32_t trash;                  // first of the 32 scratch accumulators (the plan's max_acc)
 };
 
 template <int NPE>
@@ -504,7 +506,9 @@ __global__ void k_celem_fill(const uint64_t *ckeys, int64_t nce, const int32_t *
                     if (col[mid] < cv) lo = mid + 1; else hi = mid;
                 }
                 pos[i * pos_stride + q] = (uint8_t)(lo - r0);
-                uint32_t t = AIDX_NONE;
+                // a pair whose row the patch does not own goes to a scratch slot of
+                // the lane that will hold the element, never read
+                uint32_t t = (uint32_t)(ot.trash + ((i - ot.pe_ptr[p]) & 31));
                 if (ot.node_patch[r] == gp) {
                     const int32_t kr = ot.own_idx[r];
                     if (a == b && ot.own_hv[nb + kr]) t = AIDX_HV | (uint32_t)kr;
@@ -796,7 +800,8 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
     FEM_TRY(cl.celem_pos.alloc(ar, nce * P.pos_stride, "celem positions"));
     FEM_CUDA(cudaMemsetAsync(cl.celem_pos.ptr, 0, nce * P.pos_stride, s));
     FEM_TRY(cl.celem_aidx.alloc(ar, nce * (m->np / 2), "celem accumulator targets"));
-    const OwnTables ot{P.node_patch.ptr, P.own_idx.ptr, P.own_acc.ptr, P.patch_node_ptr.ptr, P.own_hv.ptr, p0};
+    const OwnTables ot{P.node_patch.ptr,     P.own_idx.ptr, P.own_acc.ptr,          P.patch_node_ptr.ptr,
+                       P.own_hv.ptr,         cl.patch_elem_ptr.ptr, p0, (int32_t)P.max_acc};
     uint16_t *aidx16 = reinterpret_cast<uint16_t *>(cl.celem_aidx.ptr);
     if (npe == 8)
         k_celem_fill<8><<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, nce, m->E, cnkeys.ptr, cl.patch_cnode_ptr.ptr,
@@ -890,7 +895,7 @@ fem_status build_plan(fem_mesh m, cudaStream_t s) {
     P.reset();
     int64_t cap_entries = m->opt.patch_entries > 0 ? m->opt.patch_entries : 8192;
     if (cap_entries < 2 * (int64_t)m->max_row_len) cap_entries = 2 * (int64_t)m->max_row_len;
-    const int64_t cap_eff = cap_entries - m->max_row_len;
+    int64_t cap_eff = cap_entries - m->max_row_len;
     DevBuf<int64_t> pre;
     {
         DevBuf<int64_t> len, tmp;
@@ -901,6 +906,14 @@ fem_status build_plan(fem_mesh m, cudaStream_t s) {
         FEM_TRY(tmp.alloc(ar, scan_tmp_elems(N + 1), "scan scratch"));
         FEM_TRY(scan_exclusive_i64(len.ptr, pre.ptr, N, true, tmp.ptr, s));
         FEM_CUDA(cudaStreamSynchronize(s));
+    }
+    // Whole waves: the patch count is rounded up to a multiple of two blocks per
+    // SM (smaller patches, same cap), so that no block slot idles in the last
+    // wave while others run a patch more.  Below half a wave the mesh keeps its
+    // patches.
+    if (m->nnz > 0) {
+        const int64_t wave = 2 * (int64_t)num_sms(), np0 = cdiv(m->nnz, cap_eff);
+        if (np0 * 2 > wave) cap_eff = std::max<int64_t>(1, cdiv(m->nnz, cdiv(np0, wave) * wave));
     }
     P.n_patches = m->nnz > 0 ? cdiv(m->nnz, cap_eff) : 1;
     const int64_t npatch = P.n_patches;
@@ -937,8 +950,8 @@ fem_status build_plan(fem_mesh m, cudaStream_t s) {
         P.max_own = std::max(P.max_own, h_pn[p + 1] - h_pn[p]);
         P.max_acc = std::max(P.max_acc, (int64_t)h_acc[p]);
     }
-    if (P.max_own > 32767 || P.max_acc > 32767) {
-        set_error("a patch owns %lld rows and %lld entries; at most 32767 of each are supported",
+    if (P.max_own > 32767 || P.max_acc > 32767 - 32) {
+        set_error("a patch owns %lld rows and %lld entries; at most 32767 and 32735 are supported",
                   (long long)P.max_own, (long long)P.max_acc);
         return FEM_ERR_UNSUPPORTED;
     }
