@@ -233,7 +233,7 @@ static PatchArgs patch_args(fem_mesh m, fem_prec p, bool fused) {
     a.p0 = 0;
     a.p1 = m->plan.n_patches;
     a.threads = m->opt.block_threads > 0 ? m->opt.block_threads : 256;
-    if (a.threads > PATCH_MAX_THREADS) a.threads = PATCH_MAX_THREADS;
+    if (a.threads > patch_max_threads(m->npe)) a.threads = patch_max_threads(m->npe);
     a.threads = (a.threads + 31) / 32 * 32;
     a.blocks_per_sm = m->opt.blocks_per_sm;
     a.fp64_mode = fp64_mode(m->opt);

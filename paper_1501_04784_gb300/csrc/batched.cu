@@ -92,10 +92,11 @@ static fem_status create_ctx(BatchCtx &c, const void *const *X, const void *cons
     const fem_options &o = c.meshes[0]->opt;
     std::vector<std::pair<int, int>> cands;
     if (o.block_threads > 0) {
-        cands.push_back({std::min((o.block_threads + 31) / 32 * 32, PATCH_MAX_THREADS), o.blocks_per_sm});
+        cands.push_back({std::min((o.block_threads + 31) / 32 * 32, patch_max_threads(c.npe)), o.blocks_per_sm});
     } else {
         for (int t : {128, 256, 512})
-            for (int b : {0, 1}) cands.push_back({t, b});
+            if (t <= patch_max_threads(c.npe))
+                for (int b : {0, 1}) cands.push_back({t, b});
     }
     cudaEvent_t e0, e1;
     FEM_CUDA(cudaEventCreate(&e0));

@@ -72,25 +72,28 @@ __device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
 // a*b - c*d with a single rounding error (Kahan's FMA-based 2x2 determinant):
 // w = c*d is rounded, its rounding error is recovered exactly by an FMA.
 __device__ __forceinline__ float det2(float a, float b, float c, float d) {
-    const float w = c * d;
-    const float err = fmaf(-c, d, w);
-    const float f = fmaf(a, b, -w);
-    return f + err;
+    const float w = __fmul_rn(c, d);
+    const float err = __fmaf_rn(-c, d, w);
+    const float f = __fmaf_rn(a, b, -w);
+    return __fadd_rn(f, err);
 }
 __device__ __forceinline__ Vec3<float> cross3_accurate(const Vec3<float> &a, const Vec3<float> &b) {
     return {det2(a.y, b.z, a.z, b.y), det2(a.z, b.x, a.x, b.z), det2(a.x, b.y, a.y, b.x)};
 }
 
 // Error-free transformations: Knuth's TwoSum (a + b = s + e exactly) and the FMA
-// form of Dekker's product (a * b = p + e exactly).
+// form of Dekker's product (a * b = p + e exactly).  Written with the _rn
+// intrinsics, which the compiler never contracts into FMAs: a contraction of
+// p = a * b into a later sum would break the exactness, and could differ between
+// kernels that inline the same code.
 __device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 __device__ __forceinline__ void two_prod_f(float a, float b, float &p, float &e) {
-    p = a * b;
-    e = fmaf(a, b, -p);
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
 }
 
 // x - y split into a float pair (h, l) with h + l == x - y: exactly for float

@@ -375,7 +375,7 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
 }
 
 template <int NPE, typename AccT, typename S, typename CT, bool FUSED, bool MIXED>
-__global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch(PlanView pv, const S *__restrict__ X,
+__global__ void __launch_bounds__(patch_max_threads(NPE), patch_min_blocks(NPE)) k_patch(PlanView pv, const S *__restrict__ X,
                                                              const CT *__restrict__ c, const AccT *__restrict__ ke,
                                                              AccT *__restrict__ vals, float thr, int64_t p0,
                                                              int64_t p1, PatchSmem L, unsigned fp64_mode) {
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch(PlanView pv, const 
 // Persistent kernel over the patches of many meshes: work item w is patch
 // w - prefix[m] of mesh m, prefix[m] <= w < prefix[m + 1].
 template <int NPE, typename AccT, typename S, typename CT, bool MIXED>
-__global__ void __launch_bounds__(PATCH_MAX_THREADS) k_patch_batched(const BatchItem *__restrict__ items,
+__global__ void __launch_bounds__(patch_max_threads(NPE), patch_min_blocks(NPE)) k_patch_batched(const BatchItem *__restrict__ items,
                                                                      const int64_t *__restrict__ prefix, int n,
                                                                      PatchSmem L, unsigned fp64_mode) {
     const int64_t total = prefix[n];
@@ -510,6 +510,18 @@ static fem_status launch_patch_t(const PatchArgs &a, cudaStream_t s) {
                                      a.thr, 0, np, L, a.fp64_mode);
     FEM_LAUNCHED("k_patch");
     return FEM_OK;
+}
+
+int patch_blocks_per_sm(int npe, int threads) {
+    int n = 0;
+    cudaError_t e = npe == 8
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_patch<8, float, float, float, true, true>, threads, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_patch<4, float, float, float, true, true>, threads, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 2;
+    }
+    return std::max(1, n);
 }
 
 fem_status launch_patch(const PatchArgs &a, cudaStream_t s) {

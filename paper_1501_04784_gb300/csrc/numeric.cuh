@@ -9,6 +9,16 @@ namespace fem {
 
 static constexpr int PATCH_MAX_THREADS = 512;
 
+// Launch bounds of the patch kernels per element type.  Tetrahedra need few
+// registers: capping them at 256 threads and 3 resident blocks per SM (at most
+// 85 registers a thread) lets three blocks share an SM.
+__host__ __device__ constexpr int patch_max_threads(int npe) { return npe == 4 ? 256 : PATCH_MAX_THREADS; }
+__host__ __device__ constexpr int patch_min_blocks(int npe) { return npe == 4 ? 3 : 1; }
+
+// Resident blocks per SM of the mixed patch kernel at `threads` threads as its
+// registers allow (the wave size the plan aligns its patch count to).
+int patch_blocks_per_sm(int npe, int threads);
+
 // byte offsets of the patch kernel's shared-memory arrays
 struct PatchSmem {
     size_t acc, hv, xs, cown, roff, hvf, rps, gid, eid, cvs, total;

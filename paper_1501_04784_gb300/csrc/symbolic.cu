@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "mesh.cuh"
+#include "numeric.cuh"
 
 namespace fem {
 
@@ -907,12 +908,15 @@ fem_status build_plan(fem_mesh m, cudaStream_t s) {
         FEM_TRY(scan_exclusive_i64(len.ptr, pre.ptr, N, true, tmp.ptr, s));
         FEM_CUDA(cudaStreamSynchronize(s));
     }
-    // Whole waves: the patch count is rounded up to a multiple of two blocks per
-    // SM (smaller patches, same cap), so that no block slot idles in the last
-    // wave while others run a patch more.  Below half a wave the mesh keeps its
-    // patches.
+    // Whole waves: the patch count is rounded up to a multiple of the resident
+    // blocks of the patch kernel (smaller patches, same cap), so that no block
+    // slot idles in the last wave while others run a patch more.  Below half a
+    // wave the mesh keeps its patches.
     if (m->nnz > 0) {
-        const int64_t wave = 2 * (int64_t)num_sms(), np0 = cdiv(m->nnz, cap_eff);
+        int threads = m->opt.block_threads > 0 ? m->opt.block_threads : 256;
+        threads = std::min((threads + 31) / 32 * 32, patch_max_threads(m->npe));
+        const int64_t wave = (int64_t)num_sms() * patch_blocks_per_sm(m->npe, threads);
+        const int64_t np0 = cdiv(m->nnz, cap_eff);
         if (np0 * 2 > wave) cap_eff = std::max<int64_t>(1, cdiv(m->nnz, cdiv(np0, wave) * wave));
     }
     P.n_patches = m->nnz > 0 ? cdiv(m->nnz, cap_eff) : 1;
