@@ -90,7 +90,12 @@ typedef struct {
                                     determinant in double-single FP32 arithmetic (accurate to
                                     ~2^-46 of its terms, FP64-grade for the float result);
                                     1 = FP64 arithmetic */
-    int reserved[7];
+    int wait_spins;              /* polls of one device-side wait of the patch kernels before it
+                                    gives up (0 = default 2^20); a wait that gives up is reported
+                                    by fem_sync as FEM_ERR_TIMEOUT */
+    int debug_stall;             /* testing only: 1 = warp 0 of every block waits once for a
+                                    phase that cannot complete, so that the wait gives up */
+    int reserved[5];
 } fem_options;
 
 typedef struct {
@@ -198,7 +203,9 @@ fem_status fem_vjp(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, con
  * Batched build of n meshes (each with its pattern cached) in one persistent
  * launch, replayed from a CUDA graph when the same mesh set is built again.
  * X[i], c[i], vals[i] are host arrays of n device pointers; all meshes share
- * p, x_dtype and c_dtype.
+ * p, x_dtype and c_dtype.  The launch takes its options (thread count, FP64
+ * modes, wait settings) from meshes[0]; a device-side wait that gives up is
+ * reported by fem_sync(meshes[0]).
  */
 fem_status fem_build_K_batched(const fem_mesh *meshes, int n, fem_prec p, const void *const *X,
                                fem_dtype x_dtype, const void *const *c, fem_dtype c_dtype,
@@ -227,7 +234,10 @@ typedef struct {
 fem_status fem_autotune(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c, fem_dtype c_dtype,
                         void *vals, void *stream, fem_tuning *out);
 
-/* Wait for the mesh's work on `stream` and report any asynchronous error. */
+/* Wait for the mesh's work on `stream` and report any asynchronous error:
+ * FEM_ERR_CUDA for a CUDA error, FEM_ERR_TIMEOUT if a bounded device-side wait
+ * of a build gave up since the last fem_sync (the values of that build are
+ * undefined; the context stays usable and the status is cleared). */
 fem_status fem_sync(fem_mesh m, void *stream);
 
 /* Sizes and plan statistics of the mesh (after fem_pattern for the plan fields). */

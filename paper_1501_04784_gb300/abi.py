@@ -25,7 +25,8 @@ class fem_options(ctypes.Structure):
                 ("block_threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("locality_order", ctypes.c_int), ("fp64_sums", ctypes.c_int),
                 ("fp64_fused", ctypes.c_int), ("fp64_dets", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("wait_spins", ctypes.c_int), ("debug_stall", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class fem_info(ctypes.Structure):

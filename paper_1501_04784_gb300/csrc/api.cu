@@ -64,6 +64,26 @@ static fem_status check_inputs(fem_mesh m, fem_prec p, const void *X, fem_dtype 
     return FEM_OK;
 }
 
+namespace fem {
+// Wait settings of the patch kernels for mesh m.
+WaitCtl wait_ctl(fem_mesh m) {
+    return WaitCtl{m->status.ptr, m->opt.wait_spins > 0 ? m->opt.wait_spins : WAIT_SPINS_DEFAULT, m->opt.debug_stall};
+}
+
+// Reads and clears the mesh's device status word (after the stream is synchronised).
+fem_status check_status(fem_mesh m, cudaStream_t s) {
+    int h = 0;
+    FEM_CUDA(cudaMemcpyAsync(&h, m->status.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    if (h == 0) return FEM_OK;
+    FEM_CUDA(cudaMemsetAsync(m->status.ptr, 0, sizeof(int), s));
+    FEM_CUDA(cudaStreamSynchronize(s));
+    set_error("a device-side wait of a patch kernel gave up after %d polls; the values of that build are undefined",
+              m->opt.wait_spins > 0 ? m->opt.wait_spins : WAIT_SPINS_DEFAULT);
+    return FEM_ERR_TIMEOUT;
+}
+}  // namespace fem
+
 extern "C" {
 
 void fem_options_default(fem_options *opt) {
@@ -137,7 +157,12 @@ fem_status fem_mesh_create(fem_mesh *out, fem_elem type, int64_t n_nodes, int64_
     if (m->opt.valence_threshold <= 0) m->opt.valence_threshold = 8;
     m->arena.budget = m->opt.mem_budget_bytes;
     cudaStream_t s = as_stream(stream);
-    fem_status st = validate_connectivity(m, s);
+    fem_status st = m->status.alloc(m->arena, 1, "status word");
+    if (st == FEM_OK) {
+        cudaError_t e = cudaMemsetAsync(m->status.ptr, 0, sizeof(int), s);
+        if (e != cudaSuccess) st = cuda_status(e, "fem_mesh_create");
+    }
+    if (st == FEM_OK) st = validate_connectivity(m, s);
     if (st == FEM_OK) st = build_locality_order(m, X, x_dtype, s);
     if (st == FEM_OK) {
         cudaError_t e = cudaStreamSynchronize(s);
@@ -237,6 +262,7 @@ static PatchArgs patch_args(fem_mesh m, fem_prec p, bool fused) {
     a.threads = (a.threads + 31) / 32 * 32;
     a.blocks_per_sm = m->opt.blocks_per_sm;
     a.fp64_mode = fp64_mode(m->opt);
+    a.wait = wait_ctl(m);
     return a;
 }
 
@@ -339,7 +365,7 @@ fem_status fem_build_K_host(fem_mesh m, fem_prec p, const void *X_host, fem_dtyp
     FEM_TRY(fem_build_K(m, p, base + xo, x_dtype, base + co, c_dtype, base + vo, stream));
     FEM_CUDA(cudaMemcpyAsync(vals_host, base + vo, vb, cudaMemcpyDeviceToHost, s));
     FEM_CUDA(cudaStreamSynchronize(s));
-    return FEM_OK;
+    return check_status(m, s);
 }
 
 fem_status fem_vjp(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c, fem_dtype c_dtype,
@@ -463,12 +489,11 @@ fem_status fem_autotune(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype
 }
 
 fem_status fem_sync(fem_mesh m, void *stream) {
-    (void)m;
     cudaError_t e = cudaStreamSynchronize(as_stream(stream));
     if (e != cudaSuccess) return cuda_status(e, "fem_sync");
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e, "fem_sync");
-    return FEM_OK;
+    return m ? check_status(m, as_stream(stream)) : FEM_OK;
 }
 
 fem_status fem_mesh_info(fem_mesh m, fem_info *info) {

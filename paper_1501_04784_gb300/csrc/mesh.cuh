@@ -139,6 +139,8 @@ struct fem_mesh_s {
     fem::DevBuf<int64_t> inc_ptr;  // node -> incident elements (kept for the backward pass)
     fem::DevBuf<int32_t> inc_elem;
     fem::Plan plan;
+    // device status word: set by a bounded device-side wait that gave up
+    fem::DevBuf<int> status;
     // staging for the _host entry point
     fem::DevBuf<unsigned char> host_stage;
     // FP64 element matrices staged between integration and assembly (the FP64

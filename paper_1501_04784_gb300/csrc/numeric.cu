@@ -168,13 +168,66 @@ __device__ __forceinline__ void scatter_element(const uint32_t (&aw)[NPE * (NPE 
     }
 }
 
+// ------------------------------------------------------------ colour phases
+// The colour phases of a block are ordered by a ring of PHASE_RING mbarriers
+// instead of block-wide barriers.  Phases are numbered g = 0, 1, ... over the
+// block's whole run; every warp arrives once at each phase (barrier g mod
+// PHASE_RING, count = warps).  A warp with elements in phase g first waits for
+// phase g - 1 to complete; as every warp arrives at g - 1 only after its own
+// scatters of that phase and its arrival at g - 2, completion of g - 1 means all
+// scatters of phases < g are done, so each accumulator still receives its
+// contributions in colour order.  A warp with nothing to add in a phase only
+// arrives and may run ahead to integrate its next element, at most PHASE_RING - 1
+// phases ahead (before arriving at g it waits for g - PHASE_RING, the previous
+// use of that barrier).  The warp at the lowest phase waits only on phases every
+// warp has passed, so the waits always end; they are bounded all the same.
+static constexpr int PHASE_RING = 8;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void phase_init(uint64_t *mb) {
+    if (threadIdx.x == 0)
+        for (int k = 0; k < PHASE_RING; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mb + k)), "r"((int)(blockDim.x >> 5))
+                         : "memory");
+    __syncthreads();
+}
+
+// Waits until phase p has completed; after wc.spins polls it records the
+// failure and returns (the kernel then finishes with undefined values).
+__device__ __forceinline__ void phase_wait(uint64_t *mb, uint32_t p, const WaitCtl &wc) {
+    const uint32_t a = smem_u32(mb + (p % PHASE_RING)), parity = (p / PHASE_RING) & 1u;
+    for (int it = 0; it < wc.spins; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred P;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, P;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return;
+    }
+    if ((threadIdx.x & 31) == 0) atomicOr(wc.status, 1);
+}
+
+__device__ __forceinline__ void phase_arrive(uint64_t *mb, uint32_t p) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(mb + (p % PHASE_RING)))
+        : "memory");
+}
+
 // ------------------------------------------------------------------ k_patch
 // One patch: owned rows' accumulators in shared memory, the closure integrated
 // batch by batch and added colour by colour, each owned row written once.
 template <int NPE, typename AccT, typename S, typename CT, bool FUSED, bool MIXED>
 __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restrict__ X, const CT *__restrict__ c,
                                            const AccT *__restrict__ ke, AccT *__restrict__ vals, float thr,
-                                           int64_t p, const PatchSmem &L, unsigned fp64_mode) {
+                                           int64_t p, const PatchSmem &L, unsigned fp64_mode, uint64_t *mb,
+                                           uint32_t &g, const WaitCtl &wc) {
     constexpr int NP = ElemTraits<NPE>::NP;
     const bool fp64_sums = (fp64_mode & FP64_SUMS) != 0, fp64_det = (fp64_mode & FP64_DETS) != 0;
     extern __shared__ __align__(16) unsigned char patch_smem[];
@@ -340,12 +393,20 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
             }
             const int last = min(base + nthr, nel) - 1;
             const int c0 = pv.celem_color[eb + base], c1 = pv.celem_color[eb + last];
-            for (int cc = c0; cc <= c1; ++cc) {
-                if (mycol == cc)
-                    scatter_element<NPE, AccT, MIXED>(aw, roff, hv, fp64_sums, acc, kv);
-                __syncthreads();
+            // testing: phase g cannot complete while warp 0 waits before arriving at it
+            if (wc.stall && base == 0 && warp == 0) phase_wait(mb, g, wc);
+            for (int cc = c0; cc <= c1; ++cc, ++g) {
+                const bool mine = mycol == cc;
+                if (__any_sync(0xffffffffu, mine)) {
+                    if (g > 0) phase_wait(mb, g - 1, wc);
+                    if (mine) scatter_element<NPE, AccT, MIXED>(aw, roff, hv, fp64_sums, acc, kv);
+                    __syncwarp();
+                }
+                if (g >= (uint32_t)PHASE_RING) phase_wait(mb, g - PHASE_RING, wc);
+                if (lane == 0) phase_arrive(mb, g);
             }
         }
+        __syncthreads();  // every phase of the patch done
 
         // each owned row to HBM once: a group of 2^wg_shift lanes (about one row
         // length) stores one row, so a warp writes 32 >> wg_shift rows per step,
@@ -378,9 +439,13 @@ template <int NPE, typename AccT, typename S, typename CT, bool FUSED, bool MIXE
 __global__ void __launch_bounds__(patch_max_threads(NPE), patch_min_blocks(NPE)) k_patch(PlanView pv, const S *__restrict__ X,
                                                              const CT *__restrict__ c, const AccT *__restrict__ ke,
                                                              AccT *__restrict__ vals, float thr, int64_t p0,
-                                                             int64_t p1, PatchSmem L, unsigned fp64_mode) {
+                                                             int64_t p1, PatchSmem L, unsigned fp64_mode,
+                                                             WaitCtl wc) {
+    __shared__ uint64_t mb[PHASE_RING];
+    phase_init(mb);
+    uint32_t g = 0;
     for (int64_t p = p0 + blockIdx.x; p < p1; p += gridDim.x)
-        patch_body<NPE, AccT, S, CT, FUSED, MIXED>(pv, X, c, ke, vals, thr, p, L, fp64_mode);
+        patch_body<NPE, AccT, S, CT, FUSED, MIXED>(pv, X, c, ke, vals, thr, p, L, fp64_mode, mb, g, wc);
 }
 
 // Persistent kernel over the patches of many meshes: work item w is patch
@@ -388,8 +453,12 @@ __global__ void __launch_bounds__(patch_max_threads(NPE), patch_min_blocks(NPE))
 template <int NPE, typename AccT, typename S, typename CT, bool MIXED>
 __global__ void __launch_bounds__(patch_max_threads(NPE), patch_min_blocks(NPE)) k_patch_batched(const BatchItem *__restrict__ items,
                                                                      const int64_t *__restrict__ prefix, int n,
-                                                                     PatchSmem L, unsigned fp64_mode) {
+                                                                     PatchSmem L, unsigned fp64_mode,
+                                                                     WaitCtl wc) {
     const int64_t total = prefix[n];
+    __shared__ uint64_t mb[PHASE_RING];
+    phase_init(mb);
+    uint32_t g = 0;
     for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
         int lo = 0, hi = n;
         while (hi - lo > 1) {
@@ -398,7 +467,7 @@ __global__ void __launch_bounds__(patch_max_threads(NPE), patch_min_blocks(NPE))
         }
         const BatchItem &it = items[lo];
         patch_body<NPE, AccT, S, CT, true, MIXED>(it.pv, (const S *)it.X, (const CT *)it.c, nullptr,
-                                                   (AccT *)it.vals, it.thr, w - prefix[lo], L, fp64_mode);
+                                                   (AccT *)it.vals, it.thr, w - prefix[lo], L, fp64_mode, mb, g, wc);
     }
 }
 
@@ -507,7 +576,7 @@ static fem_status launch_patch_t(const PatchArgs &a, cudaStream_t s) {
     if (np <= 0) return FEM_OK;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np, (int64_t)num_sms() * per_sm));
     f<<<grid, threads, L.total, s>>>(P.view(cl), (const S *)a.X, (const CT *)a.c, (const AccT *)a.ke, (AccT *)a.vals,
-                                     a.thr, 0, np, L, a.fp64_mode);
+                                     a.thr, 0, np, L, a.fp64_mode, a.wait);
     FEM_LAUNCHED("k_patch");
     return FEM_OK;
 }
@@ -589,7 +658,7 @@ fem_status batched_config(int npe, bool mixed, const PlanMax &pm, int threads, i
 fem_status launch_batched_kernel(const BatchLaunch &bl, cudaStream_t s) {
 #define FEM_B(NPE, T, MX)                                                                                   \
     k_patch_batched<NPE, T, T, T, MX><<<bl.grid, bl.threads, bl.L.total, s>>>(bl.items, bl.prefix, bl.n, bl.L, \
-                                                                               bl.fp64_mode)
+                                                                               bl.fp64_mode, bl.wait)
     if (bl.mixed) {
         if (bl.npe == 8) FEM_B(8, float, true); else FEM_B(4, float, true);
     } else {

@@ -29,6 +29,18 @@ struct PatchSmem {
 // Bits of the FP64 mode of the mixed kernels (fem_options.fp64_sums, fp64_dets).
 static constexpr unsigned FP64_SUMS = 1u, FP64_DETS = 2u;
 
+// Device-side waits of the patch kernels (colour phases on mbarriers): each wait
+// polls at most `spins` times, then records the failure in *status (read by
+// fem_sync as FEM_ERR_TIMEOUT) and lets the thread go on, so the kernel ends.
+// `stall` (testing) makes warp 0 of every block wait once for a phase that
+// cannot complete, to exercise that path.
+struct WaitCtl {
+    int *status;
+    int spins;
+    int stall;
+};
+static constexpr int WAIT_SPINS_DEFAULT = 1 << 20;
+
 struct IntegrateArgs {
     int npe;
     bool mixed;
@@ -53,6 +65,7 @@ struct PatchArgs {
     float thr;
     int64_t p0, p1;
     int threads, blocks_per_sm;
+    WaitCtl wait;
     unsigned fp64_mode;  // FP64_SUMS: high-valence sums with FP64 adds instead of FP32 TwoSum pairs;
                          // FP64_DETS: distorted tetrahedra's determinant in FP64 arithmetic
 };
@@ -87,6 +100,7 @@ struct BatchLaunch {
     int n = 0;
     PatchSmem L{};
     int threads = 256, grid = 1;
+    WaitCtl wait{nullptr, WAIT_SPINS_DEFAULT, 0};
 };
 
 // Shared memory, residency and grid of the batched kernel for `threads` threads
@@ -95,6 +109,9 @@ fem_status batched_config(int npe, bool mixed, const PlanMax &pm, int threads, i
 fem_status launch_batched_kernel(const BatchLaunch &bl, cudaStream_t s);
 
 fem_status launch_integrate(const IntegrateArgs &a, cudaStream_t s);
+
+WaitCtl wait_ctl(fem_mesh m);
+fem_status check_status(fem_mesh m, cudaStream_t s);
 
 inline unsigned fp64_mode(const fem_options &o) {
     return (o.fp64_sums ? FP64_SUMS : 0u) | (o.fp64_dets ? FP64_DETS : 0u);

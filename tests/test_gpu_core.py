@@ -230,6 +230,27 @@ def test_distorted_tet_determinant_modes(fem, fp64_dets):
     assert rel_err(vals, refK["vals"], refK["cs"]) <= TOL_MIXED
 
 
+def test_device_wait_timeout_is_reported(fem):
+    """Failure detection without a fault: with debug_stall, warp 0 of every block
+    waits (at most wait_spins polls) for a colour phase that cannot complete.
+    The wait gives up, the kernel still finishes, fem_sync reports
+    FEM_ERR_TIMEOUT once, and the context stays usable: a later build is
+    correct."""
+    from paper_1501_04784_gb300 import abi
+    m = MESHES["hex_7x5x3"]()
+    Xd, cd, X, c = inputs(m, "mixed")
+    stalled = make(fem, m, debug_stall=1, wait_spins=64)
+    stalled.build_K(Xd, cd, "mixed")
+    with pytest.raises(abi.FemError, match="FEM_ERR_TIMEOUT"):
+        stalled.sync()
+    stalled.sync()   # the status word was cleared
+    ok = make(fem, m)
+    vals = ok.build_K(Xd, cd, "mixed")
+    ok.sync()
+    ref = oracle_K(m, X, c)
+    assert rel_err(vals.cpu().numpy(), ref["vals"], ref["cs"]) <= TOL_MIXED
+
+
 @pytest.mark.parametrize("fp64_sums", [0, 1])
 def test_high_valence_summation_modes(fem, fp64_sums):
     """Tet diagonals (up to 24 contributions) are summed FP64-accurately either by
