@@ -293,7 +293,8 @@ def run_ours(args):
     alg = algorithmic_bytes(m.n_nodes, m.n_elems, 8, nnz, 4, 4, 4)
     alg64 = algorithmic_bytes(m.n_nodes, m.n_elems, 8, nnz, 8, 8, 8)
     achieved = alg / (ms_step / 1e3) / 1e9
-    wkey = f"hex8_n{args.n}_mixed"
+    # the profiled DRAM traffic of the same kernel sources, workload and patch size
+    wkey = f"hex8_n{args.n}_mixed_p{(tuning or {}).get('patch_entries', 0)}"
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     alu_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12          # TFLOP/s at the sampled clock
     alu_achieved = BRICK_FLOPS * m.n_elems / (ms_step / 1e3) / 1e12
