@@ -336,13 +336,17 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
             c_n1 = e0 >= 0 ? __ldg(c + e0) : CT(0);
             eid_n2 = tid + nthr < nel ? pv.celem_id[eb + tid + nthr] : -1;
         }
-        // tets (short integration): closure-local node indices and colours of the
-        // next batch are loaded one batch ahead as well; bricks load them in place
+        // tets (short integration): closure-local node indices, colours and
+        // accumulator targets of the next batch are loaded one batch ahead as well;
+        // bricks load them in place
         uint16_t ln_n[NPE];
+        uint32_t aw_n[NP / 2];
         int col_n = -1;
         if (NPE == 4 && tid < nel) {
             load_lnodes<NPE>(pv.celem_lnode, eb + tid, ln_n);
             col_n = pv.celem_color[eb + tid];
+#pragma unroll
+            for (int w = 0; w < NP / 2; ++w) aw_n[w] = __ldg(pv.celem_aidx + w * pv.aidx_n + eb + tid);
         }
         for (int base = 0; base < nel; base += nthr) {
             const int i = base + tid;
@@ -355,10 +359,14 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
             if constexpr (NPE == 4) {
 #pragma unroll
                 for (int a = 0; a < NPE; ++a) ln[a] = ln_n[a];
+#pragma unroll
+                for (int w = 0; w < NP / 2; ++w) aw[w] = aw_n[w];
                 if (act) mycol = col_n;
                 if (i + nthr < nel) {
                     load_lnodes<NPE>(pv.celem_lnode, ci + nthr, ln_n);
                     col_n = pv.celem_color[ci + nthr];
+#pragma unroll
+                    for (int w = 0; w < NP / 2; ++w) aw_n[w] = __ldg(pv.celem_aidx + w * pv.aidx_n + ci + nthr);
                 }
             } else if (act) {
                 load_lnodes<NPE>(pv.celem_lnode, ci, ln);
@@ -386,10 +394,13 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
 #pragma unroll
                     for (int q = 0; q < NP; ++q) kv[q] = __ldg(ke + e * NP + q);
                 }
-                // accumulator targets before the colour phases, so that no phase
-                // waits on its own global load (one exposed latency per batch)
+                // bricks: accumulator targets after the integration, before the colour
+                // phases, so that no phase waits on its own load (tets take them a
+                // batch ahead, above)
+                if constexpr (NPE == 8) {
 #pragma unroll
-                for (int w = 0; w < NP / 2; ++w) aw[w] = __ldg(pv.celem_aidx + w * pv.aidx_n + ci);
+                    for (int w = 0; w < NP / 2; ++w) aw[w] = __ldg(pv.celem_aidx + w * pv.aidx_n + ci);
+                }
             }
             const int last = min(base + nthr, nel) - 1;
             const int c0 = pv.celem_color[eb + base], c1 = pv.celem_color[eb + last];
