@@ -44,11 +44,11 @@ def lib():
     if _lib is None:
         build()
         L = ctypes.CDLL(_LIB_PATH)
-        L.oracle_ke_dense.argtypes = [_int, _p, ctypes.c_double, _p]
+        L.oracle_ke_dense.argtypes = [_int, _int, _p, ctypes.c_double, _p]
         L.oracle_ke_dense.restype = _int
-        L.oracle_ke_packed.argtypes = [_int, _i64, _p, _p, _p, _p, _p]
+        L.oracle_ke_packed.argtypes = [_int, _int, _i64, _p, _p, _p, _p, _p]
         L.oracle_ke_packed.restype = _i64
-        L.oracle_triplets.argtypes = [_int, _i64, _p, _p, _p, _p, _p, _p, _p]
+        L.oracle_triplets.argtypes = [_int, _int, _i64, _p, _p, _p, _p, _p, _p, _p]
         L.oracle_triplets.restype = _i64
         L.oracle_compress.argtypes = [_i64, _i64, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]
         L.oracle_compress.restype = _i64
@@ -73,26 +73,30 @@ def npairs(npe: int) -> int:
     return npe * (npe + 1) // 2
 
 
-def ke_dense(npe: int, xe, c: float) -> np.ndarray:
+# Operators: the stiffness matrix of Eq. 9 and the mass matrix (Section 5).
+OPS = {"stiffness": 0, "mass": 1}
+
+
+def ke_dense(npe: int, xe, c: float, op: str = "stiffness") -> np.ndarray:
     """Full npe x npe element matrix of one element with node coordinates xe [npe, 3]."""
     xe = np.ascontiguousarray(xe, dtype=np.float64).reshape(npe, 3)
     ke = np.zeros((npe, npe))
-    lib().oracle_ke_dense(npe, _ptr(xe), float(c), _ptr(ke))
+    lib().oracle_ke_dense(OPS[op], npe, _ptr(xe), float(c), _ptr(ke))
     return ke
 
 
-def ke_packed(npe: int, X, E, c):
+def ke_packed(npe: int, X, E, c, op: str = "stiffness"):
     """Packed lower k_e [n_elems, npe(npe+1)/2] (p = a(a+1)/2 + b), the Cauchy-Schwarz
     scales sqrt(k_aa k_bb) of each entry, and the number of elements with det J <= 0."""
     X, E, c = _inputs(X, E, c)
     n = E.shape[0]
     ke = np.zeros((n, npairs(npe)))
     cs = np.zeros((n, npairs(npe)))
-    bad = lib().oracle_ke_packed(npe, n, _ptr(E), _ptr(X), _ptr(c), _ptr(ke), _ptr(cs))
+    bad = lib().oracle_ke_packed(OPS[op], npe, n, _ptr(E), _ptr(X), _ptr(c), _ptr(ke), _ptr(cs))
     return ke, cs, int(bad)
 
 
-def triplets(npe: int, X, E, c):
+def triplets(npe: int, X, E, c, op: str = "stiffness"):
     """Algorithm 1's triplet arrays (rows, cols, vals) plus per-triplet scales."""
     X, E, c = _inputs(X, E, c)
     nt = E.shape[0] * npairs(npe)
@@ -100,7 +104,7 @@ def triplets(npe: int, X, E, c):
     cols = np.zeros(nt, np.int32)
     vals = np.zeros(nt)
     cs = np.zeros(nt)
-    bad = lib().oracle_triplets(npe, E.shape[0], _ptr(E), _ptr(X), _ptr(c), _ptr(rows),
+    bad = lib().oracle_triplets(OPS[op], npe, E.shape[0], _ptr(E), _ptr(X), _ptr(c), _ptr(rows),
                                 _ptr(cols), _ptr(vals), _ptr(cs))
     return rows, cols, vals, cs, int(bad)
 
@@ -121,14 +125,14 @@ def compress(n_nodes: int, rows, cols, vals, cs):
                 cs=sc[:nnz].copy(), slot=slot[:nt].copy(), nnz=int(nnz))
 
 
-def build_K(npe: int, X, E, c):
-    """Algorithm 1 end to end: global lower-triangular CSR K in FP64.
+def build_K(npe: int, X, E, c, op: str = "stiffness"):
+    """Algorithm 1 end to end: global lower-triangular CSR K (or M, op="mass") in FP64.
 
     Returns a dict with rowptr, col, vals, abs (sum of |contribution|), cs (sum of
     Cauchy-Schwarz scales), slot (CSR position of each packed (e, p)), nnz, and
     n_bad (elements with a non-positive Jacobian determinant)."""
     X, E, c = _inputs(X, E, c)
-    rows, cols, vals, cs, bad = triplets(npe, X, E, c)
+    rows, cols, vals, cs, bad = triplets(npe, X, E, c, op)
     out = compress(X.shape[0], rows, cols, vals, cs)
     out["n_bad"] = bad
     return out

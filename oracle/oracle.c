@@ -147,14 +147,77 @@ static double re_z(double complex x) { return creal(x); }
 DEFINE_ELEMENT_ROUTINES(d, double, re_d)
 DEFINE_ELEMENT_ROUTINES(z, double complex, re_z)
 
-static int element_dense(int npe, const double *xe, double c, double *ke) {
+/*
+ * The mass matrix of the same elements, M_ab = integral c N_a N_b dOmega: the
+ * other operator the paper says its construction generalises to (Section 5,
+ * Conclusions).  The brick uses the same 2x2x2 Gauss rule and the same |det J|
+ * of Eq. 8 as k_e; the tetrahedron the 4-point rule that is exact for
+ * quadratics (barycentric points (a, b, b, b) and its permutations,
+ * a = (5 + 3 sqrt 5) / 20, b = (5 - sqrt 5) / 20, each weighted by a quarter of
+ * the volume).  Returns the number of points with det J <= 0.
+ */
+static int me_brick(const double xe[24], double c, double me[64]) {
+    const double g = 1.0 / sqrt(3.0);
+    const double pts[2] = {-g, g};
+    int nonpos = 0;
+    for (int i = 0; i < 64; ++i) me[i] = 0;
+    for (int ir = 0; ir < 2; ++ir)
+        for (int is = 0; is < 2; ++is)
+            for (int it = 0; it < 2; ++it) {
+                const double r = pts[ir], s = pts[is], t = pts[it];
+                double N[8], dN[3][8];
+                for (int a = 0; a < 8; ++a) {
+                    const double ra = BRICK_NODES[a][0], sa = BRICK_NODES[a][1], ta = BRICK_NODES[a][2];
+                    N[a] = 0.125 * (1 + r * ra) * (1 + s * sa) * (1 + t * ta);
+                    dN[0][a] = 0.125 * ra * (1 + s * sa) * (1 + t * ta);
+                    dN[1][a] = 0.125 * sa * (1 + r * ra) * (1 + t * ta);
+                    dN[2][a] = 0.125 * ta * (1 + r * ra) * (1 + s * sa);
+                }
+                double J[3][3];
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) {
+                        double acc = 0;
+                        for (int a = 0; a < 8; ++a) acc += dN[i][a] * xe[3 * a + j];
+                        J[i][j] = acc;
+                    }
+                double det, inv[3][3];
+                inv3_d(J, &det, inv);
+                if (det <= 0) ++nonpos;
+                const double absdet = fabs(det);
+                for (int a = 0; a < 8; ++a)
+                    for (int b = 0; b < 8; ++b) me[8 * a + b] += c * absdet * N[a] * N[b];
+            }
+    return nonpos;
+}
+
+static int me_tet(const double xe[12], double c, double me[16]) {
+    double J[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) J[i][j] = xe[3 * (i + 1) + j] - xe[j];
+    double det, inv[3][3];
+    inv3_d(J, &det, inv);
+    const double vol = fabs(det) / 6.0;
+    const double qa = (5.0 + 3.0 * sqrt(5.0)) / 20.0, qb = (5.0 - sqrt(5.0)) / 20.0;
+    for (int i = 0; i < 16; ++i) me[i] = 0;
+    for (int q = 0; q < 4; ++q) {
+        double lam[4];
+        for (int a = 0; a < 4; ++a) lam[a] = a == q ? qa : qb;
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) me[4 * a + b] += c * (vol / 4.0) * lam[a] * lam[b];
+    }
+    return det <= 0 ? 1 : 0;
+}
+
+/* Operators: 0 = stiffness k_e (Eq. 9), 1 = mass m_e. */
+static int element_dense(int op, int npe, const double *xe, double c, double *ke) {
+    if (op == 1) return npe == 8 ? me_brick(xe, c, ke) : me_tet(xe, c, ke);
     return npe == 8 ? ke_brick_d(xe, c, ke) : ke_tet_d(xe, c, ke);
 }
 
 /* Full dense element matrix of one element (row-major npe x npe). */
-int oracle_ke_dense(int npe, const double *xe, double c, double *ke) {
-    if (npe != 8 && npe != 4) return -1;
-    return element_dense(npe, xe, c, ke);
+int oracle_ke_dense(int op, int npe, const double *xe, double c, double *ke) {
+    if ((npe != 8 && npe != 4) || (op != 0 && op != 1)) return -1;
+    return element_dense(op, npe, xe, c, ke);
 }
 
 static void gather(int npe, const int32_t *E, const double *X, int64_t e, double *xe) {
@@ -167,19 +230,20 @@ static void gather(int npe, const int32_t *E, const double *X, int64_t e, double
 }
 
 /*
- * Packed lower triangle of every element matrix: entry p = a(a+1)/2 + b for
- * b <= a (row-major lower order).  cs[p] = sqrt(k_aa k_bb), the Cauchy-Schwarz
- * bound of |k_ab| for the positive semidefinite k_e, used to scale errors.
+ * Packed lower triangle of every element matrix of operator op: entry
+ * p = a(a+1)/2 + b for b <= a (row-major lower order).  cs[p] = sqrt(k_aa k_bb),
+ * the Cauchy-Schwarz bound of |k_ab| for the positive semidefinite k_e (or m_e),
+ * used to scale errors.
  * Returns the number of elements with some det J <= 0.
  */
-int64_t oracle_ke_packed(int npe, int64_t n_elems, const int32_t *E, const double *X,
+int64_t oracle_ke_packed(int op, int npe, int64_t n_elems, const int32_t *E, const double *X,
                          const double *c, double *ke_out, double *cs_out) {
     const int np = npe * (npe + 1) / 2;
     int64_t bad = 0;
     double xe[24], ke[64];
     for (int64_t e = 0; e < n_elems; ++e) {
         gather(npe, E, X, e, xe);
-        if (element_dense(npe, xe, c[e], ke) > 0) ++bad;
+        if (element_dense(op, npe, xe, c[e], ke) > 0) ++bad;
         for (int a = 0; a < npe; ++a)
             for (int b = 0; b <= a; ++b) {
                 const int p = a * (a + 1) / 2 + b;
@@ -196,14 +260,14 @@ int64_t oracle_ke_packed(int npe, int64_t n_elems, const int32_t *E, const doubl
  * (max(g_a, g_b), min(g_a, g_b)) with value k_e[a][b] (k_e is symmetric).
  * rows/cols/vals/cs have room for n_elems * npe(npe+1)/2 entries.
  */
-int64_t oracle_triplets(int npe, int64_t n_elems, const int32_t *E, const double *X,
+int64_t oracle_triplets(int op, int npe, int64_t n_elems, const int32_t *E, const double *X,
                         const double *c, int64_t *rows, int32_t *cols, double *vals, double *cs) {
     const int np = npe * (npe + 1) / 2;
     int64_t bad = 0;
     double xe[24], ke[64];
     for (int64_t e = 0; e < n_elems; ++e) {
         gather(npe, E, X, e, xe);
-        if (element_dense(npe, xe, c[e], ke) > 0) ++bad;
+        if (element_dense(op, npe, xe, c[e], ke) > 0) ++bad;
         for (int a = 0; a < npe; ++a)
             for (int b = 0; b <= a; ++b) {
                 const int64_t t = e * np + a * (a + 1) / 2 + b;
@@ -291,7 +355,7 @@ void oracle_vjp(int npe, int64_t n_elems, const int32_t *E, const double *X, con
     double complex xz[24], kz[64];
     for (int64_t e = 0; e < n_elems; ++e) {
         gather(npe, E, X, e, xe);
-        element_dense(npe, xe, 1.0, ke);
+        element_dense(0, npe, xe, 1.0, ke);
         double l1 = 0.0;
         for (int a = 0; a < npe; ++a)
             for (int b = 0; b <= a; ++b) l1 += S[e * np + a * (a + 1) / 2 + b] * ke[npe * a + b];

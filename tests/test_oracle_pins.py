@@ -345,12 +345,12 @@ def test_planted_mistakes_are_caught(tmp_path, name):
     so = tmp_path / "libmut.so"
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", str(so), str(path), "-lm"])
     L = ctypes.CDLL(str(so))
-    L.oracle_ke_dense.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
+    L.oracle_ke_dense.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
 
     def ke_dense(npe, xe, c):
         xe = np.ascontiguousarray(xe, dtype=np.float64)
         ke = np.zeros((npe, npe))
-        L.oracle_ke_dense(npe, xe.ctypes.data_as(ctypes.c_void_p), float(c), ke.ctypes.data_as(ctypes.c_void_p))
+        L.oracle_ke_dense(0, npe, xe.ctypes.data_as(ctypes.c_void_p), float(c), ke.ctypes.data_as(ctypes.c_void_p))
         return ke
 
     res = run_pins(ke_dense)
