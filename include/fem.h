@@ -95,7 +95,12 @@ typedef struct {
                                     by fem_sync as FEM_ERR_TIMEOUT */
     int debug_stall;             /* testing only: 1 = warp 0 of every block waits once for a
                                     phase that cannot complete, so that the wait gives up */
-    int reserved[5];
+    int operator_kind;           /* 0 (default) = stiffness matrix k_e = c int B^T B (Eq. 9);
+                                    1 = mass matrix m_e = c int N^T N (the other operator the
+                                    paper's construction generalises to, Section 5): same
+                                    quadrature, packing, pattern and assembly; fem_vjp is for
+                                    the stiffness operator only */
+    int reserved[4];
 } fem_options;
 
 typedef struct {

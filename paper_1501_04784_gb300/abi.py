@@ -26,7 +26,7 @@ class fem_options(ctypes.Structure):
                 ("locality_order", ctypes.c_int), ("fp64_sums", ctypes.c_int),
                 ("fp64_fused", ctypes.c_int), ("fp64_dets", ctypes.c_int),
                 ("wait_spins", ctypes.c_int), ("debug_stall", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("operator_kind", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class fem_info(ctypes.Structure):

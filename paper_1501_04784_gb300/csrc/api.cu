@@ -155,6 +155,11 @@ fem_status fem_mesh_create(fem_mesh *out, fem_elem type, int64_t n_nodes, int64_
     m->E = E;
     if (opt) m->opt = *opt; else fem_options_default(&m->opt);
     if (m->opt.valence_threshold <= 0) m->opt.valence_threshold = 8;
+    if (m->opt.operator_kind != 0 && m->opt.operator_kind != 1) {
+        delete m;
+        set_error("operator_kind must be 0 (stiffness) or 1 (mass)");
+        return FEM_ERR_ARG;
+    }
     m->arena.budget = m->opt.mem_budget_bytes;
     cudaStream_t s = as_stream(stream);
     fem_status st = m->status.alloc(m->arena, 1, "status word");
@@ -243,7 +248,7 @@ fem_status fem_integrate_local(fem_mesh m, fem_prec p, const void *X, fem_dtype 
         return FEM_ERR_ARG;
     }
     IntegrateArgs a{m->npe, p == FEM_MIXED, x_dtype, c_dtype, m->E, m->n_elems, X, c, ke_out,
-                    default_threshold(m), nullptr, m->opt.fp64_dets != 0};
+                    default_threshold(m), nullptr, kernel_mode(m->opt)};
     return launch_integrate(a, as_stream(stream));
 }
 
@@ -261,7 +266,7 @@ static PatchArgs patch_args(fem_mesh m, fem_prec p, bool fused) {
     if (a.threads > patch_max_threads(m->npe)) a.threads = patch_max_threads(m->npe);
     a.threads = (a.threads + 31) / 32 * 32;
     a.blocks_per_sm = m->opt.blocks_per_sm;
-    a.fp64_mode = fp64_mode(m->opt);
+    a.mode = kernel_mode(m->opt);
     a.wait = wait_ctl(m);
     return a;
 }
@@ -315,7 +320,7 @@ fem_status fem_build_K(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype,
         fem_status st = m->ke64.n >= n ? FEM_OK : m->ke64.alloc(m->arena, n, "FP64 element matrices");
         if (st == FEM_OK) {
             IntegrateArgs ia{m->npe, false, x_dtype, c_dtype, m->E, m->n_elems, X, c, m->ke64.ptr,
-                             default_threshold(m), nullptr};
+                             default_threshold(m), nullptr, kernel_mode(m->opt)};
             FEM_TRY(launch_integrate(ia, s));
             PatchArgs a = patch_args(m, p, false);
             a.xd = FEM_F64;
@@ -379,6 +384,10 @@ fem_status fem_vjp(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, con
     if (!G || !dX || !dc || !aligned(G, w) || !aligned(dX, w) || !aligned(dc, w)) {
         set_error("G, dX and dc must be non-null aligned device pointers");
         return FEM_ERR_ARG;
+    }
+    if (m->opt.operator_kind != 0) {
+        set_error("the backward pass covers the stiffness operator only");
+        return FEM_ERR_UNSUPPORTED;
     }
     return launch_vjp(m, p == FEM_MIXED, X, x_dtype, c, c_dtype, G, dX, dc, as_stream(stream));
 }

@@ -109,7 +109,7 @@ static fem_status create_ctx(BatchCtx &c, const void *const *X, const void *cons
         bl.items = c.d_items;
         bl.prefix = c.d_prefix;
         bl.n = n;
-        bl.fp64_mode = fp64_mode(c.meshes[0]->opt);
+        bl.mode = kernel_mode(c.meshes[0]->opt);
         bl.wait = wait_ctl(c.meshes[0]);
         if (batched_config(c.npe, c.mixed, pm, cd.first, cd.second, &bl) != FEM_OK) continue;
         FEM_TRY(launch_batched_kernel(bl, s));  // warm-up

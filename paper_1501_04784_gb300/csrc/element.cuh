@@ -395,6 +395,80 @@ __device__ __forceinline__ bool brick_ke_mixed(const S (*xc)[3], float c, float 
     return flagged;
 }
 
+// ----------------------------------------------------------- brick mass matrix
+// M_ab = c integral N_a N_b (the mass operator of Section 5's generalisation) by
+// the same 2x2x2 rule: M_ab = c sum_q |det J_q| N_a(q) N_b(q).  N_a(q) is a product
+// of 1D hats, so the sum factorises like the stiffness matrix: with
+// D[q1][q2][q3] = |det J_q| and V = D contracted with the hat products F_c on every
+// axis, M_ab = c V[cls(a1,b1)][cls(a2,b2)][cls(a3,b3)].  det(2 J_q) = 8 det J_q.
+template <typename T>
+__device__ __forceinline__ void brick_dets(const Vec3<T> (&row)[3][2][2], T (&det)[8]) {
+#pragma unroll
+    for (int q1 = 0; q1 < 2; ++q1)
+#pragma unroll
+        for (int q2 = 0; q2 < 2; ++q2)
+#pragma unroll
+            for (int q3 = 0; q3 < 2; ++q3)
+                det[4 * q1 + 2 * q2 + q3] = dot3(row[0][q2][q3], cross3(row[1][q1][q3], row[2][q1][q2]));
+}
+
+template <typename T>
+__device__ __forceinline__ void brick_mass_from_dets(const T (&det)[8], T c, T (&m)[36]) {
+    T D[2][2][2];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) D[q >> 2][(q >> 1) & 1][q & 1] = det[q] < T(0) ? -det[q] : det[q];
+    T V[3][3][3];
+    contract_cross<T, 1, 1, 1>(D, V);
+    const T s = c * T(0.125);
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b <= a; ++b)
+            m[a * (a + 1) / 2 + b] = s * V[hcls(hb1(a), hb1(b))][hcls(hb2(a), hb2(b))][hcls(hb3(a), hb3(b))];
+}
+
+template <typename T, typename S>
+__device__ __forceinline__ void brick_me(const S (*xc)[3], T c, T (&m)[36]) {
+    Vec3<T> e[3][2][2];
+    brick_edges<T, S>(xc, e);
+    Vec3<T> row[3][2][2];
+    brick_jrows(e, row);
+    T det[8];
+    brick_dets(row, det);
+    brick_mass_from_dets(det, c, m);
+}
+
+// Mixed precision: FP32, except that an element whose max_q det J / min_q det J
+// exceeds `thr` (or with a det J <= 0) takes its determinants from FP64.
+template <typename S>
+__device__ __forceinline__ bool brick_me_mixed(const S (*xc)[3], float c, float thr, float (&m)[36]) {
+    Vec3<float> e[3][2][2];
+    brick_edges<float, S>(xc, e);
+    Vec3<float> row[3][2][2];
+    brick_jrows(e, row);
+    float det[8];
+    brick_dets(row, det);
+    float dmin = det[0], dmax = det[0];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) {
+        dmin = fminf(dmin, det[q]);
+        dmax = fmaxf(dmax, det[q]);
+    }
+    const bool flagged = !(dmin > 0.f) || dmax > thr * dmin;
+    if (flagged) {
+        Vec3<double> ed[3][2][2];
+        brick_edges<double, S>(xc, ed);
+        Vec3<double> rowd[3][2][2];
+        brick_jrows(ed, rowd);
+        double detd[8];
+        brick_dets(rowd, detd);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) det[q] = (float)detd[q];
+    }
+    brick_mass_from_dets(det, c, m);
+    return flagged;
+}
+
 // ---------------------------------------------------------------- tetrahedron
 // Rows of J are the edge vectors x_i - x_0 (i = 1..3).  The gradient of the
 // barycentric function lambda_a is F_a / det J, where F_a is twice the area
@@ -455,11 +529,10 @@ __device__ __forceinline__ void tet_ke(const S (*xc)[3], T c, T (&k)[10]) {
 // FP64 arithmetic when fp64_det is set -- and rounded once.  Returns true when
 // the accurate path was taken.
 template <typename S>
-__device__ __forceinline__ bool tet_ke_mixed(const S (*xc)[3], float c, float thr, bool fp64_det, float (&k)[10]) {
+__device__ __forceinline__ bool tet_geometry_mixed(const S (*xc)[3], float thr, bool fp64_det, Vec3<float> (&F)[4],
+                                                   float &det) {
     TetGeom<float> g;
     tet_geom<float, S>(xc, g);
-    Vec3<float> F[4];
-    float det;
     tet_faces(g, F, det);
     const Vec3<float> E5 = {g.R2.x - g.R1.x, g.R2.y - g.R1.y, g.R2.z - g.R1.z};
     const float L2 = fmaxf(fmaxf(fmaxf(dot3(g.R0, g.R0), dot3(g.R1, g.R1)), fmaxf(dot3(g.R2, g.R2), dot3(g.D1, g.D1))),
@@ -491,7 +564,46 @@ __device__ __forceinline__ bool tet_ke_mixed(const S (*xc)[3], float c, float th
             det = det3_ds<S>(xc);
         }
     }
+    return flagged;
+}
+
+template <typename S>
+__device__ __forceinline__ bool tet_ke_mixed(const S (*xc)[3], float c, float thr, bool fp64_det, float (&k)[10]) {
+    Vec3<float> F[4];
+    float det;
+    const bool flagged = tet_geometry_mixed<S>(xc, thr, fp64_det, F, det);
     tet_from_faces(F, det, c, k);
+    return flagged;
+}
+
+// ------------------------------------------------------------ tet mass matrix
+// M_ab = c integral lambda_a lambda_b = c |T| (1 + delta_ab) / 20, |T| = |det J| / 6.
+template <typename T>
+__device__ __forceinline__ void tet_mass_from_det(T det, T c, T (&m)[10]) {
+    const T s = c * (det < T(0) ? -det : det) * T(1.0 / 120.0);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b <= a; ++b) m[a * (a + 1) / 2 + b] = a == b ? s + s : s;
+}
+
+template <typename T, typename S>
+__device__ __forceinline__ void tet_me(const S (*xc)[3], T c, T (&m)[10]) {
+    TetGeom<T> g;
+    tet_geom<T, S>(xc, g);
+    Vec3<T> F[4];
+    T det;
+    tet_faces(g, F, det);
+    tet_mass_from_det(det, c, m);
+}
+
+// Mixed precision: the same indicator and FP64-accurate determinant as k_e.
+template <typename S>
+__device__ __forceinline__ bool tet_me_mixed(const S (*xc)[3], float c, float thr, bool fp64_det, float (&m)[10]) {
+    Vec3<float> F[4];
+    float det;
+    const bool flagged = tet_geometry_mixed<S>(xc, thr, fp64_det, F, det);
+    tet_mass_from_det(det, c, m);
     return flagged;
 }
 

@@ -55,8 +55,19 @@ __device__ __forceinline__ void load_lnodes(const uint16_t *__restrict__ L, int6
 // Element matrix in the arithmetic of the precision mode.  FP64: everything in
 // double.  MIXED: float, FP64 Jacobians for distorted elements.
 template <int NPE, typename AccT, typename S, bool MIXED, typename CT>
-__device__ __forceinline__ bool element_matrix(const S (*xc)[3], CT ce, float thr, bool fp64_det,
+__device__ __forceinline__ bool element_matrix(const S (*xc)[3], CT ce, float thr, unsigned mode,
                                                AccT (&k)[ElemTraits<NPE>::NP]) {
+    const bool fp64_det = (mode & FP64_DETS) != 0;
+    if (mode & OP_MASS) {
+        if constexpr (MIXED) {
+            if constexpr (NPE == 8) return brick_me_mixed<S>(xc, static_cast<float>(ce), thr, k);
+            else return tet_me_mixed<S>(xc, static_cast<float>(ce), thr, fp64_det, k);
+        } else {
+            if constexpr (NPE == 8) brick_me<double, S>(xc, static_cast<double>(ce), k);
+            else tet_me<double, S>(xc, static_cast<double>(ce), k);
+            return false;
+        }
+    }
     if constexpr (MIXED) {
         if constexpr (NPE == 8) return brick_ke_mixed<S>(xc, static_cast<float>(ce), thr, k);
         else return tet_ke_mixed<S>(xc, static_cast<float>(ce), thr, fp64_det, k);
@@ -82,7 +93,7 @@ static constexpr int INT_THREADS = 128;
 template <int NPE, typename T, typename S, typename CT, bool MIXED>
 __global__ void __launch_bounds__(INT_THREADS) k_integrate(const int32_t *__restrict__ E, int64_t nel,
                                                            const S *__restrict__ X, const CT *__restrict__ c,
-                                                           T *__restrict__ ke_out, float thr, bool fp64_det,
+                                                           T *__restrict__ ke_out, float thr, unsigned mode,
                                                            unsigned long long *nflag) {
     constexpr int NP = ElemTraits<NPE>::NP;
     constexpr int LD = NP + 1;  // odd stride: conflict-free staging
@@ -103,7 +114,7 @@ __global__ void __launch_bounds__(INT_THREADS) k_integrate(const int32_t *__rest
                 xc[a][2] = __ldg(X + 3 * (int64_t)g[a] + 2);
             }
             T k[NP];
-            fl = element_matrix<NPE, T, S, MIXED>(xc, __ldg(c + e), thr, fp64_det, k);
+            fl = element_matrix<NPE, T, S, MIXED>(xc, __ldg(c + e), thr, mode, k);
 #pragma unroll
             for (int p = 0; p < NP; ++p) st[threadIdx.x * LD + p] = k[p];
         }
@@ -226,10 +237,10 @@ __device__ __forceinline__ void phase_arrive(uint64_t *mb, uint32_t p) {
 template <int NPE, typename AccT, typename S, typename CT, bool FUSED, bool MIXED>
 __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restrict__ X, const CT *__restrict__ c,
                                            const AccT *__restrict__ ke, AccT *__restrict__ vals, float thr,
-                                           int64_t p, const PatchSmem &L, unsigned fp64_mode, uint64_t *mb,
+                                           int64_t p, const PatchSmem &L, unsigned mode, uint64_t *mb,
                                            uint32_t &g, const WaitCtl &wc) {
     constexpr int NP = ElemTraits<NPE>::NP;
-    const bool fp64_sums = (fp64_mode & FP64_SUMS) != 0, fp64_det = (fp64_mode & FP64_DETS) != 0;
+    const bool fp64_sums = (mode & FP64_SUMS) != 0;
     extern __shared__ __align__(16) unsigned char patch_smem[];
     AccT *acc = reinterpret_cast<AccT *>(patch_smem + L.acc);
     double *hv = reinterpret_cast<double *>(patch_smem + L.hv);
@@ -388,7 +399,7 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
                         xc[a][1] = xs[ln[a]][1];
                         xc[a][2] = xs[ln[a]][2];
                     }
-                    element_matrix<NPE, AccT, S, MIXED>(xc, ce, thr, fp64_det, kv);
+                    element_matrix<NPE, AccT, S, MIXED>(xc, ce, thr, mode, kv);
                 } else {
                     const int64_t e = pv.celem_id[ci];
 #pragma unroll
@@ -450,13 +461,13 @@ template <int NPE, typename AccT, typename S, typename CT, bool FUSED, bool MIXE
 __global__ void __launch_bounds__(patch_max_threads(NPE), patch_min_blocks(NPE)) k_patch(PlanView pv, const S *__restrict__ X,
                                                              const CT *__restrict__ c, const AccT *__restrict__ ke,
                                                              AccT *__restrict__ vals, float thr, int64_t p0,
-                                                             int64_t p1, PatchSmem L, unsigned fp64_mode,
+                                                             int64_t p1, PatchSmem L, unsigned mode,
                                                              WaitCtl wc) {
     __shared__ uint64_t mb[PHASE_RING];
     phase_init(mb);
     uint32_t g = 0;
     for (int64_t p = p0 + blockIdx.x; p < p1; p += gridDim.x)
-        patch_body<NPE, AccT, S, CT, FUSED, MIXED>(pv, X, c, ke, vals, thr, p, L, fp64_mode, mb, g, wc);
+        patch_body<NPE, AccT, S, CT, FUSED, MIXED>(pv, X, c, ke, vals, thr, p, L, mode, mb, g, wc);
 }
 
 // Persistent kernel over the patches of many meshes: work item w is patch
@@ -464,7 +475,7 @@ __global__ void __launch_bounds__(patch_max_threads(NPE), patch_min_blocks(NPE))
 template <int NPE, typename AccT, typename S, typename CT, bool MIXED>
 __global__ void __launch_bounds__(patch_max_threads(NPE), patch_min_blocks(NPE)) k_patch_batched(const BatchItem *__restrict__ items,
                                                                      const int64_t *__restrict__ prefix, int n,
-                                                                     PatchSmem L, unsigned fp64_mode,
+                                                                     PatchSmem L, unsigned mode,
                                                                      WaitCtl wc) {
     const int64_t total = prefix[n];
     __shared__ uint64_t mb[PHASE_RING];
@@ -478,7 +489,7 @@ __global__ void __launch_bounds__(patch_max_threads(NPE), patch_min_blocks(NPE))
         }
         const BatchItem &it = items[lo];
         patch_body<NPE, AccT, S, CT, true, MIXED>(it.pv, (const S *)it.X, (const CT *)it.c, nullptr,
-                                                   (AccT *)it.vals, it.thr, w - prefix[lo], L, fp64_mode, mb, g, wc);
+                                                   (AccT *)it.vals, it.thr, w - prefix[lo], L, mode, mb, g, wc);
     }
 }
 
@@ -491,7 +502,7 @@ static fem_status set_smem(F *f, size_t bytes) {
 
 template <int NPE, typename T, typename S, typename CT, bool MIXED>
 static fem_status launch_integrate_t(const int32_t *E, int64_t nel, const void *X, const void *c, void *ke, float thr,
-                                     bool fp64_det, unsigned long long *nflag, cudaStream_t s) {
+                                     unsigned mode, unsigned long long *nflag, cudaStream_t s) {
     constexpr int NP = ElemTraits<NPE>::NP;
     const size_t smem = (size_t)INT_THREADS * (NP + 1) * sizeof(T);
     auto f = k_integrate<NPE, T, S, CT, MIXED>;
@@ -501,7 +512,7 @@ static fem_status launch_integrate_t(const int32_t *E, int64_t nel, const void *
     if (per_sm < 1) per_sm = 1;
     const int64_t tiles = cdiv(nel, INT_THREADS);
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms() * per_sm));
-    f<<<grid, INT_THREADS, smem, s>>>(E, nel, (const S *)X, (const CT *)c, (T *)ke, thr, fp64_det, nflag);
+    f<<<grid, INT_THREADS, smem, s>>>(E, nel, (const S *)X, (const CT *)c, (T *)ke, thr, mode, nflag);
     FEM_LAUNCHED("k_integrate");
     return FEM_OK;
 }
@@ -509,7 +520,7 @@ static fem_status launch_integrate_t(const int32_t *E, int64_t nel, const void *
 fem_status launch_integrate(const IntegrateArgs &a, cudaStream_t s) {
     if (a.nel <= 0) return FEM_OK;
 #define FEM_INT(NPE, T, S, CT, MX) \
-    return launch_integrate_t<NPE, T, S, CT, MX>(a.E, a.nel, a.X, a.c, a.ke, a.thr, a.fp64_det, a.nflag, s)
+    return launch_integrate_t<NPE, T, S, CT, MX>(a.E, a.nel, a.X, a.c, a.ke, a.thr, a.mode, a.nflag, s)
     if (!a.mixed) {
         if (a.npe == 8) FEM_INT(8, double, double, double, false);
         FEM_INT(4, double, double, double, false);
@@ -587,7 +598,7 @@ static fem_status launch_patch_t(const PatchArgs &a, cudaStream_t s) {
     if (np <= 0) return FEM_OK;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np, (int64_t)num_sms() * per_sm));
     f<<<grid, threads, L.total, s>>>(P.view(cl), (const S *)a.X, (const CT *)a.c, (const AccT *)a.ke, (AccT *)a.vals,
-                                     a.thr, 0, np, L, a.fp64_mode, a.wait);
+                                     a.thr, 0, np, L, a.mode, a.wait);
     FEM_LAUNCHED("k_patch");
     return FEM_OK;
 }
@@ -669,7 +680,7 @@ fem_status batched_config(int npe, bool mixed, const PlanMax &pm, int threads, i
 fem_status launch_batched_kernel(const BatchLaunch &bl, cudaStream_t s) {
 #define FEM_B(NPE, T, MX)                                                                                   \
     k_patch_batched<NPE, T, T, T, MX><<<bl.grid, bl.threads, bl.L.total, s>>>(bl.items, bl.prefix, bl.n, bl.L, \
-                                                                               bl.fp64_mode, bl.wait)
+                                                                               bl.mode, bl.wait)
     if (bl.mixed) {
         if (bl.npe == 8) FEM_B(8, float, true); else FEM_B(4, float, true);
     } else {

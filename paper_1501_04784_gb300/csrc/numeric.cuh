@@ -26,8 +26,10 @@ struct PatchSmem {
     int hv_on;     // the hv region exists (some owned row has an FP64-accurate diagonal)
 };
 
-// Bits of the FP64 mode of the mixed kernels (fem_options.fp64_sums, fp64_dets).
-static constexpr unsigned FP64_SUMS = 1u, FP64_DETS = 2u;
+// Mode bits of the element kernels: FP64_SUMS, FP64_DETS (mixed kernels;
+// fem_options.fp64_sums, fp64_dets) and OP_MASS (fem_options.operator_kind: the
+// mass matrix instead of the stiffness matrix).
+static constexpr unsigned FP64_SUMS = 1u, FP64_DETS = 2u, OP_MASS = 4u;
 
 // Device-side waits of the patch kernels (colour phases on mbarriers): each wait
 // polls at most `spins` times, then records the failure in *status (read by
@@ -51,7 +53,7 @@ struct IntegrateArgs {
     void *ke;
     float thr;
     unsigned long long *nflag;
-    bool fp64_det = false;  // distorted tetrahedra: FP64 determinant instead of double-single
+    unsigned mode = 0;  // FP64_DETS, OP_MASS
 };
 
 struct PatchArgs {
@@ -66,8 +68,8 @@ struct PatchArgs {
     int64_t p0, p1;
     int threads, blocks_per_sm;
     WaitCtl wait;
-    unsigned fp64_mode;  // FP64_SUMS: high-valence sums with FP64 adds instead of FP32 TwoSum pairs;
-                         // FP64_DETS: distorted tetrahedra's determinant in FP64 arithmetic
+    unsigned mode;  // FP64_SUMS: high-valence sums with FP64 adds instead of FP32 TwoSum pairs;
+                    // FP64_DETS: distorted tetrahedra's determinant in FP64 arithmetic; OP_MASS
 };
 
 // Largest per-patch sizes over the plans a launch covers (sizes shared memory).
@@ -94,7 +96,7 @@ struct BatchItem {
 struct BatchLaunch {
     int npe = 8;
     bool mixed = true;
-    unsigned fp64_mode = 0;
+    unsigned mode = 0;
     const BatchItem *items = nullptr;
     const int64_t *prefix = nullptr;
     int n = 0;
@@ -113,8 +115,8 @@ fem_status launch_integrate(const IntegrateArgs &a, cudaStream_t s);
 WaitCtl wait_ctl(fem_mesh m);
 fem_status check_status(fem_mesh m, cudaStream_t s);
 
-inline unsigned fp64_mode(const fem_options &o) {
-    return (o.fp64_sums ? FP64_SUMS : 0u) | (o.fp64_dets ? FP64_DETS : 0u);
+inline unsigned kernel_mode(const fem_options &o) {
+    return (o.fp64_sums ? FP64_SUMS : 0u) | (o.fp64_dets ? FP64_DETS : 0u) | (o.operator_kind == 1 ? OP_MASS : 0u);
 }
 fem_status launch_patch(const PatchArgs &a, cudaStream_t s);
 PatchSmem patch_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsize, size_t csize);

@@ -28,16 +28,16 @@ def rounded_inputs(m, prec):
     return m.X, m.c
 
 
-def oracle_K(m, X=None, c=None):
+def oracle_K(m, X=None, c=None, op="stiffness"):
     X = m.X if X is None else X
     c = m.c if c is None else c
-    return oracle.build_K(m.npe, np.asarray(X, np.float64), m.E, np.asarray(c, np.float64))
+    return oracle.build_K(m.npe, np.asarray(X, np.float64), m.E, np.asarray(c, np.float64), op)
 
 
-def oracle_ke(m, X=None, c=None):
+def oracle_ke(m, X=None, c=None, op="stiffness"):
     X = m.X if X is None else X
     c = m.c if c is None else c
-    return oracle.ke_packed(m.npe, np.asarray(X, np.float64), m.E, np.asarray(c, np.float64))
+    return oracle.ke_packed(m.npe, np.asarray(X, np.float64), m.E, np.asarray(c, np.float64), op)
 
 
 def rel_err(got, ref, scale):
@@ -45,14 +45,14 @@ def rel_err(got, ref, scale):
     return float(np.max(np.abs(got - ref) / np.maximum(scale, 1e-300))) if len(ref) else 0.0
 
 
-def oracle_rows(m, rows, X=None, c=None):
+def oracle_rows(m, rows, X=None, c=None, op="stiffness"):
     """Exact rows of K for a sample of nodes: the oracle run on the elements that
     touch any sampled node (those rows are then complete)."""
     X = m.X if X is None else X
     c = m.c if c is None else c
     rows = np.unique(np.asarray(rows))
     touch = np.isin(m.E, rows).any(axis=1)
-    sub = oracle.build_K(m.npe, np.asarray(X, np.float64), m.E[touch], np.asarray(c, np.float64)[touch])
+    sub = oracle.build_K(m.npe, np.asarray(X, np.float64), m.E[touch], np.asarray(c, np.float64)[touch], op)
     out = {}
     for r in rows:
         a, b = sub["rowptr"][r], sub["rowptr"][r + 1]
