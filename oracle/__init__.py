@@ -54,6 +54,8 @@ def lib():
         L.oracle_compress.restype = _i64
         L.oracle_vjp.argtypes = [_int, _i64, _p, _p, _p, _p, _p, _p]
         L.oracle_vjp.restype = None
+        L.oracle_load.argtypes = [_int, _i64, _p, _p, _p, _p]
+        L.oracle_load.restype = _i64
         _lib = L
     return _lib
 
@@ -153,3 +155,12 @@ def vjp_from_G(npe: int, X, E, c, G, slot):
     each packed pair counted once) given the CSR slot map from ``build_K``."""
     S = np.asarray(G)[np.asarray(slot)]
     return vjp(npe, X, E, c, S)
+
+
+def load_vector(npe: int, X, E, s):
+    """Global load vector F [n_nodes] of a per-element constant source s [n_elems]
+    (F_n = sum over elements of s_e * integral N_a, a the element's local index of n)."""
+    X, E, s = _inputs(X, E, s)
+    F = np.zeros(X.shape[0])
+    lib().oracle_load(npe, E.shape[0], _ptr(E), _ptr(X), _ptr(s), _ptr(F))
+    return F
