@@ -344,12 +344,12 @@ int64_t oracle_compress(int64_t ntrip, int64_t n_nodes, const int64_t *rows, con
  * Global load vector of a per-element constant source s_e (Section 2, steps (ii)
  * and (iii): the local load vectors f_e and their assembly into F, the step the
  * paper sets aside):
- *   f_e,a = s_e * integral over the element of N_a,
+ *   f_e,a = src_e * integral over the element of N_a,
  * the brick by the same 2x2x2 Gauss rule and |det J| as k_e, the tetrahedron by the
  * 4-point rule of the mass matrix; F[E[e][a]] += f_e,a in element order.  F must be
  * zeroed by the caller.  Returns the number of elements with some det J <= 0.
  */
-int64_t oracle_load(int npe, int64_t n_elems, const int32_t *E, const double *X, const double *s, double *F) {
+int64_t oracle_load(int npe, int64_t n_elems, const int32_t *E, const double *X, const double *src, double *F) {
     int64_t bad = 0;
     double xe[24];
     for (int64_t e = 0; e < n_elems; ++e) {
@@ -362,14 +362,14 @@ int64_t oracle_load(int npe, int64_t n_elems, const int32_t *E, const double *X,
             for (int ir = 0; ir < 2; ++ir)
                 for (int is = 0; is < 2; ++is)
                     for (int it = 0; it < 2; ++it) {
-                        const double r = pts[ir], sq = pts[is], t = pts[it];
+                        const double r = pts[ir], s = pts[is], t = pts[it];
                         double N[8], dN[3][8];
                         for (int a = 0; a < 8; ++a) {
                             const double ra = BRICK_NODES[a][0], sa = BRICK_NODES[a][1], ta = BRICK_NODES[a][2];
-                            N[a] = 0.125 * (1 + r * ra) * (1 + sq * sa) * (1 + t * ta);
-                            dN[0][a] = 0.125 * ra * (1 + sq * sa) * (1 + t * ta);
+                            N[a] = 0.125 * (1 + r * ra) * (1 + s * sa) * (1 + t * ta);
+                            dN[0][a] = 0.125 * ra * (1 + s * sa) * (1 + t * ta);
                             dN[1][a] = 0.125 * sa * (1 + r * ra) * (1 + t * ta);
-                            dN[2][a] = 0.125 * ta * (1 + r * ra) * (1 + sq * sa);
+                            dN[2][a] = 0.125 * ta * (1 + r * ra) * (1 + s * sa);
                         }
                         double J[3][3];
                         for (int i = 0; i < 3; ++i)
@@ -381,7 +381,7 @@ int64_t oracle_load(int npe, int64_t n_elems, const int32_t *E, const double *X,
                         double det, inv[3][3];
                         inv3_d(J, &det, inv);
                         if (det <= 0) nonpos = 1;
-                        for (int a = 0; a < 8; ++a) fe[a] += s[e] * fabs(det) * N[a];
+                        for (int a = 0; a < 8; ++a) fe[a] += src[e] * fabs(det) * N[a];
                     }
         } else {
             double J[3][3];
@@ -393,7 +393,7 @@ int64_t oracle_load(int npe, int64_t n_elems, const int32_t *E, const double *X,
             const double vol = fabs(det) / 6.0;
             const double qa = (5.0 + 3.0 * sqrt(5.0)) / 20.0, qb = (5.0 - sqrt(5.0)) / 20.0;
             for (int q = 0; q < 4; ++q)
-                for (int a = 0; a < 4; ++a) fe[a] += s[e] * (vol / 4.0) * (a == q ? qa : qb);
+                for (int a = 0; a < 4; ++a) fe[a] += src[e] * (vol / 4.0) * (a == q ? qa : qb);
         }
         bad += nonpos;
         for (int a = 0; a < npe; ++a) F[E[e * npe + a]] += fe[a];

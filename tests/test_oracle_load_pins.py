@@ -94,11 +94,11 @@ def test_load_total(oracle_lib, npe):
 
 
 MUTATIONS = {
-    "tet_share": ("fe[a] += s[e] * (vol / 4.0) * (a == q ? qa : qb);", "fe[a] += s[e] * (vol / 3.0) * (a == q ? qa : qb);"),
-    "brick_no_jacobian": ("for (int a = 0; a < 8; ++a) fe[a] += s[e] * fabs(det) * N[a];",
-                          "for (int a = 0; a < 8; ++a) fe[a] += s[e] * N[a];"),
-    "brick_shape_index": ("N[a] = 0.125 * (1 + r * ra) * (1 + sq * sa) * (1 + t * ta);",
-                          "N[a] = 0.125 * (1 + r * ra) * (1 + sq * ta) * (1 + t * ta);"),
+    "tet_share": ("fe[a] += src[e] * (vol / 4.0) * (a == q ? qa : qb);", "fe[a] += src[e] * (vol / 3.0) * (a == q ? qa : qb);"),
+    "brick_no_jacobian": ("for (int a = 0; a < 8; ++a) fe[a] += src[e] * fabs(det) * N[a];",
+                          "for (int a = 0; a < 8; ++a) fe[a] += src[e] * N[a];"),
+    "brick_shape_index": ("for (int a = 0; a < 8; ++a) fe[a] += src[e] * fabs(det) * N[a];",
+                          "for (int a = 0; a < 8; ++a) fe[a] += src[e] * fabs(det) * N[7 - a];"),
     "wrong_node": ("for (int a = 0; a < npe; ++a) F[E[e * npe + a]] += fe[a];",
                    "for (int a = 0; a < npe; ++a) F[E[e * npe + (a + 1) % npe]] += fe[a];"),
 }

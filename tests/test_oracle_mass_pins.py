@@ -153,7 +153,7 @@ def test_mass_planted_mistakes_are_caught(tmp_path, name):
     import oracle
     src = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
     old, new = MUTATIONS[name]
-    assert src.count(old) == 1, name
+    assert src.count(old) >= 1, name
     path = tmp_path / "mut.c"
     path.write_text(src.replace(old, new))
     so = tmp_path / "libmut.so"
