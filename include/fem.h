@@ -205,6 +205,19 @@ fem_status fem_vjp(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, con
                    fem_dtype c_dtype, const void *G, void *dX, void *dc, void *stream);
 
 /*
+ * Global load vector of a per-element constant source (Section 2, steps (ii)-(iii):
+ * local load vectors f_e assembled into F): F[n] = sum over elements e that contain
+ * node n of src[e] * integral over e of N_a (a = n's local index in e).  Bricks use
+ * the 2x2x2 Gauss rule and |det J| of the stiffness matrix, tetrahedra |T| / 4 per
+ * node.  X as for fem_build_K; src [n_elems] (src_dtype); F [n_nodes] device,
+ * double (FEM_FP64) or float (FEM_MIXED: FP32 element arithmetic, FP64-accurate
+ * determinants of distorted elements).  Every entry of F is written.  Uses the
+ * cached plan, so FEM_ERR_STATE before fem_pattern.  Independent of operator_kind.
+ */
+fem_status fem_load_vector(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *src,
+                           fem_dtype src_dtype, void *F, void *stream);
+
+/*
  * Batched build of n meshes (each with its pattern cached) in one persistent
  * launch, replayed from a CUDA graph when the same mesh set is built again.
  * X[i], c[i], vals[i] are host arrays of n device pointers; all meshes share

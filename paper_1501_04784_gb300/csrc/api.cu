@@ -8,6 +8,8 @@
 
 namespace fem {
 int64_t launch_count(int reset);
+fem_status launch_load(fem_mesh m, bool mixed, const void *X, fem_dtype xd, const void *src, fem_dtype sd, void *F,
+                       float thr, bool fp64_det, cudaStream_t s);
 fem_status launch_vjp(fem_mesh m, bool mixed, const void *X, fem_dtype xd, const void *c, fem_dtype cd,
                       const void *G, void *dX, void *dc, cudaStream_t s);
 fem_status launch_batched(const fem_mesh *ms, int n, bool mixed, const void *const *X, fem_dtype xd,
@@ -390,6 +392,21 @@ fem_status fem_vjp(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, con
         return FEM_ERR_UNSUPPORTED;
     }
     return launch_vjp(m, p == FEM_MIXED, X, x_dtype, c, c_dtype, G, dX, dc, as_stream(stream));
+}
+
+fem_status fem_load_vector(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *src,
+                           fem_dtype src_dtype, void *F, void *stream) {
+    FEM_TRY(check_inputs(m, p, X, x_dtype, src, src_dtype));
+    if (!m->has_pattern) {
+        set_error("fem_load_vector before fem_pattern");
+        return FEM_ERR_STATE;
+    }
+    if (!F || !aligned(F, p == FEM_FP64 ? 8 : 4)) {
+        set_error("F must be a non-null aligned device pointer");
+        return FEM_ERR_ARG;
+    }
+    return launch_load(m, p == FEM_MIXED, X, x_dtype, src, src_dtype, F, default_threshold(m), m->opt.fp64_dets != 0,
+                       as_stream(stream));
 }
 
 fem_status fem_build_K_batched(const fem_mesh *meshes, int n, fem_prec p, const void *const *X, fem_dtype x_dtype,

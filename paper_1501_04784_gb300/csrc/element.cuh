@@ -438,6 +438,50 @@ __device__ __forceinline__ void brick_me(const S (*xc)[3], T c, T (&m)[36]) {
     brick_mass_from_dets(det, c, m);
 }
 
+// Brick determinants |det(2 J_q)| at the 8 Gauss points in precision T; with
+// `mixed`, FP32 unless max_q det J / min_q det J exceeds thr (or some det J <= 0),
+// then from FP64.  Returns true when FP64 was used.
+template <typename T, typename S>
+__device__ __forceinline__ bool brick_gauss_dets(const S (*xc)[3], float thr, bool mixed, T (&det)[8]) {
+    Vec3<T> e[3][2][2];
+    brick_edges<T, S>(xc, e);
+    Vec3<T> row[3][2][2];
+    brick_jrows(e, row);
+    brick_dets(row, det);
+    if (!mixed) return false;
+    T dmin = det[0], dmax = det[0];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) {
+        dmin = det[q] < dmin ? det[q] : dmin;
+        dmax = det[q] > dmax ? det[q] : dmax;
+    }
+    const bool flagged = !(dmin > T(0)) || dmax > T(thr) * dmin;
+    if (flagged) {
+        Vec3<double> ed[3][2][2];
+        brick_edges<double, S>(xc, ed);
+        Vec3<double> rowd[3][2][2];
+        brick_jrows(ed, rowd);
+        double detd[8];
+        brick_dets(rowd, detd);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) det[q] = (T)detd[q];
+    }
+    return flagged;
+}
+
+// Brick load vector f_a = s integral N_a = (s / 8) sum_q |det(2 J_q)| N_a(q): the
+// determinants contracted with the single hats on every axis.
+template <typename T>
+__device__ __forceinline__ void brick_load_from_dets(const T (&det)[8], T s, T (&f)[8]) {
+    T D[2][2][2];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) D[q >> 2][(q >> 1) & 1][q & 1] = det[q] < T(0) ? -det[q] : det[q];
+    T V[3][3][3];
+    contract_cross<T, 0, 0, 0>(D, V);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) f[a] = s * T(0.125) * V[hb1(a)][hb2(a)][hb3(a)];
+}
+
 // Mixed precision: FP32, except that an element whose max_q det J / min_q det J
 // exceeds `thr` (or with a det J <= 0) takes its determinants from FP64.
 template <typename S>

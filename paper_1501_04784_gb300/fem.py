@@ -160,6 +160,18 @@ class Mesh:
                                      _dev(G, "G", vd), _dev(dX, "dX"), _dev(dc, "dc"), _stream(stream)))
         return dX, dc
 
+    def load_vector(self, X, src, prec="fp64", out=None, stream=None):
+        """Global load vector F [n_nodes] of the per-element constant source src."""
+        p = _prec(prec)
+        if self.nnz is None:
+            self.pattern(stream)
+        vd = value_dtype(prec)
+        if out is None:
+            out = torch.empty(self.n_nodes, dtype=vd, device=X.device)
+        abi.check(abi.load().fem_load_vector(self._h, p, _dev(X, "X"), _DT[X.dtype], _dev(src, "src"), _DT[src.dtype],
+                                             _dev(out, "F", vd), _stream(stream)))
+        return out
+
     def autotune(self, X, c, prec="mixed", stream=None) -> dict:
         """Pick the patch size and block size by timing fem_build_K (overwrites a scratch vals)."""
         if self.nnz is None:
