@@ -205,7 +205,7 @@ fem_status fem_vjp(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, con
                    fem_dtype c_dtype, const void *G, void *dX, void *dc, void *stream);
 
 /*
- * Global load vector of a per-element constant source (Section 2, steps (ii)-(iii):
+ * Global load vector of a per-element constant source (Section 1, FEM steps (ii)-(iii):
  * local load vectors f_e assembled into F): F[n] = sum over elements e that contain
  * node n of src[e] * integral over e of N_a (a = n's local index in e).  Bricks use
  * the 2x2x2 Gauss rule and |det J| of the stiffness matrix, tetrahedra |T| / 4 per

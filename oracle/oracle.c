@@ -341,7 +341,7 @@ int64_t oracle_compress(int64_t ntrip, int64_t n_nodes, const int64_t *rows, con
 }
 
 /*
- * Global load vector of a per-element constant source s_e (Section 2, steps (ii)
+ * Global load vector of a per-element constant source s_e (Section 1, steps (ii)
  * and (iii): the local load vectors f_e and their assembly into F, the step the
  * paper sets aside):
  *   f_e,a = src_e * integral over the element of N_a,

@@ -1,6 +1,6 @@
 // load.cu -- global load vector of a per-element constant source s_e:
 // F_n = sum over elements e containing node n of f_e,a, f_e,a = s_e * integral N_a
-// (Section 2, steps (ii)-(iii): the local load vectors f_e and their assembly into F).
+// (Section 1, steps (ii)-(iii) of the FEM procedure of Fig. 1: the local load vectors f_e and their assembly into F).
 //
 // Bricks use the same 2x2x2 Gauss rule and |det J| as the stiffness matrix, with the
 // sum factorised over the axes; tetrahedra take |T| / 4 per node.  In mixed

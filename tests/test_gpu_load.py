@@ -1,4 +1,4 @@
-"""Global load vector F = sum_e src_e int N (Section 2's f_e and F) on the GPU against
+"""Global load vector F = sum_e src_e int N (Section 1's f_e and F) on the GPU against
 the oracle's load vector (pinned in test_oracle_load_pins.py), and against the GPU's
 own mass matrix (F = M 1 when src = c)."""
 import numpy as np

@@ -1,4 +1,4 @@
-"""Pins of the oracle's load vector, F_n = sum_e s_e * integral N_a (Section 2, steps
+"""Pins of the oracle's load vector, F_n = sum_e s_e * integral N_a (Section 1, steps
 (ii)-(iii): local load vectors f_e assembled into F).
 
 The references are:
