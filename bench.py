@@ -295,9 +295,25 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(ne):
             mesh.build_K_host(Xh, ch, "mixed", out=vh)
+        dt_serial = (time.perf_counter() - t0) / ne
+        # the asynchronous host entry point on two streams: each step still copies
+        # its inputs in and its result out, but a step's copy-in and build overlap
+        # the previous step's copy-out
+        vh2 = [vh, torch.empty(nnz, dtype=torch.float32).pin_memory()]
+        st2 = [torch.cuda.Stream(), torch.cuda.Stream()]
+        for k in range(4):
+            mesh.build_K_host_async(Xh, ch, "mixed", out=vh2[k % 2], stream=st2[k % 2])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(ne):
+            mesh.build_K_host_async(Xh, ch, "mixed", out=vh2[k % 2], stream=st2[k % 2])
+        torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / ne
+        mesh.sync()
         e2e = {"value": m.n_elems / dt, "unit": "elements/s", "h2d_bytes_per_step": Xh.nbytes + ch.nbytes,
-               "d2h_bytes_per_step": nnz * 4}
+               "d2h_bytes_per_step": nnz * 4,
+               "api": "fem_build_K_host_async, two streams (copy-in and build of a step overlap the previous copy-out)",
+               "serial": {"value": m.n_elems / dt_serial, "api": "fem_build_K_host (synchronous)"}}
 
     peak, peak_kind = measured_peaks()
     alg = algorithmic_bytes(m.n_nodes, m.n_elems, 8, nnz, 4, 4, 4)

@@ -46,7 +46,7 @@ class fem_tuning(ctypes.Structure):
 
 EXPORTS = ["fem_options_default", "fem_status_str", "fem_last_error", "fem_mesh_create", "fem_mesh_destroy",
            "fem_pattern", "fem_get_pattern", "fem_pattern_ptrs", "fem_integrate_local", "fem_assemble_csr",
-           "fem_build_K", "fem_build_K_host", "fem_vjp", "fem_load_vector", "fem_build_K_batched", "fem_sync", "fem_mesh_info",
+           "fem_build_K", "fem_build_K_host", "fem_build_K_host_async", "fem_vjp", "fem_load_vector", "fem_build_K_batched", "fem_sync", "fem_mesh_info",
            "fem_launch_count", "fem_pattern_noalloc", "fem_batched_config", "fem_autotune"]
 
 _lib = None
@@ -93,6 +93,8 @@ def load(build_if_missing: bool = False):
     L.fem_build_K.restype = S
     L.fem_build_K_host.argtypes = [P, INT, P, INT, P, INT, P, P]
     L.fem_build_K_host.restype = S
+    L.fem_build_K_host_async.argtypes = L.fem_build_K_host.argtypes
+    L.fem_build_K_host_async.restype = S
     L.fem_vjp.argtypes = [P, INT, P, INT, P, INT, P, P, P, P]
     L.fem_vjp.restype = S
     L.fem_load_vector.argtypes = [P, INT, P, INT, P, INT, P, P]

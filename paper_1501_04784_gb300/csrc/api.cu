@@ -348,11 +348,14 @@ fem_status fem_build_K(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype,
     });
 }
 
-fem_status fem_build_K_host(fem_mesh m, fem_prec p, const void *X_host, fem_dtype x_dtype, const void *c_host,
-                            fem_dtype c_dtype, void *vals_host, void *stream) {
+namespace fem {
+// Copy in, build, copy out, ordered on s through one of the mesh's two staging
+// slots (see fem_mesh_s::host_stage); returns without waiting.
+static fem_status host_build(fem_mesh m, fem_prec p, const void *X_host, fem_dtype x_dtype, const void *c_host,
+                             fem_dtype c_dtype, void *vals_host, cudaStream_t s, const char *who) {
     FEM_TRY(check_inputs(m, p, X_host, x_dtype, c_host, c_dtype));
     if (!m->has_pattern) {
-        set_error("fem_build_K_host before fem_pattern");
+        set_error("%s before fem_pattern", who);
         return FEM_ERR_STATE;
     }
     if (!vals_host) {
@@ -364,15 +367,52 @@ fem_status fem_build_K_host(fem_mesh m, fem_prec p, const void *X_host, fem_dtyp
     const size_t vb = (size_t)m->nnz * (p == FEM_FP64 ? 8 : 4);
     const size_t xo = 0, co = (xb + 255) / 256 * 256, vo = co + (cb + 255) / 256 * 256;
     const size_t total = vo + vb;
-    if (m->host_stage.n < total) FEM_TRY(m->host_stage.alloc(m->arena, total, "host staging"));
-    unsigned char *base = m->host_stage.ptr;
-    cudaStream_t s = as_stream(stream);
+    const int k = m->stage_next;
+    for (cudaEvent_t *e : {&m->stage_free[0], &m->stage_free[1], &m->built})
+        if (!*e) FEM_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    if (m->host_stage[k].n < total) {
+        FEM_CUDA(cudaEventSynchronize(m->stage_free[k]));  // the slot's last output copy is done
+        m->host_stage[k].free();
+        FEM_TRY(m->host_stage[k].alloc(m->arena, total, "host staging"));
+    }
+    m->stage_next ^= 1;
+    unsigned char *base = m->host_stage[k].ptr;
+    FEM_CUDA(cudaStreamWaitEvent(s, m->stage_free[k], 0));
     FEM_CUDA(cudaMemcpyAsync(base + xo, X_host, xb, cudaMemcpyHostToDevice, s));
     FEM_CUDA(cudaMemcpyAsync(base + co, c_host, cb, cudaMemcpyHostToDevice, s));
-    FEM_TRY(fem_build_K(m, p, base + xo, x_dtype, base + co, c_dtype, base + vo, stream));
+    FEM_CUDA(cudaStreamWaitEvent(s, m->built, 0));
+    FEM_TRY(fem_build_K(m, p, base + xo, x_dtype, base + co, c_dtype, base + vo, s));
+    FEM_CUDA(cudaEventRecord(m->built, s));
     FEM_CUDA(cudaMemcpyAsync(vals_host, base + vo, vb, cudaMemcpyDeviceToHost, s));
+    FEM_CUDA(cudaEventRecord(m->stage_free[k], s));
+    return FEM_OK;
+}
+
+static bool pinned(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+}  // namespace fem
+
+fem_status fem_build_K_host(fem_mesh m, fem_prec p, const void *X_host, fem_dtype x_dtype, const void *c_host,
+                            fem_dtype c_dtype, void *vals_host, void *stream) {
+    cudaStream_t s = as_stream(stream);
+    FEM_TRY(host_build(m, p, X_host, x_dtype, c_host, c_dtype, vals_host, s, "fem_build_K_host"));
     FEM_CUDA(cudaStreamSynchronize(s));
     return check_status(m, s);
+}
+
+fem_status fem_build_K_host_async(fem_mesh m, fem_prec p, const void *X_host, fem_dtype x_dtype, const void *c_host,
+                                  fem_dtype c_dtype, void *vals_host, void *stream) {
+    if (!pinned(X_host) || !pinned(c_host) || !pinned(vals_host)) {
+        set_error("fem_build_K_host_async needs page-locked host buffers (cudaHostAlloc or cudaHostRegister)");
+        return FEM_ERR_ARG;
+    }
+    return host_build(m, p, X_host, x_dtype, c_host, c_dtype, vals_host, as_stream(stream), "fem_build_K_host_async");
 }
 
 fem_status fem_vjp(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c, fem_dtype c_dtype,

@@ -151,6 +151,22 @@ class Mesh:
                                               ctypes.c_void_p(out.data_ptr()), _stream(stream)))
         return out[: self.nnz]
 
+    def build_K_host_async(self, X, c, prec="fp64", out=None, stream=None):
+        """Page-locked host tensors in and out, ordered on `stream`; out is complete once
+        the stream is synchronised."""
+        p = _prec(prec)
+        if self.nnz is None:
+            self.pattern(stream)
+        for t, n in ((X, "X"), (c, "c")):
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError(f"{n} must be a contiguous host tensor")
+        if out is None:
+            out = torch.empty(max(self.nnz, 1), dtype=value_dtype(prec), pin_memory=True)
+        abi.check(abi.load().fem_build_K_host_async(self._h, p, ctypes.c_void_p(X.data_ptr()), _DT[X.dtype],
+                                                    ctypes.c_void_p(c.data_ptr()), _DT[c.dtype],
+                                                    ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out[: self.nnz]
+
     def vjp(self, X, c, G, prec="fp64", stream=None):
         p = _prec(prec)
         vd = value_dtype(prec)

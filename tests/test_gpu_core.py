@@ -266,3 +266,28 @@ def test_high_valence_summation_modes(fem, fp64_sums):
     # the diagonal sum itself: within a few FP32 roundings of the exact sum
     d_err = np.abs(vals[diag].astype(np.float64) - ref["vals"][diag]) / ref["cs"][diag]
     assert d_err.max() <= 4e-7
+
+
+def test_host_async_two_streams(fem):
+    """fem_build_K_host_async on alternating streams with two staging slots: every
+    step's values equal the device build's, and pageable buffers are refused."""
+    from paper_1501_04784_gb300 import abi
+    m = MESHES["hex_7x5x3"]()
+    mesh = make(fem, m)
+    Xd, cd, X, c = inputs(m, "mixed")
+    ref = mesh.build_K(Xd, cd, "mixed").cpu()
+    Xh, ch = Xd.cpu().pin_memory(), cd.cpu().pin_memory()
+    scale = [1.0, 1.5, 2.0, 0.5]
+    outs = [torch.empty(mesh.nnz, dtype=torch.float32).pin_memory() for _ in scale]
+    cs = [(ch * s).pin_memory() for s in scale]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for k, s in enumerate(scale):
+        mesh.build_K_host_async(Xh, cs[k], "mixed", out=outs[k], stream=streams[k % 2])
+    torch.cuda.synchronize()
+    mesh.sync()
+    for k, s in enumerate(scale):
+        want = mesh.build_K(Xd, (cd * s).contiguous(), "mixed").cpu()
+        assert torch.equal(outs[k], want)
+    assert torch.equal(outs[0], ref)
+    with pytest.raises(abi.FemError, match="FEM_ERR_ARG"):
+        mesh.build_K_host_async(Xd.cpu(), cd.cpu(), "mixed")
