@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--n", type=int, default=100, help="grid cells per axis (100 = the 1M-brick workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the 512-mesh batched build and the 27M-brick budgeted build")
     ap.add_argument("--once", choices=["mixed", "fp64"], default=None,
                     help="profiling mode: build K twice in this precision and exit (no timing, no JSON)")
     ap.add_argument("--workload", choices=["hex", "tet"], default="hex",
@@ -355,8 +357,13 @@ def run_ours(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(m)
-        print(json.dumps(out))
     mesh.close()
+    if not args.no_workloads:
+        extra = other_workloads(flush, stream)
+        if rank == 0:
+            out["workloads"] = extra
+    if rank == 0:
+        print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
 
@@ -398,6 +405,61 @@ def run_reference(args):
                          "sample": f"{per_step} consecutive elements of the workload per step (rotating)"},
         "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def other_workloads(flush, stream):
+    """The batched and the large workload beside the headline (mixed precision, pattern
+    cached, L2 flushed before every timed build): 512 uneven brick meshes in one
+    persistent launch replayed from a CUDA graph, and 300^3 bricks built in patch
+    groups under a 16 GB library budget."""
+    import numpy as np
+    import torch
+
+    import meshgen
+    from paper_1501_04784_gb300 import fem
+
+    def dev(a, dt):
+        return torch.as_tensor(np.ascontiguousarray(a), device="cuda").to(dt)
+
+    def timed(fn, n):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return statistics.median([a.elapsed_time(b) for a, b in evs])
+
+    out = {}
+    ms = meshgen.batch_meshes()
+    meshes = [fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64)) for m in ms]
+    Xs = [dev(m.X, torch.float32) for m in ms]
+    cs = [dev(m.c, torch.float32) for m in ms]
+    vals = [torch.empty(mesh.pattern(), dtype=torch.float32, device="cuda") for mesh in meshes]
+    nel = sum(m.n_elems for m in ms)
+    t = timed(lambda: fem.build_K_batched(meshes, Xs, cs, "mixed", out=vals), 10)
+    out["batched"] = {"workload": f"{len(ms)} uneven brick meshes, {nel} elements, one graph launch",
+                      "value": nel / (t / 1e3), "unit": "elements/s", "ms_per_step": t,
+                      "launch": fem.batched_config(meshes, "mixed")}
+    for mesh in meshes:
+        mesh.close()
+    del meshes, Xs, cs, vals
+    m = meshgen.config_mesh(4)
+    mesh = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), mem_budget_bytes=16 << 30)
+    nnz = mesh.pattern()
+    X, c = dev(m.X, torch.float32), dev(m.c, torch.float32)
+    v = torch.empty(nnz, dtype=torch.float32, device="cuda")
+    t = timed(lambda: mesh.build_K(X, c, "mixed", out=v), 3)
+    info = mesh.info()
+    out["large"] = {"workload": "300^3 bricks (27M elements), 16 GB library budget", "value": m.n_elems / (t / 1e3),
+                    "unit": "elements/s", "ms_per_step": t, "patch_groups": info["n_groups"],
+                    "plan_bytes": info["plan_bytes"]}
+    mesh.close()
+    return out
 
 
 def run_once(args):

@@ -249,7 +249,7 @@ fem_status fem_batched_config(const fem_mesh *meshes, int n, fem_prec p, int *bl
 typedef struct {
     int patch_entries;  /* chosen assembly tile: lower-CSR entries per thread block */
     int block_threads;  /* chosen threads per block (elements integrated per batch) */
-    float ms;           /* time of one fem_build_K with the chosen configuration */
+    float ms;           /* median time of one fem_build_K from a cold L2, chosen configuration */
     int tried;          /* candidate configurations timed */
     int reserved[4];
 } fem_tuning;
@@ -257,9 +257,11 @@ typedef struct {
 /*
  * Tuner: rebuilds the mesh's plan for each candidate patch size (the assembly
  * tile) and times fem_build_K for each candidate block size on the given inputs
- * (vals is overwritten); the mesh keeps the fastest configuration.  Gauss-point
- * unrolling is not a candidate: the sum-factorised brick couples all 8 points.
- * Blocks.  FEM_ERR_STATE before fem_pattern.
+ * (vals is overwritten): the median of 5 builds, each after a 256 MB scratch
+ * rewrite that clears the L2 (skipped when the memory budget has no room for
+ * it); the mesh keeps the fastest configuration.  Gauss-point unrolling is not a
+ * candidate: the sum-factorised brick couples all 8 points.  Blocks.
+ * FEM_ERR_STATE before fem_pattern.
  */
 fem_status fem_autotune(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c, fem_dtype c_dtype,
                         void *vals, void *stream, fem_tuning *out);
