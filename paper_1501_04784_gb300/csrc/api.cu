@@ -192,6 +192,7 @@ void fem_mesh_destroy(fem_mesh m) {
 }
 
 fem_status fem_pattern(fem_mesh m, int64_t *nnz_out, void *stream) {
+    NvtxRange nvtx_range("fem_pattern");
     if (!m) {
         set_error("null mesh");
         return FEM_ERR_ARG;
@@ -306,6 +307,7 @@ fem_status fem_assemble_csr(fem_mesh m, fem_prec p, const void *ke, void *vals, 
 
 fem_status fem_build_K(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c, fem_dtype c_dtype,
                        void *vals, void *stream) {
+    NvtxRange nvtx_range("fem_build_K");
     FEM_TRY(check_inputs(m, p, X, x_dtype, c, c_dtype));
     if (!m->has_pattern) {
         set_error("fem_build_K before fem_pattern");
@@ -354,6 +356,7 @@ namespace fem {
 // slots (see fem_mesh_s::host_stage); returns without waiting.
 static fem_status host_build(fem_mesh m, fem_prec p, const void *X_host, fem_dtype x_dtype, const void *c_host,
                              fem_dtype c_dtype, void *vals_host, cudaStream_t s, const char *who) {
+    NvtxRange nvtx_range(who);
     FEM_TRY(check_inputs(m, p, X_host, x_dtype, c_host, c_dtype));
     if (!m->has_pattern) {
         set_error("%s before fem_pattern", who);
@@ -418,6 +421,7 @@ fem_status fem_build_K_host_async(fem_mesh m, fem_prec p, const void *X_host, fe
 
 fem_status fem_vjp(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c, fem_dtype c_dtype,
                    const void *G, void *dX, void *dc, void *stream) {
+    NvtxRange nvtx_range("fem_vjp");
     FEM_TRY(check_inputs(m, p, X, x_dtype, c, c_dtype));
     if (!m->has_pattern) {
         set_error("fem_vjp before fem_pattern");
@@ -437,6 +441,7 @@ fem_status fem_vjp(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, con
 
 fem_status fem_load_vector(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *src,
                            fem_dtype src_dtype, void *F, void *stream) {
+    NvtxRange nvtx_range("fem_load_vector");
     FEM_TRY(check_inputs(m, p, X, x_dtype, src, src_dtype));
     if (!m->has_pattern) {
         set_error("fem_load_vector before fem_pattern");
@@ -452,6 +457,7 @@ fem_status fem_load_vector(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dt
 
 fem_status fem_build_K_batched(const fem_mesh *meshes, int n, fem_prec p, const void *const *X, fem_dtype x_dtype,
                                const void *const *c, fem_dtype c_dtype, void *const *vals, void *stream) {
+    NvtxRange nvtx_range("fem_build_K_batched");
     if (!meshes || n < 0 || (n > 0 && (!X || !c || !vals))) {
         set_error("bad batch arguments");
         return FEM_ERR_ARG;
@@ -490,6 +496,7 @@ fem_status fem_batched_config(const fem_mesh *meshes, int n, fem_prec p, int *bl
 // the caller's inputs; the mesh keeps the fastest.
 fem_status fem_autotune(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c, fem_dtype c_dtype,
                         void *vals, void *stream, fem_tuning *out) {
+    NvtxRange nvtx_range("fem_autotune");
     FEM_TRY(check_inputs(m, p, X, x_dtype, c, c_dtype));
     if (!m->has_pattern) {
         set_error("fem_autotune before fem_pattern");

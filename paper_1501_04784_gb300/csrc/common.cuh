@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <cstdio>
@@ -31,6 +32,15 @@ void count_launch(int n = 1);
         cudaError_t _e = (expr);                                        \
         if (_e != cudaSuccess) return ::fem::cuda_status(_e, #expr);    \
     } while (0)
+
+// A named NVTX range over a scope (API calls and symbolic phases appear on a
+// profiler's timeline; without an attached tool a push is a no-op).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 #define FEM_LAUNCHED(what)                                                     \
     do {                                                                       \
