@@ -56,7 +56,9 @@ typedef enum {
     FEM_OK = 0,
     FEM_ERR_ARG = 1,         /* null or misaligned pointer, bad size, bad enum value */
     FEM_ERR_INDEX = 2,       /* a node id in E outside [0, n_nodes) */
-    FEM_ERR_DEGENERATE = 3,  /* a node repeated within one element */
+    FEM_ERR_DEGENERATE = 3,  /* a node repeated within one element (fem_mesh_create), or an
+                                element matrix that is not finite: zero volume, non-finite
+                                input (reported by fem_sync after the build) */
     FEM_ERR_OOM = 4,         /* a device allocation failed */
     FEM_ERR_BUDGET = 5,      /* the memory budget cannot hold the smallest unit of work */
     FEM_ERR_CUDA = 6,        /* a CUDA runtime call or kernel failed */
@@ -267,9 +269,11 @@ fem_status fem_autotune(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype
                         void *vals, void *stream, fem_tuning *out);
 
 /* Wait for the mesh's work on `stream` and report any asynchronous error:
- * FEM_ERR_CUDA for a CUDA error, FEM_ERR_TIMEOUT if a bounded device-side wait
- * of a build gave up since the last fem_sync (the values of that build are
- * undefined; the context stays usable and the status is cleared). */
+ * FEM_ERR_CUDA for a CUDA error; FEM_ERR_DEGENERATE if a build since the last
+ * fem_sync met an element matrix that is not finite (an element of zero volume,
+ * or non-finite coordinates or coefficients); FEM_ERR_TIMEOUT if a bounded
+ * device-side wait of a build gave up.  The values of that build are undefined;
+ * the context stays usable and the status is cleared. */
 fem_status fem_sync(fem_mesh m, void *stream);
 
 /* Sizes and plan statistics of the mesh (after fem_pattern for the plan fields). */

@@ -81,6 +81,11 @@ fem_status check_status(fem_mesh m, cudaStream_t s) {
     if (h == 0) return FEM_OK;
     FEM_CUDA(cudaMemsetAsync(m->status.ptr, 0, sizeof(int), s));
     FEM_CUDA(cudaStreamSynchronize(s));
+    if (h & STATUS_NONFINITE) {
+        set_error("an element matrix was not finite (an element with a zero Jacobian determinant, or non-finite "
+                  "coordinates or coefficients); the values of that build are undefined");
+        return FEM_ERR_DEGENERATE;
+    }
     set_error("a device-side wait of a patch kernel gave up after %d polls; the values of that build are undefined",
               m->opt.wait_spins > 0 ? m->opt.wait_spins : WAIT_SPINS_DEFAULT);
     return FEM_ERR_TIMEOUT;
@@ -252,7 +257,7 @@ fem_status fem_integrate_local(fem_mesh m, fem_prec p, const void *X, fem_dtype 
         return FEM_ERR_ARG;
     }
     IntegrateArgs a{m->npe, p == FEM_MIXED, x_dtype, c_dtype, m->E, m->n_elems, X, c, ke_out,
-                    default_threshold(m), nullptr, kernel_mode(m->opt)};
+                    default_threshold(m), nullptr, kernel_mode(m->opt), m->status.ptr};
     return launch_integrate(a, as_stream(stream));
 }
 
@@ -325,7 +330,7 @@ fem_status fem_build_K(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype,
         fem_status st = m->ke64.n >= n ? FEM_OK : m->ke64.alloc(m->arena, n, "FP64 element matrices");
         if (st == FEM_OK) {
             IntegrateArgs ia{m->npe, false, x_dtype, c_dtype, m->E, m->n_elems, X, c, m->ke64.ptr,
-                             default_threshold(m), nullptr, kernel_mode(m->opt)};
+                             default_threshold(m), nullptr, kernel_mode(m->opt), m->status.ptr};
             FEM_TRY(launch_integrate(ia, s));
             PatchArgs a = patch_args(m, p, false);
             a.xd = FEM_F64;

@@ -94,7 +94,7 @@ template <int NPE, typename T, typename S, typename CT, bool MIXED>
 __global__ void __launch_bounds__(INT_THREADS) k_integrate(const int32_t *__restrict__ E, int64_t nel,
                                                            const S *__restrict__ X, const CT *__restrict__ c,
                                                            T *__restrict__ ke_out, float thr, unsigned mode,
-                                                           unsigned long long *nflag) {
+                                                           unsigned long long *nflag, int *status) {
     constexpr int NP = ElemTraits<NPE>::NP;
     constexpr int LD = NP + 1;  // odd stride: conflict-free staging
     extern __shared__ __align__(16) unsigned char int_smem[];
@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(INT_THREADS) k_integrate(const int32_t *__rest
             }
             T k[NP];
             fl = element_matrix<NPE, T, S, MIXED>(xc, __ldg(c + e), thr, mode, k);
+            if (status && !isfinite(k[0])) atomicOr(status, STATUS_NONFINITE);
 #pragma unroll
             for (int p = 0; p < NP; ++p) st[threadIdx.x * LD + p] = k[p];
         }
@@ -221,7 +222,7 @@ __device__ __forceinline__ void phase_wait(uint64_t *mb, uint32_t p, const WaitC
             : "memory");
         if (done) return;
     }
-    if ((threadIdx.x & 31) == 0) atomicOr(wc.status, 1);
+    if ((threadIdx.x & 31) == 0) atomicOr(wc.status, STATUS_TIMEOUT);
 }
 
 __device__ __forceinline__ void phase_arrive(uint64_t *mb, uint32_t p) {
@@ -400,6 +401,8 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
                         xc[a][2] = xs[ln[a]][2];
                     }
                     element_matrix<NPE, AccT, S, MIXED>(xc, ce, thr, mode, kv);
+                    // k_00 (m_00) is positive and finite for any element of nonzero volume
+                    if (!isfinite(kv[0])) atomicOr(wc.status, STATUS_NONFINITE);
                 } else {
                     const int64_t e = pv.celem_id[ci];
 #pragma unroll
@@ -502,7 +505,7 @@ static fem_status set_smem(F *f, size_t bytes) {
 
 template <int NPE, typename T, typename S, typename CT, bool MIXED>
 static fem_status launch_integrate_t(const int32_t *E, int64_t nel, const void *X, const void *c, void *ke, float thr,
-                                     unsigned mode, unsigned long long *nflag, cudaStream_t s) {
+                                     unsigned mode, unsigned long long *nflag, int *status, cudaStream_t s) {
     constexpr int NP = ElemTraits<NPE>::NP;
     const size_t smem = (size_t)INT_THREADS * (NP + 1) * sizeof(T);
     auto f = k_integrate<NPE, T, S, CT, MIXED>;
@@ -512,7 +515,7 @@ static fem_status launch_integrate_t(const int32_t *E, int64_t nel, const void *
     if (per_sm < 1) per_sm = 1;
     const int64_t tiles = cdiv(nel, INT_THREADS);
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms() * per_sm));
-    f<<<grid, INT_THREADS, smem, s>>>(E, nel, (const S *)X, (const CT *)c, (T *)ke, thr, mode, nflag);
+    f<<<grid, INT_THREADS, smem, s>>>(E, nel, (const S *)X, (const CT *)c, (T *)ke, thr, mode, nflag, status);
     FEM_LAUNCHED("k_integrate");
     return FEM_OK;
 }
@@ -520,7 +523,7 @@ static fem_status launch_integrate_t(const int32_t *E, int64_t nel, const void *
 fem_status launch_integrate(const IntegrateArgs &a, cudaStream_t s) {
     if (a.nel <= 0) return FEM_OK;
 #define FEM_INT(NPE, T, S, CT, MX) \
-    return launch_integrate_t<NPE, T, S, CT, MX>(a.E, a.nel, a.X, a.c, a.ke, a.thr, a.mode, a.nflag, s)
+    return launch_integrate_t<NPE, T, S, CT, MX>(a.E, a.nel, a.X, a.c, a.ke, a.thr, a.mode, a.nflag, a.status, s)
     if (!a.mixed) {
         if (a.npe == 8) FEM_INT(8, double, double, double, false);
         FEM_INT(4, double, double, double, false);

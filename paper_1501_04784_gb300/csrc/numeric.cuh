@@ -43,6 +43,10 @@ struct WaitCtl {
 };
 static constexpr int WAIT_SPINS_DEFAULT = 1 << 20;
 
+// Bits of the mesh's device status word.
+static constexpr int STATUS_TIMEOUT = 1;    // a bounded device-side wait gave up
+static constexpr int STATUS_NONFINITE = 2;  // an element matrix was not finite (zero det J, non-finite input)
+
 struct IntegrateArgs {
     int npe;
     bool mixed;
@@ -53,7 +57,8 @@ struct IntegrateArgs {
     void *ke;
     float thr;
     unsigned long long *nflag;
-    unsigned mode = 0;  // FP64_DETS, OP_MASS
+    unsigned mode = 0;     // FP64_DETS, OP_MASS
+    int *status = nullptr;  // STATUS_NONFINITE is or-ed in here
 };
 
 struct PatchArgs {

@@ -291,3 +291,26 @@ def test_host_async_two_streams(fem):
     assert torch.equal(outs[0], ref)
     with pytest.raises(abi.FemError, match="FEM_ERR_ARG"):
         mesh.build_K_host_async(Xd.cpu(), cd.cpu(), "mixed")
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_zero_volume_element_is_reported(fem, prec):
+    """A brick flattened to zero volume has no finite element matrix: the build
+    finishes, fem_sync reports FEM_ERR_DEGENERATE once (status cleared), and a
+    valid build on the same context afterwards is correct."""
+    from paper_1501_04784_gb300 import abi
+    m = MESHES["hex_7x5x3"]()
+    X = m.X.copy()
+    e0 = m.E[0]
+    X[e0, 2] = X[e0[0], 2]             # all 8 nodes of element 0 in one z plane
+    bad = make(fem, m)
+    dt = torch.float32 if prec == "mixed" else torch.float64
+    bad.build_K(dev(X, dt), dev(m.c, dt), prec)
+    with pytest.raises(abi.FemError, match="FEM_ERR_DEGENERATE"):
+        bad.sync()
+    bad.sync()
+    Xd, cd, Xr, c = inputs(m, prec)
+    vals = bad.build_K(Xd, cd, prec)
+    bad.sync()
+    ref = oracle_K(m, Xr, c)
+    assert rel_err(vals.cpu().numpy(), ref["vals"], ref["cs"]) <= (TOL_FP64 if prec == "fp64" else TOL_MIXED)
