@@ -55,7 +55,8 @@ typedef struct fem_mesh_s *fem_mesh; /* opaque, library-owned */
 typedef enum {
     FEM_OK = 0,
     FEM_ERR_ARG = 1,         /* null or misaligned pointer, bad size, bad enum value */
-    FEM_ERR_INDEX = 2,       /* a node id in E outside [0, n_nodes) */
+    FEM_ERR_INDEX = 2,       /* a node id in E outside [0, n_nodes); in the bounds-check build,
+                                also an out-of-range index met inside a patch kernel */
     FEM_ERR_DEGENERATE = 3,  /* a node repeated within one element (fem_mesh_create), or an
                                 element matrix that is not finite: zero volume, non-finite
                                 input (reported by fem_sync after the build) */
@@ -96,7 +97,11 @@ typedef struct {
                                     gives up (0 = default 2^20); a wait that gives up is reported
                                     by fem_sync as FEM_ERR_TIMEOUT */
     int debug_stall;             /* testing only: 1 = warp 0 of every block waits once for a
-                                    phase that cannot complete, so that the wait gives up */
+                                    phase that cannot complete, so that the wait gives up;
+                                    2 (library built with -DFEM_DEBUG_BOUNDS only, else
+                                    FEM_ERR_ARG) = one out-of-range node id is planted per
+                                    block, caught by the bounds checks of that build and
+                                    reported by fem_sync as FEM_ERR_INDEX */
     int operator_kind;           /* 0 (default) = stiffness matrix k_e = c int B^T B (Eq. 9);
                                     1 = mass matrix m_e = c int N^T N (the other operator the
                                     paper's construction generalises to, Section 5): same

@@ -3,6 +3,11 @@
 Each ``csrc/*.cu`` translation unit is compiled in parallel to an object in
 ``_build/``, then linked into ``_build/libfem.so``.  Objects are rebuilt only
 when a source or header is newer.
+
+With ``FEM_DEBUG_BOUNDS=1`` in the environment the same sources are built with
+``-DFEM_DEBUG_BOUNDS`` into ``_build/debug/libfem.so`` and that library is the
+one loaded: the bounds-check build, in which the patch kernels test every index
+taken from plan data before using it and report a bad one as FEM_ERR_INDEX.
 """
 from __future__ import annotations
 
@@ -14,8 +19,10 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-OUT = os.path.join(HERE, "_build")
+DEBUG_BOUNDS = os.environ.get("FEM_DEBUG_BOUNDS", "0") not in ("", "0")
+OUT = os.path.join(HERE, "_build", "debug") if DEBUG_BOUNDS else os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfem.so")
+DEBUG_FLAGS = ["-DFEM_DEBUG_BOUNDS"] if DEBUG_BOUNDS else []
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-I", os.path.join(ROOT, "include")]
@@ -43,7 +50,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
         if not force and os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_t):
             return obj
-        cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj + ".tmp"]
+        cmd = [nvcc(), *ARCH, *FLAGS, *DEBUG_FLAGS, *extra, "-c", src, "-o", obj + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

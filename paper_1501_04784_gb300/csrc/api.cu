@@ -81,6 +81,11 @@ fem_status check_status(fem_mesh m, cudaStream_t s) {
     if (h == 0) return FEM_OK;
     FEM_CUDA(cudaMemsetAsync(m->status.ptr, 0, sizeof(int), s));
     FEM_CUDA(cudaStreamSynchronize(s));
+    if (h & STATUS_BOUNDS) {
+        set_error("bounds-check build: a patch kernel met an out-of-range index (caught, the access skipped); "
+                  "the values of that build are undefined");
+        return FEM_ERR_INDEX;
+    }
     if (h & STATUS_NONFINITE) {
         set_error("an element matrix was not finite (an element with a zero Jacobian determinant, or non-finite "
                   "coordinates or coefficients); the values of that build are undefined");
@@ -166,6 +171,16 @@ fem_status fem_mesh_create(fem_mesh *out, fem_elem type, int64_t n_nodes, int64_
     if (m->opt.operator_kind != 0 && m->opt.operator_kind != 1) {
         delete m;
         set_error("operator_kind must be 0 (stiffness) or 1 (mass)");
+        return FEM_ERR_ARG;
+    }
+#ifdef FEM_DEBUG_BOUNDS
+    const int max_stall = 2;
+#else
+    const int max_stall = 1;
+#endif
+    if (m->opt.debug_stall < 0 || m->opt.debug_stall > max_stall) {
+        delete m;
+        set_error("debug_stall must be 0 or 1 (2 only in the bounds-check build)");
         return FEM_ERR_ARG;
     }
     m->arena.budget = m->opt.mem_budget_bytes;

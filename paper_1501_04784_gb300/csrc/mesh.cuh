@@ -42,6 +42,7 @@ struct PlanView {
     // diagonal is summed FP64-accurately.
     const uint32_t *celem_aidx;
     int64_t aidx_n;                  // total celems (the word stride)
+    int64_t n_nodes, n_elems, nnz;   // sizes of X, c and vals (bounds checks of the debug build)
 };
 
 // Marker bit of celem_aidx's FP64-accurate diagonals; scratch accumulators per block.
@@ -74,6 +75,7 @@ struct Closure {
 struct Plan {
     int64_t n_patches = 0;
     int64_t max_acc = 0, max_own = 0;
+    int64_t n_nodes = 0, n_elems = 0, nnz = 0;
     int pos_stride = 0;
     bool any_hv = false;  // some row's diagonal is summed FP64-accurately (mixed)
     DevBuf<int64_t> patch_node_ptr, own_rowptr;
@@ -103,6 +105,9 @@ struct Plan {
         v.n_patches = cl.p1 - cl.p0;
         v.celem_aidx = cl.celem_aidx.ptr;
         v.aidx_n = cl.total_celems;
+        v.n_nodes = n_nodes;
+        v.n_elems = n_elems;
+        v.nnz = nnz;
         return v;
     }
     PlanView view() const { return view(full); }

@@ -52,6 +52,16 @@ __device__ __forceinline__ void load_lnodes(const uint16_t *__restrict__ L, int6
     }
 }
 
+// Bounds-check build (-DFEM_DEBUG_BOUNDS, a stand-in for a memory checker): every
+// index that comes from plan data is tested against its array before the access;
+// a bad one sets STATUS_BOUNDS in the status word (fem_sync: FEM_ERR_INDEX) and
+// the access is skipped.  In the normal build the tests compile away.
+#ifdef FEM_DEBUG_BOUNDS
+#define FEM_IN_BOUNDS(cond, status) ((cond) ? true : (atomicOr((status), STATUS_BOUNDS), false))
+#else
+#define FEM_IN_BOUNDS(cond, status) true
+#endif
+
 // Element matrix in the arithmetic of the precision mode.  FP64: everything in
 // double.  MIXED: float, FP64 Jacobians for distorted elements.
 template <int NPE, typename AccT, typename S, bool MIXED, typename CT>
@@ -143,7 +153,11 @@ __host__ __device__ constexpr int tri_row(int q) {
 template <int NPE, typename AccT, bool MIXED>
 __device__ __forceinline__ void scatter_element(const uint32_t (&aw)[NPE * (NPE + 1) / 4], const int32_t *roff,
                                                 void *hv, bool fp64_sums, AccT *acc,
-                                                const AccT (&kv)[NPE * (NPE + 1) / 2]) {
+                                                const AccT (&kv)[NPE * (NPE + 1) / 2], int acc_cap, int nown,
+                                                int *status) {
+    (void)acc_cap;
+    (void)nown;
+    (void)status;
     constexpr int NP = NPE * (NPE + 1) / 2;
     constexpr int G = 12;
 #pragma unroll
@@ -159,6 +173,7 @@ __device__ __forceinline__ void scatter_element(const uint32_t (&aw)[NPE * (NPE 
                 if (q == a * (a + 1) / 2 + a && t >= AIDX_HV) {
                     // a diagonal summed FP64-accurately
                     const int k = (int)(t & 0x7fffu);
+                    if (!FEM_IN_BOUNDS(k < nown, status)) continue;
                     if constexpr (MIXED) {
                         if (fp64_sums) static_cast<double *>(hv)[k] += (double)kv[q];
                         else two_sum_acc(static_cast<float2 *>(hv)[k], (float)kv[q]);
@@ -168,6 +183,7 @@ __device__ __forceinline__ void scatter_element(const uint32_t (&aw)[NPE * (NPE 
                 } else {
                     idx[j] = (int)t;  // owned entry, or the lane's scratch slot
                 }
+                if (idx[j] >= 0 && !FEM_IN_BOUNDS(idx[j] < acc_cap, status)) idx[j] = -1;
             }
         }
         AccT old[G];
@@ -321,7 +337,12 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
 #pragma unroll
                 for (int k = 0; k < CH; ++k) {
                     const int j = j0 + k * nthr + tid;
-                    const int64_t g = j < ncn ? gid[j] : 0;
+                    int64_t g = j < ncn ? gid[j] : 0;
+#ifdef FEM_DEBUG_BOUNDS
+                    // testing the checks: one planted out-of-range node id per block
+                    if (wc.stall == 2 && j == 0) g = pv.n_nodes;
+#endif
+                    if (!FEM_IN_BOUNDS(g >= 0 && g < pv.n_nodes, wc.status)) g = 0;
                     v[k][0] = j < ncn ? __ldg(X + 3 * g + 0) : S(0);
                     v[k][1] = j < ncn ? __ldg(X + 3 * g + 1) : S(0);
                     v[k][2] = j < ncn ? __ldg(X + 3 * g + 2) : S(0);
@@ -387,6 +408,7 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
             CT ce = CT(0);
             if constexpr (FUSED) {
                 ce = c_n1;
+                if (!FEM_IN_BOUNDS(eid_n2 < pv.n_elems, wc.status)) eid_n2 = -1;
                 c_n1 = eid_n2 >= 0 ? __ldg(c + eid_n2) : CT(0);
                 const int i2 = i + 2 * nthr;
                 eid_n2 = i2 < nel ? pv.celem_id[eb + i2] : -1;
@@ -396,6 +418,7 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
                     S xc[NPE][3];
 #pragma unroll
                     for (int a = 0; a < NPE; ++a) {
+                        if (!FEM_IN_BOUNDS(ln[a] < ncn, wc.status)) ln[a] = 0;
                         xc[a][0] = xs[ln[a]][0];
                         xc[a][1] = xs[ln[a]][1];
                         xc[a][2] = xs[ln[a]][2];
@@ -404,7 +427,8 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
                     // k_00 (m_00) is positive and finite for any element of nonzero volume
                     if (!isfinite(kv[0])) atomicOr(wc.status, STATUS_NONFINITE);
                 } else {
-                    const int64_t e = pv.celem_id[ci];
+                    int64_t e = pv.celem_id[ci];
+                    if (!FEM_IN_BOUNDS(e >= 0 && e < pv.n_elems, wc.status)) e = 0;
 #pragma unroll
                     for (int q = 0; q < NP; ++q) kv[q] = __ldg(ke + e * NP + q);
                 }
@@ -419,12 +443,12 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
             const int last = min(base + nthr, nel) - 1;
             const int c0 = pv.celem_color[eb + base], c1 = pv.celem_color[eb + last];
             // testing: phase g cannot complete while warp 0 waits before arriving at it
-            if (wc.stall && base == 0 && warp == 0) phase_wait(mb, g, wc);
+            if (wc.stall == 1 && base == 0 && warp == 0) phase_wait(mb, g, wc);
             for (int cc = c0; cc <= c1; ++cc, ++g) {
                 const bool mine = mycol == cc;
                 if (__any_sync(0xffffffffu, mine)) {
                     if (g > 0) phase_wait(mb, g - 1, wc);
-                    if (mine) scatter_element<NPE, AccT, MIXED>(aw, roff, hv, fp64_sums, acc, kv);
+                    if (mine) scatter_element<NPE, AccT, MIXED>(aw, roff, hv, fp64_sums, acc, kv, L.acc_cap, nown, wc.status);
                     __syncwarp();
                 }
                 if (g >= (uint32_t)PHASE_RING) phase_wait(mb, g - PHASE_RING, wc);
@@ -439,7 +463,10 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
         const int gsh = L.wg_shift, gsz = 1 << gsh;
         const int rows_step = nwarps << (5 - gsh);
         for (int k = (warp << (5 - gsh)) + (lane >> gsh); k < nown; k += rows_step) {
-            const int o0 = roff[k], len = roff[k + 1] - o0;
+            int o0 = roff[k], len = roff[k + 1] - o0;
+            if (!FEM_IN_BOUNDS(o0 >= 0 && len >= 0 && o0 + len <= L.acc_cap && rps[k] >= 0 && rps[k] + len <= pv.nnz,
+                               wc.status))
+                len = 0;
             AccT *dst = vals + rps[k];
             const AccT *src = acc + o0;
             // the diagonal (last entry of a lower row) of a high-valence row comes
@@ -548,6 +575,7 @@ PatchSmem patch_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsi
     const size_t accsz = mixed ? sizeof(float) : sizeof(double);
     size_t o = 0;
     L.acc = o;
+    L.acc_cap = (int)(P.max_acc + ACC_SCRATCH);
     o = align16(o + (size_t)(P.max_acc + ACC_SCRATCH) * accsz);
     L.hv = o;
     L.hv_on = mixed && P.any_hv;

@@ -23,6 +23,7 @@ int patch_blocks_per_sm(int npe, int threads);
 struct PatchSmem {
     size_t acc, hv, xs, cown, roff, hvf, rps, gid, eid, cvs, total;
     int wg_shift;  // log2 of the lanes that store one owned row
+    int acc_cap;   // accumulators a block holds (largest patch + scratch slots)
     int hv_on;     // the hv region exists (some owned row has an FP64-accurate diagonal)
 };
 
@@ -34,8 +35,9 @@ static constexpr unsigned FP64_SUMS = 1u, FP64_DETS = 2u, OP_MASS = 4u;
 // Device-side waits of the patch kernels (colour phases on mbarriers): each wait
 // polls at most `spins` times, then records the failure in *status (read by
 // fem_sync as FEM_ERR_TIMEOUT) and lets the thread go on, so the kernel ends.
-// `stall` (testing) makes warp 0 of every block wait once for a phase that
-// cannot complete, to exercise that path.
+// `stall` (testing) = 1 makes warp 0 of every block wait once for a phase that
+// cannot complete, to exercise that path; = 2 (bounds-check build only) plants
+// one out-of-range node id per block, to exercise the bounds checks.
 struct WaitCtl {
     int *status;
     int spins;
@@ -46,6 +48,7 @@ static constexpr int WAIT_SPINS_DEFAULT = 1 << 20;
 // Bits of the mesh's device status word.
 static constexpr int STATUS_TIMEOUT = 1;    // a bounded device-side wait gave up
 static constexpr int STATUS_NONFINITE = 2;  // an element matrix was not finite (zero det J, non-finite input)
+static constexpr int STATUS_BOUNDS = 4;     // bounds-check build: an out-of-range index, caught and skipped
 
 struct IntegrateArgs {
     int npe;

@@ -920,6 +920,9 @@ fem_status build_plan(fem_mesh m, cudaStream_t s) {
         if (np0 * 2 > wave) cap_eff = std::max<int64_t>(1, cdiv(m->nnz, cdiv(np0, wave) * wave));
     }
     P.n_patches = m->nnz > 0 ? cdiv(m->nnz, cap_eff) : 1;
+    P.n_nodes = m->n_nodes;
+    P.n_elems = m->n_elems;
+    P.nnz = m->nnz;
     const int64_t npatch = P.n_patches;
     if (npatch >= (1ll << 23)) {
         set_error("too many patches (%lld)", (long long)npatch);
