@@ -14,7 +14,9 @@ orderings of the benchmark configurations:
   node / element numbering, c_e laws;
 * ``kuhn_tets`` -- the same grid with every cell split into 6 tetrahedra along
   its main diagonal;
-* ``batch_specs`` -- grid shapes for a batch of uneven meshes.
+* ``batch_specs`` -- grid shapes for a batch of uneven meshes;
+* ``lame`` -- per-element Lame parameters (lambda, mu) for the elasticity
+  operator: Young's modulus c_e and a seeded Poisson ratio per element.
 
 Randomness is counter-based SplitMix64 (Steele, Lea & Flood 2014): value i of
 stream (seed, name) is mix(key + (i + 1) * 0x9E3779B97F4A7C15), so every draw
@@ -250,3 +252,15 @@ def batch_meshes(n_meshes: int = 512, seed: int = BASE_SEED + 3, jitter: float =
     specs = batch_specs(n_meshes, seed=seed)
     return [hex_grid(nx, ny, nz, jitter=jitter, seed=seed * 1000 + m, c_sigma=sigma)
             for m, (nx, ny, nz) in enumerate(specs)]
+
+
+def lame(m: "Mesh", seed: int | None = None, nu_lo: float = 0.1, nu_hi: float = 0.45) -> np.ndarray:
+    """[n_elems, 2] Lame parameters (lambda_e, mu_e) of an isotropic material with
+    Young's modulus c_e and Poisson ratio nu_e ~ U[nu_lo, nu_hi] (stream "nu"):
+    lambda = E nu / ((1 + nu)(1 - 2 nu)), mu = E / (2 (1 + nu))."""
+    seed = m.meta.get("seed", BASE_SEED) if seed is None else seed
+    nu = nu_lo + (nu_hi - nu_lo) * stream_uniform(seed, "nu", m.E.shape[0])
+    E = np.asarray(m.c, np.float64)
+    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    mu = E / (2.0 * (1.0 + nu))
+    return np.ascontiguousarray(np.stack([lam, mu], axis=1))

@@ -39,24 +39,31 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def declare(L):
+    """Declares the argument types of the oracle's C routines on a loaded library
+    (this one, or a test's copy built from a modified source)."""
+    L.oracle_ke_dense.argtypes = [_int, _int, _p, ctypes.c_double, _p]
+    L.oracle_ke_dense.restype = _int
+    L.oracle_ke_elastic_dense.argtypes = [_int, _p, ctypes.c_double, ctypes.c_double, _p]
+    L.oracle_ke_elastic_dense.restype = _int
+    L.oracle_ke_packed.argtypes = [_int, _int, _i64, _p, _p, _p, _p, _p]
+    L.oracle_ke_packed.restype = _i64
+    L.oracle_triplets.argtypes = [_int, _int, _i64, _p, _p, _p, _p, _p, _p, _p]
+    L.oracle_triplets.restype = _i64
+    L.oracle_compress.argtypes = [_i64, _i64, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]
+    L.oracle_compress.restype = _i64
+    L.oracle_vjp.argtypes = [_int, _i64, _p, _p, _p, _p, _p, _p]
+    L.oracle_vjp.restype = None
+    L.oracle_load.argtypes = [_int, _i64, _p, _p, _p, _p]
+    L.oracle_load.restype = _i64
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = ctypes.CDLL(_LIB_PATH)
-        L.oracle_ke_dense.argtypes = [_int, _int, _p, ctypes.c_double, _p]
-        L.oracle_ke_dense.restype = _int
-        L.oracle_ke_packed.argtypes = [_int, _int, _i64, _p, _p, _p, _p, _p]
-        L.oracle_ke_packed.restype = _i64
-        L.oracle_triplets.argtypes = [_int, _int, _i64, _p, _p, _p, _p, _p, _p, _p]
-        L.oracle_triplets.restype = _i64
-        L.oracle_compress.argtypes = [_i64, _i64, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]
-        L.oracle_compress.restype = _i64
-        L.oracle_vjp.argtypes = [_int, _i64, _p, _p, _p, _p, _p, _p]
-        L.oracle_vjp.restype = None
-        L.oracle_load.argtypes = [_int, _i64, _p, _p, _p, _p]
-        L.oracle_load.restype = _i64
-        _lib = L
+        _lib = declare(ctypes.CDLL(_LIB_PATH))
     return _lib
 
 
@@ -71,12 +78,19 @@ def _inputs(X, E, c):
     return X, E, c
 
 
-def npairs(npe: int) -> int:
-    return npe * (npe + 1) // 2
+# Operators: the stiffness matrix of Eq. 9, the mass matrix (Section 5) and
+# linear elasticity (three DOFs per node; c is then [n_elems, 2] = (lambda, mu)).
+OPS = {"stiffness": 0, "mass": 1, "elasticity": 2}
 
 
-# Operators: the stiffness matrix of Eq. 9 and the mass matrix (Section 5).
-OPS = {"stiffness": 0, "mass": 1}
+def dofs(op: str = "stiffness") -> int:
+    """Degrees of freedom per node (Algorithm 1's DOFxn)."""
+    return 3 if op == "elasticity" else 1
+
+
+def npairs(npe: int, op: str = "stiffness") -> int:
+    nk = dofs(op) * npe
+    return nk * (nk + 1) // 2
 
 
 def ke_dense(npe: int, xe, c: float, op: str = "stiffness") -> np.ndarray:
@@ -87,13 +101,22 @@ def ke_dense(npe: int, xe, c: float, op: str = "stiffness") -> np.ndarray:
     return ke
 
 
+def ke_elastic_dense(npe: int, xe, lam: float, mu: float) -> np.ndarray:
+    """Dense (3 npe) x (3 npe) elasticity matrix of one element (DOF 3a + i)."""
+    xe = np.ascontiguousarray(xe, dtype=np.float64).reshape(npe, 3)
+    ke = np.zeros((3 * npe, 3 * npe))
+    lib().oracle_ke_elastic_dense(npe, _ptr(xe), float(lam), float(mu), _ptr(ke))
+    return ke
+
+
 def ke_packed(npe: int, X, E, c, op: str = "stiffness"):
-    """Packed lower k_e [n_elems, npe(npe+1)/2] (p = a(a+1)/2 + b), the Cauchy-Schwarz
-    scales sqrt(k_aa k_bb) of each entry, and the number of elements with det J <= 0."""
+    """Packed lower k_e [n_elems, nk(nk+1)/2] (p = A(A+1)/2 + B over the nk local
+    DOFs), the Cauchy-Schwarz scales sqrt(k_AA k_BB) of each entry, and the number
+    of elements with det J <= 0."""
     X, E, c = _inputs(X, E, c)
     n = E.shape[0]
-    ke = np.zeros((n, npairs(npe)))
-    cs = np.zeros((n, npairs(npe)))
+    ke = np.zeros((n, npairs(npe, op)))
+    cs = np.zeros((n, npairs(npe, op)))
     bad = lib().oracle_ke_packed(OPS[op], npe, n, _ptr(E), _ptr(X), _ptr(c), _ptr(ke), _ptr(cs))
     return ke, cs, int(bad)
 
@@ -101,7 +124,7 @@ def ke_packed(npe: int, X, E, c, op: str = "stiffness"):
 def triplets(npe: int, X, E, c, op: str = "stiffness"):
     """Algorithm 1's triplet arrays (rows, cols, vals) plus per-triplet scales."""
     X, E, c = _inputs(X, E, c)
-    nt = E.shape[0] * npairs(npe)
+    nt = E.shape[0] * npairs(npe, op)
     rows = np.zeros(nt, np.int64)
     cols = np.zeros(nt, np.int32)
     vals = np.zeros(nt)
@@ -113,7 +136,8 @@ def triplets(npe: int, X, E, c, op: str = "stiffness"):
 
 def compress(n_nodes: int, rows, cols, vals, cs):
     """The sparse conversion: lower CSR with per-entry sums of |val| and of scales,
-    and the CSR slot of every triplet."""
+    and the CSR slot of every triplet (n_nodes = number of rows: nodes times DOFs
+    per node)."""
     nt = rows.shape[0]
     rowptr = np.zeros(n_nodes + 1, np.int64)
     col = np.zeros(max(nt, 1), np.int32)
@@ -128,14 +152,15 @@ def compress(n_nodes: int, rows, cols, vals, cs):
 
 
 def build_K(npe: int, X, E, c, op: str = "stiffness"):
-    """Algorithm 1 end to end: global lower-triangular CSR K (or M, op="mass") in FP64.
+    """Algorithm 1 end to end: global lower-triangular CSR K (or M, op="mass"; or
+    the 3N x 3N elasticity matrix, op="elasticity") in FP64.
 
     Returns a dict with rowptr, col, vals, abs (sum of |contribution|), cs (sum of
     Cauchy-Schwarz scales), slot (CSR position of each packed (e, p)), nnz, and
     n_bad (elements with a non-positive Jacobian determinant)."""
     X, E, c = _inputs(X, E, c)
     rows, cols, vals, cs, bad = triplets(npe, X, E, c, op)
-    out = compress(X.shape[0], rows, cols, vals, cs)
+    out = compress(X.shape[0] * dofs(op), rows, cols, vals, cs)
     out["n_bad"] = bad
     return out
 

@@ -21,6 +21,11 @@
  *     sort by (row, col) and a sum of repeated entries in emission order
  *     (footnote on the triplet format), giving a lower-triangular CSR matrix.
  *   - Eq. 6 as the sum K = sum_e k_e is exactly what that conversion produces.
+ *   - the mass matrix m_e = c * integral N^T N (the generalisation of Section 5)
+ *     and the load vector of a per-element source (Section 1, steps (ii)-(iii));
+ *   - linear isotropic elasticity, three DOFs per node (Algorithm 1's DOFxn),
+ *     k_e = integral Be^T D Be with the same quadrature, assembled through the
+ *     same triplets and conversion over DOFs;
  *   - the gradient of L = sum over stored entries of G_ij K_ij with respect to
  *     the node coordinates, by the complex-step derivative of the element
  *     routine, and with respect to c_e (k_e is linear in c_e).
@@ -208,16 +213,126 @@ static int me_tet(const double xe[12], double c, double me[16]) {
     return det <= 0 ? 1 : 0;
 }
 
-/* Operators: 0 = stiffness k_e (Eq. 9), 1 = mass m_e. */
-static int element_dense(int op, int npe, const double *xe, double c, double *ke) {
-    if (op == 1) return npe == 8 ? me_brick(xe, c, ke) : me_tet(xe, c, ke);
-    return npe == 8 ? ke_brick_d(xe, c, ke) : ke_tet_d(xe, c, ke);
+/*
+ * Linear isotropic elasticity: the vector problem with three degrees of freedom
+ * per node (Algorithm 1 maps local to global DOFs through the number of DOFs per
+ * node, DOFxn; the paper itself only builds the scalar case, Section 3).  The
+ * operator is the textbook one, not taken from the paper:
+ *   k_e = integral Be^T D Be dOmega,
+ * Be the 6 x 3npe strain-displacement matrix in Voigt order (e_xx, e_yy, e_zz,
+ * g_xy, g_yz, g_zx, engineering shears g = 2 e) built from the physical
+ * gradients B = J^{-1} dN of the scalar routine, and D the isotropic material
+ * matrix of the element's Lame parameters (lambda, mu): lambda + 2 mu on the
+ * normal diagonal, lambda off it, mu on the shear diagonal.  Local DOF 3a + i is
+ * component i of node a.  Same Gauss rule, |det J| and node order as k_e of
+ * Eq. 9; the tetrahedron's integrand is constant (1 point, weight 1/6).
+ * ke is the dense (3npe) x (3npe) matrix.  Returns the number of points with
+ * det J <= 0.
+ */
+static void elastic_add(int npe, const double B[3][8], double w, double lam, double mu, double *ke) {
+    const int nk = 3 * npe;
+    double Be[6][24];
+    for (int k = 0; k < 6; ++k)
+        for (int A = 0; A < nk; ++A) Be[k][A] = 0.0;
+    for (int a = 0; a < npe; ++a) {
+        Be[0][3 * a + 0] = B[0][a];
+        Be[1][3 * a + 1] = B[1][a];
+        Be[2][3 * a + 2] = B[2][a];
+        Be[3][3 * a + 0] = B[1][a]; Be[3][3 * a + 1] = B[0][a];
+        Be[4][3 * a + 1] = B[2][a]; Be[4][3 * a + 2] = B[1][a];
+        Be[5][3 * a + 0] = B[2][a]; Be[5][3 * a + 2] = B[0][a];
+    }
+    double D[6][6];
+    for (int k = 0; k < 6; ++k)
+        for (int l = 0; l < 6; ++l) D[k][l] = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        for (int l = 0; l < 3; ++l) D[k][l] = lam;
+        D[k][k] = lam + 2.0 * mu;
+        D[k + 3][k + 3] = mu;
+    }
+    for (int A = 0; A < nk; ++A)
+        for (int Bc = 0; Bc < nk; ++Bc) {
+            double acc = 0.0;
+            for (int k = 0; k < 6; ++k)
+                for (int l = 0; l < 6; ++l) acc += Be[k][A] * D[k][l] * Be[l][Bc];
+            ke[nk * A + Bc] += w * acc;
+        }
 }
 
-/* Full dense element matrix of one element (row-major npe x npe). */
+static int ke_elastic(int npe, const double *xe, double lam, double mu, double *ke) {
+    const int nk = 3 * npe;
+    int nonpos = 0;
+    for (int i = 0; i < nk * nk; ++i) ke[i] = 0.0;
+    if (npe == 8) {
+        const double g = 1.0 / sqrt(3.0);
+        const double pts[2] = {-g, g};
+        for (int ir = 0; ir < 2; ++ir)
+            for (int is = 0; is < 2; ++is)
+                for (int it = 0; it < 2; ++it) {
+                    const double r = pts[ir], s = pts[is], t = pts[it];
+                    double dN[3][8];
+                    for (int a = 0; a < 8; ++a) {
+                        const double ra = BRICK_NODES[a][0], sa = BRICK_NODES[a][1], ta = BRICK_NODES[a][2];
+                        dN[0][a] = 0.125 * ra * (1 + s * sa) * (1 + t * ta);
+                        dN[1][a] = 0.125 * sa * (1 + r * ra) * (1 + t * ta);
+                        dN[2][a] = 0.125 * ta * (1 + r * ra) * (1 + s * sa);
+                    }
+                    double J[3][3];
+                    for (int i = 0; i < 3; ++i)
+                        for (int j = 0; j < 3; ++j) {
+                            double acc = 0;
+                            for (int a = 0; a < 8; ++a) acc += dN[i][a] * xe[3 * a + j];
+                            J[i][j] = acc;
+                        }
+                    double det, inv[3][3], B[3][8];
+                    inv3_d(J, &det, inv);
+                    if (det <= 0) ++nonpos;
+                    for (int i = 0; i < 3; ++i)
+                        for (int a = 0; a < 8; ++a) {
+                            double acc = 0;
+                            for (int k = 0; k < 3; ++k) acc += inv[i][k] * dN[k][a];
+                            B[i][a] = acc;
+                        }
+                    elastic_add(8, B, fabs(det), lam, mu, ke);
+                }
+    } else {
+        double J[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) J[i][j] = xe[3 * (i + 1) + j] - xe[j];
+        double det, inv[3][3], B[3][8];
+        inv3_d(J, &det, inv);
+        if (det <= 0) ++nonpos;
+        for (int i = 0; i < 3; ++i)
+            for (int a = 0; a < 4; ++a) {
+                double acc = 0;
+                for (int k = 0; k < 3; ++k) acc += inv[i][k] * TET_DL[k][a];
+                B[i][a] = acc;
+            }
+        elastic_add(4, B, fabs(det) / 6.0, lam, mu, ke);
+    }
+    return nonpos;
+}
+
+/* Operators: 0 = stiffness k_e (Eq. 9), 1 = mass m_e, 2 = elasticity (3 DOFs per
+ * node).  cv = the element's coefficients: c_e, or (lambda_e, mu_e) for op 2. */
+static int op_dofs(int op) { return op == 2 ? 3 : 1; }
+
+static int element_dense(int op, int npe, const double *xe, const double *cv, double *ke) {
+    if (op == 2) return ke_elastic(npe, xe, cv[0], cv[1], ke);
+    if (op == 1) return npe == 8 ? me_brick(xe, cv[0], ke) : me_tet(xe, cv[0], ke);
+    return npe == 8 ? ke_brick_d(xe, cv[0], ke) : ke_tet_d(xe, cv[0], ke);
+}
+
+/* Full dense element matrix of one element (row-major npe x npe), ops 0 and 1. */
 int oracle_ke_dense(int op, int npe, const double *xe, double c, double *ke) {
     if ((npe != 8 && npe != 4) || (op != 0 && op != 1)) return -1;
-    return element_dense(op, npe, xe, c, ke);
+    return element_dense(op, npe, xe, &c, ke);
+}
+
+/* Dense (3npe) x (3npe) elasticity matrix of one element (op 2). */
+int oracle_ke_elastic_dense(int npe, const double *xe, double lam, double mu, double *ke) {
+    if (npe != 8 && npe != 4) return -1;
+    return ke_elastic(npe, xe, lam, mu, ke);
 }
 
 static void gather(int npe, const int32_t *E, const double *X, int64_t e, double *xe) {
@@ -230,25 +345,26 @@ static void gather(int npe, const int32_t *E, const double *X, int64_t e, double
 }
 
 /*
- * Packed lower triangle of every element matrix of operator op: entry
- * p = a(a+1)/2 + b for b <= a (row-major lower order).  cs[p] = sqrt(k_aa k_bb),
- * the Cauchy-Schwarz bound of |k_ab| for the positive semidefinite k_e (or m_e),
- * used to scale errors.
+ * Packed lower triangle of every element matrix of operator op: with nk = DOFs
+ * per element (npe, or 3 npe for op 2), entry p = A(A+1)/2 + B for B <= A
+ * (row-major lower order over local DOFs).  c holds one coefficient per element,
+ * two (lambda, mu) for op 2.  cs[p] = sqrt(k_AA k_BB), the Cauchy-Schwarz bound
+ * of |k_AB| for the positive semidefinite k_e (or m_e), used to scale errors.
  * Returns the number of elements with some det J <= 0.
  */
 int64_t oracle_ke_packed(int op, int npe, int64_t n_elems, const int32_t *E, const double *X,
                          const double *c, double *ke_out, double *cs_out) {
-    const int np = npe * (npe + 1) / 2;
+    const int nk = op_dofs(op) * npe, np = nk * (nk + 1) / 2, nc = op == 2 ? 2 : 1;
     int64_t bad = 0;
-    double xe[24], ke[64];
+    double xe[24], ke[576];
     for (int64_t e = 0; e < n_elems; ++e) {
         gather(npe, E, X, e, xe);
-        if (element_dense(op, npe, xe, c[e], ke) > 0) ++bad;
-        for (int a = 0; a < npe; ++a)
+        if (element_dense(op, npe, xe, c + nc * e, ke) > 0) ++bad;
+        for (int a = 0; a < nk; ++a)
             for (int b = 0; b <= a; ++b) {
                 const int p = a * (a + 1) / 2 + b;
-                ke_out[e * np + p] = ke[npe * a + b];
-                if (cs_out) cs_out[e * np + p] = sqrt(fabs(ke[npe * a + a] * ke[npe * b + b]));
+                ke_out[e * np + p] = ke[nk * a + b];
+                if (cs_out) cs_out[e * np + p] = sqrt(fabs(ke[nk * a + a] * ke[nk * b + b]));
             }
     }
     return bad;
@@ -256,26 +372,29 @@ int64_t oracle_ke_packed(int op, int npe, int64_t n_elems, const int32_t *E, con
 
 /*
  * Algorithm 1, the element loop: for every element (in element order) compute k_e and
- * write its triplets.  The local pair (a, b), b <= a, goes to global
- * (max(g_a, g_b), min(g_a, g_b)) with value k_e[a][b] (k_e is symmetric).
- * rows/cols/vals/cs have room for n_elems * npe(npe+1)/2 entries.
+ * write its triplets.  Mapping(E(e), DOFxn): local DOF A = DOFxn a + i of node a
+ * is global DOF DOFxn g_a + i (components of a node adjacent).  The local pair
+ * (A, B), B <= A, goes to global (max(G_A, G_B), min(G_A, G_B)) with value
+ * k_e[A][B] (k_e is symmetric).  rows/cols/vals/cs have room for
+ * n_elems * nk(nk+1)/2 entries.
  */
 int64_t oracle_triplets(int op, int npe, int64_t n_elems, const int32_t *E, const double *X,
                         const double *c, int64_t *rows, int32_t *cols, double *vals, double *cs) {
-    const int np = npe * (npe + 1) / 2;
+    const int dofxn = op_dofs(op), nk = dofxn * npe, np = nk * (nk + 1) / 2, nc = op == 2 ? 2 : 1;
     int64_t bad = 0;
-    double xe[24], ke[64];
+    double xe[24], ke[576];
     for (int64_t e = 0; e < n_elems; ++e) {
         gather(npe, E, X, e, xe);
-        if (element_dense(op, npe, xe, c[e], ke) > 0) ++bad;
-        for (int a = 0; a < npe; ++a)
+        if (element_dense(op, npe, xe, c + nc * e, ke) > 0) ++bad;
+        for (int a = 0; a < nk; ++a)
             for (int b = 0; b <= a; ++b) {
                 const int64_t t = e * np + a * (a + 1) / 2 + b;
-                const int32_t ga = E[e * npe + a], gb = E[e * npe + b];
+                const int32_t ga = dofxn * E[e * npe + a / dofxn] + a % dofxn;
+                const int32_t gb = dofxn * E[e * npe + b / dofxn] + b % dofxn;
                 rows[t] = ga > gb ? ga : gb;
                 cols[t] = ga > gb ? gb : ga;
-                vals[t] = ke[npe * a + b];
-                cs[t] = sqrt(fabs(ke[npe * a + a] * ke[npe * b + b]));
+                vals[t] = ke[nk * a + b];
+                cs[t] = sqrt(fabs(ke[nk * a + a] * ke[nk * b + b]));
             }
     }
     return bad;
@@ -416,7 +535,8 @@ void oracle_vjp(int npe, int64_t n_elems, const int32_t *E, const double *X, con
     double complex xz[24], kz[64];
     for (int64_t e = 0; e < n_elems; ++e) {
         gather(npe, E, X, e, xe);
-        element_dense(0, npe, xe, 1.0, ke);
+        const double one = 1.0;
+        element_dense(0, npe, xe, &one, ke);
         double l1 = 0.0;
         for (int a = 0; a < npe; ++a)
             for (int b = 0; b <= a; ++b) l1 += S[e * np + a * (a + 1) / 2 + b] * ke[npe * a + b];
