@@ -105,10 +105,30 @@ typedef struct {
     int operator_kind;           /* 0 (default) = stiffness matrix k_e = c int B^T B (Eq. 9);
                                     1 = mass matrix m_e = c int N^T N (the other operator the
                                     paper's construction generalises to, Section 5): same
-                                    quadrature, packing, pattern and assembly; fem_vjp is for
-                                    the stiffness operator only */
+                                    quadrature, packing, pattern and assembly;
+                                    2 = linear isotropic elasticity, three DOFs per node
+                                    (Algorithm 1's Mapping with DOFxn = 3): see "Elasticity"
+                                    below.  fem_vjp is for the stiffness operator only */
     int reserved[4];
 } fem_options;
+
+/*
+ * Elasticity (operator_kind = 2).  k_e = int Be^T D Be: Be the 6 x 3npe strain-
+ * displacement matrix, D the isotropic material matrix of the element's Lame
+ * parameters; the same quadrature and |det J| as Eq. 9.  Degree of freedom 3g + i
+ * is displacement component i of node g.  With it, for every entry point:
+ *   - c is [n_elems][2] = (lambda_e, mu_e), interleaved, in c_dtype;
+ *   - the matrix is the lower triangle of the 3 n_nodes x 3 n_nodes matrix:
+ *     fem_pattern's nnz and fem_get_pattern's rowptr [3 n_nodes + 1] and col [nnz]
+ *     are those of the DOF matrix (node row I of length L gives DOF rows 3I..3I+2
+ *     of 9L - 3 entries in all, row 3I starting at 9 rowptr_node[I] - 3I);
+ *   - fem_integrate_local and fem_assemble_csr use [n_elems][300|78] packed
+ *     entries, p = A(A+1)/2 + B over local DOFs A = 3a + i, B <= A;
+ *   - fem_build_K fuses integration and assembly in both precisions;
+ *   - patch_entries counts node pairs (each a 3x3 block; default 2048);
+ *   - fem_pattern_ptrs, fem_vjp, fem_load_vector and fem_build_K_batched answer
+ *     FEM_ERR_UNSUPPORTED; fem_mesh_create refuses 3 n_nodes >= 2^31.
+ */
 
 typedef struct {
     int64_t n_nodes, n_elems, nnz;

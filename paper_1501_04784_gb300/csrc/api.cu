@@ -27,6 +27,13 @@ static bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_
 
 static size_t dsize(fem_dtype d) { return d == FEM_F64 ? 8 : 4; }
 
+// The elasticity operator: three DOFs per node, (lambda, mu) per element.
+static bool is_elastic(const fem_mesh m) { return m->opt.operator_kind == 2; }
+
+// Entries of the global matrix the caller sees: the node pattern's, or those of
+// the lower DOF matrix (a node row of L entries gives 9 L - 3).
+static int64_t user_nnz(const fem_mesh m) { return is_elastic(m) ? 9 * m->nnz - 3 * m->n_nodes : m->nnz; }
+
 static float default_threshold(const fem_mesh m) {
     if (m->opt.distortion_threshold > 0) return (float)m->opt.distortion_threshold;
     return m->npe == 8 ? 4.0f : 10.0f;
@@ -168,10 +175,15 @@ fem_status fem_mesh_create(fem_mesh *out, fem_elem type, int64_t n_nodes, int64_
     m->E = E;
     if (opt) m->opt = *opt; else fem_options_default(&m->opt);
     if (m->opt.valence_threshold <= 0) m->opt.valence_threshold = 8;
-    if (m->opt.operator_kind != 0 && m->opt.operator_kind != 1) {
+    if (m->opt.operator_kind < 0 || m->opt.operator_kind > 2) {
         delete m;
-        set_error("operator_kind must be 0 (stiffness) or 1 (mass)");
+        set_error("operator_kind must be 0 (stiffness), 1 (mass) or 2 (elasticity)");
         return FEM_ERR_ARG;
+    }
+    if (m->opt.operator_kind == 2 && 3 * n_nodes >= ((int64_t)1 << 31)) {
+        delete m;
+        set_error("elasticity: 3 n_nodes must stay below 2^31 (int32 DOF columns)");
+        return FEM_ERR_UNSUPPORTED;
     }
 #ifdef FEM_DEBUG_BOUNDS
     const int max_stall = 2;
@@ -229,7 +241,7 @@ fem_status fem_pattern(fem_mesh m, int64_t *nnz_out, void *stream) {
             return st;
         }
     }
-    if (nnz_out) *nnz_out = m->nnz;
+    if (nnz_out) *nnz_out = user_nnz(m);
     return FEM_OK;
 }
 
@@ -243,6 +255,7 @@ fem_status fem_get_pattern(fem_mesh m, int64_t *rowptr, int32_t *col, void *stre
         return FEM_ERR_STATE;
     }
     cudaStream_t s = as_stream(stream);
+    if (is_elastic(m)) return launch_dof_pattern(m->rowptr.ptr, m->col.ptr, m->n_nodes, rowptr, col, s);
     if (rowptr)
         FEM_CUDA(cudaMemcpyAsync(rowptr, m->rowptr.ptr, (m->n_nodes + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     if (col && m->nnz)
@@ -259,6 +272,10 @@ fem_status fem_pattern_ptrs(fem_mesh m, const int64_t **rowptr, const int32_t **
         set_error("fem_pattern_ptrs before fem_pattern");
         return FEM_ERR_STATE;
     }
+    if (is_elastic(m)) {
+        set_error("elasticity: the library keeps the node pattern only; use fem_get_pattern for the DOF pattern");
+        return FEM_ERR_UNSUPPORTED;
+    }
     if (rowptr) *rowptr = m->rowptr.ptr;
     if (col) *col = m->col.ptr;
     return FEM_OK;
@@ -273,6 +290,7 @@ fem_status fem_integrate_local(fem_mesh m, fem_prec p, const void *X, fem_dtype 
     }
     IntegrateArgs a{m->npe, p == FEM_MIXED, x_dtype, c_dtype, m->E, m->n_elems, X, c, ke_out,
                     default_threshold(m), nullptr, kernel_mode(m->opt), m->status.ptr};
+    if (is_elastic(m)) return launch_elastic_integrate(a, as_stream(stream));
     return launch_integrate(a, as_stream(stream));
 }
 
@@ -319,9 +337,10 @@ fem_status fem_assemble_csr(fem_mesh m, fem_prec p, const void *ke, void *vals, 
     a.ke = ke;
     a.vals = vals;
     cudaStream_t s = as_stream(stream);
+    const bool el = is_elastic(m);
     return for_each_group(m, s, [&](const Closure &cl) {
         a.closure = &cl;
-        return launch_patch(a, s);
+        return el ? launch_elastic_patch(a, s) : launch_patch(a, s);
     });
 }
 
@@ -338,6 +357,20 @@ fem_status fem_build_K(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype,
         return FEM_ERR_ARG;
     }
     cudaStream_t s = as_stream(stream);
+    if (is_elastic(m)) {
+        // one fused kernel in both precisions (no FP64 staging: 300 doubles per
+        // brick would outweigh the recomputation in each closure)
+        PatchArgs a = patch_args(m, p, true);
+        a.xd = x_dtype;
+        a.cd = c_dtype;
+        a.X = X;
+        a.c = c;
+        a.vals = vals;
+        return for_each_group(m, s, [&](const Closure &cl) {
+            a.closure = &cl;
+            return launch_elastic_patch(a, s);
+        });
+    }
     if (p == FEM_FP64 && !m->plan.chunked && m->opt.fp64_fused == 0) {
         // integrate once into library memory, then assemble (falls back to the
         // fused kernel if the budget refuses the buffer)
@@ -387,8 +420,8 @@ static fem_status host_build(fem_mesh m, fem_prec p, const void *X_host, fem_dty
         return FEM_ERR_ARG;
     }
     const size_t xb = (size_t)m->n_nodes * 3 * dsize(x_dtype);
-    const size_t cb = (size_t)m->n_elems * dsize(c_dtype);
-    const size_t vb = (size_t)m->nnz * (p == FEM_FP64 ? 8 : 4);
+    const size_t cb = (size_t)m->n_elems * (is_elastic(m) ? 2 : 1) * dsize(c_dtype);
+    const size_t vb = (size_t)user_nnz(m) * (p == FEM_FP64 ? 8 : 4);
     const size_t xo = 0, co = (xb + 255) / 256 * 256, vo = co + (cb + 255) / 256 * 256;
     const size_t total = vo + vb;
     const int k = m->stage_next;
@@ -467,6 +500,10 @@ fem_status fem_load_vector(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dt
         set_error("fem_load_vector before fem_pattern");
         return FEM_ERR_STATE;
     }
+    if (is_elastic(m)) {
+        set_error("the load vector covers the scalar operators (one DOF per node)");
+        return FEM_ERR_UNSUPPORTED;
+    }
     if (!F || !aligned(F, p == FEM_FP64 ? 8 : 4)) {
         set_error("F must be a non-null aligned device pointer");
         return FEM_ERR_ARG;
@@ -494,6 +531,11 @@ fem_status fem_build_K_batched(const fem_mesh *meshes, int n, fem_prec p, const 
         }
     }
     if (n == 0) return FEM_OK;
+    for (int i = 0; i < n; ++i)
+        if (is_elastic(meshes[i])) {
+            set_error("mesh %d of the batch: batched builds cover the scalar operators", i);
+            return FEM_ERR_UNSUPPORTED;
+        }
     for (int i = 0; i < n; ++i)
         if (meshes[i]->plan.chunked) {
             set_error("mesh %d of the batch is planned in groups under its memory budget", i);
@@ -528,8 +570,12 @@ fem_status fem_autotune(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype
     }
     cudaStream_t s = as_stream(stream);
     const fem_options keep = m->opt;
-    static const int entries[] = {4096, 6144, 8192, 12288, 16384};
-    static const int threads[] = {128, 256, 512};
+    static const int entries_scalar[] = {4096, 6144, 8192, 12288, 16384};
+    static const int entries_elastic[] = {1024, 1536, 2048, 2560, 3072};
+    static const int threads_scalar[] = {128, 256, 512};
+    static const int threads_elastic[] = {128, 256, 256};
+    const int *entries = is_elastic(m) ? entries_elastic : entries_scalar;
+    const int *threads = is_elastic(m) ? threads_elastic : threads_scalar;
     float best = 1e30f;
     int best_e = 0, best_t = 0, tried = 0;
     cudaEvent_t e0, e1;
@@ -541,11 +587,14 @@ fem_status fem_autotune(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype
     DevBuf<unsigned char> flush;
     const size_t flush_bytes = (size_t)256 << 20;
     if (flush.alloc(m->arena, flush_bytes, "tuner L2 flush") != FEM_OK) cudaGetLastError();
-    for (int pe : entries) {
+    for (int ie = 0; ie < 5; ++ie) {
+        const int pe = entries[ie];
         m->opt = keep;
         m->opt.patch_entries = pe;
         if (build_plan(m, s) != FEM_OK) continue;
-        for (int t : threads) {
+        for (int it = 0; it < 3; ++it) {
+            const int t = threads[it];
+            if (it > 0 && t == threads[it - 1]) continue;
             m->opt.block_threads = t;
             m->opt.blocks_per_sm = 0;
             if (fem_build_K(m, p, X, x_dtype, c, c_dtype, vals, stream) != FEM_OK) continue;
@@ -605,7 +654,7 @@ fem_status fem_mesh_info(fem_mesh m, fem_info *info) {
     std::memset(info, 0, sizeof(*info));
     info->n_nodes = m->n_nodes;
     info->n_elems = m->n_elems;
-    info->nnz = m->nnz;
+    info->nnz = user_nnz(m);
     info->n_patches = m->plan.n_patches;
     info->closure_elems = m->plan.total_celems;
     info->max_patch_entries = m->plan.max_acc;

@@ -129,4 +129,15 @@ inline unsigned kernel_mode(const fem_options &o) {
 fem_status launch_patch(const PatchArgs &a, cudaStream_t s);
 PatchSmem patch_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsize, size_t csize);
 
+// Elasticity operator (three DOFs per node, elastic.cu): the patch kernel over the
+// scalar operator's plan (3x3 block per node-pair slot), the packed element
+// matrices (elastic_np entries each) and the DOF pattern from the node pattern.
+fem_status launch_elastic_patch(const PatchArgs &a, cudaStream_t s);
+fem_status launch_elastic_integrate(const IntegrateArgs &a, cudaStream_t s);
+fem_status launch_dof_pattern(const int64_t *rowptr, const int32_t *col, int64_t n, int64_t *rowptr3, int32_t *col3,
+                              cudaStream_t s);
+PatchSmem elastic_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsize);
+int elastic_threads(int npe, int requested);
+int elastic_blocks_per_sm(int npe, int threads);
+
 }  // namespace fem

@@ -894,7 +894,9 @@ fem_status build_plan(fem_mesh m, cudaStream_t s) {
     Plan &P = m->plan;
     batch_forget(m);  // cached batched launches were sized for the old plan
     P.reset();
-    int64_t cap_entries = m->opt.patch_entries > 0 ? m->opt.patch_entries : 8192;
+    // the elasticity operator holds a 3x3 block per node pair: fewer pairs fit
+    const bool elastic = m->opt.operator_kind == 2;
+    int64_t cap_entries = m->opt.patch_entries > 0 ? m->opt.patch_entries : (elastic ? 2048 : 8192);
     if (cap_entries < 2 * (int64_t)m->max_row_len) cap_entries = 2 * (int64_t)m->max_row_len;
     int64_t cap_eff = cap_entries - m->max_row_len;
     DevBuf<int64_t> pre;
@@ -915,7 +917,17 @@ fem_status build_plan(fem_mesh m, cudaStream_t s) {
     if (m->nnz > 0) {
         int threads = m->opt.block_threads > 0 ? m->opt.block_threads : 256;
         threads = std::min((threads + 31) / 32 * 32, patch_max_threads(m->npe));
-        const int64_t wave = (int64_t)num_sms() * patch_blocks_per_sm(m->npe, threads);
+        int per_sm = 0;
+        if (elastic) {
+            // resident blocks as registers and (about) the accumulators allow
+            threads = elastic_threads(m->npe, m->opt.block_threads);
+            per_sm = elastic_blocks_per_sm(m->npe, threads);
+            const int64_t smem = 36 * (cap_entries + 32) + 16384;
+            per_sm = (int)std::max<int64_t>(1, std::min<int64_t>(per_sm, (228 * 1024) / (smem + 1024)));
+        } else {
+            per_sm = patch_blocks_per_sm(m->npe, threads);
+        }
+        const int64_t wave = (int64_t)num_sms() * per_sm;
         const int64_t np0 = cdiv(m->nnz, cap_eff);
         if (np0 * 2 > wave) cap_eff = std::max<int64_t>(1, cdiv(m->nnz, cdiv(np0, wave) * wave));
     }
@@ -939,7 +951,8 @@ fem_status build_plan(fem_mesh m, cudaStream_t s) {
     FEM_TRY(P.own_acc.alloc(ar, N, "own acc"));
     FEM_TRY(P.own_hv.alloc(ar, N, "own hv"));
     FEM_TRY(P.patch_acc.alloc(ar, npatch, "patch acc"));
-    const int hv_thr = m->opt.valence_threshold;
+    // FP64-accurate diagonals of high-valence rows: scalar operators only
+    const int hv_thr = elastic ? INT32_MAX : m->opt.valence_threshold;
     P.any_hv = m->max_deg > hv_thr;
     k_patch_nodes<<<grid_for(N), TPB, 0, s>>>(m->order.ptr, pre.ptr, P.patch_node_ptr.ptr, N, cap_eff, npatch,
                                               m->rowptr.ptr, m->inc_ptr.ptr, hv_thr, P.node_patch.ptr, P.own_idx.ptr,

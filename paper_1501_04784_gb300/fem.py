@@ -53,7 +53,11 @@ def launch_count(reset: bool = False) -> int:
 
 
 class Mesh:
-    """A mesh handle: E (int32 [n_elems, npe] on the GPU) plus the cached pattern."""
+    """A mesh handle: E (int32 [n_elems, npe] on the GPU) plus the cached pattern.
+
+    With ``operator_kind=2`` (elasticity) the matrix has three DOFs per node (DOF
+    3g + i), c is [n_elems, 2] = (lambda, mu), and the pattern, the values and the
+    packed element matrices are those of the DOF matrix."""
 
     def __init__(self, E: torch.Tensor, n_nodes: int, X: torch.Tensor | None = None, options=None, stream=None,
                  **opts):
@@ -62,13 +66,15 @@ class Mesh:
             raise ValueError("E must be [n_elems, 8] or [n_elems, 4]")
         self.E = E
         self.npe = int(E.shape[1])
-        self.np = self.npe * (self.npe + 1) // 2
         self.n_nodes = int(n_nodes)
         self.n_elems = int(E.shape[0])
         o = options if options is not None else default_options()
         for k, v in opts.items():
             setattr(o, k, v)
         self.options = o
+        self.dofs = 3 if o.operator_kind == 2 else 1      # DOFs per node
+        nk = self.dofs * self.npe
+        self.np = nk * (nk + 1) // 2                        # packed entries of one k_e
         h = ctypes.c_void_p()
         xp = _dev(X, "X") if X is not None else None
         xd = _DT.get(X.dtype, abi.FEM_F64) if X is not None else abi.FEM_F64
@@ -102,7 +108,7 @@ class Mesh:
     def get_pattern(self, stream=None):
         if self.nnz is None:
             self.pattern(stream)
-        rowptr = torch.empty(self.n_nodes + 1, dtype=torch.int64, device=self.E.device)
+        rowptr = torch.empty(self.dofs * self.n_nodes + 1, dtype=torch.int64, device=self.E.device)
         col = torch.empty(max(self.nnz, 1), dtype=torch.int32, device=self.E.device)
         abi.check(abi.load().fem_get_pattern(self._h, _dev(rowptr, "rowptr"), _dev(col, "col"), _stream(stream)))
         return rowptr, col[: self.nnz]

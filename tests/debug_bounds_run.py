@@ -12,6 +12,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 import meshgen  # noqa: E402
+import oracle  # noqa: E402
 from helpers import TOL_FP64, TOL_MIXED, oracle_K, rel_err, rounded_inputs  # noqa: E402
 
 
@@ -48,6 +49,20 @@ def main():
             out["clean"][f"{name}_{prec}"] = bool(
                 rel_err(fused, ref["vals"], ref["cs"]) <= tol and rel_err(staged, ref["vals"], ref["cs"]) <= tol
                 and all(np.array_equal(b.cpu().numpy(), fused) for b in batched))
+    # the elasticity operator's patch kernel, fused and staged
+    for name, (npe, m) in meshes.items():
+        lame = meshgen.lame(m)
+        X32, c32 = m.X.astype(np.float32), lame.astype(np.float32)
+        ref = oracle.build_K(npe, X32.astype(np.float64), m.E, c32.astype(np.float64), op="elasticity")
+        mesh = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), patch_entries=48,
+                        operator_kind=2)
+        Xd, cd = dev(X32, torch.float32), dev(c32, torch.float32)
+        fused = mesh.build_K(Xd, cd, "mixed").cpu().numpy()
+        mesh.sync()
+        staged = mesh.assemble_csr(mesh.integrate_local(Xd, cd, "mixed"), "mixed").cpu().numpy()
+        mesh.sync()
+        out["clean"][f"{name}_elastic"] = bool(rel_err(fused, ref["vals"], ref["cs"]) <= TOL_MIXED
+                                               and rel_err(staged, ref["vals"], ref["cs"]) <= TOL_MIXED)
     # one planted out-of-range node id per block: caught, skipped, reported once
     npe, m = meshes["hex"]
     X, c = rounded_inputs(m, "mixed")

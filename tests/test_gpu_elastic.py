@@ -1,0 +1,231 @@
+"""Parity of the CUDA elasticity operator (three DOFs per node, operator_kind 2)
+with the FP64 oracle, through the C ABI.
+
+The DOF pattern must be bit-exact; values within 1e-12 (FP64) or 1e-5 (mixed)
+of the oracle relative to each entry's Cauchy-Schwarz scale, as for the scalar
+operators.  Tiny patch capacities force many patches and ragged batches on small
+meshes; the full-size cases check sampled DOF rows against the oracle and the
+rigid-body null space of the whole matrix.
+"""
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+from helpers import TOL_FP64, TOL_MIXED, rel_err
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+ELASTIC = 2
+
+
+@pytest.fixture(scope="module")
+def fem():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1501_04784_gb300 import _build
+    _build.build()
+    from paper_1501_04784_gb300 import fem as F
+    return F
+
+
+def dev(a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda").to(dtype)
+
+
+def make(fem, m, **opts):
+    return fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), operator_kind=ELASTIC, **opts)
+
+
+def inputs(m, prec):
+    lame = meshgen.lame(m)
+    if prec == "mixed":
+        X, c = m.X.astype(np.float32), lame.astype(np.float32)
+    else:
+        X, c = m.X, lame
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    return dev(X, dt), dev(c, dt), np.asarray(X, np.float64), np.asarray(c, np.float64)
+
+
+def oracle_el(m, X, c):
+    return oracle.build_K(m.npe, X, m.E, c, op="elasticity")
+
+
+MESHES = {
+    "hex_6x5x4_perm": lambda: meshgen.hex_grid(6, 5, 4, jitter=0.25, seed=5, permute_nodes=True, permute_elems=True),
+    "hex_1x1x1": lambda: meshgen.hex_grid(1, 1, 1, jitter=0.0, seed=1),
+    "tet_5x4x3_perm": lambda: meshgen.kuhn_tets(5, 4, 3, jitter=0.3, seed=2, permute_nodes=True, permute_elems=True),
+}
+PATCH_CAPS = {"default": 0, "tiny": 48}
+
+
+@pytest.mark.parametrize("cap", list(PATCH_CAPS))
+@pytest.mark.parametrize("name", list(MESHES))
+def test_elastic_pattern_bit_exact(fem, name, cap):
+    m = MESHES[name]()
+    mesh = make(fem, m, patch_entries=PATCH_CAPS[cap])
+    X, c = m.X, meshgen.lame(m)
+    ref = oracle_el(m, X, c)
+    assert mesh.pattern() == ref["nnz"]
+    rowptr, col = mesh.get_pattern()
+    assert np.array_equal(rowptr.cpu().numpy(), ref["rowptr"])
+    assert np.array_equal(col.cpu().numpy(), ref["col"])
+
+
+@pytest.mark.parametrize("cap", list(PATCH_CAPS))
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", list(MESHES))
+def test_elastic_build_K(fem, name, prec, cap):
+    m = MESHES[name]()
+    mesh = make(fem, m, patch_entries=PATCH_CAPS[cap])
+    Xd, cd, X, c = inputs(m, prec)
+    ref = oracle_el(m, X, c)
+    vals = mesh.build_K(Xd, cd, prec)
+    mesh.sync()
+    err = rel_err(vals.cpu().numpy(), ref["vals"], ref["cs"])
+    assert err <= (TOL_FP64 if prec == "fp64" else TOL_MIXED), err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["hex_6x5x4_perm", "tet_5x4x3_perm"])
+def test_elastic_integrate_and_assemble(fem, name, prec):
+    """The staged path: packed element matrices (p = A(A+1)/2 + B over local DOFs)
+    against the oracle's, then their assembly against the oracle's K."""
+    m = MESHES[name]()
+    mesh = make(fem, m, patch_entries=64)
+    Xd, cd, X, c = inputs(m, prec)
+    ke = mesh.integrate_local(Xd, cd, prec)
+    ref_ke, cs, _ = oracle.ke_packed(m.npe, X, m.E, c, op="elasticity")
+    assert ke.shape == ref_ke.shape
+    tol = TOL_FP64 if prec == "fp64" else TOL_MIXED
+    assert rel_err(ke.cpu().numpy().ravel(), ref_ke.ravel(), cs.ravel()) <= tol
+    vals = mesh.assemble_csr(ke, prec)
+    mesh.sync()
+    ref = oracle_el(m, X, c)
+    assert rel_err(vals.cpu().numpy(), ref["vals"], ref["cs"]) <= tol
+
+
+def test_elastic_assemble_oracle_ke(fem):
+    """Assembly alone, of the oracle's own element matrices in FP64: only the
+    summation order differs from the oracle's sparse conversion."""
+    m = MESHES["tet_5x4x3_perm"]()
+    mesh = make(fem, m, patch_entries=64)
+    c = meshgen.lame(m)
+    ke, _, _ = oracle.ke_packed(m.npe, m.X, m.E, c, op="elasticity")
+    vals = mesh.assemble_csr(dev(ke, torch.float64), "fp64").cpu().numpy()
+    ref = oracle_el(m, m.X, c)
+    assert rel_err(vals, ref["vals"], ref["cs"]) <= 1e-14
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_elastic_reproducible_and_host_path(fem, prec):
+    m = MESHES["hex_6x5x4_perm"]()
+    Xd, cd, X, c = inputs(m, prec)
+    outs = []
+    for threads, bps in ((256, 0), (256, 0), (128, 1), (64, 2)):
+        mesh = make(fem, m, block_threads=threads, blocks_per_sm=bps, patch_entries=256)
+        outs.append(mesh.build_K(Xd, cd, prec).cpu().numpy())
+    for o in outs[1:]:
+        assert np.array_equal(o.view(np.uint8), outs[0].view(np.uint8))
+    mesh = make(fem, m, patch_entries=256)
+    hv = mesh.build_K_host(Xd.cpu().pin_memory(), cd.cpu().pin_memory(), prec).numpy()
+    assert np.array_equal(hv.view(np.uint8), outs[0].view(np.uint8))
+
+
+def dof_matvec(rp, col, vals, u):
+    """y = K u for the symmetric K stored as its lower triangle (on the GPU)."""
+    n = rp.numel() - 1
+    rows = torch.repeat_interleave(torch.arange(n, device=rp.device), rp[1:] - rp[:-1])
+    colL = col.long()
+    y = torch.zeros(n, dtype=vals.dtype, device=vals.device)
+    y.index_add_(0, rows, vals * u[colL])
+    off = rows != colL
+    y.index_add_(0, colL[off], vals[off] * u[rows[off]])
+    return y
+
+
+def rigid_modes(X):
+    n = X.shape[0]
+    modes = []
+    for i in range(3):
+        u = np.zeros((n, 3))
+        u[:, i] = 1.0
+        modes.append(u.ravel())
+    x = X - X.mean(axis=0)
+    for i in range(3):
+        w = np.zeros(3)
+        w[i] = 1.0
+        modes.append(np.cross(w, x).ravel())
+    return modes
+
+
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+def test_elastic_full_size_sampled(fem, kind):
+    """Large meshes (40^3 bricks, 24^3 cells of tetrahedra, permuted, jittered) in
+    mixed precision: DOF rows of sampled nodes against the oracle, and the six
+    rigid-body motions in the null space of the assembled matrix."""
+    if kind == "hex":
+        m = meshgen.hex_grid(40, jitter=0.25, seed=11, permute_nodes=True, permute_elems=True, c_sigma=1.0)
+    else:
+        m = meshgen.kuhn_tets(24, jitter=0.3, seed=12, permute_nodes=True, permute_elems=True)
+    mesh = make(fem, m)
+    Xd, cd, X, c = inputs(m, "mixed")
+    vals = mesh.build_K(Xd, cd, "mixed")
+    mesh.sync()
+    rowptr, col = mesh.get_pattern()
+    rp, cl, v = rowptr.cpu().numpy(), col.cpu().numpy(), vals.cpu().numpy()
+    rng = np.random.default_rng(21)
+    nodes = rng.choice(m.n_nodes, 400, replace=False)
+    touch = np.isin(m.E, nodes).any(axis=1)
+    sub = oracle.build_K(m.npe, X, m.E[touch], c[touch], op="elasticity")
+    worst = 0.0
+    for n in nodes:
+        for r in range(3 * n, 3 * n + 3):
+            a, b = sub["rowptr"][r], sub["rowptr"][r + 1]
+            assert np.array_equal(cl[rp[r]:rp[r + 1]], sub["col"][a:b])
+            worst = max(worst, rel_err(v[rp[r]:rp[r + 1]], sub["vals"][a:b], sub["cs"][a:b]))
+    assert worst <= TOL_MIXED, worst
+    # residual of each DOF relative to sum_j sqrt(K_ii K_jj) |u_j| (the
+    # Cauchy-Schwarz scale of its terms; entries themselves may cancel)
+    K64 = vals.double()
+    n = rowptr.numel() - 1
+    rows = torch.repeat_interleave(torch.arange(n, device="cuda"), rowptr[1:] - rowptr[:-1])
+    diag = torch.zeros(n, dtype=torch.float64, device="cuda")
+    on = rows == col.long()
+    diag[rows[on]] = K64[on].abs()
+    S = torch.sqrt(diag[rows] * diag[col.long()])
+    for u in rigid_modes(X):
+        ud = torch.as_tensor(u, device="cuda")
+        y = dof_matvec(rowptr, col, K64, ud)
+        scale = dof_matvec(rowptr, col, S, ud.abs())
+        assert float((y.abs() / scale.clamp_min(1e-300)).max()) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_elastic_zero_volume_element_is_reported(fem, prec):
+    from paper_1501_04784_gb300 import abi
+    m = MESHES["hex_6x5x4_perm"]()
+    X = m.X.copy()
+    X[m.E[0], 2] = X[m.E[0][0], 2]
+    bad = make(fem, m)
+    dt = torch.float32 if prec == "mixed" else torch.float64
+    bad.build_K(dev(X, dt), dev(meshgen.lame(m), dt), prec)
+    with pytest.raises(abi.FemError, match="FEM_ERR_DEGENERATE"):
+        bad.sync()
+    bad.sync()
+
+
+def test_elastic_unsupported_entry_points(fem):
+    from paper_1501_04784_gb300 import abi
+    m = MESHES["hex_1x1x1"]()
+    mesh = make(fem, m)
+    mesh.pattern()
+    Xd, cd, _, _ = inputs(m, "fp64")
+    with pytest.raises(abi.FemError, match="FEM_ERR_UNSUPPORTED"):
+        mesh.load_vector(Xd, dev(m.c, torch.float64), "fp64")
+    with pytest.raises(abi.FemError, match="FEM_ERR_UNSUPPORTED"):
+        mesh.vjp(Xd, cd, torch.zeros(mesh.nnz, dtype=torch.float64, device="cuda"), "fp64")
+    with pytest.raises(abi.FemError, match="FEM_ERR_UNSUPPORTED"):
+        fem.build_K_batched([mesh], [Xd], [cd], "fp64")
+    assert mesh.info()["nnz"] == mesh.nnz == 300
