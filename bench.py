@@ -46,6 +46,8 @@ def parse():
                     help="--once only: the 1M-brick workload or the 3.07M-tet workload")
     ap.add_argument("--patch-entries", type=int, default=0, help="--once only: plan patch size (0 = default)")
     ap.add_argument("--block-threads", type=int, default=0, help="--once only: threads per block (0 = default)")
+    ap.add_argument("--operator", choices=["stiffness", "elasticity"], default="stiffness",
+                    help="--once only: the scalar stiffness matrix or the elasticity operator")
     return ap.parse_args()
 
 
@@ -144,7 +146,7 @@ def measured_peaks():
 
 
 # the sources that determine the patch kernel's code and its plan's layout
-KERNEL_SOURCES = ("element.cuh", "mesh.cuh", "numeric.cu", "numeric.cuh", "symbolic.cu")
+KERNEL_SOURCES = ("element.cuh", "mesh.cuh", "numeric.cu", "numeric.cuh", "phases.cuh", "symbolic.cu")
 
 
 def source_hash():
@@ -179,6 +181,14 @@ def algorithmic_bytes(n_nodes, n_elems, npe, nnz, xsize, csize, vsize):
 # (300), 36 packed entries of 9 terms scaled by c/8 (648).
 BRICK_FLOPS = 36 + 216 + 584 + 17 + 12 + 120 + 300 + 648
 SMS, FP32_LANES = 152, 128
+
+# FP32 FLOPs of one brick of the elasticity operator, lower triangle only (an FMA
+# counts 2): 12 edge vectors (36); per Gauss point the 3 rows of 2J from the edges
+# (81), cofactor rows (27), determinant (5), scale 1/(8|d|) (6) -> 8 x 119 = 952;
+# gradient vectors of the 8 nodes (8 x 120 = 960) and their scaled copies
+# (8 x 24 = 192); 36 blocks of 9 products accumulated (8 x 1296 = 10368); the
+# Lame combination lambda P + mu P^T + mu tr(P) I of 36 blocks (36 x 33 = 1188).
+ELASTIC_BRICK_FLOPS = 36 + 952 + 960 + 192 + 10368 + 1188
 
 
 def cpu_baseline(m, target_s=12.0):
@@ -463,7 +473,49 @@ def other_workloads(flush, stream):
                     "unit": "elements/s", "ms_per_step": t, "patch_groups": info["n_groups"],
                     "plan_bytes": info["plan_bytes"]}
     mesh.close()
+    del mesh, X, c, v
+    out["elastic"] = elastic_workloads(timed, dev)
     return out
+
+
+def elastic_workloads(timed, dev):
+    """The elasticity operator (three DOFs per node, operator_kind 2) on the 1M-brick
+    mesh (mixed and FP64) and the 3.07M-tet mesh (mixed): Lame parameters from a
+    seeded Poisson ratio in [0.1, 0.45] and Young's modulus c_e."""
+    import torch
+
+    import meshgen
+    from paper_1501_04784_gb300 import fem
+
+    res = {}
+    for key, idx in (("hex", 1), ("tet", 2)):
+        m = meshgen.config_mesh(idx)
+        lame = meshgen.lame(m)
+        mesh = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), operator_kind=2)
+        nnz = mesh.pattern()
+        X, c = dev(m.X, torch.float32), dev(lame, torch.float32)
+        v = torch.empty(nnz, dtype=torch.float32, device="cuda")
+        t = timed(lambda: mesh.build_K(X, c, "mixed", out=v), 10)
+        mesh.sync()
+        r = {"workload": ("1M-hex8" if idx == 1 else "3.07M-tet4") + " elasticity, 3 DOFs per node",
+             "value": m.n_elems / (t / 1e3), "unit": "elements/s", "ms_per_step": t, "nnz": nnz,
+             "dof_entries_per_s": nnz / (t / 1e3), "n_patches": mesh.info()["n_patches"],
+             "closure_elems": mesh.info()["closure_elems"]}
+        if idx == 1:
+            r["alu"] = {"flops_per_element": ELASTIC_BRICK_FLOPS,
+                        "achieved_tflops": ELASTIC_BRICK_FLOPS * m.n_elems / (t / 1e3) / 1e12,
+                        "frac_of_fp32_peak_2070mhz": ELASTIC_BRICK_FLOPS * m.n_elems / (t / 1e3)
+                        / (SMS * FP32_LANES * 2 * 2070e6)}
+            X64, c64 = dev(m.X, torch.float64), dev(lame, torch.float64)
+            v64 = torch.empty(nnz, dtype=torch.float64, device="cuda")
+            t64 = timed(lambda: mesh.build_K(X64, c64, "fp64", out=v64), 3)
+            mesh.sync()
+            r["fp64"] = {"value": m.n_elems / (t64 / 1e3), "unit": "elements/s", "ms_per_step": t64}
+            del X64, c64, v64
+        res[key] = r
+        mesh.close()
+        del mesh, X, c, v
+    return res
 
 
 def run_once(args):
@@ -475,15 +527,19 @@ def run_once(args):
     _build.build()
     m = meshgen.config_mesh(1 if args.workload == "hex" else 2)
     E = torch.from_numpy(m.E).cuda()
-    X64, c64 = torch.from_numpy(m.X).cuda(), torch.from_numpy(m.c).cuda()
-    mesh = fem.Mesh(E, m.n_nodes, X=X64, patch_entries=args.patch_entries, block_threads=args.block_threads)
+    elastic = args.operator == "elasticity"
+    X64 = torch.from_numpy(m.X).cuda()
+    c64 = torch.from_numpy(meshgen.lame(m) if elastic else m.c).cuda()
+    mesh = fem.Mesh(E, m.n_nodes, X=X64, patch_entries=args.patch_entries, block_threads=args.block_threads,
+                    operator_kind=2 if elastic else 0)
     nnz = mesh.pattern()
     X, c = (X64.float(), c64.float()) if args.once == "mixed" else (X64, c64)
     v = torch.empty(nnz, dtype=X.dtype, device="cuda")
     for _ in range(2):
         mesh.build_K(X, c, args.once, out=v)
     torch.cuda.synchronize()
-    print(f"built {args.workload} {args.once}: nnz {nnz}, patches {mesh.info()['n_patches']}")
+    mesh.sync()
+    print(f"built {args.workload} {args.operator} {args.once}: nnz {nnz}, patches {mesh.info()['n_patches']}")
 
 
 if __name__ == "__main__":
