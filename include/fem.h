@@ -124,8 +124,12 @@ typedef struct {
  *     of 9L - 3 entries in all, row 3I starting at 9 rowptr_node[I] - 3I);
  *   - fem_integrate_local and fem_assemble_csr use [n_elems][300|78] packed
  *     entries, p = A(A+1)/2 + B over local DOFs A = 3a + i, B <= A;
- *   - fem_build_K fuses integration and assembly in both precisions;
- *   - patch_entries counts node pairs (each a 3x3 block; default 2048);
+ *   - fem_build_K fuses integration and assembly in FP32 (mixed); FEM_FP64 integrates
+ *     each element once into library memory (n_elems * 300|78 doubles, within the
+ *     budget; fused if it refuses or fp64_fused is set) and then assembles; patches
+ *     whose 3x3 blocks outgrow shared memory are accumulated in row windows;
+ *   - patch_entries counts node pairs (each a 3x3 block; default 4096 for bricks,
+ *     1536 for tetrahedra) and block_threads defaults to 512 for bricks;
  *   - fem_pattern_ptrs, fem_vjp, fem_load_vector and fem_build_K_batched answer
  *     FEM_ERR_UNSUPPORTED; fem_mesh_create refuses 3 n_nodes >= 2^31.
  */

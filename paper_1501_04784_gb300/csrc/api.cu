@@ -307,6 +307,7 @@ static PatchArgs patch_args(fem_mesh m, fem_prec p, bool fused) {
     a.threads = m->opt.block_threads > 0 ? m->opt.block_threads : 256;
     if (a.threads > patch_max_threads(m->npe)) a.threads = patch_max_threads(m->npe);
     a.threads = (a.threads + 31) / 32 * 32;
+    if (is_elastic(m)) a.threads = elastic_threads(m->npe, m->opt.block_threads);  // its own default and cap
     a.blocks_per_sm = m->opt.blocks_per_sm;
     a.mode = kernel_mode(m->opt);
     a.wait = wait_ctl(m);
@@ -358,8 +359,31 @@ fem_status fem_build_K(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype,
     }
     cudaStream_t s = as_stream(stream);
     if (is_elastic(m)) {
-        // one fused kernel in both precisions (no FP64 staging: 300 doubles per
-        // brick would outweigh the recomputation in each closure)
+        if (p == FEM_FP64 && m->opt.fp64_fused == 0) {
+            // FP64 integrates each element once into library memory (300 or 78
+            // doubles per element), then assembles: the FP64 pipe bounds the
+            // integration, and patches whose FP64 blocks outgrow shared memory are
+            // assembled in row windows, each of which would otherwise integrate its
+            // closure again.  Falls back to the fused kernel if the budget refuses.
+            const size_t nk = 3 * (size_t)m->npe, n = (size_t)m->n_elems * (nk * (nk + 1) / 2);
+            fem_status st = m->ke64.n >= n ? FEM_OK : m->ke64.alloc(m->arena, n, "FP64 element matrices");
+            if (st == FEM_OK) {
+                IntegrateArgs ia{m->npe, false, x_dtype, c_dtype, m->E, m->n_elems, X, c, m->ke64.ptr,
+                                 default_threshold(m), nullptr, kernel_mode(m->opt), m->status.ptr};
+                FEM_TRY(launch_elastic_integrate(ia, s));
+                PatchArgs a = patch_args(m, p, false);
+                a.xd = FEM_F64;
+                a.cd = FEM_F64;
+                a.ke = m->ke64.ptr;
+                a.vals = vals;
+                return for_each_group(m, s, [&](const Closure &cl) {
+                    a.closure = &cl;
+                    return launch_elastic_patch(a, s);
+                });
+            }
+            if (st != FEM_ERR_BUDGET) return st;
+            cudaGetLastError();
+        }
         PatchArgs a = patch_args(m, p, true);
         a.xd = x_dtype;
         a.cd = c_dtype;
@@ -571,9 +595,9 @@ fem_status fem_autotune(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype
     cudaStream_t s = as_stream(stream);
     const fem_options keep = m->opt;
     static const int entries_scalar[] = {4096, 6144, 8192, 12288, 16384};
-    static const int entries_elastic[] = {1024, 1536, 2048, 2560, 3072};
+    static const int entries_elastic[] = {1536, 2048, 3072, 4096, 5120};
     static const int threads_scalar[] = {128, 256, 512};
-    static const int threads_elastic[] = {128, 256, 256};
+    static const int threads_elastic[] = {256, 512, 512};
     const int *entries = is_elastic(m) ? entries_elastic : entries_scalar;
     const int *threads = is_elastic(m) ? threads_elastic : threads_scalar;
     float best = 1e30f;

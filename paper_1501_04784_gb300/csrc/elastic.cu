@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(EL_INT_THREADS) k_elastic_integrate(const int3
 }
 
 // ----------------------------------------------------------- k_elastic_patch
-template <int NPE, typename AccT, typename S, typename CT, bool FUSED, bool MIXED>
+template <int NPE, typename AccT, typename S, typename CT, bool FUSED, bool MIXED, bool WIN>
 __device__ __forceinline__ void elastic_patch_body(const PlanView &pv, const S *__restrict__ X,
                                                    const CT *__restrict__ c, const AccT *__restrict__ ke,
                                                    AccT *__restrict__ vals, float thr, int64_t p, const PatchSmem &L,
@@ -117,10 +117,6 @@ __device__ __forceinline__ void elastic_patch_body(const PlanView &pv, const S *
         orow[k] = pv.own_row[nb + k];
     }
     if (tid == 0) roff[nown] = nacc;
-    {
-        const int n = 9 * nacc;
-        for (int i = tid; i < n; i += nthr) acc[i] = AccT(0);
-    }
     __syncthreads();
     if constexpr (FUSED) {
         for (int j = tid; j < ncn; j += nthr) {
@@ -135,142 +131,169 @@ __device__ __forceinline__ void elastic_patch_body(const PlanView &pv, const S *
 
     const uint16_t *aidx16 = reinterpret_cast<const uint16_t *>(pv.celem_aidx);
     const int q0 = a * (a + 1) / 2;  // packed node pair (a, 0)
-    for (int base = 0; base < nel; base += epb) {
-        const int i = base + tid / NPE;
-        const bool act = i < nel;
-        const int64_t ci = eb + i;
-        uint16_t ln[NPE];
-        int mycol = -1;
-        if (act) {
-            load_lnodes<NPE>(pv.celem_lnode, ci, ln);
-            mycol = pv.celem_color[ci];
-        } else {
-#pragma unroll
-            for (int b = 0; b < NPE; ++b) ln[b] = 0;
+    // Owned rows in windows [k0, k1) whose slots fit the accumulators (L.win): with
+    // WIN false one window covers the patch; with WIN true (blocks that outgrow
+    // shared memory: FP64, or patches planned larger than the limit) each window
+    // takes one pass over the closure, and slots outside it are skipped.
+    for (int k0 = 0; k0 < nown;) {
+        int k1 = nown;
+        if constexpr (WIN) {
+            int hi = nown;
+            k1 = k0 + 1;
+            while (k1 < hi) {
+                const int mid = (k1 + hi + 1) >> 1;
+                if (roff[mid] - roff[k0] <= L.win) k1 = mid; else hi = mid - 1;
+            }
         }
-#pragma unroll
-        for (int b = 0; b < NPE; ++b)
-            if (!FEM_IN_BOUNDS(ln[b] < ncn || !act, wc.status)) ln[b] = 0;
-        AccT k[NPE][9];
-        if constexpr (FUSED) {
-            S xc[NPE][3];
-#pragma unroll
-            for (int b = 0; b < NPE; ++b) {
-                xc[b][0] = xs[ln[b]][0];
-                xc[b][1] = xs[ln[b]][1];
-                xc[b][2] = xs[ln[b]][2];
-            }
-            AccT lam = AccT(0), mu = AccT(0);
+        const int s0 = WIN ? roff[k0] : 0, s1 = WIN ? roff[k1] : nacc;
+        for (int i = tid; i < 9 * (s1 - s0); i += nthr) acc[i] = AccT(0);
+        __syncthreads();
+        for (int base = 0; base < nel; base += epb) {
+            const int i = base + tid / NPE;
+            const bool act = i < nel;
+            const int64_t ci = eb + i;
+            uint16_t ln[NPE];
+            int mycol = -1;
             if (act) {
-                int64_t e = pv.celem_id[ci];
-                if (!FEM_IN_BOUNDS(e >= 0 && e < pv.n_elems, wc.status)) e = 0;
-                lam = AccT(__ldg(c + 2 * e));
-                mu = AccT(__ldg(c + 2 * e + 1));
-            }
-            elastic_row<NPE, AccT, S, MIXED>(xc, lam, mu, a, thr, fp64_det, k);
-            if (act && !isfinite(k[0][0])) atomicOr(wc.status, STATUS_NONFINITE);
-        } else {
-            if (act) {
-                int64_t e = pv.celem_id[ci];
-                if (!FEM_IN_BOUNDS(e >= 0 && e < pv.n_elems, wc.status)) e = 0;
-                load_packed_row<NPE, AccT>(ke + e * NPK, a, k);
+                load_lnodes<NPE>(pv.celem_lnode, ci, ln);
+                mycol = pv.celem_color[ci];
             } else {
 #pragma unroll
-                for (int b = 0; b < NPE; ++b)
-#pragma unroll
-                    for (int m = 0; m < 9; ++m) k[b][m] = AccT(0);
+                for (int b = 0; b < NPE; ++b) ln[b] = 0;
             }
-        }
-        // accumulator slots of the pairs (a, b), b <= a (scratch for rows the
-        // patch does not own), and whether the pair's row is node b's: closure
-        // nodes are numbered in ascending global order, so g_a < g_b exactly when
-        // ln[a] < ln[b], and then the block goes in transposed
-        int slot[NPE];
-        const uint16_t lna = NPE == 8 ? (a & 4 ? (a & 2 ? (a & 1 ? ln[7] : ln[6]) : (a & 1 ? ln[5] : ln[4]))
-                                               : (a & 2 ? (a & 1 ? ln[3] : ln[2]) : (a & 1 ? ln[1] : ln[0])))
-                                      : (a & 2 ? (a & 1 ? ln[3] : ln[2]) : (a & 1 ? ln[1] : ln[0]));
 #pragma unroll
-        for (int b = 0; b < NPE; ++b) {
-            slot[b] = -1;
-            if (act && b <= a) {
-                const int q = q0 + b;
-                int t = aidx16[((int64_t)(q >> 1) * pv.aidx_n + ci) * 2 + (q & 1)];
-                if (!FEM_IN_BOUNDS(t < L.acc_cap, wc.status)) t = -1;
-                slot[b] = t;
+            for (int b = 0; b < NPE; ++b)
+                if (!FEM_IN_BOUNDS(ln[b] < ncn || !act, wc.status)) ln[b] = 0;
+            AccT k[NPE][9];
+            if constexpr (FUSED) {
+                S xc[NPE][3];
+#pragma unroll
+                for (int b = 0; b < NPE; ++b) {
+                    xc[b][0] = xs[ln[b]][0];
+                    xc[b][1] = xs[ln[b]][1];
+                    xc[b][2] = xs[ln[b]][2];
+                }
+                AccT lam = AccT(0), mu = AccT(0);
+                if (act) {
+                    int64_t e = pv.celem_id[ci];
+                    if (!FEM_IN_BOUNDS(e >= 0 && e < pv.n_elems, wc.status)) e = 0;
+                    lam = AccT(__ldg(c + 2 * e));
+                    mu = AccT(__ldg(c + 2 * e + 1));
+                }
+                elastic_row<NPE, AccT, S, MIXED>(xc, lam, mu, a, thr, fp64_det, k);
+                if (act && !isfinite(k[0][0])) atomicOr(wc.status, STATUS_NONFINITE);
+            } else {
+                if (act) {
+                    int64_t e = pv.celem_id[ci];
+                    if (!FEM_IN_BOUNDS(e >= 0 && e < pv.n_elems, wc.status)) e = 0;
+                    load_packed_row<NPE, AccT>(ke + e * NPK, a, k);
+                } else {
+#pragma unroll
+                    for (int b = 0; b < NPE; ++b)
+#pragma unroll
+                        for (int m = 0; m < 9; ++m) k[b][m] = AccT(0);
+                }
             }
-        }
-        const int last = min(base + epb, nel) - 1;
-        const int c0 = pv.celem_color[eb + base], c1 = pv.celem_color[eb + last];
-        if (wc.stall == 1 && base == 0 && warp == 0) phase_wait(mb, g, wc);
-        for (int cc = c0; cc <= c1; ++cc, ++g) {
-            const bool mine = mycol == cc;
-            if (__any_sync(0xffffffffu, mine)) {
-                if (g > 0) phase_wait(mb, g - 1, wc);
-                if (mine) {
+            // accumulator slots of the pairs (a, b), b <= a (scratch for rows the
+            // patch does not own), and whether the pair's row is node b's: closure
+            // nodes are numbered in ascending global order, so g_a < g_b exactly when
+            // ln[a] < ln[b], and then the block goes in transposed
+            int slot[NPE];
+            const uint16_t lna = NPE == 8 ? (a & 4 ? (a & 2 ? (a & 1 ? ln[7] : ln[6]) : (a & 1 ? ln[5] : ln[4]))
+                                                   : (a & 2 ? (a & 1 ? ln[3] : ln[2]) : (a & 1 ? ln[1] : ln[0])))
+                                          : (a & 2 ? (a & 1 ? ln[3] : ln[2]) : (a & 1 ? ln[1] : ln[0]));
 #pragma unroll
-                    for (int b = 0; b < NPE; ++b) {
-                        if (slot[b] < 0) continue;
-                        AccT *dst = acc + 9 * slot[b];
-                        if (b == a) {
-                            // diagonal block: its lower half (i >= j) only
-                            AccT o0 = dst[0], o3 = dst[3], o4 = dst[4], o6 = dst[6], o7 = dst[7], o8 = dst[8];
-                            dst[0] = o0 + k[b][0];
-                            dst[3] = o3 + k[b][3];
-                            dst[4] = o4 + k[b][4];
-                            dst[6] = o6 + k[b][6];
-                            dst[7] = o7 + k[b][7];
-                            dst[8] = o8 + k[b][8];
-                        } else {
-                            const bool tr = lna < ln[b];
-                            AccT old[9];
+            for (int b = 0; b < NPE; ++b) {
+                slot[b] = -1;
+                if (act && b <= a) {
+                    const int q = q0 + b;
+                    int t = aidx16[((int64_t)(q >> 1) * pv.aidx_n + ci) * 2 + (q & 1)];
+                    // scratch targets (rows of other patches) to the window's scratch,
+                    // owned slots outside the window skipped
+                    if constexpr (WIN) t = t >= L.trash ? L.win + (t - L.trash) : (t >= s0 && t < s1 ? t - s0 : -1);
+                    if (!FEM_IN_BOUNDS(t < L.acc_cap, wc.status)) t = -1;
+                    slot[b] = t;
+                }
+            }
+            const int last = min(base + epb, nel) - 1;
+            const int c0 = pv.celem_color[eb + base], c1 = pv.celem_color[eb + last];
+            if (wc.stall == 1 && base == 0 && warp == 0) phase_wait(mb, g, wc);
+            for (int cc = c0; cc <= c1; ++cc, ++g) {
+                const bool mine = mycol == cc;
+                if (__any_sync(0xffffffffu, mine)) {
+                    if (g > 0) phase_wait(mb, g - 1, wc);
+                    if (mine) {
 #pragma unroll
-                            for (int m = 0; m < 9; ++m) old[m] = dst[m];
+                        for (int b = 0; b < NPE; ++b) {
+                            if (slot[b] < 0) continue;
+                            AccT *dst = acc + 9 * slot[b];
+                            if (b == a) {
+                                // diagonal block: its lower half (i >= j) only
+                                AccT o0 = dst[0], o3 = dst[3], o4 = dst[4], o6 = dst[6], o7 = dst[7], o8 = dst[8];
+                                dst[0] = o0 + k[b][0];
+                                dst[3] = o3 + k[b][3];
+                                dst[4] = o4 + k[b][4];
+                                dst[6] = o6 + k[b][6];
+                                dst[7] = o7 + k[b][7];
+                                dst[8] = o8 + k[b][8];
+                            } else {
+                                const bool tr = lna < ln[b];
+                                AccT old[9];
 #pragma unroll
-                            for (int i3 = 0; i3 < 3; ++i3)
+                                for (int m = 0; m < 9; ++m) old[m] = dst[m];
 #pragma unroll
-                                for (int j3 = 0; j3 < 3; ++j3)
-                                    dst[3 * i3 + j3] = old[3 * i3 + j3] + (tr ? k[b][3 * j3 + i3] : k[b][3 * i3 + j3]);
+                                for (int i3 = 0; i3 < 3; ++i3)
+#pragma unroll
+                                    for (int j3 = 0; j3 < 3; ++j3)
+                                        dst[3 * i3 + j3] = old[3 * i3 + j3] + (tr ? k[b][3 * j3 + i3] : k[b][3 * i3 + j3]);
+                            }
                         }
                     }
+                    __syncwarp();
                 }
-                __syncwarp();
+                if (g >= (uint32_t)PHASE_RING) phase_wait(mb, g - PHASE_RING, wc);
+                if (lane == 0) phase_arrive(mb, g);
             }
-            if (g >= (uint32_t)PHASE_RING) phase_wait(mb, g - PHASE_RING, wc);
-            if (lane == 0) phase_arrive(mb, g);
         }
-    }
-    __syncthreads();  // every phase of the patch done
+        __syncthreads();  // every phase of the window done
 
-    // each owned node's 3 DOF rows, one contiguous range of vals, by one warp:
-    // DOF row r holds the node row's off-diagonal blocks' row r, then the
-    // diagonal block's entries (r, 0..r)
-    for (int k = warp; k < nown; k += nwarps) {
-        const int o0 = roff[k], len = roff[k + 1] - o0;
-        const int off3 = 3 * (len - 1);
-        const int64_t out0 = 9 * rps[k] - 3 * (int64_t)orow[k];
-        int total = 9 * len - 3;
-        if (!FEM_IN_BOUNDS(o0 >= 0 && len >= 1 && o0 + len <= L.acc_cap && out0 >= 0 && out0 + total <= pv.nnz,
-                           wc.status))
-            total = 0;
-        for (int f = lane; f < total; f += 32) {
-            const int r = f < off3 + 1 ? 0 : (f < 2 * off3 + 3 ? 1 : 2);
-            const int s = f - (r == 0 ? 0 : (r == 1 ? off3 + 1 : 2 * off3 + 3));
-            const int src = s < off3 ? 9 * (o0 + s / 3) + 3 * r + s % 3 : 9 * (o0 + len - 1) + 3 * r + (s - off3);
-            vals[out0 + f] = acc[src];
+        // each owned node's 3 DOF rows, one contiguous range of vals, by one warp:
+        // DOF row r holds the node row's off-diagonal blocks' row r, then the
+        // diagonal block's entries (r, 0..r)
+        for (int k = k0 + warp; k < k1; k += nwarps) {
+            const int o0 = roff[k] - s0, len = roff[k + 1] - roff[k];
+            const int off3 = 3 * (len - 1);
+            const int64_t out0 = 9 * rps[k] - 3 * (int64_t)orow[k];
+            int total = 9 * len - 3;
+            if (!FEM_IN_BOUNDS(o0 >= 0 && len >= 1 && o0 + len <= L.acc_cap && out0 >= 0 && out0 + total <= pv.nnz,
+                               wc.status))
+                total = 0;
+            for (int f = lane; f < total; f += 32) {
+                const int r = f < off3 + 1 ? 0 : (f < 2 * off3 + 3 ? 1 : 2);
+                const int s = f - (r == 0 ? 0 : (r == 1 ? off3 + 1 : 2 * off3 + 3));
+                const int src = s < off3 ? 9 * (o0 + s / 3) + 3 * r + s % 3 : 9 * (o0 + len - 1) + 3 * r + (s - off3);
+                vals[out0 + f] = acc[src];
+            }
         }
+        __syncthreads();
+        k0 = k1;
     }
-    __syncthreads();
 }
 
-// Launch bounds: 256 threads; FP32 bricks 2 blocks per SM (128 registers), FP32
-// tetrahedra 3; FP64 one (its 72 double accumulators need the registers).
+// Launch bounds: FP32 bricks up to 512 threads at 128 registers (2 blocks of 256
+// or 1 of 512 per SM); FP32 tetrahedra 256 threads, 3 blocks per SM; FP64 256
+// threads, one block (its 72 double accumulators need the registers).
+template <int NPE, typename AccT>
+__host__ __device__ constexpr int elastic_max_threads() {
+    return (sizeof(AccT) == 4 && NPE == 8) ? 512 : 256;
+}
 template <int NPE, typename AccT>
 __host__ __device__ constexpr int elastic_min_blocks() {
-    return sizeof(AccT) == 8 ? 1 : (NPE == 8 ? 2 : 3);
+    return sizeof(AccT) == 8 ? 1 : (NPE == 8 ? 1 : 3);
 }
 
-template <int NPE, typename AccT, typename S, typename CT, bool FUSED, bool MIXED>
-__global__ void __launch_bounds__(256, elastic_min_blocks<NPE, AccT>())
+template <int NPE, typename AccT, typename S, typename CT, bool FUSED, bool MIXED, bool WIN>
+__global__ void __launch_bounds__(elastic_max_threads<NPE, AccT>(), elastic_min_blocks<NPE, AccT>())
     k_elastic_patch(PlanView pv, const S *__restrict__ X, const CT *__restrict__ c, const AccT *__restrict__ ke,
                     AccT *__restrict__ vals, float thr, int64_t p0, int64_t p1, PatchSmem L, unsigned mode,
                     WaitCtl wc) {
@@ -278,17 +301,19 @@ __global__ void __launch_bounds__(256, elastic_min_blocks<NPE, AccT>())
     phase_init(mb);
     uint32_t g = 0;
     for (int64_t p = p0 + blockIdx.x; p < p1; p += gridDim.x)
-        elastic_patch_body<NPE, AccT, S, CT, FUSED, MIXED>(pv, X, c, ke, vals, thr, p, L, mode, mb, g, wc);
+        elastic_patch_body<NPE, AccT, S, CT, FUSED, MIXED, WIN>(pv, X, c, ke, vals, thr, p, L, mode, mb, g, wc);
 }
 
 // ------------------------------------------------------------------- launch
-PatchSmem elastic_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsize) {
+PatchSmem elastic_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsize, int win) {
     PatchSmem L{};
     const size_t accsz = mixed ? sizeof(float) : sizeof(double);
     size_t o = 0;
     L.acc = o;
-    L.acc_cap = (int)(P.max_acc + ACC_SCRATCH);
-    o = el_align16(o + (size_t)9 * (P.max_acc + ACC_SCRATCH) * accsz);
+    L.win = win;
+    L.trash = (int)P.max_acc;
+    L.acc_cap = win + ACC_SCRATCH;
+    o = el_align16(o + (size_t)9 * (win + ACC_SCRATCH) * accsz);
     L.xs = o;
     if (fused) o = el_align16(o + (size_t)P.max_cnodes * 3 * xsize);
     L.roff = o;
@@ -306,18 +331,29 @@ PatchSmem elastic_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t x
     return L;
 }
 
+// Threads per block: bricks default to 512 (one block per SM holding a 4096-pair
+// patch), tetrahedra to 256 (three blocks per SM).
+int elastic_window(const PlanMax &P, bool fused, bool mixed, size_t xsize, size_t limit) {
+    // the layout with no owned slots (scratch and staging arrays), then whole slots
+    const size_t rest = elastic_smem_layout(P, fused, mixed, xsize, 0).total;
+    const size_t per_slot = 9 * (mixed ? sizeof(float) : sizeof(double));
+    if (rest + 16 >= limit) return 0;
+    const int64_t fit = (int64_t)((limit - rest - 16) / per_slot);
+    const int win = (int)std::min<int64_t>(P.max_acc, fit);
+    return win >= 256 || win == P.max_acc ? win : 0;  // a row has at most 255 entries
+}
+
 int elastic_threads(int npe, int requested) {
-    const int t = requested > 0 ? requested : 256;
-    (void)npe;
-    return std::min(256, std::max(32, (t + 31) / 32 * 32));
+    const int t = requested > 0 ? requested : (npe == 8 ? 512 : 256);
+    return std::min(npe == 8 ? 512 : 256, std::max(32, (t + 31) / 32 * 32));
 }
 
 int elastic_blocks_per_sm(int npe, int threads) {
     int n = 0;
     cudaError_t e = npe == 8
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_elastic_patch<8, float, float, float, true, true>,
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_elastic_patch<8, float, float, float, true, true, false>,
                                                         threads, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_elastic_patch<4, float, float, float, true, true>,
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_elastic_patch<4, float, float, float, true, true, false>,
                                                         threads, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -332,17 +368,23 @@ static fem_status launch_elastic_patch_t(const PatchArgs &a, cudaStream_t s) {
     const Closure &cl = a.closure ? *a.closure : P.full;
     PlanMax pm;
     pm.add(P);
-    const PatchSmem L = elastic_smem_layout(pm, FUSED, MIXED, sizeof(S));
     int dev = 0, max_optin = 0;
     FEM_CUDA(cudaGetDevice(&dev));
     FEM_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if (L.total > (size_t)max_optin) {
-        set_error("a patch needs %zu bytes of shared memory (limit %d); lower patch_entries", L.total, max_optin);
+    cudaFuncAttributes fa{};
+    FEM_CUDA(cudaFuncGetAttributes(&fa, k_elastic_patch<NPE, AccT, S, CT, FUSED, MIXED, true>));
+    // the dynamic part shares the opt-in limit with the static mbarrier ring
+    const int win = elastic_window(pm, FUSED, MIXED, sizeof(S), (size_t)max_optin - fa.sharedSizeBytes);
+    if (win <= 0) {
+        set_error("the closure of a patch does not fit in shared memory (limit %d bytes); lower patch_entries",
+                  max_optin);
         return FEM_ERR_UNSUPPORTED;
     }
-    auto f = k_elastic_patch<NPE, AccT, S, CT, FUSED, MIXED>;
+    const PatchSmem L = elastic_smem_layout(pm, FUSED, MIXED, sizeof(S), win);
+    auto f = win >= pm.max_acc ? k_elastic_patch<NPE, AccT, S, CT, FUSED, MIXED, false>
+                               : k_elastic_patch<NPE, AccT, S, CT, FUSED, MIXED, true>;
     FEM_TRY(el_set_smem(f, L.total));
-    const int threads = elastic_threads(NPE, a.threads);
+    const int threads = std::min(elastic_threads(NPE, a.threads), elastic_max_threads<NPE, AccT>());
     int per_sm = 0;
     FEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, L.total));
     if (per_sm < 1) {

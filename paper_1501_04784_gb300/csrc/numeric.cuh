@@ -25,6 +25,8 @@ struct PatchSmem {
     int wg_shift;  // log2 of the lanes that store one owned row
     int acc_cap;   // accumulators a block holds (largest patch + scratch slots)
     int hv_on;     // the hv region exists (some owned row has an FP64-accurate diagonal)
+    int win;       // vector operators: owned node-pair slots a pass accumulates (rows in windows)
+    int trash;     // vector operators: the plan's first scratch target (its largest patch)
 };
 
 // Mode bits of the element kernels: FP64_SUMS, FP64_DETS (mixed kernels;
@@ -136,7 +138,11 @@ fem_status launch_elastic_patch(const PatchArgs &a, cudaStream_t s);
 fem_status launch_elastic_integrate(const IntegrateArgs &a, cudaStream_t s);
 fem_status launch_dof_pattern(const int64_t *rowptr, const int32_t *col, int64_t n, int64_t *rowptr3, int32_t *col3,
                               cudaStream_t s);
-PatchSmem elastic_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsize);
+PatchSmem elastic_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsize, int win);
+// Slots per pass of the elasticity patch kernel under the shared-memory limit: all
+// of the largest patch's when they fit, else as many as fit (0 if fewer than one
+// longest row).
+int elastic_window(const PlanMax &P, bool fused, bool mixed, size_t xsize, size_t limit);
 int elastic_threads(int npe, int requested);
 int elastic_blocks_per_sm(int npe, int threads);
 

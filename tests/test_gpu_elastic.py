@@ -229,3 +229,21 @@ def test_elastic_unsupported_entry_points(fem):
     with pytest.raises(abi.FemError, match="FEM_ERR_UNSUPPORTED"):
         fem.build_K_batched([mesh], [Xd], [cd], "fp64")
     assert mesh.info()["nnz"] == mesh.nnz == 300
+
+
+@pytest.mark.parametrize("prec,opts", [("mixed", dict(patch_entries=8192)), ("fp64", {}),
+                                       ("fp64", dict(fp64_fused=1))])
+def test_elastic_row_windows(fem, prec, opts):
+    """Patches whose 3x3 blocks outgrow shared memory (FP64 at the default patch
+    size; FP32 planned at 8192 node pairs) are accumulated in row windows, one
+    pass over the closure each: the FP64 build stages element matrices by default
+    (fp64_fused=1 integrates in every pass instead)."""
+    m = meshgen.hex_grid(20, 20, 12, jitter=0.25, seed=8, permute_nodes=True, permute_elems=True)
+    mesh = make(fem, m, **opts)
+    mesh.pattern()
+    assert mesh.info()["max_patch_entries"] > (3000 if prec == "fp64" else 6000)
+    Xd, cd, X, c = inputs(m, prec)
+    vals = mesh.build_K(Xd, cd, prec)
+    mesh.sync()
+    ref = oracle_el(m, X, c)
+    assert rel_err(vals.cpu().numpy(), ref["vals"], ref["cs"]) <= (TOL_FP64 if prec == "fp64" else TOL_MIXED)
