@@ -130,8 +130,9 @@ typedef struct {
  *     whose 3x3 blocks outgrow shared memory are accumulated in row windows;
  *   - patch_entries counts node pairs (each a 3x3 block; default 4096 for bricks,
  *     1536 for tetrahedra) and block_threads defaults to 512 for bricks;
- *   - fem_pattern_ptrs, fem_vjp, fem_load_vector and fem_build_K_batched answer
- *     FEM_ERR_UNSUPPORTED; fem_mesh_create refuses 3 n_nodes >= 2^31.
+ *   - fem_load_vector takes a body force [n_elems][3] and writes F [3 n_nodes];
+ *   - fem_pattern_ptrs, fem_vjp and fem_build_K_batched answer FEM_ERR_UNSUPPORTED;
+ *     fem_mesh_create refuses 3 n_nodes >= 2^31.
  */
 
 typedef struct {
@@ -255,7 +256,9 @@ fem_status fem_vjp(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, con
  * node.  X as for fem_build_K; src [n_elems] (src_dtype); F [n_nodes] device,
  * double (FEM_FP64) or float (FEM_MIXED: FP32 element arithmetic, FP64-accurate
  * determinants of distorted elements).  Every entry of F is written.  Uses the
- * cached plan, so FEM_ERR_STATE before fem_pattern.  Independent of operator_kind.
+ * cached plan, so FEM_ERR_STATE before fem_pattern.  The same for operator_kind 0
+ * and 1; for elasticity (2) src is a body force [n_elems][3] and F [3 n_nodes],
+ * F[3n + i] = sum over elements of src[e][i] * integral N_a.
  */
 fem_status fem_load_vector(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *src,
                            fem_dtype src_dtype, void *F, void *stream);

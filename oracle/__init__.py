@@ -184,7 +184,12 @@ def vjp_from_G(npe: int, X, E, c, G, slot):
 
 def load_vector(npe: int, X, E, s):
     """Global load vector F [n_nodes] of a per-element constant source s [n_elems]
-    (F_n = sum over elements of s_e * integral N_a, a the element's local index of n)."""
+    (F_n = sum over elements of s_e * integral N_a, a the element's local index of n).
+    For a body force s [n_elems, 3] (the elasticity operator) F is [3 n_nodes],
+    F[3n + i] the load of component i: the scalar load of each component."""
+    if np.ndim(s) == 2:
+        comps = [load_vector(npe, X, E, np.asarray(s)[:, i]) for i in range(np.shape(s)[1])]
+        return np.stack(comps, axis=1).ravel()
     X, E, s = _inputs(X, E, s)
     F = np.zeros(X.shape[0])
     lib().oracle_load(npe, E.shape[0], _ptr(E), _ptr(X), _ptr(s), _ptr(F))

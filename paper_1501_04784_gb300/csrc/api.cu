@@ -524,10 +524,6 @@ fem_status fem_load_vector(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dt
         set_error("fem_load_vector before fem_pattern");
         return FEM_ERR_STATE;
     }
-    if (is_elastic(m)) {
-        set_error("the load vector covers the scalar operators (one DOF per node)");
-        return FEM_ERR_UNSUPPORTED;
-    }
     if (!F || !aligned(F, p == FEM_FP64 ? 8 : 4)) {
         set_error("F must be a non-null aligned device pointer");
         return FEM_ERR_ARG;

@@ -9,6 +9,10 @@
 // of a patch adds its closure elements' node values into shared-memory accumulators
 // of its owned nodes colour by colour (a fixed order, no atomics) and writes each
 // owned node's F once.
+//
+// With NC = 3 (the elasticity operator, three DOFs per node) the source is a
+// per-element body force b_e (3 components) and F[3n + i] = sum_e b_e,i integral N_a:
+// the same integrals of N_a, times each component.
 #include "element.cuh"
 #include "mesh.cuh"
 #include "numeric.cuh"
@@ -19,7 +23,7 @@ struct LoadSmem {
     size_t xs, cown, gid, fs, total;
 };
 
-template <int NPE, typename T, typename S, typename CT, bool MIXED>
+template <int NPE, typename T, typename S, typename CT, bool MIXED, int NC>
 __global__ void __launch_bounds__(256) k_load(PlanView pv, const S *__restrict__ X, const CT *__restrict__ src,
                                               T *__restrict__ F, float thr, bool fp64_det, LoadSmem L) {
     extern __shared__ __align__(16) unsigned char load_smem[];
@@ -41,7 +45,7 @@ __global__ void __launch_bounds__(256) k_load(PlanView pv, const S *__restrict__
             xs[j][1] = X[3 * g + 1];
             xs[j][2] = X[3 * g + 2];
         }
-        for (int k = tid; k < nown; k += nthr) fs[k] = T(0);
+        for (int k = tid; k < NC * nown; k += nthr) fs[k] = T(0);
         __syncthreads();
         for (int base = 0; base < nel; base += nthr) {
             const int i = base + tid;
@@ -49,9 +53,15 @@ __global__ void __launch_bounds__(256) k_load(PlanView pv, const S *__restrict__
             int mycol = -1;
             int ln[NPE];
             T fe[NPE];
+            T b[NC];
             if (i < nel) {
                 mycol = pv.celem_color[ci];
-                const T s = (T)src[pv.celem_id[ci]];
+                const int64_t e = pv.celem_id[ci];
+                // scalar: the source scales the integrals; vector: integrals of N_a
+                // alone, each component applied at the scatter
+#pragma unroll
+                for (int k = 0; k < NC; ++k) b[k] = (T)src[NC * e + k];
+                const T s = NC == 1 ? b[0] : T(1);
                 S xc[NPE][3];
 #pragma unroll
                 for (int a = 0; a < NPE; ++a) {
@@ -89,20 +99,27 @@ __global__ void __launch_bounds__(256) k_load(PlanView pv, const S *__restrict__
 #pragma unroll
                     for (int a = 0; a < NPE; ++a) {
                         const int o = cown[ln[a]];
-                        if (o >= 0) fs[o] += fe[a];
+                        if (o >= 0) {
+                            if constexpr (NC == 1) {
+                                fs[o] += fe[a];
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < NC; ++k) fs[NC * o + k] += b[k] * fe[a];
+                            }
+                        }
                     }
                 }
                 __syncthreads();
             }
         }
-        for (int k = tid; k < nown; k += nthr) F[pv.own_row[nb + k]] = fs[k];
+        for (int k = tid; k < NC * nown; k += nthr) F[NC * (int64_t)pv.own_row[nb + k / NC] + k % NC] = fs[k];
         __syncthreads();
     }
 }
 
 static size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-template <int NPE, typename T, typename S, typename CT, bool MIXED>
+template <int NPE, typename T, typename S, typename CT, bool MIXED, int NC>
 static fem_status launch_load_t(fem_mesh m, const Closure &cl, const void *X, const void *src, void *F, float thr,
                                 bool fp64_det, cudaStream_t s) {
     const Plan &P = m->plan;
@@ -114,9 +131,9 @@ static fem_status launch_load_t(fem_mesh m, const Closure &cl, const void *X, co
     o = al16(o + (size_t)P.max_cnodes * 4);
     L.gid = o;
     L.fs = o;
-    o = al16(o + (size_t)P.max_own * sizeof(T));
+    o = al16(o + (size_t)NC * P.max_own * sizeof(T));
     L.total = o;
-    auto f = k_load<NPE, T, S, CT, MIXED>;
+    auto f = k_load<NPE, T, S, CT, MIXED, NC>;
     FEM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
     int per_sm = 0;
     FEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, 256, L.total));
@@ -135,7 +152,9 @@ static fem_status launch_load_t(fem_mesh m, const Closure &cl, const void *X, co
 static fem_status launch_load_group(fem_mesh m, const Closure &cl, bool mixed, const void *X, fem_dtype xd,
                                     const void *src, fem_dtype sd, void *F, float thr, bool fp64_det,
                                     cudaStream_t s) {
-#define FEM_L(NPE, T, S, CT, MX) return launch_load_t<NPE, T, S, CT, MX>(m, cl, X, src, F, thr, fp64_det, s)
+#define FEM_L(NPE, T, S, CT, MX)                                                                  \
+    return m->opt.operator_kind == 2 ? launch_load_t<NPE, T, S, CT, MX, 3>(m, cl, X, src, F, thr, fp64_det, s) \
+                                     : launch_load_t<NPE, T, S, CT, MX, 1>(m, cl, X, src, F, thr, fp64_det, s)
     if (!mixed) {
         if (m->npe == 8) FEM_L(8, double, double, double, false);
         FEM_L(4, double, double, double, false);

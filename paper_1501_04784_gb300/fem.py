@@ -183,13 +183,14 @@ class Mesh:
         return dX, dc
 
     def load_vector(self, X, src, prec="fp64", out=None, stream=None):
-        """Global load vector F [n_nodes] of the per-element constant source src."""
+        """Global load vector F [n_nodes] of the per-element constant source src [n_elems]
+        (elasticity: F [3 n_nodes] of the per-element body force src [n_elems, 3])."""
         p = _prec(prec)
         if self.nnz is None:
             self.pattern(stream)
         vd = value_dtype(prec)
         if out is None:
-            out = torch.empty(self.n_nodes, dtype=vd, device=X.device)
+            out = torch.empty(self.dofs * self.n_nodes, dtype=vd, device=X.device)
         abi.check(abi.load().fem_load_vector(self._h, p, _dev(X, "X"), _DT[X.dtype], _dev(src, "src"), _DT[src.dtype],
                                              _dev(out, "F", vd), _stream(stream)))
         return out

@@ -223,8 +223,6 @@ def test_elastic_unsupported_entry_points(fem):
     mesh.pattern()
     Xd, cd, _, _ = inputs(m, "fp64")
     with pytest.raises(abi.FemError, match="FEM_ERR_UNSUPPORTED"):
-        mesh.load_vector(Xd, dev(m.c, torch.float64), "fp64")
-    with pytest.raises(abi.FemError, match="FEM_ERR_UNSUPPORTED"):
         mesh.vjp(Xd, cd, torch.zeros(mesh.nnz, dtype=torch.float64, device="cuda"), "fp64")
     with pytest.raises(abi.FemError, match="FEM_ERR_UNSUPPORTED"):
         fem.build_K_batched([mesh], [Xd], [cd], "fp64")
@@ -247,3 +245,52 @@ def test_elastic_row_windows(fem, prec, opts):
     mesh.sync()
     ref = oracle_el(m, X, c)
     assert rel_err(vals.cpu().numpy(), ref["vals"], ref["cs"]) <= (TOL_FP64 if prec == "fp64" else TOL_MIXED)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_elastic_budget_groups_bitwise_equal(fem, prec):
+    """Under a budget too small for all closures the plan runs in patch groups
+    (Eq. 10): the elasticity build gives exactly the unbudgeted values."""
+    m = meshgen.hex_grid(16, jitter=0.2, seed=77, permute_nodes=True, permute_elems=True)
+    Xd, cd, _, _ = inputs(m, prec)
+    free = make(fem, m, patch_entries=256, fp64_fused=1)
+    ref = free.build_K(Xd, cd, prec)
+    need = free.info()["plan_bytes"]
+    tight = make(fem, m, patch_entries=256, mem_budget_bytes=int(need * 0.75), fp64_fused=1)
+    got = tight.build_K(Xd, cd, prec)
+    tight.sync()
+    assert tight.info()["n_groups"] > 1
+    assert torch.equal(got, ref)
+
+
+def test_elastic_autotune(fem):
+    m = MESHES["hex_6x5x4_perm"]()
+    mesh = make(fem, m)
+    Xd, cd, X, c = inputs(m, "mixed")
+    t = mesh.autotune(Xd, cd, "mixed")
+    assert t["tried"] >= 3 and t["patch_entries"] in (1536, 2048, 3072, 4096, 5120)
+    vals = mesh.build_K(Xd, cd, "mixed").cpu().numpy()
+    ref = oracle_el(m, X, c)
+    assert rel_err(vals, ref["vals"], ref["cs"]) <= TOL_MIXED
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["hex_6x5x4_perm", "tet_5x4x3_perm"])
+def test_elastic_body_force_load(fem, name, prec):
+    """The elasticity load vector: F[3n + i] = sum_e b_e,i integral N_a against the
+    oracle's scalar load of each component, and the total force sum_e b_e vol_e."""
+    m = MESHES[name]()
+    mesh = make(fem, m, patch_entries=64)
+    mesh.pattern()
+    b = np.random.default_rng(4).standard_normal((m.n_elems, 3))
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    X = m.X if prec == "fp64" else m.X.astype(np.float32)
+    bb = b if prec == "fp64" else b.astype(np.float32)
+    F = mesh.load_vector(dev(X, dt), dev(bb, dt), prec)
+    mesh.sync()
+    F = F.cpu().numpy().astype(np.float64)
+    ref = oracle.load_vector(m.npe, np.asarray(X, np.float64), m.E, np.asarray(bb, np.float64))
+    scale = oracle.load_vector(m.npe, np.asarray(X, np.float64), m.E, np.abs(np.asarray(bb, np.float64)))
+    tol = TOL_FP64 if prec == "fp64" else TOL_MIXED
+    assert F.shape == (3 * m.n_nodes,)
+    assert np.max(np.abs(F - ref) / np.maximum(scale, 1e-300)) <= tol

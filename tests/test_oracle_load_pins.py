@@ -128,3 +128,18 @@ def test_load_planted_mistakes_are_caught(tmp_path, oracle_lib, name):
 
     res = run_pins(load, oracle_lib)
     assert not all(res.values()), f"mutation {name} passed every pin: {res}"
+
+
+@pytest.mark.parametrize("npe", [8, 4])
+def test_body_force_load_components(oracle_lib, npe):
+    """The elasticity operator's load of a body force b_e: component i of F is the
+    scalar load of b_e,i, so a uniform force on the tiled unit cube totals b, and
+    its components sit at DOFs 3n + i."""
+    gen = meshgen.hex_grid if npe == 8 else meshgen.kuhn_tets
+    m = gen(3, 2, 2, jitter=0.3, seed=6, c_law="one", permute_nodes=True)
+    bvec = np.array([0.5, -2.0, 1.25])
+    F = oracle_lib.load_vector(npe, m.X, m.E, np.tile(bvec, (m.n_elems, 1)))
+    assert F.shape == (3 * m.n_nodes,)
+    assert np.allclose(F.reshape(-1, 3).sum(axis=0), bvec, rtol=0, atol=1e-13)
+    w = oracle_lib.load_vector(npe, m.X, m.E, np.ones(m.n_elems))
+    assert np.allclose(F.reshape(-1, 3), np.outer(w, bvec), rtol=0, atol=1e-15)
