@@ -109,7 +109,13 @@ typedef struct {
                                     2 = linear isotropic elasticity, three DOFs per node
                                     (Algorithm 1's Mapping with DOFxn = 3): see "Elasticity"
                                     below.  fem_vjp is for the stiffness operator only */
-    int reserved[4];
+    int host_direct;             /* fem_build_K_host / _async: 0 (default) = K's values are
+                                    built in device staging and copied out in one transfer,
+                                    unless the memory budget refuses the staging; 1 = always
+                                    write them straight into vals_host (page-locked, mapped
+                                    through unified addressing), for K larger than device
+                                    memory or the budget */
+    int reserved[3];
 } fem_options;
 
 /*
@@ -145,7 +151,10 @@ typedef struct {
     size_t plan_bytes;           /* device bytes held by the cached pattern and plan */
     size_t budget_bytes;         /* the budget in force (0 = none) */
     int32_t n_groups;            /* patch groups the numeric build runs in under the budget */
-    int32_t reserved[7];
+    int32_t reserved0;
+    size_t live_bytes;           /* device bytes the library holds for the mesh now */
+    size_t peak_bytes;           /* the most it has held at once */
+    int32_t reserved[2];
 } fem_info;
 
 /* Default options (see the field comments). */
@@ -221,7 +230,11 @@ fem_status fem_build_K(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype,
  * fem_build_K with HOST inputs and outputs (page-locked memory gives full
  * copy bandwidth; pageable memory works but is slower): copies X and c to
  * library-owned device buffers, builds, copies vals back.  Blocks until vals
- * is on the host.
+ * is on the host.  Host-resident K: when the memory budget cannot hold the
+ * values (or fem_options.host_direct is set) the kernel writes them straight
+ * into vals_host, which must then be page-locked (FEM_ERR_BUDGET otherwise);
+ * with the patch groups of the budget this builds K for meshes whose matrix
+ * exceeds device memory.
  */
 fem_status fem_build_K_host(fem_mesh m, fem_prec p, const void *X_host, fem_dtype x_dtype,
                             const void *c_host, fem_dtype c_dtype, void *vals_host, void *stream);

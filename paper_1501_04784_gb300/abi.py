@@ -26,7 +26,7 @@ class fem_options(ctypes.Structure):
                 ("locality_order", ctypes.c_int), ("fp64_sums", ctypes.c_int),
                 ("fp64_fused", ctypes.c_int), ("fp64_dets", ctypes.c_int),
                 ("wait_spins", ctypes.c_int), ("debug_stall", ctypes.c_int),
-                ("operator_kind", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("operator_kind", ctypes.c_int), ("host_direct", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class fem_info(ctypes.Structure):
@@ -36,7 +36,8 @@ class fem_info(ctypes.Structure):
                 ("max_patch_elems", ctypes.c_int64), ("n_colors", ctypes.c_int32),
                 ("max_row_len", ctypes.c_int32), ("plan_bytes", ctypes.c_size_t),
                 ("budget_bytes", ctypes.c_size_t), ("n_groups", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("reserved0", ctypes.c_int32), ("live_bytes", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class fem_tuning(ctypes.Structure):

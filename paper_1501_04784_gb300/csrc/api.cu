@@ -429,6 +429,17 @@ fem_status fem_build_K(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype,
 }
 
 namespace fem {
+// Device address of a page-locked host buffer (unified addressing), or null if
+// the buffer is not page-locked.
+static void *mapped(void *host) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // Copy in, build, copy out, ordered on s through one of the mesh's two staging
 // slots (see fem_mesh_s::host_stage); returns without waiting.
 static fem_status host_build(fem_mesh m, fem_prec p, const void *X_host, fem_dtype x_dtype, const void *c_host,
@@ -447,8 +458,22 @@ static fem_status host_build(fem_mesh m, fem_prec p, const void *X_host, fem_dty
     const size_t cb = (size_t)m->n_elems * (is_elastic(m) ? 2 : 1) * dsize(c_dtype);
     const size_t vb = (size_t)user_nnz(m) * (p == FEM_FP64 ? 8 : 4);
     const size_t xo = 0, co = (xb + 255) / 256 * 256, vo = co + (cb + 255) / 256 * 256;
-    const size_t total = vo + vb;
+    // Values in device staging and one copy out; or (host_direct, or when the
+    // budget refuses the staging) written by the kernel straight into vals_host
+    // through its device mapping.
+    void *direct = nullptr;
     const int k = m->stage_next;
+    const bool stage_fits = m->host_stage[k].n >= vo + vb || !m->arena.budget ||
+                            m->arena.live - m->host_stage[k].n + vo + vb <= m->arena.budget;
+    if (m->opt.host_direct || !stage_fits) {
+        direct = mapped(vals_host);
+        if (!direct) {
+            set_error("%s: %s; page-lock vals_host to have the values written straight into it", who,
+                      m->opt.host_direct ? "host_direct is set" : "the memory budget cannot stage the values");
+            return m->opt.host_direct ? FEM_ERR_ARG : FEM_ERR_BUDGET;
+        }
+    }
+    const size_t total = direct ? vo : vo + vb;
     for (cudaEvent_t *e : {&m->stage_free[0], &m->stage_free[1], &m->built})
         if (!*e) FEM_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     if (m->host_stage[k].n < total) {
@@ -462,9 +487,9 @@ static fem_status host_build(fem_mesh m, fem_prec p, const void *X_host, fem_dty
     FEM_CUDA(cudaMemcpyAsync(base + xo, X_host, xb, cudaMemcpyHostToDevice, s));
     FEM_CUDA(cudaMemcpyAsync(base + co, c_host, cb, cudaMemcpyHostToDevice, s));
     FEM_CUDA(cudaStreamWaitEvent(s, m->built, 0));
-    FEM_TRY(fem_build_K(m, p, base + xo, x_dtype, base + co, c_dtype, base + vo, s));
+    FEM_TRY(fem_build_K(m, p, base + xo, x_dtype, base + co, c_dtype, direct ? direct : base + vo, s));
     FEM_CUDA(cudaEventRecord(m->built, s));
-    FEM_CUDA(cudaMemcpyAsync(vals_host, base + vo, vb, cudaMemcpyDeviceToHost, s));
+    if (!direct) FEM_CUDA(cudaMemcpyAsync(vals_host, base + vo, vb, cudaMemcpyDeviceToHost, s));
     FEM_CUDA(cudaEventRecord(m->stage_free[k], s));
     return FEM_OK;
 }
@@ -685,6 +710,8 @@ fem_status fem_mesh_info(fem_mesh m, fem_info *info) {
     info->plan_bytes = m->plan.bytes() + m->rowptr.bytes() + m->col.bytes() + m->inc_ptr.bytes() + m->inc_elem.bytes();
     info->budget_bytes = m->arena.budget;
     info->n_groups = m->n_groups;
+    info->live_bytes = m->arena.live;
+    info->peak_bytes = m->arena.peak;
     return FEM_OK;
 }
 

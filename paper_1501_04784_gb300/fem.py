@@ -211,7 +211,7 @@ class Mesh:
     def info(self) -> dict:
         i = abi.fem_info()
         abi.check(abi.load().fem_mesh_info(self._h, ctypes.byref(i)))
-        return {f: getattr(i, f) for f, _ in abi.fem_info._fields_ if f != "reserved"}
+        return {f: getattr(i, f) for f, _ in abi.fem_info._fields_ if not f.startswith("reserved")}
 
 
 def batched_config(meshes, prec="mixed") -> dict:

@@ -314,3 +314,49 @@ def test_zero_volume_element_is_reported(fem, prec):
     bad.sync()
     ref = oracle_K(m, Xr, c)
     assert rel_err(vals.cpu().numpy(), ref["vals"], ref["cs"]) <= (TOL_FP64 if prec == "fp64" else TOL_MIXED)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_host_resident_K(fem, prec):
+    """K written by the kernel straight into page-locked host memory (host_direct):
+    equal to the device build bit for bit; a pageable output is refused."""
+    from paper_1501_04784_gb300 import abi
+    m = meshgen.hex_grid(24, 20, 16, jitter=0.25, seed=31, permute_nodes=True, permute_elems=True)
+    Xd, cd, X, c = inputs(m, prec)
+    ref = make(fem, m, fp64_fused=1).build_K(Xd, cd, prec)
+    Xh, ch = Xd.cpu().pin_memory(), cd.cpu().pin_memory()
+    direct = make(fem, m, host_direct=1, fp64_fused=1)
+    out = torch.empty(ref.numel(), dtype=ref.dtype).pin_memory()
+    assert torch.equal(direct.build_K_host(Xh, ch, prec, out=out), ref.cpu())
+    with pytest.raises(abi.FemError, match="FEM_ERR_ARG"):
+        direct.build_K_host(Xh, ch, prec, out=torch.empty(ref.numel(), dtype=ref.dtype))   # pageable
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_host_resident_K_under_budget(fem, prec):
+    """A memory budget with room for the symbolic phase, the plan and the inputs
+    but not for K's values (the 3N x 3N elasticity matrix, whose values outweigh the
+    symbolic phase's scratch): fem_build_K_host writes them straight into the
+    page-locked host buffer by itself, never exceeds the budget, and equals the
+    device build."""
+    m = meshgen.hex_grid(24, 20, 16, jitter=0.25, seed=31, permute_nodes=True, permute_elems=True)
+    dt = torch.float32 if prec == "mixed" else torch.float64
+    lame = meshgen.lame(m)
+    Xd, cd = dev(m.X, dt), dev(lame, dt)
+
+    def el(**o):
+        return fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), operator_kind=2,
+                        fp64_fused=1, **o)
+    ref = el().build_K(Xd, cd, prec)
+    probe = el()
+    probe.pattern()
+    info = probe.info()
+    vbytes = ref.numel() * ref.element_size()
+    inputs_bytes = Xd.numel() * Xd.element_size() + cd.numel() * cd.element_size() + 512
+    budget = max(info["peak_bytes"], info["live_bytes"] + inputs_bytes) + vbytes // 4
+    assert info["live_bytes"] + inputs_bytes + vbytes > budget
+    tight = el(mem_budget_bytes=budget)
+    out = torch.empty(ref.numel(), dtype=ref.dtype).pin_memory()
+    got = tight.build_K_host(Xd.cpu().pin_memory(), cd.cpu().pin_memory(), prec, out=out)
+    assert torch.equal(got, ref.cpu())
+    assert tight.info()["peak_bytes"] <= budget
