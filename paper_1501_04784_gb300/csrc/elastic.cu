@@ -33,11 +33,11 @@ static fem_status el_set_smem(F *f, size_t bytes) {
 
 static size_t el_align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-// Element row of the thread: block row a = threadIdx.x % NPE of its element.
+// The thread's blocks of its element (node a = threadIdx.x % NPE; see elastic.cuh).
 template <int NPE, typename T, typename S, bool MIXED>
-__device__ __forceinline__ void elastic_row(const S (*xc)[3], T lam, T mu, int a, float thr, bool fp64_det,
-                                            T (&k)[NPE][9]) {
-    if constexpr (NPE == 8) elastic_brick_row<T, S>(xc, lam, mu, k);
+__device__ __forceinline__ void elastic_blocks(const S (*xc)[3], T lam, T mu, int a, float thr, bool fp64_det,
+                                               T (&k)[elastic_nblk<NPE>()][9]) {
+    if constexpr (NPE == 8) elastic_brick_blocks<T, S>(xc, lam, mu, k);
     else elastic_tet_row<T, S, MIXED>(xc, lam, mu, a, thr, fp64_det, k);
 }
 
@@ -72,11 +72,11 @@ __global__ void __launch_bounds__(EL_INT_THREADS) k_elastic_integrate(const int3
 #pragma unroll
             for (int b = 0; b < NPE; ++b) xc[b][0] = xc[b][1] = xc[b][2] = S(0);
         }
-        T k[NPE][9];
-        elastic_row<NPE, T, S, MIXED>(xc, lam, mu, a, thr, fp64_det, k);
+        T k[elastic_nblk<NPE>()][9];
+        elastic_blocks<NPE, T, S, MIXED>(xc, lam, mu, a, thr, fp64_det, k);
         if (act) {
             if (status && !isfinite(k[0][0])) atomicOr(status, STATUS_NONFINITE);
-            store_packed_row<NPE, T>(ke_out + e * NPK, a, k);
+            store_packed_blocks<NPE, T>(ke_out + e * NPK, a, k);
         }
     }
 }
@@ -130,7 +130,6 @@ __device__ __forceinline__ void elastic_patch_body(const PlanView &pv, const S *
     __syncthreads();
 
     const uint16_t *aidx16 = reinterpret_cast<const uint16_t *>(pv.celem_aidx);
-    const int q0 = a * (a + 1) / 2;  // packed node pair (a, 0)
     // Owned rows in windows [k0, k1) whose slots fit the accumulators (L.win): with
     // WIN false one window covers the patch; with WIN true (blocks that outgrow
     // shared memory: FP64, or patches planned larger than the limit) each window
@@ -164,7 +163,8 @@ __device__ __forceinline__ void elastic_patch_body(const PlanView &pv, const S *
 #pragma unroll
             for (int b = 0; b < NPE; ++b)
                 if (!FEM_IN_BOUNDS(ln[b] < ncn || !act, wc.status)) ln[b] = 0;
-            AccT k[NPE][9];
+            constexpr int NB = elastic_nblk<NPE>();
+            AccT k[NB][9];
             if constexpr (FUSED) {
                 S xc[NPE][3];
 #pragma unroll
@@ -180,39 +180,47 @@ __device__ __forceinline__ void elastic_patch_body(const PlanView &pv, const S *
                     lam = AccT(__ldg(c + 2 * e));
                     mu = AccT(__ldg(c + 2 * e + 1));
                 }
-                elastic_row<NPE, AccT, S, MIXED>(xc, lam, mu, a, thr, fp64_det, k);
+                elastic_blocks<NPE, AccT, S, MIXED>(xc, lam, mu, a, thr, fp64_det, k);
                 if (act && !isfinite(k[0][0])) atomicOr(wc.status, STATUS_NONFINITE);
             } else {
                 if (act) {
                     int64_t e = pv.celem_id[ci];
                     if (!FEM_IN_BOUNDS(e >= 0 && e < pv.n_elems, wc.status)) e = 0;
-                    load_packed_row<NPE, AccT>(ke + e * NPK, a, k);
+                    load_packed_blocks<NPE, AccT>(ke + e * NPK, a, k);
                 } else {
 #pragma unroll
-                    for (int b = 0; b < NPE; ++b)
+                    for (int m = 0; m < NB; ++m)
 #pragma unroll
-                        for (int m = 0; m < 9; ++m) k[b][m] = AccT(0);
+                        for (int n = 0; n < 9; ++n) k[m][n] = AccT(0);
                 }
             }
-            // accumulator slots of the pairs (a, b), b <= a (scratch for rows the
+            // accumulator slots of the thread's pairs (a, b) (scratch for rows the
             // patch does not own), and whether the pair's row is node b's: closure
             // nodes are numbered in ascending global order, so g_a < g_b exactly when
             // ln[a] < ln[b], and then the block goes in transposed
-            int slot[NPE];
+            int slot[NB];
+            bool trans[NB];
             const uint16_t lna = NPE == 8 ? (a & 4 ? (a & 2 ? (a & 1 ? ln[7] : ln[6]) : (a & 1 ? ln[5] : ln[4]))
                                                    : (a & 2 ? (a & 1 ? ln[3] : ln[2]) : (a & 1 ? ln[1] : ln[0])))
                                           : (a & 2 ? (a & 1 ? ln[3] : ln[2]) : (a & 1 ? ln[1] : ln[0]));
 #pragma unroll
-            for (int b = 0; b < NPE; ++b) {
-                slot[b] = -1;
-                if (act && b <= a) {
-                    const int q = q0 + b;
+            for (int m = 0; m < NB; ++m) {
+                const int b = blk_node<NPE>(a, m);
+                // ln[b]: the partner's lane holds it as its own (bricks), or b is m
+                uint16_t lnb;
+                if constexpr (NPE == 8) lnb = (uint16_t)__shfl_sync(0xffffffffu, (int)lna, (lane & ~7) + b);
+                else lnb = ln[m];
+                trans[m] = lna < lnb;
+                slot[m] = -1;
+                if (act && blk_valid<NPE>(a, m)) {
+                    const int A = a > b ? a : b, B = a > b ? b : a;
+                    const int q = A * (A + 1) / 2 + B;
                     int t = aidx16[((int64_t)(q >> 1) * pv.aidx_n + ci) * 2 + (q & 1)];
                     // scratch targets (rows of other patches) to the window's scratch,
                     // owned slots outside the window skipped
                     if constexpr (WIN) t = t >= L.trash ? L.win + (t - L.trash) : (t >= s0 && t < s1 ? t - s0 : -1);
                     if (!FEM_IN_BOUNDS(t < L.acc_cap, wc.status)) t = -1;
-                    slot[b] = t;
+                    slot[m] = t;
                 }
             }
             const int last = min(base + epb, nel) - 1;
@@ -224,28 +232,28 @@ __device__ __forceinline__ void elastic_patch_body(const PlanView &pv, const S *
                     if (g > 0) phase_wait(mb, g - 1, wc);
                     if (mine) {
 #pragma unroll
-                        for (int b = 0; b < NPE; ++b) {
-                            if (slot[b] < 0) continue;
-                            AccT *dst = acc + 9 * slot[b];
-                            if (b == a) {
+                        for (int m = 0; m < NB; ++m) {
+                            if (slot[m] < 0) continue;
+                            AccT *dst = acc + 9 * slot[m];
+                            if (blk_node<NPE>(a, m) == a) {
                                 // diagonal block: its lower half (i >= j) only
                                 AccT o0 = dst[0], o3 = dst[3], o4 = dst[4], o6 = dst[6], o7 = dst[7], o8 = dst[8];
-                                dst[0] = o0 + k[b][0];
-                                dst[3] = o3 + k[b][3];
-                                dst[4] = o4 + k[b][4];
-                                dst[6] = o6 + k[b][6];
-                                dst[7] = o7 + k[b][7];
-                                dst[8] = o8 + k[b][8];
+                                dst[0] = o0 + k[m][0];
+                                dst[3] = o3 + k[m][3];
+                                dst[4] = o4 + k[m][4];
+                                dst[6] = o6 + k[m][6];
+                                dst[7] = o7 + k[m][7];
+                                dst[8] = o8 + k[m][8];
                             } else {
-                                const bool tr = lna < ln[b];
+                                const bool tr = trans[m];
                                 AccT old[9];
 #pragma unroll
-                                for (int m = 0; m < 9; ++m) old[m] = dst[m];
+                                for (int n = 0; n < 9; ++n) old[n] = dst[n];
 #pragma unroll
                                 for (int i3 = 0; i3 < 3; ++i3)
 #pragma unroll
                                     for (int j3 = 0; j3 < 3; ++j3)
-                                        dst[3 * i3 + j3] = old[3 * i3 + j3] + (tr ? k[b][3 * j3 + i3] : k[b][3 * i3 + j3]);
+                                        dst[3 * i3 + j3] = old[3 * i3 + j3] + (tr ? k[m][3 * j3 + i3] : k[m][3 * i3 + j3]);
                             }
                         }
                     }

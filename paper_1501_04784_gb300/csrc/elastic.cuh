@@ -12,15 +12,12 @@
 //     P_ab = sum_q s_q v_a v_b^T
 // the block is K_ab = lambda P_ab + mu P_ab^T + mu tr(P_ab) I.
 //
-// Work split.  One thread computes one block row a of k_e (the 3 DOF rows of
-// node a): the blocks K_ab for every b, kept in registers as P_ab, of which the
-// caller uses b <= a (the lower triangle).  Computing the whole row keeps every
-// register index compile-time; the blocks above the diagonal are the price.
-//   Brick: 8 threads per element.  Thread a also forms the Jacobian's cofactor
-//   rows at Gauss point q = a and hands them to the other seven by warp shuffles,
-//   so each point's geometry is computed once per element.
-//   Tetrahedron: 4 threads per element; the integrand is constant and every
-//   thread forms the (cheap) geometry itself.
+// Work split.  NPE threads per element, thread a owning node a; the blocks each
+// computes are listed below (elastic_nblk, blk_node), kept in registers as P_ab.
+//   Brick: 8 threads per element, the circulant block set; shuffles share the
+//   Gauss-point geometry and the nodes' gradient vectors.
+//   Tetrahedron: 4 threads per element, the lower block row; the integrand is
+//   constant and every thread forms the (cheap) geometry itself.
 #pragma once
 
 #include "element.cuh"
@@ -48,19 +45,7 @@ __host__ __device__ constexpr double hgrad(int a, int q, int axis) {
                        : hsig(hb3(a)) * hat1(hb1(a), q >> 2) * hat1(hb2(a), (q >> 1) & 1);
 }
 
-// 8-way select of v[a] by a run-time index (a binary tree of selects, no
-// dynamic register indexing).
-template <typename T>
-__device__ __forceinline__ Vec3<T> select8(const Vec3<T> (&v)[8], int a) {
-    const bool s0 = a & 1, s1 = a & 2, s2 = a & 4;
-    auto sel = [](bool f, const Vec3<T> &x, const Vec3<T> &y) {
-        return Vec3<T>{f ? y.x : x.x, f ? y.y : x.y, f ? y.z : x.z};
-    };
-    const Vec3<T> a0 = sel(s0, v[0], v[1]), a1 = sel(s0, v[2], v[3]);
-    const Vec3<T> a2 = sel(s0, v[4], v[5]), a3 = sel(s0, v[6], v[7]);
-    return sel(s2, sel(s1, a0, a1), sel(s1, a2, a3));
-}
-
+// Select of v[a] by a run-time index (selects, no dynamic register indexing).
 template <typename T>
 __device__ __forceinline__ Vec3<T> select4(const Vec3<T> (&v)[4], int a) {
     const bool s0 = a & 1, s1 = a & 2;
@@ -83,13 +68,33 @@ __device__ __forceinline__ void lame_block(T lam, T mu, T (&p)[9]) {
     for (int m = 0; m < 9; ++m) p[m] = k[m];
 }
 
-// Brick, block row a = lane & 7 of the 8-lane group that holds the element (all
-// 32 lanes of the warp must call it: it shuffles).  xc = the element's node
-// coordinates (any values for an idle lane).  k[b][3i + j] = entry (3a + i, 3b + j).
-// Returns det J at the lane's own Gauss point q = a, times 8 (for the caller's
-// degeneracy check).
+// Blocks a thread computes.  A brick thread (node a of its element, 8 threads per
+// element) takes the circulant set b = (a + k) mod 8, k = 0..4: its diagonal block
+// and the off-diagonal pairs at circular distance 1 to 3 from a, plus distance 4
+// for a < 4.  Over the 8 threads that covers each of the 36 node pairs exactly
+// once.  Every thread holds 5 blocks (the fifth idle for a >= 4), where a split
+// by block rows would give thread a its a + 1 blocks (up to 8), and every
+// register index stays compile-time.  A tetrahedron thread (4 per element) takes
+// its lower block row b = 0..a.
+template <int NPE>
+__host__ __device__ constexpr int elastic_nblk() { return NPE == 8 ? 5 : 4; }
+template <int NPE>
+__device__ __forceinline__ int blk_node(int a, int k) { return NPE == 8 ? ((a + k) & 7) : k; }
+template <int NPE>
+__device__ __forceinline__ bool blk_valid(int a, int k) { return NPE == 8 ? (k < 4 || a < 4) : (k <= a); }
+
+// Brick, thread a = lane & 7 of the 8-lane group that holds the element (all 32
+// lanes of the warp must call it: it shuffles).  xc = the element's node
+// coordinates (any values for an idle lane).  k[m][3i + j] = entry (3a + i, 3b + j)
+// of k_e for b = blk_node(a, m).
+//   Gauss point q = a: the thread forms the cofactor rows of 2 J_q and the point's
+//   factor and hands them to the element's other threads by shuffles, so each
+//   point's geometry is computed once per element.
+//   At every point each thread forms its own node's gradient vector v_a and
+//   takes its block partners' v_b from their lanes (shuffles again).
+// Returns det(2 J) at the thread's own point (for the caller's degeneracy check).
 template <typename T, typename S>
-__device__ __forceinline__ T elastic_brick_row(const S (*xc)[3], T lam, T mu, T (&k)[8][9]) {
+__device__ __forceinline__ T elastic_brick_blocks(const S (*xc)[3], T lam, T mu, T (&k)[5][9]) {
     const int lane = threadIdx.x & 31, a = lane & 7, base = lane & ~7;
     // this lane's Gauss point q = a: rows of 2 J (edge interpolations), cofactor
     // rows C_i = cross products of the other two rows, d = det(2 J)
@@ -109,10 +114,18 @@ __device__ __forceinline__ T elastic_brick_row(const S (*xc)[3], T lam, T mu, T 
         // s = |det J| / d^2 = 1 / (8 |d|) (Gauss weights 1)
         s = rcp_rn(T(8) * (d < T(0) ? -d : d));
     }
+    // node a's axis bits, its signs sigma_i and its hats at the two Gauss indices
+    const int b1 = (a ^ (a >> 1)) & 1, b2 = (a >> 1) & 1, b3 = a >> 2;
+    const T P = T(FEM_GP), Q = T(FEM_GQ);
+    const T f1[2] = {b1 ? Q : P, b1 ? P : Q}, f2[2] = {b2 ? Q : P, b2 ? P : Q}, f3[2] = {b3 ? Q : P, b3 ? P : Q};
+    const T g1 = b1 ? T(1) : T(-1), g2 = b2 ? T(1) : T(-1), g3 = b3 ? T(1) : T(-1);
+    int src_b[5];
 #pragma unroll
-    for (int b = 0; b < 8; ++b)
+    for (int m = 0; m < 5; ++m) src_b[m] = base + ((a + m) & 7);
 #pragma unroll
-        for (int m = 0; m < 9; ++m) k[b][m] = T(0);
+    for (int m = 0; m < 5; ++m)
+#pragma unroll
+        for (int n = 0; n < 9; ++n) k[m][n] = T(0);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int src = base + q;
@@ -123,24 +136,24 @@ __device__ __forceinline__ T elastic_brick_row(const S (*xc)[3], T lam, T mu, T 
         const Vec3<T> c2 = {__shfl_sync(0xffffffffu, C2.x, src), __shfl_sync(0xffffffffu, C2.y, src),
                             __shfl_sync(0xffffffffu, C2.z, src)};
         const T sq = __shfl_sync(0xffffffffu, s, src);
-        Vec3<T> v[8];
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const T h0 = T(hgrad(b, q, 0)), h1 = T(hgrad(b, q, 1)), h2 = T(hgrad(b, q, 2));
-            v[b] = {h0 * c0.x + h1 * c1.x + h2 * c2.x, h0 * c0.y + h1 * c1.y + h2 * c2.y,
-                    h0 * c0.z + h1 * c1.z + h2 * c2.z};
-        }
-        const Vec3<T> va = select8(v, a);
+        const int q1 = q >> 2, q2 = (q >> 1) & 1, q3 = q & 1;  // folded by the unrolling
+        const T h0 = g1 * f2[q2] * f3[q3], h1 = g2 * f1[q1] * f3[q3], h2 = g3 * f1[q1] * f2[q2];
+        const Vec3<T> va = {h0 * c0.x + h1 * c1.x + h2 * c2.x, h0 * c0.y + h1 * c1.y + h2 * c2.y,
+                            h0 * c0.z + h1 * c1.z + h2 * c2.z};
         const Vec3<T> w = {sq * va.x, sq * va.y, sq * va.z};
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            k[b][0] += w.x * v[b].x; k[b][1] += w.x * v[b].y; k[b][2] += w.x * v[b].z;
-            k[b][3] += w.y * v[b].x; k[b][4] += w.y * v[b].y; k[b][5] += w.y * v[b].z;
-            k[b][6] += w.z * v[b].x; k[b][7] += w.z * v[b].y; k[b][8] += w.z * v[b].z;
+        for (int m = 0; m < 5; ++m) {
+            Vec3<T> vb = va;
+            if (m > 0)
+                vb = {__shfl_sync(0xffffffffu, va.x, src_b[m]), __shfl_sync(0xffffffffu, va.y, src_b[m]),
+                      __shfl_sync(0xffffffffu, va.z, src_b[m])};
+            k[m][0] += w.x * vb.x; k[m][1] += w.x * vb.y; k[m][2] += w.x * vb.z;
+            k[m][3] += w.y * vb.x; k[m][4] += w.y * vb.y; k[m][5] += w.y * vb.z;
+            k[m][6] += w.z * vb.x; k[m][7] += w.z * vb.y; k[m][8] += w.z * vb.z;
         }
     }
 #pragma unroll
-    for (int b = 0; b < 8; ++b) lame_block(lam, mu, k[b]);
+    for (int m = 0; m < 5; ++m) lame_block(lam, mu, k[m]);
     return d;
 }
 
@@ -177,31 +190,43 @@ __device__ __forceinline__ T elastic_tet_row(const S (*xc)[3], T lam, T mu, int 
 // contiguous range of the packed array.
 __host__ __device__ constexpr int elastic_np(int npe) { return 3 * npe * (3 * npe + 1) / 2; }
 
+// Block (a, b) of a thread to or from the packed lower k_e: it lives in the
+// packed rows of max(a, b) (as stored, transposed when a < b); a diagonal block
+// keeps its lower half.
 template <int NPE, typename T>
-__device__ __forceinline__ void store_packed_row(T *out, int a, const T (&k)[NPE][9]) {
+__device__ __forceinline__ void store_packed_blocks(T *out, int a, const T (&k)[elastic_nblk<NPE>()][9]) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const int A = 3 * a + i;
-        T *row = out + A * (A + 1) / 2;
+    for (int m = 0; m < elastic_nblk<NPE>(); ++m) {
+        if (!blk_valid<NPE>(a, m)) continue;
+        const int b = blk_node<NPE>(a, m), A = a > b ? a : b, B = a > b ? b : a;
+        const bool tr = a < b;
 #pragma unroll
-        for (int b = 0; b < NPE; ++b)
+        for (int i = 0; i < 3; ++i) {
+            const int R = 3 * A + i;
+            T *row = out + R * (R + 1) / 2 + 3 * B;
 #pragma unroll
             for (int j = 0; j < 3; ++j)
-                if (b < a || (b == a && j <= i)) row[3 * b + j] = k[b][3 * i + j];
+                if (A != B || j <= i) row[j] = tr ? k[m][3 * j + i] : k[m][3 * i + j];
+        }
     }
 }
 
 template <int NPE, typename T>
-__device__ __forceinline__ void load_packed_row(const T *in, int a, T (&k)[NPE][9]) {
+__device__ __forceinline__ void load_packed_blocks(const T *in, int a, T (&k)[elastic_nblk<NPE>()][9]) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const int A = 3 * a + i;
-        const T *row = in + A * (A + 1) / 2;
+    for (int m = 0; m < elastic_nblk<NPE>(); ++m) {
+        const int b = blk_node<NPE>(a, m), A = a > b ? a : b, B = a > b ? b : a;
+        const bool tr = a < b, ok = blk_valid<NPE>(a, m);
 #pragma unroll
-        for (int b = 0; b < NPE; ++b)
+        for (int i = 0; i < 3; ++i) {
+            const int R = 3 * A + i;
+            const T *row = in + R * (R + 1) / 2 + 3 * B;
 #pragma unroll
-            for (int j = 0; j < 3; ++j)
-                k[b][3 * i + j] = (b < a || (b == a && j <= i)) ? __ldg(row + 3 * b + j) : T(0);
+            for (int j = 0; j < 3; ++j) {
+                const T v = (ok && (A != B || j <= i)) ? __ldg(row + j) : T(0);
+                if (tr) k[m][3 * j + i] = v; else k[m][3 * i + j] = v;
+            }
+        }
     }
 }
 
