@@ -137,8 +137,10 @@ typedef struct {
  *   - patch_entries counts node pairs (each a 3x3 block; default 4096 for bricks,
  *     1536 for tetrahedra) and block_threads defaults to 512 for bricks;
  *   - fem_load_vector takes a body force [n_elems][3] and writes F [3 n_nodes];
- *   - fem_pattern_ptrs, fem_vjp and fem_build_K_batched answer FEM_ERR_UNSUPPORTED;
- *     fem_mesh_create refuses 3 n_nodes >= 2^31.
+ *   - fem_build_K_batched takes batches of elasticity meshes only (no mixing with
+ *     scalar operators), fused in both precisions;
+ *   - fem_pattern_ptrs and fem_vjp answer FEM_ERR_UNSUPPORTED; fem_mesh_create
+ *     refuses 3 n_nodes >= 2^31.
  */
 
 typedef struct {

@@ -577,11 +577,6 @@ fem_status fem_build_K_batched(const fem_mesh *meshes, int n, fem_prec p, const 
     }
     if (n == 0) return FEM_OK;
     for (int i = 0; i < n; ++i)
-        if (is_elastic(meshes[i])) {
-            set_error("mesh %d of the batch: batched builds cover the scalar operators", i);
-            return FEM_ERR_UNSUPPORTED;
-        }
-    for (int i = 0; i < n; ++i)
         if (meshes[i]->plan.chunked) {
             set_error("mesh %d of the batch is planned in groups under its memory budget", i);
             return FEM_ERR_UNSUPPORTED;

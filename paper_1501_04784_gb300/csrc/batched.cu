@@ -24,6 +24,7 @@ struct BatchCtx {
     bool mixed = true;
     fem_dtype xd = FEM_F32, cd = FEM_F32;
     int npe = 8;
+    bool elastic = false;  // the elasticity operator (operator_kind 2)
     BatchItem *d_items = nullptr;
     int64_t *d_prefix = nullptr;
     std::vector<BatchItem> h_items;
@@ -60,8 +61,11 @@ static float mesh_threshold(fem_mesh m) {
 }
 
 static void fill_items(BatchCtx &c, const void *const *X, const void *const *cc, void *const *vals) {
-    for (size_t i = 0; i < c.meshes.size(); ++i)
+    for (size_t i = 0; i < c.meshes.size(); ++i) {
         c.h_items[i] = BatchItem{c.meshes[i]->plan.view(), X[i], cc[i], vals[i], mesh_threshold(c.meshes[i]), 0};
+        // the elasticity operator's values: the DOF matrix (bounds of the debug build)
+        if (c.elastic) c.h_items[i].pv.nnz = 9 * c.meshes[i]->nnz - 3 * c.meshes[i]->n_nodes;
+    }
 }
 
 static fem_status upload_items(BatchCtx &c, cudaStream_t s) {
@@ -91,7 +95,12 @@ static fem_status create_ctx(BatchCtx &c, const void *const *X, const void *cons
     // tuner: time every candidate launch shape on the real batch, keep the fastest
     const fem_options &o = c.meshes[0]->opt;
     std::vector<std::pair<int, int>> cands;
-    if (o.block_threads > 0) {
+    if (c.elastic) {
+        if (o.block_threads > 0) cands.push_back({elastic_threads(c.npe, o.block_threads), o.blocks_per_sm});
+        else
+            for (int t : {128, 256, 512})
+                if (t <= elastic_threads(c.npe, 512)) cands.push_back({t, 0});
+    } else if (o.block_threads > 0) {
         cands.push_back({std::min((o.block_threads + 31) / 32 * 32, patch_max_threads(c.npe)), o.blocks_per_sm});
     } else {
         for (int t : {128, 256, 512})
@@ -111,7 +120,9 @@ static fem_status create_ctx(BatchCtx &c, const void *const *X, const void *cons
         bl.n = n;
         bl.mode = kernel_mode(c.meshes[0]->opt);
         bl.wait = wait_ctl(c.meshes[0]);
-        if (batched_config(c.npe, c.mixed, pm, cd.first, cd.second, &bl) != FEM_OK) continue;
+        const fem_status cs = c.elastic ? elastic_batched_config(c.npe, c.mixed, pm, cd.first, cd.second, &bl)
+                                        : batched_config(c.npe, c.mixed, pm, cd.first, cd.second, &bl);
+        if (cs != FEM_OK) continue;
         FEM_TRY(launch_batched_kernel(bl, s));  // warm-up
         float tot = 0.f;
         const int reps = cands.size() > 1 ? 3 : 0;
@@ -173,9 +184,10 @@ static BatchCtx *find_ctx(const fem_mesh *ms, int n, bool mixed, fem_dtype xd, f
 fem_status launch_batched(const fem_mesh *ms, int n, bool mixed, const void *const *X, fem_dtype xd,
                           const void *const *c, fem_dtype cd, void *const *vals, cudaStream_t s) {
     const int npe = ms[0]->npe;
+    const bool elastic = ms[0]->opt.operator_kind == 2;
     for (int i = 1; i < n; ++i)
-        if (ms[i]->npe != npe) {
-            set_error("a batch must hold one element type");
+        if (ms[i]->npe != npe || (ms[i]->opt.operator_kind == 2) != elastic) {
+            set_error("a batch must hold one element type and either scalar or elasticity meshes only");
             return FEM_ERR_ARG;
         }
     const fem_dtype want = mixed ? FEM_F32 : FEM_F64;
@@ -192,6 +204,7 @@ fem_status launch_batched(const fem_mesh *ms, int n, bool mixed, const void *con
         nc->xd = xd;
         nc->cd = cd;
         nc->npe = npe;
+        nc->elastic = elastic;
         FEM_TRY(create_ctx(*nc, X, c, vals, s));
         if (g_batch_ctx.size() >= MAX_BATCH_CTX) g_batch_ctx.erase(g_batch_ctx.begin());
         g_batch_ctx.push_back(std::move(nc));

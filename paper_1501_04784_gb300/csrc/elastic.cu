@@ -312,6 +312,29 @@ __global__ void __launch_bounds__(elastic_max_threads<NPE, AccT>(), elastic_min_
         elastic_patch_body<NPE, AccT, S, CT, FUSED, MIXED, WIN>(pv, X, c, ke, vals, thr, p, L, mode, mb, g, wc);
 }
 
+// Persistent kernel over the patches of many meshes (as k_patch_batched): work
+// item w is patch w - prefix[m] of mesh m.
+template <int NPE, typename AccT, bool MIXED, bool WIN>
+__global__ void __launch_bounds__(elastic_max_threads<NPE, AccT>(), elastic_min_blocks<NPE, AccT>())
+    k_elastic_patch_batched(const BatchItem *__restrict__ items, const int64_t *__restrict__ prefix, int n,
+                            PatchSmem L, unsigned mode, WaitCtl wc) {
+    const int64_t total = prefix[n];
+    __shared__ uint64_t mb[PHASE_RING];
+    phase_init(mb);
+    uint32_t g = 0;
+    for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+        int lo = 0, hi = n;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (prefix[mid] <= w) lo = mid; else hi = mid;
+        }
+        const BatchItem &it = items[lo];
+        elastic_patch_body<NPE, AccT, AccT, AccT, true, MIXED, WIN>(it.pv, (const AccT *)it.X, (const AccT *)it.c,
+                                                                    nullptr, (AccT *)it.vals, it.thr, w - prefix[lo],
+                                                                    L, mode, mb, g, wc);
+    }
+}
+
 // ------------------------------------------------------------------- launch
 PatchSmem elastic_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsize, int win) {
     PatchSmem L{};
@@ -437,6 +460,70 @@ fem_status launch_elastic_patch(const PatchArgs &a, cudaStream_t s) {
     if (a.xd == FEM_F64 && a.cd == FEM_F32) FEM_E(4, float, double, float, true, true);
     FEM_E(4, float, double, double, true, true);
 #undef FEM_E
+}
+
+template <int NPE, typename AccT, bool MIXED>
+static fem_status elastic_batched_config_t(const PlanMax &pm, int threads, int blocks_per_sm, BatchLaunch *out) {
+    int dev = 0, max_optin = 0;
+    FEM_CUDA(cudaGetDevice(&dev));
+    FEM_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa{};
+    FEM_CUDA(cudaFuncGetAttributes(&fa, k_elastic_patch_batched<NPE, AccT, MIXED, true>));
+    const int win = elastic_window(pm, true, MIXED, sizeof(AccT), (size_t)max_optin - fa.sharedSizeBytes);
+    if (win <= 0) {
+        set_error("a patch of the batch does not fit in shared memory (limit %d bytes)", max_optin);
+        return FEM_ERR_UNSUPPORTED;
+    }
+    const PatchSmem L = elastic_smem_layout(pm, true, MIXED, sizeof(AccT), win);
+    const bool use_win = win < pm.max_acc;
+    auto f = use_win ? k_elastic_patch_batched<NPE, AccT, MIXED, true> : k_elastic_patch_batched<NPE, AccT, MIXED, false>;
+    FEM_TRY(el_set_smem(f, L.total));
+    threads = std::min(threads, elastic_max_threads<NPE, AccT>());
+    int per_sm = 0;
+    FEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, L.total));
+    if (per_sm < 1) {
+        set_error("batched elasticity kernel cannot be resident with %d threads", threads);
+        return FEM_ERR_UNSUPPORTED;
+    }
+    if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
+    out->L = L;
+    out->threads = threads;
+    out->grid = num_sms() * per_sm;
+    out->elastic = true;
+    out->win = use_win;
+    return FEM_OK;
+}
+
+fem_status elastic_batched_config(int npe, bool mixed, const PlanMax &pm, int threads, int blocks_per_sm,
+                                  BatchLaunch *out) {
+    out->npe = npe;
+    out->mixed = mixed;
+    if (mixed) return npe == 8 ? elastic_batched_config_t<8, float, true>(pm, threads, blocks_per_sm, out)
+                               : elastic_batched_config_t<4, float, true>(pm, threads, blocks_per_sm, out);
+    return npe == 8 ? elastic_batched_config_t<8, double, false>(pm, threads, blocks_per_sm, out)
+                    : elastic_batched_config_t<4, double, false>(pm, threads, blocks_per_sm, out);
+}
+
+fem_status launch_elastic_batched_kernel(const BatchLaunch &bl, cudaStream_t s) {
+#define FEM_EB(NPE, T, MX, W)                                                                                 \
+    k_elastic_patch_batched<NPE, T, MX, W><<<bl.grid, bl.threads, bl.L.total, s>>>(bl.items, bl.prefix, bl.n, \
+                                                                                    bl.L, bl.mode, bl.wait)
+    if (bl.mixed) {
+        if (bl.npe == 8) {
+            if (bl.win) FEM_EB(8, float, true, true); else FEM_EB(8, float, true, false);
+        } else {
+            if (bl.win) FEM_EB(4, float, true, true); else FEM_EB(4, float, true, false);
+        }
+    } else {
+        if (bl.npe == 8) {
+            if (bl.win) FEM_EB(8, double, false, true); else FEM_EB(8, double, false, false);
+        } else {
+            if (bl.win) FEM_EB(4, double, false, true); else FEM_EB(4, double, false, false);
+        }
+    }
+#undef FEM_EB
+    FEM_LAUNCHED("k_elastic_patch_batched");
+    return FEM_OK;
 }
 
 template <int NPE, typename T, typename S, typename CT, bool MIXED>

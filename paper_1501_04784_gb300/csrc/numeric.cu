@@ -636,6 +636,7 @@ fem_status batched_config(int npe, bool mixed, const PlanMax &pm, int threads, i
 }
 
 fem_status launch_batched_kernel(const BatchLaunch &bl, cudaStream_t s) {
+    if (bl.elastic) return launch_elastic_batched_kernel(bl, s);
 #define FEM_B(NPE, T, MX)                                                                                   \
     k_patch_batched<NPE, T, T, T, MX><<<bl.grid, bl.threads, bl.L.total, s>>>(bl.items, bl.prefix, bl.n, bl.L, \
                                                                                bl.mode, bl.wait)

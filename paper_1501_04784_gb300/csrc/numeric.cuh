@@ -113,6 +113,8 @@ struct BatchLaunch {
     PatchSmem L{};
     int threads = 256, grid = 1;
     WaitCtl wait{nullptr, WAIT_SPINS_DEFAULT, 0};
+    bool elastic = false;  // the elasticity operator's kernel (elastic.cu)
+    bool win = false;      // its row-window variant (the FP64 blocks outgrow shared memory)
 };
 
 // Shared memory, residency and grid of the batched kernel for `threads` threads
@@ -145,5 +147,8 @@ PatchSmem elastic_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t x
 int elastic_window(const PlanMax &P, bool fused, bool mixed, size_t xsize, size_t limit);
 int elastic_threads(int npe, int requested);
 int elastic_blocks_per_sm(int npe, int threads);
+fem_status elastic_batched_config(int npe, bool mixed, const PlanMax &pm, int threads, int blocks_per_sm,
+                                  BatchLaunch *out);
+fem_status launch_elastic_batched_kernel(const BatchLaunch &bl, cudaStream_t s);
 
 }  // namespace fem
