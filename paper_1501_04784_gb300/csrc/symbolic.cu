@@ -346,7 +346,7 @@ __global__ void k_segment_ptr(const uint64_t *keys, int64_t n, int shift, int64_
 // it.  Owned-node colour sets are 128-bit masks in shared memory; the
 // element -> owned-node table is staged chunk by chunk so that the serial loop
 // runs from shared memory.
-static constexpr int COLOR_CHUNK = 2048;
+static constexpr int COLOR_CHUNK = 256;
 
 template <int NPE>
 __global__ void k_color(const uint64_t *ckeys, const int64_t *pe_ptr, const int64_t *pn_ptr, const int32_t *E,
@@ -739,14 +739,17 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
         FEM_TRY(mxc.alloc(ar, 1, "max colour"));
         FEM_CUDA(cudaMemsetAsync(mxc.ptr, 0, sizeof(int), s));
         const size_t smem = (size_t)2 * P.max_own * sizeof(unsigned long long) + (size_t)COLOR_CHUNK * npe * sizeof(int16_t);
-        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np_, (int64_t)num_sms() * 8));
+        // one warp per patch: the greedy pass is one thread's dependent chain of
+        // shared-memory updates, so the SM is kept busy by many patches at once
+        // (small chunks of the element table keep each block's shared memory small)
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np_, (int64_t)num_sms() * 32));
         if (npe == 8) {
             FEM_CUDA(cudaFuncSetAttribute(k_color<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_color<8><<<grid, 128, smem, s>>>(ckeys.ptr, cl.patch_elem_ptr.ptr, P.patch_node_ptr.ptr + p0, m->E,
+            k_color<8><<<grid, 32, smem, s>>>(ckeys.ptr, cl.patch_elem_ptr.ptr, P.patch_node_ptr.ptr + p0, m->E,
                                                P.node_patch.ptr, P.own_idx.ptr, np_, p0, color.ptr, mxc.ptr);
         } else {
             FEM_CUDA(cudaFuncSetAttribute(k_color<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_color<4><<<grid, 128, smem, s>>>(ckeys.ptr, cl.patch_elem_ptr.ptr, P.patch_node_ptr.ptr + p0, m->E,
+            k_color<4><<<grid, 32, smem, s>>>(ckeys.ptr, cl.patch_elem_ptr.ptr, P.patch_node_ptr.ptr + p0, m->E,
                                                P.node_patch.ptr, P.own_idx.ptr, np_, p0, color.ptr, mxc.ptr);
         }
         FEM_LAUNCHED("k_color");
