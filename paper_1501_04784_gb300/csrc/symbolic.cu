@@ -494,26 +494,50 @@ __global__ void k_celem_fill(const uint64_t *ckeys, int64_t nce, const int32_t *
         }
         const int64_t gp = ot.p0 + (int64_t)p;
         const int64_t nb = ot.patch_node_ptr[gp];
+        // Each element node x as a row: the positions of the element's lower
+        // partners (g_y < g_x) in row g_x by one scan of the row, whose loads are
+        // independent (a binary search per pair is a chain of dependent loads),
+        // and the row's owner data.
+        int rl[NPE], base[NPE], hvk[NPE];
+        bool own[NPE];
+        uint8_t pxy[NPE][NPE];
+#pragma unroll
+        for (int x = 0; x < NPE; ++x) {
+            const int64_t r0 = rowptr[g[x]];
+            rl[x] = (int)(rowptr[g[x] + 1] - r0);
+            own[x] = ot.node_patch[g[x]] == gp;
+            base[x] = 0;
+            hvk[x] = -1;
+            if (own[x]) {
+                const int32_t kr = ot.own_idx[g[x]];
+                base[x] = ot.own_acc[nb + kr];
+                if (ot.own_hv[nb + kr]) hvk[x] = kr;
+            }
+#pragma unroll
+            for (int y = 0; y < NPE; ++y) pxy[x][y] = 0;
+            for (int j = 0; j < rl[x]; ++j) {
+                const int32_t cj = col[r0 + j];
+#pragma unroll
+                for (int y = 0; y < NPE; ++y)
+                    if (g[y] == cj) pxy[x][y] = (uint8_t)j;
+            }
+        }
         int q = 0;
 #pragma unroll
         for (int a = 0; a < NPE; ++a)
 #pragma unroll
             for (int b = 0; b <= a; ++b, ++q) {
-                const int32_t r = max(g[a], g[b]), cv = min(g[a], g[b]);
-                int64_t lo = rowptr[r], hi = rowptr[r + 1];
-                const int64_t r0 = lo;
-                while (lo < hi) {
-                    int64_t mid = (lo + hi) >> 1;
-                    if (col[mid] < cv) lo = mid + 1; else hi = mid;
-                }
-                pos[i * pos_stride + q] = (uint8_t)(lo - r0);
+                // the pair's row is its node with the larger global id; the
+                // diagonal closes its lower row
+                const bool ra = g[a] > g[b];
+                const int ps = a == b ? rl[a] - 1 : (ra ? pxy[a][b] : pxy[b][a]);
+                pos[i * pos_stride + q] = (uint8_t)ps;
                 // a pair whose row the patch does not own goes to a scratch slot of
                 // the lane that will hold the element, never read
                 uint32_t t = (uint32_t)(ot.trash + ((i - ot.pe_ptr[p]) & 31));
-                if (ot.node_patch[r] == gp) {
-                    const int32_t kr = ot.own_idx[r];
-                    if (a == b && ot.own_hv[nb + kr]) t = AIDX_HV | (uint32_t)kr;
-                    else t = (uint32_t)(ot.own_acc[nb + kr] + (lo - r0));
+                if (ra ? own[a] : own[b]) {
+                    if (a == b && hvk[a] >= 0) t = AIDX_HV | (uint32_t)hvk[a];
+                    else t = (uint32_t)((ra ? base[a] : base[b]) + ps);
                 }
                 // word q/2 of element i, low half for even q
                 aidx[((int64_t)(q >> 1) * nce + i) * 2 + (q & 1)] = (uint16_t)t;
