@@ -538,11 +538,14 @@ static fem_status launch_patch_t(const PatchArgs &a, cudaStream_t s) {
     int dev = 0, max_optin = 0;
     FEM_CUDA(cudaGetDevice(&dev));
     FEM_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if (L.total > (size_t)max_optin) {
+    auto f = k_patch<NPE, AccT, S, CT, FUSED, MIXED>;
+    cudaFuncAttributes fa{};
+    FEM_CUDA(cudaFuncGetAttributes(&fa, f));
+    // the dynamic part shares the opt-in limit with the static mbarrier ring
+    if (L.total + fa.sharedSizeBytes > (size_t)max_optin) {
         set_error("a patch needs %zu bytes of shared memory (limit %d); lower patch_entries", L.total, max_optin);
         return FEM_ERR_UNSUPPORTED;
     }
-    auto f = k_patch<NPE, AccT, S, CT, FUSED, MIXED>;
     FEM_TRY(set_smem(f, L.total));
     const int threads = a.threads;
     int per_sm = 0;
@@ -607,11 +610,13 @@ static fem_status batched_config_t(const PlanMax &pm, int threads, int blocks_pe
     int dev = 0, max_optin = 0;
     FEM_CUDA(cudaGetDevice(&dev));
     FEM_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if (L.total > (size_t)max_optin) {
+    auto f = k_patch_batched<NPE, AccT, T, T, MIXED>;
+    cudaFuncAttributes fa{};
+    FEM_CUDA(cudaFuncGetAttributes(&fa, f));
+    if (L.total + fa.sharedSizeBytes > (size_t)max_optin) {
         set_error("a patch of the batch needs %zu bytes of shared memory (limit %d)", L.total, max_optin);
         return FEM_ERR_UNSUPPORTED;
     }
-    auto f = k_patch_batched<NPE, AccT, T, T, MIXED>;
     FEM_TRY(set_smem(f, L.total));
     int per_sm = 0;
     FEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, L.total));
