@@ -315,6 +315,15 @@ typedef struct {
 fem_status fem_autotune(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c, fem_dtype c_dtype,
                         void *vals, void *stream, fem_tuning *out);
 
+/*
+ * Apply a tuning chosen earlier (fem_autotune's patch_entries and block_threads,
+ * for example from a cache kept by the caller per GPU, element type, precision and
+ * operator): sets the two options and rebuilds the plan if the pattern exists
+ * (else fem_pattern plans with them).  0 restores a default.  Blocks.
+ * Errors: FEM_ERR_ARG, and those of fem_pattern.
+ */
+fem_status fem_set_tuning(fem_mesh m, int patch_entries, int block_threads, void *stream);
+
 /* Wait for the mesh's work on `stream` and report any asynchronous error:
  * FEM_ERR_CUDA for a CUDA error; FEM_ERR_DEGENERATE if a build since the last
  * fem_sync met an element matrix that is not finite (an element of zero volume,

@@ -48,7 +48,7 @@ class fem_tuning(ctypes.Structure):
 EXPORTS = ["fem_options_default", "fem_status_str", "fem_last_error", "fem_mesh_create", "fem_mesh_destroy",
            "fem_pattern", "fem_get_pattern", "fem_pattern_ptrs", "fem_integrate_local", "fem_assemble_csr",
            "fem_build_K", "fem_build_K_host", "fem_build_K_host_async", "fem_vjp", "fem_load_vector", "fem_build_K_batched", "fem_sync", "fem_mesh_info",
-           "fem_launch_count", "fem_pattern_noalloc", "fem_batched_config", "fem_autotune"]
+           "fem_launch_count", "fem_pattern_noalloc", "fem_batched_config", "fem_autotune", "fem_set_tuning"]
 
 _lib = None
 
@@ -116,6 +116,8 @@ def load(build_if_missing: bool = False):
     L.fem_batched_config.restype = S
     L.fem_autotune.argtypes = [P, INT, P, INT, P, INT, P, P, ctypes.POINTER(fem_tuning)]
     L.fem_autotune.restype = S
+    L.fem_set_tuning.argtypes = [P, INT, INT, P]
+    L.fem_set_tuning.restype = S
     _lib = L
     return L
 

@@ -678,6 +678,26 @@ fem_status fem_autotune(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype
     return FEM_OK;
 }
 
+// A tuning chosen before (by fem_autotune, possibly in another process): the plan
+// is rebuilt for it without timing anything.
+fem_status fem_set_tuning(fem_mesh m, int patch_entries, int block_threads, void *stream) {
+    if (!m || patch_entries < 0 || block_threads < 0 || block_threads > 1024) {
+        set_error("bad tuning arguments");
+        return FEM_ERR_ARG;
+    }
+    m->opt.patch_entries = patch_entries;
+    m->opt.block_threads = block_threads;
+    m->opt.blocks_per_sm = 0;
+    if (!m->has_pattern) return FEM_OK;  // fem_pattern will plan with these settings
+    cudaStream_t s = as_stream(stream);
+    fem_status st = build_plan(m, s);
+    if (st == FEM_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_status(e, "fem_set_tuning");
+    }
+    return st;
+}
+
 fem_status fem_sync(fem_mesh m, void *stream) {
     cudaError_t e = cudaStreamSynchronize(as_stream(stream));
     if (e != cudaSuccess) return cuda_status(e, "fem_sync");

@@ -195,15 +195,46 @@ class Mesh:
                                              _dev(out, "F", vd), _stream(stream)))
         return out
 
-    def autotune(self, X, c, prec="mixed", stream=None) -> dict:
-        """Pick the patch size and block size by timing fem_build_K (overwrites a scratch vals)."""
+    def autotune(self, X, c, prec="mixed", stream=None, cache: str | None = None) -> dict:
+        """Pick the patch size and block size by timing fem_build_K (overwrites a scratch vals).
+
+        With ``cache`` (a JSON file path), a tuning stored for the same GPU model,
+        element type, precision, operator and mesh size class (elements to the
+        nearest power of two) is applied without timing (``tried`` = 0); a new one
+        is timed and stored."""
         if self.nnz is None:
             self.pattern(stream)
+        key = None
+        if cache is not None:
+            import json
+            import math
+            import os
+            key = "|".join([torch.cuda.get_device_name(X.device), f"npe={self.npe}", prec,
+                            f"op={self.options.operator_kind}", f"log2n={round(math.log2(max(self.n_elems, 1)))}"])
+            table = json.load(open(cache)) if os.path.exists(cache) else {}
+            if key in table:
+                hit = table[key]
+                abi.check(abi.load().fem_set_tuning(self._h, int(hit["patch_entries"]), int(hit["block_threads"]),
+                                                    _stream(stream)))
+                return dict(patch_entries=hit["patch_entries"], block_threads=hit["block_threads"],
+                            ms=hit["ms"], tried=0)
         vals = torch.empty(max(self.nnz, 1), dtype=value_dtype(prec), device=X.device)
         t = abi.fem_tuning()
         abi.check(abi.load().fem_autotune(self._h, _prec(prec), _dev(X, "X"), _DT[X.dtype], _dev(c, "c"),
                                           _DT[c.dtype], _dev(vals, "vals"), _stream(stream), ctypes.byref(t)))
-        return dict(patch_entries=t.patch_entries, block_threads=t.block_threads, ms=t.ms, tried=t.tried)
+        out = dict(patch_entries=t.patch_entries, block_threads=t.block_threads, ms=t.ms, tried=t.tried)
+        if key is not None:
+            table = json.load(open(cache)) if os.path.exists(cache) else {}
+            table[key] = dict(patch_entries=out["patch_entries"], block_threads=out["block_threads"], ms=out["ms"])
+            tmp = f"{cache}.{os.getpid()}.tmp"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return out
+
+    def set_tuning(self, patch_entries: int, block_threads: int, stream=None):
+        """Apply a known tuning (rebuilds the plan if the pattern exists)."""
+        abi.check(abi.load().fem_set_tuning(self._h, int(patch_entries), int(block_threads), _stream(stream)))
 
     def sync(self, stream=None):
         abi.check(abi.load().fem_sync(self._h, _stream(stream)))

@@ -122,3 +122,20 @@ def test_autotune_keeps_values_in_tolerance(fem):
     vals = mesh.build_K(X, c, "mixed").cpu().numpy()
     ref = oracle_K(m, m.X.astype(np.float32), m.c.astype(np.float32))
     assert rel_err(vals, ref["vals"], ref["cs"]) <= TOL_MIXED
+
+
+def test_autotune_cache(fem, tmp_path):
+    """The tuner cache: the first call times the candidates and stores the choice
+    keyed by GPU, element type, precision, operator and size class; a second mesh
+    of the same kind applies it without timing and builds the same values."""
+    m = meshgen.config_mesh(0)
+    X, c = dev(m.X, torch.float32), dev(m.c, torch.float32)
+    cache = str(tmp_path / "tune.json")
+    a = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64))
+    ta = a.autotune(X, c, "mixed", cache=cache)
+    assert ta["tried"] >= 3
+    b = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64))
+    tb = b.autotune(X, c, "mixed", cache=cache)
+    assert tb["tried"] == 0 and (tb["patch_entries"], tb["block_threads"]) == (ta["patch_entries"], ta["block_threads"])
+    assert b.info()["n_patches"] == a.info()["n_patches"]
+    assert torch.equal(a.build_K(X, c, "mixed"), b.build_K(X, c, "mixed"))
