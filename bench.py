@@ -208,7 +208,57 @@ def cpu_baseline(m, target_s=12.0):
             break
         n = min(2 * n, m.n_elems)
     return {"value": n / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {n} of {m.n_elems} elements of the workload: element loop + stable sort/reduce to CSR, FP64, 1 thread"}
+            "sample": f"first {n} of {m.n_elems} elements of the workload: element loop + stable sort/reduce to CSR, FP64, 1 thread",
+            "nproc": os.cpu_count(), "cpu_model": cpu_model()}
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    import platform
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip() + f" ({platform.machine()})"
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
+def oracle_error(m, rowptr, col, builds, n_rows=2000, seed=12):
+    """Accuracy of the timed builds, from the same leg as the CPU baseline: the
+    oracle's exact rows of n_rows random nodes (all elements touching them), against
+    each build, as the largest |K_ij - K*_ij| / sum_e sqrt(k_aa k_bb) (the per-entry
+    Cauchy-Schwarz scale of the contributions).  builds = {name: (vals, X, c)},
+    X and c as that build read them."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(seed)
+    rows = np.unique(rng.choice(m.n_nodes, n_rows, replace=False))
+    touch = np.isin(m.E, rows).any(axis=1)
+    rp, cl = rowptr, col
+    out = {}
+    for name, (vals, X, c) in builds.items():
+        sub = oracle.build_K(m.npe, np.asarray(X, np.float64), m.E[touch], np.asarray(c, np.float64)[touch])
+        worst = 0.0
+        for r in rows:
+            a, b = sub["rowptr"][r], sub["rowptr"][r + 1]
+            g0, g1 = rp[r], rp[r + 1]
+            if not np.array_equal(cl[g0:g1], sub["col"][a:b]):
+                worst = float("inf")
+                break
+            err = np.abs(vals[g0:g1].astype(np.float64) - sub["vals"][a:b]) / np.maximum(sub["cs"][a:b], 1e-300)
+            worst = max(worst, float(err.max()))
+        out[name] = worst
+    out["rows_sampled"] = int(len(rows))
+    out["metric"] = "max |K - K_oracle| / sum_e sqrt(k_aa k_bb) over the sampled rows"
+    return out
 
 
 # --------------------------------------------------------------- our arm
@@ -386,6 +436,11 @@ def run_ours(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(m)
+            rowptr, col = mesh.get_pattern()
+            mesh.build_K(Xf, cf, "mixed", out=vals)  # vals held the mass matrix since
+            out["error"] = oracle_error(m, rowptr.cpu().numpy(), col.cpu().numpy(), {
+                "mixed": (vals.cpu().numpy(), m.X.astype(np.float32), m.c.astype(np.float32)),
+                "fp64": (vals64.cpu().numpy(), m.X, m.c)})
     mesh.close()
     if not args.no_workloads:
         extra = other_workloads(flush, stream)
