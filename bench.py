@@ -412,6 +412,10 @@ def run_ours(args):
             "algorithmic_flops_per_launch": BRICK_FLOPS * m.n_elems,
             "hbm": {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                     "peak_source": peak_kind, "algorithmic_bytes_per_launch": alg}}
+    if roof["traffic"]:
+        # DRAM bytes the kernel really moves (ncu) over the launch time measured here
+        roof["hbm"]["dram_gbs"] = round(roof["traffic"] / (ms_step / 1e3) / 1e9, 1)
+        roof["hbm"]["dram_frac"] = round(roof["hbm"]["dram_gbs"] / peak, 4)
 
     if rank == 0:
         out = {
