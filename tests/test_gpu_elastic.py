@@ -316,3 +316,24 @@ def test_elastic_batched(fem, kind, prec):
             else:
                 ref = oracle_el(m, m.X, meshgen.lame(m))
                 assert rel_err(g.cpu().numpy(), ref["vals"], ref["cs"]) <= TOL_FP64
+
+
+@pytest.mark.parametrize("fp64_dets", [0, 1])
+def test_elastic_sliver_tets(fem, fp64_dets):
+    """Slivers (a fourth node 1e-4 above a unit triangle, rotated and shifted): the
+    elasticity kernel takes the scalar operator's FP64-accurate determinant and face
+    vectors, so the mixed build still meets the tolerance against the oracle."""
+    rng = np.random.default_rng(7)
+    P = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0.3, 0.3, 1e-4]], float)
+    X, E = [], []
+    for t in range(48):
+        Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        X.append(P @ Q.T + rng.normal(size=3))
+        E.append([4 * t, 4 * t + 1, 4 * t + 2, 4 * t + 3])
+    m = meshgen.Mesh(X=np.vstack(X), E=np.asarray(E, np.int32), c=rng.lognormal(0, 0.5, 48), npe=4, shape=(48, 1, 1))
+    mesh = make(fem, m, fp64_dets=fp64_dets)
+    Xd, cd, X64, c64 = inputs(m, "mixed")
+    vals = mesh.build_K(Xd, cd, "mixed")
+    mesh.sync()
+    ref = oracle_el(m, X64, c64)
+    assert rel_err(vals.cpu().numpy(), ref["vals"], ref["cs"]) <= TOL_MIXED
