@@ -54,6 +54,8 @@ def declare(L):
     L.oracle_compress.restype = _i64
     L.oracle_vjp.argtypes = [_int, _i64, _p, _p, _p, _p, _p, _p]
     L.oracle_vjp.restype = None
+    L.oracle_vjp_op.argtypes = [_int, _int, _i64, _p, _p, _p, _p, _p, _p]
+    L.oracle_vjp_op.restype = None
     L.oracle_load.argtypes = [_int, _i64, _p, _p, _p, _p]
     L.oracle_load.restype = _i64
     return L
@@ -165,21 +167,22 @@ def build_K(npe: int, X, E, c, op: str = "stiffness"):
     return out
 
 
-def vjp(npe: int, X, E, c, S):
-    """Gradient of L = sum_(e,p) S[e,p] k_e[p] with respect to X [n_nodes, 3] and c [n_elems]."""
+def vjp(npe: int, X, E, c, S, op: str = "stiffness"):
+    """Gradient of L = sum_(e,p) S[e,p] k_e[p] with respect to X [n_nodes, 3] and c [n_elems]
+    (op: "stiffness" or "mass")."""
     X, E, c = _inputs(X, E, c)
     S = np.ascontiguousarray(S, dtype=np.float64).reshape(E.shape[0], npairs(npe))
     dX = np.zeros_like(X)
     dc = np.zeros(E.shape[0])
-    lib().oracle_vjp(npe, E.shape[0], _ptr(E), _ptr(X), _ptr(c), _ptr(S), _ptr(dX), _ptr(dc))
+    lib().oracle_vjp_op(OPS[op], npe, E.shape[0], _ptr(E), _ptr(X), _ptr(c), _ptr(S), _ptr(dX), _ptr(dc))
     return dX, dc
 
 
-def vjp_from_G(npe: int, X, E, c, G, slot):
+def vjp_from_G(npe: int, X, E, c, G, slot, op: str = "stiffness"):
     """Gradient of L = sum over stored entries G_ij K_ij (Section 3's lower storage,
     each packed pair counted once) given the CSR slot map from ``build_K``."""
     S = np.asarray(G)[np.asarray(slot)]
-    return vjp(npe, X, E, c, S)
+    return vjp(npe, X, E, c, S, op)
 
 
 def load_vector(npe: int, X, E, s):

@@ -521,22 +521,75 @@ int64_t oracle_load(int npe, int64_t n_elems, const int32_t *E, const double *X,
 }
 
 /*
+ * The mass matrix of the brick and the tetrahedron in complex arithmetic, the
+ * same steps as me_brick and me_tet, for the complex-step derivative below.  The
+ * sign of det J is read from its real part.
+ */
+static void me_brick_z(const double complex xe[24], double complex c, double complex me[64]) {
+    const double g = 1.0 / sqrt(3.0);
+    const double pts[2] = {-g, g};
+    for (int i = 0; i < 64; ++i) me[i] = 0;
+    for (int ir = 0; ir < 2; ++ir)
+        for (int is = 0; is < 2; ++is)
+            for (int it = 0; it < 2; ++it) {
+                const double r = pts[ir], s = pts[is], t = pts[it];
+                double N[8], dN[3][8];
+                for (int a = 0; a < 8; ++a) {
+                    const double ra = BRICK_NODES[a][0], sa = BRICK_NODES[a][1], ta = BRICK_NODES[a][2];
+                    N[a] = 0.125 * (1 + r * ra) * (1 + s * sa) * (1 + t * ta);
+                    dN[0][a] = 0.125 * ra * (1 + s * sa) * (1 + t * ta);
+                    dN[1][a] = 0.125 * sa * (1 + r * ra) * (1 + t * ta);
+                    dN[2][a] = 0.125 * ta * (1 + r * ra) * (1 + s * sa);
+                }
+                double complex J[3][3];
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) {
+                        double complex acc = 0;
+                        for (int a = 0; a < 8; ++a) acc += dN[i][a] * xe[3 * a + j];
+                        J[i][j] = acc;
+                    }
+                double complex det, inv[3][3];
+                inv3_z(J, &det, inv);
+                const double complex absdet = creal(det) < 0 ? -det : det;
+                for (int a = 0; a < 8; ++a)
+                    for (int b = 0; b < 8; ++b) me[8 * a + b] += c * absdet * N[a] * N[b];
+            }
+}
+
+static void me_tet_z(const double complex xe[12], double complex c, double complex me[16]) {
+    double complex J[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) J[i][j] = xe[3 * (i + 1) + j] - xe[j];
+    double complex det, inv[3][3];
+    inv3_z(J, &det, inv);
+    const double complex vol = (creal(det) < 0 ? -det : det) / 6.0;
+    const double qa = (5.0 + 3.0 * sqrt(5.0)) / 20.0, qb = (5.0 - sqrt(5.0)) / 20.0;
+    for (int i = 0; i < 16; ++i) me[i] = 0;
+    for (int q = 0; q < 4; ++q) {
+        double lam[4];
+        for (int a = 0; a < 4; ++a) lam[a] = a == q ? qa : qb;
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) me[4 * a + b] += c * (vol / 4.0) * lam[a] * lam[b];
+    }
+}
+
+/*
  * Gradient of L = sum_(e, p) S[e, p] * k_e[p] over the packed lower entries p of
  * every element (S is the upstream value G_ij of the CSR entry that (e, p) lands
- * in).  dc[e] = sum_p S[e, p] k_e[p] / c_e because k_e is linear in c_e.
- * dX[g] += d L / d x_g by the complex-step derivative Im L(x + i h e_j) / h of
- * the element routine (exact up to rounding for this analytic function).
- * dX must be zeroed by the caller.
+ * in), for operator op (0 stiffness, 1 mass).  dc[e] = sum_p S[e, p] k_e[p] / c_e
+ * because k_e is linear in c_e.  dX[g] += d L / d x_g by the complex-step
+ * derivative Im L(x + i h e_j) / h of the element routine (exact up to rounding
+ * for this analytic function).  dX must be zeroed by the caller.
  */
-void oracle_vjp(int npe, int64_t n_elems, const int32_t *E, const double *X, const double *c,
-                const double *S, double *dX, double *dc) {
+void oracle_vjp_op(int op, int npe, int64_t n_elems, const int32_t *E, const double *X, const double *c,
+                   const double *S, double *dX, double *dc) {
     const int np = npe * (npe + 1) / 2;
     double xe[24], ke[64];
     double complex xz[24], kz[64];
     for (int64_t e = 0; e < n_elems; ++e) {
         gather(npe, E, X, e, xe);
         const double one = 1.0;
-        element_dense(0, npe, xe, &one, ke);
+        element_dense(op, npe, xe, &one, ke);
         double l1 = 0.0;
         for (int a = 0; a < npe; ++a)
             for (int b = 0; b <= a; ++b) l1 += S[e * np + a * (a + 1) / 2 + b] * ke[npe * a + b];
@@ -545,7 +598,11 @@ void oracle_vjp(int npe, int64_t n_elems, const int32_t *E, const double *X, con
             const double h = 1e-30 * (fabs(xe[k]) > 1.0 ? fabs(xe[k]) : 1.0);
             for (int m = 0; m < 3 * npe; ++m) xz[m] = xe[m];
             xz[k] += h * I;
-            if (npe == 8) ke_brick_z(xz, c[e], kz); else ke_tet_z(xz, c[e], kz);
+            if (op == 1) {
+                if (npe == 8) me_brick_z(xz, c[e], kz); else me_tet_z(xz, c[e], kz);
+            } else {
+                if (npe == 8) ke_brick_z(xz, c[e], kz); else ke_tet_z(xz, c[e], kz);
+            }
             double dl = 0.0;
             for (int a = 0; a < npe; ++a)
                 for (int b = 0; b <= a; ++b)
@@ -553,4 +610,10 @@ void oracle_vjp(int npe, int64_t n_elems, const int32_t *E, const double *X, con
             dX[3 * (int64_t)E[e * npe + k / 3] + k % 3] += dl;
         }
     }
+}
+
+/* The stiffness operator's gradient (op 0 of oracle_vjp_op). */
+void oracle_vjp(int npe, int64_t n_elems, const int32_t *E, const double *X, const double *c,
+                const double *S, double *dX, double *dc) {
+    oracle_vjp_op(0, npe, n_elems, E, X, c, S, dX, dc);
 }

@@ -169,3 +169,30 @@ def test_mass_planted_mistakes_are_caught(tmp_path, name):
 
     res = run_pins(me)
     assert not all(res.values()), f"mutation {name} passed every pin: {res}"
+
+
+def test_mass_gradient_complex_step_vs_central_differences(oracle_lib):
+    """The oracle's gradient of L = sum G_ij M_ij (complex step of its mass routine)
+    against central differences of its real mass matrix, in X and c."""
+    for npe, gen in ((8, meshgen.hex_grid), (4, meshgen.kuhn_tets)):
+        m = gen(2, 2, 2, jitter=0.2, seed=8, permute_nodes=True)
+        M = oracle_lib.build_K(npe, m.X, m.E, m.c, op="mass")
+        G = np.random.default_rng(2).standard_normal(M["nnz"])
+        dX, dc = oracle_lib.vjp_from_G(npe, m.X, m.E, m.c, G, M["slot"], op="mass")
+
+        def L(X, c):
+            return float(G @ oracle_lib.build_K(npe, X, m.E, c, op="mass")["vals"])
+
+        h = 1e-6
+        fd = np.zeros_like(m.X)
+        for i in range(m.n_nodes):
+            for j in range(3):
+                Xp, Xm = m.X.copy(), m.X.copy()
+                Xp[i, j] += h
+                Xm[i, j] -= h
+                fd[i, j] = (L(Xp, m.c) - L(Xm, m.c)) / (2 * h)
+        assert np.abs(dX - fd).max() <= 1e-6 * np.abs(fd).max()
+        fdc = np.array([(L(m.X, m.c + h * (np.arange(m.n_elems) == e)) -
+                         L(m.X, m.c - h * (np.arange(m.n_elems) == e))) / (2 * h)
+                        for e in range(m.n_elems)])
+        assert np.abs(dc - fdc).max() <= 1e-6 * np.abs(fdc).max()
