@@ -108,7 +108,7 @@ typedef struct {
                                     quadrature, packing, pattern and assembly;
                                     2 = linear isotropic elasticity, three DOFs per node
                                     (Algorithm 1's Mapping with DOFxn = 3): see "Elasticity"
-                                    below.  fem_vjp is for the stiffness operator only */
+                                    below.  fem_vjp covers operators 0 and 1 */
     int host_direct;             /* fem_build_K_host / _async: 0 (default) = K's values are
                                     built in device staging and copied out in one transfer,
                                     unless the memory budget refuses the staging; 1 = always
@@ -258,7 +258,9 @@ fem_status fem_build_K_host_async(fem_mesh m, fem_prec p, const void *X_host, fe
  * (a, b) of an element counted once), write dX [n_nodes][3] = dL/dX and
  * dc [n_elems] = dL/dc, recomputing J and B (nothing is kept from the forward
  * pass).  FEM_FP64: G, X, c, dX, dc double.  FEM_MIXED: G float, X and c per
- * dtype, dX and dc float; arithmetic FP32.  Every output entry is written.
+ * dtype, dX and dc float; arithmetic FP32.  Every output entry is written.  For
+ * the stiffness matrix (operator_kind 0) and the mass matrix (1; K = M there);
+ * FEM_ERR_UNSUPPORTED for elasticity.
  */
 fem_status fem_vjp(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c,
                    fem_dtype c_dtype, const void *G, void *dX, void *dc, void *stream);

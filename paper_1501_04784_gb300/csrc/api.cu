@@ -534,8 +534,8 @@ fem_status fem_vjp(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, con
         set_error("G, dX and dc must be non-null aligned device pointers");
         return FEM_ERR_ARG;
     }
-    if (m->opt.operator_kind != 0) {
-        set_error("the backward pass covers the stiffness operator only");
+    if (is_elastic(m)) {
+        set_error("the backward pass covers the scalar operators (stiffness and mass)");
         return FEM_ERR_UNSUPPORTED;
     }
     return launch_vjp(m, p == FEM_MIXED, X, x_dtype, c, c_dtype, G, dX, dc, as_stream(stream));

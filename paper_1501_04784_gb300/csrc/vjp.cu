@@ -12,6 +12,11 @@
 // J = dN X_e, dL/dX_e = sum_q dN_q^T dL/dJ_q.  J, det J, A and B are recomputed
 // here from X; nothing is stored by the forward pass.
 //
+// The mass operator (M_ab = c sum_q |det J_q| N_a(q) N_b(q)) has
+// L_e = c sum_q |det J_q| phi_q with phi_q = N_q^T Ssym N_q, hence dL/dc_e =
+// sum_q |det J_q| phi_q and dL/dJ_q = c phi_q |det J_q| A^T (the tetrahedron:
+// phi = sum_ab Ssym_ab (1 + delta_ab) / 20 over the volume |det J| / 6).
+//
 // Accumulation is owner-computes as in the forward kernel: the block of a patch
 // visits its closure elements colour by colour and adds each element's node
 // gradients into shared-memory accumulators of its owned nodes, then writes
@@ -196,6 +201,104 @@ __device__ __forceinline__ void tet_vjp(const S (*xc)[3], T c, const T (&Sp)[10]
         for (int j = 0; j < 3; ++j) dx[a][j] = D[0][a] * G[0][j] + D[1][a] * G[1][j] + D[2][a] * G[2][j];
 }
 
+// Symmetric element upstream from the packed one (each packed pair counted once).
+template <int NPE, typename T>
+__device__ __forceinline__ void sym_upstream(const T (&Sp)[NPE * (NPE + 1) / 2], T (&Ss)[NPE][NPE]) {
+#pragma unroll
+    for (int a = 0; a < NPE; ++a)
+#pragma unroll
+        for (int b = 0; b <= a; ++b) {
+            const T v = Sp[a * (a + 1) / 2 + b];
+            Ss[a][b] = a == b ? v : T(0.5) * v;
+            Ss[b][a] = Ss[a][b];
+        }
+}
+
+// Mass operator, brick: the same 2x2x2 rule; N_a(q) are products of 1D hats.
+template <typename T, typename S>
+__device__ __forceinline__ void brick_mass_vjp(const S (*xc)[3], T c, const T (&Sp)[36], T (&dx)[8][3], T &dc) {
+    Vec3<T> e[3][2][2];
+    brick_edges<T, S>(xc, e);
+    Vec3<T> row[3][2][2];
+    brick_jrows(e, row);
+    T Ss[8][8];
+    sym_upstream<8, T>(Sp, Ss);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) dx[a][0] = dx[a][1] = dx[a][2] = T(0);
+    dc = T(0);
+    const T P = T(FEM_GP), Q = T(FEM_GQ);
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+        const int q1 = q >> 2, q2 = (q >> 1) & 1, q3 = q & 1;
+        Vec3<T> R = row[0][q2][q3], Sv = row[1][q1][q3], U = row[2][q1][q2];
+        R = {T(0.5) * R.x, T(0.5) * R.y, T(0.5) * R.z};
+        Sv = {T(0.5) * Sv.x, T(0.5) * Sv.y, T(0.5) * Sv.z};
+        U = {T(0.5) * U.x, T(0.5) * U.y, T(0.5) * U.z};
+        const Vec3<T> C0 = cross3(Sv, U), C1 = cross3(U, R), C2 = cross3(R, Sv);
+        const T d = dot3(R, C0);
+        const T ad = d < T(0) ? -d : d;
+        const T id = T(1) / d;
+        // A = J^{-1}: A[i][j] = C_j[i] / d
+        const T A[3][3] = {{C0.x * id, C1.x * id, C2.x * id}, {C0.y * id, C1.y * id, C2.y * id},
+                           {C0.z * id, C1.z * id, C2.z * id}};
+        T N[8], D[3][8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const int a1 = hb1(a), a2 = hb2(a), a3 = hb3(a);
+            const T f1 = a1 == q1 ? P : Q, f2 = a2 == q2 ? P : Q, f3 = a3 == q3 ? P : Q;
+            N[a] = f1 * f2 * f3;
+            D[0][a] = T(0.5 * hsig(a1)) * f2 * f3;
+            D[1][a] = T(0.5 * hsig(a2)) * f1 * f3;
+            D[2][a] = T(0.5 * hsig(a3)) * f1 * f2;
+        }
+        T phi = T(0);
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            T s = T(0);
+#pragma unroll
+            for (int b = 0; b < 8; ++b) s += Ss[a][b] * N[b];
+            phi += N[a] * s;
+        }
+        dc += ad * phi;
+        // dL/dJ = c phi |det J| A^T
+        const T k = c * phi * ad;
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                dx[a][j] += k * (D[0][a] * A[j][0] + D[1][a] * A[j][1] + D[2][a] * A[j][2]);
+    }
+}
+
+// Mass operator, tetrahedron: M = c |det J| / 120 (1 + delta_ab).
+template <typename T, typename S>
+__device__ __forceinline__ void tet_mass_vjp(const S (*xc)[3], T c, const T (&Sp)[10], T (&dx)[4][3], T &dc) {
+    TetGeom<T> tg;
+    tet_geom<T, S>(xc, tg);
+    const Vec3<T> R0 = tg.R0, R1 = tg.R1, R2 = tg.R2;
+    const Vec3<T> C0 = cross3(R1, R2), C1 = cross3(R2, R0), C2 = cross3(R0, R1);
+    const T d = dot3(R0, C0);
+    const T ad = d < T(0) ? -d : d;
+    const T id = T(1) / d;
+    const T A[3][3] = {{C0.x * id, C1.x * id, C2.x * id}, {C0.y * id, C1.y * id, C2.y * id},
+                       {C0.z * id, C1.z * id, C2.z * id}};
+    T Ss[4][4];
+    sym_upstream<4, T>(Sp, Ss);
+    T psi = T(0);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) psi += Ss[a][b] * (a == b ? T(2) : T(1));
+    psi *= T(1.0 / 120.0);
+    dc = ad * psi;
+    const T D[3][4] = {{T(-1), T(1), T(0), T(0)}, {T(-1), T(0), T(1), T(0)}, {T(-1), T(0), T(0), T(1)}};
+    const T k = c * psi * ad;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) dx[a][j] = k * (D[0][a] * A[j][0] + D[1][a] * A[j][1] + D[2][a] * A[j][2]);
+}
+
 struct VjpSmem {
     size_t xs, cown, gid, dxs, total;
 };
@@ -204,7 +307,7 @@ template <int NPE, typename T, typename S, typename CT>
 __global__ void __launch_bounds__(256) k_vjp(PlanView pv, const int64_t *__restrict__ rowptr,
                                              const S *__restrict__ X, const CT *__restrict__ c,
                                              const T *__restrict__ G, T *__restrict__ dX, T *__restrict__ dcout,
-                                             VjpSmem L) {
+                                             VjpSmem L, bool mass) {
     constexpr int NP = NPE * (NPE + 1) / 2;
     extern __shared__ __align__(16) unsigned char vjp_smem[];
     S(*xs)[3] = reinterpret_cast<S(*)[3]>(vjp_smem + L.xs);
@@ -259,8 +362,13 @@ __global__ void __launch_bounds__(256) k_vjp(PlanView pv, const int64_t *__restr
                         Sp[q] = G[rowptr[r] + pp[q]];
                     }
                 T dcv;
-                if constexpr (NPE == 8) brick_vjp<T, S>(xc, (T)c[e], Sp, dx, dcv);
-                else tet_vjp<T, S>(xc, (T)c[e], Sp, dx, dcv);
+                if (mass) {
+                    if constexpr (NPE == 8) brick_mass_vjp<T, S>(xc, (T)c[e], Sp, dx, dcv);
+                    else tet_mass_vjp<T, S>(xc, (T)c[e], Sp, dx, dcv);
+                } else {
+                    if constexpr (NPE == 8) brick_vjp<T, S>(xc, (T)c[e], Sp, dx, dcv);
+                    else tet_vjp<T, S>(xc, (T)c[e], Sp, dx, dcv);
+                }
                 if (cown[ln[0]] >= 0) dcout[e] = dcv;
             }
             const int last = min(base + nthr, nel) - 1;
@@ -319,7 +427,7 @@ static fem_status launch_vjp_t(fem_mesh m, const Closure &cl, const void *X, con
     if (np <= 0) return FEM_OK;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np, (int64_t)num_sms() * per_sm));
     f<<<grid, 256, L.total, s>>>(P.view(cl), m->rowptr.ptr, (const S *)X, (const CT *)c, (const T *)G, (T *)dX,
-                                 (T *)dc, L);
+                                 (T *)dc, L, m->opt.operator_kind == 1);
     FEM_LAUNCHED("k_vjp");
     return FEM_OK;
 }

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import meshgen
+import oracle
 from helpers import TOL_FP64, TOL_MIXED, oracle_K, oracle_ke, oracle_rows, rel_err, rounded_inputs
 
 pytestmark = pytest.mark.gpu
@@ -112,12 +113,23 @@ def test_mass_full_size_sampled(fem):
     assert nnz == 14150601 and worst <= TOL_MIXED, worst
 
 
-def test_mass_backward_is_refused(fem):
-    from paper_1501_04784_gb300 import abi
-    m = MESHES["hex_7x5x3"]()
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["hex_7x5x3", "tet10_perm"])
+def test_mass_backward(fem, name, prec):
+    """The backward pass of the mass operator: dL/dX and dL/dc of L = sum G_ij M_ij
+    against the oracle's complex-step gradient."""
+    m = MESHES[name]()
     mesh = mass_mesh(fem, m)
-    Xd, cd, X, c = inputs(m, "fp64")
-    nnz = mesh.pattern()
-    G = torch.ones(nnz, dtype=torch.float64, device="cuda")
-    with pytest.raises(abi.FemError, match="FEM_ERR_UNSUPPORTED"):
-        mesh.vjp(Xd, cd, G, "fp64")
+    Xd, cd, X, c = inputs(m, prec)
+    ref = oracle.build_K(m.npe, X, m.E, c, op="mass")
+    G = np.random.default_rng(9).standard_normal(ref["nnz"])
+    if prec == "mixed":
+        G = G.astype(np.float32)
+    dX_ref, dc_ref = oracle.vjp_from_G(m.npe, X, m.E, c, G.astype(np.float64), ref["slot"], op="mass")
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    mesh.pattern()
+    dX, dc = mesh.vjp(Xd, cd, dev(G, dt), prec)
+    dX, dc = dX.cpu().numpy().astype(np.float64), dc.cpu().numpy().astype(np.float64)
+    tol = 1e-11 if prec == "fp64" else 2e-4
+    assert np.abs(dX - dX_ref).max() <= tol * np.abs(dX_ref).max()
+    assert np.abs(dc - dc_ref).max() <= tol * np.abs(dc_ref).max()
