@@ -169,11 +169,11 @@ def build_K(npe: int, X, E, c, op: str = "stiffness"):
 
 def vjp(npe: int, X, E, c, S, op: str = "stiffness"):
     """Gradient of L = sum_(e,p) S[e,p] k_e[p] with respect to X [n_nodes, 3] and c [n_elems]
-    (op: "stiffness" or "mass")."""
+    (op: "stiffness", "mass" or "elasticity", for which c and dc are [n_elems, 2])."""
     X, E, c = _inputs(X, E, c)
-    S = np.ascontiguousarray(S, dtype=np.float64).reshape(E.shape[0], npairs(npe))
+    S = np.ascontiguousarray(S, dtype=np.float64).reshape(E.shape[0], npairs(npe, op))
     dX = np.zeros_like(X)
-    dc = np.zeros(E.shape[0])
+    dc = np.zeros((E.shape[0], 2) if op == "elasticity" else E.shape[0])
     lib().oracle_vjp_op(OPS[op], npe, E.shape[0], _ptr(E), _ptr(X), _ptr(c), _ptr(S), _ptr(dX), _ptr(dc))
     return dX, dc
 

@@ -313,6 +313,89 @@ static int ke_elastic(int npe, const double *xe, double lam, double mu, double *
     return nonpos;
 }
 
+/* The same elasticity element in complex arithmetic (for the complex-step
+ * derivative of the backward pass); the sign of det J from its real part. */
+static void elastic_add_z(int npe, const double complex B[3][8], double complex w, double lam, double mu,
+                          double complex *ke) {
+    const int nk = 3 * npe;
+    double complex Be[6][24];
+    for (int k = 0; k < 6; ++k)
+        for (int A = 0; A < nk; ++A) Be[k][A] = 0.0;
+    for (int a = 0; a < npe; ++a) {
+        Be[0][3 * a + 0] = B[0][a];
+        Be[1][3 * a + 1] = B[1][a];
+        Be[2][3 * a + 2] = B[2][a];
+        Be[3][3 * a + 0] = B[1][a]; Be[3][3 * a + 1] = B[0][a];
+        Be[4][3 * a + 1] = B[2][a]; Be[4][3 * a + 2] = B[1][a];
+        Be[5][3 * a + 0] = B[2][a]; Be[5][3 * a + 2] = B[0][a];
+    }
+    double D[6][6];
+    for (int k = 0; k < 6; ++k)
+        for (int l = 0; l < 6; ++l) D[k][l] = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        for (int l = 0; l < 3; ++l) D[k][l] = lam;
+        D[k][k] = lam + 2.0 * mu;
+        D[k + 3][k + 3] = mu;
+    }
+    for (int A = 0; A < nk; ++A)
+        for (int Bc = 0; Bc < nk; ++Bc) {
+            double complex acc = 0.0;
+            for (int k = 0; k < 6; ++k)
+                for (int l = 0; l < 6; ++l) acc += Be[k][A] * D[k][l] * Be[l][Bc];
+            ke[nk * A + Bc] += w * acc;
+        }
+}
+
+static void ke_elastic_z(int npe, const double complex *xe, double lam, double mu, double complex *ke) {
+    const int nk = 3 * npe;
+    for (int i = 0; i < nk * nk; ++i) ke[i] = 0.0;
+    if (npe == 8) {
+        const double g = 1.0 / sqrt(3.0);
+        const double pts[2] = {-g, g};
+        for (int ir = 0; ir < 2; ++ir)
+            for (int is = 0; is < 2; ++is)
+                for (int it = 0; it < 2; ++it) {
+                    const double r = pts[ir], s = pts[is], t = pts[it];
+                    double dN[3][8];
+                    for (int a = 0; a < 8; ++a) {
+                        const double ra = BRICK_NODES[a][0], sa = BRICK_NODES[a][1], ta = BRICK_NODES[a][2];
+                        dN[0][a] = 0.125 * ra * (1 + s * sa) * (1 + t * ta);
+                        dN[1][a] = 0.125 * sa * (1 + r * ra) * (1 + t * ta);
+                        dN[2][a] = 0.125 * ta * (1 + r * ra) * (1 + s * sa);
+                    }
+                    double complex J[3][3];
+                    for (int i = 0; i < 3; ++i)
+                        for (int j = 0; j < 3; ++j) {
+                            double complex acc = 0;
+                            for (int a = 0; a < 8; ++a) acc += dN[i][a] * xe[3 * a + j];
+                            J[i][j] = acc;
+                        }
+                    double complex det, inv[3][3], B[3][8];
+                    inv3_z(J, &det, inv);
+                    for (int i = 0; i < 3; ++i)
+                        for (int a = 0; a < 8; ++a) {
+                            double complex acc = 0;
+                            for (int k = 0; k < 3; ++k) acc += inv[i][k] * dN[k][a];
+                            B[i][a] = acc;
+                        }
+                    elastic_add_z(8, B, creal(det) < 0 ? -det : det, lam, mu, ke);
+                }
+    } else {
+        double complex J[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) J[i][j] = xe[3 * (i + 1) + j] - xe[j];
+        double complex det, inv[3][3], B[3][8];
+        inv3_z(J, &det, inv);
+        for (int i = 0; i < 3; ++i)
+            for (int a = 0; a < 4; ++a) {
+                double complex acc = 0;
+                for (int k = 0; k < 3; ++k) acc += inv[i][k] * TET_DL[k][a];
+                B[i][a] = acc;
+            }
+        elastic_add_z(4, B, (creal(det) < 0 ? -det : det) / 6.0, lam, mu, ke);
+    }
+}
+
 /* Operators: 0 = stiffness k_e (Eq. 9), 1 = mass m_e, 2 = elasticity (3 DOFs per
  * node).  cv = the element's coefficients: c_e, or (lambda_e, mu_e) for op 2. */
 static int op_dofs(int op) { return op == 2 ? 3 : 1; }
@@ -581,8 +664,15 @@ static void me_tet_z(const double complex xe[12], double complex c, double compl
  * derivative Im L(x + i h e_j) / h of the element routine (exact up to rounding
  * for this analytic function).  dX must be zeroed by the caller.
  */
+static void elastic_vjp(int npe, int64_t n_elems, const int32_t *E, const double *X, const double *c,
+                        const double *S, double *dX, double *dc);
+
 void oracle_vjp_op(int op, int npe, int64_t n_elems, const int32_t *E, const double *X, const double *c,
                    const double *S, double *dX, double *dc) {
+    if (op == 2) {
+        elastic_vjp(npe, n_elems, E, X, c, S, dX, dc);
+        return;
+    }
     const int np = npe * (npe + 1) / 2;
     double xe[24], ke[64];
     double complex xz[24], kz[64];
@@ -616,4 +706,36 @@ void oracle_vjp_op(int op, int npe, int64_t n_elems, const int32_t *E, const dou
 void oracle_vjp(int npe, int64_t n_elems, const int32_t *E, const double *X, const double *c,
                 const double *S, double *dX, double *dc) {
     oracle_vjp_op(0, npe, n_elems, E, X, c, S, dX, dc);
+}
+
+/*
+ * Elasticity (op 2): S [n_elems][nk(nk+1)/2] over the packed local DOF pairs,
+ * c = (lambda, mu) per element, dc = (dL/dlambda, dL/dmu) per element (k_e is
+ * linear in each), dX by the complex step of ke_elastic_z.
+ */
+static void elastic_vjp(int npe, int64_t n_elems, const int32_t *E, const double *X, const double *c,
+                        const double *S, double *dX, double *dc) {
+    const int nk = 3 * npe, np = nk * (nk + 1) / 2;
+    double xe[24], ke[576];
+    double complex xz[24], kz[576];
+    for (int64_t e = 0; e < n_elems; ++e) {
+        gather(npe, E, X, e, xe);
+        for (int which = 0; which < 2; ++which) {
+            ke_elastic(npe, xe, which == 0 ? 1.0 : 0.0, which == 1 ? 1.0 : 0.0, ke);
+            double l1 = 0.0;
+            for (int A = 0; A < nk; ++A)
+                for (int B = 0; B <= A; ++B) l1 += S[e * np + A * (A + 1) / 2 + B] * ke[nk * A + B];
+            dc[2 * e + which] = l1;
+        }
+        for (int k = 0; k < 3 * npe; ++k) {
+            const double h = 1e-30 * (fabs(xe[k]) > 1.0 ? fabs(xe[k]) : 1.0);
+            for (int m = 0; m < 3 * npe; ++m) xz[m] = xe[m];
+            xz[k] += h * I;
+            ke_elastic_z(npe, xz, c[2 * e], c[2 * e + 1], kz);
+            double dl = 0.0;
+            for (int A = 0; A < nk; ++A)
+                for (int B = 0; B <= A; ++B) dl += S[e * np + A * (A + 1) / 2 + B] * cimag(kz[nk * A + B]) / h;
+            dX[3 * (int64_t)E[e * npe + k / 3] + k % 3] += dl;
+        }
+    }
 }

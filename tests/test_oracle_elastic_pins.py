@@ -314,7 +314,7 @@ def test_elastic_planted_mistakes_are_caught(tmp_path, oracle_lib, monkeypatch, 
     pytest.importorskip("scipy")
     src = open(os.path.join(os.path.dirname(oracle_lib.__file__), "oracle.c")).read()
     old, new = MUTATIONS[name]
-    assert src.count(old) == 1, name
+    assert src.count(old) >= 1, name  # the complex copy of the routine repeats some lines
     path = tmp_path / "mut.c"
     path.write_text(src.replace(old, new))
     so = tmp_path / "libmut.so"
@@ -323,3 +323,36 @@ def test_elastic_planted_mistakes_are_caught(tmp_path, oracle_lib, monkeypatch, 
     monkeypatch.setattr(oracle_lib, "_lib", oracle_lib.declare(ctypes.CDLL(str(so))))
     res = run_pins(elastic_of(oracle_lib), scalar_of(oracle_lib), builder_of(oracle_lib))
     assert not all(res.values()), f"mutation {name} passed every pin: {res}"
+
+
+def test_elastic_gradient_complex_step_vs_central_differences(oracle_lib):
+    """The oracle's gradient of L = sum G_ij K_ij for elasticity (complex step of its
+    complex element routine) against central differences of its real matrix, in X,
+    lambda and mu."""
+    for npe, gen in ((8, meshgen.hex_grid), (4, meshgen.kuhn_tets)):
+        m = gen(2, 1, 1, jitter=0.2, seed=8, permute_nodes=True)
+        c = meshgen.lame(m)
+        K = oracle_lib.build_K(npe, m.X, m.E, c, op="elasticity")
+        G = np.random.default_rng(3).standard_normal(K["nnz"])
+        dX, dc = oracle_lib.vjp_from_G(npe, m.X, m.E, c, G, K["slot"], op="elasticity")
+
+        def L(X, cc):
+            return float(G @ oracle_lib.build_K(npe, X, m.E, cc, op="elasticity")["vals"])
+
+        h = 1e-6
+        fd = np.zeros_like(m.X)
+        for i in range(m.n_nodes):
+            for j in range(3):
+                Xp, Xm = m.X.copy(), m.X.copy()
+                Xp[i, j] += h
+                Xm[i, j] -= h
+                fd[i, j] = (L(Xp, c) - L(Xm, c)) / (2 * h)
+        assert np.abs(dX - fd).max() <= 1e-6 * np.abs(fd).max()
+        fdc = np.zeros_like(c)
+        for e in range(m.n_elems):
+            for k in range(2):
+                cp, cm = c.copy(), c.copy()
+                cp[e, k] += h
+                cm[e, k] -= h
+                fdc[e, k] = (L(m.X, cp) - L(m.X, cm)) / (2 * h)
+        assert np.abs(dc - fdc).max() <= 1e-6 * np.abs(fdc).max()
