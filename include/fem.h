@@ -108,7 +108,7 @@ typedef struct {
                                     quadrature, packing, pattern and assembly;
                                     2 = linear isotropic elasticity, three DOFs per node
                                     (Algorithm 1's Mapping with DOFxn = 3): see "Elasticity"
-                                    below.  fem_vjp covers operators 0 and 1 */
+                                    below.  fem_vjp covers all three */
     int host_direct;             /* fem_build_K_host / _async: 0 (default) = K's values are
                                     built in device staging and copied out in one transfer,
                                     unless the memory budget refuses the staging; 1 = always
@@ -259,8 +259,10 @@ fem_status fem_build_K_host_async(fem_mesh m, fem_prec p, const void *X_host, fe
  * dc [n_elems] = dL/dc, recomputing J and B (nothing is kept from the forward
  * pass).  FEM_FP64: G, X, c, dX, dc double.  FEM_MIXED: G float, X and c per
  * dtype, dX and dc float; arithmetic FP32.  Every output entry is written.  For
- * the stiffness matrix (operator_kind 0) and the mass matrix (1; K = M there);
- * FEM_ERR_UNSUPPORTED for elasticity.
+ * the stiffness matrix (operator_kind 0) and the mass matrix (1; K = M there).
+ * Elasticity (2): G has the DOF pattern (fem_pattern's), each stored DOF entry
+ * counted once, and dc is [n_elems][2] = (dL/dlambda_e, dL/dmu_e); K is linear
+ * in (lambda, mu), so these are the two halves of the element's L.
  */
 fem_status fem_vjp(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c,
                    fem_dtype c_dtype, const void *G, void *dX, void *dc, void *stream);

@@ -13,6 +13,8 @@ fem_status launch_load(fem_mesh m, bool mixed, const void *X, fem_dtype xd, cons
                        float thr, bool fp64_det, cudaStream_t s);
 fem_status launch_vjp(fem_mesh m, bool mixed, const void *X, fem_dtype xd, const void *c, fem_dtype cd,
                       const void *G, void *dX, void *dc, cudaStream_t s);
+fem_status launch_elastic_vjp(fem_mesh m, bool mixed, const void *X, fem_dtype xd, const void *c, fem_dtype cd,
+                              const void *G, void *dX, void *dc, cudaStream_t s);
 fem_status launch_batched(const fem_mesh *ms, int n, bool mixed, const void *const *X, fem_dtype xd,
                           const void *const *c, fem_dtype cd, void *const *vals, cudaStream_t s);
 fem_status batched_query(const fem_mesh *ms, int n, bool mixed, int *threads, int *blocks_per_sm, int *grid);
@@ -534,10 +536,8 @@ fem_status fem_vjp(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, con
         set_error("G, dX and dc must be non-null aligned device pointers");
         return FEM_ERR_ARG;
     }
-    if (is_elastic(m)) {
-        set_error("the backward pass covers the scalar operators (stiffness and mass)");
-        return FEM_ERR_UNSUPPORTED;
-    }
+    if (is_elastic(m))
+        return launch_elastic_vjp(m, p == FEM_MIXED, X, x_dtype, c, c_dtype, G, dX, dc, as_stream(stream));
     return launch_vjp(m, p == FEM_MIXED, X, x_dtype, c, c_dtype, G, dX, dc, as_stream(stream));
 }
 

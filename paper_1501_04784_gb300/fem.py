@@ -174,10 +174,12 @@ class Mesh:
         return out[: self.nnz]
 
     def vjp(self, X, c, G, prec="fp64", stream=None):
+        """dL/dX [n_nodes, 3] and dL/dc of L = sum over stored entries G_ij K_ij:
+        dc is [n_elems], or [n_elems, 2] (dL/dlambda, dL/dmu) for elasticity."""
         p = _prec(prec)
         vd = value_dtype(prec)
         dX = torch.empty(self.n_nodes, 3, dtype=vd, device=X.device)
-        dc = torch.empty(self.n_elems, dtype=vd, device=X.device)
+        dc = torch.empty((self.n_elems, 2) if self.dofs == 3 else (self.n_elems,), dtype=vd, device=X.device)
         abi.check(abi.load().fem_vjp(self._h, p, _dev(X, "X"), _DT[X.dtype], _dev(c, "c"), _DT[c.dtype],
                                      _dev(G, "G", vd), _dev(dX, "dX"), _dev(dc, "dc"), _stream(stream)))
         return dX, dc

@@ -216,16 +216,53 @@ def test_elastic_zero_volume_element_is_reported(fem, prec):
     bad.sync()
 
 
-def test_elastic_unsupported_entry_points(fem):
-    """The backward pass covers the scalar stiffness operator only."""
-    from paper_1501_04784_gb300 import abi
-    m = MESHES["hex_1x1x1"]()
-    mesh = make(fem, m)
+@pytest.mark.parametrize("cap", list(PATCH_CAPS))
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", list(MESHES))
+def test_elastic_backward(fem, name, prec, cap):
+    """The backward pass of the elasticity operator: dL/dX and (dL/dlambda, dL/dmu)
+    of L = sum over stored DOF entries G_ij K_ij against the oracle's complex-step
+    gradient; the tiny patch capacity makes many patches and ragged batches."""
+    m = MESHES[name]()
+    mesh = make(fem, m, patch_entries=PATCH_CAPS[cap])
+    Xd, cd, X, c = inputs(m, prec)
+    ref = oracle_el(m, X, c)
+    G = np.random.default_rng(11).standard_normal(ref["nnz"])
+    if prec == "mixed":
+        G = G.astype(np.float32)
+    dX_ref, dc_ref = oracle.vjp_from_G(m.npe, X, m.E, c, G.astype(np.float64), ref["slot"], op="elasticity")
+    dt = torch.float64 if prec == "fp64" else torch.float32
     mesh.pattern()
-    Xd, cd, _, _ = inputs(m, "fp64")
-    with pytest.raises(abi.FemError, match="FEM_ERR_UNSUPPORTED"):
-        mesh.vjp(Xd, cd, torch.zeros(mesh.nnz, dtype=torch.float64, device="cuda"), "fp64")
-    assert mesh.info()["nnz"] == mesh.nnz == 300
+    assert mesh.nnz == ref["nnz"]
+    dX, dc = mesh.vjp(Xd, cd, dev(G, dt), prec)
+    assert dc.shape == (m.n_elems, 2)
+    dX, dc = dX.cpu().numpy().astype(np.float64), dc.cpu().numpy().astype(np.float64)
+    tol = 1e-11 if prec == "fp64" else 2e-4
+    assert np.abs(dX - dX_ref).max() <= tol * np.abs(dX_ref).max()
+    assert np.abs(dc - dc_ref).max() <= tol * np.abs(dc_ref).max()
+    # bitwise reproducible: owner-computes accumulation in a fixed colour order
+    dX2, dc2 = mesh.vjp(Xd, cd, dev(G, dt), prec)
+    assert np.array_equal(dX2.cpu().numpy().astype(np.float64), dX)
+    assert np.array_equal(dc2.cpu().numpy().astype(np.float64), dc)
+
+
+def test_elastic_autograd(fem):
+    """torch.autograd through build_K: the gradient of a scalar function of K's
+    values reaches X and the Lame parameters [n_elems, 2]."""
+    from paper_1501_04784_gb300 import autograd
+    m = MESHES["hex_6x5x4_perm"]()
+    mesh = make(fem, m)
+    Xd, cd, X, c = inputs(m, "fp64")
+    Xd.requires_grad_(True)
+    cd.requires_grad_(True)
+    vals = autograd.build_K(mesh, Xd, cd, "fp64")
+    G = np.random.default_rng(12).standard_normal(mesh.nnz)
+    (vals * dev(G, torch.float64)).sum().backward()
+    ref = oracle_el(m, X, c)
+    dX_ref, dc_ref = oracle.vjp_from_G(m.npe, X, m.E, c, G, ref["slot"], op="elasticity")
+    assert Xd.grad.shape == (m.n_nodes, 3) and cd.grad.shape == (m.n_elems, 2)
+    assert np.abs(Xd.grad.cpu().numpy() - dX_ref).max() <= 1e-11 * np.abs(dX_ref).max()
+    assert np.abs(cd.grad.cpu().numpy() - dc_ref).max() <= 1e-11 * np.abs(dc_ref).max()
 
 
 @pytest.mark.parametrize("prec,opts", [("mixed", dict(patch_entries=8192)), ("fp64", {}),
