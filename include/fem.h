@@ -115,7 +115,13 @@ typedef struct {
                                     write them straight into vals_host (page-locked, mapped
                                     through unified addressing), for K larger than device
                                     memory or the budget */
-    int reserved[3];
+    int vjp_fused;               /* fem_vjp: 0 (default) = each element's node gradients are
+                                    computed once into library memory (n_elems * npe * 3
+                                    values), then gathered into the owned nodes of every
+                                    patch; 1 = recomputed in every patch whose closure holds
+                                    the element (no library memory; also used when the
+                                    budget refuses it or the plan is built per patch group) */
+    int reserved[2];
 } fem_options;
 
 /*

@@ -26,7 +26,8 @@ class fem_options(ctypes.Structure):
                 ("locality_order", ctypes.c_int), ("fp64_sums", ctypes.c_int),
                 ("fp64_fused", ctypes.c_int), ("fp64_dets", ctypes.c_int),
                 ("wait_spins", ctypes.c_int), ("debug_stall", ctypes.c_int),
-                ("operator_kind", ctypes.c_int), ("host_direct", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("operator_kind", ctypes.c_int), ("host_direct", ctypes.c_int), ("vjp_fused", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class fem_info(ctypes.Structure):

@@ -254,8 +254,59 @@ __device__ __forceinline__ void load_upstream(const T *__restrict__ G, const int
 }
 
 struct ElVjpSmem {
-    size_t xs, cown, gid, dxs, total;
+    size_t xs, cown, gid, dxs, total;  // dxs: owned-node accumulators (fused) or the
+                                       // compacted element list (staged)
 };
+
+// One element of a closure on its NPE lanes (all lanes of the warp call it: the
+// brick shuffles): lane a gets dx_a, and dlam, dmu summed over the element.
+template <int NPE, typename T, typename S, typename CT>
+__device__ __forceinline__ void elastic_element_vjp(const PlanView &pv, const int64_t *__restrict__ rowptr,
+                                                    const CT *__restrict__ c, const T *__restrict__ G,
+                                                    const S (*xs)[3], const int32_t *gid, int pos_stride,
+                                                    bool act, int64_t ci, int a, uint16_t (&ln)[NPE], int64_t &e,
+                                                    T (&dx)[3], T &dlam, T &dmu) {
+    S xc[NPE][3];
+    T lam = T(0), mu = T(0);
+    T W[elastic_nblk<NPE>()][9];
+    e = 0;
+    if (act) {
+        e = pv.celem_id[ci];
+#pragma unroll
+        for (int k = 0; k < NPE; ++k) ln[k] = pv.celem_lnode[ci * NPE + k];
+        lam = T(c[2 * e]);
+        mu = T(c[2 * e + 1]);
+        load_upstream<NPE, T>(G, rowptr, pv.celem_pos + ci * pos_stride, gid, ln, a, W);
+    } else {
+#pragma unroll
+        for (int k = 0; k < NPE; ++k) ln[k] = 0;
+#pragma unroll
+        for (int m = 0; m < elastic_nblk<NPE>(); ++m)
+#pragma unroll
+            for (int n = 0; n < 9; ++n) W[m][n] = T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < NPE; ++k) {
+        xc[k][0] = xs[ln[k]][0];
+        xc[k][1] = xs[ln[k]][1];
+        xc[k][2] = xs[ln[k]][2];
+    }
+    if constexpr (NPE == 8) elastic_brick_vjp<T, S>(xc, lam, mu, W, dx, dlam, dmu);
+    else elastic_tet_vjp<T, S>(xc, lam, mu, W, dx, dlam, dmu);
+}
+
+template <typename S>
+__device__ __forceinline__ void load_cnodes(const PlanView &pv, int64_t cb, int ncn, const S *__restrict__ X,
+                                            S (*xs)[3], int32_t *cown, int32_t *gid) {
+    for (int j = threadIdx.x; j < ncn; j += blockDim.x) {
+        const int32_t g = pv.cnode_gid[cb + j];
+        gid[j] = g;
+        cown[j] = pv.cnode_own[cb + j];
+        xs[j][0] = X[3 * (int64_t)g + 0];
+        xs[j][1] = X[3 * (int64_t)g + 1];
+        xs[j][2] = X[3 * (int64_t)g + 2];
+    }
+}
 
 template <int NPE, typename T, typename S, typename CT>
 __global__ void __launch_bounds__(256) k_elastic_vjp(PlanView pv, const int64_t *__restrict__ rowptr,
@@ -275,14 +326,7 @@ __global__ void __launch_bounds__(256) k_elastic_vjp(PlanView pv, const int64_t 
         const int ncn = (int)(pv.patch_cnode_ptr[p + 1] - cb);
         const int64_t eb = pv.patch_elem_ptr[p];
         const int nel = (int)(pv.patch_elem_ptr[p + 1] - eb);
-        for (int j = tid; j < ncn; j += nthr) {
-            const int32_t g = pv.cnode_gid[cb + j];
-            gid[j] = g;
-            cown[j] = pv.cnode_own[cb + j];
-            xs[j][0] = X[3 * (int64_t)g + 0];
-            xs[j][1] = X[3 * (int64_t)g + 1];
-            xs[j][2] = X[3 * (int64_t)g + 2];
-        }
+        load_cnodes<S>(pv, cb, ncn, X, xs, cown, gid);
         for (int k = tid; k < nown; k += nthr) dxs[k][0] = dxs[k][1] = dxs[k][2] = T(0);
         __syncthreads();
         // the loop bound is uniform over the block: every lane takes part in the
@@ -291,37 +335,12 @@ __global__ void __launch_bounds__(256) k_elastic_vjp(PlanView pv, const int64_t 
             const int i = base + tid / NPE;
             const bool act = i < nel;
             const int64_t ci = eb + i;
-            int mycol = -1;
+            const int mycol = act ? (int)pv.celem_color[ci] : -1;
             uint16_t ln[NPE];
-            S xc[NPE][3];
-            T lam = T(0), mu = T(0);
-            T W[elastic_nblk<NPE>()][9];
-            int64_t e = 0;
-            if (act) {
-                mycol = pv.celem_color[ci];
-                e = pv.celem_id[ci];
-#pragma unroll
-                for (int k = 0; k < NPE; ++k) ln[k] = pv.celem_lnode[ci * NPE + k];
-                lam = T(c[2 * e]);
-                mu = T(c[2 * e + 1]);
-                load_upstream<NPE, T>(G, rowptr, pv.celem_pos + ci * pos_stride, gid, ln, a, W);
-            } else {
-#pragma unroll
-                for (int k = 0; k < NPE; ++k) ln[k] = 0;
-#pragma unroll
-                for (int m = 0; m < elastic_nblk<NPE>(); ++m)
-#pragma unroll
-                    for (int n = 0; n < 9; ++n) W[m][n] = T(0);
-            }
-#pragma unroll
-            for (int k = 0; k < NPE; ++k) {
-                xc[k][0] = xs[ln[k]][0];
-                xc[k][1] = xs[ln[k]][1];
-                xc[k][2] = xs[ln[k]][2];
-            }
+            int64_t e;
             T dx[3], dlam, dmu;
-            if constexpr (NPE == 8) elastic_brick_vjp<T, S>(xc, lam, mu, W, dx, dlam, dmu);
-            else elastic_tet_vjp<T, S>(xc, lam, mu, W, dx, dlam, dmu);
+            elastic_element_vjp<NPE, T, S, CT>(pv, rowptr, c, G, xs, gid, pos_stride, act, ci, a, ln, e, dx, dlam,
+                                               dmu);
             uint16_t lna = ln[0];
 #pragma unroll
             for (int k = 1; k < NPE; ++k)
@@ -354,12 +373,68 @@ __global__ void __launch_bounds__(256) k_elastic_vjp(PlanView pv, const int64_t 
     }
 }
 
+// Staged pass 1: every element once (its instance in the patch that owns its
+// first node), node gradients to dxe [n_elems][NPE][3] -- lane a writes node a's
+// three -- and (dL/dlambda_e, dL/dmu_e) to dc.  Pass 2 is the scalar operators'
+// gather (vjp.cu).
+template <int NPE, typename T, typename S, typename CT>
+__global__ void __launch_bounds__(256) k_elastic_vjp_elem(PlanView pv, const int64_t *__restrict__ rowptr,
+                                                          const S *__restrict__ X, const CT *__restrict__ c,
+                                                          const T *__restrict__ G, T *__restrict__ dxe,
+                                                          T *__restrict__ dcout, int pos_stride, ElVjpSmem L) {
+    extern __shared__ __align__(16) unsigned char evje_smem[];
+    __shared__ int n_prim;
+    S(*xs)[3] = reinterpret_cast<S(*)[3]>(evje_smem + L.xs);
+    int32_t *cown = reinterpret_cast<int32_t *>(evje_smem + L.cown);
+    int32_t *gid = reinterpret_cast<int32_t *>(evje_smem + L.gid);
+    int32_t *list = reinterpret_cast<int32_t *>(evje_smem + L.dxs);
+    const int tid = threadIdx.x, nthr = blockDim.x, a = tid % NPE, epb = nthr / NPE;
+    for (int64_t p = blockIdx.x; p < pv.n_patches; p += gridDim.x) {
+        const int64_t cb = pv.patch_cnode_ptr[p];
+        const int ncn = (int)(pv.patch_cnode_ptr[p + 1] - cb);
+        const int64_t eb = pv.patch_elem_ptr[p];
+        const int nel = (int)(pv.patch_elem_ptr[p + 1] - eb);
+        load_cnodes<S>(pv, cb, ncn, X, xs, cown, gid);
+        if (tid == 0) n_prim = 0;
+        __syncthreads();
+        for (int j = tid; j < nel; j += nthr)
+            if (cown[pv.celem_lnode[(eb + j) * NPE]] >= 0) list[atomicAdd(&n_prim, 1)] = j;
+        __syncthreads();
+        const int np = n_prim;
+        for (int base = 0; base < np; base += epb) {  // uniform bound: see k_elastic_vjp
+            const int i = base + tid / NPE;
+            const bool act = i < np;
+            const int64_t ci = eb + (act ? list[i] : 0);
+            uint16_t ln[NPE];
+            int64_t e;
+            T dx[3], dlam, dmu;
+            elastic_element_vjp<NPE, T, S, CT>(pv, rowptr, c, G, xs, gid, pos_stride, act, ci, a, ln, e, dx, dlam,
+                                               dmu);
+            if (act) {
+                T *o = dxe + e * (NPE * 3) + 3 * a;
+                o[0] = dx[0];
+                o[1] = dx[1];
+                o[2] = dx[2];
+                if (a == 0) {
+                    dcout[2 * e] = dlam;
+                    dcout[2 * e + 1] = dmu;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+fem_status vjp_scratch(fem_mesh m, bool fp64, void **dxe);
+fem_status launch_vjp_gather(fem_mesh m, bool fp64, const void *dxe, void *dX, cudaStream_t s);
+
 static size_t ev_a16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 template <int NPE, typename T, typename S, typename CT>
 static fem_status launch_elastic_vjp_t(fem_mesh m, const Closure &cl, const void *X, const void *c, const void *G,
-                                       void *dX, void *dc, cudaStream_t s) {
+                                       void *dX, void *dc, void *dxe, cudaStream_t s) {
     const Plan &P = m->plan;
+    const bool staged = dxe != nullptr;
     ElVjpSmem L{};
     size_t o = 0;
     L.xs = o;
@@ -369,9 +444,10 @@ static fem_status launch_elastic_vjp_t(fem_mesh m, const Closure &cl, const void
     L.gid = o;
     o = ev_a16(o + (size_t)P.max_cnodes * 4);
     L.dxs = o;
-    o = ev_a16(o + (size_t)P.max_own * 3 * sizeof(T));
+    o = ev_a16(o + (staged ? (size_t)std::max<int64_t>(cl.max_celems, P.max_celems) * 4
+                           : (size_t)P.max_own * 3 * sizeof(T)));
     L.total = o;
-    auto f = k_elastic_vjp<NPE, T, S, CT>;
+    auto f = staged ? k_elastic_vjp_elem<NPE, T, S, CT> : k_elastic_vjp<NPE, T, S, CT>;
     FEM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
     int per_sm = 0;
     FEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, 256, L.total));
@@ -382,32 +458,44 @@ static fem_status launch_elastic_vjp_t(fem_mesh m, const Closure &cl, const void
     const int64_t np = cl.p1 - cl.p0;
     if (np <= 0) return FEM_OK;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np, (int64_t)num_sms() * per_sm));
-    f<<<grid, 256, L.total, s>>>(P.view(cl), m->rowptr.ptr, (const S *)X, (const CT *)c, (const T *)G, (T *)dX,
-                                 (T *)dc, P.pos_stride, L);
-    FEM_LAUNCHED("k_elastic_vjp");
+    f<<<grid, 256, L.total, s>>>(P.view(cl), m->rowptr.ptr, (const S *)X, (const CT *)c, (const T *)G,
+                                 (T *)(staged ? dxe : dX), (T *)dc, P.pos_stride, L);
+    FEM_LAUNCHED(staged ? "k_elastic_vjp_elem" : "k_elastic_vjp");
     return FEM_OK;
 }
 
+static fem_status launch_elastic_vjp_group(fem_mesh m, const Closure &cl, bool mixed, const void *X, fem_dtype xd,
+                                           const void *c, fem_dtype cd, const void *G, void *dX, void *dc, void *dxe,
+                                           cudaStream_t s) {
+#define FEM_EV(NPE, T, S, CT) return launch_elastic_vjp_t<NPE, T, S, CT>(m, cl, X, c, G, dX, dc, dxe, s)
+    if (!mixed) {
+        if (m->npe == 8) FEM_EV(8, double, double, double);
+        FEM_EV(4, double, double, double);
+    }
+    if (m->npe == 8) {
+        if (xd == FEM_F32 && cd == FEM_F32) FEM_EV(8, float, float, float);
+        if (xd == FEM_F32 && cd == FEM_F64) FEM_EV(8, float, float, double);
+        if (xd == FEM_F64 && cd == FEM_F32) FEM_EV(8, float, double, float);
+        FEM_EV(8, float, double, double);
+    }
+    if (xd == FEM_F32 && cd == FEM_F32) FEM_EV(4, float, float, float);
+    if (xd == FEM_F32 && cd == FEM_F64) FEM_EV(4, float, float, double);
+    if (xd == FEM_F64 && cd == FEM_F32) FEM_EV(4, float, double, float);
+    FEM_EV(4, float, double, double);
+#undef FEM_EV
+}
+
+// Staged (element pass, then the gather) when the library memory for the node
+// gradients is granted, else the fused kernel.
 fem_status launch_elastic_vjp(fem_mesh m, bool mixed, const void *X, fem_dtype xd, const void *c, fem_dtype cd,
                               const void *G, void *dX, void *dc, cudaStream_t s) {
-    return for_each_group(m, s, [&](const Closure &cl) -> fem_status {
-#define FEM_EV(NPE, T, S, CT) return launch_elastic_vjp_t<NPE, T, S, CT>(m, cl, X, c, G, dX, dc, s)
-        if (!mixed) {
-            if (m->npe == 8) FEM_EV(8, double, double, double);
-            FEM_EV(4, double, double, double);
-        }
-        if (m->npe == 8) {
-            if (xd == FEM_F32 && cd == FEM_F32) FEM_EV(8, float, float, float);
-            if (xd == FEM_F32 && cd == FEM_F64) FEM_EV(8, float, float, double);
-            if (xd == FEM_F64 && cd == FEM_F32) FEM_EV(8, float, double, float);
-            FEM_EV(8, float, double, double);
-        }
-        if (xd == FEM_F32 && cd == FEM_F32) FEM_EV(4, float, float, float);
-        if (xd == FEM_F32 && cd == FEM_F64) FEM_EV(4, float, float, double);
-        if (xd == FEM_F64 && cd == FEM_F32) FEM_EV(4, float, double, float);
-        FEM_EV(4, float, double, double);
-#undef FEM_EV
-    });
+    void *dxe = nullptr;
+    const fem_status st = vjp_scratch(m, !mixed, &dxe);
+    if (st != FEM_OK && st != FEM_ERR_BUDGET) return st;
+    FEM_TRY(for_each_group(m, s, [&](const Closure &cl) {
+        return launch_elastic_vjp_group(m, cl, mixed, X, xd, c, cd, G, dX, dc, dxe, s);
+    }));
+    return dxe ? launch_vjp_gather(m, !mixed, dxe, dX, s) : FEM_OK;
 }
 
 }  // namespace fem

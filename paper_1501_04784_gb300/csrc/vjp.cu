@@ -432,6 +432,286 @@ static fem_status launch_vjp_t(fem_mesh m, const Closure &cl, const void *X, con
     return FEM_OK;
 }
 
+// ------------------------------------------------------------ staged backward
+// Pass 1 (k_vjp_elem) integrates every element once -- its instance in the
+// closure of the patch that owns its first node -- and writes the element's node
+// gradients to dxe [n_elems][NPE][3] (library memory) and dc_e.  Pass 2
+// (k_vjp_gather) adds dxe into the owned nodes of each patch colour by colour,
+// the order of the fused kernel above, and writes dX.  The element work is done
+// once instead of once per patch whose closure holds the element.
+
+struct ElemSmem {
+    size_t xs, cown, gid, list, total;
+};
+
+template <typename T, int N>
+__device__ __forceinline__ void store_row(T *__restrict__ o, const T (&v)[N]) {
+    // o is 16-byte aligned (N * sizeof(T) is a multiple of 16 for every use)
+    static_assert((N * sizeof(T)) % 16 == 0, "row of 16-byte chunks");
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int k = 0; k < N; k += 4) reinterpret_cast<float4 *>(o)[k / 4] = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; k += 2) reinterpret_cast<double2 *>(o)[k / 2] = make_double2(v[k], v[k + 1]);
+    }
+}
+
+// Closure elements of patch p whose first node the patch owns, compacted into
+// list[0 .. return) (in no particular order: each element's outputs are its own).
+__device__ __forceinline__ int primary_elems(const PlanView &pv, int npe, int64_t eb, int nel, const int32_t *cown,
+                                             int32_t *list, int *count) {
+    if (threadIdx.x == 0) *count = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < nel; j += blockDim.x)
+        if (cown[pv.celem_lnode[(eb + j) * npe]] >= 0) list[atomicAdd(count, 1)] = j;
+    __syncthreads();
+    return *count;
+}
+
+template <int NPE, typename T, typename S, typename CT>
+__global__ void __launch_bounds__(256) k_vjp_elem(PlanView pv, const int64_t *__restrict__ rowptr,
+                                                  const S *__restrict__ X, const CT *__restrict__ c,
+                                                  const T *__restrict__ G, T *__restrict__ dxe,
+                                                  T *__restrict__ dcout, ElemSmem L, bool mass) {
+    constexpr int NP = NPE * (NPE + 1) / 2;
+    extern __shared__ __align__(16) unsigned char vel_smem[];
+    __shared__ int n_prim;
+    S(*xs)[3] = reinterpret_cast<S(*)[3]>(vel_smem + L.xs);
+    int32_t *cown = reinterpret_cast<int32_t *>(vel_smem + L.cown);
+    int32_t *gid = reinterpret_cast<int32_t *>(vel_smem + L.gid);
+    int32_t *list = reinterpret_cast<int32_t *>(vel_smem + L.list);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int64_t p = blockIdx.x; p < pv.n_patches; p += gridDim.x) {
+        const int64_t cb = pv.patch_cnode_ptr[p];
+        const int ncn = (int)(pv.patch_cnode_ptr[p + 1] - cb);
+        const int64_t eb = pv.patch_elem_ptr[p];
+        const int nel = (int)(pv.patch_elem_ptr[p + 1] - eb);
+        for (int j = tid; j < ncn; j += nthr) {
+            const int32_t g = pv.cnode_gid[cb + j];
+            gid[j] = g;
+            cown[j] = pv.cnode_own[cb + j];
+            xs[j][0] = X[3 * (int64_t)g + 0];
+            xs[j][1] = X[3 * (int64_t)g + 1];
+            xs[j][2] = X[3 * (int64_t)g + 2];
+        }
+        const int np = primary_elems(pv, NPE, eb, nel, cown, list, &n_prim);
+        for (int k = tid; k < np; k += nthr) {
+            const int64_t ci = eb + list[k];
+            const int64_t e = pv.celem_id[ci];
+            int ln[NPE];
+#pragma unroll
+            for (int a = 0; a < NPE; ++a) ln[a] = pv.celem_lnode[ci * NPE + a];
+            S xc[NPE][3];
+#pragma unroll
+            for (int a = 0; a < NPE; ++a) {
+                xc[a][0] = xs[ln[a]][0];
+                xc[a][1] = xs[ln[a]][1];
+                xc[a][2] = xs[ln[a]][2];
+            }
+            T Sp[NP];
+            const uint8_t *pp = pv.celem_pos + ci * ((NP + 3) / 4 * 4);
+#pragma unroll
+            for (int a = 0; a < NPE; ++a)
+#pragma unroll
+                for (int b = 0; b <= a; ++b) {
+                    const int q = a * (a + 1) / 2 + b;
+                    const int32_t r = gid[ln[a] > ln[b] ? ln[a] : ln[b]];
+                    Sp[q] = G[rowptr[r] + pp[q]];
+                }
+            T dx[NPE][3], dcv;
+            if (mass) {
+                if constexpr (NPE == 8) brick_mass_vjp<T, S>(xc, (T)c[e], Sp, dx, dcv);
+                else tet_mass_vjp<T, S>(xc, (T)c[e], Sp, dx, dcv);
+            } else {
+                if constexpr (NPE == 8) brick_vjp<T, S>(xc, (T)c[e], Sp, dx, dcv);
+                else tet_vjp<T, S>(xc, (T)c[e], Sp, dx, dcv);
+            }
+            T flat[NPE * 3];
+#pragma unroll
+            for (int a = 0; a < NPE; ++a)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) flat[3 * a + j] = dx[a][j];
+            store_row<T, NPE * 3>(dxe + e * (NPE * 3), flat);
+            dcout[e] = dcv;
+        }
+        __syncthreads();
+    }
+}
+
+struct GatherSmem {
+    size_t cown, dxs, total;
+};
+
+template <int NPE, typename T>
+__global__ void __launch_bounds__(256) k_vjp_gather(PlanView pv, const T *__restrict__ dxe, T *__restrict__ dX,
+                                                    GatherSmem L) {
+    extern __shared__ __align__(16) unsigned char vg_smem[];
+    int32_t *cown = reinterpret_cast<int32_t *>(vg_smem + L.cown);
+    T(*dxs)[3] = reinterpret_cast<T(*)[3]>(vg_smem + L.dxs);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int64_t p = blockIdx.x; p < pv.n_patches; p += gridDim.x) {
+        const int64_t nb = pv.patch_node_ptr[p];
+        const int nown = (int)(pv.patch_node_ptr[p + 1] - nb);
+        const int64_t cb = pv.patch_cnode_ptr[p];
+        const int ncn = (int)(pv.patch_cnode_ptr[p + 1] - cb);
+        const int64_t eb = pv.patch_elem_ptr[p];
+        const int nel = (int)(pv.patch_elem_ptr[p + 1] - eb);
+        for (int j = tid; j < ncn; j += nthr) cown[j] = pv.cnode_own[cb + j];
+        for (int k = tid; k < nown; k += nthr) dxs[k][0] = dxs[k][1] = dxs[k][2] = T(0);
+        __syncthreads();
+        for (int base = 0; base < nel; base += nthr) {
+            const int i = base + tid;
+            int mycol = -1;
+            int own[NPE];
+            T v[NPE][3];
+            if (i < nel) {
+                const int64_t ci = eb + i;
+                mycol = pv.celem_color[ci];
+                const int64_t e = pv.celem_id[ci];
+                const T *src = dxe + e * (NPE * 3);
+#pragma unroll
+                for (int a = 0; a < NPE; ++a) {
+                    own[a] = cown[pv.celem_lnode[ci * NPE + a]];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) v[a][j] = own[a] >= 0 ? src[3 * a + j] : T(0);
+                }
+            }
+            const int last = min(base + nthr, nel) - 1;
+            const int c0 = pv.celem_color[eb + base], c1 = pv.celem_color[eb + last];
+            for (int cc = c0; cc <= c1; ++cc) {
+                if (mycol == cc) {
+#pragma unroll
+                    for (int a = 0; a < NPE; ++a) {
+                        const int o = own[a];
+                        if (o >= 0) {
+                            dxs[o][0] += v[a][0];
+                            dxs[o][1] += v[a][1];
+                            dxs[o][2] += v[a][2];
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int k = tid; k < nown; k += nthr) {
+            const int64_t g = pv.own_row[nb + k];
+            dX[3 * g + 0] = dxs[k][0];
+            dX[3 * g + 1] = dxs[k][1];
+            dX[3 * g + 2] = dxs[k][2];
+        }
+        __syncthreads();
+    }
+}
+
+static int grid_for(const void *f, int threads, size_t smem, int64_t np, const char *what, fem_status *st) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, smem);
+    if (e != cudaSuccess || per_sm < 1) {
+        set_error("%s cannot be resident with %zu bytes of shared memory", what, smem);
+        *st = e != cudaSuccess ? cuda_status(e, what) : FEM_ERR_UNSUPPORTED;
+        return 0;
+    }
+    *st = FEM_OK;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(np, (int64_t)num_sms() * per_sm));
+}
+
+ElemSmem elem_smem(const Plan &P, const Closure &cl, size_t xsize) {
+    ElemSmem L{};
+    size_t o = 0;
+    L.xs = o;
+    o = a16(o + (size_t)P.max_cnodes * 3 * xsize);
+    L.cown = o;
+    o = a16(o + (size_t)P.max_cnodes * 4);
+    L.gid = o;
+    o = a16(o + (size_t)P.max_cnodes * 4);
+    L.list = o;
+    o = a16(o + (size_t)std::max<int64_t>(cl.max_celems, P.max_celems) * 4);
+    L.total = o;
+    return L;
+}
+
+template <int NPE, typename T, typename S, typename CT>
+static fem_status launch_vjp_elem_t(fem_mesh m, const Closure &cl, const void *X, const void *c, const void *G,
+                                    void *dxe, void *dc, cudaStream_t s) {
+    const Plan &P = m->plan;
+    const ElemSmem L = elem_smem(P, cl, sizeof(S));
+    auto f = k_vjp_elem<NPE, T, S, CT>;
+    FEM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+    const int64_t np = cl.p1 - cl.p0;
+    if (np <= 0) return FEM_OK;
+    fem_status st;
+    const int grid = grid_for((const void *)f, 256, L.total, np, "backward element kernel", &st);
+    if (st != FEM_OK) return st;
+    f<<<grid, 256, L.total, s>>>(P.view(cl), m->rowptr.ptr, (const S *)X, (const CT *)c, (const T *)G, (T *)dxe,
+                                 (T *)dc, L, m->opt.operator_kind == 1);
+    FEM_LAUNCHED("k_vjp_elem");
+    return FEM_OK;
+}
+
+template <int NPE, typename T>
+static fem_status launch_gather_t(fem_mesh m, const Closure &cl, const void *dxe, void *dX, cudaStream_t s) {
+    const Plan &P = m->plan;
+    GatherSmem L{};
+    size_t o = 0;
+    L.cown = o;
+    o = a16(o + (size_t)P.max_cnodes * 4);
+    L.dxs = o;
+    o = a16(o + (size_t)P.max_own * 3 * sizeof(T));
+    L.total = o;
+    auto f = k_vjp_gather<NPE, T>;
+    FEM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+    const int64_t np = cl.p1 - cl.p0;
+    if (np <= 0) return FEM_OK;
+    fem_status st;
+    const int grid = grid_for((const void *)f, 256, L.total, np, "backward gather kernel", &st);
+    if (st != FEM_OK) return st;
+    f<<<grid, 256, L.total, s>>>(P.view(cl), (const T *)dxe, (T *)dX, L);
+    FEM_LAUNCHED("k_vjp_gather");
+    return FEM_OK;
+}
+
+// Pass 2 for every operator (the elasticity kernel writes the same dxe layout).
+fem_status launch_vjp_gather(fem_mesh m, bool fp64, const void *dxe, void *dX, cudaStream_t s) {
+    return for_each_group(m, s, [&](const Closure &cl) -> fem_status {
+        if (fp64) return m->npe == 8 ? launch_gather_t<8, double>(m, cl, dxe, dX, s)
+                                     : launch_gather_t<4, double>(m, cl, dxe, dX, s);
+        return m->npe == 8 ? launch_gather_t<8, float>(m, cl, dxe, dX, s) : launch_gather_t<4, float>(m, cl, dxe, dX, s);
+    });
+}
+
+// Library memory for dxe, in the mesh's FP64 element-matrix buffer (grown if
+// needed); FEM_ERR_BUDGET when the budget refuses it.  Only for a plan whose
+// closures are resident (pass 2 needs every element's pass 1 first).
+fem_status vjp_scratch(fem_mesh m, bool fp64, void **dxe) {
+    *dxe = nullptr;
+    if (m->plan.chunked || m->opt.vjp_fused != 0) return FEM_ERR_BUDGET;
+    const size_t need = ((size_t)m->n_elems * m->npe * 3 * (fp64 ? 8 : 4) + 7) / 8;
+    if (m->ke64.n < need) FEM_TRY(m->ke64.alloc(m->arena, need, "backward element gradients"));
+    *dxe = m->ke64.ptr;
+    return FEM_OK;
+}
+
+static fem_status launch_vjp_elem(fem_mesh m, const Closure &cl, bool mixed, const void *X, fem_dtype xd,
+                                  const void *c, fem_dtype cd, const void *G, void *dxe, void *dc, cudaStream_t s) {
+#define FEM_E(NPE, T, S, CT) return launch_vjp_elem_t<NPE, T, S, CT>(m, cl, X, c, G, dxe, dc, s)
+    if (!mixed) {
+        if (m->npe == 8) FEM_E(8, double, double, double);
+        FEM_E(4, double, double, double);
+    }
+    if (m->npe == 8) {
+        if (xd == FEM_F32 && cd == FEM_F32) FEM_E(8, float, float, float);
+        if (xd == FEM_F32 && cd == FEM_F64) FEM_E(8, float, float, double);
+        if (xd == FEM_F64 && cd == FEM_F32) FEM_E(8, float, double, float);
+        FEM_E(8, float, double, double);
+    }
+    if (xd == FEM_F32 && cd == FEM_F32) FEM_E(4, float, float, float);
+    if (xd == FEM_F32 && cd == FEM_F64) FEM_E(4, float, float, double);
+    if (xd == FEM_F64 && cd == FEM_F32) FEM_E(4, float, double, float);
+    FEM_E(4, float, double, double);
+#undef FEM_E
+}
+
 static fem_status launch_vjp_group(fem_mesh m, const Closure &cl, bool mixed, const void *X, fem_dtype xd,
                                    const void *c, fem_dtype cd, const void *G, void *dX, void *dc, cudaStream_t s) {
 #define FEM_V(NPE, T, S, CT) return launch_vjp_t<NPE, T, S, CT>(m, cl, X, c, G, dX, dc, s)
@@ -454,6 +734,15 @@ static fem_status launch_vjp_group(fem_mesh m, const Closure &cl, bool mixed, co
 
 fem_status launch_vjp(fem_mesh m, bool mixed, const void *X, fem_dtype xd, const void *c, fem_dtype cd,
                       const void *G, void *dX, void *dc, cudaStream_t s) {
+    void *dxe = nullptr;
+    const fem_status st = vjp_scratch(m, !mixed, &dxe);
+    if (st == FEM_OK) {
+        FEM_TRY(for_each_group(m, s, [&](const Closure &cl) {
+            return launch_vjp_elem(m, cl, mixed, X, xd, c, cd, G, dxe, dc, s);
+        }));
+        return launch_vjp_gather(m, !mixed, dxe, dX, s);
+    }
+    if (st != FEM_ERR_BUDGET) return st;
     return for_each_group(m, s, [&](const Closure &cl) {
         return launch_vjp_group(m, cl, mixed, X, xd, c, cd, G, dX, dc, s);
     });

@@ -75,8 +75,10 @@ def test_budget_groups_bitwise_equal(fem, prec):
     m = meshgen.hex_grid(24, jitter=0.2, seed=77, permute_nodes=True, permute_elems=True)
     dt = torch.float32 if prec == "mixed" else torch.float64
     X, c = dev(m.X, dt), dev(m.c, dt)
-    # FP64 builds fuse here on both sides, so the two differ only in the grouping
-    free = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), patch_entries=1024, fp64_fused=1)
+    # FP64 builds and backward passes fuse here on both sides (a plan built per
+    # patch group always fuses them), so the two differ only in the grouping
+    free = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), patch_entries=1024, fp64_fused=1,
+                    vjp_fused=1)
     ref = free.build_K(X, c, prec)
     need = free.info()["plan_bytes"]
     tight = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), patch_entries=1024,

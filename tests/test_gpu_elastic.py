@@ -246,6 +246,25 @@ def test_elastic_backward(fem, name, prec, cap):
     assert np.array_equal(dc2.cpu().numpy().astype(np.float64), dc)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["hex_6x5x4_perm", "tet_5x4x3_perm"])
+def test_elastic_backward_staged_and_fused_agree(fem, name, prec):
+    """The staged elasticity backward (element pass into library memory, then the
+    gather) against the fused one, up to the rounding of the element arithmetic."""
+    m = MESHES[name]()
+    Xd, cd, _, _ = inputs(m, prec)
+    staged, fused = make(fem, m, patch_entries=48), make(fem, m, patch_entries=48, vjp_fused=1)
+    nnz = staged.pattern()
+    fused.pattern()
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    G = dev(np.random.default_rng(13).standard_normal(nnz), dt)
+    a, b = staged.vjp(Xd, cd, G, prec), fused.vjp(Xd, cd, G, prec)
+    tol = 1e-13 if prec == "fp64" else 2e-6
+    for u, v in zip(a, b):
+        assert (u - v).abs().max().item() <= tol * v.abs().max().item()
+    assert staged.info()["live_bytes"] > fused.info()["live_bytes"]
+
+
 def test_elastic_autograd(fem):
     """torch.autograd through build_K: the gradient of a scalar function of K's
     values reaches X and the Lame parameters [n_elems, 2]."""

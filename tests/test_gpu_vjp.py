@@ -54,6 +54,30 @@ def test_vjp_matches_oracle_gradient(fem, name, prec):
     assert np.abs(dc - dc_ref).max() <= tol * np.abs(dc_ref).max()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["hex_4x3x3", "tet_3x3x2", "hex20_perm"])
+def test_vjp_staged_and_fused_agree(fem, name, prec):
+    """The staged backward (every element once into library memory, then a gather in
+    colour order) and the fused one (recomputed in every closure holding the
+    element) give the same gradients up to the rounding of the element arithmetic.
+    (A plan built per patch group always takes the fused pass: test_gpu_batch_budget.)"""
+    m = CASES[name]()
+    X, c = rounded_inputs(m, prec)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    Xd, cd = dev(X, dt), dev(c, dt)
+    staged = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), patch_entries=512)
+    fused = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), patch_entries=512, vjp_fused=1)
+    nnz = staged.pattern()
+    fused.pattern()
+    G = dev(np.random.default_rng(8).standard_normal(nnz), dt)
+    a, b = staged.vjp(Xd, cd, G, prec), fused.vjp(Xd, cd, G, prec)
+    tol = 1e-13 if prec == "fp64" else 2e-6
+    for u, v in zip(a, b):
+        assert (u - v).abs().max().item() <= tol * v.abs().max().item()
+    scratch = m.n_elems * m.npe * 3 * (8 if prec == "fp64" else 4)
+    assert staged.info()["live_bytes"] >= fused.info()["live_bytes"] + scratch
+
+
 def test_vjp_bitwise_reproducible(fem):
     m = CASES["hex20_perm"]()
     mesh = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64))
