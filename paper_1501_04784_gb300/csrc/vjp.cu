@@ -27,110 +27,213 @@
 
 namespace fem {
 
-// Brick: packed upstream Sp[36] -> node gradients dx[8][3] and dc.
-template <typename T, typename S>
-__device__ __forceinline__ void brick_vjp(const S (*xc)[3], T c, const T (&Sp)[36], T (&dx)[8][3], T &dc) {
-    Vec3<T> e[3][2][2];
-    brick_edges<T, S>(xc, e);
-    Vec3<T> row[3][2][2];
-    brick_jrows(e, row);
-    T Ss[8][8];
+// Coefficient of the 1D operator along one axis of the brick contraction:
+// kind 0 = the hats phi_i at the Gauss points (2 x 2), kind 1 = the hat
+// products F_i (3 x 2: F_0 = (PP, QQ), F_1 = (QQ, PP), F_2 = (PQ, PQ)).
+template <typename T, int K>
+__device__ __forceinline__ T axis_coef(int i, int a) {
+    if (K) return i == 2 ? T(FEM_GPQ) : (i == a ? T(FEM_GPP) : T(FEM_GQQ));
+    return i == a ? T(FEM_GP) : T(FEM_GQ);
+}
+
+// Adjoint of contract_FF: Abar[u][v] = sum_cd F_c(u) F_d(v) Tbar[c][d].
+template <typename T>
+__device__ __forceinline__ void contract_FF_adj(const T (&Tb)[3][3], T (&Ab)[2][2]) {
+    T Z[3][2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int v = 0; v < 2; ++v)
+            Z[c][v] = axis_coef<T, 1>(0, v) * Tb[c][0] + axis_coef<T, 1>(1, v) * Tb[c][1] +
+                      axis_coef<T, 1>(2, v) * Tb[c][2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v)
+            Ab[u][v] = axis_coef<T, 1>(0, u) * Z[0][v] + axis_coef<T, 1>(1, u) * Z[1][v] +
+                       axis_coef<T, 1>(2, u) * Z[2][v];
+}
+
+// Adjoint of contract_cross<K1, K2, K3>: the forward applies one 1D operator per
+// axis to m[2][2][2]; the adjoint applies their transposes to Vbar.
+template <typename T, int K1, int K2, int K3>
+__device__ __forceinline__ void contract_cross_adj(const T (&Vb)[3][3][3], T (&mb)[2][2][2]) {
+    constexpr int N1 = K1 ? 3 : 2, N2 = K2 ? 3 : 2, N3 = K3 ? 3 : 2;
+    T Y[2][3][3];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int j = 0; j < N2; ++j)
+#pragma unroll
+            for (int k = 0; k < N3; ++k) {
+                T v = T(0);
+#pragma unroll
+                for (int i = 0; i < N1; ++i) v += axis_coef<T, K1>(i, a) * Vb[i][j][k];
+                Y[a][j][k] = v;
+            }
+    T W[2][2][3];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int k = 0; k < N3; ++k) {
+                T v = T(0);
+#pragma unroll
+                for (int j = 0; j < N2; ++j) v += axis_coef<T, K2>(j, b) * Y[a][j][k];
+                W[a][b][k] = v;
+            }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                T v = T(0);
+#pragma unroll
+                for (int k = 0; k < N3; ++k) v += axis_coef<T, K3>(k, c) * W[a][b][k];
+                mb[a][b][c] = v;
+            }
+}
+
+// Adjoint of brick_contract with s = 1/8 (c is applied by the caller):
+// Mb[q][6] = dL/dM~_q for L = sum_p Sp[p] k_p / c.
+template <typename T>
+__device__ __forceinline__ void brick_contract_adj(const T (&Sp)[36], T (&Mb)[8][6]) {
+    T Trr[3][3], Tss[3][3], Ttt[3][3], Vrs[3][3][3], Vrt[3][3][3], Vst[3][3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            Trr[i][j] = Tss[i][j] = Ttt[i][j] = T(0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) Vrs[i][j][k] = Vrt[i][j][k] = Vst[i][j][k] = T(0);
+        }
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int b = 0; b <= a; ++b) {
-            const T v = Sp[a * (a + 1) / 2 + b];
-            Ss[a][b] = a == b ? v : T(0.5) * v;
-            Ss[b][a] = Ss[a][b];
+            const int a1 = hb1(a), a2 = hb2(a), a3 = hb3(a);
+            const int b1 = hb1(b), b2 = hb2(b), b3 = hb3(b);
+            const int c1 = hcls(a1, b1), c2 = hcls(a2, b2), c3 = hcls(a3, b3);
+            const T v = T(0.125) * Sp[a * (a + 1) / 2 + b];
+            Trr[c2][c3] += T(hsig(a1) * hsig(b1)) * v;
+            Tss[c1][c3] += T(hsig(a2) * hsig(b2)) * v;
+            Ttt[c1][c2] += T(hsig(a3) * hsig(b3)) * v;
+            Vrs[b1][a2][c3] += T(hsig(a1) * hsig(b2)) * v;
+            Vrs[a1][b2][c3] += T(hsig(a2) * hsig(b1)) * v;
+            Vrt[b1][c2][a3] += T(hsig(a1) * hsig(b3)) * v;
+            Vrt[a1][c2][b3] += T(hsig(a3) * hsig(b1)) * v;
+            Vst[c1][b2][a3] += T(hsig(a2) * hsig(b3)) * v;
+            Vst[c1][a2][b3] += T(hsig(a3) * hsig(b2)) * v;
         }
+    T Arr[2][2], Ass[2][2], Att[2][2], mrs[2][2][2], mrt[2][2][2], mst[2][2][2];
+    contract_FF_adj(Trr, Arr);
+    contract_FF_adj(Tss, Ass);
+    contract_FF_adj(Ttt, Att);
+    contract_cross_adj<T, 0, 0, 1>(Vrs, mrs);
+    contract_cross_adj<T, 0, 1, 0>(Vrt, mrt);
+    contract_cross_adj<T, 1, 0, 0>(Vst, mst);
+#pragma unroll
+    for (int q1 = 0; q1 < 2; ++q1)
+#pragma unroll
+        for (int q2 = 0; q2 < 2; ++q2)
+#pragma unroll
+            for (int q3 = 0; q3 < 2; ++q3) {
+                const int q = 4 * q1 + 2 * q2 + q3;
+                Mb[q][0] = Arr[q2][q3];  // M~_q,rr enters A_rr summed over q1
+                Mb[q][1] = Ass[q1][q3];
+                Mb[q][2] = Att[q1][q2];
+                Mb[q][3] = mrs[q1][q2][q3];
+                Mb[q][4] = mrt[q1][q2][q3];
+                Mb[q][5] = mst[q1][q2][q3];
+            }
+}
+
+// Brick: packed upstream Sp[36] -> node gradients dx[8][3] and dc, by reverse
+// mode through the forward's own steps (brick_edges -> brick_jrows -> brick_M ->
+// brick_contract).  With the rows R, S, U of 2J_q, cofactors C0 = S x U,
+// C1 = U x R, C2 = R x S, d = R.C0 and M~_ij = C_i.C_j / |d|, the point's share
+// L_q = phi / |d| with phi = sum_ij Mb_ij C_i.C_j gives, with Y_i = sum_j Mb_ij C_j
+// (Mb symmetric, off-diagonal halves) and lambda = phi / (|d| d),
+//     dL/dR = (2/|d|)(Y1 x U + S x Y2) - lambda C0,
+//     dL/dS = (2/|d|)(U x Y0 + Y2 x R) - lambda C1,
+//     dL/dU = (2/|d|)(Y0 x S + R x Y1) - lambda C2.
+// The row interpolation's 1D operator is symmetric, so brick_jrows is its own
+// adjoint; the edges are node differences.  k is linear in c: dc = L / c.
+template <typename T, typename S>
+__device__ __forceinline__ void brick_vjp(const S (*xc)[3], T c, const T (&Sp)[36], T (&dx)[8][3], T &dc) {
+    T Mb[8][6];
+    brick_contract_adj(Sp, Mb);
+    Vec3<T> e[3][2][2];
+    brick_edges<T, S>(xc, e);
+    Vec3<T> row[3][2][2];
+    brick_jrows(e, row);
+    Vec3<T> rb[3][2][2];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int v = 0; v < 2; ++v) rb[ax][u][v] = {T(0), T(0), T(0)};
+    dc = T(0);
+    const T h = T(0.5);
+#pragma unroll
+    for (int q1 = 0; q1 < 2; ++q1)
+#pragma unroll
+        for (int q2 = 0; q2 < 2; ++q2)
+#pragma unroll
+            for (int q3 = 0; q3 < 2; ++q3) {
+                const int q = 4 * q1 + 2 * q2 + q3;
+                const Vec3<T> &R = row[0][q2][q3];
+                const Vec3<T> &Sv = row[1][q1][q3];
+                const Vec3<T> &U = row[2][q1][q2];
+                const Vec3<T> C0 = cross3(Sv, U), C1 = cross3(U, R), C2 = cross3(R, Sv);
+                const T d = dot3(R, C0);
+                const T inv = T(1) / (d < T(0) ? -d : d);
+                const T m0 = Mb[q][0], m1 = Mb[q][1], m2 = Mb[q][2];
+                const T m3 = h * Mb[q][3], m4 = h * Mb[q][4], m5 = h * Mb[q][5];
+                const Vec3<T> Y0 = {m0 * C0.x + m3 * C1.x + m4 * C2.x, m0 * C0.y + m3 * C1.y + m4 * C2.y,
+                                    m0 * C0.z + m3 * C1.z + m4 * C2.z};
+                const Vec3<T> Y1 = {m3 * C0.x + m1 * C1.x + m5 * C2.x, m3 * C0.y + m1 * C1.y + m5 * C2.y,
+                                    m3 * C0.z + m1 * C1.z + m5 * C2.z};
+                const Vec3<T> Y2 = {m4 * C0.x + m5 * C1.x + m2 * C2.x, m4 * C0.y + m5 * C1.y + m2 * C2.y,
+                                    m4 * C0.z + m5 * C1.z + m2 * C2.z};
+                const T phi = dot3(C0, Y0) + dot3(C1, Y1) + dot3(C2, Y2);
+                dc += phi * inv;
+                const T lam = phi * inv / d, t = T(2) * inv;
+                const Vec3<T> a0 = cross3(Y1, U), b0 = cross3(Sv, Y2);
+                const Vec3<T> a1 = cross3(U, Y0), b1 = cross3(Y2, R);
+                const Vec3<T> a2 = cross3(Y0, Sv), b2 = cross3(R, Y1);
+                Vec3<T> &r0 = rb[0][q2][q3], &r1 = rb[1][q1][q3], &r2 = rb[2][q1][q2];
+                r0 = {r0.x + t * (a0.x + b0.x) - lam * C0.x, r0.y + t * (a0.y + b0.y) - lam * C0.y,
+                      r0.z + t * (a0.z + b0.z) - lam * C0.z};
+                r1 = {r1.x + t * (a1.x + b1.x) - lam * C1.x, r1.y + t * (a1.y + b1.y) - lam * C1.y,
+                      r1.z + t * (a1.z + b1.z) - lam * C1.z};
+                r2 = {r2.x + t * (a2.x + b2.x) - lam * C2.x, r2.y + t * (a2.y + b2.y) - lam * C2.y,
+                      r2.z + t * (a2.z + b2.z) - lam * C2.z};
+            }
+    Vec3<T> eb[3][2][2];
+    brick_jrows(rb, eb);
 #pragma unroll
     for (int a = 0; a < 8; ++a) dx[a][0] = dx[a][1] = dx[a][2] = T(0);
-    dc = T(0);
-    const T P = T(FEM_GP), Q = T(FEM_GQ);
-#pragma unroll 1
-    for (int q = 0; q < 8; ++q) {
-        const int q1 = q >> 2, q2 = (q >> 1) & 1, q3 = q & 1;
-        // true Jacobian rows (the stored rows are 2J)
-        Vec3<T> R = row[0][q2][q3], Sv = row[1][q1][q3], U = row[2][q1][q2];
-        R = {T(0.5) * R.x, T(0.5) * R.y, T(0.5) * R.z};
-        Sv = {T(0.5) * Sv.x, T(0.5) * Sv.y, T(0.5) * Sv.z};
-        U = {T(0.5) * U.x, T(0.5) * U.y, T(0.5) * U.z};
-        const Vec3<T> C0 = cross3(Sv, U), C1 = cross3(U, R), C2 = cross3(R, Sv);
-        const T d = dot3(R, C0);
-        const T ad = d < T(0) ? -d : d;
-        // A = J^{-1}: A[i][j] = C_j[i] / d
-        const T id = T(1) / d;
-        T A[3][3] = {{C0.x * id, C1.x * id, C2.x * id}, {C0.y * id, C1.y * id, C2.y * id},
-                     {C0.z * id, C1.z * id, C2.z * id}};
-        const T iad = T(1) / ad;
-        T M[3][3];
-        M[0][0] = dot3(C0, C0) * iad; M[1][1] = dot3(C1, C1) * iad; M[2][2] = dot3(C2, C2) * iad;
-        M[0][1] = M[1][0] = dot3(C0, C1) * iad;
-        M[0][2] = M[2][0] = dot3(C0, C2) * iad;
-        M[1][2] = M[2][1] = dot3(C1, C2) * iad;
-        // natural derivatives at q: D[i][a]
-        T D[3][8];
 #pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            const int a1 = hb1(a), a2 = hb2(a), a3 = hb3(a);
-            const T f1 = a1 == q1 ? P : Q, f2 = a2 == q2 ? P : Q, f3 = a3 == q3 ? P : Q;
-            D[0][a] = T(0.5 * hsig(a1)) * f2 * f3;
-            D[1][a] = T(0.5 * hsig(a2)) * f1 * f3;
-            D[2][a] = T(0.5 * hsig(a3)) * f1 * f2;
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int n0[3] = {hnode(0, i, j), hnode(i, 0, j), hnode(i, j, 0)};
+            const int n1[3] = {hnode(1, i, j), hnode(i, 1, j), hnode(i, j, 1)};
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                const Vec3<T> &g = eb[ax][i][j];
+                dx[n1[ax]][0] += c * g.x;
+                dx[n1[ax]][1] += c * g.y;
+                dx[n1[ax]][2] += c * g.z;
+                dx[n0[ax]][0] -= c * g.x;
+                dx[n0[ax]][1] -= c * g.y;
+                dx[n0[ax]][2] -= c * g.z;
+            }
         }
-        // H = D Ss D^T
-        T V[3][8];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                T s = T(0);
-#pragma unroll
-                for (int a = 0; a < 8; ++a) s += D[i][a] * Ss[a][b];
-                V[i][b] = s;
-            }
-        T H[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                T s = T(0);
-#pragma unroll
-                for (int b = 0; b < 8; ++b) s += V[i][b] * D[j][b];
-                H[i][j] = s;
-            }
-        T f = T(0);
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) f += M[i][j] * H[i][j];
-        dc += f;
-        // G = c (f I - 2 M H) A^T
-        T W[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                T s = T(0);
-#pragma unroll
-                for (int l = 0; l < 3; ++l) s += M[i][l] * H[l][k];
-                W[i][k] = (i == k ? f : T(0)) - T(2) * s;
-            }
-        T G[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                T s = T(0);
-#pragma unroll
-                for (int k = 0; k < 3; ++k) s += W[i][k] * A[j][k];
-                G[i][j] = c * s;
-            }
-#pragma unroll
-        for (int a = 0; a < 8; ++a)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) dx[a][j] += D[0][a] * G[0][j] + D[1][a] * G[1][j] + D[2][a] * G[2][j];
-    }
 }
 
 // Tetrahedron: one point, weight 1/6, D = reference barycentric gradients.
