@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--block-threads", type=int, default=0, help="--once only: threads per block (0 = default)")
     ap.add_argument("--operator", choices=["stiffness", "elasticity"], default="stiffness",
                     help="--once only: the scalar stiffness matrix or the elasticity operator")
+    ap.add_argument("--backward", action="store_true",
+                    help="--once only: run the backward pass (fem_vjp, seeded upstream) instead of the build")
     return ap.parse_args()
 
 
@@ -646,11 +648,18 @@ def run_once(args):
     nnz = mesh.pattern()
     X, c = (X64.float(), c64.float()) if args.once == "mixed" else (X64, c64)
     v = torch.empty(nnz, dtype=X.dtype, device="cuda")
+    if args.backward:
+        import numpy as np
+        G = torch.from_numpy(np.random.default_rng(21).standard_normal(nnz)).cuda().to(X.dtype)
     for _ in range(2):
-        mesh.build_K(X, c, args.once, out=v)
+        if args.backward:
+            mesh.vjp(X, c, G, args.once)
+        else:
+            mesh.build_K(X, c, args.once, out=v)
     torch.cuda.synchronize()
     mesh.sync()
-    print(f"built {args.workload} {args.operator} {args.once}: nnz {nnz}, patches {mesh.info()['n_patches']}")
+    what = "backward" if args.backward else "built"
+    print(f"{what} {args.workload} {args.operator} {args.once}: nnz {nnz}, patches {mesh.info()['n_patches']}")
 
 
 if __name__ == "__main__":

@@ -24,6 +24,7 @@
 // element's first node.  No atomics; bitwise reproducible.
 #include "element.cuh"
 #include "mesh.cuh"
+#include "phases.cuh"
 
 namespace fem {
 
@@ -406,11 +407,11 @@ struct VjpSmem {
     size_t xs, cown, gid, dxs, total;
 };
 
-template <int NPE, typename T, typename S, typename CT>
+template <int NPE, typename T, typename S, typename CT, bool MASS>
 __global__ void __launch_bounds__(256) k_vjp(PlanView pv, const int64_t *__restrict__ rowptr,
                                              const S *__restrict__ X, const CT *__restrict__ c,
                                              const T *__restrict__ G, T *__restrict__ dX, T *__restrict__ dcout,
-                                             VjpSmem L, bool mass) {
+                                             VjpSmem L) {
     constexpr int NP = NPE * (NPE + 1) / 2;
     extern __shared__ __align__(16) unsigned char vjp_smem[];
     S(*xs)[3] = reinterpret_cast<S(*)[3]>(vjp_smem + L.xs);
@@ -465,7 +466,7 @@ __global__ void __launch_bounds__(256) k_vjp(PlanView pv, const int64_t *__restr
                         Sp[q] = G[rowptr[r] + pp[q]];
                     }
                 T dcv;
-                if (mass) {
+                if constexpr (MASS) {
                     if constexpr (NPE == 8) brick_mass_vjp<T, S>(xc, (T)c[e], Sp, dx, dcv);
                     else tet_mass_vjp<T, S>(xc, (T)c[e], Sp, dx, dcv);
                 } else {
@@ -518,7 +519,7 @@ static fem_status launch_vjp_t(fem_mesh m, const Closure &cl, const void *X, con
     L.dxs = o;
     o = a16(o + (size_t)P.max_own * 3 * sizeof(T));
     L.total = o;
-    auto f = k_vjp<NPE, T, S, CT>;
+    auto f = m->opt.operator_kind == 1 ? k_vjp<NPE, T, S, CT, true> : k_vjp<NPE, T, S, CT, false>;
     FEM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
     int per_sm = 0;
     FEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, 256, L.total));
@@ -530,7 +531,7 @@ static fem_status launch_vjp_t(fem_mesh m, const Closure &cl, const void *X, con
     if (np <= 0) return FEM_OK;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np, (int64_t)num_sms() * per_sm));
     f<<<grid, 256, L.total, s>>>(P.view(cl), m->rowptr.ptr, (const S *)X, (const CT *)c, (const T *)G, (T *)dX,
-                                 (T *)dc, L, m->opt.operator_kind == 1);
+                                 (T *)dc, L);
     FEM_LAUNCHED("k_vjp");
     return FEM_OK;
 }
@@ -572,11 +573,17 @@ __device__ __forceinline__ int primary_elems(const PlanView &pv, int npe, int64_
     return *count;
 }
 
-template <int NPE, typename T, typename S, typename CT>
+// FP64 element work holds ~220 registers a thread: 128-thread blocks leave a
+// smaller idle tail per patch at the same 8 warps per SM (measured: 4.83 -> 4.45
+// ms on 1M bricks); FP32 runs 256-thread blocks (measured faster there).
+template <typename T>
+constexpr int vjp_elem_threads() { return sizeof(T) == 8 ? 128 : 256; }
+
+template <int NPE, typename T, typename S, typename CT, bool MASS>
 __global__ void __launch_bounds__(256) k_vjp_elem(PlanView pv, const int64_t *__restrict__ rowptr,
                                                   const S *__restrict__ X, const CT *__restrict__ c,
                                                   const T *__restrict__ G, T *__restrict__ dxe,
-                                                  T *__restrict__ dcout, ElemSmem L, bool mass) {
+                                                  T *__restrict__ dcout, ElemSmem L) {
     constexpr int NP = NPE * (NPE + 1) / 2;
     extern __shared__ __align__(16) unsigned char vel_smem[];
     __shared__ int n_prim;
@@ -623,7 +630,7 @@ __global__ void __launch_bounds__(256) k_vjp_elem(PlanView pv, const int64_t *__
                     Sp[q] = G[rowptr[r] + pp[q]];
                 }
             T dx[NPE][3], dcv;
-            if (mass) {
+            if constexpr (MASS) {
                 if constexpr (NPE == 8) brick_mass_vjp<T, S>(xc, (T)c[e], Sp, dx, dcv);
                 else tet_mass_vjp<T, S>(xc, (T)c[e], Sp, dx, dcv);
             } else {
@@ -646,13 +653,19 @@ struct GatherSmem {
     size_t cown, dxs, total;
 };
 
+// The colour order is kept by the forward kernel's ring of mbarrier phases
+// (phases.cuh) instead of block-wide barriers: a warp with nothing to add in a
+// colour only arrives and moves on.
 template <int NPE, typename T>
 __global__ void __launch_bounds__(256) k_vjp_gather(PlanView pv, const T *__restrict__ dxe, T *__restrict__ dX,
-                                                    GatherSmem L) {
+                                                    GatherSmem L, WaitCtl wc) {
     extern __shared__ __align__(16) unsigned char vg_smem[];
+    __shared__ __align__(8) uint64_t mb[PHASE_RING];
     int32_t *cown = reinterpret_cast<int32_t *>(vg_smem + L.cown);
     T(*dxs)[3] = reinterpret_cast<T(*)[3]>(vg_smem + L.dxs);
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
+    phase_init(mb);
+    uint32_t g = 0;  // the block's running phase number
     for (int64_t p = blockIdx.x; p < pv.n_patches; p += gridDim.x) {
         const int64_t nb = pv.patch_node_ptr[p];
         const int nown = (int)(pv.patch_node_ptr[p + 1] - nb);
@@ -668,40 +681,51 @@ __global__ void __launch_bounds__(256) k_vjp_gather(PlanView pv, const T *__rest
             int mycol = -1;
             int own[NPE];
             T v[NPE][3];
+#pragma unroll
+            for (int a = 0; a < NPE; ++a) own[a] = -1;
             if (i < nel) {
                 const int64_t ci = eb + i;
                 mycol = pv.celem_color[ci];
                 const int64_t e = pv.celem_id[ci];
                 const T *src = dxe + e * (NPE * 3);
+                uint16_t ln[NPE];
+                load_lnodes<NPE>(pv.celem_lnode, ci, ln);
 #pragma unroll
                 for (int a = 0; a < NPE; ++a) {
-                    own[a] = cown[pv.celem_lnode[ci * NPE + a]];
+                    own[a] = cown[ln[a]];
 #pragma unroll
-                    for (int j = 0; j < 3; ++j) v[a][j] = own[a] >= 0 ? src[3 * a + j] : T(0);
+                    for (int j = 0; j < 3; ++j) v[a][j] = own[a] >= 0 ? __ldg(src + 3 * a + j) : T(0);
                 }
             }
             const int last = min(base + nthr, nel) - 1;
             const int c0 = pv.celem_color[eb + base], c1 = pv.celem_color[eb + last];
-            for (int cc = c0; cc <= c1; ++cc) {
-                if (mycol == cc) {
+            for (int cc = c0; cc <= c1; ++cc, ++g) {
+                const bool mine = mycol == cc;
+                if (__any_sync(0xffffffffu, mine)) {
+                    if (g > 0) phase_wait(mb, g - 1, wc);
+                    if (mine) {
 #pragma unroll
-                    for (int a = 0; a < NPE; ++a) {
-                        const int o = own[a];
-                        if (o >= 0) {
-                            dxs[o][0] += v[a][0];
-                            dxs[o][1] += v[a][1];
-                            dxs[o][2] += v[a][2];
+                        for (int a = 0; a < NPE; ++a) {
+                            const int o = own[a];
+                            if (o >= 0) {
+                                dxs[o][0] += v[a][0];
+                                dxs[o][1] += v[a][1];
+                                dxs[o][2] += v[a][2];
+                            }
                         }
                     }
+                    __syncwarp();
                 }
-                __syncthreads();
+                if (g >= (uint32_t)PHASE_RING) phase_wait(mb, g - PHASE_RING, wc);
+                if (lane == 0) phase_arrive(mb, g);
             }
         }
+        __syncthreads();  // every phase of the patch done
         for (int k = tid; k < nown; k += nthr) {
-            const int64_t g = pv.own_row[nb + k];
-            dX[3 * g + 0] = dxs[k][0];
-            dX[3 * g + 1] = dxs[k][1];
-            dX[3 * g + 2] = dxs[k][2];
+            const int64_t gr = pv.own_row[nb + k];
+            dX[3 * gr + 0] = dxs[k][0];
+            dX[3 * gr + 1] = dxs[k][1];
+            dX[3 * gr + 2] = dxs[k][2];
         }
         __syncthreads();
     }
@@ -739,15 +763,16 @@ static fem_status launch_vjp_elem_t(fem_mesh m, const Closure &cl, const void *X
                                     void *dxe, void *dc, cudaStream_t s) {
     const Plan &P = m->plan;
     const ElemSmem L = elem_smem(P, cl, sizeof(S));
-    auto f = k_vjp_elem<NPE, T, S, CT>;
+    auto f = m->opt.operator_kind == 1 ? k_vjp_elem<NPE, T, S, CT, true> : k_vjp_elem<NPE, T, S, CT, false>;
     FEM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
     const int64_t np = cl.p1 - cl.p0;
     if (np <= 0) return FEM_OK;
     fem_status st;
-    const int grid = grid_for((const void *)f, 256, L.total, np, "backward element kernel", &st);
+    constexpr int nt = vjp_elem_threads<T>();
+    const int grid = grid_for((const void *)f, nt, L.total, np, "backward element kernel", &st);
     if (st != FEM_OK) return st;
-    f<<<grid, 256, L.total, s>>>(P.view(cl), m->rowptr.ptr, (const S *)X, (const CT *)c, (const T *)G, (T *)dxe,
-                                 (T *)dc, L, m->opt.operator_kind == 1);
+    f<<<grid, nt, L.total, s>>>(P.view(cl), m->rowptr.ptr, (const S *)X, (const CT *)c, (const T *)G,
+                                              (T *)dxe, (T *)dc, L);
     FEM_LAUNCHED("k_vjp_elem");
     return FEM_OK;
 }
@@ -769,7 +794,8 @@ static fem_status launch_gather_t(fem_mesh m, const Closure &cl, const void *dxe
     fem_status st;
     const int grid = grid_for((const void *)f, 256, L.total, np, "backward gather kernel", &st);
     if (st != FEM_OK) return st;
-    f<<<grid, 256, L.total, s>>>(P.view(cl), (const T *)dxe, (T *)dX, L);
+    const WaitCtl wc{m->status.ptr, m->opt.wait_spins > 0 ? m->opt.wait_spins : WAIT_SPINS_DEFAULT, 0};
+    f<<<grid, 256, L.total, s>>>(P.view(cl), (const T *)dxe, (T *)dX, L, wc);
     FEM_LAUNCHED("k_vjp_gather");
     return FEM_OK;
 }
