@@ -558,7 +558,8 @@ def other_workloads(flush, stream):
 def backward_workloads(timed, dev):
     """The backward pass (fem_vjp: dL/dX and dL/dc of L = sum over stored entries
     G_ij K_ij) on the 1M-brick mesh, for the stiffness operator in both precisions
-    and for the elasticity operator in mixed precision; G is a seeded standard
+    and for the elasticity operator in mixed precision, and on the 3.07M-tet mesh
+    for the stiffness operator in mixed precision; G is a seeded standard
     normal upstream on K's pattern.  Algorithmic bytes: X, E, c and G read once,
     dX and dc written once."""
     import numpy as np
@@ -567,21 +568,22 @@ def backward_workloads(timed, dev):
     import meshgen
     from paper_1501_04784_gb300 import fem
 
-    m = meshgen.config_mesh(1)
     res = {}
-    for op, key in ((0, "stiffness"), (2, "elasticity")):
+    for op, key, idx in ((0, "stiffness", 1), (2, "elasticity", 1), (0, "stiffness_tet", 2)):
+        m = meshgen.config_mesh(idx)
         mesh = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), operator_kind=op)
         nnz = mesh.pattern()
         c = meshgen.lame(m) if op == 2 else m.c
         G = np.random.default_rng(21).standard_normal(nnz)
-        r = {"workload": "1M-hex8 " + key + " backward (dL/dX, dL/dc)", "nnz": nnz}
-        for prec in (("mixed", "fp64") if op == 0 else ("mixed",)):
+        name = "1M-hex8 " if idx == 1 else "3.07M-tet4 "
+        r = {"workload": name + key.split("_")[0] + " backward (dL/dX, dL/dc)", "nnz": nnz}
+        for prec in (("mixed", "fp64") if key == "stiffness" else ("mixed",)):
             dt = torch.float32 if prec == "mixed" else torch.float64
             w = 4 if prec == "mixed" else 8
             X, cd, Gd = dev(m.X, dt), dev(c, dt), dev(G, dt)
             t = timed(lambda: mesh.vjp(X, cd, Gd, prec), 10)
             mesh.sync()
-            nb = (m.n_nodes * 3 * w * 2 + m.n_elems * 8 * 4 + cd.numel() * w * 2 + nnz * w)
+            nb = (m.n_nodes * 3 * w * 2 + m.n_elems * m.npe * 4 + cd.numel() * w * 2 + nnz * w)
             r[prec] = {"value": m.n_elems / (t / 1e3), "unit": "elements/s", "ms_per_step": t,
                        "algorithmic_bytes": nb, "achieved_gbs": nb / (t / 1e3) / 1e9}
             del X, cd, Gd

@@ -206,47 +206,48 @@ __device__ __forceinline__ void elastic_tet_vjp(const S (*xc)[3], T lam, T mu, c
 // larger global id) of length L gives DOF row 3R + r at 9 rowptr[R] - 3R +
 // r 3 (L - 1) + r (r + 1) / 2; node column C at in-row position p gives DOF
 // columns 3p + j (C != R) or 3 (L - 1) + j (the diagonal block, j <= r).
+// db[j] = 9 rowptr[g] - 3 g and rl[j] = the node row length of closure node j
+// (closure-local indices ascend with the global id).
 template <int NPE, typename T>
-__device__ __forceinline__ void load_upstream(const T *__restrict__ G, const int64_t *__restrict__ rowptr,
-                                              const uint8_t *pos, const int32_t *gid, const uint16_t (&ln)[NPE],
-                                              int a, T (&W)[elastic_nblk<NPE>()][9]) {
-    int32_t ga = gid[ln[0]];
+__device__ __forceinline__ void load_upstream(const T *__restrict__ G, const uint8_t *pos, const int64_t *db,
+                                              const int32_t *rl, const uint16_t (&ln)[NPE], int a,
+                                              T (&W)[elastic_nblk<NPE>()][9]) {
+    int la = ln[0];
 #pragma unroll
     for (int k = 1; k < NPE; ++k)
-        if (a == k) ga = gid[ln[k]];
+        if (a == k) la = ln[k];
 #pragma unroll
     for (int m = 0; m < elastic_nblk<NPE>(); ++m) {
 #pragma unroll
         for (int n = 0; n < 9; ++n) W[m][n] = T(0);
         if (!blk_valid<NPE>(a, m)) continue;
         const int b = blk_node<NPE>(a, m);
-        int32_t gb = gid[ln[0]];
+        int lb = ln[0];
 #pragma unroll
         for (int k = 1; k < NPE; ++k)
-            if (b == k) gb = gid[ln[k]];
+            if (b == k) lb = ln[k];
         const int A = a > b ? a : b, B = a > b ? b : a;
         const int q = A * (A + 1) / 2 + B;
-        const int64_t R = ga > gb ? ga : gb;
-        const int64_t r0 = rowptr[R];
-        const int L = (int)(rowptr[R + 1] - r0);
-        const int64_t base = 9 * r0 - 3 * R;
+        const int lr = la > lb ? la : lb;
+        const int64_t base = db[lr];
+        const int L = rl[lr];
         if (a == b) {
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
                 for (int j = 0; j <= i; ++j) {
-                    const T v = G[base + i * 3 * (L - 1) + i * (i + 1) / 2 + 3 * (L - 1) + j];
+                    const T v = __ldg(G + base + i * 3 * (L - 1) + i * (i + 1) / 2 + 3 * (L - 1) + j);
                     W[m][3 * i + j] = i == j ? v : T(0.5) * v;
                     W[m][3 * j + i] = W[m][3 * i + j];
                 }
         } else {
             const int p = pos[q];
-            const bool row_a = ga > gb;  // else the block is stored transposed, in row b
+            const bool row_a = la > lb;  // else the block is stored transposed, in row b
 #pragma unroll
             for (int r = 0; r < 3; ++r)
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
-                    const T v = T(0.5) * G[base + r * 3 * (L - 1) + r * (r + 1) / 2 + 3 * p + j];
+                    const T v = T(0.5) * __ldg(G + base + r * 3 * (L - 1) + r * (r + 1) / 2 + 3 * p + j);
                     if (row_a) W[m][3 * r + j] = v; else W[m][3 * j + r] = v;
                 }
         }
@@ -254,16 +255,17 @@ __device__ __forceinline__ void load_upstream(const T *__restrict__ G, const int
 }
 
 struct ElVjpSmem {
-    size_t xs, cown, gid, dxs, total;  // dxs: owned-node accumulators (fused) or the
-                                       // compacted element list (staged)
+    size_t xs, cown, db, rl, dxs, total;  // dxs: owned-node accumulators (fused) or the
+                                          // compacted element list (staged)
 };
 
 // One element of a closure on its NPE lanes (all lanes of the warp call it: the
 // brick shuffles): lane a gets dx_a, and dlam, dmu summed over the element.
 template <int NPE, typename T, typename S, typename CT>
-__device__ __forceinline__ void elastic_element_vjp(const PlanView &pv, const int64_t *__restrict__ rowptr,
-                                                    const CT *__restrict__ c, const T *__restrict__ G,
-                                                    const S (*xs)[3], const int32_t *gid, int pos_stride,
+__device__ __forceinline__ void elastic_element_vjp(const PlanView &pv, const CT *__restrict__ c,
+                                                    const T *__restrict__ G,
+                                                    const S (*xs)[3], const int64_t *db, const int32_t *rl,
+                                                    int pos_stride,
                                                     bool act, int64_t ci, int a, uint16_t (&ln)[NPE], int64_t &e,
                                                     T (&dx)[3], T &dlam, T &dmu) {
     S xc[NPE][3];
@@ -276,7 +278,7 @@ __device__ __forceinline__ void elastic_element_vjp(const PlanView &pv, const in
         for (int k = 0; k < NPE; ++k) ln[k] = pv.celem_lnode[ci * NPE + k];
         lam = T(c[2 * e]);
         mu = T(c[2 * e + 1]);
-        load_upstream<NPE, T>(G, rowptr, pv.celem_pos + ci * pos_stride, gid, ln, a, W);
+        load_upstream<NPE, T>(G, pv.celem_pos + ci * pos_stride, db, rl, ln, a, W);
     } else {
 #pragma unroll
         for (int k = 0; k < NPE; ++k) ln[k] = 0;
@@ -296,11 +298,14 @@ __device__ __forceinline__ void elastic_element_vjp(const PlanView &pv, const in
 }
 
 template <typename S>
-__device__ __forceinline__ void load_cnodes(const PlanView &pv, int64_t cb, int ncn, const S *__restrict__ X,
-                                            S (*xs)[3], int32_t *cown, int32_t *gid) {
+__device__ __forceinline__ void load_cnodes(const PlanView &pv, const int64_t *__restrict__ rowptr, int64_t cb,
+                                            int ncn, const S *__restrict__ X, S (*xs)[3], int32_t *cown, int64_t *db,
+                                            int32_t *rl) {
     for (int j = threadIdx.x; j < ncn; j += blockDim.x) {
         const int32_t g = pv.cnode_gid[cb + j];
-        gid[j] = g;
+        const int64_t r0 = rowptr[g];
+        db[j] = 9 * r0 - 3 * (int64_t)g;
+        rl[j] = (int)(rowptr[g + 1] - r0);
         cown[j] = pv.cnode_own[cb + j];
         xs[j][0] = X[3 * (int64_t)g + 0];
         xs[j][1] = X[3 * (int64_t)g + 1];
@@ -316,7 +321,8 @@ __global__ void __launch_bounds__(256) k_elastic_vjp(PlanView pv, const int64_t 
     extern __shared__ __align__(16) unsigned char evjp_smem[];
     S(*xs)[3] = reinterpret_cast<S(*)[3]>(evjp_smem + L.xs);
     int32_t *cown = reinterpret_cast<int32_t *>(evjp_smem + L.cown);
-    int32_t *gid = reinterpret_cast<int32_t *>(evjp_smem + L.gid);
+    int64_t *db = reinterpret_cast<int64_t *>(evjp_smem + L.db);
+    int32_t *rl = reinterpret_cast<int32_t *>(evjp_smem + L.rl);
     T(*dxs)[3] = reinterpret_cast<T(*)[3]>(evjp_smem + L.dxs);
     const int tid = threadIdx.x, nthr = blockDim.x, a = tid % NPE, epb = nthr / NPE;
     for (int64_t p = blockIdx.x; p < pv.n_patches; p += gridDim.x) {
@@ -326,7 +332,7 @@ __global__ void __launch_bounds__(256) k_elastic_vjp(PlanView pv, const int64_t 
         const int ncn = (int)(pv.patch_cnode_ptr[p + 1] - cb);
         const int64_t eb = pv.patch_elem_ptr[p];
         const int nel = (int)(pv.patch_elem_ptr[p + 1] - eb);
-        load_cnodes<S>(pv, cb, ncn, X, xs, cown, gid);
+        load_cnodes<S>(pv, rowptr, cb, ncn, X, xs, cown, db, rl);
         for (int k = tid; k < nown; k += nthr) dxs[k][0] = dxs[k][1] = dxs[k][2] = T(0);
         __syncthreads();
         // the loop bound is uniform over the block: every lane takes part in the
@@ -339,7 +345,7 @@ __global__ void __launch_bounds__(256) k_elastic_vjp(PlanView pv, const int64_t 
             uint16_t ln[NPE];
             int64_t e;
             T dx[3], dlam, dmu;
-            elastic_element_vjp<NPE, T, S, CT>(pv, rowptr, c, G, xs, gid, pos_stride, act, ci, a, ln, e, dx, dlam,
+            elastic_element_vjp<NPE, T, S, CT>(pv, c, G, xs, db, rl, pos_stride, act, ci, a, ln, e, dx, dlam,
                                                dmu);
             uint16_t lna = ln[0];
 #pragma unroll
@@ -386,7 +392,8 @@ __global__ void __launch_bounds__(256) k_elastic_vjp_elem(PlanView pv, const int
     __shared__ int n_prim;
     S(*xs)[3] = reinterpret_cast<S(*)[3]>(evje_smem + L.xs);
     int32_t *cown = reinterpret_cast<int32_t *>(evje_smem + L.cown);
-    int32_t *gid = reinterpret_cast<int32_t *>(evje_smem + L.gid);
+    int64_t *db = reinterpret_cast<int64_t *>(evje_smem + L.db);
+    int32_t *rl = reinterpret_cast<int32_t *>(evje_smem + L.rl);
     int32_t *list = reinterpret_cast<int32_t *>(evje_smem + L.dxs);
     const int tid = threadIdx.x, nthr = blockDim.x, a = tid % NPE, epb = nthr / NPE;
     for (int64_t p = blockIdx.x; p < pv.n_patches; p += gridDim.x) {
@@ -394,11 +401,19 @@ __global__ void __launch_bounds__(256) k_elastic_vjp_elem(PlanView pv, const int
         const int ncn = (int)(pv.patch_cnode_ptr[p + 1] - cb);
         const int64_t eb = pv.patch_elem_ptr[p];
         const int nel = (int)(pv.patch_elem_ptr[p + 1] - eb);
-        load_cnodes<S>(pv, cb, ncn, X, xs, cown, gid);
+        load_cnodes<S>(pv, rowptr, cb, ncn, X, xs, cown, db, rl);
         if (tid == 0) n_prim = 0;
         __syncthreads();
-        for (int j = tid; j < nel; j += nthr)
-            if (cown[pv.celem_lnode[(eb + j) * NPE]] >= 0) list[atomicAdd(&n_prim, 1)] = j;
+        // compaction with one counter update per warp (see k_vjp_elem)
+        for (int j0 = 0; j0 < nel; j0 += nthr) {
+            const int j = j0 + tid, lane = tid & 31;
+            const bool f = j < nel && cown[pv.celem_lnode[(eb + j) * NPE]] >= 0;
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            int w0 = 0;
+            if (lane == 0 && bal) w0 = atomicAdd(&n_prim, __popc(bal));
+            w0 = __shfl_sync(0xffffffffu, w0, 0);
+            if (f) list[w0 + __popc(bal & ((1u << lane) - 1u))] = j;
+        }
         __syncthreads();
         const int np = n_prim;
         for (int base = 0; base < np; base += epb) {  // uniform bound: see k_elastic_vjp
@@ -408,7 +423,7 @@ __global__ void __launch_bounds__(256) k_elastic_vjp_elem(PlanView pv, const int
             uint16_t ln[NPE];
             int64_t e;
             T dx[3], dlam, dmu;
-            elastic_element_vjp<NPE, T, S, CT>(pv, rowptr, c, G, xs, gid, pos_stride, act, ci, a, ln, e, dx, dlam,
+            elastic_element_vjp<NPE, T, S, CT>(pv, c, G, xs, db, rl, pos_stride, act, ci, a, ln, e, dx, dlam,
                                                dmu);
             if (act) {
                 T *o = dxe + e * (NPE * 3) + 3 * a;
@@ -441,7 +456,9 @@ static fem_status launch_elastic_vjp_t(fem_mesh m, const Closure &cl, const void
     o = ev_a16(o + (size_t)P.max_cnodes * 3 * sizeof(S));
     L.cown = o;
     o = ev_a16(o + (size_t)P.max_cnodes * 4);
-    L.gid = o;
+    L.db = o;
+    o = ev_a16(o + (size_t)P.max_cnodes * 8);
+    L.rl = o;
     o = ev_a16(o + (size_t)P.max_cnodes * 4);
     L.dxs = o;
     o = ev_a16(o + (staged ? (size_t)std::max<int64_t>(cl.max_celems, P.max_celems) * 4

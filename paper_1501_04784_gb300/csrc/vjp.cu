@@ -545,7 +545,7 @@ static fem_status launch_vjp_t(fem_mesh m, const Closure &cl, const void *X, con
 // once instead of once per patch whose closure holds the element.
 
 struct ElemSmem {
-    size_t xs, cown, gid, list, total;
+    size_t xs, cown, rp, list, total;  // rp: rowptr of each closure node
 };
 
 template <typename T, int N>
@@ -567,8 +567,18 @@ __device__ __forceinline__ int primary_elems(const PlanView &pv, int npe, int64_
                                              int32_t *list, int *count) {
     if (threadIdx.x == 0) *count = 0;
     __syncthreads();
-    for (int j = threadIdx.x; j < nel; j += blockDim.x)
-        if (cown[pv.celem_lnode[(eb + j) * npe]] >= 0) list[atomicAdd(count, 1)] = j;
+    // one counter update per warp (ballot), not per element: same-address shared
+    // atomics serialise; the loop bound is warp-uniform
+    const int lane = threadIdx.x & 31;
+    for (int j0 = 0; j0 < nel; j0 += blockDim.x) {
+        const int j = j0 + threadIdx.x;
+        const bool f = j < nel && cown[pv.celem_lnode[(eb + j) * npe]] >= 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        int w0 = 0;
+        if (lane == 0 && bal) w0 = atomicAdd(count, __popc(bal));
+        w0 = __shfl_sync(0xffffffffu, w0, 0);
+        if (f) list[w0 + __popc(bal & ((1u << lane) - 1u))] = j;
+    }
     __syncthreads();
     return *count;
 }
@@ -589,7 +599,7 @@ __global__ void __launch_bounds__(256) k_vjp_elem(PlanView pv, const int64_t *__
     __shared__ int n_prim;
     S(*xs)[3] = reinterpret_cast<S(*)[3]>(vel_smem + L.xs);
     int32_t *cown = reinterpret_cast<int32_t *>(vel_smem + L.cown);
-    int32_t *gid = reinterpret_cast<int32_t *>(vel_smem + L.gid);
+    int64_t *rp = reinterpret_cast<int64_t *>(vel_smem + L.rp);
     int32_t *list = reinterpret_cast<int32_t *>(vel_smem + L.list);
     const int tid = threadIdx.x, nthr = blockDim.x;
     for (int64_t p = blockIdx.x; p < pv.n_patches; p += gridDim.x) {
@@ -599,7 +609,7 @@ __global__ void __launch_bounds__(256) k_vjp_elem(PlanView pv, const int64_t *__
         const int nel = (int)(pv.patch_elem_ptr[p + 1] - eb);
         for (int j = tid; j < ncn; j += nthr) {
             const int32_t g = pv.cnode_gid[cb + j];
-            gid[j] = g;
+            rp[j] = rowptr[g];
             cown[j] = pv.cnode_own[cb + j];
             xs[j][0] = X[3 * (int64_t)g + 0];
             xs[j][1] = X[3 * (int64_t)g + 1];
@@ -619,15 +629,24 @@ __global__ void __launch_bounds__(256) k_vjp_elem(PlanView pv, const int64_t *__
                 xc[a][1] = xs[ln[a]][1];
                 xc[a][2] = xs[ln[a]][2];
             }
+            // the pair's row is its node with the larger global id (closure-local
+            // indices ascend with it); positions read as 32-bit words
+            constexpr int NW = (NP + 3) / 4;
+            uint32_t pw[NW];
+            const uint32_t *pp = reinterpret_cast<const uint32_t *>(pv.celem_pos + ci * (NW * 4));
+#pragma unroll
+            for (int w = 0; w < NW; ++w) pw[w] = __ldg(pp + w);
+            int64_t rb[NPE];
+#pragma unroll
+            for (int a = 0; a < NPE; ++a) rb[a] = rp[ln[a]];
             T Sp[NP];
-            const uint8_t *pp = pv.celem_pos + ci * ((NP + 3) / 4 * 4);
 #pragma unroll
             for (int a = 0; a < NPE; ++a)
 #pragma unroll
                 for (int b = 0; b <= a; ++b) {
                     const int q = a * (a + 1) / 2 + b;
-                    const int32_t r = gid[ln[a] > ln[b] ? ln[a] : ln[b]];
-                    Sp[q] = G[rowptr[r] + pp[q]];
+                    const int64_t r0 = ln[a] > ln[b] ? rb[a] : rb[b];
+                    Sp[q] = __ldg(G + r0 + ((pw[q >> 2] >> (8 * (q & 3))) & 0xff));
                 }
             T dx[NPE][3], dcv;
             if constexpr (MASS) {
@@ -750,8 +769,8 @@ ElemSmem elem_smem(const Plan &P, const Closure &cl, size_t xsize) {
     o = a16(o + (size_t)P.max_cnodes * 3 * xsize);
     L.cown = o;
     o = a16(o + (size_t)P.max_cnodes * 4);
-    L.gid = o;
-    o = a16(o + (size_t)P.max_cnodes * 4);
+    L.rp = o;
+    o = a16(o + (size_t)P.max_cnodes * 8);
     L.list = o;
     o = a16(o + (size_t)std::max<int64_t>(cl.max_celems, P.max_celems) * 4);
     L.total = o;
