@@ -501,7 +501,7 @@ def other_workloads(flush, stream):
     """The batched and the large workload beside the headline (mixed precision, pattern
     cached, L2 flushed before every timed build): 512 uneven brick meshes in one
     persistent launch replayed from a CUDA graph, and 300^3 bricks built in patch
-    groups under a 16 GB library budget."""
+    groups under a 16 GB library budget, with its backward pass."""
     import numpy as np
     import torch
 
@@ -548,8 +548,14 @@ def other_workloads(flush, stream):
     out["large"] = {"workload": "300^3 bricks (27M elements), 16 GB library budget", "value": m.n_elems / (t / 1e3),
                     "unit": "elements/s", "ms_per_step": t, "patch_groups": info["n_groups"],
                     "plan_bytes": info["plan_bytes"]}
+    # its backward: dL/dX (FP32) and dL/dc of L = sum G_ij K_ij, G seeded standard normal
+    G = torch.randn(nnz, generator=torch.Generator(device="cuda").manual_seed(21), device="cuda")
+    tb = timed(lambda: mesh.vjp(X, c, G, "mixed"), 3)
+    mesh.sync()
+    out["large"]["backward"] = {"value": m.n_elems / (tb / 1e3), "unit": "elements/s", "ms_per_step": tb,
+                                "library_bytes": mesh.info()["live_bytes"]}
     mesh.close()
-    del mesh, X, c, v
+    del mesh, X, c, v, G
     out["elastic"] = elastic_workloads(timed, dev)
     out["backward"] = backward_workloads(timed, dev)
     return out
