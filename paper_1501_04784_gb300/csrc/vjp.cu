@@ -10,7 +10,9 @@
 //     dL/dJ_q = c_e (<M_q, H_q> I - 2 M_q H_q) A^T,
 // (from d|det J| = |det J| tr(A dJ) and dA = -A dJ A), and because
 // J = dN X_e, dL/dX_e = sum_q dN_q^T dL/dJ_q.  J, det J, A and B are recomputed
-// here from X; nothing is stored by the forward pass.
+// here from X; nothing is stored by the forward pass.  The brick computes this
+// gradient by reverse mode through the forward's own factorised steps
+// (brick_vjp below); the tetrahedron evaluates it directly.
 //
 // The mass operator (M_ab = c sum_q |det J_q| N_a(q) N_b(q)) has
 // L_e = c sum_q |det J_q| phi_q with phi_q = N_q^T Ssym N_q, hence dL/dc_e =
@@ -21,7 +23,10 @@
 // visits its closure elements colour by colour and adds each element's node
 // gradients into shared-memory accumulators of its owned nodes, then writes
 // dX of every owned node once; dc_e is written by the patch that owns the
-// element's first node.  No atomics; bitwise reproducible.
+// element's first node.  No atomics on values; bitwise reproducible.  By default
+// the pass is staged (k_vjp_elem: every element once, node gradients to library
+// memory; k_vjp_gather: the colour-ordered adds); the fused kernel k_vjp
+// recomputes an element in every closure that holds it and needs no memory.
 #include "element.cuh"
 #include "mesh.cuh"
 #include "phases.cuh"
