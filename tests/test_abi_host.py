@@ -66,3 +66,34 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(abi, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         abi.load()
+
+
+def test_struct_mirrors_match_the_header(tmp_path):
+    """The binding's ctypes mirrors of fem_options, fem_info and fem_tuning have
+    the C structs' size and every field's offset (a C program compiled against
+    include/fem.h prints them)."""
+    import shutil
+    import subprocess
+    from paper_1501_04784_gb300 import abi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [("fem_options", abi.fem_options), ("fem_info", abi.fem_info), ("fem_tuning", abi.fem_tuning)]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "fem.h"', "int main(void) {"]
+    for cname, py in structs:
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        s, f, v = line.split()
+        got[(s, f)] = int(v)
+    for cname, py in structs:
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
