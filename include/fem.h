@@ -58,8 +58,9 @@ typedef enum {
     FEM_ERR_INDEX = 2,       /* a node id in E outside [0, n_nodes); in the bounds-check build,
                                 also an out-of-range index met inside a patch kernel */
     FEM_ERR_DEGENERATE = 3,  /* a node repeated within one element (fem_mesh_create), or an
-                                element matrix that is not finite: zero volume, non-finite
-                                input (reported by fem_sync after the build) */
+                                element matrix (build) or element gradient (fem_vjp) that is
+                                not finite: zero volume, non-finite input (reported by
+                                fem_sync after the call) */
     FEM_ERR_OOM = 4,         /* a device allocation failed */
     FEM_ERR_BUDGET = 5,      /* the memory budget cannot hold the smallest unit of work */
     FEM_ERR_CUDA = 6,        /* a CUDA runtime call or kernel failed */
@@ -335,11 +336,12 @@ fem_status fem_autotune(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype
 fem_status fem_set_tuning(fem_mesh m, int patch_entries, int block_threads, void *stream);
 
 /* Wait for the mesh's work on `stream` and report any asynchronous error:
- * FEM_ERR_CUDA for a CUDA error; FEM_ERR_DEGENERATE if a build since the last
- * fem_sync met an element matrix that is not finite (an element of zero volume,
- * or non-finite coordinates or coefficients); FEM_ERR_TIMEOUT if a bounded
- * device-side wait of a build gave up.  The values of that build are undefined;
- * the context stays usable and the status is cleared. */
+ * FEM_ERR_CUDA for a CUDA error; FEM_ERR_DEGENERATE if a build or backward pass
+ * since the last fem_sync met an element matrix or element gradient that is not
+ * finite (an element of zero volume, or non-finite coordinates, coefficients or
+ * upstream values); FEM_ERR_TIMEOUT if a bounded device-side wait gave up.  The
+ * values of that call are undefined; the context stays usable and the status
+ * is cleared. */
 fem_status fem_sync(fem_mesh m, void *stream);
 
 /* Sizes and plan statistics of the mesh (after fem_pattern for the plan fields). */

@@ -96,8 +96,9 @@ fem_status check_status(fem_mesh m, cudaStream_t s) {
         return FEM_ERR_INDEX;
     }
     if (h & STATUS_NONFINITE) {
-        set_error("an element matrix was not finite (an element with a zero Jacobian determinant, or non-finite "
-                  "coordinates or coefficients); the values of that build are undefined");
+        set_error("an element matrix or element gradient was not finite (an element with a zero Jacobian "
+                  "determinant, or non-finite coordinates, coefficients or upstream values); the values of that "
+                  "call are undefined");
         return FEM_ERR_DEGENERATE;
     }
     set_error("a device-side wait of a patch kernel gave up after %d polls; the values of that build are undefined",

@@ -317,7 +317,8 @@ template <int NPE, typename T, typename S, typename CT>
 __global__ void __launch_bounds__(256) k_elastic_vjp(PlanView pv, const int64_t *__restrict__ rowptr,
                                                      const S *__restrict__ X, const CT *__restrict__ c,
                                                      const T *__restrict__ G, T *__restrict__ dX,
-                                                     T *__restrict__ dcout, int pos_stride, ElVjpSmem L) {
+                                                     T *__restrict__ dcout, int pos_stride, ElVjpSmem L,
+                                                     int *status) {
     extern __shared__ __align__(16) unsigned char evjp_smem[];
     S(*xs)[3] = reinterpret_cast<S(*)[3]>(evjp_smem + L.xs);
     int32_t *cown = reinterpret_cast<int32_t *>(evjp_smem + L.cown);
@@ -354,6 +355,7 @@ __global__ void __launch_bounds__(256) k_elastic_vjp(PlanView pv, const int64_t 
             if (act && a == 0 && cown[ln[0]] >= 0) {
                 dcout[2 * e] = dlam;
                 dcout[2 * e + 1] = dmu;
+                if (!isfinite(dlam) || !isfinite(dmu)) atomicOr(status, STATUS_NONFINITE);  // e.g. zero det J
             }
             const int last = min(base + epb, nel) - 1;
             const int c0 = pv.celem_color[eb + base], c1 = pv.celem_color[eb + last];
@@ -387,7 +389,8 @@ template <int NPE, typename T, typename S, typename CT>
 __global__ void __launch_bounds__(256) k_elastic_vjp_elem(PlanView pv, const int64_t *__restrict__ rowptr,
                                                           const S *__restrict__ X, const CT *__restrict__ c,
                                                           const T *__restrict__ G, T *__restrict__ dxe,
-                                                          T *__restrict__ dcout, int pos_stride, ElVjpSmem L) {
+                                                          T *__restrict__ dcout, int pos_stride, ElVjpSmem L,
+                                                     int *status) {
     extern __shared__ __align__(16) unsigned char evje_smem[];
     __shared__ int n_prim;
     S(*xs)[3] = reinterpret_cast<S(*)[3]>(evje_smem + L.xs);
@@ -433,6 +436,7 @@ __global__ void __launch_bounds__(256) k_elastic_vjp_elem(PlanView pv, const int
                 if (a == 0) {
                     dcout[2 * e] = dlam;
                     dcout[2 * e + 1] = dmu;
+                    if (!isfinite(dlam) || !isfinite(dmu)) atomicOr(status, STATUS_NONFINITE);  // e.g. zero det J
                 }
             }
         }
@@ -476,7 +480,7 @@ static fem_status launch_elastic_vjp_t(fem_mesh m, const Closure &cl, const void
     if (np <= 0) return FEM_OK;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np, (int64_t)num_sms() * per_sm));
     f<<<grid, 256, L.total, s>>>(P.view(cl), m->rowptr.ptr, (const S *)X, (const CT *)c, (const T *)G,
-                                 (T *)(staged ? dxe : dX), (T *)dc, P.pos_stride, L);
+                                 (T *)(staged ? dxe : dX), (T *)dc, P.pos_stride, L, m->status.ptr);
     FEM_LAUNCHED(staged ? "k_elastic_vjp_elem" : "k_elastic_vjp");
     return FEM_OK;
 }

@@ -416,7 +416,7 @@ template <int NPE, typename T, typename S, typename CT, bool MASS>
 __global__ void __launch_bounds__(256) k_vjp(PlanView pv, const int64_t *__restrict__ rowptr,
                                              const S *__restrict__ X, const CT *__restrict__ c,
                                              const T *__restrict__ G, T *__restrict__ dX, T *__restrict__ dcout,
-                                             VjpSmem L) {
+                                             VjpSmem L, int *status) {
     constexpr int NP = NPE * (NPE + 1) / 2;
     extern __shared__ __align__(16) unsigned char vjp_smem[];
     S(*xs)[3] = reinterpret_cast<S(*)[3]>(vjp_smem + L.xs);
@@ -478,7 +478,10 @@ __global__ void __launch_bounds__(256) k_vjp(PlanView pv, const int64_t *__restr
                     if constexpr (NPE == 8) brick_vjp<T, S>(xc, (T)c[e], Sp, dx, dcv);
                     else tet_vjp<T, S>(xc, (T)c[e], Sp, dx, dcv);
                 }
-                if (cown[ln[0]] >= 0) dcout[e] = dcv;
+                if (cown[ln[0]] >= 0) {
+                    dcout[e] = dcv;
+                    if (!isfinite(dcv)) atomicOr(status, STATUS_NONFINITE);  // e.g. zero det J
+                }
             }
             const int last = min(base + nthr, nel) - 1;
             const int c0 = pv.celem_color[eb + base], c1 = pv.celem_color[eb + last];
@@ -536,7 +539,7 @@ static fem_status launch_vjp_t(fem_mesh m, const Closure &cl, const void *X, con
     if (np <= 0) return FEM_OK;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np, (int64_t)num_sms() * per_sm));
     f<<<grid, 256, L.total, s>>>(P.view(cl), m->rowptr.ptr, (const S *)X, (const CT *)c, (const T *)G, (T *)dX,
-                                 (T *)dc, L);
+                                 (T *)dc, L, m->status.ptr);
     FEM_LAUNCHED("k_vjp");
     return FEM_OK;
 }
@@ -598,7 +601,7 @@ template <int NPE, typename T, typename S, typename CT, bool MASS>
 __global__ void __launch_bounds__(256) k_vjp_elem(PlanView pv, const int64_t *__restrict__ rowptr,
                                                   const S *__restrict__ X, const CT *__restrict__ c,
                                                   const T *__restrict__ G, T *__restrict__ dxe,
-                                                  T *__restrict__ dcout, ElemSmem L) {
+                                                  T *__restrict__ dcout, ElemSmem L, int *status) {
     constexpr int NP = NPE * (NPE + 1) / 2;
     extern __shared__ __align__(16) unsigned char vel_smem[];
     __shared__ int n_prim;
@@ -668,6 +671,7 @@ __global__ void __launch_bounds__(256) k_vjp_elem(PlanView pv, const int64_t *__
                 for (int j = 0; j < 3; ++j) flat[3 * a + j] = dx[a][j];
             store_row<T, NPE * 3>(dxe + e * (NPE * 3), flat);
             dcout[e] = dcv;
+            if (!isfinite(dcv)) atomicOr(status, STATUS_NONFINITE);  // e.g. zero det J
         }
         __syncthreads();
     }
@@ -796,7 +800,7 @@ static fem_status launch_vjp_elem_t(fem_mesh m, const Closure &cl, const void *X
     const int grid = grid_for((const void *)f, nt, L.total, np, "backward element kernel", &st);
     if (st != FEM_OK) return st;
     f<<<grid, nt, L.total, s>>>(P.view(cl), m->rowptr.ptr, (const S *)X, (const CT *)c, (const T *)G,
-                                              (T *)dxe, (T *)dc, L);
+                                              (T *)dxe, (T *)dc, L, m->status.ptr);
     FEM_LAUNCHED("k_vjp_elem");
     return FEM_OK;
 }

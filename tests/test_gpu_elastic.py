@@ -214,6 +214,12 @@ def test_elastic_zero_volume_element_is_reported(fem, prec):
     with pytest.raises(abi.FemError, match="FEM_ERR_DEGENERATE"):
         bad.sync()
     bad.sync()
+    # the backward pass reports it the same way
+    G = torch.ones(bad.nnz, dtype=dt, device="cuda")
+    bad.vjp(dev(X, dt), dev(meshgen.lame(m), dt), G, prec)
+    with pytest.raises(abi.FemError, match="FEM_ERR_DEGENERATE"):
+        bad.sync()
+    bad.sync()
 
 
 @pytest.mark.parametrize("cap", list(PATCH_CAPS))
