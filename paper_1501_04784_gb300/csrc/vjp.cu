@@ -793,6 +793,12 @@ static fem_status launch_vjp_elem_t(fem_mesh m, const Closure &cl, const void *X
     const ElemSmem L = elem_smem(P, cl, sizeof(S));
     auto f = m->opt.operator_kind == 1 ? k_vjp_elem<NPE, T, S, CT, true> : k_vjp_elem<NPE, T, S, CT, false>;
     FEM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+    if constexpr (NPE == 4) {
+        // tets: shared memory for two blocks per SM, the rest of the unified L1/shared
+        // array kept as L1 for the element's gathers
+        const int pct = (int)std::min<size_t>(100, (2 * (L.total + 1024) * 100 + 228 * 1024 - 1) / (228 * 1024));
+        FEM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+    }
     const int64_t np = cl.p1 - cl.p0;
     if (np <= 0) return FEM_OK;
     fem_status st;
