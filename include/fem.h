@@ -252,10 +252,10 @@ fem_status fem_build_K_host(fem_mesh m, fem_prec p, const void *X_host, fem_dtyp
  * Asynchronous fem_build_K_host: the same copies and build, ordered on `stream`,
  * returning without waiting.  X_host, c_host and vals_host must be page-locked
  * (FEM_ERR_ARG otherwise) and stay untouched until the stream is synchronised;
- * vals_host is complete then.  Consecutive calls on one mesh use two device
- * staging slots in turn, so with two streams a call's input copy and build
- * overlap the previous call's output copy; the builds themselves run one after
- * the other.  Errors of the build surface at fem_sync.
+ * vals_host is complete then.  Consecutive calls on one mesh use three device
+ * staging slots in turn, so with streams taken in turn a call's input copy and
+ * build overlap the output copies of the calls before it; the builds themselves
+ * run one after the other.  Errors of the build surface at fem_sync.
  */
 fem_status fem_build_K_host_async(fem_mesh m, fem_prec p, const void *X_host, fem_dtype x_dtype,
                                   const void *c_host, fem_dtype c_dtype, void *vals_host, void *stream);

@@ -443,7 +443,7 @@ static void *mapped(void *host) {
     return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
-// Copy in, build, copy out, ordered on s through one of the mesh's two staging
+// Copy in, build, copy out, ordered on s through one of the mesh's staging
 // slots (see fem_mesh_s::host_stage); returns without waiting.
 static fem_status host_build(fem_mesh m, fem_prec p, const void *X_host, fem_dtype x_dtype, const void *c_host,
                              fem_dtype c_dtype, void *vals_host, cudaStream_t s, const char *who) {
@@ -477,14 +477,15 @@ static fem_status host_build(fem_mesh m, fem_prec p, const void *X_host, fem_dty
         }
     }
     const size_t total = direct ? vo : vo + vb;
-    for (cudaEvent_t *e : {&m->stage_free[0], &m->stage_free[1], &m->built})
-        if (!*e) FEM_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    for (cudaEvent_t &e : m->stage_free)
+        if (!e) FEM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (!m->built) FEM_CUDA(cudaEventCreateWithFlags(&m->built, cudaEventDisableTiming));
     if (m->host_stage[k].n < total) {
         FEM_CUDA(cudaEventSynchronize(m->stage_free[k]));  // the slot's last output copy is done
         m->host_stage[k].free();
         FEM_TRY(m->host_stage[k].alloc(m->arena, total, "host staging"));
     }
-    m->stage_next ^= 1;
+    m->stage_next = (k + 1) % fem_mesh_s::HOST_STAGES;
     unsigned char *base = m->host_stage[k].ptr;
     FEM_CUDA(cudaStreamWaitEvent(s, m->stage_free[k], 0));
     FEM_CUDA(cudaMemcpyAsync(base + xo, X_host, xb, cudaMemcpyHostToDevice, s));

@@ -146,18 +146,22 @@ struct fem_mesh_s {
     fem::Plan plan;
     // device status word: set by a bounded device-side wait that gave up
     fem::DevBuf<int> status;
-    // staging of the host-buffer entry points: two slots used in turn, so that a
-    // call's input copy and build can overlap the previous call's output copy;
+    // staging of the host-buffer entry points: HOST_STAGES slots used in turn, so
+    // that a call's input copy and build overlap the output copies of the calls
+    // before it (with three, a call's input copy does not wait for the output
+    // copy of the call two before it, and the output link stays busy);
     // stage_free[k] is recorded after slot k's output copy, `built` after each
     // call's build kernels (the next call's kernels wait for it: builds of one
     // mesh never run concurrently, they share library buffers)
-    fem::DevBuf<unsigned char> host_stage[2];
-    cudaEvent_t stage_free[2] = {nullptr, nullptr};
+    static constexpr int HOST_STAGES = 3;
+    fem::DevBuf<unsigned char> host_stage[HOST_STAGES];
+    cudaEvent_t stage_free[HOST_STAGES] = {};
     cudaEvent_t built = nullptr;
     int stage_next = 0;
     ~fem_mesh_s() {
-        for (cudaEvent_t e : {stage_free[0], stage_free[1], built})
+        for (cudaEvent_t e : stage_free)
             if (e) cudaEventDestroy(e);
+        if (built) cudaEventDestroy(built);
     }
     // FP64 element matrices staged between integration and assembly (the FP64
     // pipe is the bound there, so integrating each element once beats recomputing

@@ -268,21 +268,23 @@ def test_high_valence_summation_modes(fem, fp64_sums):
     assert d_err.max() <= 4e-7
 
 
-def test_host_async_two_streams(fem):
-    """fem_build_K_host_async on alternating streams with two staging slots: every
-    step's values equal the device build's, and pageable buffers are refused."""
+@pytest.mark.parametrize("n_streams", [1, 2, 3, 4])
+def test_host_async_streams(fem, n_streams):
+    """fem_build_K_host_async on streams taken in turn, through the mesh's three
+    staging slots (more steps than slots, so every slot is reused): every step's
+    values equal the device build's, and pageable buffers are refused."""
     from paper_1501_04784_gb300 import abi
     m = MESHES["hex_7x5x3"]()
     mesh = make(fem, m)
     Xd, cd, X, c = inputs(m, "mixed")
     ref = mesh.build_K(Xd, cd, "mixed").cpu()
     Xh, ch = Xd.cpu().pin_memory(), cd.cpu().pin_memory()
-    scale = [1.0, 1.5, 2.0, 0.5]
+    scale = [1.0, 1.5, 2.0, 0.5, 3.0, 0.25, 1.25]
     outs = [torch.empty(mesh.nnz, dtype=torch.float32).pin_memory() for _ in scale]
     cs = [(ch * s).pin_memory() for s in scale]
-    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    streams = [torch.cuda.Stream() for _ in range(n_streams)]
     for k, s in enumerate(scale):
-        mesh.build_K_host_async(Xh, cs[k], "mixed", out=outs[k], stream=streams[k % 2])
+        mesh.build_K_host_async(Xh, cs[k], "mixed", out=outs[k], stream=streams[k % n_streams])
     torch.cuda.synchronize()
     mesh.sync()
     for k, s in enumerate(scale):
