@@ -564,8 +564,8 @@ def other_workloads(flush, stream):
 def backward_workloads(timed, dev):
     """The backward pass (fem_vjp: dL/dX and dL/dc of L = sum over stored entries
     G_ij K_ij) on the 1M-brick mesh, for the stiffness operator in both precisions
-    and for the elasticity operator in mixed precision, and on the 3.07M-tet mesh
-    for both operators in mixed precision; G is a seeded standard
+    and for the elasticity and mass operators in mixed precision, and on the
+    3.07M-tet mesh for the stiffness and elasticity operators in mixed precision; G is a seeded standard
     normal upstream on K's pattern.  Algorithmic bytes: X, E, c and G read once,
     dX and dc written once."""
     import numpy as np
@@ -575,7 +575,7 @@ def backward_workloads(timed, dev):
     from paper_1501_04784_gb300 import fem
 
     res = {}
-    for op, key, idx in ((0, "stiffness", 1), (2, "elasticity", 1), (0, "stiffness_tet", 2),
+    for op, key, idx in ((0, "stiffness", 1), (2, "elasticity", 1), (1, "mass", 1), (0, "stiffness_tet", 2),
                          (2, "elasticity_tet", 2)):
         m = meshgen.config_mesh(idx)
         mesh = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), operator_kind=op)
