@@ -26,15 +26,6 @@
 
 namespace fem {
 
-template <typename T>
-__device__ __forceinline__ Vec3<T> sel8v(const Vec3<T> (&v)[8], int i) {
-    Vec3<T> r = v[0];
-#pragma unroll
-    for (int k = 1; k < 8; ++k)
-        if (i == k) r = v[k];
-    return r;
-}
-
 // Sum over the element's NPE lanes (lanes base .. base + NPE - 1 of the warp).
 template <int NPE, typename T>
 __device__ __forceinline__ T group_sum(T v) {
@@ -105,11 +96,14 @@ __device__ __forceinline__ void add_dx(const T (&A)[3][3], T phi, const T (&P)[9
 
 // Brick: node a = lane & 7; all 32 lanes call it (it shuffles).  W = the thread's
 // blocks of the symmetric upstream.  Outputs dx_a and (summed over the element)
-// dlam, dmu.
+// dlam, dmu.  At each point the thread forms only its own node's gradient G_a and
+// takes its block partners' from their lanes; Psi_a (= dPhi/dG_a) gathers its own
+// blocks' shares and, by shuffles back, the shares of the blocks in which node a
+// is the partner, so sum_a Psi_a G_a^T needs one outer product per thread.
 template <typename T, typename S>
 __device__ __forceinline__ void elastic_brick_vjp(const S (*xc)[3], T lam, T mu, const T (&W)[5][9], T (&dx)[3],
                                                   T &dlam, T &dmu) {
-    const int a = threadIdx.x & 7;
+    const int lane = threadIdx.x & 31, a = lane & 7, base = lane & ~7;
     Vec3<T> e[3][2][2];
     brick_edges<T, S>(xc, e);
     Vec3<T> row[3][2][2];
@@ -117,6 +111,17 @@ __device__ __forceinline__ void elastic_brick_vjp(const S (*xc)[3], T lam, T mu,
     dx[0] = dx[1] = dx[2] = T(0);
     dlam = dmu = T(0);
     const T P = T(FEM_GP), Q = T(FEM_GQ);
+    const int a1 = (a ^ (a >> 1)) & 1, a2 = (a >> 1) & 1, a3 = a >> 2;  // node a's axis bits
+    const T s1 = a1 ? T(0.5) : T(-0.5), s2 = a2 ? T(0.5) : T(-0.5), s3 = a3 ? T(0.5) : T(-0.5);
+    int src_b[5], src_r[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        src_b[m] = base + ((a + m) & 7);  // the partner of block m
+        src_r[m] = base + ((a - m) & 7);  // the lane whose block m has node a as partner
+    }
+    T tr[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) tr[m] = W[m][0] + W[m][4] + W[m][8];
 #pragma unroll 1
     for (int q = 0; q < 8; ++q) {
         const int q1 = q >> 2, q2 = (q >> 1) & 1, q3 = q & 1;
@@ -131,28 +136,54 @@ __device__ __forceinline__ void elastic_brick_vjp(const S (*xc)[3], T lam, T mu,
         const T A[3][3] = {{C0.x * id, C1.x * id, C2.x * id}, {C0.y * id, C1.y * id, C2.y * id},
                            {C0.z * id, C1.z * id, C2.z * id}};
         const T wd = d < T(0) ? -d : d;  // Gauss weights 1
-        // natural derivatives and physical gradients of every node at q
-        Vec3<T> Gn[8];
-        T Da[3] = {T(0), T(0), T(0)};
+        // node a's natural derivatives and physical gradient at q
+        const T f1 = a1 == q1 ? P : Q, f2 = a2 == q2 ? P : Q, f3 = a3 == q3 ? P : Q;
+        const T Da[3] = {s1 * f2 * f3, s2 * f1 * f3, s3 * f1 * f2};
+        const T g_a[3] = {A[0][0] * Da[0] + A[0][1] * Da[1] + A[0][2] * Da[2],
+                          A[1][0] * Da[0] + A[1][1] * Da[1] + A[1][2] * Da[2],
+                          A[2][0] * Da[0] + A[2][1] * Da[1] + A[2][2] * Da[2]};
+        T phi = T(0), psi[3] = {T(0), T(0), T(0)}, u2[5][3];
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const int b1 = hb1(b), b2 = hb2(b), b3 = hb3(b);
-            const T f1 = b1 == q1 ? P : Q, f2 = b2 == q2 ? P : Q, f3 = b3 == q3 ? P : Q;
-            const T D0 = T(0.5 * hsig(b1)) * f2 * f3, D1 = T(0.5 * hsig(b2)) * f1 * f3, D2 = T(0.5 * hsig(b3)) * f1 * f2;
-            Gn[b] = {A[0][0] * D0 + A[0][1] * D1 + A[0][2] * D2, A[1][0] * D0 + A[1][1] * D1 + A[1][2] * D2,
-                     A[2][0] * D0 + A[2][1] * D1 + A[2][2] * D2};
-            if (b == a) {
-                Da[0] = D0;
-                Da[1] = D1;
-                Da[2] = D2;
+        for (int m = 0; m < 5; ++m) {
+            T g_b[3] = {g_a[0], g_a[1], g_a[2]};
+            if (m > 0) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) g_b[i] = __shfl_sync(0xffffffffu, g_a[i], src_b[m]);
+            }
+            u2[m][0] = u2[m][1] = u2[m][2] = T(0);
+            if (!blk_valid<8>(a, m)) continue;
+            const T mult = m == 0 ? T(1) : T(2);
+            const T t = tr[m];
+            T Wgb[3], WTgb[3], Wga[3], WTga[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                Wgb[i] = W[m][3 * i] * g_b[0] + W[m][3 * i + 1] * g_b[1] + W[m][3 * i + 2] * g_b[2];
+                WTgb[i] = W[m][i] * g_b[0] + W[m][3 + i] * g_b[1] + W[m][6 + i] * g_b[2];
+                Wga[i] = W[m][3 * i] * g_a[0] + W[m][3 * i + 1] * g_a[1] + W[m][3 * i + 2] * g_a[2];
+                WTga[i] = W[m][i] * g_a[0] + W[m][3 + i] * g_a[1] + W[m][6 + i] * g_a[2];
+            }
+            const T lt = g_a[0] * Wgb[0] + g_a[1] * Wgb[1] + g_a[2] * Wgb[2];  // G_a^T W G_b
+            const T mt = g_b[0] * Wga[0] + g_b[1] * Wga[1] + g_b[2] * Wga[2];  // G_b^T W G_a
+            const T gab = g_a[0] * g_b[0] + g_a[1] * g_b[1] + g_a[2] * g_b[2];
+            phi += mult * (lam * lt + mu * (mt + t * gab));
+            dlam += wd * mult * lt;
+            dmu += wd * mult * (mt + t * gab);
+            // dPhi/dG_a from this block: 2 T^ab G_b; for b != a, dPhi/dG_b = 2 T^ba G_a
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                psi[i] += T(2) * (lam * Wgb[i] + mu * WTgb[i] + mu * t * g_b[i]);
+                if (m > 0) u2[m][i] = T(2) * (lam * WTga[i] + mu * Wga[i] + mu * t * g_a[i]);
             }
         }
-        const Vec3<T> ga = sel8v(Gn, a);
-        Vec3<T> gb[5];
 #pragma unroll
-        for (int m = 0; m < 5; ++m) gb[m] = sel8v(Gn, blk_node<8>(a, m));
-        T phi, Pm[9];
-        point_shares<8, T>(W, ga, gb, a, lam, mu, wd, phi, Pm, dlam, dmu);
+        for (int m = 1; m < 5; ++m)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) psi[i] += __shfl_sync(0xffffffffu, u2[m][i], src_r[m]);
+        T Pm[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Pm[3 * i + j] = psi[i] * g_a[j];
         phi = group_sum<8, T>(phi);
 #pragma unroll
         for (int n = 0; n < 9; ++n) Pm[n] = group_sum<8, T>(Pm[n]);
