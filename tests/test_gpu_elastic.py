@@ -311,7 +311,8 @@ def test_elastic_row_windows(fem, prec, opts):
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_elastic_budget_groups_bitwise_equal(fem, prec):
     """Under a budget too small for all closures the plan runs in patch groups
-    (Eq. 10): the elasticity build gives exactly the unbudgeted values."""
+    (Eq. 10): the elasticity build and its backward pass give exactly the
+    unbudgeted values."""
     m = meshgen.hex_grid(16, jitter=0.2, seed=77, permute_nodes=True, permute_elems=True)
     Xd, cd, _, _ = inputs(m, prec)
     free = make(fem, m, patch_entries=256, fp64_fused=1)
@@ -322,6 +323,15 @@ def test_elastic_budget_groups_bitwise_equal(fem, prec):
     tight.sync()
     assert tight.info()["n_groups"] > 1
     assert torch.equal(got, ref)
+    # the backward pass in patch groups (always the fused kernel there) equals the
+    # unbudgeted fused pass bit for bit
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    G = torch.randn(free.nnz, generator=torch.Generator(device="cuda").manual_seed(15), device="cuda").to(dt)
+    fused = make(fem, m, patch_entries=256, fp64_fused=1, vjp_fused=1)
+    fused.pattern()
+    a, b = fused.vjp(Xd, cd, G, prec), tight.vjp(Xd, cd, G, prec)
+    tight.sync()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
 
 
 def test_elastic_autotune(fem):
