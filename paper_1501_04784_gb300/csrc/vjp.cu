@@ -719,11 +719,27 @@ __global__ void __launch_bounds__(256) k_vjp_gather(PlanView pv, const T *__rest
                 const T *src = dxe + e * (NPE * 3);
                 uint16_t ln[NPE];
                 load_lnodes<NPE>(pv.celem_lnode, ci, ln);
+                // the element's row of node gradients in 16-byte pieces (rows are
+                // 16-byte aligned: NPE * 3 values of 4 or 8 bytes)
+                T row[NPE * 3];
+                if constexpr (sizeof(T) == 4) {
+#pragma unroll
+                    for (int k = 0; k < NPE * 3; k += 4) {
+                        const float4 w = __ldg(reinterpret_cast<const float4 *>(src) + k / 4);
+                        row[k] = w.x; row[k + 1] = w.y; row[k + 2] = w.z; row[k + 3] = w.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < NPE * 3; k += 2) {
+                        const double2 w = __ldg(reinterpret_cast<const double2 *>(src) + k / 2);
+                        row[k] = w.x; row[k + 1] = w.y;
+                    }
+                }
 #pragma unroll
                 for (int a = 0; a < NPE; ++a) {
                     own[a] = cown[ln[a]];
 #pragma unroll
-                    for (int j = 0; j < 3; ++j) v[a][j] = own[a] >= 0 ? __ldg(src + 3 * a + j) : T(0);
+                    for (int j = 0; j < 3; ++j) v[a][j] = row[3 * a + j];
                 }
             }
             const int last = min(base + nthr, nel) - 1;
