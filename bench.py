@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--workload", choices=["hex", "tet"], default="hex",
                     help="--once only: the 1M-brick workload or the 3.07M-tet workload")
     ap.add_argument("--patch-entries", type=int, default=0, help="--once only: plan patch size (0 = default)")
+    ap.add_argument("--tile-elems", type=int, default=0, help="--once only: elements per tile (0 = default)")
+    ap.add_argument("--assembly", type=int, default=-1,
+                    help="--once only: 0 = element tiles, 1 = node patches (-1 = the library's default)")
     ap.add_argument("--block-threads", type=int, default=0, help="--once only: threads per block (0 = default)")
     ap.add_argument("--operator", choices=["stiffness", "elasticity"], default="stiffness",
                     help="--once only: the scalar stiffness matrix or the elasticity operator")
@@ -193,24 +196,32 @@ SMS, FP32_LANES = 152, 128
 ELASTIC_BRICK_FLOPS = 36 + 952 + 960 + 192 + 10368 + 1188
 
 
+# The oracle's sample, shared by the reference arm and the CPU baseline: rotating
+# slices of SAMPLE_ELEMS consecutive elements of the workload, each slice built
+# end to end (element loop, stable sort, reduction to CSR) in FP64 on one thread.
+SAMPLE_ELEMS = 8192
+
+
+def oracle_slice(m, k):
+    import oracle
+    lo = (k * SAMPLE_ELEMS) % max(1, m.n_elems - SAMPLE_ELEMS)
+    oracle.build_K(m.npe, m.X, m.E[lo:lo + SAMPLE_ELEMS], m.c[lo:lo + SAMPLE_ELEMS])
+
+
 def cpu_baseline(m, target_s=12.0):
-    """The FP64 oracle (Algorithm 1 as written, single thread) on a bounded sample
-    of the workload's elements: whole passes over growing prefixes until ~target_s."""
-    import numpy as np
+    """The FP64 oracle (Algorithm 1 as written, single thread) on the shared sample:
+    slices until about target_s seconds of work."""
     import oracle
     oracle.build()
-    n = 4096
-    spent = 0.0
-    while True:
-        t0 = time.perf_counter()
-        oracle.build_K(m.npe, m.X, m.E[:n], m.c[:n])
-        dt = time.perf_counter() - t0
-        spent += dt
-        if spent + 2.5 * dt > target_s or n >= m.n_elems:
-            break
-        n = min(2 * n, m.n_elems)
-    return {"value": n / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {n} of {m.n_elems} elements of the workload: element loop + stable sort/reduce to CSR, FP64, 1 thread",
+    oracle_slice(m, 0)
+    k, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < target_s:
+        oracle_slice(m, k)
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": k * SAMPLE_ELEMS / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
+            "sample": f"{k} rotating slices of {SAMPLE_ELEMS} consecutive elements (the reference arm's steps), "
+                      "each built end to end (element loop, stable sort, reduction to CSR), FP64, 1 thread",
             "nproc": os.cpu_count(), "cpu_model": cpu_model()}
 
 
@@ -233,37 +244,68 @@ def cpu_model():
     return platform.machine()
 
 
-def oracle_error(m, rowptr, col, builds, n_rows=2000, seed=12):
-    """Accuracy of the timed builds, from the same leg as the CPU baseline: the
-    oracle's exact rows of n_rows random nodes (all elements touching them), against
-    each build, as the largest |K_ij - K*_ij| / sum_e sqrt(k_aa k_bb) (the per-entry
-    Cauchy-Schwarz scale of the contributions).  builds = {name: (vals, X, c)},
-    X and c as that build read them."""
+def sampled_error(m, rowptr, col, vals, X, c, n_rows=2000, seed=12):
+    """Accuracy of one build against the oracle's exact rows of n_rows random nodes
+    (the oracle run on every element touching them; X and c as the build read
+    them).  Three measures, each the largest over the sampled entries:
+      r13   |K - K*| / sum_e sqrt(k_aa k_bb)   (the per-entry scale the tests gate on)
+      c14   |K - K*| / sum_e |k_ab|            (the sum of |contributions|)
+      plain |K - K*| / |K*| on entries with |K*| >= 1e-3 of their r13 scale.
+    An entry whose column differs from the oracle's makes every measure inf."""
     import numpy as np
     import oracle
     rng = np.random.default_rng(seed)
-    rows = np.unique(rng.choice(m.n_nodes, n_rows, replace=False))
+    rows = np.unique(rng.choice(m.n_nodes, min(n_rows, m.n_nodes), replace=False))
     touch = np.isin(m.E, rows).any(axis=1)
-    rp, cl = rowptr, col
-    out = {}
-    for name, (vals, X, c) in builds.items():
-        sub = oracle.build_K(m.npe, np.asarray(X, np.float64), m.E[touch], np.asarray(c, np.float64)[touch])
-        worst = 0.0
-        for r in rows:
-            a, b = sub["rowptr"][r], sub["rowptr"][r + 1]
-            g0, g1 = rp[r], rp[r + 1]
-            if not np.array_equal(cl[g0:g1], sub["col"][a:b]):
-                worst = float("inf")
-                break
-            err = np.abs(vals[g0:g1].astype(np.float64) - sub["vals"][a:b]) / np.maximum(sub["cs"][a:b], 1e-300)
-            worst = max(worst, float(err.max()))
-        out[name] = worst
-    out["rows_sampled"] = int(len(rows))
-    out["metric"] = "max |K - K_oracle| / sum_e sqrt(k_aa k_bb) over the sampled rows"
-    return out
+    sub = oracle.build_K(m.npe, np.asarray(X, np.float64), m.E[touch], np.asarray(c, np.float64)[touch])
+    idx_g, idx_o = [], []
+    for r in rows:
+        a, b = sub["rowptr"][r], sub["rowptr"][r + 1]
+        g0, g1 = rowptr[r], rowptr[r + 1]
+        if not np.array_equal(col[g0:g1], sub["col"][a:b]):
+            return {"r13": float("inf"), "c14": float("inf"), "plain": float("inf"), "rows": int(len(rows))}
+        idx_g.append(np.arange(g0, g1))
+        idx_o.append(np.arange(a, b))
+    ig, io = np.concatenate(idx_g), np.concatenate(idx_o)
+    got = np.asarray(vals, np.float64)[ig]
+    ref, cs, ab = sub["vals"][io], sub["cs"][io], sub["abs"][io]
+    d = np.abs(got - ref)
+    keep = np.abs(ref) >= 1e-3 * cs
+    return {"r13": float((d / np.maximum(cs, 1e-300)).max()), "c14": float((d / np.maximum(ab, 1e-300)).max()),
+            "plain": float((d[keep] / np.abs(ref[keep])).max()) if keep.any() else 0.0, "rows": int(len(rows))}
+
+
+def sig(x, n=4):
+    """x rounded to n significant digits (keeps the JSON line short)."""
+    if isinstance(x, float) and x == x and x not in (float("inf"), float("-inf")) and x != 0.0:
+        from math import floor, log10
+        return round(x, n - 1 - int(floor(log10(abs(x)))))
+    return x
+
+
+def compact(d):
+    if isinstance(d, dict):
+        return {k: compact(v) for k, v in d.items()}
+    if isinstance(d, (list, tuple)):
+        return [compact(v) for v in d]
+    return sig(d)
 
 
 # --------------------------------------------------------------- our arm
+def median_ms(fn, n, flush, stream):
+    """Median of n device times of fn (CUDA events on the launching stream), each
+    after a 256 MB write that flushes the L2."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return statistics.median([a.elapsed_time(b) for a, b in evs])
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -294,13 +336,10 @@ def run_ours(args):
     mesh.build_K(Xf, cf, "mixed", out=vals)
     torch.cuda.synchronize()
     cold_s = time.perf_counter() - t0
-    info = mesh.info()
 
-    # tuner (untimed): assembly tile and threads per block on the real inputs
+    # tuner (untimed): work unit and threads per block on the real inputs
     tuning = mesh.autotune(Xf, cf, "mixed")
     info = mesh.info()
-    vals = torch.empty(nnz, dtype=torch.float32, device="cuda")
-
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
     def timed(prec, X, c, out, steps, mh=None):
@@ -328,30 +367,28 @@ def run_ours(args):
     barrier(dist)
     clocks = clk.stop() if clk else None
 
-    total_s = sum(ms) / 1e3
-    max_total = max_over_ranks(dist, total_s)
-    elems_all = sum_over_ranks(dist, float(m.n_elems * args.steps))
-    value = elems_all / max_total
-    ms_step = statistics.mean(ms)
+    ms_step = statistics.median(ms)
+    max_step = max_over_ranks(dist, ms_step)
+    elems_all = sum_over_ranks(dist, float(m.n_elems))
+    value = elems_all / (max_step / 1e3)
 
     # FP64 build beside it
     vals64 = torch.empty(nnz, dtype=torch.float64, device="cuda")
     for _ in range(3):
         mesh.build_K(X64, c64, "fp64", out=vals64)
-    steps64 = max(3, min(args.steps, 20))
-    ms64 = timed("fp64", X64, c64, vals64, steps64)
-    fp64_eps = m.n_elems / (statistics.mean(ms64) / 1e3)
+    ms64 = statistics.median(timed("fp64", X64, c64, vals64, max(5, min(args.steps, 20))))
+    fp64_eps = m.n_elems / (ms64 / 1e3)
 
-    # the mass operator on the same mesh and tuned tile (Section 5's other matrix)
-    mass_mesh = fem.Mesh(E, m.n_nodes, X=X64, operator_kind=1, patch_entries=tuning["patch_entries"],
-                         block_threads=tuning["block_threads"])
+    # the mass operator on the same mesh and tuning (Section 5's other matrix)
+    mass_mesh = fem.Mesh(E, m.n_nodes, X=X64, operator_kind=1)
     mass_mesh.pattern()
+    mass_mesh.set_tuning(tuning["patch_entries"], tuning["block_threads"])
     for _ in range(3):
         mass_mesh.build_K(Xf, cf, "mixed", out=vals)
-    ms_mass = timed("mixed", Xf, cf, vals, max(3, min(args.steps, 20)), mass_mesh)
+    ms_mass = statistics.median(timed("mixed", Xf, cf, vals, max(5, min(args.steps, 20)), mass_mesh))
     mass_mesh.close()
 
-    # end to end through the host-buffer C-ABI call (pinned inputs and outputs)
+    # end to end through the host-buffer C-ABI calls (pinned inputs and outputs)
     e2e = None
     if not args.no_e2e:
         Xh = Xf.cpu().pin_memory()
@@ -380,9 +417,9 @@ def run_ours(args):
         mesh.sync()
         # host-resident K: the kernel writes the values straight into the pinned
         # host buffer (the path a matrix larger than device memory takes)
-        dmesh = fem.Mesh(E, m.n_nodes, X=X64, host_direct=1, patch_entries=tuning["patch_entries"],
-                         block_threads=tuning["block_threads"])
+        dmesh = fem.Mesh(E, m.n_nodes, X=X64, host_direct=1)
         dmesh.pattern()
+        dmesh.set_tuning(tuning["patch_entries"], tuning["block_threads"])
         for _ in range(3):
             dmesh.build_K_host(Xh, ch, "mixed", out=vh)
         t0 = time.perf_counter()
@@ -392,33 +429,30 @@ def run_ours(args):
         dmesh.close()
         e2e = {"value": m.n_elems / dt, "unit": "elements/s", "h2d_bytes_per_step": Xh.nbytes + ch.nbytes,
                "d2h_bytes_per_step": nnz * 4,
-               "api": "fem_build_K_host_async, three streams (copy-in and build of a step overlap the earlier copy-outs)",
-               "serial": {"value": m.n_elems / dt_serial, "api": "fem_build_K_host (synchronous)"},
-               "host_resident": {"value": m.n_elems / dt_direct, "ms_per_step": dt_direct * 1e3,
-                                 "api": "fem_build_K_host with host_direct: values written by the kernel into "
-                                        "pinned host memory, no device copy of K"}}
+               "api": "fem_build_K_host_async on three streams (a step's copy-in and build overlap earlier copy-outs)",
+               "serial": m.n_elems / dt_serial, "host_resident": m.n_elems / dt_direct}
 
     peak, peak_kind = measured_peaks()
     alg = algorithmic_bytes(m.n_nodes, m.n_elems, 8, nnz, 4, 4, 4)
     alg64 = algorithmic_bytes(m.n_nodes, m.n_elems, 8, nnz, 8, 8, 8)
     achieved = alg / (ms_step / 1e3) / 1e9
-    # the profiled DRAM traffic of the same kernel sources, workload and patch size
-    wkey = f"hex8_n{args.n}_mixed_p{(tuning or {}).get('patch_entries', 0)}"
+    kernel = "k_tile" if info["assembly"] == 1 else "k_patch"
+    wkey = f"hex8_n{args.n}_mixed_{'t' if info['assembly'] == 1 else 'p'}{tuning.get('patch_entries', 0)}"
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     alu_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12          # TFLOP/s at the sampled clock
     alu_achieved = BRICK_FLOPS * m.n_elems / (ms_step / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": round(alu_achieved, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
-            "frac": round(alu_achieved / alu_peak, 4), "traffic": profiled_traffic("k_patch", wkey),
+    roof = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s",
+            "frac": alu_achieved / alu_peak, "traffic": profiled_traffic(kernel, wkey),
             "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz (sampled)",
-            "kernel": "k_patch (fused integrate + assemble)", "flops_per_element": BRICK_FLOPS,
-            "algorithmic_flops_per_launch": BRICK_FLOPS * m.n_elems,
-            "hbm": {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                    "peak_source": peak_kind, "algorithmic_bytes_per_launch": alg}}
+            "kernel": f"{kernel} (fused integrate + assemble) and its launches",
+            "flops_per_element": BRICK_FLOPS,
+            "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "peak_source": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                    "algorithmic_bytes_per_launch": alg}}
     if roof["traffic"]:
-        # DRAM bytes the kernel really moves (ncu) over the launch time measured here
-        roof["hbm"]["dram_gbs"] = round(roof["traffic"] / (ms_step / 1e3) / 1e9, 1)
-        roof["hbm"]["dram_frac"] = round(roof["hbm"]["dram_gbs"] / peak, 4)
+        roof["hbm"]["dram_gbs"] = roof["traffic"] / (ms_step / 1e3) / 1e9
 
+    out = None
     if rank == 0:
         out = {
             "metric": "global-K build elements/s (integrate+assemble), % HBM roofline, mixed vs FP64",
@@ -426,34 +460,42 @@ def run_ours(args):
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 (f64 Jacobians of distorted elements)", "data": "synthetic (seeded)",
             "config": {"workload": WORKLOAD if args.n == 100 else f"{args.n}^3 bricks", "n_elems": m.n_elems,
-                       "n_nodes": m.n_nodes, "nnz": nnz, "precision": "mixed", "pattern": "cached",
-                       "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before every step"},
-            "hbm_frac": round(achieved / peak, 4),
-            "fp64": {"value": fp64_eps, "unit": "elements/s", "ms_per_step": statistics.mean(ms64),
-                     "hbm_frac": round(alg64 / (statistics.mean(ms64) / 1e3) / 1e9 / peak, 4),
-                     "mixed_speedup": value / world / fp64_eps},
-            "mass": {"value": m.n_elems / (statistics.mean(ms_mass) / 1e3), "unit": "elements/s",
-                     "ms_per_step": statistics.mean(ms_mass), "operator": "consistent mass matrix, mixed"},
-            "cold_build": {"value": m.n_elems / cold_s, "unit": "elements/s", "seconds": cold_s,
-                           "includes": "validation, locality order, pattern, plan, first numeric build"},
-            "plan": {k: info[k] for k in ("n_patches", "closure_elems", "n_colors", "plan_bytes")},
-            "tuning": tuning,
+                       "nnz": nnz, "precision": "mixed", "pattern": "cached", "parallelism": f"replicas x{world}",
+                       "l2": "flushed (256 MB write) before every step", "timing": "median of steps",
+                       "assembly": "element tiles" if info["assembly"] == 1 else "node patches"},
             "roofline": roof, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
         }
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(m)
-            rowptr, col = mesh.get_pattern()
-            mesh.build_K(Xf, cf, "mixed", out=vals)  # vals held the mass matrix since
-            out["error"] = oracle_error(m, rowptr.cpu().numpy(), col.cpu().numpy(), {
-                "mixed": (vals.cpu().numpy(), m.X.astype(np.float32), m.c.astype(np.float32)),
-                "fp64": (vals64.cpu().numpy(), m.X, m.c)})
+    rowptr, col = mesh.get_pattern()
+    rp, cl = rowptr.cpu().numpy(), col.cpu().numpy()
+    mesh.build_K(Xf, cf, "mixed", out=vals)
+    err = {}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        err["hex1M"] = {"mixed": sampled_error(m, rp, cl, vals.cpu().numpy(), m.X.astype(np.float32),
+                                               m.c.astype(np.float32)),
+                        "fp64": sampled_error(m, rp, cl, vals64.cpu().numpy(), m.X, m.c)}
     mesh.close()
+    del vals, vals64
+    extra = None
     if not args.no_workloads:
-        extra = other_workloads(flush, stream)
-        if rank == 0:
-            out["workloads"] = extra
+        extra, werr = other_workloads(flush, stream, with_error=(rank == 0 and world == 1 and not args.no_cpu_baseline))
+        err.update(werr)
     if rank == 0:
-        print(json.dumps(out))
+        if extra is not None:
+            out["workloads"] = extra
+        out["plan"] = {"tiles_or_patches": info["n_patches"], "border_rows": info["border_rows"],
+                       "n_colors": info["n_colors"], "plan_bytes": info["plan_bytes"]}
+        out["tuning"] = {k: tuning[k] for k in ("patch_entries", "block_threads", "assembly") if k in tuning}
+        out["mass"] = {"ms_per_step": ms_mass, "value": m.n_elems / (ms_mass / 1e3)}
+        out["cold_build"] = {"seconds": cold_s, "value": m.n_elems / cold_s,
+                             "includes": "validation, locality order, pattern, plan, first numeric build"}
+        out["fp64"] = {"value": fp64_eps, "ms_per_step": ms64, "hbm_frac": alg64 / (ms64 / 1e3) / 1e9 / peak,
+                       "mixed_speedup": (value / world) / fp64_eps}
+        if err:
+            out["error"] = err
+        out["hbm_frac"] = achieved / peak
+        print(json.dumps(compact(out), separators=(",", ":")))
     if dist is not None:
         dist.destroy_process_group()
 
@@ -461,7 +503,8 @@ def run_ours(args):
 # -------------------------------------------------------- reference arm
 def run_reference(args):
     """The oracle (the plain FP64 CPU program of Algorithm 1) on the host cores,
-    each step one bounded slice of the same workload."""
+    each step one slice of the shared sample (SAMPLE_ELEMS consecutive elements of
+    the same workload), the same sample the CPU baseline of our arm times."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -469,43 +512,37 @@ def run_reference(args):
     import oracle
     oracle.build()
     m = meshgen.config_mesh(1, nx=args.n)
-    per_step = 8192
-    off = 0
-
-    def step():
-        nonlocal off
-        lo = off % max(1, m.n_elems - per_step)
-        oracle.build_K(m.npe, m.X, m.E[lo:lo + per_step], m.c[lo:lo + per_step])
-        off += per_step
-
-    for _ in range(args.warmup):
-        step()
+    for k in range(args.warmup):
+        oracle_slice(m, k)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
+    for k in range(args.steps):
+        oracle_slice(m, args.warmup + k)
     dt = time.perf_counter() - t0
-    value = per_step * args.steps / dt
-    print(json.dumps({
+    value = SAMPLE_ELEMS * args.steps / dt
+    print(json.dumps(compact({
         "impl": "reference", "metric": "global-K build elements/s (integrate+assemble), % HBM roofline, mixed vs FP64",
         "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded)",
         "config": {"workload": WORKLOAD if args.n == 100 else f"{args.n}^3 bricks", "precision": "fp64 oracle"},
         "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{per_step} consecutive elements of the workload per step (rotating)"},
+                         "sample": f"rotating slices of {SAMPLE_ELEMS} consecutive elements, one per step"},
         "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }))
+    }), separators=(",", ":")))
 
 
-def other_workloads(flush, stream):
-    """The batched and the large workload beside the headline (mixed precision, pattern
-    cached, L2 flushed before every timed build): 512 uneven brick meshes in one
-    persistent launch replayed from a CUDA graph, and 300^3 bricks built in patch
-    groups under a 16 GB library budget, with its backward pass."""
+def other_workloads(flush, stream, with_error):
+    """The workloads beside the headline (pattern cached, L2 flushed before every
+    timed build, median of the timed builds): the 8,000-brick FP64 build (latency),
+    the 3.07M-tetrahedron build (mixed), 512 uneven brick meshes in one persistent
+    launch replayed from a CUDA graph, 300^3 bricks under a 16 GB library budget and
+    under a budget that forces patch groups, with its backward pass, the
+    elasticity operator and the backward passes.  Returns (workloads, errors)."""
     import numpy as np
     import torch
 
     import meshgen
+    import oracle
     from paper_1501_04784_gb300 import fem
 
     def dev(a, dt):
@@ -515,16 +552,50 @@ def other_workloads(flush, stream):
         for _ in range(2):
             fn()
         torch.cuda.synchronize()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
-        for a, b in evs:
-            flush.zero_()
-            a.record(stream)
-            fn()
-            b.record(stream)
-        torch.cuda.synchronize()
-        return statistics.median([a.elapsed_time(b) for a, b in evs])
+        return median_ms(fn, n, flush, stream)
 
-    out = {}
+    out, err = {}, {}
+    # the small FP64 workload: one build's latency (pattern cached) and its cold build
+    m = meshgen.config_mesh(0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mesh = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64))
+    nnz = mesh.pattern()
+    X, c = dev(m.X, torch.float64), dev(m.c, torch.float64)
+    v = torch.empty(nnz, dtype=torch.float64, device="cuda")
+    mesh.build_K(X, c, "fp64", out=v)
+    torch.cuda.synchronize()
+    cold = time.perf_counter() - t0
+    t = timed(lambda: mesh.build_K(X, c, "fp64", out=v), 20)
+    out["hex8k_fp64"] = {"ms": t, "value": m.n_elems / (t / 1e3), "cold_s": cold}
+    if with_error:
+        ref = oracle.build_K(8, m.X, m.E, m.c)
+        vv = v.cpu().numpy()
+        d = np.abs(vv - ref["vals"])
+        keep = np.abs(ref["vals"]) >= 1e-3 * ref["cs"]
+        err["hex8k"] = {"fp64": {"r13": float((d / ref["cs"]).max()), "c14": float((d / ref["abs"]).max()),
+                                 "plain": float((d[keep] / np.abs(ref["vals"][keep])).max()), "rows": m.n_nodes}}
+    mesh.close()
+
+    # 3.07M tetrahedra, mixed
+    m = meshgen.config_mesh(2)
+    mesh = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64))
+    nnz = mesh.pattern()
+    X, c = dev(m.X, torch.float32), dev(m.c, torch.float32)
+    v = torch.empty(nnz, dtype=torch.float32, device="cuda")
+    tt = mesh.autotune(X, c, "mixed")
+    t = timed(lambda: mesh.build_K(X, c, "mixed", out=v), 20)
+    alg = algorithmic_bytes(m.n_nodes, m.n_elems, 4, nnz, 4, 4, 4)
+    peak, _ = measured_peaks()
+    out["tet3M"] = {"ms": t, "value": m.n_elems / (t / 1e3), "hbm_frac": alg / (t / 1e3) / 1e9 / peak,
+                    "tile": tt["patch_entries"], "threads": tt["block_threads"]}
+    if with_error:
+        rowptr, col = mesh.get_pattern()
+        err["tet3M"] = {"mixed": sampled_error(m, rowptr.cpu().numpy(), col.cpu().numpy(), v.cpu().numpy(),
+                                               m.X.astype(np.float32), m.c.astype(np.float32))}
+    mesh.close()
+    del mesh, X, c, v
+
     ms = meshgen.batch_meshes()
     meshes = [fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64)) for m in ms]
     Xs = [dev(m.X, torch.float32) for m in ms]
@@ -532,42 +603,57 @@ def other_workloads(flush, stream):
     vals = [torch.empty(mesh.pattern(), dtype=torch.float32, device="cuda") for mesh in meshes]
     nel = sum(m.n_elems for m in ms)
     t = timed(lambda: fem.build_K_batched(meshes, Xs, cs, "mixed", out=vals), 10)
-    out["batched"] = {"workload": f"{len(ms)} uneven brick meshes, {nel} elements, one graph launch",
-                      "value": nel / (t / 1e3), "unit": "elements/s", "ms_per_step": t,
-                      "launch": fem.batched_config(meshes, "mixed")}
+    cfg = fem.batched_config(meshes, "mixed")
+    out["batch512"] = {"ms": t, "value": nel / (t / 1e3), "n_elems": nel, "threads": cfg["block_threads"],
+                       "grid": cfg["grid"]}
+    if with_error:
+        worst = {"r13": 0.0, "c14": 0.0, "plain": 0.0}
+        for i in sorted(range(len(ms)), key=lambda i: ms[i].n_elems)[:3]:
+            mi = ms[i]
+            rowptr, col = meshes[i].get_pattern()
+            e = sampled_error(mi, rowptr.cpu().numpy(), col.cpu().numpy(), vals[i].cpu().numpy(),
+                              mi.X.astype(np.float32), mi.c.astype(np.float32), n_rows=mi.n_nodes)
+            worst = {k: max(worst[k], e[k]) for k in worst}
+        err["batch512"] = {"mixed": dict(worst, meshes=3)}
     for mesh in meshes:
         mesh.close()
     del meshes, Xs, cs, vals
+
     m = meshgen.config_mesh(4)
-    mesh = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), mem_budget_bytes=16 << 30)
-    nnz = mesh.pattern()
     X, c = dev(m.X, torch.float32), dev(m.c, torch.float32)
-    v = torch.empty(nnz, dtype=torch.float32, device="cuda")
-    t = timed(lambda: mesh.build_K(X, c, "mixed", out=v), 3)
-    info = mesh.info()
-    out["large"] = {"workload": "300^3 bricks (27M elements), 16 GB library budget", "value": m.n_elems / (t / 1e3),
-                    "unit": "elements/s", "ms_per_step": t, "patch_groups": info["n_groups"],
-                    "plan_bytes": info["plan_bytes"]}
-    # its backward: dL/dX (FP32) and dL/dc of L = sum G_ij K_ij, G seeded standard normal
-    G = torch.randn(nnz, generator=torch.Generator(device="cuda").manual_seed(21), device="cuda")
-    tb = timed(lambda: mesh.vjp(X, c, G, "mixed"), 3)
-    mesh.sync()
-    out["large"]["backward"] = {"value": m.n_elems / (tb / 1e3), "unit": "elements/s", "ms_per_step": tb,
-                                "library_bytes": mesh.info()["live_bytes"]}
-    mesh.close()
-    del mesh, X, c, v, G
+    for key, budget in (("large27M", 16 << 30), ("large27M_groups", 7 << 30)):
+        mesh = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), mem_budget_bytes=budget)
+        nnz = mesh.pattern()
+        v = torch.empty(nnz, dtype=torch.float32, device="cuda")
+        t = timed(lambda: mesh.build_K(X, c, "mixed", out=v), 3)
+        info = mesh.info()
+        out[key] = {"ms": t, "value": m.n_elems / (t / 1e3), "budget_gb": budget / 2 ** 30,
+                    "groups": info["n_groups"], "assembly": info["assembly"], "plan_gb": info["plan_bytes"] / 1e9}
+        if with_error:
+            rowptr, col = mesh.get_pattern()
+            err[key] = {"mixed": sampled_error(m, rowptr.cpu().numpy(), col.cpu().numpy(), v.cpu().numpy(),
+                                               m.X.astype(np.float32), m.c.astype(np.float32), n_rows=500)}
+        if key == "large27M":
+            # its backward: dL/dX (FP32) and dL/dc of L = sum G_ij K_ij, G seeded standard normal
+            G = torch.randn(nnz, generator=torch.Generator(device="cuda").manual_seed(21), device="cuda")
+            tb = timed(lambda: mesh.vjp(X, c, G, "mixed"), 3)
+            mesh.sync()
+            out[key]["backward_ms"] = tb
+            out[key]["backward_lib_gb"] = mesh.info()["live_bytes"] / 1e9
+            del G
+        mesh.close()
+        del mesh, v
+    del X, c
     out["elastic"] = elastic_workloads(timed, dev)
     out["backward"] = backward_workloads(timed, dev)
-    return out
+    return out, err
 
 
 def backward_workloads(timed, dev):
     """The backward pass (fem_vjp: dL/dX and dL/dc of L = sum over stored entries
-    G_ij K_ij) on the 1M-brick mesh, for the stiffness operator in both precisions
-    and for the elasticity and mass operators in mixed precision, and on the
-    3.07M-tet mesh for the stiffness and elasticity operators in mixed precision; G is a seeded standard
-    normal upstream on K's pattern.  Algorithmic bytes: X, E, c and G read once,
-    dX and dc written once."""
+    G_ij K_ij, G a seeded standard normal on K's pattern): stiffness on the 1M-brick
+    mesh in both precisions and on the 3.07M-tet mesh, mass and elasticity in mixed
+    precision.  Algorithmic bytes: X, E, c and G read once, dX and dc written once."""
     import numpy as np
     import torch
 
@@ -582,8 +668,7 @@ def backward_workloads(timed, dev):
         nnz = mesh.pattern()
         c = meshgen.lame(m) if op == 2 else m.c
         G = np.random.default_rng(21).standard_normal(nnz)
-        name = "1M-hex8 " if idx == 1 else "3.07M-tet4 "
-        r = {"workload": name + key.split("_")[0] + " backward (dL/dX, dL/dc)", "nnz": nnz}
+        r = {}
         for prec in (("mixed", "fp64") if key == "stiffness" else ("mixed",)):
             dt = torch.float32 if prec == "mixed" else torch.float64
             w = 4 if prec == "mixed" else 8
@@ -591,8 +676,8 @@ def backward_workloads(timed, dev):
             t = timed(lambda: mesh.vjp(X, cd, Gd, prec), 10)
             mesh.sync()
             nb = (m.n_nodes * 3 * w * 2 + m.n_elems * m.npe * 4 + cd.numel() * w * 2 + nnz * w)
-            r[prec] = {"value": m.n_elems / (t / 1e3), "unit": "elements/s", "ms_per_step": t,
-                       "algorithmic_bytes": nb, "achieved_gbs": nb / (t / 1e3) / 1e9}
+            r[prec] = t
+            r[prec + "_gbs"] = nb / (t / 1e3) / 1e9
             del X, cd, Gd
         res[key] = r
         mesh.close()
@@ -619,20 +704,13 @@ def elastic_workloads(timed, dev):
         v = torch.empty(nnz, dtype=torch.float32, device="cuda")
         t = timed(lambda: mesh.build_K(X, c, "mixed", out=v), 10)
         mesh.sync()
-        r = {"workload": ("1M-hex8" if idx == 1 else "3.07M-tet4") + " elasticity, 3 DOFs per node",
-             "value": m.n_elems / (t / 1e3), "unit": "elements/s", "ms_per_step": t, "nnz": nnz,
-             "dof_entries_per_s": nnz / (t / 1e3), "n_patches": mesh.info()["n_patches"],
-             "closure_elems": mesh.info()["closure_elems"]}
+        r = {"ms": t, "dof_entries_per_s": nnz / (t / 1e3)}
         if idx == 1:
-            r["alu"] = {"flops_per_element": ELASTIC_BRICK_FLOPS,
-                        "achieved_tflops": ELASTIC_BRICK_FLOPS * m.n_elems / (t / 1e3) / 1e12,
-                        "frac_of_fp32_peak_2070mhz": ELASTIC_BRICK_FLOPS * m.n_elems / (t / 1e3)
-                        / (SMS * FP32_LANES * 2 * 2070e6)}
+            r["alu_frac_2070mhz"] = ELASTIC_BRICK_FLOPS * m.n_elems / (t / 1e3) / (SMS * FP32_LANES * 2 * 2070e6)
             X64, c64 = dev(m.X, torch.float64), dev(lame, torch.float64)
             v64 = torch.empty(nnz, dtype=torch.float64, device="cuda")
-            t64 = timed(lambda: mesh.build_K(X64, c64, "fp64", out=v64), 3)
+            r["fp64_ms"] = timed(lambda: mesh.build_K(X64, c64, "fp64", out=v64), 3)
             mesh.sync()
-            r["fp64"] = {"value": m.n_elems / (t64 / 1e3), "unit": "elements/s", "ms_per_step": t64}
             del X64, c64, v64
         res[key] = r
         mesh.close()
@@ -652,8 +730,11 @@ def run_once(args):
     elastic = args.operator == "elasticity"
     X64 = torch.from_numpy(m.X).cuda()
     c64 = torch.from_numpy(meshgen.lame(m) if elastic else m.c).cuda()
-    mesh = fem.Mesh(E, m.n_nodes, X=X64, patch_entries=args.patch_entries, block_threads=args.block_threads,
-                    operator_kind=2 if elastic else 0)
+    opts = dict(patch_entries=args.patch_entries, tile_elems=args.tile_elems, block_threads=args.block_threads,
+                operator_kind=2 if elastic else 0)
+    if args.assembly >= 0:
+        opts["assembly"] = args.assembly
+    mesh = fem.Mesh(E, m.n_nodes, X=X64, **opts)
     nnz = mesh.pattern()
     X, c = (X64.float(), c64.float()) if args.once == "mixed" else (X64, c64)
     v = torch.empty(nnz, dtype=X.dtype, device="cuda")

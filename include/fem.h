@@ -122,7 +122,17 @@ typedef struct {
                                     patch; 1 = recomputed in every patch whose closure holds
                                     the element (no library memory; also used when the
                                     budget refuses it or the plan is built per patch group) */
-    int reserved[2];
+    int assembly;                /* scalar operators (stiffness, mass), fem_build_K, the host-
+                                    buffer builds and batched builds: 0 (default) = node
+                                    patches: each patch integrates every element that touches
+                                    the rows it owns; 1 = element tiles: every element is
+                                    integrated once, and a row whose elements span several
+                                    tiles is summed from the tiles' partial rows, in a fixed
+                                    order, by a second kernel (falls back to patches when the
+                                    memory budget cannot hold the tile plan).  Elasticity,
+                                    fem_vjp, fem_load_vector and fem_assemble_csr use patches,
+                                    planned on their first call when tiles serve the builds */
+    int tile_elems;              /* elements per tile (0 = default: 512 bricks, 2048 tetrahedra) */
 } fem_options;
 
 /*
@@ -160,10 +170,17 @@ typedef struct {
     size_t plan_bytes;           /* device bytes held by the cached pattern and plan */
     size_t budget_bytes;         /* the budget in force (0 = none) */
     int32_t n_groups;            /* patch groups the numeric build runs in under the budget */
-    int32_t reserved0;
+    int32_t assembly;            /* what fem_build_K runs on: 0 = node patches, 1 = element tiles
+                                    (then n_patches ... n_colors describe the tiles: n_patches =
+                                    tiles, closure_elems = n_elems, max_patch_entries = the
+                                    largest tile's accumulator entries, max_patch_cnodes its
+                                    rows) */
     size_t live_bytes;           /* device bytes the library holds for the mesh now */
     size_t peak_bytes;           /* the most it has held at once */
     int32_t reserved[2];
+    int64_t tile_rows;           /* rows summed in tiles (a row in k tiles counts k times) */
+    int64_t border_rows;         /* rows whose elements span several tiles */
+    int64_t partial_values;      /* values of the border rows' partial sums */
 } fem_info;
 
 /* Default options (see the field comments). */
@@ -307,16 +324,20 @@ fem_status fem_batched_config(const fem_mesh *meshes, int n, fem_prec p, int *bl
                               int *grid);
 
 typedef struct {
-    int patch_entries;  /* chosen assembly tile: lower-CSR entries per thread block */
+    int patch_entries;  /* chosen work unit of one thread block: elements per tile when the
+                           builds run on element tiles (assembly 1), lower-CSR entries per
+                           patch otherwise */
     int block_threads;  /* chosen threads per block (elements integrated per batch) */
     float ms;           /* median time of one fem_build_K from a cold L2, chosen configuration */
     int tried;          /* candidate configurations timed */
-    int reserved[4];
+    int assembly;       /* 0 = node patches, 1 = element tiles (see fem_info.assembly) */
+    int reserved[3];
 } fem_tuning;
 
 /*
- * Tuner: rebuilds the mesh's plan for each candidate patch size (the assembly
- * tile) and times fem_build_K for each candidate block size on the given inputs
+ * Tuner: rebuilds the mesh's plan for each candidate work unit (elements per tile
+ * when the builds run on element tiles, lower-CSR entries per patch otherwise)
+ * and times fem_build_K for each candidate block size on the given inputs
  * (vals is overwritten): the median of 5 builds, each after a 256 MB scratch
  * rewrite that clears the L2 (skipped when the memory budget has no room for
  * it); the mesh keeps the fastest configuration.  Gauss-point unrolling is not a
@@ -328,9 +349,10 @@ fem_status fem_autotune(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype
 
 /*
  * Apply a tuning chosen earlier (fem_autotune's patch_entries and block_threads,
- * for example from a cache kept by the caller per GPU, element type, precision and
- * operator): sets the two options and rebuilds the plan if the pattern exists
- * (else fem_pattern plans with them).  0 restores a default.  Blocks.
+ * for example from a cache kept by the caller per GPU, element type, precision,
+ * operator and assembly): sets fem_options.tile_elems (builds on element tiles)
+ * or patch_entries (on patches) and block_threads, and rebuilds the plan if the
+ * pattern exists (else fem_pattern plans with them).  0 restores a default.  Blocks.
  * Errors: FEM_ERR_ARG, and those of fem_pattern.
  */
 fem_status fem_set_tuning(fem_mesh m, int patch_entries, int block_threads, void *stream);
@@ -365,10 +387,11 @@ int64_t fem_launch_count(int reset);
  * allocating routine.  Its working memory is one static device array of
  * FEM_NOALLOC_SCRATCH_BYTES (16 MiB) inside the library, which every GPU that
  * loads the library holds until the process exits; the scratch needed is about
- * 24 * n_nodes + 4 * npe * n_elems bytes (about 300,000 bricks).
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current); make that first call
- *     before any stream capture.
+ * 28 * n_nodes + 4 * npe * n_elems bytes (a 64^3 brick grid, 262,144 elements,
+ * fits; 65^3 does not).
+ *   - Every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress); the first call on a device may load the library's
+ *     device code, so make it before any stream capture.
  *   - Every call shares the array and leaves its contents behind; each call
  *     clears what must start at zero.  Calls that overlap on the GPU (other
  *     streams, other host threads) race on the array: serialise them.

@@ -15,7 +15,7 @@ fem_status launch_vjp(fem_mesh m, bool mixed, const void *X, fem_dtype xd, const
                       const void *G, void *dX, void *dc, cudaStream_t s);
 fem_status launch_elastic_vjp(fem_mesh m, bool mixed, const void *X, fem_dtype xd, const void *c, fem_dtype cd,
                               const void *G, void *dX, void *dc, cudaStream_t s);
-fem_status launch_batched(const fem_mesh *ms, int n, bool mixed, const void *const *X, fem_dtype xd,
+fem_status launch_batched(const fem_mesh *ms, int n, bool mixed, bool tiles, const void *const *X, fem_dtype xd,
                           const void *const *c, fem_dtype cd, void *const *vals, cudaStream_t s);
 fem_status batched_query(const fem_mesh *ms, int n, bool mixed, int *threads, int *blocks_per_sm, int *grid);
 void batch_forget(fem_mesh m);
@@ -40,6 +40,26 @@ static float default_threshold(const fem_mesh m) {
     if (m->opt.distortion_threshold > 0) return (float)m->opt.distortion_threshold;
     return m->npe == 8 ? 4.0f : 10.0f;
 }
+
+// Threads per block of the tile kernel (fem_options.block_threads, capped per element type).
+static int tile_threads(const fem_mesh m) {
+    int t = m->opt.block_threads > 0 ? m->opt.block_threads : 256;
+    t = (t + 31) / 32 * 32;
+    return std::min(t, tile_max_threads(m->npe));
+}
+
+// fem_build_K runs on element tiles: scalar operators with a tile plan.
+static bool use_tiles(const fem_mesh m) { return !is_elastic(m) && m->opt.assembly == 1 && m->tiles.ready; }
+
+namespace fem {
+// The patch plan, built on first use when the builds run on tiles.
+fem_status ensure_plan(fem_mesh m, cudaStream_t s) {
+    if (m->plan_built) return FEM_OK;
+    FEM_TRY(build_plan(m, s));
+    m->plan_built = true;
+    return FEM_OK;
+}
+}  // namespace fem
 
 static fem_status check_dtype(fem_dtype d, const char *what) {
     if (d != FEM_F32 && d != FEM_F64) {
@@ -234,7 +254,20 @@ fem_status fem_pattern(fem_mesh m, int64_t *nnz_out, void *stream) {
     }
     if (!m->has_pattern) {
         cudaStream_t s = as_stream(stream);
-        fem_status st = build_pattern_and_plan(m, s);
+        fem_status st = build_pattern(m, s);
+        if (st == FEM_OK) {
+            if (!is_elastic(m) && m->opt.assembly == 1) {
+                st = build_tiles(m, s);
+                if (st == FEM_ERR_BUDGET || st == FEM_ERR_UNSUPPORTED) {
+                    // the budget cannot hold the tile plan (or a tile is out of
+                    // range): the builds run on patches, in groups if need be
+                    m->tiles.reset();
+                    cudaGetLastError();
+                    st = FEM_OK;
+                }
+            }
+            if (st == FEM_OK && !use_tiles(m)) st = ensure_plan(m, s);
+        }
         if (st == FEM_OK) {
             cudaError_t e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) st = cuda_status(e, "fem_pattern");
@@ -243,6 +276,7 @@ fem_status fem_pattern(fem_mesh m, int64_t *nnz_out, void *stream) {
             m->has_pattern = false;
             return st;
         }
+        m->has_pattern = true;
     }
     if (nnz_out) *nnz_out = user_nnz(m);
     return FEM_OK;
@@ -335,12 +369,13 @@ fem_status fem_assemble_csr(fem_mesh m, fem_prec p, const void *ke, void *vals, 
         set_error("ke and vals must be non-null aligned device pointers");
         return FEM_ERR_ARG;
     }
+    cudaStream_t s = as_stream(stream);
+    FEM_TRY(ensure_plan(m, s));
     PatchArgs a = patch_args(m, p, false);
     a.xd = FEM_F32;
     a.cd = FEM_F32;
     a.ke = ke;
     a.vals = vals;
-    cudaStream_t s = as_stream(stream);
     const bool el = is_elastic(m);
     return for_each_group(m, s, [&](const Closure &cl) {
         a.closure = &cl;
@@ -361,6 +396,39 @@ fem_status fem_build_K(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype,
         return FEM_ERR_ARG;
     }
     cudaStream_t s = as_stream(stream);
+    if (use_tiles(m)) {
+        // element tiles: each element integrated once, in the build's precision
+        TilePlan &T = m->tiles;
+        const size_t w = p == FEM_FP64 ? sizeof(double) : sizeof(float);
+        const size_t need = (size_t)std::max<int64_t>(T.partial_n, 1) * w;
+        fem_status st = FEM_OK;
+        if (T.partial.n < need) {
+            batch_forget(m);  // cached batched launches hold the old buffer
+            st = T.partial.alloc(m->arena, need, "tile partial rows");
+        }
+        if (st == FEM_OK) {
+            TileArgs a{};
+            a.plan = &T;
+            a.view = T.view(m);
+            a.npe = m->npe;
+            a.mixed = p == FEM_MIXED;
+            a.xd = x_dtype;
+            a.cd = c_dtype;
+            a.X = X;
+            a.c = c;
+            a.vals = vals;
+            a.part = T.partial.ptr;
+            a.thr = default_threshold(m);
+            a.threads = tile_threads(m);
+            a.blocks_per_sm = m->opt.blocks_per_sm;
+            a.wait = wait_ctl(m);
+            a.mode = kernel_mode(m->opt);
+            return launch_tile(a, s);
+        }
+        if (st != FEM_ERR_BUDGET) return st;
+        cudaGetLastError();  // no room for the partials: patches
+    }
+    FEM_TRY(ensure_plan(m, s));
     if (is_elastic(m)) {
         if (p == FEM_FP64 && m->opt.fp64_fused == 0) {
             // FP64 integrates each element once into library memory (300 or 78
@@ -538,6 +606,7 @@ fem_status fem_vjp(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, con
         set_error("G, dX and dc must be non-null aligned device pointers");
         return FEM_ERR_ARG;
     }
+    FEM_TRY(ensure_plan(m, as_stream(stream)));
     if (is_elastic(m))
         return launch_elastic_vjp(m, p == FEM_MIXED, X, x_dtype, c, c_dtype, G, dX, dc, as_stream(stream));
     return launch_vjp(m, p == FEM_MIXED, X, x_dtype, c, c_dtype, G, dX, dc, as_stream(stream));
@@ -555,6 +624,7 @@ fem_status fem_load_vector(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dt
         set_error("F must be a non-null aligned device pointer");
         return FEM_ERR_ARG;
     }
+    FEM_TRY(ensure_plan(m, as_stream(stream)));
     return launch_load(m, p == FEM_MIXED, X, x_dtype, src, src_dtype, F, default_threshold(m), m->opt.fp64_dets != 0,
                        as_stream(stream));
 }
@@ -578,12 +648,30 @@ fem_status fem_build_K_batched(const fem_mesh *meshes, int n, fem_prec p, const 
         }
     }
     if (n == 0) return FEM_OK;
-    for (int i = 0; i < n; ++i)
-        if (meshes[i]->plan.chunked) {
-            set_error("mesh %d of the batch is planned in groups under its memory budget", i);
-            return FEM_ERR_UNSUPPORTED;
+    cudaStream_t s = as_stream(stream);
+    // element tiles when every mesh of the batch builds on them (each mesh's
+    // partials buffer sized for the precision first), else patches
+    bool tiles = true;
+    for (int i = 0; i < n; ++i) tiles = tiles && use_tiles(meshes[i]);
+    if (tiles) {
+        const size_t w = p == FEM_FP64 ? sizeof(double) : sizeof(float);
+        for (int i = 0; i < n; ++i) {
+            TilePlan &T = meshes[i]->tiles;
+            const size_t need = (size_t)std::max<int64_t>(T.partial_n, 1) * w;
+            if (T.partial.n < need) {
+                batch_forget(meshes[i]);  // cached launches hold the old buffer
+                FEM_TRY(T.partial.alloc(meshes[i]->arena, need, "tile partial rows"));
+            }
         }
-    return launch_batched(meshes, n, p == FEM_MIXED, X, x_dtype, c, c_dtype, vals, as_stream(stream));
+    } else {
+        for (int i = 0; i < n; ++i) FEM_TRY(ensure_plan(meshes[i], s));
+        for (int i = 0; i < n; ++i)
+            if (meshes[i]->plan.chunked) {
+                set_error("mesh %d of the batch is planned in groups under its memory budget", i);
+                return FEM_ERR_UNSUPPORTED;
+            }
+    }
+    return launch_batched(meshes, n, p == FEM_MIXED, tiles, X, x_dtype, c, c_dtype, vals, s);
 }
 
 fem_status fem_batched_config(const fem_mesh *meshes, int n, fem_prec p, int *block_threads, int *blocks_per_sm,
@@ -592,12 +680,18 @@ fem_status fem_batched_config(const fem_mesh *meshes, int n, fem_prec p, int *bl
         set_error("bad batch arguments");
         return FEM_ERR_ARG;
     }
+    for (int i = 0; i < n; ++i)
+        if (!meshes[i] || !meshes[i]->has_pattern) {
+            set_error("mesh %d of the batch has no pattern", i);
+            return FEM_ERR_STATE;
+        }
     return batched_query(meshes, n, p == FEM_MIXED, block_threads, blocks_per_sm, grid);
 }
 
-// Tuner of the assembly tile (patch size) and of the threads per block: the
-// plan is rebuilt for each candidate patch size and every candidate is timed on
-// the caller's inputs; the mesh keeps the fastest.
+// Tuner of the assembly tile and of the threads per block: the plan is rebuilt
+// for each candidate size (elements per tile when the builds run on tiles,
+// lower-CSR entries per patch otherwise) and every candidate is timed on the
+// caller's inputs; the mesh keeps the fastest.
 fem_status fem_autotune(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c, fem_dtype c_dtype,
                         void *vals, void *stream, fem_tuning *out) {
     NvtxRange nvtx_range("fem_autotune");
@@ -611,13 +705,23 @@ fem_status fem_autotune(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype
         return FEM_ERR_ARG;
     }
     cudaStream_t s = as_stream(stream);
+    const bool tiles = use_tiles(m);
     const fem_options keep = m->opt;
     static const int entries_scalar[] = {4096, 6144, 8192, 12288, 16384};
     static const int entries_elastic[] = {1536, 2048, 3072, 4096, 5120};
+    static const int tiles_brick[] = {256, 384, 512, 768, 1024};
+    static const int tiles_tet[] = {512, 1024, 1536, 2048, 2048};
     static const int threads_scalar[] = {128, 256, 512};
     static const int threads_elastic[] = {256, 512, 512};
-    const int *entries = is_elastic(m) ? entries_elastic : entries_scalar;
+    const int *sizes = tiles ? (m->npe == 8 ? tiles_brick : tiles_tet)
+                             : (is_elastic(m) ? entries_elastic : entries_scalar);
     const int *threads = is_elastic(m) ? threads_elastic : threads_scalar;
+    auto replan = [&](cudaStream_t st) -> fem_status {
+        if (tiles) return build_tiles(m, st);
+        fem_status r = build_plan(m, st);
+        if (r == FEM_OK) m->plan_built = true;
+        return r;
+    };
     float best = 1e30f;
     int best_e = 0, best_t = 0, tried = 0;
     cudaEvent_t e0, e1;
@@ -630,15 +734,22 @@ fem_status fem_autotune(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype
     const size_t flush_bytes = (size_t)256 << 20;
     if (flush.alloc(m->arena, flush_bytes, "tuner L2 flush") != FEM_OK) cudaGetLastError();
     for (int ie = 0; ie < 5; ++ie) {
-        const int pe = entries[ie];
-        m->opt = keep;
-        m->opt.patch_entries = pe;
-        if (build_plan(m, s) != FEM_OK) continue;
+        const int pe = sizes[ie];
+        if (ie > 0 && pe == sizes[ie - 1]) continue;
         for (int it = 0; it < 3; ++it) {
             const int t = threads[it];
             if (it > 0 && t == threads[it - 1]) continue;
+            if (tiles && t > tile_max_threads(m->npe)) continue;
+            m->opt = keep;
+            if (tiles) m->opt.tile_elems = pe; else m->opt.patch_entries = pe;
             m->opt.block_threads = t;
             m->opt.blocks_per_sm = 0;
+            // the plan does not depend on the block size
+            if (it == 0 && replan(s) != FEM_OK) {
+                cudaGetLastError();
+                if (tiles) continue;
+                break;
+            }
             if (fem_build_K(m, p, X, x_dtype, c, c_dtype, vals, stream) != FEM_OK) continue;
             float rep[5];
             for (int r = 0; r < 5; ++r) {
@@ -663,19 +774,20 @@ fem_status fem_autotune(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype
     cudaEventDestroy(e1);
     m->opt = keep;
     if (!tried) {
-        FEM_TRY(build_plan(m, s));
+        FEM_TRY(replan(s));
         set_error("no candidate configuration ran");
         return FEM_ERR_UNSUPPORTED;
     }
-    m->opt.patch_entries = best_e;
+    if (tiles) m->opt.tile_elems = best_e; else m->opt.patch_entries = best_e;
     m->opt.block_threads = best_t;
-    FEM_TRY(build_plan(m, s));
+    FEM_TRY(replan(s));
     if (out) {
         std::memset(out, 0, sizeof(*out));
         out->patch_entries = best_e;
         out->block_threads = best_t;
         out->ms = best;
         out->tried = tried;
+        out->assembly = tiles ? 1 : 0;
     }
     return FEM_OK;
 }
@@ -687,12 +799,18 @@ fem_status fem_set_tuning(fem_mesh m, int patch_entries, int block_threads, void
         set_error("bad tuning arguments");
         return FEM_ERR_ARG;
     }
-    m->opt.patch_entries = patch_entries;
+    const bool tiles = use_tiles(m) || (!m->has_pattern && !is_elastic(m) && m->opt.assembly == 1);
+    if (tiles) m->opt.tile_elems = patch_entries; else m->opt.patch_entries = patch_entries;
     m->opt.block_threads = block_threads;
     m->opt.blocks_per_sm = 0;
     if (!m->has_pattern) return FEM_OK;  // fem_pattern will plan with these settings
     cudaStream_t s = as_stream(stream);
-    fem_status st = build_plan(m, s);
+    fem_status st = FEM_OK;
+    if (use_tiles(m)) {
+        st = build_tiles(m, s);
+    } else if (m->plan_built) {
+        st = build_plan(m, s);
+    }
     if (st == FEM_OK) {
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_status(e, "fem_set_tuning");
@@ -717,14 +835,30 @@ fem_status fem_mesh_info(fem_mesh m, fem_info *info) {
     info->n_nodes = m->n_nodes;
     info->n_elems = m->n_elems;
     info->nnz = user_nnz(m);
-    info->n_patches = m->plan.n_patches;
-    info->closure_elems = m->plan.total_celems;
-    info->max_patch_entries = m->plan.max_acc;
-    info->max_patch_cnodes = m->plan.max_cnodes;
-    info->max_patch_elems = m->plan.max_celems;
-    info->n_colors = m->plan.n_colors;
+    if (use_tiles(m)) {
+        const TilePlan &T = m->tiles;
+        info->assembly = 1;
+        info->n_patches = T.n_tiles;
+        info->closure_elems = m->n_elems;
+        info->max_patch_entries = T.max_acc;
+        info->max_patch_cnodes = T.max_tnodes;
+        info->max_patch_elems = T.max_elems;
+        info->n_colors = T.n_colors;
+        info->tile_rows = T.n_tnodes;
+        info->border_rows = T.n_brows;
+        info->partial_values = T.partial_n;
+    } else {
+        info->assembly = 0;
+        info->n_patches = m->plan.n_patches;
+        info->closure_elems = m->plan.total_celems;
+        info->max_patch_entries = m->plan.max_acc;
+        info->max_patch_cnodes = m->plan.max_cnodes;
+        info->max_patch_elems = m->plan.max_celems;
+        info->n_colors = m->plan.n_colors;
+    }
     info->max_row_len = m->max_row_len;
-    info->plan_bytes = m->plan.bytes() + m->rowptr.bytes() + m->col.bytes() + m->inc_ptr.bytes() + m->inc_elem.bytes();
+    info->plan_bytes = m->plan.bytes() + m->tiles.bytes() + m->rowptr.bytes() + m->col.bytes() + m->inc_ptr.bytes() +
+                       m->inc_elem.bytes();
     info->budget_bytes = m->arena.budget;
     info->n_groups = m->n_groups;
     info->live_bytes = m->arena.live;

@@ -4,7 +4,8 @@
 // A batch context is keyed by the exact list of mesh handles, the precision and
 // the dtypes.  On first use it lays out a device table of per-mesh descriptors
 // (plan view, input and output pointers) and the prefix sums of the meshes'
-// patch counts (the work table of the persistent kernel), picks the kernel's
+// work units -- element tiles, or patches where the meshes build on patches --
+// (the work table of the persistent kernel), picks the kernel's
 // threads per block and blocks per SM by timing the candidates on the real batch
 // (the tuner), and captures the single launch into a CUDA graph.  Later calls
 // with the same meshes only refresh the descriptor table (inputs and outputs may
@@ -25,8 +26,12 @@ struct BatchCtx {
     fem_dtype xd = FEM_F32, cd = FEM_F32;
     int npe = 8;
     bool elastic = false;  // the elasticity operator (operator_kind 2)
+    bool tiles = false;    // the meshes build on element tiles
     BatchItem *d_items = nullptr;
+    TileBatchItem *d_titems = nullptr;
+    std::vector<TileBatchItem> h_titems;
     int64_t *d_prefix = nullptr;
+    int64_t *d_bprefix = nullptr;  // tiles: prefix sums of the border rows
     std::vector<BatchItem> h_items;
     BatchLaunch bl;
     cudaGraph_t graph = nullptr;
@@ -37,7 +42,9 @@ struct BatchCtx {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (d_items) cudaFree(d_items);
+        if (d_titems) cudaFree(d_titems);
         if (d_prefix) cudaFree(d_prefix);
+        if (d_bprefix) cudaFree(d_bprefix);
     }
 };
 
@@ -61,6 +68,14 @@ static float mesh_threshold(fem_mesh m) {
 }
 
 static void fill_items(BatchCtx &c, const void *const *X, const void *const *cc, void *const *vals) {
+    if (c.tiles) {
+        for (size_t i = 0; i < c.meshes.size(); ++i) {
+            const fem_mesh m = c.meshes[i];
+            c.h_titems[i] = TileBatchItem{m->tiles.view(m), X[i], cc[i], vals[i], m->tiles.partial.ptr,
+                                          mesh_threshold(m), 0};
+        }
+        return;
+    }
     for (size_t i = 0; i < c.meshes.size(); ++i) {
         c.h_items[i] = BatchItem{c.meshes[i]->plan.view(), X[i], cc[i], vals[i], mesh_threshold(c.meshes[i]), 0};
         // the elasticity operator's values: the DOF matrix (bounds of the debug build)
@@ -71,24 +86,41 @@ static void fill_items(BatchCtx &c, const void *const *X, const void *const *cc,
 static fem_status upload_items(BatchCtx &c, cudaStream_t s) {
     // pageable source: the copy is staged before the call returns, so the host
     // table can be refilled by the next call at once
-    FEM_CUDA(cudaMemcpyAsync(c.d_items, c.h_items.data(), c.h_items.size() * sizeof(BatchItem),
-                             cudaMemcpyHostToDevice, s));
+    if (c.tiles)
+        FEM_CUDA(cudaMemcpyAsync(c.d_titems, c.h_titems.data(), c.h_titems.size() * sizeof(TileBatchItem),
+                                 cudaMemcpyHostToDevice, s));
+    else
+        FEM_CUDA(cudaMemcpyAsync(c.d_items, c.h_items.data(), c.h_items.size() * sizeof(BatchItem),
+                                 cudaMemcpyHostToDevice, s));
     return FEM_OK;
 }
 
 static fem_status create_ctx(BatchCtx &c, const void *const *X, const void *const *cc, void *const *vals,
                              cudaStream_t s) {
     const int n = (int)c.meshes.size();
-    std::vector<int64_t> prefix(n + 1, 0);
+    std::vector<int64_t> prefix(n + 1, 0), bprefix(n + 1, 0);
     PlanMax pm;
+    TileMax tm;
     for (int i = 0; i < n; ++i) {
-        prefix[i + 1] = prefix[i] + c.meshes[i]->plan.n_patches;
-        pm.add(c.meshes[i]->plan);
+        if (c.tiles) {
+            prefix[i + 1] = prefix[i] + c.meshes[i]->tiles.n_tiles;
+            bprefix[i + 1] = bprefix[i] + c.meshes[i]->tiles.n_brows;
+            tm.add(c.meshes[i]->tiles);
+        } else {
+            prefix[i + 1] = prefix[i] + c.meshes[i]->plan.n_patches;
+            pm.add(c.meshes[i]->plan);
+        }
     }
-    FEM_CUDA(cudaMalloc(&c.d_items, n * sizeof(BatchItem)));
+    if (c.tiles) FEM_CUDA(cudaMalloc(&c.d_titems, n * sizeof(TileBatchItem)));
+    else FEM_CUDA(cudaMalloc(&c.d_items, n * sizeof(BatchItem)));
     FEM_CUDA(cudaMalloc(&c.d_prefix, (n + 1) * sizeof(int64_t)));
     FEM_CUDA(cudaMemcpyAsync(c.d_prefix, prefix.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    if (c.tiles) {
+        FEM_CUDA(cudaMalloc(&c.d_bprefix, (n + 1) * sizeof(int64_t)));
+        FEM_CUDA(cudaMemcpyAsync(c.d_bprefix, bprefix.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    }
     c.h_items.resize(n);
+    c.h_titems.resize(n);
     fill_items(c, X, cc, vals);
     FEM_TRY(upload_items(c, s));
 
@@ -101,10 +133,12 @@ static fem_status create_ctx(BatchCtx &c, const void *const *X, const void *cons
             for (int t : {128, 256, 512})
                 if (t <= elastic_threads(c.npe, 512)) cands.push_back({t, 0});
     } else if (o.block_threads > 0) {
-        cands.push_back({std::min((o.block_threads + 31) / 32 * 32, patch_max_threads(c.npe)), o.blocks_per_sm});
+        const int cap = c.tiles ? tile_max_threads(c.npe) : patch_max_threads(c.npe);
+        cands.push_back({std::min((o.block_threads + 31) / 32 * 32, cap), o.blocks_per_sm});
     } else {
+        const int cap = c.tiles ? tile_max_threads(c.npe) : patch_max_threads(c.npe);
         for (int t : {128, 256, 512})
-            if (t <= patch_max_threads(c.npe))
+            if (t <= cap)
                 for (int b : {0, 1}) cands.push_back({t, b});
     }
     cudaEvent_t e0, e1;
@@ -116,11 +150,14 @@ static fem_status create_ctx(BatchCtx &c, const void *const *X, const void *cons
     for (auto &cd : cands) {
         BatchLaunch bl;
         bl.items = c.d_items;
+        bl.titems = c.d_titems;
+        bl.bprefix = c.d_bprefix;
         bl.prefix = c.d_prefix;
         bl.n = n;
         bl.mode = kernel_mode(c.meshes[0]->opt);
         bl.wait = wait_ctl(c.meshes[0]);
         const fem_status cs = c.elastic ? elastic_batched_config(c.npe, c.mixed, pm, cd.first, cd.second, &bl)
+                              : c.tiles ? tile_batched_config(c.npe, c.mixed, tm, cd.first, cd.second, &bl)
                                         : batched_config(c.npe, c.mixed, pm, cd.first, cd.second, &bl);
         if (cs != FEM_OK) continue;
         FEM_TRY(launch_batched_kernel(bl, s));  // warm-up
@@ -167,10 +204,10 @@ static fem_status create_ctx(BatchCtx &c, const void *const *X, const void *cons
     return FEM_OK;
 }
 
-static BatchCtx *find_ctx(const fem_mesh *ms, int n, bool mixed, fem_dtype xd, fem_dtype cd) {
+static BatchCtx *find_ctx(const fem_mesh *ms, int n, bool mixed, bool tiles, fem_dtype xd, fem_dtype cd) {
     for (auto it = g_batch_ctx.begin(); it != g_batch_ctx.end(); ++it) {
         BatchCtx &c = **it;
-        if (c.mixed != mixed || c.xd != xd || c.cd != cd || (int)c.meshes.size() != n) continue;
+        if (c.mixed != mixed || c.tiles != tiles || c.xd != xd || c.cd != cd || (int)c.meshes.size() != n) continue;
         if (!std::equal(c.meshes.begin(), c.meshes.end(), ms)) continue;
         // move to the back (most recent)
         std::unique_ptr<BatchCtx> p = std::move(*it);
@@ -181,7 +218,7 @@ static BatchCtx *find_ctx(const fem_mesh *ms, int n, bool mixed, fem_dtype xd, f
     return nullptr;
 }
 
-fem_status launch_batched(const fem_mesh *ms, int n, bool mixed, const void *const *X, fem_dtype xd,
+fem_status launch_batched(const fem_mesh *ms, int n, bool mixed, bool tiles, const void *const *X, fem_dtype xd,
                           const void *const *c, fem_dtype cd, void *const *vals, cudaStream_t s) {
     const int npe = ms[0]->npe;
     const bool elastic = ms[0]->opt.operator_kind == 2;
@@ -196,11 +233,12 @@ fem_status launch_batched(const fem_mesh *ms, int n, bool mixed, const void *con
         return FEM_ERR_UNSUPPORTED;
     }
     std::lock_guard<std::mutex> lock(g_batch_mu);
-    BatchCtx *ctx = find_ctx(ms, n, mixed, xd, cd);
+    BatchCtx *ctx = find_ctx(ms, n, mixed, tiles, xd, cd);
     if (!ctx) {
         auto nc = std::make_unique<BatchCtx>();
         nc->meshes.assign(ms, ms + n);
         nc->mixed = mixed;
+        nc->tiles = tiles;
         nc->xd = xd;
         nc->cd = cd;
         nc->npe = npe;

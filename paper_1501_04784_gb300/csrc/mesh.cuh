@@ -14,6 +14,7 @@
 #include <functional>
 
 #include "common.cuh"
+#include "tile.cuh"
 
 namespace fem {
 
@@ -144,6 +145,8 @@ struct fem_mesh_s {
     fem::DevBuf<int64_t> inc_ptr;  // node -> incident elements (kept for the backward pass)
     fem::DevBuf<int32_t> inc_elem;
     fem::Plan plan;
+    bool plan_built = false;  // the patch plan exists (it is built on first use when tiles serve the builds)
+    fem::TilePlan tiles;      // element tiles of the scalar operators (tile.cuh)
     // device status word: set by a bounded device-side wait that gave up
     fem::DevBuf<int> status;
     // staging of the host-buffer entry points: HOST_STAGES slots used in turn, so

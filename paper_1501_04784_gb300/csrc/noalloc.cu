@@ -8,8 +8,6 @@
 // output arrays, and the working memory of the symbolic phase (node degrees,
 // node -> element incidence, row counts, scan partials) lives in one
 // fixed-size array of device memory that is part of the library image.
-#include <mutex>
-
 #include "mesh.cuh"
 
 namespace fem {
@@ -23,31 +21,19 @@ fem_status pattern_steps_rows(const int32_t *E, int npe, int64_t N, const int64_
 
 // 16 MiB of scratch, held by every GPU that loads the library until the process
 // exits.  In host code `g_pattern_scratch` is only a stand-in for the symbol:
-// its device address comes from cudaGetSymbolAddress, once per device.
+// its device address comes from cudaGetSymbolAddress, with the device current.
 static constexpr size_t NOALLOC_SCRATCH_BYTES = FEM_NOALLOC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_pattern_scratch[NOALLOC_SCRATCH_BYTES];
 
-static std::mutex g_scratch_mu;
-static constexpr int MAX_DEVICES = 64;
-static unsigned char *g_scratch_addr[MAX_DEVICES] = {};
-
-// Device address of the scratch array on the current device (set up on the
-// first call per device, with that device current).
+// Device address of the scratch array on the current device, looked up on every
+// call (it allocates nothing and costs little): an address kept from an earlier
+// call would dangle after a reset of the device's primary context, which loads
+// the library's device code again.
 static fem_status scratch_address(unsigned char **out) {
-    int dev = 0;
-    FEM_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= MAX_DEVICES) {
-        set_error("device ordinal %d out of range", dev);
-        return FEM_ERR_UNSUPPORTED;
-    }
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_pattern_scratch);
-        if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(pattern scratch)");
-        g_scratch_addr[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_pattern_scratch);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(pattern scratch)");
+    *out = static_cast<unsigned char *>(p);
     return FEM_OK;
 }
 

@@ -103,6 +103,37 @@ struct BatchItem {
     int pad;
 };
 
+// Shared memory of the tile kernels (byte offsets) and the largest tile sizes
+// over the plans a launch covers.
+struct TileSmem {
+    size_t acc, hv, xs;                          // accumulators, FP64-accurate diagonals, coordinates
+    size_t s_id, s_col, s_ln, s_pos;             // staged element slices of the tile (bulk copies)
+    size_t s_gid, s_info, s_dest;                // staged row slices of the tile (bulk copies)
+    size_t total;
+    int hv_on;     // the plans have FP64-accurate diagonals
+    int wg_shift;  // log2 of the lanes that store one row
+};
+struct TileMax {
+    int64_t max_acc = 0, max_epad = 0, max_npad = 0;
+    bool any_hv = false;
+    void add(const TilePlan &T) {
+        any_hv = any_hv || T.any_hv;
+        max_acc = std::max(max_acc, T.max_acc);
+        max_epad = std::max(max_epad, T.max_epad);
+        max_npad = std::max(max_npad, T.max_npad);
+    }
+};
+TileSmem tile_smem_layout(const TileMax &T, int npe, bool mixed, size_t xsize);
+
+// One mesh of a batched build on element tiles.
+struct TileBatchItem {
+    TileView tv;
+    const void *X, *c;
+    void *vals, *part;
+    float thr;
+    int pad;
+};
+
 struct BatchLaunch {
     int npe = 8;
     bool mixed = true;
@@ -115,6 +146,11 @@ struct BatchLaunch {
     WaitCtl wait{nullptr, WAIT_SPINS_DEFAULT, 0};
     bool elastic = false;  // the elasticity operator's kernel (elastic.cu)
     bool win = false;      // its row-window variant (the FP64 blocks outgrow shared memory)
+    bool tiles = false;    // the element-tile kernel (tile.cu) over titems
+    const TileBatchItem *titems = nullptr;
+    const int64_t *bprefix = nullptr;  // tiles: prefix sums of the meshes' border rows (the combine's work)
+    TileSmem tl{};
+    int combine_grid = 1;
 };
 
 // Shared memory, residency and grid of the batched kernel for `threads` threads
@@ -131,6 +167,29 @@ inline unsigned kernel_mode(const fem_options &o) {
     return (o.fp64_sums ? FP64_SUMS : 0u) | (o.fp64_dets ? FP64_DETS : 0u) | (o.operator_kind == 1 ? OP_MASS : 0u);
 }
 fem_status launch_patch(const PatchArgs &a, cudaStream_t s);
+
+// Element-tile build of the scalar operators (tile.cu, tile_plan.cu).
+struct TileArgs {
+    const TilePlan *plan;
+    TileView view;
+    int npe;
+    bool mixed;
+    fem_dtype xd, cd;
+    const void *X, *c;
+    void *vals;
+    void *part;  // the plan's partials buffer, partial_n values of the build's precision
+    float thr;
+    int threads, blocks_per_sm;
+    WaitCtl wait;
+    unsigned mode;  // FP64_SUMS, FP64_DETS, OP_MASS
+};
+fem_status launch_tile(const TileArgs &a, cudaStream_t s);
+fem_status tile_batched_config(int npe, bool mixed, const TileMax &tm, int threads, int blocks_per_sm,
+                               BatchLaunch *out);
+fem_status launch_tile_batched_kernel(const BatchLaunch &bl, cudaStream_t s);
+int tile_blocks_per_sm(int npe, int threads);
+// Element tiles of mesh m (after its pattern).
+fem_status build_tiles(fem_mesh m, cudaStream_t s);
 PatchSmem patch_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsize, size_t csize);
 
 // Elasticity operator (three DOFs per node, elastic.cu): the patch kernel over the

@@ -545,6 +545,15 @@ __global__ void k_celem_fill(const uint64_t *ckeys, int64_t nce, const int32_t *
     }
 }
 
+// Shared memory of the row-pattern kernel above the 48 KB default (a node in up
+// to 2048 / npe elements needs up to 64 KB for 8 warps): opted in per launch.
+static fem_status row_pattern_smem(int npe, size_t smem) {
+    if (smem <= (48u << 10)) return FEM_OK;
+    if (npe == 8) FEM_CUDA(cudaFuncSetAttribute(k_row_pattern<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    else FEM_CUDA(cudaFuncSetAttribute(k_row_pattern<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return FEM_OK;
+}
+
 // --------------------------------------------------------------- orchestration
 static int bits_for(int64_t v) {
     int b = 1;
@@ -629,6 +638,7 @@ fem_status build_pattern(fem_mesh m, cudaStream_t s) {
         const int wpb = 8;
         const size_t smem = (size_t)wpb * (cap > 0 ? cap : 1) * sizeof(int32_t);
         const unsigned grid = (unsigned)std::min<int64_t>(cdiv(N, wpb), (int64_t)num_sms() * 64);
+        FEM_TRY(row_pattern_smem((int)npe, smem));
         if (npe == 8)
             k_row_pattern<8><<<grid, wpb * 32, smem, s>>>(m->E, m->inc_ptr.ptr, m->inc_elem.ptr, N, cap, cnt.ptr,
                                                           nullptr, nullptr);
@@ -1070,6 +1080,7 @@ fem_status pattern_steps_rows(const int32_t *E, int npe, int64_t N, const int64_
     const int wpb = 8;
     const size_t smem = (size_t)wpb * (cap > 0 ? cap : 1) * sizeof(int32_t);
     const unsigned grid = (unsigned)std::min<int64_t>(cdiv(N, wpb), (int64_t)num_sms() * 64);
+    FEM_TRY(row_pattern_smem(npe, smem));
     if (npe == 8)
         k_row_pattern<8><<<grid, wpb * 32, smem, s>>>(E, inc_ptr, inc_elem, N, cap, cnt, rowptr, col);
     else

@@ -207,8 +207,10 @@ __device__ __forceinline__ void brick_vjp(const S (*xc)[3], T c, const T (&Sp)[3
                                     m4 * C0.z + m5 * C1.z + m2 * C2.z};
                 const T phi = dot3(C0, Y0) + dot3(C1, Y1) + dot3(C2, Y2);
                 dc += phi * inv;
-                // 1/d = sign(d) / |d|: one division per point, not two
-                const T lam = (d < T(0) ? -phi : phi) * inv * inv, t = T(2) * inv;
+                // 1/d = sign(d) / |d|: one division per point, not two; phi is scaled by
+                // 1/|d| before the second factor, so no 1/d^2 is ever formed (it would
+                // overflow FP32 for |d| below ~1e-19 where phi/|d|^2 stays finite)
+                const T lam = ((d < T(0) ? -phi : phi) * inv) * inv, t = T(2) * inv;
                 const Vec3<T> a0 = cross3(Y1, U), b0 = cross3(Sv, Y2);
                 const Vec3<T> a1 = cross3(U, Y0), b1 = cross3(Y2, R);
                 const Vec3<T> a2 = cross3(Y0, Sv), b2 = cross3(R, Y1);

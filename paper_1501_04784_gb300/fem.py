@@ -198,7 +198,8 @@ class Mesh:
         return out
 
     def autotune(self, X, c, prec="mixed", stream=None, cache: str | None = None) -> dict:
-        """Pick the patch size and block size by timing fem_build_K (overwrites a scratch vals).
+        """Pick the work unit (elements per tile, or entries per patch) and block size by
+        timing fem_build_K (overwrites a scratch vals).
 
         With ``cache`` (a JSON file path), a tuning stored for the same GPU model,
         element type, precision, operator and mesh size class (elements to the
@@ -212,7 +213,8 @@ class Mesh:
             import math
             import os
             key = "|".join([torch.cuda.get_device_name(X.device), f"npe={self.npe}", prec,
-                            f"op={self.options.operator_kind}", f"log2n={round(math.log2(max(self.n_elems, 1)))}"])
+                            f"op={self.options.operator_kind}", f"asm={self.options.assembly}",
+                            f"log2n={round(math.log2(max(self.n_elems, 1)))}"])
             table = json.load(open(cache)) if os.path.exists(cache) else {}
             if key in table:
                 hit = table[key]
@@ -224,7 +226,8 @@ class Mesh:
         t = abi.fem_tuning()
         abi.check(abi.load().fem_autotune(self._h, _prec(prec), _dev(X, "X"), _DT[X.dtype], _dev(c, "c"),
                                           _DT[c.dtype], _dev(vals, "vals"), _stream(stream), ctypes.byref(t)))
-        out = dict(patch_entries=t.patch_entries, block_threads=t.block_threads, ms=t.ms, tried=t.tried)
+        out = dict(patch_entries=t.patch_entries, block_threads=t.block_threads, ms=t.ms, tried=t.tried,
+                   assembly=t.assembly)
         if key is not None:
             table = json.load(open(cache)) if os.path.exists(cache) else {}
             table[key] = dict(patch_entries=out["patch_entries"], block_threads=out["block_threads"], ms=out["ms"])

@@ -37,11 +37,13 @@ def small_batch(n, kind="hex"):
     return out
 
 
+@pytest.mark.parametrize("assembly", [0, 1], ids=["patches", "tiles"])
 @pytest.mark.parametrize("kind,prec", [("hex", "mixed"), ("tet", "mixed"), ("hex", "fp64")])
-def test_batched_equals_single_builds(fem, kind, prec):
+def test_batched_equals_single_builds(fem, kind, prec, assembly):
     ms = small_batch(17, kind)
     dt = torch.float32 if prec == "mixed" else torch.float64
-    meshes = [fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), patch_entries=512) for m in ms]
+    meshes = [fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), patch_entries=512,
+                       tile_elems=64, assembly=assembly) for m in ms]
     Xs = [dev(m.X, dt) for m in ms]
     cs = [dev(m.c, dt) for m in ms]
     single = [mesh.build_K(X, c, prec).clone() for mesh, X, c in zip(meshes, Xs, cs)]
@@ -107,6 +109,19 @@ def test_fp64_staged_and_fused_agree(fem):
     assert np.abs(staged - fused).max() <= 1e-14 * np.abs(ref["cs"]).max()
 
 
+def test_autotune_tiles(fem):
+    """The tuner on a mesh that builds on element tiles picks a tile size."""
+    m = meshgen.config_mesh(0)
+    mesh = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), assembly=1)
+    X, c = dev(m.X, torch.float32), dev(m.c, torch.float32)
+    t = mesh.autotune(X, c, "mixed")
+    assert t["assembly"] == 1 and t["tried"] >= 3 and t["patch_entries"] in (256, 384, 512, 768, 1024)
+    assert mesh.info()["assembly"] == 1
+    vals = mesh.build_K(X, c, "mixed").cpu().numpy()
+    ref = oracle_K(m, m.X.astype(np.float32), m.c.astype(np.float32))
+    assert rel_err(vals, ref["vals"], ref["cs"]) <= TOL_MIXED
+
+
 def test_budget_too_small_for_one_patch(fem):
     from paper_1501_04784_gb300 import abi
     m = meshgen.hex_grid(12, jitter=0.2, seed=5)
@@ -120,7 +135,7 @@ def test_autotune_keeps_values_in_tolerance(fem):
     mesh = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64))
     X, c = dev(m.X, torch.float32), dev(m.c, torch.float32)
     t = mesh.autotune(X, c, "mixed")
-    assert t["tried"] >= 3 and t["patch_entries"] in (4096, 6144, 8192, 12288, 16384)
+    assert t["assembly"] == 0 and t["tried"] >= 3 and t["patch_entries"] in (4096, 6144, 8192, 12288, 16384)
     vals = mesh.build_K(X, c, "mixed").cpu().numpy()
     ref = oracle_K(m, m.X.astype(np.float32), m.c.astype(np.float32))
     assert rel_err(vals, ref["vals"], ref["cs"]) <= TOL_MIXED

@@ -49,6 +49,10 @@ MESHES = {
     "tet_6x4x3": lambda: meshgen.kuhn_tets(6, 4, 3, jitter=0.3, seed=2, permute_nodes=True, permute_elems=True),
 }
 PATCH_CAPS = {"default": 0, "tiny": 64}
+# the two assemblies of the scalar operators: node patches (default) and element
+# tiles (each element integrated once, border rows summed from tile partials);
+# tiny tiles make most rows border rows
+ASSEMBLIES = {"patches": {}, "tiles": dict(assembly=1), "tiles_tiny": dict(assembly=1, tile_elems=8)}
 
 
 @pytest.mark.parametrize("cap", list(PATCH_CAPS))
@@ -87,6 +91,28 @@ def test_build_K(fem, name, prec, cap):
     vals = mesh.build_K(Xd, cd, prec).cpu().numpy()
     err = rel_err(vals, ref["vals"], ref["cs"])
     assert err <= (TOL_FP64 if prec == "fp64" else TOL_MIXED), err
+
+
+@pytest.mark.parametrize("asm", ["tiles", "tiles_tiny"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", list(MESHES))
+def test_build_K_tiles(fem, name, prec, asm):
+    """The element-tile assembly: every value against the oracle, the same build
+    twice bitwise equal, and the same values from any block size (the plan fixes
+    every sum's order)."""
+    m = MESHES[name]()
+    mesh = make(fem, m, **ASSEMBLIES[asm])
+    Xd, cd, X, c = inputs(m, prec)
+    ref = oracle_K(m, X, c)
+    nnz = mesh.pattern()
+    assert mesh.info()["assembly"] == 1
+    assert nnz == ref["nnz"]
+    vals = mesh.build_K(Xd, cd, prec)
+    err = rel_err(vals.cpu().numpy(), ref["vals"], ref["cs"])
+    assert err <= (TOL_FP64 if prec == "fp64" else TOL_MIXED), err
+    assert torch.equal(vals, mesh.build_K(Xd, cd, prec))
+    other = make(fem, m, block_threads=128, **ASSEMBLIES[asm])
+    assert torch.equal(vals, other.build_K(Xd, cd, prec))
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])

@@ -12,7 +12,7 @@ import pytest
 
 import meshgen
 import oracle
-from helpers import TOL_FP64, TOL_MIXED, rel_err
+from helpers import TOL_FP64, TOL_MIXED, TOL_VJP_FP64, TOL_VJP_MIXED, rel_err, vjp_err, vjp_scales
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -243,9 +243,10 @@ def test_elastic_backward(fem, name, prec, cap):
     dX, dc = mesh.vjp(Xd, cd, dev(G, dt), prec)
     assert dc.shape == (m.n_elems, 2)
     dX, dc = dX.cpu().numpy().astype(np.float64), dc.cpu().numpy().astype(np.float64)
-    tol = 1e-11 if prec == "fp64" else 2e-4
-    assert np.abs(dX - dX_ref).max() <= tol * np.abs(dX_ref).max()
-    assert np.abs(dc - dc_ref).max() <= tol * np.abs(dc_ref).max()
+    sx, sc = vjp_scales(m, X, c, np.asarray(G, np.float64)[ref["slot"]], op="elasticity")
+    tol = TOL_VJP_FP64 if prec == "fp64" else TOL_VJP_MIXED
+    assert vjp_err(dX, dX_ref, sx) <= tol, vjp_err(dX, dX_ref, sx)
+    assert vjp_err(dc, dc_ref, sc) <= tol, vjp_err(dc, dc_ref, sc)
     # bitwise reproducible: owner-computes accumulation in a fixed colour order
     dX2, dc2 = mesh.vjp(Xd, cd, dev(G, dt), prec)
     assert np.array_equal(dX2.cpu().numpy().astype(np.float64), dX)

@@ -7,7 +7,8 @@ import pytest
 
 import meshgen
 import oracle
-from helpers import TOL_FP64, TOL_MIXED, oracle_K, oracle_ke, oracle_rows, rel_err, rounded_inputs
+from helpers import (TOL_FP64, TOL_MIXED, TOL_VJP_FP64, TOL_VJP_MIXED, oracle_K, oracle_ke, oracle_rows, rel_err,
+                     rounded_inputs, vjp_err, vjp_scales)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -130,6 +131,7 @@ def test_mass_backward(fem, name, prec):
     mesh.pattern()
     dX, dc = mesh.vjp(Xd, cd, dev(G, dt), prec)
     dX, dc = dX.cpu().numpy().astype(np.float64), dc.cpu().numpy().astype(np.float64)
-    tol = 1e-11 if prec == "fp64" else 2e-4
-    assert np.abs(dX - dX_ref).max() <= tol * np.abs(dX_ref).max()
-    assert np.abs(dc - dc_ref).max() <= tol * np.abs(dc_ref).max()
+    sx, sc = vjp_scales(m, X, c, np.asarray(G, np.float64)[ref["slot"]], op="mass")
+    tol = TOL_VJP_FP64 if prec == "fp64" else TOL_VJP_MIXED
+    assert vjp_err(dX, dX_ref, sx) <= tol, vjp_err(dX, dX_ref, sx)
+    assert vjp_err(dc, dc_ref, sc) <= tol, vjp_err(dc, dc_ref, sc)

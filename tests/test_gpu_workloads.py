@@ -86,3 +86,29 @@ def test_27M_bricks_under_16GB_budget(fem):
         assert worst <= tol, (prec, worst)
         del vals
     mesh.close()
+
+
+def test_27M_bricks_in_groups_under_7GB(fem):
+    """The 27M-brick workload under a 7 GB library budget, too small for the whole
+    plan: the numeric build runs in two or more patch groups one after the other
+    (Eq. 10), and sampled rows match the oracle."""
+    m = meshgen.config_mesh(4)
+    mesh = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), mem_budget_bytes=7 << 30)
+    nnz = mesh.pattern()
+    assert nnz == 379_351_801
+    Xh, ch = m.X.astype(np.float32), m.c.astype(np.float32)
+    vals = mesh.build_K(dev(Xh, torch.float32), dev(ch, torch.float32), "mixed")
+    mesh.sync()
+    info = mesh.info()
+    assert info["n_groups"] >= 2 and info["peak_bytes"] <= 7 << 30
+    vals = vals.cpu().numpy()
+    rowptr, col = mesh.get_pattern()
+    rp, cl = rowptr.cpu().numpy(), col.cpu().numpy()
+    sample = np.random.default_rng(28).choice(m.n_nodes, 2000, replace=False)
+    worst = 0.0
+    for r, (cols, v, cs) in oracle_rows(m, sample, Xh, ch).items():
+        a, b = rp[r], rp[r + 1]
+        assert np.array_equal(cl[a:b], cols)
+        worst = max(worst, rel_err(vals[a:b], v, cs))
+    assert worst <= TOL_MIXED, worst
+    mesh.close()

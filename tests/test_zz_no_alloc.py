@@ -78,3 +78,23 @@ def test_noalloc_reports_limits(lib):
     st = lib.fem_pattern_noalloc(8, 10_000_000, 10_000_000, ptr(E), ptr(rowptr), ptr(col), 16, ctypes.byref(big),
                                  stream())
     assert st == 5 and b"scratch" in lib.fem_last_error()   # FEM_ERR_BUDGET, checked before any GPU work
+
+
+@pytest.mark.parametrize("n,fits", [(64, True), (66, False)])
+def test_noalloc_documented_size_limit(lib, n, fits):
+    """The documented limit: a 64^3 brick grid fits the 16 MiB scratch, a 66^3 grid
+    is refused with FEM_ERR_BUDGET before any GPU work."""
+    m = meshgen.hex_grid(n, jitter=0.0, seed=1)
+    E = torch.from_numpy(np.ascontiguousarray(m.E)).cuda()
+    nnz_closed = ((3 * n + 1) ** 3 + (n + 1) ** 3) // 2
+    rowptr = torch.empty(m.n_nodes + 1, dtype=torch.int64, device="cuda")
+    col = torch.empty(nnz_closed if fits else 16, dtype=torch.int32, device="cuda")
+    got = ctypes.c_int64(-1)
+    st = lib.fem_pattern_noalloc(8, m.n_nodes, m.n_elems, ptr(E), ptr(rowptr), ptr(col), col.numel(),
+                                 ctypes.byref(got), stream())
+    if fits:
+        assert st == 0, lib.fem_last_error()
+        assert got.value == nnz_closed
+        assert int(rowptr[-1]) == nnz_closed
+    else:
+        assert st == 5 and b"scratch" in lib.fem_last_error()
