@@ -14,6 +14,10 @@ orderings of the benchmark configurations:
   node / element numbering, c_e laws;
 * ``kuhn_tets`` -- the same grid with every cell split into 6 tetrahedra along
   its main diagonal;
+* ``delaunay_tets`` -- genuinely unstructured tetrahedra: the Delaunay
+  tetrahedralisation of seeded uniform random points in the unit cube;
+* ``graded_bricks`` -- a brick grid whose spacing grows geometrically along each
+  axis (cell sizes spanning a stated ratio), with interior-node jitter;
 * ``batch_specs`` -- grid shapes for a batch of uneven meshes;
 * ``lame`` -- per-element Lame parameters (lambda, mu) for the elasticity
   operator: Young's modulus c_e and a seeded Poisson ratio per element.
@@ -207,6 +211,50 @@ def kuhn_tets(nx: int, ny: int | None = None, nz: int | None = None, *, jitter: 
         raise ValueError(c_law)
     X, E, c = _renumber(X, E, c, seed, permute_nodes, permute_elems)
     return Mesh(X, E, c, 4, (nx, ny, nz), dict(kind="tet4", jitter=jitter, seed=seed))
+
+
+def delaunay_tets(n_points: int, *, seed: int = BASE_SEED + 10, permute_nodes: bool = True,
+                  permute_elems: bool = True, c_law: str = "lognormal", c_sigma: float = 0.5) -> Mesh:
+    """Delaunay tetrahedralisation (Qhull, through scipy) of n_points seeded uniform
+    random points in the unit cube.  Node valence, row lengths and colour counts
+    vary from node to node as in a mesher's output, unlike the structured grids;
+    simplices come in either orientation (the method uses |det J|)."""
+    from scipy.spatial import Delaunay
+    X = stream_uniform(seed, "points", 3 * n_points).reshape(-1, 3)
+    E = np.ascontiguousarray(Delaunay(X).simplices, dtype=np.int64)
+    if c_law == "lognormal":
+        c = _c_lognormal(seed, E.shape[0], c_sigma)
+    elif c_law == "subboxes":
+        c = _c_subboxes(seed, X[E].mean(axis=1))
+    elif c_law == "one":
+        c = np.ones(E.shape[0])
+    else:
+        raise ValueError(c_law)
+    X, E, c = _renumber(X, E, c, seed, permute_nodes, permute_elems)
+    return Mesh(X, E, c, 4, (n_points,), dict(kind="tet4-delaunay", seed=seed))
+
+
+def graded_bricks(n: int, *, ratio: float = 50.0, jitter: float = 0.2, seed: int = BASE_SEED + 11,
+                  permute_nodes: bool = True, permute_elems: bool = True, c_sigma: float = 0.5) -> Mesh:
+    """n^3 bricks on the unit cube with geometrically graded spacing: along every
+    axis the cell widths grow by a constant factor from the first cell to the last,
+    whose width is `ratio` times the first's.  Interior nodes are jittered by up to
+    `jitter` times the smaller of their two neighbouring widths on each axis."""
+    w = ratio ** (np.arange(n) / max(n - 1, 1))
+    t = np.concatenate([[0.0], np.cumsum(w)]) / w.sum()           # node positions along an axis
+    ijk = _grid_nodes(n, n, n)
+    X = t[ijk]
+    if jitter > 0.0:
+        gap = np.minimum(np.diff(t, prepend=np.inf)[ijk], np.diff(t, append=np.inf)[ijk])
+        interior = ((ijk > 0) & (ijk < n)).all(axis=1)
+        u = stream_uniform(seed, "jitter", 3 * X.shape[0]).reshape(-1, 3)
+        X = X + np.where(interior[:, None], (2.0 * u - 1.0) * jitter * gap, 0.0)
+    cells = _cells(n, n, n)
+    corners = cells[:, None, :] + HEX_NODE_OFFSETS[None, :, :]
+    E = _node_id(corners[..., 0], corners[..., 1], corners[..., 2], n, n)
+    c = _c_lognormal(seed, E.shape[0], c_sigma)
+    X, E, c = _renumber(X, E, c, seed, permute_nodes, permute_elems)
+    return Mesh(X, E, c, 8, (n, n, n), dict(kind="hex8-graded", ratio=ratio, jitter=jitter, seed=seed))
 
 
 def batch_specs(n_meshes: int = 512, seed: int = BASE_SEED + 3, lo: float = 1e3, hi: float = 2e5,

@@ -55,6 +55,7 @@ namespace fem {
 // The patch plan, built on first use when the builds run on tiles.
 fem_status ensure_plan(fem_mesh m, cudaStream_t s) {
     if (m->plan_built) return FEM_OK;
+    ArenaKeep keep(m->arena);
     FEM_TRY(build_plan(m, s));
     m->plan_built = true;
     return FEM_OK;
@@ -221,15 +222,18 @@ fem_status fem_mesh_create(fem_mesh *out, fem_elem type, int64_t n_nodes, int64_
     m->arena.budget = m->opt.mem_budget_bytes;
     cudaStream_t s = as_stream(stream);
     fem_status st = m->status.alloc(m->arena, 1, "status word");
-    if (st == FEM_OK) {
-        cudaError_t e = cudaMemsetAsync(m->status.ptr, 0, sizeof(int), s);
-        if (e != cudaSuccess) st = cuda_status(e, "fem_mesh_create");
-    }
-    if (st == FEM_OK) st = validate_connectivity(m, s);
-    if (st == FEM_OK) st = build_locality_order(m, X, x_dtype, s);
-    if (st == FEM_OK) {
-        cudaError_t e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) st = cuda_status(e, "fem_mesh_create");
+    {
+        ArenaKeep keep(m->arena);  // ends (and frees the kept blocks) before m may be deleted
+        if (st == FEM_OK) {
+            cudaError_t e = cudaMemsetAsync(m->status.ptr, 0, sizeof(int), s);
+            if (e != cudaSuccess) st = cuda_status(e, "fem_mesh_create");
+        }
+        if (st == FEM_OK) st = validate_connectivity(m, s);
+        if (st == FEM_OK) st = build_locality_order(m, X, x_dtype, s);
+        if (st == FEM_OK) {
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) st = cuda_status(e, "fem_mesh_create");
+        }
     }
     if (st != FEM_OK) {
         delete m;
@@ -254,6 +258,7 @@ fem_status fem_pattern(fem_mesh m, int64_t *nnz_out, void *stream) {
     }
     if (!m->has_pattern) {
         cudaStream_t s = as_stream(stream);
+        ArenaKeep keep(m->arena);
         fem_status st = build_pattern(m, s);
         if (st == FEM_OK) {
             if (!is_elastic(m) && m->opt.assembly == 1) {
@@ -805,6 +810,7 @@ fem_status fem_set_tuning(fem_mesh m, int patch_entries, int block_threads, void
     m->opt.blocks_per_sm = 0;
     if (!m->has_pattern) return FEM_OK;  // fem_pattern will plan with these settings
     cudaStream_t s = as_stream(stream);
+    ArenaKeep keep(m->arena);
     fem_status st = FEM_OK;
     if (use_tiles(m)) {
         st = build_tiles(m, s);

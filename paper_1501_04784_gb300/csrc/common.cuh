@@ -10,6 +10,9 @@
 
 #include <cstdio>
 #include <string>
+#include <unordered_map>
+#include <utility>
+#include <vector>
 
 #include "fem.h"  // include/ is on the include path
 
@@ -52,11 +55,34 @@ struct NvtxRange {
 // ------------------------------------------------------- budgeted device memory
 // Every device allocation of a mesh goes through its Arena, which refuses to go
 // beyond the mesh's budget (FEM_ERR_BUDGET) and frees everything on destroy.
+//
+// While a symbolic phase runs (one stream, synchronised before it returns),
+// released blocks are kept for reuse instead of freed: cudaFree waits for the
+// whole device, and the phase allocates and drops dozens of temporaries.  The
+// kept blocks count against the budget (they are freed first when an allocation
+// would exceed it) and are all freed when the phase ends.
 struct Arena {
-    size_t budget = 0;  // 0 = unlimited
-    size_t live = 0, peak = 0;
+    size_t budget = 0;      // 0 = unlimited
+    size_t live = 0, peak = 0;  // bytes in use by buffers; most ever held (in use + kept)
+    size_t kept = 0;        // bytes of released blocks kept for reuse
+    bool keep = false;      // keep released blocks (inside a symbolic phase)
+    std::vector<std::pair<void *, size_t>> pool;        // kept blocks
+    std::unordered_map<void *, size_t> block;           // size of every block handed out
     fem_status alloc(void **p, size_t bytes, const char *what);
     void release(void *p, size_t bytes);
+    void trim();  // frees the kept blocks
+    ~Arena() { trim(); }
+};
+
+// Keeps released blocks for the lifetime of the guard (a symbolic phase).
+struct ArenaKeep {
+    Arena &a;
+    bool was;
+    explicit ArenaKeep(Arena &ar) : a(ar), was(ar.keep) { a.keep = true; }
+    ~ArenaKeep() {
+        a.keep = was;
+        if (!was) a.trim();
+    }
 };
 
 template <typename T>

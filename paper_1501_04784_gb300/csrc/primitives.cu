@@ -33,26 +33,64 @@ int64_t launch_count(int reset) {
 
 fem_status Arena::alloc(void **p, size_t bytes, const char *what) {
     *p = nullptr;
-    if (budget && live + bytes > budget) {
+    const size_t need = bytes ? bytes : 1;
+    // a kept block of at least the size and at most twice it (the smallest such)
+    size_t best = pool.size();
+    for (size_t i = 0; i < pool.size(); ++i)
+        if (pool[i].second >= need && pool[i].second <= 2 * need &&
+            (best == pool.size() || pool[i].second < pool[best].second))
+            best = i;
+    if (best < pool.size()) {
+        *p = pool[best].first;
+        const size_t sz = pool[best].second;
+        pool.erase(pool.begin() + (std::ptrdiff_t)best);
+        kept -= sz;
+        live += sz;
+        block[*p] = sz;
+        return FEM_OK;
+    }
+    if (budget && live + kept + need > budget) trim();
+    if (budget && live + need > budget) {
         set_error("memory budget: %s needs %zu bytes, %zu of %zu in use", what, bytes, live, budget);
         return FEM_ERR_BUDGET;
     }
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = cudaMalloc(p, need);
+    if (e != cudaSuccess && !pool.empty()) {
+        cudaGetLastError();
+        trim();
+        e = cudaMalloc(p, need);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("cudaMalloc(%zu) for %s: %s", bytes, what, cudaGetErrorString(e));
         *p = nullptr;
         return FEM_ERR_OOM;
     }
-    live += bytes;
-    if (live > peak) peak = live;
+    live += need;
+    block[*p] = need;
+    if (live + kept > peak) peak = live + kept;
     return FEM_OK;
 }
 
 void Arena::release(void *p, size_t bytes) {
+    (void)bytes;
     if (!p) return;
+    auto it = block.find(p);
+    const size_t sz = it != block.end() ? it->second : bytes;
+    if (it != block.end()) block.erase(it);
+    live -= sz;
+    if (keep) {
+        pool.emplace_back(p, sz);
+        kept += sz;
+        return;
+    }
     cudaFree(p);
-    live -= bytes;
+}
+
+void Arena::trim() {
+    for (auto &b : pool) cudaFree(b.first);
+    pool.clear();
+    kept = 0;
 }
 
 int num_sms() {
