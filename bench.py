@@ -151,7 +151,8 @@ def measured_peaks():
 
 
 # the sources that determine the patch kernel's code and its plan's layout
-KERNEL_SOURCES = ("element.cuh", "mesh.cuh", "numeric.cu", "numeric.cuh", "phases.cuh", "symbolic.cu")
+KERNEL_SOURCES = ("element.cuh", "elem_ops.cuh", "mesh.cuh", "tile.cuh", "numeric.cu", "numeric.cuh", "phases.cuh",
+                  "symbolic.cu", "tile.cu", "tile_plan.cu")
 
 
 def source_hash():

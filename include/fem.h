@@ -33,6 +33,11 @@
  *   - Every call is ordered on `stream` (a cudaStream_t; NULL = legacy default
  *     stream) and returns without waiting, except where stated.  Asynchronous
  *     CUDA errors surface at the next call on the mesh or at fem_sync.
+ *   - Calls on one mesh handle must not overlap on the GPU: they share the
+ *     mesh's library buffers (plan, staged element matrices or gradients, tile
+ *     partials, host staging).  Order them on one stream, or synchronise between
+ *     the streams they use (fem_build_K_host_async orders its own calls on one
+ *     mesh across streams).  Different meshes are independent.
  *   - Every call returns a status; nothing throws across this boundary.  A
  *     one-line detail of the last failure on the calling thread is available
  *     from fem_last_error().
@@ -213,7 +218,7 @@ void fem_mesh_destroy(fem_mesh m);
  * that shares an element, explicit zeros included -- and the per-block plan of
  * the numeric kernels.  Writes nnz to *nnz_out.  Idempotent.  Blocks (reads nnz
  * back).  Errors: FEM_ERR_OOM, FEM_ERR_BUDGET, FEM_ERR_UNSUPPORTED (a row with
- * more than 255 entries, more than 128 colours), FEM_ERR_CUDA.
+ * more than 255 entries, more than 255 colours), FEM_ERR_CUDA.
  */
 fem_status fem_pattern(fem_mesh m, int64_t *nnz_out, void *stream);
 

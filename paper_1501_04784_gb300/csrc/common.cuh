@@ -63,7 +63,8 @@ struct NvtxRange {
 // would exceed it) and are all freed when the phase ends.
 struct Arena {
     size_t budget = 0;      // 0 = unlimited
-    size_t live = 0, peak = 0;  // bytes in use by buffers; most ever held (in use + kept)
+    size_t live = 0, peak = 0;  // bytes in use by buffers; most ever in use (kept blocks are
+                                // returned before an allocation would exceed the budget)
     size_t kept = 0;        // bytes of released blocks kept for reuse
     bool keep = false;      // keep released blocks (inside a symbolic phase)
     std::vector<std::pair<void *, size_t>> pool;        // kept blocks

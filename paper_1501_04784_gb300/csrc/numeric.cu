@@ -17,6 +17,35 @@
 
 namespace fem {
 
+// One element's packed k_e from the staged element matrices, in the widest
+// vector loads its alignment allows (a row of 36 floats or of 10 or 36 doubles is
+// a whole number of 16-byte units; a row of 10 floats, of 8-byte units).
+template <int NP, typename T>
+__device__ __forceinline__ void load_packed(const T *__restrict__ src, T (&kv)[NP]) {
+    if constexpr (sizeof(T) == 4 && (NP * 4) % 16 == 0) {
+#pragma unroll
+        for (int w = 0; w < NP / 4; ++w) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(src) + w);
+            kv[4 * w] = v.x; kv[4 * w + 1] = v.y; kv[4 * w + 2] = v.z; kv[4 * w + 3] = v.w;
+        }
+    } else if constexpr (sizeof(T) == 4 && NP % 2 == 0) {
+#pragma unroll
+        for (int w = 0; w < NP / 2; ++w) {
+            const float2 v = __ldg(reinterpret_cast<const float2 *>(src) + w);
+            kv[2 * w] = v.x; kv[2 * w + 1] = v.y;
+        }
+    } else if constexpr (sizeof(T) == 8 && NP % 2 == 0) {
+#pragma unroll
+        for (int w = 0; w < NP / 2; ++w) {
+            const double2 v = __ldg(reinterpret_cast<const double2 *>(src) + w);
+            kv[2 * w] = v.x; kv[2 * w + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) kv[q] = __ldg(src + q);
+    }
+}
+
 // ------------------------------------------------------------- k_integrate
 static constexpr int INT_THREADS = 128;
 
@@ -292,8 +321,7 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
                 } else {
                     int64_t e = pv.celem_id[ci];
                     if (!FEM_IN_BOUNDS(e >= 0 && e < pv.n_elems, wc.status)) e = 0;
-#pragma unroll
-                    for (int q = 0; q < NP; ++q) kv[q] = __ldg(ke + e * NP + q);
+                    load_packed<NP>(ke + e * NP, kv);
                 }
                 // bricks: accumulator targets after the integration, before the colour
                 // phases, so that no phase waits on its own load (tets take them a

@@ -47,6 +47,7 @@ fem_status Arena::alloc(void **p, size_t bytes, const char *what) {
         kept -= sz;
         live += sz;
         block[*p] = sz;
+        if (live > peak) peak = live;
         return FEM_OK;
     }
     if (budget && live + kept + need > budget) trim();
@@ -68,7 +69,7 @@ fem_status Arena::alloc(void **p, size_t bytes, const char *what) {
     }
     live += need;
     block[*p] = need;
-    if (live + kept > peak) peak = live + kept;
+    if (live > peak) peak = live;
     return FEM_OK;
 }
 

@@ -343,10 +343,11 @@ __global__ void k_segment_ptr(const uint64_t *keys, int64_t n, int shift, int64_
 
 // Greedy colouring of a patch's closure (elements in ascending id): an element
 // takes the lowest colour not yet used by an element sharing an owned node with
-// it.  Owned-node colour sets are 128-bit masks in shared memory; the
-// element -> owned-node table is staged chunk by chunk so that the serial loop
-// runs from shared memory.
+// it.  Owned-node colour sets are 256-bit masks in shared memory (colours 0-254;
+// 255 marks an element no colour was left for); the element -> owned-node table is
+// staged chunk by chunk so that the serial loop runs from shared memory.
 static constexpr int COLOR_CHUNK = 256;
+static constexpr int COLOR_WORDS = 4;
 
 template <int NPE>
 __global__ void k_color(const uint64_t *ckeys, const int64_t *pe_ptr, const int64_t *pn_ptr, const int32_t *E,
@@ -355,9 +356,9 @@ __global__ void k_color(const uint64_t *ckeys, const int64_t *pe_ptr, const int6
     extern __shared__ unsigned long long col_smem[];
     for (int64_t p = blockIdx.x; p < npatch; p += gridDim.x) {
         const int nown = (int)(pn_ptr[p + 1] - pn_ptr[p]);
-        unsigned long long *mask = col_smem;                                // [2 * nown]
-        int16_t *tab = reinterpret_cast<int16_t *>(col_smem + 2 * nown);    // [COLOR_CHUNK * NPE]
-        for (int i = threadIdx.x; i < 2 * nown; i += blockDim.x) mask[i] = 0;
+        unsigned long long *mask = col_smem;                                            // [4 * nown]
+        int16_t *tab = reinterpret_cast<int16_t *>(col_smem + COLOR_WORDS * nown);      // [COLOR_CHUNK * NPE]
+        for (int i = threadIdx.x; i < COLOR_WORDS * nown; i += blockDim.x) mask[i] = 0;
         const int64_t b = pe_ptr[p], n = pe_ptr[p + 1] - b;
         int local_max = -1;
         for (int64_t c0 = 0; c0 < n; c0 += COLOR_CHUNK) {
@@ -371,25 +372,25 @@ __global__ void k_color(const uint64_t *ckeys, const int64_t *pe_ptr, const int6
             __syncthreads();
             if (threadIdx.x == 0) {
                 for (int i = 0; i < cn; ++i) {
-                    unsigned long long m0 = 0, m1 = 0;
+                    unsigned long long m[COLOR_WORDS] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll
                     for (int a = 0; a < NPE; ++a) {
                         const int o = tab[i * NPE + a];
-                        if (o >= 0) {
-                            m0 |= mask[2 * o];
-                            m1 |= mask[2 * o + 1];
-                        }
+                        if (o >= 0)
+#pragma unroll
+                            for (int w = 0; w < COLOR_WORDS; ++w) m[w] |= mask[COLOR_WORDS * o + w];
                     }
-                    int c;
-                    if (~m0) c = __ffsll((long long)~m0) - 1;
-                    else if (~m1) c = 64 + __ffsll((long long)~m1) - 1;
-                    else c = 255;
+                    int c = 255;
+#pragma unroll
+                    for (int w = COLOR_WORDS - 1; w >= 0; --w)
+                        if (~m[w]) c = 64 * w + __ffsll((long long)~m[w]) - 1;
+                    if (c > 254) c = 255;
                     color_out[b + c0 + i] = (uint8_t)c;
-                    if (c < 128) {
+                    if (c < 255) {
 #pragma unroll
                         for (int a = 0; a < NPE; ++a) {
                             const int o = tab[i * NPE + a];
-                            if (o >= 0) mask[2 * o + (c >> 6)] |= 1ull << (c & 63);
+                            if (o >= 0) mask[COLOR_WORDS * o + (c >> 6)] |= 1ull << (c & 63);
                         }
                     }
                     local_max = max(local_max, c);
@@ -772,7 +773,8 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
         FEM_TRY(color.alloc(ar, nce, "colours"));
         FEM_TRY(mxc.alloc(ar, 1, "max colour"));
         FEM_CUDA(cudaMemsetAsync(mxc.ptr, 0, sizeof(int), s));
-        const size_t smem = (size_t)2 * P.max_own * sizeof(unsigned long long) + (size_t)COLOR_CHUNK * npe * sizeof(int16_t);
+        const size_t smem = (size_t)COLOR_WORDS * P.max_own * sizeof(unsigned long long) +
+                            (size_t)COLOR_CHUNK * npe * sizeof(int16_t);
         // one warp per patch: the greedy pass is one thread's dependent chain of
         // shared-memory updates, so the SM is kept busy by many patches at once
         // (small chunks of the element table keep each block's shared memory small)
@@ -789,8 +791,8 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
         FEM_LAUNCHED("k_color");
         int h_mxc = 0;
         FEM_TRY(read_scalar(mxc.ptr, &h_mxc, s));
-        if (h_mxc >= 128) {
-            set_error("the closure colouring needs more than 128 colours");
+        if (h_mxc >= 255) {
+            set_error("the closure colouring needs more than 255 colours (more than 255 elements share a node)");
             return FEM_ERR_UNSUPPORTED;
         }
         cl.n_colors = h_mxc + 1;

@@ -213,7 +213,7 @@ FillSmem fill_layout(int npe, int64_t pmax, int64_t ncn_max) {
     L.sbuf = o; o = al(o + sz * 4);
     L.ug = o; o = al(o + (size_t)ncn_max * 4);
     L.uinfo = o; o = al(o + (size_t)ncn_max * 4);
-    L.mask = o; o = al(o + (size_t)ncn_max * 16);
+    L.mask = o; o = al(o + (size_t)ncn_max * 32);
     L.ln = o; o = al(o + (size_t)pmax * npe * 2);
     L.ecol = o; o = al(o + (size_t)pmax);
     L.total = o;
@@ -286,28 +286,30 @@ __global__ void __launch_bounds__(TP_THREADS) k_tile_fill(TileIn in, int64_t n_t
             const int32_t g = in.E[(int64_t)in.eorder[eb + i / NPE] * NPE + i % NPE];
             ln[i] = (uint16_t)lower_bound_i32(ug, ncn, g);
         }
-        for (int i = tid; i < 2 * ncn; i += nthr) mask[i] = 0ull;
+        for (int i = tid; i < 4 * ncn; i += nthr) mask[i] = 0ull;
         __syncthreads();
         // greedy colouring in sweep order: the lowest colour no element sharing a
-        // node has taken (colour sets are 128-bit masks per row)
+        // node has taken (colour sets are 256-bit masks per row; colours 0-254, 255
+        // marks an element no colour was left for)
         if (tid == 0) {
             int cmax = 0;
             for (int e = 0; e < ne; ++e) {
-                unsigned long long m0 = 0, m1 = 0;
+                unsigned long long mw[4] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll
                 for (int a = 0; a < NPE; ++a) {
                     const int o = ln[e * NPE + a];
-                    m0 |= mask[2 * o];
-                    m1 |= mask[2 * o + 1];
-                }
-                int c;
-                if (~m0) c = __ffsll((long long)~m0) - 1;
-                else if (~m1) c = 64 + __ffsll((long long)~m1) - 1;
-                else c = 255;
-                ecol[e] = (uint8_t)c;
-                if (c < 128) {
 #pragma unroll
-                    for (int a = 0; a < NPE; ++a) mask[2 * ln[e * NPE + a] + (c >> 6)] |= 1ull << (c & 63);
+                    for (int w = 0; w < 4; ++w) mw[w] |= mask[4 * o + w];
+                }
+                int c = 255;
+#pragma unroll
+                for (int w = 3; w >= 0; --w)
+                    if (~mw[w]) c = 64 * w + __ffsll((long long)~mw[w]) - 1;
+                if (c > 254) c = 255;
+                ecol[e] = (uint8_t)c;
+                if (c < 255) {
+#pragma unroll
+                    for (int a = 0; a < NPE; ++a) mask[4 * ln[e * NPE + a] + (c >> 6)] |= 1ull << (c & 63);
                 }
                 cmax = max(cmax, c);
             }
@@ -547,8 +549,17 @@ fem_status build_tiles(fem_mesh m, cudaStream_t s) {
         FEM_CUDA(cudaStreamSynchronize(s));
         max_ncn = *std::max_element(h_ncn.begin(), h_ncn.end());
         max_acc = *std::max_element(h_nacc.begin(), h_nacc.end());
-        // (the pass's static shared memory stays well inside the 1 KB margin)
-        const bool fits = max_acc < 32768 && fill_layout(npe, pmax, max_ncn).total + 1024 <= (size_t)max_optin;
+        // (the pass's static shared memory stays well inside the 1 KB margin); the
+        // tile kernel's own shared memory is checked for its largest form (FP64
+        // accumulators and double coordinates), which the same plan serves
+        TileMax tm;
+        tm.max_acc = max_acc;
+        tm.max_epad = cdiv(pmax, TILE_EPAD) * TILE_EPAD;
+        tm.max_npad = cdiv(max_ncn, TILE_NPAD) * TILE_NPAD;
+        tm.any_hv = m->max_deg > hv_thr;
+        const size_t kernel_smem = tile_smem_layout(tm, npe, false, sizeof(double)).total;
+        const bool fits = max_acc < 32768 && fill_layout(npe, pmax, max_ncn).total + 1024 <= (size_t)max_optin &&
+                          kernel_smem + 1024 <= (size_t)max_optin;
         if (fits) break;
         if (P <= 1 || attempt > 16) {
             set_error("element tiles: one element's rows need %lld accumulator entries; at most 32767 fit",
@@ -645,8 +656,8 @@ fem_status build_tiles(fem_mesh m, cudaStream_t s) {
         FEM_LAUNCHED("k_tile_fill");
         int h_mxc = 0;
         FEM_TRY(read_scalar(mxc.ptr, &h_mxc, s));
-        if (h_mxc >= 128) {
-            set_error("element tiles: the colouring of a tile needs more than 128 colours");
+        if (h_mxc >= 255) {
+            set_error("element tiles: the colouring of a tile needs more than 255 colours");
             return FEM_ERR_UNSUPPORTED;
         }
         T.n_colors = h_mxc + 1;

@@ -4,7 +4,7 @@ valence, row lengths and colour counts vary from node to node, and brick grids
 with geometrically graded spacing (cell sizes over a 50x range), at 10^4 to 10^5
 elements, every value against the oracle in both precisions and both assemblies.
 Also the library's limits on such meshes: the longest lower row (255 entries)
-and the colour count (128) are reported against what these meshes reach, and a
+and the colour count (255) are reported against what these meshes reach, and a
 mesh beyond them is refused cleanly."""
 import numpy as np
 import pytest
@@ -59,9 +59,9 @@ def test_unstructured_against_oracle(fem, name, prec, assembly):
     assert err <= (TOL_FP64 if prec == "fp64" else TOL_MIXED), err
     info = mesh.info()
     # how close these meshes come to the library's limits
-    assert info["max_row_len"] <= 255 and info["n_colors"] <= 128
+    assert info["max_row_len"] <= 255 and info["n_colors"] <= 255
     print(f"{name} {prec} asm={assembly}: max lower row {info['max_row_len']} of 255, "
-          f"colours {info['n_colors']} of 128, error {err:.2e}")
+          f"colours {info['n_colors']} of 255, error {err:.2e}")
 
 
 def fan(n_rim, seed=5):
@@ -77,10 +77,11 @@ def fan(n_rim, seed=5):
     return P, np.ascontiguousarray(E)
 
 
-@pytest.mark.parametrize("n_rim,what", [(258, "row"), (300, "elements")])
+@pytest.mark.parametrize("n_rim,what", [(258, "row"), (300, "elements"), (140, "colours")])
 def test_beyond_the_limits_is_refused(fem, n_rim, what):
-    """A node whose lower row outgrows 255 entries, or that more than 512
-    tetrahedra touch, is refused with FEM_ERR_UNSUPPORTED and a message; nothing
+    """A node whose lower row outgrows 255 entries, that more than 512 tetrahedra
+    touch, or whose elements need more than 255 colours (more than 255 elements
+    on one node), is refused with FEM_ERR_UNSUPPORTED and a message; nothing
     faults."""
     from paper_1501_04784_gb300 import abi
     P, E = fan(n_rim)
@@ -90,12 +91,12 @@ def test_beyond_the_limits_is_refused(fem, n_rim, what):
     with pytest.raises(abi.FemError, match="FEM_ERR_UNSUPPORTED"):
         mesh.pattern()
     msg = abi.load().fem_last_error().decode()
-    assert ("255" in msg) if what == "row" else ("elements" in msg), msg
+    assert {"row": "255", "elements": "elements", "colours": "colours"}[what] in msg, msg
 
 
 def test_fan_within_the_limits_matches_oracle(fem):
-    """The same fan with 120 rim points (a 121-entry row, about 236 elements at one
-    node) is inside the limits: pattern and values against the oracle."""
+    """The same fan with 120 rim points (a 121-entry row, 236 elements at one node,
+    236 colours) is inside the limits: pattern and values against the oracle."""
     P, E = fan(120)
     from types import SimpleNamespace
     m = SimpleNamespace(X=P, E=E, c=np.ones(E.shape[0]), npe=4, n_nodes=P.shape[0], n_elems=E.shape[0])
