@@ -232,16 +232,17 @@ fem_status fem_pattern_ptrs(fem_mesh m, const int64_t **rowptr, const int32_t **
 /*
  * Numerical integration (Algorithm 2, Eqs. 7-9): packed lower k_e of every
  * element into ke_out [n_elems][36|10] (double for FEM_FP64, float for
- * FEM_MIXED).  Needs no pattern.
+ * FEM_MIXED; 16-byte aligned, each row stored with vector stores).  Needs no
+ * pattern.  FEM_ERR_ARG for a null or misaligned ke_out.
  */
 fem_status fem_integrate_local(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype,
                                const void *c, fem_dtype c_dtype, void *ke_out, void *stream);
 
 /*
  * Assembly (Section 3: triplet-to-compressed conversion, Eq. 6): sum the packed
- * element matrices ke [n_elems][36|10] into vals [nnz] of the cached pattern.
- * Every entry is written (no need to clear vals).  FEM_ERR_STATE before
- * fem_pattern.
+ * element matrices ke [n_elems][36|10] (16-byte aligned, read as vectors) into
+ * vals [nnz] of the cached pattern.  Every entry is written (no need to clear
+ * vals).  FEM_ERR_STATE before fem_pattern; FEM_ERR_ARG for a misaligned ke.
  */
 fem_status fem_assemble_csr(fem_mesh m, fem_prec p, const void *ke, void *vals, void *stream);
 

@@ -326,8 +326,8 @@ fem_status fem_pattern_ptrs(fem_mesh m, const int64_t **rowptr, const int32_t **
 fem_status fem_integrate_local(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c,
                                fem_dtype c_dtype, void *ke_out, void *stream) {
     FEM_TRY(check_inputs(m, p, X, x_dtype, c, c_dtype));
-    if (!ke_out || !aligned(ke_out, p == FEM_FP64 ? 8 : 4)) {
-        set_error("ke_out must be a non-null aligned device pointer");
+    if (!ke_out || !aligned(ke_out, 16)) {
+        set_error("ke_out must be a non-null device pointer aligned to 16 bytes");
         return FEM_ERR_ARG;
     }
     IntegrateArgs a{m->npe, p == FEM_MIXED, x_dtype, c_dtype, m->E, m->n_elems, X, c, ke_out,
@@ -370,8 +370,8 @@ fem_status fem_assemble_csr(fem_mesh m, fem_prec p, const void *ke, void *vals, 
         return FEM_ERR_ARG;
     }
     const size_t w = p == FEM_FP64 ? 8 : 4;
-    if (!ke || !vals || !aligned(ke, w) || !aligned(vals, w)) {
-        set_error("ke and vals must be non-null aligned device pointers");
+    if (!ke || !vals || !aligned(ke, 16) || !aligned(vals, w)) {
+        set_error("ke (16-byte aligned) and vals (aligned to its element size) must be non-null device pointers");
         return FEM_ERR_ARG;
     }
     cudaStream_t s = as_stream(stream);
