@@ -13,6 +13,7 @@
 #include <functional>
 #include <vector>
 
+#include "block_prims.cuh"
 #include "mesh.cuh"
 #include "numeric.cuh"
 
@@ -222,10 +223,25 @@ __global__ void k_row_pattern(const int32_t *__restrict__ E, const int64_t *__re
     for (int64_t i = (int64_t)blockIdx.x * wpb + wib; i < N; i += (int64_t)gridDim.x * wpb) {
         const int64_t b0 = inc_ptr[i];
         const int n = (int)(inc_ptr[i + 1] - b0) * NPE;
-        for (int t = lane; t < n; t += 32) {
-            const int32_t e = inc_elem[b0 + t / NPE];
-            const int32_t g = E[(int64_t)e * NPE + t % NPE];
-            buf[t] = (g <= i) ? g : INT_MAX;
+        // candidates gathered four per lane at a time: the incidence loads, then the
+        // connectivity loads, each four-wide
+        for (int t0 = lane; t0 < n; t0 += 128) {
+            int32_t e[4], g[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = t0 + 32 * u;
+                e[u] = t < n ? inc_elem[b0 + t / NPE] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = t0 + 32 * u;
+                g[u] = t < n ? E[(int64_t)e[u] * NPE + t % NPE] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = t0 + 32 * u;
+                if (t < n) buf[t] = (g[u] <= i) ? g[u] : INT_MAX;
+            }
         }
         __syncwarp();
         // mark repeats (keep the first occurrence); items of this lane: t = lane + 32 k
@@ -364,10 +380,33 @@ __global__ void k_color(const uint64_t *ckeys, const int64_t *pe_ptr, const int6
         for (int64_t c0 = 0; c0 < n; c0 += COLOR_CHUNK) {
             const int cn = (int)min((int64_t)COLOR_CHUNK, n - c0);
             __syncthreads();
-            for (int t = threadIdx.x; t < cn * NPE; t += blockDim.x) {
-                const int64_t e = (int64_t)(uint32_t)ckeys[b + c0 + t / NPE];
-                const int32_t g = E[e * NPE + t % NPE];
-                tab[t] = node_patch[g] == (int32_t)(p0 + p) ? (int16_t)own_idx[g] : (int16_t)-1;
+            // the chunk's element -> owned-node table: U entries per thread at a time,
+            // so that each of the three dependent loads goes out U-wide
+            constexpr int U = 8;
+            const int ntab = cn * NPE;
+            for (int t0 = threadIdx.x; t0 < ntab; t0 += blockDim.x * U) {
+                int64_t e[U];
+                int32_t g[U], np_[U], oi[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int t = t0 + u * blockDim.x;
+                    e[u] = t < ntab ? (int64_t)(uint32_t)ckeys[b + c0 + t / NPE] : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int t = t0 + u * blockDim.x;
+                    g[u] = t < ntab ? E[e[u] * NPE + t % NPE] : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    np_[u] = node_patch[g[u]];
+                    oi[u] = own_idx[g[u]];
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int t = t0 + u * blockDim.x;
+                    if (t < ntab) tab[t] = np_[u] == (int32_t)(p0 + p) ? (int16_t)oi[u] : (int16_t)-1;
+                }
             }
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -445,6 +484,41 @@ __global__ void k_cnode_pairs(const uint64_t *ckeys, int64_t nce, int npe, const
     }
 }
 
+// Closure nodes of each patch in shared memory (one block per patch): the node
+// ids of the patch's closure elements are sorted (bitonic, padded to a power of
+// two) and the distinct ones counted (cnt) or written as (patch << 32) | id at the
+// patch's offset (out).  Used when a patch's closure holds at most
+// CNODE_SMEM_KEYS node slots; larger closures take the global sort.
+static constexpr int CNODE_SMEM_KEYS = 8192;
+
+template <int NPE>
+__global__ void __launch_bounds__(512) k_patch_cnodes(const uint64_t *ckeys, const int64_t *pe_ptr, int64_t np_,
+                                                      const int32_t *__restrict__ E, int64_t *cnt,
+                                                      const int64_t *off, uint64_t *out) {
+    extern __shared__ __align__(16) unsigned char cn_smem[];
+    uint32_t *keys = reinterpret_cast<uint32_t *>(cn_smem);                    // [CNODE_SMEM_KEYS]
+    int *flag = reinterpret_cast<int *>(cn_smem + CNODE_SMEM_KEYS * sizeof(uint32_t));  // [CNODE_SMEM_KEYS]
+    __shared__ int ws[32];
+    for (int64_t p = blockIdx.x; p < np_; p += gridDim.x) {
+        const int64_t b = pe_ptr[p];
+        const int n = (int)(pe_ptr[p + 1] - b) * NPE, sz = pow2_at_least(n);
+        for (int i = threadIdx.x; i < sz; i += blockDim.x)
+            keys[i] = i < n ? (uint32_t)E[(int64_t)(uint32_t)ckeys[b + i / NPE] * NPE + i % NPE] : 0xffffffffu;
+        __syncthreads();
+        block_bitonic(keys, sz);
+        for (int i = threadIdx.x; i < sz; i += blockDim.x) flag[i] = (i < n && (i == 0 || keys[i] != keys[i - 1])) ? 1 : 0;
+        __syncthreads();
+        const int u = block_scan(flag, sz, ws);
+        if (cnt) {
+            if (threadIdx.x == 0) cnt[p] = u;
+        } else {
+            for (int i = threadIdx.x; i < n; i += blockDim.x)
+                if (i == 0 || keys[i] != keys[i - 1]) out[off[p] + flag[i]] = ((uint64_t)p << 32) | keys[i];
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void k_cnode_own(const uint64_t *cn_keys, int64_t ncn, int64_t p0, const int32_t *node_patch,
                             const int32_t *own_idx, int32_t *gid, int32_t *own) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ncn; j += (int64_t)gridDim.x * blockDim.x) {
@@ -470,28 +544,36 @@ struct OwnTables {
 };
 
 template <int NPE>
-__global__ void k_celem_fill(const uint64_t *ckeys, int64_t nce, const int32_t *__restrict__ E,
+// One block per patch: the patch's closure-node ids (ascending) are staged in
+// shared memory, so that the closure-local index of each element node is a
+// binary search there rather than a chain of dependent global loads.
+__global__ void k_celem_fill(const uint64_t *ckeys, int64_t np_, const int32_t *__restrict__ E,
                              const uint64_t *cn_keys, const int64_t *pc_ptr, const int64_t *__restrict__ rowptr,
                              const int32_t *__restrict__ col, int pos_stride, OwnTables ot, int32_t *celem_id,
                              uint8_t *celem_color, uint16_t *lnode, uint8_t *pos, uint16_t *aidx) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nce; i += (int64_t)gridDim.x * blockDim.x) {
+    extern __shared__ int32_t cn_gid[];
+    const int64_t nce = ot.pe_ptr[np_];
+  for (int64_t pb = blockIdx.x; pb < np_; pb += gridDim.x) {
+    const int64_t cb = pc_ptr[pb];
+    const int ncn = (int)(pc_ptr[pb + 1] - cb);
+    for (int j = threadIdx.x; j < ncn; j += blockDim.x) cn_gid[j] = (int32_t)(uint32_t)cn_keys[cb + j];
+    __syncthreads();
+    for (int64_t i = ot.pe_ptr[pb] + threadIdx.x; i < ot.pe_ptr[pb + 1]; i += blockDim.x) {
         const uint64_t k = ckeys[i];
         const uint64_t p = k >> 40;
         const int64_t e = (int64_t)(k & 0xffffffffull);
         celem_id[i] = (int32_t)e;
         celem_color[i] = (uint8_t)((k >> 32) & 0xff);
         int32_t g[NPE];
-        const int64_t cb = pc_ptr[p], ce = pc_ptr[p + 1];
 #pragma unroll
         for (int a = 0; a < NPE; ++a) {
             g[a] = E[e * NPE + a];
-            const uint64_t key = (p << 32) | (uint64_t)(uint32_t)g[a];
-            int64_t lo = cb, hi = ce;
+            int lo = 0, hi = ncn;
             while (lo < hi) {
-                int64_t mid = (lo + hi) >> 1;
-                if (cn_keys[mid] < key) lo = mid + 1; else hi = mid;
+                const int mid = (lo + hi) >> 1;
+                if (cn_gid[mid] < g[a]) lo = mid + 1; else hi = mid;
             }
-            lnode[i * NPE + a] = (uint16_t)(lo - cb);
+            lnode[i * NPE + a] = (uint16_t)lo;
         }
         const int64_t gp = ot.p0 + (int64_t)p;
         const int64_t nb = ot.patch_node_ptr[gp];
@@ -544,6 +626,8 @@ __global__ void k_celem_fill(const uint64_t *ckeys, int64_t nce, const int32_t *
                 aidx[((int64_t)(q >> 1) * nce + i) * 2 + (q & 1)] = (uint16_t)t;
             }
     }
+    __syncthreads();
+  }
 }
 
 // Shared memory of the row-pattern kernel above the 48 KB default (a node in up
@@ -554,6 +638,7 @@ static fem_status row_pattern_smem(int npe, size_t smem) {
     else FEM_CUDA(cudaFuncSetAttribute(k_row_pattern<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return FEM_OK;
 }
+
 
 // --------------------------------------------------------------- orchestration
 static int bits_for(int64_t v) {
@@ -775,17 +860,18 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
         FEM_CUDA(cudaMemsetAsync(mxc.ptr, 0, sizeof(int), s));
         const size_t smem = (size_t)COLOR_WORDS * P.max_own * sizeof(unsigned long long) +
                             (size_t)COLOR_CHUNK * npe * sizeof(int16_t);
-        // one warp per patch: the greedy pass is one thread's dependent chain of
-        // shared-memory updates, so the SM is kept busy by many patches at once
-        // (small chunks of the element table keep each block's shared memory small)
-        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np_, (int64_t)num_sms() * 32));
+        // four warps per patch: they stage the element table (the greedy pass itself
+        // is one thread's dependent chain of shared-memory updates, so the SM is kept
+        // busy by many patches at once; small chunks of the table keep each block's
+        // shared memory small)
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np_, (int64_t)num_sms() * 16));
         if (npe == 8) {
             FEM_CUDA(cudaFuncSetAttribute(k_color<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_color<8><<<grid, 32, smem, s>>>(ckeys.ptr, cl.patch_elem_ptr.ptr, P.patch_node_ptr.ptr + p0, m->E,
+            k_color<8><<<grid, 128, smem, s>>>(ckeys.ptr, cl.patch_elem_ptr.ptr, P.patch_node_ptr.ptr + p0, m->E,
                                                P.node_patch.ptr, P.own_idx.ptr, np_, p0, color.ptr, mxc.ptr);
         } else {
             FEM_CUDA(cudaFuncSetAttribute(k_color<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_color<4><<<grid, 32, smem, s>>>(ckeys.ptr, cl.patch_elem_ptr.ptr, P.patch_node_ptr.ptr + p0, m->E,
+            k_color<4><<<grid, 128, smem, s>>>(ckeys.ptr, cl.patch_elem_ptr.ptr, P.patch_node_ptr.ptr + p0, m->E,
                                                P.node_patch.ptr, P.own_idx.ptr, np_, p0, color.ptr, mxc.ptr);
         }
         FEM_LAUNCHED("k_color");
@@ -816,7 +902,36 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
     // ---- closure nodes of each patch
     DevBuf<uint64_t> cnkeys;
     int64_t ncn = 0;
-    {
+    if (cl.max_celems * npe <= CNODE_SMEM_KEYS) {
+        // per patch in shared memory: a count pass, a prefix on the host, a fill pass
+        DevBuf<int64_t> cnt, off;
+        FEM_TRY(cnt.alloc(ar, np_, "closure node counts"));
+        FEM_TRY(off.alloc(ar, np_ + 1, "closure node offsets"));
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np_, (int64_t)num_sms() * 3));
+        const size_t smem = (size_t)CNODE_SMEM_KEYS * (sizeof(uint32_t) + sizeof(int));
+        FEM_CUDA(cudaFuncSetAttribute(k_patch_cnodes<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FEM_CUDA(cudaFuncSetAttribute(k_patch_cnodes<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (npe == 8)
+            k_patch_cnodes<8><<<grid, 512, smem, s>>>(ckeys.ptr, cl.patch_elem_ptr.ptr, np_, m->E, cnt.ptr, nullptr, nullptr);
+        else
+            k_patch_cnodes<4><<<grid, 512, smem, s>>>(ckeys.ptr, cl.patch_elem_ptr.ptr, np_, m->E, cnt.ptr, nullptr, nullptr);
+        FEM_LAUNCHED("k_patch_cnodes(count)");
+        std::vector<int64_t> h_cnt(np_), h_off(np_ + 1, 0);
+        FEM_CUDA(cudaMemcpyAsync(h_cnt.data(), cnt.ptr, np_ * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        FEM_CUDA(cudaStreamSynchronize(s));
+        for (int64_t p = 0; p < np_; ++p) h_off[p + 1] = h_off[p] + h_cnt[p];
+        ncn = h_off[np_];
+        FEM_CUDA(cudaMemcpyAsync(off.ptr, h_off.data(), (np_ + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        FEM_TRY(cnkeys.alloc(ar, std::max<int64_t>(ncn, 1), "closure nodes"));
+        if (npe == 8)
+            k_patch_cnodes<8><<<grid, 512, smem, s>>>(ckeys.ptr, cl.patch_elem_ptr.ptr, np_, m->E, nullptr, off.ptr,
+                                                      cnkeys.ptr);
+        else
+            k_patch_cnodes<4><<<grid, 512, smem, s>>>(ckeys.ptr, cl.patch_elem_ptr.ptr, np_, m->E, nullptr, off.ptr,
+                                                      cnkeys.ptr);
+        FEM_LAUNCHED("k_patch_cnodes(fill)");
+        FEM_CUDA(cudaStreamSynchronize(s));  // h_off and the offsets buffer are released on return
+    } else {
         DevBuf<uint64_t> pairs;
         FEM_TRY(pairs.alloc(ar, nce * npe, "closure node pairs"));
         k_cnode_pairs<<<grid_for(nce * npe), TPB, 0, s>>>(ckeys.ptr, nce, (int)npe, m->E, pairs.ptr);
@@ -843,21 +958,28 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
     const OwnTables ot{P.node_patch.ptr,     P.own_idx.ptr, P.own_acc.ptr,          P.patch_node_ptr.ptr,
                        P.own_hv.ptr,         cl.patch_elem_ptr.ptr, p0, (int32_t)P.max_acc};
     uint16_t *aidx16 = reinterpret_cast<uint16_t *>(cl.celem_aidx.ptr);
-    if (npe == 8)
-        k_celem_fill<8><<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, nce, m->E, cnkeys.ptr, cl.patch_cnode_ptr.ptr,
-                                                      m->rowptr.ptr, m->col.ptr, P.pos_stride, ot, cl.celem_id.ptr,
-                                                      cl.celem_color.ptr, cl.celem_lnode.ptr, cl.celem_pos.ptr, aidx16);
-    else
-        k_celem_fill<4><<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, nce, m->E, cnkeys.ptr, cl.patch_cnode_ptr.ptr,
-                                                      m->rowptr.ptr, m->col.ptr, P.pos_stride, ot, cl.celem_id.ptr,
-                                                      cl.celem_color.ptr, cl.celem_lnode.ptr, cl.celem_pos.ptr, aidx16);
-    FEM_LAUNCHED("k_celem_fill");
     FEM_CUDA(cudaMemcpyAsync(h_pc.data(), cl.patch_cnode_ptr.ptr, (np_ + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     FEM_CUDA(cudaStreamSynchronize(s));
     for (int64_t p = 0; p < np_; ++p) cl.max_cnodes = std::max(cl.max_cnodes, h_pc[p + 1] - h_pc[p]);
-    if (cl.max_cnodes > 65535) {
-        set_error("a patch touches %lld nodes; at most 65535 are supported", (long long)cl.max_cnodes);
+    if (cl.max_cnodes > 32768) {
+        set_error("a patch touches %lld nodes; at most 32768 are supported", (long long)cl.max_cnodes);
         return FEM_ERR_UNSUPPORTED;
+    }
+    {
+        const size_t smem = (size_t)std::max<int64_t>(cl.max_cnodes, 1) * sizeof(int32_t);
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np_, (int64_t)num_sms() * 8));
+        if (npe == 8) {
+            FEM_CUDA(cudaFuncSetAttribute(k_celem_fill<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_celem_fill<8><<<grid, TPB, smem, s>>>(ckeys.ptr, np_, m->E, cnkeys.ptr, cl.patch_cnode_ptr.ptr,
+                                                    m->rowptr.ptr, m->col.ptr, P.pos_stride, ot, cl.celem_id.ptr,
+                                                    cl.celem_color.ptr, cl.celem_lnode.ptr, cl.celem_pos.ptr, aidx16);
+        } else {
+            FEM_CUDA(cudaFuncSetAttribute(k_celem_fill<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_celem_fill<4><<<grid, TPB, smem, s>>>(ckeys.ptr, np_, m->E, cnkeys.ptr, cl.patch_cnode_ptr.ptr,
+                                                    m->rowptr.ptr, m->col.ptr, P.pos_stride, ot, cl.celem_id.ptr,
+                                                    cl.celem_color.ptr, cl.celem_lnode.ptr, cl.celem_pos.ptr, aidx16);
+        }
+        FEM_LAUNCHED("k_celem_fill");
     }
     return FEM_OK;
 }
