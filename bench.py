@@ -645,9 +645,50 @@ def other_workloads(flush, stream, with_error):
         mesh.close()
         del mesh, v
     del X, c
+    out["large27M_host"] = host_pipeline_workload(m, dev)
     out["elastic"] = elastic_workloads(timed, dev)
     out["backward"] = backward_workloads(timed, dev)
     return out, err
+
+
+def host_pipeline_workload(m, dev, chunks=16, reps=3):
+    """The 27M-brick build end to end through fem_build_K_host (page-locked host
+    inputs and output, one blocking call a step), K's values staged whole on the
+    device and copied out in one transfer, against the row-range pipeline
+    (fem_options.host_chunks): range k + 1 built while range k's values are copied
+    out, two ranges of values on the device.  staging_gb: the library's device
+    memory the host build adds (inputs, then K's values or two ranges of them)."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_1501_04784_gb300 import fem
+
+    Xh = torch.from_numpy(m.X.astype(np.float32)).pin_memory()
+    ch = torch.from_numpy(m.c.astype(np.float32)).pin_memory()
+    res = {}
+    for key, hc in (("whole", 0), ("pipelined", chunks)):
+        mesh = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), host_chunks=hc)
+        nnz = mesh.pattern()
+        before = mesh.info()["live_bytes"]
+        vh = torch.empty(nnz, dtype=torch.float32).pin_memory()
+        for _ in range(2):
+            mesh.build_K_host(Xh, ch, "mixed", out=vh)
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            mesh.build_K_host(Xh, ch, "mixed", out=vh)
+            ts.append(time.perf_counter() - t0)
+        info = mesh.info()
+        ms = 1e3 * float(np.median(ts))
+        res[key] = {"ms": round(ms, 3), "value": m.n_elems / (ms / 1e3), "chunks": info["n_chunks"],
+                    "staging_gb": round((info["live_bytes"] - before) / 1e9, 3)}
+        mesh.close()
+        del mesh, vh
+    res["h2d_bytes_per_step"] = Xh.nbytes + ch.nbytes
+    res["d2h_bytes_per_step"] = nnz * 4
+    return res
 
 
 def backward_workloads(timed, dev):

@@ -138,6 +138,18 @@ typedef struct {
                                     fem_vjp, fem_load_vector and fem_assemble_csr use patches,
                                     planned on their first call when tiles serve the builds */
     int tile_elems;              /* elements per tile (0 = default: 512 bricks, 2048 tetrahedra) */
+    int host_chunks;             /* scalar operators, fem_build_K_host / _async without
+                                    host_direct: 0 (default) = K's values are built whole in
+                                    device staging and copied out in one transfer; n > 1 =
+                                    the rows are split into n contiguous ranges of about
+                                    n_nodes / n rows (the node order runs range by range,
+                                    each along its own Morton curve, and the node patches
+                                    are planned inside the ranges; fixed at
+                                    fem_mesh_create), and range k + 1 is built into one of two device
+                                    slots while range k's values are copied to vals_host
+                                    from the other (Section 4.3's overlap of one group's
+                                    transfer with the next group's integration): device
+                                    memory holds 2 ranges of values, not K */
 } fem_options;
 
 /*
@@ -182,7 +194,9 @@ typedef struct {
                                     rows) */
     size_t live_bytes;           /* device bytes the library holds for the mesh now */
     size_t peak_bytes;           /* the most it has held at once */
-    int32_t reserved[2];
+    int32_t n_chunks;            /* row ranges of the host pipeline (fem_options.host_chunks;
+                                    1 = none) */
+    int32_t reserved0;
     int64_t tile_rows;           /* rows summed in tiles (a row in k tiles counts k times) */
     int64_t border_rows;         /* rows whose elements span several tiles */
     int64_t partial_values;      /* values of the border rows' partial sums */
@@ -261,12 +275,15 @@ fem_status fem_build_K(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype,
 /*
  * fem_build_K with HOST inputs and outputs (page-locked memory gives full
  * copy bandwidth; pageable memory works but is slower): copies X and c to
- * library-owned device buffers, builds, copies vals back.  Blocks until vals
- * is on the host.  Host-resident K: when the memory budget cannot hold the
- * values (or fem_options.host_direct is set) the kernel writes them straight
- * into vals_host, which must then be page-locked (FEM_ERR_BUDGET otherwise);
- * with the patch groups of the budget this builds K for meshes whose matrix
- * exceeds device memory.
+ * library-owned device buffers (one staging slot, kept for the next call),
+ * builds, copies vals back.  Blocks until vals is on the host.  With
+ * fem_options.host_chunks the values are built and copied out row range by row
+ * range, the copy of one range overlapping the build of the next, and the
+ * device holds two ranges of them.  Host-resident K: when the memory budget
+ * cannot hold the values (or fem_options.host_direct is set) the kernel writes
+ * them straight into vals_host, which must then be page-locked
+ * (FEM_ERR_BUDGET otherwise); with the patch groups of the budget this builds
+ * K for meshes whose matrix exceeds device memory.
  */
 fem_status fem_build_K_host(fem_mesh m, fem_prec p, const void *X_host, fem_dtype x_dtype,
                             const void *c_host, fem_dtype c_dtype, void *vals_host, void *stream);

@@ -27,7 +27,8 @@ class fem_options(ctypes.Structure):
                 ("fp64_fused", ctypes.c_int), ("fp64_dets", ctypes.c_int),
                 ("wait_spins", ctypes.c_int), ("debug_stall", ctypes.c_int),
                 ("operator_kind", ctypes.c_int), ("host_direct", ctypes.c_int), ("vjp_fused", ctypes.c_int),
-                ("assembly", ctypes.c_int), ("tile_elems", ctypes.c_int)]
+                ("assembly", ctypes.c_int), ("tile_elems", ctypes.c_int),
+                ("host_chunks", ctypes.c_int)]
 
 
 class fem_info(ctypes.Structure):
@@ -38,7 +39,8 @@ class fem_info(ctypes.Structure):
                 ("max_row_len", ctypes.c_int32), ("plan_bytes", ctypes.c_size_t),
                 ("budget_bytes", ctypes.c_size_t), ("n_groups", ctypes.c_int32),
                 ("assembly", ctypes.c_int32), ("live_bytes", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t),
-                ("reserved", ctypes.c_int32 * 2), ("tile_rows", ctypes.c_int64), ("border_rows", ctypes.c_int64),
+                ("n_chunks", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("tile_rows", ctypes.c_int64),
+                ("border_rows", ctypes.c_int64),
                 ("partial_values", ctypes.c_int64)]
 
 

@@ -516,10 +516,83 @@ static void *mapped(void *host) {
     return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
+// Host pipeline over the plan's row ranges (fem_options.host_chunks): range k is
+// built into device slot k % 2 on s while the values of range k - 1 go from the
+// other slot to vals_host on the mesh's copy stream (Section 4.3: one group's
+// transfer overlapped with the next group's integration).  Device memory holds
+// two ranges of values.  On return s is ordered after the last copy.
+static fem_status chunk_pipeline(fem_mesh m, fem_prec p, const void *X, fem_dtype xd, const void *c, fem_dtype cd,
+                                 void *vals_host, cudaStream_t s) {
+    Plan &P = m->plan;
+    const size_t w = p == FEM_FP64 ? sizeof(double) : sizeof(float);
+    const size_t slot = ((size_t)P.max_chunk_vals * w + 255) / 256 * 256;
+    if (!m->copy_stream) FEM_CUDA(cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking));
+    for (int j = 0; j < 2; ++j) {
+        if (!m->chunk_built[j]) FEM_CUDA(cudaEventCreateWithFlags(&m->chunk_built[j], cudaEventDisableTiming));
+        if (!m->slot_free[j]) FEM_CUDA(cudaEventCreateWithFlags(&m->slot_free[j], cudaEventDisableTiming));
+    }
+    if (m->chunk_slots.n < 2 * slot) {
+        for (cudaEvent_t e : m->slot_free) FEM_CUDA(cudaEventSynchronize(e));  // no copy reads the old slots
+        m->chunk_slots.free();
+        fem_status st = m->chunk_slots.alloc(m->arena, 2 * slot, "host pipeline value slots");
+        if (st == FEM_ERR_BUDGET)
+            set_error("the memory budget cannot hold two row ranges of values (%zu bytes); raise host_chunks", 2 * slot);
+        FEM_TRY(st);
+    }
+    // FP64 integrates every element once up front (the FP64 pipe bounds it) and
+    // assembles the ranges from those matrices; falls back to the fused kernel
+    // when the budget refuses them
+    bool staged = false;
+    if (p == FEM_FP64 && !P.chunked && m->opt.fp64_fused == 0) {
+        const size_t n = (size_t)m->n_elems * m->np;
+        fem_status st = m->ke64.n >= n ? FEM_OK : m->ke64.alloc(m->arena, n, "FP64 element matrices");
+        if (st == FEM_OK) {
+            IntegrateArgs ia{m->npe, false, xd, cd, m->E, m->n_elems, X, c, m->ke64.ptr,
+                             default_threshold(m), nullptr, kernel_mode(m->opt), m->status.ptr};
+            FEM_TRY(launch_integrate(ia, s));
+            staged = true;
+        } else if (st != FEM_ERR_BUDGET) {
+            return st;
+        }
+    }
+    PatchArgs a = patch_args(m, p, !staged);
+    if (staged) {
+        a.xd = a.cd = FEM_F64;
+        a.ke = m->ke64.ptr;
+    } else {
+        a.xd = xd;
+        a.cd = cd;
+        a.X = X;
+        a.c = c;
+    }
+    unsigned char *host = static_cast<unsigned char *>(vals_host);
+    for (int k = 0; k < P.n_chunks(); ++k) {
+        const int j = k & 1;
+        const int64_t v0 = P.chunk_val[k], nv = P.chunk_val[k + 1] - v0;
+        if (nv == 0) continue;
+        unsigned char *dst = m->chunk_slots.ptr + j * slot;
+        FEM_CUDA(cudaStreamWaitEvent(s, m->slot_free[j], 0));  // the slot's previous range has left
+        a.vals = dst;
+        a.val_off = v0;
+        a.p0 = P.chunk_patch[k];
+        a.p1 = P.chunk_patch[k + 1];
+        FEM_TRY(for_each_group_in(m, a.p0, a.p1, s, [&](const Closure &cl) {
+            a.closure = &cl;
+            return launch_patch(a, s);
+        }));
+        FEM_CUDA(cudaEventRecord(m->chunk_built[j], s));
+        FEM_CUDA(cudaStreamWaitEvent(m->copy_stream, m->chunk_built[j], 0));
+        FEM_CUDA(cudaMemcpyAsync(host + v0 * w, dst, nv * w, cudaMemcpyDeviceToHost, m->copy_stream));
+        FEM_CUDA(cudaEventRecord(m->slot_free[j], m->copy_stream));
+    }
+    for (cudaEvent_t e : m->slot_free) FEM_CUDA(cudaStreamWaitEvent(s, e, 0));
+    return FEM_OK;
+}
+
 // Copy in, build, copy out, ordered on s through one of the mesh's staging
 // slots (see fem_mesh_s::host_stage); returns without waiting.
 static fem_status host_build(fem_mesh m, fem_prec p, const void *X_host, fem_dtype x_dtype, const void *c_host,
-                             fem_dtype c_dtype, void *vals_host, cudaStream_t s, const char *who) {
+                             fem_dtype c_dtype, void *vals_host, cudaStream_t s, const char *who, bool rotate) {
     NvtxRange nvtx_range(who);
     FEM_TRY(check_inputs(m, p, X_host, x_dtype, c_host, c_dtype));
     if (!m->has_pattern) {
@@ -537,9 +610,17 @@ static fem_status host_build(fem_mesh m, fem_prec p, const void *X_host, fem_dty
     // Values in device staging and one copy out; or (host_direct, or when the
     // budget refuses the staging) written by the kernel straight into vals_host
     // through its device mapping.
+    // Or (host_chunks) built and copied out row range by row range.
     void *direct = nullptr;
-    const int k = m->stage_next;
-    const bool stage_fits = m->host_stage[k].n >= vo + vb || !m->arena.budget ||
+    // the asynchronous entry takes the slots in turn; the blocking one always
+    // takes slot 0 (it is done with it on return), so it holds one slot
+    const int k = rotate ? m->stage_next : 0;
+    bool pipe = m->opt.host_chunks > 1 && !m->opt.host_direct && !is_elastic(m);
+    if (pipe) {
+        FEM_TRY(ensure_plan(m, s));
+        pipe = m->plan.n_chunks() > 1;
+    }
+    const bool stage_fits = pipe || m->host_stage[k].n >= vo + vb || !m->arena.budget ||
                             m->arena.live - m->host_stage[k].n + vo + vb <= m->arena.budget;
     if (m->opt.host_direct || !stage_fits) {
         direct = mapped(vals_host);
@@ -549,7 +630,7 @@ static fem_status host_build(fem_mesh m, fem_prec p, const void *X_host, fem_dty
             return m->opt.host_direct ? FEM_ERR_ARG : FEM_ERR_BUDGET;
         }
     }
-    const size_t total = direct ? vo : vo + vb;
+    const size_t total = (direct || pipe) ? vo : vo + vb;
     for (cudaEvent_t &e : m->stage_free)
         if (!e) FEM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     if (!m->built) FEM_CUDA(cudaEventCreateWithFlags(&m->built, cudaEventDisableTiming));
@@ -558,15 +639,18 @@ static fem_status host_build(fem_mesh m, fem_prec p, const void *X_host, fem_dty
         m->host_stage[k].free();
         FEM_TRY(m->host_stage[k].alloc(m->arena, total, "host staging"));
     }
-    m->stage_next = (k + 1) % fem_mesh_s::HOST_STAGES;
+    if (rotate) m->stage_next = (k + 1) % fem_mesh_s::HOST_STAGES;
     unsigned char *base = m->host_stage[k].ptr;
     FEM_CUDA(cudaStreamWaitEvent(s, m->stage_free[k], 0));
     FEM_CUDA(cudaMemcpyAsync(base + xo, X_host, xb, cudaMemcpyHostToDevice, s));
     FEM_CUDA(cudaMemcpyAsync(base + co, c_host, cb, cudaMemcpyHostToDevice, s));
     FEM_CUDA(cudaStreamWaitEvent(s, m->built, 0));
-    FEM_TRY(fem_build_K(m, p, base + xo, x_dtype, base + co, c_dtype, direct ? direct : base + vo, s));
+    if (pipe)
+        FEM_TRY(chunk_pipeline(m, p, base + xo, x_dtype, base + co, c_dtype, vals_host, s));
+    else
+        FEM_TRY(fem_build_K(m, p, base + xo, x_dtype, base + co, c_dtype, direct ? direct : base + vo, s));
     FEM_CUDA(cudaEventRecord(m->built, s));
-    if (!direct) FEM_CUDA(cudaMemcpyAsync(vals_host, base + vo, vb, cudaMemcpyDeviceToHost, s));
+    if (!direct && !pipe) FEM_CUDA(cudaMemcpyAsync(vals_host, base + vo, vb, cudaMemcpyDeviceToHost, s));
     FEM_CUDA(cudaEventRecord(m->stage_free[k], s));
     return FEM_OK;
 }
@@ -584,7 +668,7 @@ static bool pinned(const void *p) {
 fem_status fem_build_K_host(fem_mesh m, fem_prec p, const void *X_host, fem_dtype x_dtype, const void *c_host,
                             fem_dtype c_dtype, void *vals_host, void *stream) {
     cudaStream_t s = as_stream(stream);
-    FEM_TRY(host_build(m, p, X_host, x_dtype, c_host, c_dtype, vals_host, s, "fem_build_K_host"));
+    FEM_TRY(host_build(m, p, X_host, x_dtype, c_host, c_dtype, vals_host, s, "fem_build_K_host", false));
     FEM_CUDA(cudaStreamSynchronize(s));
     return check_status(m, s);
 }
@@ -595,7 +679,8 @@ fem_status fem_build_K_host_async(fem_mesh m, fem_prec p, const void *X_host, fe
         set_error("fem_build_K_host_async needs page-locked host buffers (cudaHostAlloc or cudaHostRegister)");
         return FEM_ERR_ARG;
     }
-    return host_build(m, p, X_host, x_dtype, c_host, c_dtype, vals_host, as_stream(stream), "fem_build_K_host_async");
+    return host_build(m, p, X_host, x_dtype, c_host, c_dtype, vals_host, as_stream(stream), "fem_build_K_host_async",
+                      true);
 }
 
 fem_status fem_vjp(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, const void *c, fem_dtype c_dtype,
@@ -867,6 +952,7 @@ fem_status fem_mesh_info(fem_mesh m, fem_info *info) {
                        m->inc_elem.bytes();
     info->budget_bytes = m->arena.budget;
     info->n_groups = m->n_groups;
+    info->n_chunks = m->plan_built ? m->plan.n_chunks() : 1;
     info->live_bytes = m->arena.live;
     info->peak_bytes = m->arena.peak;
     return FEM_OK;

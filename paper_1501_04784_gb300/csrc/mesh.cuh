@@ -43,6 +43,8 @@ struct PlanView {
     // diagonal is summed FP64-accurately.
     const uint32_t *celem_aidx;
     int64_t aidx_n;                  // total celems (the word stride)
+    int64_t val_off;                 // subtracted from own_rowptr: vals holds the values from
+                                     // this CSR position on (a row range of the host pipeline)
     int64_t n_nodes, n_elems, nnz;   // sizes of X, c and vals (bounds checks of the debug build)
 };
 
@@ -87,6 +89,14 @@ struct Plan {
     // aggregate statistics (over all groups when chunked)
     int64_t total_cnodes = 0, total_celems = 0, max_cnodes = 0, max_celems = 0;
     int n_colors = 0;
+    // Row ranges of the host pipeline (fem_options.host_chunks; one range when
+    // off): range k owns rows [chunk_row[k], chunk_row[k+1]), whose values are
+    // CSR positions [chunk_val[k], chunk_val[k+1]), and patches
+    // [chunk_patch[k], chunk_patch[k+1]) (no patch owns rows of two ranges).
+    std::vector<int64_t> chunk_row, chunk_val, chunk_patch;
+    int64_t max_chunk_vals = 0;
+    int64_t cap_entries = 0;  // entries a patch was cut to hold
+    int n_chunks() const { return chunk_row.empty() ? 1 : (int)chunk_row.size() - 1; }
     PlanView view(const Closure &cl) const {
         PlanView v{};
         v.patch_node_ptr = patch_node_ptr.ptr + cl.p0;
@@ -106,6 +116,7 @@ struct Plan {
         v.n_patches = cl.p1 - cl.p0;
         v.celem_aidx = cl.celem_aidx.ptr;
         v.aidx_n = cl.total_celems;
+        v.val_off = 0;
         v.n_nodes = n_nodes;
         v.n_elems = n_elems;
         v.nnz = nnz;
@@ -119,6 +130,11 @@ struct Plan {
         n_colors = 0;
         chunked = false;
         any_hv = false;
+        chunk_row.clear();
+        chunk_val.clear();
+        chunk_patch.clear();
+        max_chunk_vals = 0;
+        cap_entries = 0;
     }
     size_t bytes() const {
         return patch_node_ptr.bytes() + own_rowptr.bytes() + patch_acc.bytes() + own_acc.bytes() + own_row.bytes() +
@@ -135,7 +151,8 @@ struct fem_mesh_s {
     const int32_t *E = nullptr;  // caller-owned connectivity
     fem_options opt;
     fem::Arena arena;
-    fem::DevBuf<int32_t> order;    // node order along the locality curve
+    fem::DevBuf<int32_t> order;    // node order along the locality curve (range by range, see chunk_rows)
+    std::vector<int64_t> chunk_rows;  // row ranges of the host pipeline: [chunk_rows[k], chunk_rows[k+1])
     bool has_pattern = false;
     int64_t nnz = 0;
     int max_row_len = 0;
@@ -165,11 +182,22 @@ struct fem_mesh_s {
         for (cudaEvent_t e : stage_free)
             if (e) cudaEventDestroy(e);
         if (built) cudaEventDestroy(built);
+        for (int j = 0; j < 2; ++j) {
+            if (chunk_built[j]) cudaEventDestroy(chunk_built[j]);
+            if (slot_free[j]) cudaEventDestroy(slot_free[j]);
+        }
+        if (copy_stream) cudaStreamDestroy(copy_stream);
     }
     // FP64 element matrices staged between integration and assembly (the FP64
     // pipe is the bound there, so integrating each element once beats recomputing
     // it in every closure that contains it)
     fem::DevBuf<double> ke64;
+    // host pipeline over row ranges: two device value slots used in turn, the
+    // stream their copies to the host run on, chunk_built[j] recorded after the
+    // build of the range in slot j, slot_free[j] after its copy out
+    fem::DevBuf<unsigned char> chunk_slots;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t chunk_built[2] = {}, slot_free[2] = {};
     int n_groups = 1;
     int64_t group_patches = 0;  // patches per group when the closures are built per group
 };
@@ -185,4 +213,8 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
 // Runs fn over the closure of every patch group (one group covering all patches
 // unless the plan is chunked under the memory budget).
 fem_status for_each_group(fem_mesh m, cudaStream_t s, const std::function<fem_status(const Closure &)> &fn);
+// The same over patches [pa, pb) only: closures that hold them (the whole plan's
+// when it is not chunked; the caller restricts the launch to [pa, pb)).
+fem_status for_each_group_in(fem_mesh m, int64_t pa, int64_t pb, cudaStream_t s,
+                             const std::function<fem_status(const Closure &)> &fn);
 }  // namespace fem

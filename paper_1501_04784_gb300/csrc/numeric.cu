@@ -222,7 +222,7 @@ __device__ __forceinline__ void patch_body(const PlanView &pv, const S *__restri
             for (int k = 0; k < CH; ++k) {
                 const int kk = k0 + k * nthr + tid;
                 vr[k] = kk < nown ? pv.own_acc[nb + kk] : 0;
-                vp[k] = kk < nown ? pv.own_rowptr[nb + kk] : 0;
+                vp[k] = kk < nown ? pv.own_rowptr[nb + kk] - pv.val_off : 0;
                 vh[k] = (MIXED && kk < nown) ? pv.own_hv[nb + kk] : 0;
             }
 #pragma unroll
@@ -545,11 +545,14 @@ static fem_status launch_patch_t(const PatchArgs &a, cudaStream_t s) {
         return FEM_ERR_UNSUPPORTED;
     }
     if (a.blocks_per_sm > 0 && a.blocks_per_sm < per_sm) per_sm = a.blocks_per_sm;
-    const int64_t np = cl.p1 - cl.p0;
-    if (np <= 0) return FEM_OK;
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np, (int64_t)num_sms() * per_sm));
-    f<<<grid, threads, L.total, s>>>(P.view(cl), (const S *)a.X, (const CT *)a.c, (const AccT *)a.ke, (AccT *)a.vals,
-                                     a.thr, 0, np, L, a.mode, a.wait);
+    // the patches of [a.p0, a.p1) that the closure holds, relative to its first
+    const int64_t q0 = std::max(a.p0, cl.p0) - cl.p0, q1 = std::min(a.p1, cl.p1) - cl.p0;
+    if (q1 <= q0) return FEM_OK;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(q1 - q0, (int64_t)num_sms() * per_sm));
+    PlanView pv = P.view(cl);
+    pv.val_off = a.val_off;
+    f<<<grid, threads, L.total, s>>>(pv, (const S *)a.X, (const CT *)a.c, (const AccT *)a.ke, (AccT *)a.vals, a.thr,
+                                     q0, q1, L, a.mode, a.wait);
     FEM_LAUNCHED("k_patch");
     return FEM_OK;
 }

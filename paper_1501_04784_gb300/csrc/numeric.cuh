@@ -75,7 +75,8 @@ struct PatchArgs {
     const void *X, *c, *ke;
     void *vals;
     float thr;
-    int64_t p0, p1;
+    int64_t p0, p1;    // patches to run (absolute numbers; those the closure holds)
+    int64_t val_off;   // vals holds the CSR values from this position on (scalar operators)
     int threads, blocks_per_sm;
     WaitCtl wait;
     unsigned mode;  // FP64_SUMS: high-valence sums with FP64 adds instead of FP32 TwoSum pairs;

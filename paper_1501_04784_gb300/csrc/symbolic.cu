@@ -77,23 +77,51 @@ __device__ __forceinline__ double ord_val(unsigned long long k) {
     return __longlong_as_double((long long)b);
 }
 
+// The row range (fem_options.host_chunks) holding node g: the last k < nr with
+// rows[k] <= g; range 0 when there are none (rows null).
+__device__ __forceinline__ int range_of(const int64_t *rows, int nr, int64_t g) {
+    int k = 0;
+    if (rows)
+        for (int lo = 0, hi = nr - 1; lo <= hi;) {
+            const int mid = (lo + hi) >> 1;
+            if (rows[mid] <= g) { k = mid; lo = mid + 1; } else hi = mid - 1;
+        }
+    return k;
+}
+
+// Bounding box of each row range's nodes (one box when rows is null):
+// bb[6k .. 6k+5] = min xyz, max xyz.  A warp whose 32 nodes share a range
+// reduces them before its atomics.
 template <typename S>
-__global__ void k_bbox(const S *__restrict__ X, int64_t N, unsigned long long *bb /*6: min xyz, max xyz*/) {
-    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+__global__ void k_bbox(const S *__restrict__ X, int64_t N, const int64_t *rows, int nr, unsigned long long *bb) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (N + 31) / 32 * 32;  // every lane of a warp takes the same trips
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nw; i += (int64_t)gridDim.x * blockDim.x) {
+        const bool valid = i < N;
+        const int r = valid ? range_of(rows, nr, i) : -1;
+        double lo[3], hi[3];
         for (int d = 0; d < 3; ++d) {
-            double v = (double)X[3 * i + d];
-            lo[d] = fmin(lo[d], v);
-            hi[d] = fmax(hi[d], v);
+            const double v = valid ? (double)X[3 * i + d] : 0.0;
+            lo[d] = valid ? v : 1e300;
+            hi[d] = valid ? v : -1e300;
         }
-    for (int d = 0; d < 3; ++d) {
-        for (int o = 16; o > 0; o >>= 1) {
-            lo[d] = fmin(lo[d], __shfl_down_sync(0xffffffffu, lo[d], o));
-            hi[d] = fmax(hi[d], __shfl_down_sync(0xffffffffu, hi[d], o));
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicMin(&bb[d], ord_key(lo[d]));
-            atomicMax(&bb[3 + d], ord_key(hi[d]));
+        const int r0 = __shfl_sync(0xffffffffu, r, 0);
+        if (__all_sync(0xffffffffu, r == r0 || r < 0)) {
+            for (int d = 0; d < 3; ++d)
+                for (int o = 16; o > 0; o >>= 1) {
+                    lo[d] = fmin(lo[d], __shfl_down_sync(0xffffffffu, lo[d], o));
+                    hi[d] = fmax(hi[d], __shfl_down_sync(0xffffffffu, hi[d], o));
+                }
+            if (lane == 0 && r0 >= 0)
+                for (int d = 0; d < 3; ++d) {
+                    atomicMin(&bb[6 * r0 + d], ord_key(lo[d]));
+                    atomicMax(&bb[6 * r0 + 3 + d], ord_key(hi[d]));
+                }
+        } else if (valid) {
+            for (int d = 0; d < 3; ++d) {
+                atomicMin(&bb[6 * r + d], ord_key(lo[d]));
+                atomicMax(&bb[6 * r + 3 + d], ord_key(hi[d]));
+            }
         }
     }
 }
@@ -107,23 +135,37 @@ __device__ __forceinline__ uint32_t spread10(uint32_t v) {
     return v;
 }
 
+// Key of node i: its row range above the 30-bit Morton code of its coordinates
+// in that range's bounding box, scaled alike on the three axes.
 template <typename S>
-__global__ void k_morton(const S *__restrict__ X, int64_t N, const unsigned long long *bb, uint64_t *keys,
-                         uint32_t *vals) {
-    double lo[3], sc[3];
-    for (int d = 0; d < 3; ++d) {
-        lo[d] = ord_val(bb[d]);
-        double w = ord_val(bb[3 + d]) - lo[d];
-        sc[d] = w > 0 ? 1023.0 / w : 0.0;
-    }
+__global__ void k_morton(const S *__restrict__ X, int64_t N, const unsigned long long *bb, const int64_t *rows,
+                         int nr, uint64_t *keys, uint32_t *vals) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int r = range_of(rows, nr, i);
+        double lo[3], ext[3], w = 0.0, vol = 1.0;
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = ord_val(bb[6 * r + d]);
+            ext[d] = ord_val(bb[6 * r + 3 + d]) - lo[d];
+            w = fmax(w, ext[d]);
+            vol *= fmax(ext[d], 1e-300);
+        }
+        // one scale for the three axes (cubic cells, whatever the box's shape)
+        const double sc = w > 0 ? 1023.0 / w : 0.0;
+        // Ranges: coordinates within half a mean node spacing of the box's faces
+        // are moved onto that inset, so a layer of nodes on a face (a plane of a
+        // structured numbering cut by the range) keeps one code per axis there
+        // instead of straddling a coarse cell boundary, whose far side would hold
+        // only that layer's nodes, visited apart from their neighbours.
+        const double h = rows ? cbrt(vol / (double)(rows[r + 1] - rows[r])) : 0.0;
         uint32_t q[3];
         for (int d = 0; d < 3; ++d) {
-            double t = ((double)X[3 * i + d] - lo[d]) * sc[d];
+            const double in = fmin(0.5 * h, 0.25 * ext[d]);
+            const double v = fmin(fmax((double)X[3 * i + d], lo[d] + in), lo[d] + ext[d] - in);
+            double t = (v - lo[d]) * sc;
             t = t < 0 ? 0 : (t > 1023 ? 1023 : t);
             q[d] = (uint32_t)t;
         }
-        keys[i] = (uint64_t)(spread10(q[0]) | (spread10(q[1]) << 1) | (spread10(q[2]) << 2));
+        keys[i] = ((uint64_t)r << 30) | (uint64_t)(spread10(q[0]) | (spread10(q[1]) << 1) | (spread10(q[2]) << 2));
         vals[i] = (uint32_t)i;
     }
 }
@@ -135,35 +177,56 @@ __global__ void k_iota(int32_t *o, int64_t n) {
 
 fem_status build_locality_order(fem_mesh m, const void *X, fem_dtype xd, cudaStream_t s) {
     const int64_t N = m->n_nodes;
+    // Row ranges of the host pipeline (fem_options.host_chunks, scalar operators):
+    // n_r ranges of about N / n_r rows each.  The order then runs range by range,
+    // each range along the Morton curve of its own bounding box: a range cut
+    // through a plane of a structured numbering would otherwise leave the cut
+    // plane's nodes that the global curve visits with the next range's nodes as a
+    // scattered tail of this range.
+    const int nr = (m->opt.host_chunks > 1 && m->opt.operator_kind != 2 && N > 0)
+                       ? (int)std::min<int64_t>(std::min(m->opt.host_chunks, 4096), N)
+                       : 1;
+    m->chunk_rows.assign(nr + 1, 0);
+    for (int k = 0; k <= nr; ++k) m->chunk_rows[k] = (int64_t)k * N / nr;
     FEM_TRY(m->order.alloc(m->arena, N, "node order"));
     if (!X || !m->opt.locality_order) {
-        k_iota<<<grid_for(N), TPB, 0, s>>>(m->order.ptr, N);
+        k_iota<<<grid_for(N), TPB, 0, s>>>(m->order.ptr, N);  // ids: already grouped by range
         FEM_LAUNCHED("k_iota");
         return FEM_OK;
     }
     DevBuf<unsigned long long> bb;
     DevBuf<uint64_t> keys, alt;
     DevBuf<uint32_t> alt_vals;
-    DevBuf<int64_t> hist;
-    FEM_TRY(bb.alloc(m->arena, 6, "bbox"));
+    DevBuf<int64_t> hist, rows;
+    FEM_TRY(bb.alloc(m->arena, 6 * (size_t)nr, "bbox"));
     FEM_TRY(keys.alloc(m->arena, N, "morton keys"));
     FEM_TRY(alt.alloc(m->arena, N, "morton keys'"));
     FEM_TRY(alt_vals.alloc(m->arena, N, "morton vals'"));
     FEM_TRY(hist.alloc(m->arena, radix_hist_elems(N), "radix histogram"));
-    unsigned long long init[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
-    FEM_CUDA(cudaMemcpyAsync(bb.ptr, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    std::vector<unsigned long long> init(6 * (size_t)nr);
+    for (int k = 0; k < nr; ++k)
+        for (int d = 0; d < 3; ++d) init[6 * k + d] = ~0ull, init[6 * k + 3 + d] = 0ull;
+    FEM_CUDA(cudaMemcpyAsync(bb.ptr, init.data(), init.size() * sizeof(init[0]), cudaMemcpyHostToDevice, s));
+    const int64_t *rp = nullptr;
+    if (nr > 1) {
+        FEM_TRY(rows.alloc(m->arena, nr + 1, "row ranges"));
+        FEM_CUDA(cudaMemcpyAsync(rows.ptr, m->chunk_rows.data(), (nr + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        rp = rows.ptr;
+    }
     uint32_t *vals = reinterpret_cast<uint32_t *>(m->order.ptr);
     if (xd == FEM_F64) {
-        k_bbox<double><<<grid_for(N), TPB, 0, s>>>((const double *)X, N, bb.ptr);
+        k_bbox<double><<<grid_for(N), TPB, 0, s>>>((const double *)X, N, rp, nr, bb.ptr);
         FEM_LAUNCHED("k_bbox");
-        k_morton<double><<<grid_for(N), TPB, 0, s>>>((const double *)X, N, bb.ptr, keys.ptr, vals);
+        k_morton<double><<<grid_for(N), TPB, 0, s>>>((const double *)X, N, bb.ptr, rp, nr, keys.ptr, vals);
     } else {
-        k_bbox<float><<<grid_for(N), TPB, 0, s>>>((const float *)X, N, bb.ptr);
+        k_bbox<float><<<grid_for(N), TPB, 0, s>>>((const float *)X, N, rp, nr, bb.ptr);
         FEM_LAUNCHED("k_bbox");
-        k_morton<float><<<grid_for(N), TPB, 0, s>>>((const float *)X, N, bb.ptr, keys.ptr, vals);
+        k_morton<float><<<grid_for(N), TPB, 0, s>>>((const float *)X, N, bb.ptr, rp, nr, keys.ptr, vals);
     }
     FEM_LAUNCHED("k_morton");
-    FEM_TRY(radix_sort_u64(keys.ptr, vals, N, 30, alt.ptr, alt_vals.ptr, hist.ptr, s));
+    int bits = 0;
+    while ((1 << bits) < nr) ++bits;
+    FEM_TRY(radix_sort_u64(keys.ptr, vals, N, 30 + bits, alt.ptr, alt_vals.ptr, hist.ptr, s));
     FEM_CUDA(cudaStreamSynchronize(s));  // temporaries are freed on return
     return FEM_OK;
 }
@@ -293,32 +356,48 @@ __global__ void k_len_in_order(const int32_t *order, const int64_t *rowptr, int6
 }
 
 // first index with pre[k] >= p * cap (lower bound), p = 0..npatch-1; ptr[npatch] = N
-__global__ void k_patch_bounds(const int64_t *pre, int64_t N, int64_t cap, int64_t npatch, int64_t *ptr) {
+// Patch bounds inside row ranges.  Range k covers positions [c_row[k], c_row[k+1])
+// of the node order and patches [c_patch[k], c_patch[k+1]); its patch j starts at
+// the first position whose row-length prefix reaches pre[c_row[k]] + j * c_cap[k].
+// One range spanning every node is the plain cut into patches of `cap` entries.
+__global__ void k_patch_bounds(const int64_t *pre, const int64_t *c_row, const int64_t *c_patch,
+                               const int64_t *c_cap, int nc, int64_t npatch, int64_t *ptr) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p <= npatch; p += (int64_t)gridDim.x * blockDim.x) {
         if (p == npatch) {
-            ptr[p] = N;
+            ptr[p] = c_row[nc];
             continue;
         }
-        const int64_t target = p * cap;
-        int64_t lo = 0, hi = N;
+        int k = 0;  // the range holding patch p: the last with c_patch[k] <= p
+        for (int lo = 0, hi = nc - 1; lo <= hi;) {
+            const int mid = (lo + hi) >> 1;
+            if (c_patch[mid] <= p) { k = mid; lo = mid + 1; } else hi = mid - 1;
+        }
+        const int64_t j = p - c_patch[k], r0 = c_row[k];
+        if (j == 0) {
+            ptr[p] = r0;
+            continue;
+        }
+        const int64_t target = pre[r0] + j * c_cap[k];
+        int64_t lo = r0, hi = c_row[k + 1];
         while (lo < hi) {
-            int64_t mid = (lo + hi) >> 1;
+            const int64_t mid = (lo + hi) >> 1;
             if (pre[mid] < target) lo = mid + 1; else hi = mid;
         }
-        ptr[p] = (p == 0) ? 0 : lo;
+        ptr[p] = lo;
     }
 }
 
 __global__ void k_patch_nodes(const int32_t *order, const int64_t *pre, const int64_t *pn_ptr, int64_t N,
-                              int64_t cap, int64_t npatch, const int64_t *rowptr, const int64_t *inc_ptr, int hv_thr,
+                              int64_t npatch, const int64_t *rowptr, const int64_t *inc_ptr, int hv_thr,
                               int32_t *node_patch, int32_t *own_idx, int32_t *own_row, int64_t *own_rowptr,
                               int32_t *own_acc, uint8_t *own_hv) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
-        int64_t p = pre[k] / cap;
-        if (p > npatch - 1) p = npatch - 1;
-        // a row that starts exactly at a boundary may have been put in the next patch by the bound search
-        while (p > 0 && pn_ptr[p] > k) --p;
-        while (p < npatch - 1 && pn_ptr[p + 1] <= k) ++p;
+        // the patch holding position k: the last p < npatch with pn_ptr[p] <= k
+        int64_t p = 0;
+        for (int64_t lo = 0, hi = npatch - 1; lo <= hi;) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (pn_ptr[mid] <= k) { p = mid; lo = mid + 1; } else hi = mid - 1;
+        }
         const int32_t g = order[k];
         node_patch[g] = (int32_t)p;
         own_idx[g] = (int32_t)(k - pn_ptr[p]);
@@ -332,6 +411,11 @@ __global__ void k_patch_nodes(const int32_t *order, const int64_t *pre, const in
 __global__ void k_patch_acc(const int64_t *pre, const int64_t *pn_ptr, int64_t npatch, int32_t *acc) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npatch; p += (int64_t)gridDim.x * blockDim.x)
         acc[p] = (int32_t)(pre[pn_ptr[p + 1]] - pre[pn_ptr[p]]);
+}
+
+// CSR start of each row range: val[k] = rowptr[row[k]], k = 0 .. nr.
+__global__ void k_range_vals(const int64_t *rowptr, const int64_t *row, int nr, int64_t *val) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= nr; k += gridDim.x * blockDim.x) val[k] = rowptr[row[k]];
 }
 
 // ------------------------------------------------------------- closure lists
@@ -1017,6 +1101,16 @@ fem_status for_each_group(fem_mesh m, cudaStream_t s, const std::function<fem_st
     return FEM_OK;
 }
 
+fem_status for_each_group_in(fem_mesh m, int64_t pa, int64_t pb, cudaStream_t s,
+                             const std::function<fem_status(const Closure &)> &fn) {
+    Plan &P = m->plan;
+    if (!P.chunked) return fn(P.full);
+    int groups = 0;
+    for (int64_t p0 = pa; p0 < pb; p0 += m->group_patches)
+        FEM_TRY(closure_range(m, p0, std::min(pb, p0 + m->group_patches), s, fn, &groups));
+    return FEM_OK;
+}
+
 static fem_status plan_groups(fem_mesh m, cudaStream_t s) {
     Plan &P = m->plan;
     int64_t G = std::max<int64_t>(1, P.n_patches / 2);
@@ -1049,7 +1143,7 @@ static fem_status plan_groups(fem_mesh m, cudaStream_t s) {
 // Global part of the plan (patches of consecutive nodes in locality order, the
 // owned-row tables), then the closures of all patches at once if the memory
 // budget holds them, else closures are built per patch group by each numeric call.
-fem_status build_plan(fem_mesh m, cudaStream_t s) {
+static fem_status build_plan_cap(fem_mesh m, cudaStream_t s, int64_t cap_in) {
     Arena &ar = m->arena;
     const int64_t N = m->n_nodes;
     Plan &P = m->plan;
@@ -1058,10 +1152,27 @@ fem_status build_plan(fem_mesh m, cudaStream_t s) {
     // the elasticity operator holds a 3x3 block per node pair: fewer pairs fit
     const bool elastic = m->opt.operator_kind == 2;
     // (defaults measured on the 1M-brick and 3.07M-tet workloads)
-    int64_t cap_entries = m->opt.patch_entries > 0 ? m->opt.patch_entries
-                                                   : (elastic ? (m->npe == 8 ? 4096 : 1536) : 8192);
+    int64_t cap_entries = cap_in > 0 ? cap_in
+                                     : m->opt.patch_entries > 0 ? m->opt.patch_entries
+                                                                : (elastic ? (m->npe == 8 ? 4096 : 1536) : 8192);
     if (cap_entries < 2 * (int64_t)m->max_row_len) cap_entries = 2 * (int64_t)m->max_row_len;
+    P.cap_entries = cap_entries;
     int64_t cap_eff = cap_entries - m->max_row_len;
+    // Row ranges of the host pipeline (fixed with the node order, which runs
+    // range by range): their CSR starts.
+    const int nc = (!elastic && m->nnz > 0 && m->chunk_rows.size() > 2) ? (int)m->chunk_rows.size() - 1 : 1;
+    std::vector<int64_t> c_row(nc + 1), c_val(nc + 1);
+    c_row[0] = 0, c_row[nc] = N, c_val[0] = 0, c_val[nc] = m->nnz;
+    if (nc > 1) {
+        c_row = m->chunk_rows;
+        DevBuf<int64_t> rv;
+        FEM_TRY(rv.alloc(ar, 2 * (nc + 1), "row ranges"));
+        FEM_CUDA(cudaMemcpyAsync(rv.ptr, c_row.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        k_range_vals<<<1, 256, 0, s>>>(m->rowptr.ptr, rv.ptr, nc, rv.ptr + nc + 1);
+        FEM_LAUNCHED("k_range_vals");
+        FEM_CUDA(cudaMemcpyAsync(c_val.data(), rv.ptr + nc + 1, (nc + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        FEM_CUDA(cudaStreamSynchronize(s));
+    }
     DevBuf<int64_t> pre;
     {
         DevBuf<int64_t> len, tmp;
@@ -1073,10 +1184,11 @@ fem_status build_plan(fem_mesh m, cudaStream_t s) {
         FEM_TRY(scan_exclusive_i64(len.ptr, pre.ptr, N, true, tmp.ptr, s));
         FEM_CUDA(cudaStreamSynchronize(s));
     }
-    // Whole waves: the patch count is rounded up to a multiple of the resident
-    // blocks of the patch kernel (smaller patches, same cap), so that no block
-    // slot idles in the last wave while others run a patch more.  Below half a
-    // wave the mesh keeps its patches.
+    // Whole waves: a range's patch count is rounded up to a multiple of the
+    // resident blocks of the patch kernel (smaller patches, same cap), so that no
+    // block slot idles in the last wave while others run a patch more.  Below
+    // half a wave the range keeps its patches.
+    int64_t wave = 0;
     if (m->nnz > 0) {
         int threads = m->opt.block_threads > 0 ? m->opt.block_threads : 256;
         threads = std::min((threads + 31) / 32 * 32, patch_max_threads(m->npe));
@@ -1090,11 +1202,19 @@ fem_status build_plan(fem_mesh m, cudaStream_t s) {
         } else {
             per_sm = patch_blocks_per_sm(m->npe, threads);
         }
-        const int64_t wave = (int64_t)num_sms() * per_sm;
-        const int64_t np0 = cdiv(m->nnz, cap_eff);
-        if (np0 * 2 > wave) cap_eff = std::max<int64_t>(1, cdiv(m->nnz, cdiv(np0, wave) * wave));
+        wave = (int64_t)num_sms() * per_sm;
     }
-    P.n_patches = m->nnz > 0 ? cdiv(m->nnz, cap_eff) : 1;
+    std::vector<int64_t> c_patch(nc + 1, 0), c_cap(nc, cap_eff);
+    for (int k = 0; k < nc; ++k) {
+        const int64_t e = c_val[k + 1] - c_val[k];
+        int64_t cap = cap_eff;
+        const int64_t n0 = cdiv(e, cap);
+        if (e > 0 && n0 * 2 > wave) cap = std::max<int64_t>(1, cdiv(e, cdiv(n0, wave) * wave));
+        c_cap[k] = cap;
+        c_patch[k + 1] = c_patch[k] + (e > 0 ? cdiv(e, cap) : 0);
+    }
+    if (c_patch[nc] == 0) c_patch[nc] = 1;  // no entries: one empty patch
+    P.n_patches = c_patch[nc];
     P.n_nodes = m->n_nodes;
     P.n_elems = m->n_elems;
     P.nnz = m->nnz;
@@ -1103,10 +1223,23 @@ fem_status build_plan(fem_mesh m, cudaStream_t s) {
         set_error("too many patches (%lld)", (long long)npatch);
         return FEM_ERR_UNSUPPORTED;
     }
+    P.chunk_row = c_row;
+    P.chunk_val = c_val;
+    P.chunk_patch = c_patch;
+    for (int k = 0; k < nc; ++k) P.max_chunk_vals = std::max(P.max_chunk_vals, c_val[k + 1] - c_val[k]);
     P.pos_stride = (int)((m->np + 3) / 4 * 4);
     FEM_TRY(P.patch_node_ptr.alloc(ar, npatch + 1, "patch node ptr"));
-    k_patch_bounds<<<grid_for(npatch + 1), TPB, 0, s>>>(pre.ptr, N, cap_eff, npatch, P.patch_node_ptr.ptr);
-    FEM_LAUNCHED("k_patch_bounds");
+    {
+        DevBuf<int64_t> tab;
+        FEM_TRY(tab.alloc(ar, 3 * (size_t)nc + 2, "range table"));
+        FEM_CUDA(cudaMemcpyAsync(tab.ptr, c_row.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        FEM_CUDA(cudaMemcpyAsync(tab.ptr + nc + 1, c_patch.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        FEM_CUDA(cudaMemcpyAsync(tab.ptr + 2 * nc + 2, c_cap.data(), nc * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        k_patch_bounds<<<grid_for(npatch + 1), TPB, 0, s>>>(pre.ptr, tab.ptr, tab.ptr + nc + 1, tab.ptr + 2 * nc + 2,
+                                                            nc, npatch, P.patch_node_ptr.ptr);
+        FEM_LAUNCHED("k_patch_bounds");
+        FEM_CUDA(cudaStreamSynchronize(s));  // the table is freed on leaving
+    }
     FEM_TRY(P.node_patch.alloc(ar, N, "node patch"));
     FEM_TRY(P.own_idx.alloc(ar, N, "own index"));
     FEM_TRY(P.own_row.alloc(ar, N, "own row"));
@@ -1117,7 +1250,7 @@ fem_status build_plan(fem_mesh m, cudaStream_t s) {
     // FP64-accurate diagonals of high-valence rows: scalar operators only
     const int hv_thr = elastic ? INT32_MAX : m->opt.valence_threshold;
     P.any_hv = m->max_deg > hv_thr;
-    k_patch_nodes<<<grid_for(N), TPB, 0, s>>>(m->order.ptr, pre.ptr, P.patch_node_ptr.ptr, N, cap_eff, npatch,
+    k_patch_nodes<<<grid_for(N), TPB, 0, s>>>(m->order.ptr, pre.ptr, P.patch_node_ptr.ptr, N, npatch,
                                               m->rowptr.ptr, m->inc_ptr.ptr, hv_thr, P.node_patch.ptr, P.own_idx.ptr,
                                               P.own_row.ptr, P.own_rowptr.ptr, P.own_acc.ptr, P.own_hv.ptr);
     FEM_LAUNCHED("k_patch_nodes");
@@ -1155,6 +1288,28 @@ fem_status build_plan(fem_mesh m, cudaStream_t s) {
     P.n_colors = P.full.n_colors;
     m->n_groups = 1;
     return FEM_OK;
+}
+
+// The plan, with its patches halved until the largest closure fits the fused
+// scalar kernel's shared memory (mixed precision, FP64 coordinates: its largest
+// layout).  Closures that outgrow it come from patches whose owned nodes are
+// scattered, e.g. row ranges of the host pipeline cut from a numbering without
+// locality; the elasticity operator accumulates large patches in row windows.
+fem_status build_plan(fem_mesh m, cudaStream_t s) {
+    int dev = 0, limit = 0;
+    FEM_CUDA(cudaGetDevice(&dev));
+    FEM_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    int64_t cap = 0;
+    for (;;) {
+        FEM_TRY(build_plan_cap(m, s, cap));
+        if (m->opt.operator_kind == 2) return FEM_OK;
+        PlanMax pm;
+        pm.add(m->plan);
+        const size_t need = patch_smem_layout(pm, true, true, sizeof(double), sizeof(double)).total + 1024;
+        const int64_t half = m->plan.cap_entries / 2;
+        if (need <= (size_t)limit || half < 2 * (int64_t)m->max_row_len) return FEM_OK;
+        cap = half;
+    }
 }
 
 fem_status build_pattern_and_plan(fem_mesh m, cudaStream_t s) {
