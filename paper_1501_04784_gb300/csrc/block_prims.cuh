@@ -1,6 +1,6 @@
-// block_prims.cuh -- block-wide primitives of the symbolic kernels: an ascending
-// bitonic sort of a power-of-two number of keys in shared memory and an in-place
-// exclusive prefix sum.
+// block_prims.cuh -- block-wide primitives of the symbolic kernels: ascending
+// bitonic sorts of a power-of-two number of 32- or 64-bit keys in shared memory
+// and an in-place exclusive prefix sum.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -23,6 +23,25 @@ __device__ inline void block_bitonic(uint32_t *keys, int n) {
                 const int ixj = i ^ j;
                 if (ixj > i) {
                     const uint32_t a = keys[i], b = keys[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+// The same for 64-bit keys.
+__device__ inline void block_bitonic64(uint64_t *keys, int n) {
+    for (int k = 2; k <= n; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t a = keys[i], b = keys[ixj];
                     const bool up = (i & k) == 0;
                     if ((a > b) == up) {
                         keys[i] = b;

@@ -205,7 +205,6 @@ struct fem_mesh_s {
 namespace fem {
 fem_status build_locality_order(fem_mesh m, const void *X, fem_dtype xd, cudaStream_t s);
 fem_status validate_connectivity(fem_mesh m, cudaStream_t s);
-fem_status build_pattern_and_plan(fem_mesh m, cudaStream_t s);
 void batch_forget(fem_mesh m);  // drops cached batched launches that use m's plan
 fem_status build_pattern(fem_mesh m, cudaStream_t s);
 fem_status build_plan(fem_mesh m, cudaStream_t s);

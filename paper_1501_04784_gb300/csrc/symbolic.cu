@@ -338,6 +338,112 @@ __global__ void k_row_pattern(const int32_t *__restrict__ E, const int64_t *__re
     }
 }
 
+// Ascending bitonic sort of the 32 K values a warp holds, K per lane in blocked
+// order (value t = lane K + k): pairs closer than K swap in registers, the others
+// through shuffles.
+template <int K>
+__device__ __forceinline__ void warp_bitonic(int32_t (&v)[K], int lane) {
+#pragma unroll
+    for (int size = 2; size <= 32 * K; size <<= 1)
+#pragma unroll
+        for (int j = size >> 1; j > 0; j >>= 1) {
+            if (j < K) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const int kp = k ^ j;
+                    if (kp > k) {
+                        const bool up = ((lane * K + k) & size) == 0;
+                        const int32_t a = v[k], b = v[kp];
+                        if ((a > b) == up) {
+                            v[k] = b;
+                            v[kp] = a;
+                        }
+                    }
+                }
+            } else {
+                const int pl = j / K;
+                const bool lower = (lane & pl) == 0;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const int32_t o = __shfl_xor_sync(0xffffffffu, v[k], pl);
+                    const bool up = ((lane * K + k) & size) == 0;
+                    v[k] = (lower == up) ? min(v[k], o) : max(v[k], o);
+                }
+            }
+        }
+}
+
+// k_row_pattern for rows of at most 32 K candidates: the warp sorts them in
+// registers, so repeats are neighbours and a column's position in its row is the
+// number of distinct smaller columns (a ballot count), not a scan over all
+// candidates.  Same passes and outputs as k_row_pattern, and with tmp (S slots
+// a row) the count pass also keeps each row's first S columns there, so that
+// the fill pass copies the rows of at most S entries instead of rebuilding them.
+template <int NPE, int K>
+__global__ void k_row_pattern_reg(const int32_t *__restrict__ E, const int64_t *__restrict__ inc_ptr,
+                                  const int32_t *__restrict__ inc_elem, int64_t N, int64_t *cnt,
+                                  const int64_t *__restrict__ rowptr, int32_t *col, int32_t *tmp, int S) {
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int64_t i = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < N; i += (int64_t)gridDim.x * wpb) {
+        if (col && tmp) {
+            const int64_t r0 = rowptr[i], len = rowptr[i + 1] - r0;
+            if (len <= S) {  // warp-uniform
+                if (lane < len) col[r0 + lane] = tmp[i * S + lane];
+                continue;
+            }
+        }
+        const int64_t b0 = inc_ptr[i];
+        const int n = (int)(inc_ptr[i + 1] - b0) * NPE;
+        int32_t e[K], v[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int t = lane * K + k;
+            e[k] = t < n ? inc_elem[b0 + t / NPE] : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int t = lane * K + k;
+            const int32_t g = e[k] >= 0 ? E[(int64_t)e[k] * NPE + t % NPE] : INT_MAX;
+            v[k] = g <= i ? g : INT_MAX;
+        }
+        warp_bitonic<K>(v, lane);
+        // first occurrences: the predecessor of value t is v[k-1], or lane-1's last
+        const int32_t prev_last = __shfl_up_sync(0xffffffffu, v[K - 1], 1);
+        unsigned first = 0;
+        int mine = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int32_t pv = k > 0 ? v[k - 1] : (lane > 0 ? prev_last : INT_MIN);
+            if (v[k] != INT_MAX && v[k] != pv) {
+                first |= 1u << k;
+                ++mine;
+            }
+        }
+        int incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (col) {
+            int r = incl - mine;
+            const int64_t base = rowptr[i];
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (first >> k & 1u) col[base + r++] = v[k];
+        } else if (tmp) {
+            int r = incl - mine;
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (first >> k & 1u) {
+                    if (r < S) tmp[i * S + r] = v[k];
+                    ++r;
+                }
+        }
+        if (cnt && lane == 31) cnt[i] = incl;
+    }
+}
+
 __global__ void k_row_len_max(const int64_t *rowptr, int64_t N, unsigned long long *mx) {
     unsigned long long m = 0;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < N; g += (int64_t)gridDim.x * blockDim.x)
@@ -493,29 +599,29 @@ __global__ void k_color(const uint64_t *ckeys, const int64_t *pe_ptr, const int6
                 }
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
+            // the greedy pass, element after element, by warp 0: lane (a, w) holds
+            // word w of node a's used-colour mask, the words of the element's owned
+            // nodes are or-ed across lanes, and the lowest free colour is the first
+            // zero bit of the lowest word that has one
+            if (threadIdx.x < 32) {
+                const int lane = threadIdx.x, a = lane >> 2, w = lane & (COLOR_WORDS - 1);
                 for (int i = 0; i < cn; ++i) {
-                    unsigned long long m[COLOR_WORDS] = {0ull, 0ull, 0ull, 0ull};
-#pragma unroll
-                    for (int a = 0; a < NPE; ++a) {
-                        const int o = tab[i * NPE + a];
-                        if (o >= 0)
-#pragma unroll
-                            for (int w = 0; w < COLOR_WORDS; ++w) m[w] |= mask[COLOR_WORDS * o + w];
-                    }
+                    const int o = a < NPE ? tab[i * NPE + a] : -1;
+                    unsigned long long mw = o >= 0 ? mask[COLOR_WORDS * o + w] : 0ull;
+                    mw |= __shfl_xor_sync(0xffffffffu, mw, 4);
+                    mw |= __shfl_xor_sync(0xffffffffu, mw, 8);
+                    mw |= __shfl_xor_sync(0xffffffffu, mw, 16);
+                    const unsigned freew = __ballot_sync(0xffffffffu, lane < COLOR_WORDS && ~mw != 0ull);
                     int c = 255;
-#pragma unroll
-                    for (int w = COLOR_WORDS - 1; w >= 0; --w)
-                        if (~m[w]) c = 64 * w + __ffsll((long long)~m[w]) - 1;
-                    if (c > 254) c = 255;
-                    color_out[b + c0 + i] = (uint8_t)c;
-                    if (c < 255) {
-#pragma unroll
-                        for (int a = 0; a < NPE; ++a) {
-                            const int o = tab[i * NPE + a];
-                            if (o >= 0) mask[COLOR_WORDS * o + (c >> 6)] |= 1ull << (c & 63);
-                        }
+                    if (freew) {  // warp-uniform
+                        const int w0 = __ffs((int)freew) - 1;
+                        const unsigned long long m0 = __shfl_sync(0xffffffffu, mw, w0);
+                        c = 64 * w0 + __ffsll((long long)~m0) - 1;
                     }
+                    if (c > 254) c = 255;
+                    if (lane == 0) color_out[b + c0 + i] = (uint8_t)c;
+                    if (c < 255 && o >= 0 && w == (c >> 6)) mask[COLOR_WORDS * o + w] |= 1ull << (c & 63);
+                    __syncwarp();
                     local_max = max(local_max, c);
                 }
             }
@@ -568,41 +674,6 @@ __global__ void k_cnode_pairs(const uint64_t *ckeys, int64_t nce, int npe, const
     }
 }
 
-// Closure nodes of each patch in shared memory (one block per patch): the node
-// ids of the patch's closure elements are sorted (bitonic, padded to a power of
-// two) and the distinct ones counted (cnt) or written as (patch << 32) | id at the
-// patch's offset (out).  Used when a patch's closure holds at most
-// CNODE_SMEM_KEYS node slots; larger closures take the global sort.
-static constexpr int CNODE_SMEM_KEYS = 8192;
-
-template <int NPE>
-__global__ void __launch_bounds__(512) k_patch_cnodes(const uint64_t *ckeys, const int64_t *pe_ptr, int64_t np_,
-                                                      const int32_t *__restrict__ E, int64_t *cnt,
-                                                      const int64_t *off, uint64_t *out) {
-    extern __shared__ __align__(16) unsigned char cn_smem[];
-    uint32_t *keys = reinterpret_cast<uint32_t *>(cn_smem);                    // [CNODE_SMEM_KEYS]
-    int *flag = reinterpret_cast<int *>(cn_smem + CNODE_SMEM_KEYS * sizeof(uint32_t));  // [CNODE_SMEM_KEYS]
-    __shared__ int ws[32];
-    for (int64_t p = blockIdx.x; p < np_; p += gridDim.x) {
-        const int64_t b = pe_ptr[p];
-        const int n = (int)(pe_ptr[p + 1] - b) * NPE, sz = pow2_at_least(n);
-        for (int i = threadIdx.x; i < sz; i += blockDim.x)
-            keys[i] = i < n ? (uint32_t)E[(int64_t)(uint32_t)ckeys[b + i / NPE] * NPE + i % NPE] : 0xffffffffu;
-        __syncthreads();
-        block_bitonic(keys, sz);
-        for (int i = threadIdx.x; i < sz; i += blockDim.x) flag[i] = (i < n && (i == 0 || keys[i] != keys[i - 1])) ? 1 : 0;
-        __syncthreads();
-        const int u = block_scan(flag, sz, ws);
-        if (cnt) {
-            if (threadIdx.x == 0) cnt[p] = u;
-        } else {
-            for (int i = threadIdx.x; i < n; i += blockDim.x)
-                if (i == 0 || keys[i] != keys[i - 1]) out[off[p] + flag[i]] = ((uint64_t)p << 32) | keys[i];
-        }
-        __syncthreads();
-    }
-}
-
 __global__ void k_cnode_own(const uint64_t *cn_keys, int64_t ncn, int64_t p0, const int32_t *node_patch,
                             const int32_t *own_idx, int32_t *gid, int32_t *own) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ncn; j += (int64_t)gridDim.x * blockDim.x) {
@@ -649,6 +720,7 @@ __global__ void k_celem_fill(const uint64_t *ckeys, int64_t np_, const int32_t *
         celem_id[i] = (int32_t)e;
         celem_color[i] = (uint8_t)((k >> 32) & 0xff);
         int32_t g[NPE];
+        uint32_t lw[NPE / 2];  // the local indices, two to a word
 #pragma unroll
         for (int a = 0; a < NPE; ++a) {
             g[a] = E[e * NPE + a];
@@ -657,21 +729,21 @@ __global__ void k_celem_fill(const uint64_t *ckeys, int64_t np_, const int32_t *
                 const int mid = (lo + hi) >> 1;
                 if (cn_gid[mid] < g[a]) lo = mid + 1; else hi = mid;
             }
-            lnode[i * NPE + a] = (uint16_t)lo;
+            if (a & 1) lw[a >> 1] |= (uint32_t)lo << 16; else lw[a >> 1] = (uint32_t)lo;
         }
+        if constexpr (NPE == 8) reinterpret_cast<uint4 *>(lnode)[i] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        else reinterpret_cast<uint2 *>(lnode)[i] = make_uint2(lw[0], lw[1]);
         const int64_t gp = ot.p0 + (int64_t)p;
         const int64_t nb = ot.patch_node_ptr[gp];
-        // Each element node x as a row: the positions of the element's lower
-        // partners (g_y < g_x) in row g_x by one scan of the row, whose loads are
-        // independent (a binary search per pair is a chain of dependent loads),
-        // and the row's owner data.
+        // Each element node x as a row: its start and length, and the row's
+        // owner data.
+        int64_t r0[NPE];
         int rl[NPE], base[NPE], hvk[NPE];
         bool own[NPE];
-        uint8_t pxy[NPE][NPE];
 #pragma unroll
         for (int x = 0; x < NPE; ++x) {
-            const int64_t r0 = rowptr[g[x]];
-            rl[x] = (int)(rowptr[g[x] + 1] - r0);
+            r0[x] = rowptr[g[x]];
+            rl[x] = (int)(rowptr[g[x] + 1] - r0[x]);
             own[x] = ot.node_patch[g[x]] == gp;
             base[x] = 0;
             hvk[x] = -1;
@@ -680,25 +752,34 @@ __global__ void k_celem_fill(const uint64_t *ckeys, int64_t np_, const int32_t *
                 base[x] = ot.own_acc[nb + kr];
                 if (ot.own_hv[nb + kr]) hvk[x] = kr;
             }
-#pragma unroll
-            for (int y = 0; y < NPE; ++y) pxy[x][y] = 0;
-            for (int j = 0; j < rl[x]; ++j) {
-                const int32_t cj = col[r0 + j];
-#pragma unroll
-                for (int y = 0; y < NPE; ++y)
-                    if (g[y] == cj) pxy[x][y] = (uint8_t)j;
-            }
         }
+        constexpr int NP = NPE * (NPE + 1) / 2;
+        uint32_t pw[(NP + 3) / 4], aw[NP / 2];  // positions four to a word, targets two to a word
+#pragma unroll
+        for (int w = 0; w < (NP + 3) / 4; ++w) pw[w] = 0;
         int q = 0;
 #pragma unroll
         for (int a = 0; a < NPE; ++a)
 #pragma unroll
             for (int b = 0; b <= a; ++b, ++q) {
                 // the pair's row is its node with the larger global id; the
-                // diagonal closes its lower row
+                // diagonal closes its lower row; an off-diagonal pair's position is
+                // a binary search of the smaller id in that (ascending) row, the
+                // searches of an element's pairs independent of one another
                 const bool ra = g[a] > g[b];
-                const int ps = a == b ? rl[a] - 1 : (ra ? pxy[a][b] : pxy[b][a]);
-                pos[i * pos_stride + q] = (uint8_t)ps;
+                int ps = rl[a] - 1;
+                if (a != b) {
+                    const int64_t rb = ra ? r0[a] : r0[b];
+                    const int32_t v = ra ? g[b] : g[a];
+                    int lo = 0, n = ra ? rl[a] : rl[b];
+                    while (n > 1) {
+                        const int half = n >> 1;
+                        if (col[rb + lo + half] <= v) lo += half;
+                        n -= half;
+                    }
+                    ps = lo;
+                }
+                pw[q >> 2] |= (uint32_t)(ps & 0xff) << (8 * (q & 3));
                 // a pair whose row the patch does not own goes to a scratch slot of
                 // the lane that will hold the element, never read
                 uint32_t t = (uint32_t)(ot.trash + ((i - ot.pe_ptr[p]) & 31));
@@ -707,19 +788,51 @@ __global__ void k_celem_fill(const uint64_t *ckeys, int64_t np_, const int32_t *
                     else t = (uint32_t)((ra ? base[a] : base[b]) + ps);
                 }
                 // word q/2 of element i, low half for even q
-                aidx[((int64_t)(q >> 1) * nce + i) * 2 + (q & 1)] = (uint16_t)t;
+                if (q & 1) aw[q >> 1] |= (t & 0xffffu) << 16; else aw[q >> 1] = t & 0xffffu;
             }
+        // the positions as whole words (pos_stride is a multiple of 4: the padding
+        // bytes are written as zeros), the targets word-major
+        uint32_t *pos32 = reinterpret_cast<uint32_t *>(pos + i * pos_stride);
+#pragma unroll
+        for (int w = 0; w < (NP + 3) / 4; ++w) pos32[w] = pw[w];
+        for (int w = (NP + 3) / 4; w < pos_stride / 4; ++w) pos32[w] = 0;
+        uint32_t *aidx32 = reinterpret_cast<uint32_t *>(aidx);
+#pragma unroll
+        for (int w = 0; w < NP / 2; ++w) aidx32[(int64_t)w * nce + i] = aw[w];
     }
     __syncthreads();
   }
 }
 
-// Shared memory of the row-pattern kernel above the 48 KB default (a node in up
-// to 2048 / npe elements needs up to 64 KB for 8 warps): opted in per launch.
-static fem_status row_pattern_smem(int npe, size_t smem) {
-    if (smem <= (48u << 10)) return FEM_OK;
-    if (npe == 8) FEM_CUDA(cudaFuncSetAttribute(k_row_pattern<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    else FEM_CUDA(cudaFuncSetAttribute(k_row_pattern<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+// One pass of the row pattern (cnt: counts; else the columns at rowptr) over
+// rows of at most cap candidates: sorted in registers up to 256 candidates, else
+// by the shared-memory kernel.  That kernel's shared memory above the 48 KB
+// default (a node in up to 2048 / npe elements needs up to 64 KB for 8 warps)
+// is opted in per launch.
+static fem_status launch_row_pattern(const int32_t *E, int npe, int64_t N, const int64_t *inc_ptr,
+                                     const int32_t *inc_elem, int cap, int64_t *cnt, const int64_t *rowptr,
+                                     int32_t *col, cudaStream_t s, int32_t *tmp = nullptr, int S = 0) {
+    const int wpb = 8;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(N, wpb), (int64_t)num_sms() * 64));
+#define FEM_RP(K)                                                                                           \
+    do {                                                                                                    \
+        if (npe == 8) k_row_pattern_reg<8, K><<<grid, wpb * 32, 0, s>>>(E, inc_ptr, inc_elem, N, cnt, rowptr, col, tmp, S); \
+        else k_row_pattern_reg<4, K><<<grid, wpb * 32, 0, s>>>(E, inc_ptr, inc_elem, N, cnt, rowptr, col, tmp, S);          \
+        FEM_LAUNCHED("k_row_pattern_reg");                                                                  \
+        return FEM_OK;                                                                                      \
+    } while (0)
+    if (cap <= 64) FEM_RP(2);
+    if (cap <= 128) FEM_RP(4);
+    if (cap <= 256) FEM_RP(8);
+#undef FEM_RP
+    const size_t smem = (size_t)wpb * (cap > 0 ? cap : 1) * sizeof(int32_t);
+    if (smem > (48u << 10)) {
+        if (npe == 8) FEM_CUDA(cudaFuncSetAttribute(k_row_pattern<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        else FEM_CUDA(cudaFuncSetAttribute(k_row_pattern<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    if (npe == 8) k_row_pattern<8><<<grid, wpb * 32, smem, s>>>(E, inc_ptr, inc_elem, N, cap, cnt, rowptr, col);
+    else k_row_pattern<4><<<grid, wpb * 32, smem, s>>>(E, inc_ptr, inc_elem, N, cap, cnt, rowptr, col);
+    FEM_LAUNCHED("k_row_pattern");
     return FEM_OK;
 }
 
@@ -805,28 +918,25 @@ fem_status build_pattern(fem_mesh m, cudaStream_t s) {
     {
         DevBuf<int64_t> cnt, tmp;
         FEM_TRY(cnt.alloc(ar, N + 1, "row counts"));
-        const int wpb = 8;
-        const size_t smem = (size_t)wpb * (cap > 0 ? cap : 1) * sizeof(int32_t);
-        const unsigned grid = (unsigned)std::min<int64_t>(cdiv(N, wpb), (int64_t)num_sms() * 64);
-        FEM_TRY(row_pattern_smem((int)npe, smem));
-        if (npe == 8)
-            k_row_pattern<8><<<grid, wpb * 32, smem, s>>>(m->E, m->inc_ptr.ptr, m->inc_elem.ptr, N, cap, cnt.ptr,
-                                                          nullptr, nullptr);
-        else
-            k_row_pattern<4><<<grid, wpb * 32, smem, s>>>(m->E, m->inc_ptr.ptr, m->inc_elem.ptr, N, cap, cnt.ptr,
-                                                          nullptr, nullptr);
-        FEM_LAUNCHED("k_row_pattern(count)");
+        // the count pass keeps up to S columns a row (when the budget allows the
+        // N S slots; the register-sorted kernel only), so that the fill pass copies
+        const int S = npe == 8 ? 16 : 32;
+        DevBuf<int32_t> rows;
+        const size_t rows_bytes = (size_t)N * S * sizeof(int32_t);
+        if (cap <= 256 && (!ar.budget || ar.live + ar.kept + rows_bytes <= ar.budget) &&
+            rows.alloc(ar, (size_t)N * S, "row columns (first pass)") != FEM_OK) {
+            cudaGetLastError();
+            rows.free();
+        }
+        FEM_TRY(launch_row_pattern(m->E, (int)npe, N, m->inc_ptr.ptr, m->inc_elem.ptr, cap, cnt.ptr, nullptr, nullptr,
+                                   s, rows.ptr, rows.ptr ? S : 0));
         FEM_TRY(tmp.alloc(ar, scan_tmp_elems(N + 1), "scan scratch"));
         FEM_TRY(scan_exclusive_i64(cnt.ptr, m->rowptr.ptr, N, true, tmp.ptr, s));
         FEM_TRY(read_scalar(m->rowptr.ptr + N, &m->nnz, s));
         FEM_TRY(m->col.alloc(ar, m->nnz, "col"));
-        if (npe == 8)
-            k_row_pattern<8><<<grid, wpb * 32, smem, s>>>(m->E, m->inc_ptr.ptr, m->inc_elem.ptr, N, cap, nullptr,
-                                                          m->rowptr.ptr, m->col.ptr);
-        else
-            k_row_pattern<4><<<grid, wpb * 32, smem, s>>>(m->E, m->inc_ptr.ptr, m->inc_elem.ptr, N, cap, nullptr,
-                                                          m->rowptr.ptr, m->col.ptr);
-        FEM_LAUNCHED("k_row_pattern(fill)");
+        FEM_TRY(launch_row_pattern(m->E, (int)npe, N, m->inc_ptr.ptr, m->inc_elem.ptr, cap, nullptr, m->rowptr.ptr,
+                                   m->col.ptr, s, rows.ptr, rows.ptr ? S : 0));
+        FEM_CUDA(cudaStreamSynchronize(s));  // the first-pass columns are freed on leaving
         DevBuf<unsigned long long> mx;
         FEM_TRY(mx.alloc(ar, 1, "max"));
         FEM_CUDA(cudaMemsetAsync(mx.ptr, 0, sizeof(unsigned long long), s));
@@ -865,6 +975,166 @@ __global__ void k_range_pairs(const int32_t *own_row, const int32_t *node_patch,
     }
 }
 
+// Per-patch set building in shared memory: an open-addressing hash set of 32-bit
+// keys (empty = all ones; linear probing, so an insert ends within `size` probes
+// while the set holds fewer keys than slots) whose new members are appended to
+// list[*count] in arrival order.  A set that fills its table sets *full (the
+// key is then dropped, and the caller discards the set).
+__device__ __forceinline__ void set_insert(uint32_t *table, int size, uint32_t key, uint32_t *list, int *count,
+                                           int *full) {
+    int h = (int)((key * 2654435761u) & (uint32_t)(size - 1));
+    for (int probe = 0; probe < size; ++probe) {
+        const uint32_t old = atomicCAS(&table[h], 0xffffffffu, key);
+        if (old == 0xffffffffu) {
+            list[atomicAdd(count, 1)] = key;
+            return;
+        }
+        if (old == key) return;
+        h = (h + 1) & (size - 1);
+    }
+    *full = 1;
+}
+
+// Largest table of the per-patch sets (slots of 4 bytes; a block holds the table
+// and a list of as many slots).
+static constexpr int SET_MAX_SLOTS = 16384;
+
+// Closure elements of each patch (one block per patch), in the order the
+// colouring sweeps them: the elements incident to the patch's owned nodes, made
+// unique in a shared-memory hash set, then sorted by the smallest owned index
+// among their nodes, ties by element id.  Written to tmp from the patch's
+// candidate offset (cand_off: the incident slots of the earlier patches), with
+// their number in cnt; k_patch_compact moves them into place.  A patch whose
+// sort does not fit in the table's memory sets *overflow.
+template <int NPE>
+__global__ void __launch_bounds__(256) k_patch_celems(const int64_t *pn_ptr, int64_t np_, int64_t p0,
+                                                      const int32_t *__restrict__ own_row,
+                                                      const int64_t *__restrict__ inc_ptr,
+                                                      const int32_t *__restrict__ inc_elem,
+                                                      const int32_t *__restrict__ E, const int32_t *node_patch,
+                                                      const int32_t *own_idx, const int64_t *cand_off, int hsize,
+                                                      uint32_t *tmp, int64_t *cnt, int *overflow) {
+    extern __shared__ __align__(16) unsigned char ce_smem[];
+    uint32_t *table = reinterpret_cast<uint32_t *>(ce_smem);  // [hsize], then hsize / 2 sort keys
+    uint64_t *skeys = reinterpret_cast<uint64_t *>(ce_smem);
+    uint32_t *list = reinterpret_cast<uint32_t *>(ce_smem + (size_t)hsize * sizeof(uint32_t));  // [hsize]
+    __shared__ int n_set, s_full;
+    for (int64_t p = blockIdx.x; p < np_; p += gridDim.x) {
+        for (int i = threadIdx.x; i < hsize; i += blockDim.x) table[i] = 0xffffffffu;
+        if (threadIdx.x == 0) n_set = s_full = 0;
+        __syncthreads();
+        const int64_t k0 = pn_ptr[p], nown = pn_ptr[p + 1] - k0;
+        for (int64_t k = threadIdx.x; k < nown; k += blockDim.x) {
+            const int32_t g = own_row[k0 + k];
+            for (int64_t t = inc_ptr[g]; t < inc_ptr[g + 1]; ++t)
+                set_insert(table, hsize, (uint32_t)inc_elem[t], list, &n_set, &s_full);
+        }
+        __syncthreads();
+        const int u = n_set, su = pow2_at_least(u);
+        if (s_full || 2 * su > hsize) {  // a full table, or sort keys that would not fit in its memory
+            if (threadIdx.x == 0) {
+                *overflow = 1;
+                cnt[p] = 0;
+            }
+            __syncthreads();
+            continue;
+        }
+        const int32_t pg = (int32_t)(p0 + p);
+        for (int j = threadIdx.x; j < su; j += blockDim.x) {
+            uint64_t key = ~0ull;
+            if (j < u) {
+                const uint32_t e = list[j];
+                int mo = 32767;
+#pragma unroll
+                for (int a = 0; a < NPE; ++a) {
+                    const int32_t g = E[(int64_t)e * NPE + a];
+                    if (node_patch[g] == pg) mo = min(mo, own_idx[g]);
+                }
+                key = ((uint64_t)mo << 32) | e;
+            }
+            skeys[j] = key;
+        }
+        __syncthreads();
+        block_bitonic64(skeys, su);
+        for (int r = threadIdx.x; r < u; r += blockDim.x) tmp[cand_off[p] + r] = (uint32_t)skeys[r];
+        if (threadIdx.x == 0) cnt[p] = u;
+        __syncthreads();
+    }
+}
+
+// Closure nodes of each patch (one block per patch): the nodes of the patch's
+// closure elements, made unique in a shared-memory hash set and sorted
+// ascending, written to tmp from the patch's offset (npe slots per closure
+// element) with their number in cnt.
+template <int NPE>
+__global__ void __launch_bounds__(256) k_patch_cnodes(const uint64_t *ckeys, const int64_t *pe_ptr, int64_t np_,
+                                                      const int32_t *__restrict__ E, int hsize, uint32_t *tmp,
+                                                      int64_t *cnt, int *overflow) {
+    extern __shared__ __align__(16) unsigned char cn_smem[];
+    uint32_t *table = reinterpret_cast<uint32_t *>(cn_smem);  // [hsize], then the sort keys
+    uint32_t *list = reinterpret_cast<uint32_t *>(cn_smem + (size_t)hsize * sizeof(uint32_t));  // [hsize]
+    __shared__ int n_set, s_full;
+    for (int64_t p = blockIdx.x; p < np_; p += gridDim.x) {
+        for (int i = threadIdx.x; i < hsize; i += blockDim.x) table[i] = 0xffffffffu;
+        if (threadIdx.x == 0) n_set = s_full = 0;
+        __syncthreads();
+        const int64_t b = pe_ptr[p];
+        const int n = (int)(pe_ptr[p + 1] - b) * NPE;
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+            set_insert(table, hsize, (uint32_t)E[(int64_t)(uint32_t)ckeys[b + i / NPE] * NPE + i % NPE], list, &n_set,
+                       &s_full);
+        __syncthreads();
+        if (s_full) {
+            if (threadIdx.x == 0) {
+                *overflow = 1;
+                cnt[p] = 0;
+            }
+            __syncthreads();
+            continue;
+        }
+        const int u = n_set, su = pow2_at_least(u);
+        for (int j = threadIdx.x; j < su; j += blockDim.x) table[j] = j < u ? list[j] : 0xffffffffu;
+        __syncthreads();
+        block_bitonic(table, su);
+        for (int r = threadIdx.x; r < u; r += blockDim.x) tmp[b * NPE + r] = table[r];
+        if (threadIdx.x == 0) cnt[p] = u;
+        __syncthreads();
+    }
+}
+
+// out[off[p] + r] = (p << 32) | tmp[from[p] * scale + r] for r < off[p + 1] - off[p].
+__global__ void k_patch_compact(const uint32_t *tmp, const int64_t *from, int scale, const int64_t *off, int64_t np_,
+                                uint64_t *out) {
+    for (int64_t p = blockIdx.x; p < np_; p += gridDim.x) {
+        const int64_t src = from[p] * scale, dst = off[p], n = off[p + 1] - dst;
+        for (int64_t r = threadIdx.x; r < n; r += blockDim.x) out[dst + r] = ((uint64_t)p << 32) | tmp[src + r];
+    }
+}
+
+// Candidate offset of each patch: off[p] = pre[pn[p] - k0].
+__global__ void k_take_offsets(const int64_t *pre, const int64_t *pn, int64_t k0, int64_t np_, int64_t *off) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p <= np_; p += (int64_t)gridDim.x * blockDim.x)
+        off[p] = pre[pn[p] - k0];
+}
+
+// Closure elements of each patch reordered by (colour, element id), one block per
+// patch: out[i] = (patch << 40) | (colour << 32) | element, the layout of the
+// global sort's keys.  Patches of at most SET_MAX_SLOTS / 2 elements.
+__global__ void __launch_bounds__(512) k_patch_color_order(const uint64_t *ckeys, const uint8_t *color,
+                                                           const int64_t *pe_ptr, int64_t np_, uint64_t *out) {
+    extern __shared__ __align__(16) uint64_t co_keys[];
+    for (int64_t p = blockIdx.x; p < np_; p += gridDim.x) {
+        const int64_t b = pe_ptr[p];
+        const int n = (int)(pe_ptr[p + 1] - b), sz = pow2_at_least(n);
+        for (int i = threadIdx.x; i < sz; i += blockDim.x)
+            co_keys[i] = i < n ? ((uint64_t)color[b + i] << 32) | (ckeys[b + i] & 0xffffffffull) : ~0ull;
+        __syncthreads();
+        block_bitonic64(co_keys, sz);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) out[b + i] = ((uint64_t)p << 40) | co_keys[i];
+        __syncthreads();
+    }
+}
+
 fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaStream_t s) {
     Arena &ar = m->arena;
     Plan &P = m->plan;
@@ -880,10 +1150,64 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
     const int64_t k0 = h_pn[0], nk = h_pn[np_] - h_pn[0];
     const int pbits = bits_for(np_);
 
-    // ---- closure elements of each patch: unique (patch, element) pairs
+    // ---- closure elements of each patch, in the colouring's sweep order: per
+    // patch in shared memory, or (a patch too large for it) by global sorts
     DevBuf<uint64_t> ckeys;
     int64_t nce = 0;
+    std::vector<int64_t> h_pe(np_ + 1, 0), h_pc(np_ + 1);
+    bool swept = false;
+    FEM_TRY(cl.patch_elem_ptr.alloc(ar, np_ + 1, "patch elem ptr"));
     {
+        DevBuf<int64_t> deg, stmp, coff, cnt;
+        DevBuf<int> ovf;
+        FEM_TRY(deg.alloc(ar, nk + 1, "closure degrees"));
+        k_range_degree<<<grid_for(nk), TPB, 0, s>>>(P.own_row.ptr, m->inc_ptr.ptr, k0, nk, deg.ptr);
+        FEM_LAUNCHED("k_range_degree");
+        FEM_TRY(stmp.alloc(ar, scan_tmp_elems(nk + 1), "scan scratch"));
+        FEM_TRY(scan_exclusive_i64(deg.ptr, deg.ptr, nk, true, stmp.ptr, s));
+        FEM_TRY(coff.alloc(ar, np_ + 1, "candidate offsets"));
+        k_take_offsets<<<grid_for(np_ + 1), TPB, 0, s>>>(deg.ptr, P.patch_node_ptr.ptr + p0, k0, np_, coff.ptr);
+        FEM_LAUNCHED("k_take_offsets");
+        std::vector<int64_t> h_coff(np_ + 1);
+        FEM_CUDA(cudaMemcpyAsync(h_coff.data(), coff.ptr, (np_ + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        FEM_CUDA(cudaStreamSynchronize(s));
+        int64_t max_cand = 1;
+        for (int64_t p = 0; p < np_; ++p) max_cand = std::max(max_cand, h_coff[p + 1] - h_coff[p]);
+        const int hsize = pow2_at_least((int)std::min<int64_t>(max_cand, SET_MAX_SLOTS));
+        DevBuf<uint32_t> ctmp;
+        FEM_TRY(ctmp.alloc(ar, std::max<int64_t>(h_coff[np_], 1), "closure elements (unordered)"));
+        FEM_TRY(cnt.alloc(ar, np_, "closure element counts"));
+        FEM_TRY(ovf.alloc(ar, 1, "overflow flag"));
+        FEM_CUDA(cudaMemsetAsync(ovf.ptr, 0, sizeof(int), s));
+        const size_t smem = 2 * (size_t)hsize * sizeof(uint32_t);
+        auto f = npe == 8 ? k_patch_celems<8> : k_patch_celems<4>;
+        FEM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 1;
+        FEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, 256, smem));
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np_, (int64_t)num_sms() * std::max(per_sm, 1)));
+        f<<<grid, 256, smem, s>>>(P.patch_node_ptr.ptr + p0, np_, p0, P.own_row.ptr, m->inc_ptr.ptr, m->inc_elem.ptr,
+                                  m->E, P.node_patch.ptr, P.own_idx.ptr, coff.ptr, hsize, ctmp.ptr, cnt.ptr, ovf.ptr);
+        FEM_LAUNCHED("k_patch_celems");
+        int h_ovf = 0;
+        std::vector<int64_t> h_cnt(np_);
+        FEM_CUDA(cudaMemcpyAsync(h_cnt.data(), cnt.ptr, np_ * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        FEM_CUDA(cudaMemcpyAsync(&h_ovf, ovf.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FEM_CUDA(cudaStreamSynchronize(s));
+        if (!h_ovf) {
+            for (int64_t p = 0; p < np_; ++p) h_pe[p + 1] = h_pe[p] + h_cnt[p];
+            nce = h_pe[np_];
+            FEM_CUDA(cudaMemcpyAsync(cl.patch_elem_ptr.ptr, h_pe.data(), (np_ + 1) * sizeof(int64_t),
+                                     cudaMemcpyHostToDevice, s));
+            FEM_TRY(ckeys.alloc(ar, std::max<int64_t>(nce, 1), "closure keys (sweep order)"));
+            const unsigned cg = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np_, (int64_t)num_sms() * 8));
+            k_patch_compact<<<cg, 256, 0, s>>>(ctmp.ptr, coff.ptr, 1, cl.patch_elem_ptr.ptr, np_, ckeys.ptr);
+            FEM_LAUNCHED("k_patch_compact(elems)");
+            FEM_CUDA(cudaStreamSynchronize(s));  // h_pe is read by the copy above; temporaries freed on return
+            swept = true;
+        }
+    }
+    if (!swept) {
+        // unique (patch, element) pairs
         DevBuf<int64_t> deg, tmp;
         FEM_TRY(deg.alloc(ar, nk + 1, "closure degrees"));
         k_range_degree<<<grid_for(nk), TPB, 0, s>>>(P.own_row.ptr, m->inc_ptr.ptr, k0, nk, deg.ptr);
@@ -900,19 +1224,18 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
         deg.free();
         tmp.free();
         FEM_TRY(sort_unique(ar, pairs, npairs, 32 + pbits, ckeys, &nce, s));
+        k_segment_ptr<<<grid_for(np_ + 1), TPB, 0, s>>>(ckeys.ptr, nce, 32, np_, cl.patch_elem_ptr.ptr);
+        FEM_LAUNCHED("k_segment_ptr(elems)");
+        FEM_CUDA(cudaMemcpyAsync(h_pe.data(), cl.patch_elem_ptr.ptr, (np_ + 1) * sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, s));
+        FEM_CUDA(cudaStreamSynchronize(s));
     }
     cl.total_celems = nce;
-    FEM_TRY(cl.patch_elem_ptr.alloc(ar, np_ + 1, "patch elem ptr"));
-    k_segment_ptr<<<grid_for(np_ + 1), TPB, 0, s>>>(ckeys.ptr, nce, 32, np_, cl.patch_elem_ptr.ptr);
-    FEM_LAUNCHED("k_segment_ptr(elems)");
-    std::vector<int64_t> h_pe(np_ + 1), h_pc(np_ + 1);
-    FEM_CUDA(cudaMemcpyAsync(h_pe.data(), cl.patch_elem_ptr.ptr, (np_ + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    FEM_CUDA(cudaStreamSynchronize(s));
     for (int64_t p = 0; p < np_; ++p) cl.max_celems = std::max(cl.max_celems, h_pe[p + 1] - h_pe[p]);
 
     // ---- colouring of each closure (in sweep order), then order each closure by (colour, element)
-    {
-        DevBuf<uint64_t> skeys, salt, swept;
+    if (!swept) {
+        DevBuf<uint64_t> skeys, salt, swk;
         DevBuf<uint32_t> sperm, spalt;
         DevBuf<int64_t> shist;
         FEM_TRY(skeys.alloc(ar, nce, "sweep keys"));
@@ -928,13 +1251,13 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
         FEM_TRY(spalt.alloc(ar, nce, "sort scratch"));
         FEM_TRY(shist.alloc(ar, radix_hist_elems(nce), "sort histogram"));
         FEM_TRY(radix_sort_u64(skeys.ptr, sperm.ptr, nce, 15 + pbits, salt.ptr, spalt.ptr, shist.ptr, s));
-        FEM_TRY(swept.alloc(ar, nce, "closure keys (sweep order)"));
-        k_gather_u64<<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, sperm.ptr, nce, swept.ptr);
+        FEM_TRY(swk.alloc(ar, nce, "closure keys (sweep order)"));
+        k_gather_u64<<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, sperm.ptr, nce, swk.ptr);
         FEM_LAUNCHED("k_gather_u64");
         FEM_CUDA(cudaStreamSynchronize(s));
-        std::swap(ckeys.ptr, swept.ptr);
-        std::swap(ckeys.n, swept.n);
-        std::swap(ckeys.arena, swept.arena);
+        std::swap(ckeys.ptr, swk.ptr);
+        std::swap(ckeys.n, swk.n);
+        std::swap(ckeys.arena, swk.arena);
     }
     {
         DevBuf<uint8_t> color;
@@ -968,16 +1291,28 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
         cl.n_colors = h_mxc + 1;
         DevBuf<uint64_t> ck2, alt;
         DevBuf<int64_t> hist;
-        FEM_TRY(ck2.alloc(ar, nce, "closure keys"));
-        k_color_keys<<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, color.ptr, nce, ck2.ptr);
-        FEM_LAUNCHED("k_color_keys");
-        FEM_CUDA(cudaStreamSynchronize(s));
-        color.free();
-        ckeys.free();
-        FEM_TRY(alt.alloc(ar, nce, "sort scratch"));
-        FEM_TRY(hist.alloc(ar, radix_hist_elems(nce), "sort histogram"));
-        FEM_TRY(radix_sort_u64(ck2.ptr, nullptr, nce, 40 + pbits, alt.ptr, nullptr, hist.ptr, s));
-        FEM_CUDA(cudaStreamSynchronize(s));
+        FEM_TRY(ck2.alloc(ar, std::max<int64_t>(nce, 1), "closure keys"));
+        if (cl.max_celems <= SET_MAX_SLOTS / 2) {
+            // per patch in shared memory
+            const size_t csm = (size_t)pow2_at_least((int)std::max<int64_t>(cl.max_celems, 1)) * sizeof(uint64_t);
+            FEM_CUDA(cudaFuncSetAttribute(k_patch_color_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+            const unsigned cgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np_, (int64_t)num_sms() * 2));
+            k_patch_color_order<<<cgrid, 512, csm, s>>>(ckeys.ptr, color.ptr, cl.patch_elem_ptr.ptr, np_, ck2.ptr);
+            FEM_LAUNCHED("k_patch_color_order");
+            FEM_CUDA(cudaStreamSynchronize(s));
+            color.free();
+            ckeys.free();
+        } else {
+            k_color_keys<<<grid_for(nce), TPB, 0, s>>>(ckeys.ptr, color.ptr, nce, ck2.ptr);
+            FEM_LAUNCHED("k_color_keys");
+            FEM_CUDA(cudaStreamSynchronize(s));
+            color.free();
+            ckeys.free();
+            FEM_TRY(alt.alloc(ar, nce, "sort scratch"));
+            FEM_TRY(hist.alloc(ar, radix_hist_elems(nce), "sort histogram"));
+            FEM_TRY(radix_sort_u64(ck2.ptr, nullptr, nce, 40 + pbits, alt.ptr, nullptr, hist.ptr, s));
+            FEM_CUDA(cudaStreamSynchronize(s));
+        }
         std::swap(ckeys.ptr, ck2.ptr);
         std::swap(ckeys.n, ck2.n);
         std::swap(ckeys.arena, ck2.arena);
@@ -986,36 +1321,45 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
     // ---- closure nodes of each patch
     DevBuf<uint64_t> cnkeys;
     int64_t ncn = 0;
-    if (cl.max_celems * npe <= CNODE_SMEM_KEYS) {
-        // per patch in shared memory: a count pass, a prefix on the host, a fill pass
-        DevBuf<int64_t> cnt, off;
+    bool cn_done = false;
+    {
+        // per patch in shared memory; a patch whose set outgrows its table takes
+        // the global sort instead
+        const int hsize = pow2_at_least((int)std::min<int64_t>(std::max<int64_t>(cl.max_celems * npe, 1), 8192));
+        DevBuf<uint32_t> ntmp;
+        DevBuf<int64_t> cnt, pc;
+        DevBuf<int> ovf;
+        FEM_TRY(ntmp.alloc(ar, std::max<int64_t>(nce * npe, 1), "closure nodes (per patch)"));
         FEM_TRY(cnt.alloc(ar, np_, "closure node counts"));
-        FEM_TRY(off.alloc(ar, np_ + 1, "closure node offsets"));
-        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np_, (int64_t)num_sms() * 3));
-        const size_t smem = (size_t)CNODE_SMEM_KEYS * (sizeof(uint32_t) + sizeof(int));
-        FEM_CUDA(cudaFuncSetAttribute(k_patch_cnodes<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        FEM_CUDA(cudaFuncSetAttribute(k_patch_cnodes<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        if (npe == 8)
-            k_patch_cnodes<8><<<grid, 512, smem, s>>>(ckeys.ptr, cl.patch_elem_ptr.ptr, np_, m->E, cnt.ptr, nullptr, nullptr);
-        else
-            k_patch_cnodes<4><<<grid, 512, smem, s>>>(ckeys.ptr, cl.patch_elem_ptr.ptr, np_, m->E, cnt.ptr, nullptr, nullptr);
-        FEM_LAUNCHED("k_patch_cnodes(count)");
+        FEM_TRY(ovf.alloc(ar, 1, "overflow flag"));
+        FEM_CUDA(cudaMemsetAsync(ovf.ptr, 0, sizeof(int), s));
+        const size_t smem = 2 * (size_t)hsize * sizeof(uint32_t);
+        auto f = npe == 8 ? k_patch_cnodes<8> : k_patch_cnodes<4>;
+        FEM_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 1;
+        FEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, 256, smem));
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np_, (int64_t)num_sms() * std::max(per_sm, 1)));
+        f<<<grid, 256, smem, s>>>(ckeys.ptr, cl.patch_elem_ptr.ptr, np_, m->E, hsize, ntmp.ptr, cnt.ptr, ovf.ptr);
+        FEM_LAUNCHED("k_patch_cnodes");
+        int h_ovf = 0;
         std::vector<int64_t> h_cnt(np_), h_off(np_ + 1, 0);
         FEM_CUDA(cudaMemcpyAsync(h_cnt.data(), cnt.ptr, np_ * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        FEM_CUDA(cudaMemcpyAsync(&h_ovf, ovf.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
         FEM_CUDA(cudaStreamSynchronize(s));
-        for (int64_t p = 0; p < np_; ++p) h_off[p + 1] = h_off[p] + h_cnt[p];
-        ncn = h_off[np_];
-        FEM_CUDA(cudaMemcpyAsync(off.ptr, h_off.data(), (np_ + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-        FEM_TRY(cnkeys.alloc(ar, std::max<int64_t>(ncn, 1), "closure nodes"));
-        if (npe == 8)
-            k_patch_cnodes<8><<<grid, 512, smem, s>>>(ckeys.ptr, cl.patch_elem_ptr.ptr, np_, m->E, nullptr, off.ptr,
-                                                      cnkeys.ptr);
-        else
-            k_patch_cnodes<4><<<grid, 512, smem, s>>>(ckeys.ptr, cl.patch_elem_ptr.ptr, np_, m->E, nullptr, off.ptr,
-                                                      cnkeys.ptr);
-        FEM_LAUNCHED("k_patch_cnodes(fill)");
-        FEM_CUDA(cudaStreamSynchronize(s));  // h_off and the offsets buffer are released on return
-    } else {
+        if (!h_ovf) {
+            for (int64_t p = 0; p < np_; ++p) h_off[p + 1] = h_off[p] + h_cnt[p];
+            ncn = h_off[np_];
+            FEM_TRY(pc.alloc(ar, np_ + 1, "closure node offsets"));
+            FEM_CUDA(cudaMemcpyAsync(pc.ptr, h_off.data(), (np_ + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+            FEM_TRY(cnkeys.alloc(ar, std::max<int64_t>(ncn, 1), "closure nodes"));
+            const unsigned cg = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np_, (int64_t)num_sms() * 8));
+            k_patch_compact<<<cg, 256, 0, s>>>(ntmp.ptr, cl.patch_elem_ptr.ptr, (int)npe, pc.ptr, np_, cnkeys.ptr);
+            FEM_LAUNCHED("k_patch_compact(nodes)");
+            FEM_CUDA(cudaStreamSynchronize(s));  // h_off is read by the copy above; temporaries freed on return
+            cn_done = true;
+        }
+    }
+    if (!cn_done) {
         DevBuf<uint64_t> pairs;
         FEM_TRY(pairs.alloc(ar, nce * npe, "closure node pairs"));
         k_cnode_pairs<<<grid_for(nce * npe), TPB, 0, s>>>(ckeys.ptr, nce, (int)npe, m->E, pairs.ptr);
@@ -1037,7 +1381,6 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
     FEM_TRY(cl.celem_color.alloc(ar, nce, "celem colour"));
     FEM_TRY(cl.celem_lnode.alloc(ar, nce * npe, "celem local nodes"));
     FEM_TRY(cl.celem_pos.alloc(ar, nce * P.pos_stride, "celem positions"));
-    FEM_CUDA(cudaMemsetAsync(cl.celem_pos.ptr, 0, nce * P.pos_stride, s));
     FEM_TRY(cl.celem_aidx.alloc(ar, nce * (m->np / 2), "celem accumulator targets"));
     const OwnTables ot{P.node_patch.ptr,     P.own_idx.ptr, P.own_acc.ptr,          P.patch_node_ptr.ptr,
                        P.own_hv.ptr,         cl.patch_elem_ptr.ptr, p0, (int32_t)P.max_acc};
@@ -1312,12 +1655,6 @@ fem_status build_plan(fem_mesh m, cudaStream_t s) {
     }
 }
 
-fem_status build_pattern_and_plan(fem_mesh m, cudaStream_t s) {
-    FEM_TRY(build_pattern(m, s));
-    FEM_TRY(build_plan(m, s));
-    m->has_pattern = true;
-    return FEM_OK;
-}
 
 }  // namespace fem
 
@@ -1356,16 +1693,7 @@ fem_status pattern_steps_incidence(const int32_t *E, int64_t nel, int npe, int64
 
 fem_status pattern_steps_rows(const int32_t *E, int npe, int64_t N, const int64_t *inc_ptr, const int32_t *inc_elem,
                               int cap, int64_t *cnt, const int64_t *rowptr, int32_t *col, cudaStream_t s) {
-    const int wpb = 8;
-    const size_t smem = (size_t)wpb * (cap > 0 ? cap : 1) * sizeof(int32_t);
-    const unsigned grid = (unsigned)std::min<int64_t>(cdiv(N, wpb), (int64_t)num_sms() * 64);
-    FEM_TRY(row_pattern_smem(npe, smem));
-    if (npe == 8)
-        k_row_pattern<8><<<grid, wpb * 32, smem, s>>>(E, inc_ptr, inc_elem, N, cap, cnt, rowptr, col);
-    else
-        k_row_pattern<4><<<grid, wpb * 32, smem, s>>>(E, inc_ptr, inc_elem, N, cap, cnt, rowptr, col);
-    FEM_LAUNCHED("k_row_pattern");
-    return FEM_OK;
+    return launch_row_pattern(E, npe, N, inc_ptr, inc_elem, cap, cnt, rowptr, col, s);
 }
 
 }  // namespace fem
