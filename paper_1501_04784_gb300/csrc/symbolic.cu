@@ -702,7 +702,7 @@ template <int NPE>
 // One block per patch: the patch's closure-node ids (ascending) are staged in
 // shared memory, so that the closure-local index of each element node is a
 // binary search there rather than a chain of dependent global loads.
-__global__ void k_celem_fill(const uint64_t *ckeys, int64_t np_, const int32_t *__restrict__ E,
+__global__ void __launch_bounds__(256, 3) k_celem_fill(const uint64_t *ckeys, int64_t np_, const int32_t *__restrict__ E,
                              const uint64_t *cn_keys, const int64_t *pc_ptr, const int64_t *__restrict__ rowptr,
                              const int32_t *__restrict__ col, int pos_stride, OwnTables ot, int32_t *celem_id,
                              uint8_t *celem_color, uint16_t *lnode, uint8_t *pos, uint16_t *aidx) {
@@ -753,10 +753,14 @@ __global__ void k_celem_fill(const uint64_t *ckeys, int64_t np_, const int32_t *
                 if (ot.own_hv[nb + kr]) hvk[x] = kr;
             }
         }
+        // positions four to a word, targets two to a word (word-major), each word
+        // stored once complete; pos_stride is a multiple of 4, its padding bytes
+        // written as zeros
         constexpr int NP = NPE * (NPE + 1) / 2;
-        uint32_t pw[(NP + 3) / 4], aw[NP / 2];  // positions four to a word, targets two to a word
-#pragma unroll
-        for (int w = 0; w < (NP + 3) / 4; ++w) pw[w] = 0;
+        static_assert(NP % 2 == 0, "targets pair up into words");
+        uint32_t *pos32 = reinterpret_cast<uint32_t *>(pos + i * pos_stride);
+        uint32_t *aidx32 = reinterpret_cast<uint32_t *>(aidx);
+        uint32_t pw = 0, alo = 0;
         int q = 0;
 #pragma unroll
         for (int a = 0; a < NPE; ++a)
@@ -779,7 +783,11 @@ __global__ void k_celem_fill(const uint64_t *ckeys, int64_t np_, const int32_t *
                     }
                     ps = lo;
                 }
-                pw[q >> 2] |= (uint32_t)(ps & 0xff) << (8 * (q & 3));
+                pw |= (uint32_t)(ps & 0xff) << (8 * (q & 3));
+                if ((q & 3) == 3 || q == NP - 1) {
+                    pos32[q >> 2] = pw;
+                    pw = 0;
+                }
                 // a pair whose row the patch does not own goes to a scratch slot of
                 // the lane that will hold the element, never read
                 uint32_t t = (uint32_t)(ot.trash + ((i - ot.pe_ptr[p]) & 31));
@@ -788,17 +796,10 @@ __global__ void k_celem_fill(const uint64_t *ckeys, int64_t np_, const int32_t *
                     else t = (uint32_t)((ra ? base[a] : base[b]) + ps);
                 }
                 // word q/2 of element i, low half for even q
-                if (q & 1) aw[q >> 1] |= (t & 0xffffu) << 16; else aw[q >> 1] = t & 0xffffu;
+                if (q & 1) aidx32[(int64_t)(q >> 1) * nce + i] = alo | ((t & 0xffffu) << 16);
+                else alo = t & 0xffffu;
             }
-        // the positions as whole words (pos_stride is a multiple of 4: the padding
-        // bytes are written as zeros), the targets word-major
-        uint32_t *pos32 = reinterpret_cast<uint32_t *>(pos + i * pos_stride);
-#pragma unroll
-        for (int w = 0; w < (NP + 3) / 4; ++w) pos32[w] = pw[w];
         for (int w = (NP + 3) / 4; w < pos_stride / 4; ++w) pos32[w] = 0;
-        uint32_t *aidx32 = reinterpret_cast<uint32_t *>(aidx);
-#pragma unroll
-        for (int w = 0; w < NP / 2; ++w) aidx32[(int64_t)w * nce + i] = aw[w];
     }
     __syncthreads();
   }
