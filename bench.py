@@ -328,6 +328,20 @@ def run_ours(args):
     Xf, cf = X64.float(), c64.float()
     stream = torch.cuda.current_stream()
 
+    # Process warm-up: a small mesh through the same calls, so that the cold build
+    # below is that of a mesh the library has not seen, not the one-time loading of
+    # the library's kernels (reported separately as first_in_process_s).
+    sm = meshgen.config_mesh(1, nx=12)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    wmesh = fem.Mesh(torch.from_numpy(sm.E).cuda(), sm.n_nodes, X=torch.from_numpy(sm.X).cuda())
+    wv = torch.empty(wmesh.pattern(), dtype=torch.float32, device="cuda")
+    wmesh.build_K(torch.from_numpy(sm.X).float().cuda(), torch.from_numpy(sm.c).float().cuda(), "mixed", out=wv)
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t0
+    wmesh.close()
+    del wv
+
     # cold build: handle creation (validation + locality order) + symbolic + first numeric build
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -490,7 +504,9 @@ def run_ours(args):
         out["tuning"] = {k: tuning[k] for k in ("patch_entries", "block_threads", "assembly") if k in tuning}
         out["mass"] = {"ms_per_step": ms_mass, "value": m.n_elems / (ms_mass / 1e3)}
         out["cold_build"] = {"seconds": cold_s, "value": m.n_elems / cold_s,
-                             "includes": "validation, locality order, pattern, plan, first numeric build"}
+                             "includes": "validation, locality order, pattern, plan, first numeric build",
+                             "first_in_process_s": first_s,
+                             "first_in_process": "12^3 bricks, the process's first mesh (loads the kernels)"}
         out["fp64"] = {"value": fp64_eps, "ms_per_step": ms64, "hbm_frac": alg64 / (ms64 / 1e3) / 1e9 / peak,
                        "mixed_speedup": (value / world) / fp64_eps}
         if err:

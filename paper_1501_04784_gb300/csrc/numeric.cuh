@@ -22,6 +22,11 @@ int patch_blocks_per_sm(int npe, int threads);
 // byte offsets of the patch kernel's shared-memory arrays
 struct PatchSmem {
     size_t acc, hv, xs, cown, roff, hvf, rps, gid, eid, cvs, total;
+    // the fused kernel with prefetch: a second set of the prologue arrays, which
+    // receives the next patch's closure ids, coordinates and owned-row tables by
+    // asynchronous copies while the block works on the current patch
+    size_t xs2, roff2, rps2, gid2;
+    int prefetch;
     int wg_shift;  // log2 of the lanes that store one owned row
     int acc_cap;   // accumulators a block holds (largest patch + scratch slots)
     int hv_on;     // the hv region exists (some owned row has an FP64-accurate diagonal)
@@ -191,7 +196,8 @@ fem_status launch_tile_batched_kernel(const BatchLaunch &bl, cudaStream_t s);
 int tile_blocks_per_sm(int npe, int threads);
 // Element tiles of mesh m (after its pattern).
 fem_status build_tiles(fem_mesh m, cudaStream_t s);
-PatchSmem patch_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsize, size_t csize);
+PatchSmem patch_smem_layout(const PlanMax &P, bool fused, bool mixed, size_t xsize, size_t csize,
+                            bool prefetch = false);
 
 // Elasticity operator (three DOFs per node, elastic.cu): the patch kernel over the
 // scalar operator's plan (3x3 block per node-pair slot), the packed element
