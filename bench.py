@@ -459,7 +459,7 @@ def run_ours(args):
     roof = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s",
             "frac": alu_achieved / alu_peak, "traffic": profiled_traffic(kernel, wkey),
             "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz (sampled)",
-            "kernel": f"{kernel} (fused integrate + assemble) and its launches",
+            "kernel": f"{kernel} (fused integrate + assemble; bricks run its prefetching form k_patch_prefetch) and its launches",
             "flops_per_element": BRICK_FLOPS,
             "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "peak_source": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind,
