@@ -152,6 +152,22 @@ __device__ __forceinline__ Vec3<T> lerp2(T wa, const Vec3<T> &a, T wb, const Vec
     return {wa * a.x + wb * b.x, wa * a.y + wb * b.y, wa * a.z + wb * b.z};
 }
 
+// The two Gauss-point values (P a + Q b, Q a + P b) of the linear hats through
+// a and b.  P + Q = 1, so they are b + P (a - b) and a - P (a - b): one
+// subtraction and two explicit FMAs instead of two products and two FMAs.
+template <typename T>
+__device__ __forceinline__ void hat_pair(T a, T b, T &o0, T &o1) {
+    const T d = a - b;
+    o0 = fma(T(FEM_GP), d, b);
+    o1 = fma(-T(FEM_GP), d, a);
+}
+template <typename T>
+__device__ __forceinline__ void hat_pair(const Vec3<T> &a, const Vec3<T> &b, Vec3<T> &o0, Vec3<T> &o1) {
+    hat_pair(a.x, b.x, o0.x, o1.x);
+    hat_pair(a.y, b.y, o0.y, o1.y);
+    hat_pair(a.z, b.z, o0.z, o1.z);
+}
+
 // Edge vectors of a brick along each axis, e[axis][i][j], the two other axes'
 // bits (i, j) in increasing axis order.  xc[a] = coordinates of node a (input
 // precision S); the differences are formed in S and rounded once to T.
@@ -174,27 +190,21 @@ __device__ __forceinline__ void brick_edges(const S (*xc)[3], Vec3<T> (&e)[3][2]
 // Gauss indices of the two other axes.  row = sum_ij phi_i(u) phi_j(v) e[i][j].
 template <typename T>
 __device__ __forceinline__ void brick_jrows(const Vec3<T> (&e)[3][2][2], Vec3<T> (&row)[3][2][2]) {
-    const T P = T(FEM_GP), Q = T(FEM_GQ);
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         Vec3<T> m[2][2];  // m[i][v] = interpolation along the last axis
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            m[i][0] = lerp2(P, e[ax][i][0], Q, e[ax][i][1]);
-            m[i][1] = lerp2(Q, e[ax][i][0], P, e[ax][i][1]);
-        }
+        for (int i = 0; i < 2; ++i) hat_pair(e[ax][i][0], e[ax][i][1], m[i][0], m[i][1]);
 #pragma unroll
-        for (int v = 0; v < 2; ++v) {
-            row[ax][0][v] = lerp2(P, m[0][v], Q, m[1][v]);
-            row[ax][1][v] = lerp2(Q, m[0][v], P, m[1][v]);
-        }
+        for (int v = 0; v < 2; ++v) hat_pair(m[0][v], m[1][v], row[ax][0][v], row[ax][1][v]);
     }
 }
 
 // M_q (times 2, see brick_ke) for the 8 Gauss points q = 4 q1 + 2 q2 + q3, as
-// (rr, ss, tt, rs, rt, st); det[q] = det(2 J_q).
+// (rr, ss, tt, rs, rt, st), times the factor s (the element's c / 8, applied
+// once per point instead of once per packed entry); det[q] = det(2 J_q).
 template <typename T>
-__device__ __forceinline__ void brick_M(const Vec3<T> (&row)[3][2][2], T (&M)[8][6], T (&det)[8]) {
+__device__ __forceinline__ void brick_M(const Vec3<T> (&row)[3][2][2], T s, T (&M)[8][6], T (&det)[8]) {
 #pragma unroll
     for (int q1 = 0; q1 < 2; ++q1)
 #pragma unroll
@@ -208,7 +218,7 @@ __device__ __forceinline__ void brick_M(const Vec3<T> (&row)[3][2][2], T (&M)[8]
                 const Vec3<T> C0 = cross3(S, U), C1 = cross3(U, R), C2 = cross3(R, S);
                 const T d = dot3(R, C0);
                 det[q] = d;
-                const T inv = rcp_rn(d < T(0) ? -d : d);
+                const T inv = rcp_rn(d < T(0) ? -d : d) * s;
                 M[q][0] = dot3(C0, C0) * inv;
                 M[q][1] = dot3(C1, C1) * inv;
                 M[q][2] = dot3(C2, C2) * inv;
@@ -242,7 +252,6 @@ __device__ __forceinline__ void contract_FF(const T (&A)[2][2], T (&out)[3][3]) 
 // The cross terms need V[x or c][y or c][z or c] over the three axes in turn.
 template <typename T, int K1, int K2, int K3>
 __device__ __forceinline__ void contract_cross(const T (&m)[2][2][2], T (&V)[3][3][3]) {
-    const T P = T(FEM_GP), Q = T(FEM_GQ);
     const T PP = T(FEM_GPP), QQ = T(FEM_GQQ), PQ = T(FEM_GPQ);
     constexpr int N1 = K1 ? 3 : 2, N2 = K2 ? 3 : 2, N3 = K3 ? 3 : 2;
     T W[2][2][3];
@@ -256,8 +265,7 @@ __device__ __forceinline__ void contract_cross(const T (&m)[2][2][2], T (&V)[3][
                 W[a][b][1] = QQ * m0 + PP * m1;
                 W[a][b][2] = PQ * (m0 + m1);
             } else {
-                W[a][b][0] = P * m0 + Q * m1;
-                W[a][b][1] = Q * m0 + P * m1;
+                hat_pair(m0, m1, W[a][b][0], W[a][b][1]);
             }
         }
     T Y[2][3][3];
@@ -271,8 +279,7 @@ __device__ __forceinline__ void contract_cross(const T (&m)[2][2][2], T (&V)[3][
                 Y[a][1][k] = QQ * w0 + PP * w1;
                 Y[a][2][k] = PQ * (w0 + w1);
             } else {
-                Y[a][0][k] = P * w0 + Q * w1;
-                Y[a][1][k] = Q * w0 + P * w1;
+                hat_pair(w0, w1, Y[a][0][k], Y[a][1][k]);
             }
         }
 #pragma unroll
@@ -285,8 +292,7 @@ __device__ __forceinline__ void contract_cross(const T (&m)[2][2][2], T (&V)[3][
                 V[1][j][k] = QQ * y0 + PP * y1;
                 V[2][j][k] = PQ * (y0 + y1);
             } else {
-                V[0][j][k] = P * y0 + Q * y1;
-                V[1][j][k] = Q * y0 + P * y1;
+                hat_pair(y0, y1, V[0][j][k], V[1][j][k]);
             }
         }
     (void)N1;
@@ -294,9 +300,9 @@ __device__ __forceinline__ void contract_cross(const T (&m)[2][2][2], T (&V)[3][
 
 // Packed lower k_e (36 entries, p = a(a+1)/2 + b) from the M_q of brick_M.
 // With J~ = 2J and dN~ = 2 dN (signs instead of +-1/2), M = M~/2 and
-// k_ab = (c / 8) sum_q dN~_a^T M~_q dN~_b.
+// k_ab = (c / 8) sum_q dN~_a^T M~_q dN~_b; the factor c / 8 comes in M (brick_M).
 template <typename T>
-__device__ __forceinline__ void brick_contract(const T (&M)[8][6], T c, T (&k)[36]) {
+__device__ __forceinline__ void brick_contract(const T (&M)[8][6], T (&k)[36]) {
     T Arr[2][2], Ass[2][2], Att[2][2];
     T mrs[2][2][2], mrt[2][2][2], mst[2][2][2];
 #pragma unroll
@@ -326,7 +332,6 @@ __device__ __forceinline__ void brick_contract(const T (&M)[8][6], T c, T (&k)[3
     contract_cross<T, 0, 0, 1>(mrs, Vrs);  // [x][y][c3]
     contract_cross<T, 0, 1, 0>(mrt, Vrt);  // [x][c2][z]
     contract_cross<T, 1, 0, 0>(mst, Vst);  // [c1][y][z]
-    const T s = c * T(0.125);
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
 #pragma unroll
@@ -343,7 +348,7 @@ __device__ __forceinline__ void brick_contract(const T (&M)[8][6], T c, T (&k)[3
             v += T(hsig(a3) * hsig(b1)) * Vrt[a1][c2][b3];
             v += T(hsig(a2) * hsig(b3)) * Vst[c1][b2][a3];
             v += T(hsig(a3) * hsig(b2)) * Vst[c1][a2][b3];
-            k[a * (a + 1) / 2 + b] = s * v;
+            k[a * (a + 1) / 2 + b] = v;
         }
     }
 }
@@ -356,8 +361,8 @@ __device__ __forceinline__ void brick_ke(const S (*xc)[3], T c, T (&k)[36]) {
     Vec3<T> row[3][2][2];
     brick_jrows(e, row);
     T M[8][6], det[8];
-    brick_M(row, M, det);
-    brick_contract(M, c, k);
+    brick_M(row, c * T(0.125), M, det);
+    brick_contract(M, k);
 }
 
 // Mixed precision brick: FP32 throughout, except that an element whose ratio
@@ -371,7 +376,7 @@ __device__ __forceinline__ bool brick_ke_mixed(const S (*xc)[3], float c, float 
     Vec3<float> row[3][2][2];
     brick_jrows(e, row);
     float M[8][6], det[8];
-    brick_M(row, M, det);
+    brick_M(row, c * 0.125f, M, det);
     float dmin = det[0], dmax = det[0];
 #pragma unroll
     for (int q = 1; q < 8; ++q) {
@@ -385,13 +390,13 @@ __device__ __forceinline__ bool brick_ke_mixed(const S (*xc)[3], float c, float 
         Vec3<double> rowd[3][2][2];
         brick_jrows(ed, rowd);
         double Md[8][6], detd[8];
-        brick_M(rowd, Md, detd);
+        brick_M(rowd, (double)c * 0.125, Md, detd);
 #pragma unroll
         for (int q = 0; q < 8; ++q)
 #pragma unroll
             for (int i = 0; i < 6; ++i) M[q][i] = (float)Md[q][i];
     }
-    brick_contract(M, c, k);
+    brick_contract(M, k);
     return flagged;
 }
 
