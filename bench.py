@@ -657,6 +657,7 @@ def other_workloads(flush, stream, with_error):
             mesh.sync()
             out[key]["backward_ms"] = tb
             out[key]["backward_lib_gb"] = mesh.info()["live_bytes"] / 1e9
+            out[key]["backward_plan_gb"] = mesh.info()["plan_bytes"] / 1e9  # with the in-row positions
             del G
         mesh.close()
         del mesh, v

@@ -697,6 +697,7 @@ fem_status fem_vjp(fem_mesh m, fem_prec p, const void *X, fem_dtype x_dtype, con
         return FEM_ERR_ARG;
     }
     FEM_TRY(ensure_plan(m, as_stream(stream)));
+    FEM_TRY(ensure_positions(m, as_stream(stream)));
     if (is_elastic(m))
         return launch_elastic_vjp(m, p == FEM_MIXED, X, x_dtype, c, c_dtype, G, dX, dc, as_stream(stream));
     return launch_vjp(m, p == FEM_MIXED, X, x_dtype, c, c_dtype, G, dX, dc, as_stream(stream));

@@ -163,6 +163,7 @@ struct fem_mesh_s {
     fem::DevBuf<int32_t> inc_elem;
     fem::Plan plan;
     bool plan_built = false;  // the patch plan exists (it is built on first use when tiles serve the builds)
+    bool want_pos = false;    // closures carry the in-row positions (set by the first backward pass)
     fem::TilePlan tiles;      // element tiles of the scalar operators (tile.cuh)
     // device status word: set by a bounded device-side wait that gave up
     fem::DevBuf<int> status;
@@ -209,6 +210,8 @@ void batch_forget(fem_mesh m);  // drops cached batched launches that use m's pl
 fem_status build_pattern(fem_mesh m, cudaStream_t s);
 fem_status build_plan(fem_mesh m, cudaStream_t s);
 fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaStream_t s);
+// From now on the closures carry the in-row positions the backward pass reads.
+fem_status ensure_positions(fem_mesh m, cudaStream_t s);
 // Runs fn over the closure of every patch group (one group covering all patches
 // unless the plan is chunked under the memory budget).
 fem_status for_each_group(fem_mesh m, cudaStream_t s, const std::function<fem_status(const Closure &)> &fn);

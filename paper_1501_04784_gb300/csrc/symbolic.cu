@@ -698,10 +698,31 @@ struct OwnTables {
     int32_t trash;                  // first of the 32 scratch accumulators (the plan's max_acc)
 };
 
+// Position of packed pair (a, b) of an element with node ids g in its lower-CSR
+// row: the pair's row is its node with the larger global id; the diagonal closes
+// its lower row; an off-diagonal pair's position is a binary search of the
+// smaller id in that (ascending) row.  r0, rl: start and length of each node's row.
+template <int NPE>
+__device__ __forceinline__ int pair_position(const int32_t (&g)[NPE], const int64_t (&r0)[NPE], const int (&rl)[NPE],
+                                             int a, int b, const int32_t *__restrict__ col) {
+    if (a == b) return rl[a] - 1;
+    const bool ra = g[a] > g[b];
+    const int64_t rb = ra ? r0[a] : r0[b];
+    const int32_t v = ra ? g[b] : g[a];
+    int lo = 0, n = ra ? rl[a] : rl[b];
+    while (n > 1) {
+        const int half = n >> 1;
+        if (col[rb + lo + half] <= v) lo += half;
+        n -= half;
+    }
+    return lo;
+}
+
 template <int NPE>
 // One block per patch: the patch's closure-node ids (ascending) are staged in
 // shared memory, so that the closure-local index of each element node is a
-// binary search there rather than a chain of dependent global loads.
+// binary search there rather than a chain of dependent global loads.  The in-row
+// positions (pos) are written only when the closures carry them (pos non-null).
 __global__ void __launch_bounds__(256, 3) k_celem_fill(const uint64_t *ckeys, int64_t np_, const int32_t *__restrict__ E,
                              const uint64_t *cn_keys, const int64_t *pc_ptr, const int64_t *__restrict__ rowptr,
                              const int32_t *__restrict__ col, int pos_stride, OwnTables ot, int32_t *celem_id,
@@ -766,26 +787,12 @@ __global__ void __launch_bounds__(256, 3) k_celem_fill(const uint64_t *ckeys, in
         for (int a = 0; a < NPE; ++a)
 #pragma unroll
             for (int b = 0; b <= a; ++b, ++q) {
-                // the pair's row is its node with the larger global id; the
-                // diagonal closes its lower row; an off-diagonal pair's position is
-                // a binary search of the smaller id in that (ascending) row, the
-                // searches of an element's pairs independent of one another
+                // the searches of an element's pairs are independent of one another
                 const bool ra = g[a] > g[b];
-                int ps = rl[a] - 1;
-                if (a != b) {
-                    const int64_t rb = ra ? r0[a] : r0[b];
-                    const int32_t v = ra ? g[b] : g[a];
-                    int lo = 0, n = ra ? rl[a] : rl[b];
-                    while (n > 1) {
-                        const int half = n >> 1;
-                        if (col[rb + lo + half] <= v) lo += half;
-                        n -= half;
-                    }
-                    ps = lo;
-                }
+                const int ps = pair_position<NPE>(g, r0, rl, a, b, col);
                 pw |= (uint32_t)(ps & 0xff) << (8 * (q & 3));
                 if ((q & 3) == 3 || q == NP - 1) {
-                    pos32[q >> 2] = pw;
+                    if (pos) pos32[q >> 2] = pw;
                     pw = 0;
                 }
                 // a pair whose row the patch does not own goes to a scratch slot of
@@ -799,10 +806,47 @@ __global__ void __launch_bounds__(256, 3) k_celem_fill(const uint64_t *ckeys, in
                 if (q & 1) aidx32[(int64_t)(q >> 1) * nce + i] = alo | ((t & 0xffffu) << 16);
                 else alo = t & 0xffffu;
             }
-        for (int w = (NP + 3) / 4; w < pos_stride / 4; ++w) pos32[w] = 0;
+        if (pos)
+            for (int w = (NP + 3) / 4; w < pos_stride / 4; ++w) pos32[w] = 0;
     }
     __syncthreads();
   }
+}
+
+// The in-row positions of every closure element of an existing closure (the
+// backward pass reads them; closures built before the first backward call do not
+// carry them): the same positions k_celem_fill writes, from the element's ids.
+template <int NPE>
+__global__ void k_celem_pos(const int32_t *__restrict__ celem_id, int64_t nce, const int32_t *__restrict__ E,
+                            const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col, int pos_stride,
+                            uint8_t *pos) {
+    constexpr int NP = NPE * (NPE + 1) / 2;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nce; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = celem_id[i];
+        int32_t g[NPE];
+        int64_t r0[NPE];
+        int rl[NPE];
+#pragma unroll
+        for (int x = 0; x < NPE; ++x) {
+            g[x] = E[e * NPE + x];
+            r0[x] = rowptr[g[x]];
+            rl[x] = (int)(rowptr[g[x] + 1] - r0[x]);
+        }
+        uint32_t *pos32 = reinterpret_cast<uint32_t *>(pos + i * pos_stride);
+        uint32_t pw = 0;
+        int q = 0;
+#pragma unroll
+        for (int a = 0; a < NPE; ++a)
+#pragma unroll
+            for (int b = 0; b <= a; ++b, ++q) {
+                pw |= (uint32_t)(pair_position<NPE>(g, r0, rl, a, b, col) & 0xff) << (8 * (q & 3));
+                if ((q & 3) == 3 || q == NP - 1) {
+                    pos32[q >> 2] = pw;
+                    pw = 0;
+                }
+            }
+        for (int w = (NP + 3) / 4; w < pos_stride / 4; ++w) pos32[w] = 0;
+    }
 }
 
 // One pass of the row pattern (cnt: counts; else the columns at rowptr) over
@@ -1381,7 +1425,7 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
     FEM_TRY(cl.celem_id.alloc(ar, nce, "celem id"));
     FEM_TRY(cl.celem_color.alloc(ar, nce, "celem colour"));
     FEM_TRY(cl.celem_lnode.alloc(ar, nce * npe, "celem local nodes"));
-    FEM_TRY(cl.celem_pos.alloc(ar, nce * P.pos_stride, "celem positions"));
+    if (m->want_pos) FEM_TRY(cl.celem_pos.alloc(ar, nce * P.pos_stride, "celem positions"));
     FEM_TRY(cl.celem_aidx.alloc(ar, nce * (m->np / 2), "celem accumulator targets"));
     const OwnTables ot{P.node_patch.ptr,     P.own_idx.ptr, P.own_acc.ptr,          P.patch_node_ptr.ptr,
                        P.own_hv.ptr,         cl.patch_elem_ptr.ptr, p0, (int32_t)P.max_acc};
@@ -1400,14 +1444,53 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
             FEM_CUDA(cudaFuncSetAttribute(k_celem_fill<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_celem_fill<8><<<grid, TPB, smem, s>>>(ckeys.ptr, np_, m->E, cnkeys.ptr, cl.patch_cnode_ptr.ptr,
                                                     m->rowptr.ptr, m->col.ptr, P.pos_stride, ot, cl.celem_id.ptr,
-                                                    cl.celem_color.ptr, cl.celem_lnode.ptr, cl.celem_pos.ptr, aidx16);
+                                                    cl.celem_color.ptr, cl.celem_lnode.ptr,
+                                                    m->want_pos ? cl.celem_pos.ptr : nullptr, aidx16);
         } else {
             FEM_CUDA(cudaFuncSetAttribute(k_celem_fill<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_celem_fill<4><<<grid, TPB, smem, s>>>(ckeys.ptr, np_, m->E, cnkeys.ptr, cl.patch_cnode_ptr.ptr,
                                                     m->rowptr.ptr, m->col.ptr, P.pos_stride, ot, cl.celem_id.ptr,
-                                                    cl.celem_color.ptr, cl.celem_lnode.ptr, cl.celem_pos.ptr, aidx16);
+                                                    cl.celem_color.ptr, cl.celem_lnode.ptr,
+                                                    m->want_pos ? cl.celem_pos.ptr : nullptr, aidx16);
         }
         FEM_LAUNCHED("k_celem_fill");
+    }
+    return FEM_OK;
+}
+
+// The closures carry the in-row positions from now on (the backward pass reads
+// them; forward builds do not, so a mesh that only builds K does not hold them).
+// Closures built per patch group get them when they are built; the cached full
+// closure gets them here.  If the budget cannot hold them beside the cached
+// closures, the plan is built again (in patch groups if need be).
+fem_status ensure_positions(fem_mesh m, cudaStream_t s) {
+    if (m->want_pos) return FEM_OK;
+    m->want_pos = true;
+    if (!m->plan_built || m->plan.chunked) return FEM_OK;
+    Plan &P = m->plan;
+    Closure &cl = P.full;
+    const int64_t nce = cl.total_celems;
+    fem_status st = cl.celem_pos.alloc(m->arena, (size_t)nce * P.pos_stride, "celem positions");
+    if (st == FEM_ERR_BUDGET) {
+        cudaGetLastError();
+        cl.celem_pos.free();
+        batch_forget(m);
+        m->plan_built = false;
+        ArenaKeep keep(m->arena);
+        FEM_TRY(build_plan(m, s));
+        m->plan_built = true;
+        return FEM_OK;
+    }
+    FEM_TRY(st);
+    if (nce > 0) {
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(nce, TPB), (int64_t)num_sms() * 8));
+        if (m->npe == 8)
+            k_celem_pos<8><<<grid, TPB, 0, s>>>(cl.celem_id.ptr, nce, m->E, m->rowptr.ptr, m->col.ptr, P.pos_stride,
+                                                cl.celem_pos.ptr);
+        else
+            k_celem_pos<4><<<grid, TPB, 0, s>>>(cl.celem_id.ptr, nce, m->E, m->rowptr.ptr, m->col.ptr, P.pos_stride,
+                                                cl.celem_pos.ptr);
+        FEM_LAUNCHED("k_celem_pos");
     }
     return FEM_OK;
 }
