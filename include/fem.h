@@ -150,6 +150,15 @@ typedef struct {
                                     from the other (Section 4.3's overlap of one group's
                                     transfer with the next group's integration): device
                                     memory holds 2 ranges of values, not K */
+    int group_cache;             /* plans built per patch group (Eq. 10: the memory budget
+                                    cannot hold every patch's closure at once): 1 (default) =
+                                    each group's closure is built once and a copy kept in
+                                    page-locked host memory (about 93 bytes per closure
+                                    element, 129 once fem_vjp has run); later calls copy each
+                                    group back to the device, one at a time, instead of
+                                    building it again; 0 = build every group's closure at
+                                    every call (no host memory).  A group whose copy does not
+                                    fit beside the call's other buffers is built instead. */
 } fem_options;
 
 /*

@@ -28,7 +28,7 @@ class fem_options(ctypes.Structure):
                 ("wait_spins", ctypes.c_int), ("debug_stall", ctypes.c_int),
                 ("operator_kind", ctypes.c_int), ("host_direct", ctypes.c_int), ("vjp_fused", ctypes.c_int),
                 ("assembly", ctypes.c_int), ("tile_elems", ctypes.c_int),
-                ("host_chunks", ctypes.c_int)]
+                ("host_chunks", ctypes.c_int), ("group_cache", ctypes.c_int)]
 
 
 class fem_info(ctypes.Structure):

@@ -140,6 +140,7 @@ void fem_options_default(fem_options *opt) {
     opt->block_threads = 0;
     opt->blocks_per_sm = 0;
     opt->locality_order = 1;
+    opt->group_cache = 1;
 }
 
 const char *fem_status_str(fem_status s) {

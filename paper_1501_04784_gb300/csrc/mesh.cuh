@@ -11,7 +11,10 @@
 // the result is bitwise reproducible without atomics.
 #pragma once
 
+#include <cstring>
 #include <functional>
+#include <utility>
+#include <vector>
 
 #include "common.cuh"
 #include "tile.cuh"
@@ -142,6 +145,39 @@ struct Plan {
     }
 };
 
+// A copy, in page-locked host memory, of one patch group's closure (plans built
+// per patch group under the memory budget): the numeric calls copy it back to the
+// device instead of building the closure again (fem_options.group_cache).
+struct HostClosure {
+    int64_t p0 = 0, p1 = 0, total_cnodes = 0, total_celems = 0, max_cnodes = 0, max_celems = 0;
+    int n_colors = 0;
+    bool has_pos = false;   // the in-row positions are part of the copy
+    unsigned char *host = nullptr;
+    size_t bytes = 0;
+    // byte offsets of the arrays in `host` and their element counts
+    size_t o_pep, o_pcp, o_gid, o_own, o_id, o_col, o_pos, o_ln, o_aidx;
+    size_t n_pep, n_pcp, n_gid, n_own, n_id, n_col, n_pos, n_ln, n_aidx;
+    HostClosure() = default;
+    HostClosure(const HostClosure &) = delete;
+    HostClosure &operator=(const HostClosure &) = delete;
+    HostClosure(HostClosure &&o) noexcept { *this = std::move(o); }
+    HostClosure &operator=(HostClosure &&o) noexcept {
+        if (this != &o) {
+            release();
+            std::memcpy(static_cast<void *>(this), static_cast<const void *>(&o), sizeof(HostClosure));
+            o.host = nullptr;
+            o.bytes = 0;
+        }
+        return *this;
+    }
+    void release() {
+        if (host) cudaFreeHost(host);
+        host = nullptr;
+        bytes = 0;
+    }
+    ~HostClosure() { release(); }
+};
+
 }  // namespace fem
 
 struct fem_mesh_s {
@@ -201,6 +237,10 @@ struct fem_mesh_s {
     cudaEvent_t chunk_built[2] = {}, slot_free[2] = {};
     int n_groups = 1;
     int64_t group_patches = 0;  // patches per group when the closures are built per group
+    // host copies of the patch groups' closures, in patch order (fem_options.group_cache);
+    // valid when non-empty and built with the current want_pos
+    std::vector<fem::HostClosure> group_cache;
+    bool group_cache_pos = false;
 };
 
 namespace fem {

@@ -1466,6 +1466,7 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
 fem_status ensure_positions(fem_mesh m, cudaStream_t s) {
     if (m->want_pos) return FEM_OK;
     m->want_pos = true;
+    m->group_cache.clear();  // copies without the positions
     if (!m->plan_built || m->plan.chunked) return FEM_OK;
     Plan &P = m->plan;
     Closure &cl = P.full;
@@ -1500,20 +1501,107 @@ fem_status ensure_positions(fem_mesh m, cudaStream_t s) {
 // of G patches is tried, halved while its closure does not fit, and every group
 // is built once here to record the sizes the kernels' shared memory needs; the
 // numeric calls rebuild each group's closure, run it and free it.
+// A page-locked host copy of a built closure (the group cache).  Returns false
+// (and leaves `h` empty) if the host memory cannot be had.
+static bool closure_to_host(fem_mesh m, const Closure &cl, HostClosure &h, cudaStream_t s) {
+    const int64_t np_ = cl.p1 - cl.p0;
+    h.p0 = cl.p0, h.p1 = cl.p1, h.total_cnodes = cl.total_cnodes, h.total_celems = cl.total_celems;
+    h.max_cnodes = cl.max_cnodes, h.max_celems = cl.max_celems, h.n_colors = cl.n_colors;
+    h.has_pos = cl.celem_pos.ptr != nullptr;
+    h.n_pep = h.n_pcp = (size_t)np_ + 1;
+    h.n_gid = h.n_own = (size_t)cl.total_cnodes;
+    h.n_id = h.n_col = (size_t)cl.total_celems;
+    h.n_pos = h.has_pos ? cl.celem_pos.n : 0;
+    h.n_ln = cl.celem_lnode.n;
+    h.n_aidx = cl.celem_aidx.n;
+    size_t o = 0;
+    auto take = [&](size_t &off, size_t bytes) { off = o; o += (bytes + 255) & ~(size_t)255; };
+    take(h.o_pep, h.n_pep * 8);
+    take(h.o_pcp, h.n_pcp * 8);
+    take(h.o_gid, h.n_gid * 4);
+    take(h.o_own, h.n_own * 4);
+    take(h.o_id, h.n_id * 4);
+    take(h.o_col, h.n_col);
+    take(h.o_pos, h.n_pos);
+    take(h.o_ln, h.n_ln * 2);
+    take(h.o_aidx, h.n_aidx * 4);
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, o, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    h.host = static_cast<unsigned char *>(p);
+    h.bytes = o;
+    auto down = [&](size_t off, const void *src, size_t bytes) {
+        return bytes == 0 || cudaMemcpyAsync(h.host + off, src, bytes, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    };
+    bool ok = down(h.o_pep, cl.patch_elem_ptr.ptr, h.n_pep * 8) && down(h.o_pcp, cl.patch_cnode_ptr.ptr, h.n_pcp * 8) &&
+              down(h.o_gid, cl.cnode_gid.ptr, h.n_gid * 4) && down(h.o_own, cl.cnode_own.ptr, h.n_own * 4) &&
+              down(h.o_id, cl.celem_id.ptr, h.n_id * 4) && down(h.o_col, cl.celem_color.ptr, h.n_col) &&
+              down(h.o_pos, cl.celem_pos.ptr, h.n_pos) && down(h.o_ln, cl.celem_lnode.ptr, h.n_ln * 2) &&
+              down(h.o_aidx, cl.celem_aidx.ptr, h.n_aidx * 4);
+    ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        h.release();
+    }
+    (void)m;
+    return ok;
+}
+
+// The closure of a host copy, back in device memory (under the budget).
+static fem_status closure_from_host(fem_mesh m, const HostClosure &h, Closure &cl, cudaStream_t s) {
+    Arena &ar = m->arena;
+    cl.p0 = h.p0, cl.p1 = h.p1, cl.total_cnodes = h.total_cnodes, cl.total_celems = h.total_celems;
+    cl.max_cnodes = h.max_cnodes, cl.max_celems = h.max_celems, cl.n_colors = h.n_colors;
+    FEM_TRY(cl.patch_elem_ptr.alloc(ar, h.n_pep, "patch elem ptr"));
+    FEM_TRY(cl.patch_cnode_ptr.alloc(ar, h.n_pcp, "patch cnode ptr"));
+    FEM_TRY(cl.cnode_gid.alloc(ar, h.n_gid, "cnode gid"));
+    FEM_TRY(cl.cnode_own.alloc(ar, h.n_own, "cnode own"));
+    FEM_TRY(cl.celem_id.alloc(ar, h.n_id, "celem id"));
+    FEM_TRY(cl.celem_color.alloc(ar, h.n_col, "celem colour"));
+    if (h.has_pos) FEM_TRY(cl.celem_pos.alloc(ar, h.n_pos, "celem positions"));
+    FEM_TRY(cl.celem_lnode.alloc(ar, h.n_ln, "celem local nodes"));
+    FEM_TRY(cl.celem_aidx.alloc(ar, h.n_aidx, "celem accumulator targets"));
+    auto up = [&](void *dst, size_t off, size_t bytes) -> fem_status {
+        if (bytes) FEM_CUDA(cudaMemcpyAsync(dst, h.host + off, bytes, cudaMemcpyHostToDevice, s));
+        return FEM_OK;
+    };
+    FEM_TRY(up(cl.patch_elem_ptr.ptr, h.o_pep, h.n_pep * 8));
+    FEM_TRY(up(cl.patch_cnode_ptr.ptr, h.o_pcp, h.n_pcp * 8));
+    FEM_TRY(up(cl.cnode_gid.ptr, h.o_gid, h.n_gid * 4));
+    FEM_TRY(up(cl.cnode_own.ptr, h.o_own, h.n_own * 4));
+    FEM_TRY(up(cl.celem_id.ptr, h.o_id, h.n_id * 4));
+    FEM_TRY(up(cl.celem_color.ptr, h.o_col, h.n_col));
+    if (h.has_pos) FEM_TRY(up(cl.celem_pos.ptr, h.o_pos, h.n_pos));
+    FEM_TRY(up(cl.celem_lnode.ptr, h.o_ln, h.n_ln * 2));
+    FEM_TRY(up(cl.celem_aidx.ptr, h.o_aidx, h.n_aidx * 4));
+    return FEM_OK;
+}
+
+// Builds the closure of patches [p0, p1) (halving the range while the budget
+// refuses it), runs fn on it and frees it; with `rec`, a host copy of every
+// closure built is appended to it (cleared if host memory runs out).
 static fem_status closure_range(fem_mesh m, int64_t p0, int64_t p1, cudaStream_t s,
-                                const std::function<fem_status(const Closure &)> &fn, int *groups) {
+                                const std::function<fem_status(const Closure &)> &fn, int *groups,
+                                std::vector<HostClosure> *rec = nullptr, bool *rec_ok = nullptr) {
     Closure cl;
     fem_status st = build_closure(m, p0, p1, cl, s);
     if (st == FEM_ERR_BUDGET && p1 - p0 > 1) {
         cl.reset();
         cudaGetLastError();
         const int64_t mid = p0 + (p1 - p0) / 2;
-        FEM_TRY(closure_range(m, p0, mid, s, fn, groups));
-        return closure_range(m, mid, p1, s, fn, groups);
+        FEM_TRY(closure_range(m, p0, mid, s, fn, groups, rec, rec_ok));
+        return closure_range(m, mid, p1, s, fn, groups, rec, rec_ok);
     }
     FEM_TRY(st);
     ++*groups;
     FEM_TRY(fn(cl));
+    if (rec && *rec_ok) {
+        HostClosure h;
+        if (closure_to_host(m, cl, h, s)) rec->push_back(std::move(h));
+        else *rec_ok = false;
+    }
     FEM_CUDA(cudaStreamSynchronize(s));  // the closure's buffers are freed on return
     return FEM_OK;
 }
@@ -1522,9 +1610,39 @@ fem_status for_each_group(fem_mesh m, cudaStream_t s, const std::function<fem_st
     Plan &P = m->plan;
     if (!P.chunked) return fn(P.full);
     int groups = 0;
+    const bool use_cache = m->opt.group_cache != 0;
+    if (use_cache && !m->group_cache.empty() && m->group_cache_pos == m->want_pos) {
+        // the groups' closures copied back from host memory, one at a time
+        for (const HostClosure &h : m->group_cache) {
+            Closure cl;
+            fem_status st = closure_from_host(m, h, cl, s);
+            if (st == FEM_ERR_BUDGET) {
+                // the budget cannot hold this copy beside what the call holds now:
+                // build the group's closure in smaller parts instead
+                cl.reset();
+                cudaGetLastError();
+                FEM_CUDA(cudaStreamSynchronize(s));
+                FEM_TRY(closure_range(m, h.p0, h.p1, s, fn, &groups));
+                continue;
+            }
+            FEM_TRY(st);
+            ++groups;
+            FEM_TRY(fn(cl));
+            FEM_CUDA(cudaStreamSynchronize(s));  // the closure's buffers are freed on return
+        }
+        m->n_groups = groups;
+        return FEM_OK;
+    }
+    std::vector<HostClosure> rec;
+    bool rec_ok = use_cache;
     for (int64_t p0 = 0; p0 < P.n_patches; p0 += m->group_patches)
-        FEM_TRY(closure_range(m, p0, std::min(P.n_patches, p0 + m->group_patches), s, fn, &groups));
+        FEM_TRY(closure_range(m, p0, std::min(P.n_patches, p0 + m->group_patches), s, fn, &groups,
+                              use_cache ? &rec : nullptr, &rec_ok));
     m->n_groups = groups;
+    if (use_cache && rec_ok) {
+        m->group_cache = std::move(rec);
+        m->group_cache_pos = m->want_pos;
+    }
     return FEM_OK;
 }
 
@@ -1576,6 +1694,7 @@ static fem_status build_plan_cap(fem_mesh m, cudaStream_t s, int64_t cap_in) {
     Plan &P = m->plan;
     batch_forget(m);  // cached batched launches were sized for the old plan
     P.reset();
+    m->group_cache.clear();
     // the elasticity operator holds a 3x3 block per node pair: fewer pairs fit
     const bool elastic = m->opt.operator_kind == 2;
     // (defaults measured on the 1M-brick and 3.07M-tet workloads)

@@ -109,6 +109,35 @@ def test_fp64_staged_and_fused_agree(fem):
     assert np.abs(staged - fused).max() <= 1e-14 * np.abs(ref["cs"]).max()
 
 
+def test_group_cache_equals_rebuilt_groups(fem):
+    """Patch groups copied back from the host copies of their closures (group_cache,
+    the default) give the values of groups built again at every call
+    (group_cache = 0) and of the unbudgeted build, bitwise, on repeated calls; the
+    first backward pass (which adds the in-row positions and so renews the copies)
+    agrees too, and the builds after it still do.  Both match the oracle."""
+    m = meshgen.hex_grid(24, jitter=0.2, seed=78, permute_nodes=True, permute_elems=True)
+    X, c = dev(m.X, torch.float32), dev(m.c, torch.float32)
+    E, X64 = dev(m.E, torch.int32), dev(m.X, torch.float64)
+    free = fem.Mesh(E, m.n_nodes, X=X64, patch_entries=1024, vjp_fused=1)
+    ref = free.build_K(X, c, "mixed")
+    budget = int(free.info()["plan_bytes"] * 0.75)
+    cached = fem.Mesh(E, m.n_nodes, X=X64, patch_entries=1024, mem_budget_bytes=budget)
+    rebuilt = fem.Mesh(E, m.n_nodes, X=X64, patch_entries=1024, mem_budget_bytes=budget, group_cache=0)
+    for _ in range(2):
+        assert torch.equal(cached.build_K(X, c, "mixed"), ref)
+        assert torch.equal(rebuilt.build_K(X, c, "mixed"), ref)
+    assert cached.info()["n_groups"] > 1 and rebuilt.info()["n_groups"] > 1
+    o = oracle_K(m, m.X.astype(np.float32), m.c.astype(np.float32))
+    assert rel_err(ref.cpu().numpy(), o["vals"], o["cs"]) <= TOL_MIXED
+    G = dev(np.random.default_rng(5).standard_normal(free.nnz), torch.float32)
+    a, b, r = cached.vjp(X, c, G, "mixed"), rebuilt.vjp(X, c, G, "mixed"), free.vjp(X, c, G, "mixed")
+    for u, v, w in zip(a, b, r):
+        assert torch.equal(u, v) and torch.equal(u, w)
+    assert torch.equal(cached.build_K(X, c, "mixed"), ref)
+    cached.sync()
+    rebuilt.sync()
+
+
 def test_autotune_tiles(fem):
     """The tuner on a mesh that builds on element tiles picks a tile size."""
     m = meshgen.config_mesh(0)
