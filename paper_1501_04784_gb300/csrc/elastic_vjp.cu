@@ -332,15 +332,41 @@ template <typename S>
 __device__ __forceinline__ void load_cnodes(const PlanView &pv, const int64_t *__restrict__ rowptr, int64_t cb,
                                             int ncn, const S *__restrict__ X, S (*xs)[3], int32_t *cown, int64_t *db,
                                             int32_t *rl) {
-    for (int j = threadIdx.x; j < ncn; j += blockDim.x) {
-        const int32_t g = pv.cnode_gid[cb + j];
-        const int64_t r0 = rowptr[g];
-        db[j] = 9 * r0 - 3 * (int64_t)g;
-        rl[j] = (int)(rowptr[g + 1] - r0);
-        cown[j] = pv.cnode_own[cb + j];
-        xs[j][0] = X[3 * (int64_t)g + 0];
-        xs[j][1] = X[3 * (int64_t)g + 1];
-        xs[j][2] = X[3 * (int64_t)g + 2];
+    // ids first, then their rows and coordinates, CH nodes in flight per thread
+    constexpr int CH = 4;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int j0 = 0; j0 < ncn; j0 += CH * nthr) {
+        int32_t gv[CH], ov[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const int j = j0 + u * nthr + tid;
+            gv[u] = j < ncn ? pv.cnode_gid[cb + j] : 0;
+            ov[u] = j < ncn ? pv.cnode_own[cb + j] : -1;
+        }
+        int64_t r0[CH], r1[CH];
+        S xv[CH][3];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const int j = j0 + u * nthr + tid;
+            const int64_t g = gv[u];
+            r0[u] = j < ncn ? rowptr[g] : 0;
+            r1[u] = j < ncn ? rowptr[g + 1] : 0;
+            xv[u][0] = j < ncn ? X[3 * g + 0] : S(0);
+            xv[u][1] = j < ncn ? X[3 * g + 1] : S(0);
+            xv[u][2] = j < ncn ? X[3 * g + 2] : S(0);
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const int j = j0 + u * nthr + tid;
+            if (j < ncn) {
+                db[j] = 9 * r0[u] - 3 * (int64_t)gv[u];
+                rl[j] = (int)(r1[u] - r0[u]);
+                cown[j] = ov[u];
+                xs[j][0] = xv[u][0];
+                xs[j][1] = xv[u][1];
+                xs[j][2] = xv[u][2];
+            }
+        }
     }
 }
 

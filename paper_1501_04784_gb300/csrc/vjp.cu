@@ -618,21 +618,49 @@ __global__ void __launch_bounds__(256) k_vjp_elem(PlanView pv, const int64_t *__
         const int ncn = (int)(pv.patch_cnode_ptr[p + 1] - cb);
         const int64_t eb = pv.patch_elem_ptr[p];
         const int nel = (int)(pv.patch_elem_ptr[p + 1] - eb);
-        for (int j = tid; j < ncn; j += nthr) {
-            const int32_t g = pv.cnode_gid[cb + j];
-            rp[j] = rowptr[g];
-            cown[j] = pv.cnode_own[cb + j];
-            xs[j][0] = X[3 * (int64_t)g + 0];
-            xs[j][1] = X[3 * (int64_t)g + 1];
-            xs[j][2] = X[3 * (int64_t)g + 2];
+        // closure nodes: ids, then their row starts and coordinates, CH nodes in
+        // flight per thread (the second loads depend on the first)
+        constexpr int CH = 4;
+        for (int j0 = 0; j0 < ncn; j0 += CH * nthr) {
+            int32_t gv[CH], ov[CH];
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                const int j = j0 + u * nthr + tid;
+                gv[u] = j < ncn ? pv.cnode_gid[cb + j] : 0;
+                ov[u] = j < ncn ? pv.cnode_own[cb + j] : -1;
+            }
+            int64_t rv[CH];
+            S xv[CH][3];
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                const int j = j0 + u * nthr + tid;
+                const int64_t g = gv[u];
+                rv[u] = j < ncn ? rowptr[g] : 0;
+                xv[u][0] = j < ncn ? X[3 * g + 0] : S(0);
+                xv[u][1] = j < ncn ? X[3 * g + 1] : S(0);
+                xv[u][2] = j < ncn ? X[3 * g + 2] : S(0);
+            }
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                const int j = j0 + u * nthr + tid;
+                if (j < ncn) {
+                    rp[j] = rv[u];
+                    cown[j] = ov[u];
+                    xs[j][0] = xv[u][0];
+                    xs[j][1] = xv[u][1];
+                    xs[j][2] = xv[u][2];
+                }
+            }
         }
         const int np = primary_elems(pv, NPE, eb, nel, cown, list, &n_prim);
         for (int k = tid; k < np; k += nthr) {
             const int64_t ci = eb + list[k];
             const int64_t e = pv.celem_id[ci];
+            uint16_t lv[NPE];
+            load_lnodes<NPE>(pv.celem_lnode, ci, lv);
             int ln[NPE];
 #pragma unroll
-            for (int a = 0; a < NPE; ++a) ln[a] = pv.celem_lnode[ci * NPE + a];
+            for (int a = 0; a < NPE; ++a) ln[a] = lv[a];
             S xc[NPE][3];
 #pragma unroll
             for (int a = 0; a < NPE; ++a) {
