@@ -184,3 +184,31 @@ def test_autograd_central_differences_10cube(fem):
         cm[e] -= h
         fd = (Lval(Xd, cp) - Lval(Xd, cm)) / (2 * h)
         assert abs(fd - float(c.grad[e])) <= 1e-6 * (abs(fd) + 1e-3)
+
+
+@pytest.mark.parametrize("name", ["hex_4x3x3", "tet_3x3x2"])
+def test_positions_added_by_first_backward(fem, name):
+    """A mesh that only builds K holds no in-row positions (they serve the backward
+    pass only): the first backward pass adds them to the cached closures (the plan
+    grows by 4 bytes per packed pair, padded, per closure element), its gradient
+    matches the oracle, and the builds before and after it are bitwise equal."""
+    m = CASES[name]()
+    X, c = rounded_inputs(m, "mixed")
+    Xd, cd = dev(X, torch.float32), dev(c, torch.float32)
+    mesh = fem.Mesh(dev(m.E, torch.int32), m.n_nodes, X=dev(m.X, torch.float64), patch_entries=512)
+    nnz = mesh.pattern()
+    before = mesh.build_K(Xd, cd, "mixed").clone()
+    info0 = mesh.info()
+    ref = oracle.build_K(m.npe, X.astype(np.float64), m.E, c.astype(np.float64))
+    G = np.random.default_rng(9).standard_normal(nnz).astype(np.float32)
+    dX_ref, dc_ref = oracle.vjp_from_G(m.npe, X.astype(np.float64), m.E, c.astype(np.float64),
+                                       G.astype(np.float64), ref["slot"])
+    dX, dc = mesh.vjp(Xd, cd, dev(G, torch.float32), "mixed")
+    mesh.sync()
+    npairs = m.npe * (m.npe + 1) // 2
+    grown = mesh.info()["plan_bytes"] - info0["plan_bytes"]
+    assert grown == info0["closure_elems"] * ((npairs + 3) // 4 * 4)
+    sx, sc = vjp_scales(m, X, c, G[ref["slot"]])
+    assert vjp_err(dX.cpu().numpy(), dX_ref, sx) <= TOL_VJP_MIXED
+    assert vjp_err(dc.cpu().numpy(), dc_ref, sc) <= TOL_VJP_MIXED
+    assert torch.equal(mesh.build_K(Xd, cd, "mixed"), before)
