@@ -1,0 +1,313 @@
+// groups.cu -- plans built per patch group under the memory budget (Eq. 10):
+// the numeric calls run the groups one after the other, each group's closure
+// either built for the call (closure_range) or copied back from its page-locked
+// host copy (fem_options.group_cache) into one of two reusable device slots,
+// the next group's copy overlapping the current group's run.
+#include <algorithm>
+#include <functional>
+#include <vector>
+
+#include "mesh.cuh"
+#include "numeric.cuh"
+
+namespace fem {
+
+// A page-locked host copy of a built closure (the group cache).  Returns false
+// (and leaves `h` empty) if the host memory cannot be had.
+static bool closure_to_host(fem_mesh m, const Closure &cl, HostClosure &h, cudaStream_t s) {
+    const int64_t np_ = cl.p1 - cl.p0;
+    h.p0 = cl.p0, h.p1 = cl.p1, h.total_cnodes = cl.total_cnodes, h.total_celems = cl.total_celems;
+    h.max_cnodes = cl.max_cnodes, h.max_celems = cl.max_celems, h.n_colors = cl.n_colors;
+    h.has_pos = cl.celem_pos.ptr != nullptr;
+    h.n_pep = h.n_pcp = (size_t)np_ + 1;
+    h.n_gid = h.n_own = (size_t)cl.total_cnodes;
+    h.n_id = h.n_col = (size_t)cl.total_celems;
+    h.n_pos = h.has_pos ? cl.celem_pos.n : 0;
+    h.n_ln = cl.celem_lnode.n;
+    h.n_aidx = cl.celem_aidx.n;
+    size_t o = 0;
+    auto take = [&](size_t &off, size_t bytes) { off = o; o += (bytes + 255) & ~(size_t)255; };
+    take(h.o_pep, h.n_pep * 8);
+    take(h.o_pcp, h.n_pcp * 8);
+    take(h.o_gid, h.n_gid * 4);
+    take(h.o_own, h.n_own * 4);
+    take(h.o_id, h.n_id * 4);
+    take(h.o_col, h.n_col);
+    take(h.o_pos, h.n_pos);
+    take(h.o_ln, h.n_ln * 2);
+    take(h.o_aidx, h.n_aidx * 4);
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, o, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    h.host = static_cast<unsigned char *>(p);
+    h.bytes = o;
+    auto down = [&](size_t off, const void *src, size_t bytes) {
+        return bytes == 0 || cudaMemcpyAsync(h.host + off, src, bytes, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    };
+    bool ok = down(h.o_pep, cl.patch_elem_ptr.ptr, h.n_pep * 8) && down(h.o_pcp, cl.patch_cnode_ptr.ptr, h.n_pcp * 8) &&
+              down(h.o_gid, cl.cnode_gid.ptr, h.n_gid * 4) && down(h.o_own, cl.cnode_own.ptr, h.n_own * 4) &&
+              down(h.o_id, cl.celem_id.ptr, h.n_id * 4) && down(h.o_col, cl.celem_color.ptr, h.n_col) &&
+              down(h.o_pos, cl.celem_pos.ptr, h.n_pos) && down(h.o_ln, cl.celem_lnode.ptr, h.n_ln * 2) &&
+              down(h.o_aidx, cl.celem_aidx.ptr, h.n_aidx * 4);
+    ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        h.release();
+    }
+    (void)m;
+    return ok;
+}
+
+// The closure of a host copy, back in device memory (under the budget).
+static fem_status closure_from_host(fem_mesh m, const HostClosure &h, Closure &cl, cudaStream_t s) {
+    Arena &ar = m->arena;
+    cl.p0 = h.p0, cl.p1 = h.p1, cl.total_cnodes = h.total_cnodes, cl.total_celems = h.total_celems;
+    cl.max_cnodes = h.max_cnodes, cl.max_celems = h.max_celems, cl.n_colors = h.n_colors;
+    FEM_TRY(cl.patch_elem_ptr.alloc(ar, h.n_pep, "patch elem ptr"));
+    FEM_TRY(cl.patch_cnode_ptr.alloc(ar, h.n_pcp, "patch cnode ptr"));
+    FEM_TRY(cl.cnode_gid.alloc(ar, h.n_gid, "cnode gid"));
+    FEM_TRY(cl.cnode_own.alloc(ar, h.n_own, "cnode own"));
+    FEM_TRY(cl.celem_id.alloc(ar, h.n_id, "celem id"));
+    FEM_TRY(cl.celem_color.alloc(ar, h.n_col, "celem colour"));
+    if (h.has_pos) FEM_TRY(cl.celem_pos.alloc(ar, h.n_pos, "celem positions"));
+    FEM_TRY(cl.celem_lnode.alloc(ar, h.n_ln, "celem local nodes"));
+    FEM_TRY(cl.celem_aidx.alloc(ar, h.n_aidx, "celem accumulator targets"));
+    auto up = [&](void *dst, size_t off, size_t bytes) -> fem_status {
+        if (bytes) FEM_CUDA(cudaMemcpyAsync(dst, h.host + off, bytes, cudaMemcpyHostToDevice, s));
+        return FEM_OK;
+    };
+    FEM_TRY(up(cl.patch_elem_ptr.ptr, h.o_pep, h.n_pep * 8));
+    FEM_TRY(up(cl.patch_cnode_ptr.ptr, h.o_pcp, h.n_pcp * 8));
+    FEM_TRY(up(cl.cnode_gid.ptr, h.o_gid, h.n_gid * 4));
+    FEM_TRY(up(cl.cnode_own.ptr, h.o_own, h.n_own * 4));
+    FEM_TRY(up(cl.celem_id.ptr, h.o_id, h.n_id * 4));
+    FEM_TRY(up(cl.celem_color.ptr, h.o_col, h.n_col));
+    if (h.has_pos) FEM_TRY(up(cl.celem_pos.ptr, h.o_pos, h.n_pos));
+    FEM_TRY(up(cl.celem_lnode.ptr, h.o_ln, h.n_ln * 2));
+    FEM_TRY(up(cl.celem_aidx.ptr, h.o_aidx, h.n_aidx * 4));
+    return FEM_OK;
+}
+
+// Builds the closure of patches [p0, p1) (halving the range while the budget
+// refuses it), runs fn on it and frees it; with `rec`, a host copy of every
+// closure built is appended to it (cleared if host memory runs out).
+static fem_status closure_range(fem_mesh m, int64_t p0, int64_t p1, cudaStream_t s,
+                                const std::function<fem_status(const Closure &)> &fn, int *groups,
+                                std::vector<HostClosure> *rec = nullptr, bool *rec_ok = nullptr) {
+    Closure cl;
+    fem_status st = build_closure(m, p0, p1, cl, s);
+    if (st == FEM_ERR_BUDGET && p1 - p0 > 1) {
+        cl.reset();
+        cudaGetLastError();
+        const int64_t mid = p0 + (p1 - p0) / 2;
+        FEM_TRY(closure_range(m, p0, mid, s, fn, groups, rec, rec_ok));
+        return closure_range(m, mid, p1, s, fn, groups, rec, rec_ok);
+    }
+    FEM_TRY(st);
+    ++*groups;
+    FEM_TRY(fn(cl));
+    if (rec && *rec_ok) {
+        HostClosure h;
+        if (closure_to_host(m, cl, h, s)) rec->push_back(std::move(h));
+        else *rec_ok = false;
+    }
+    FEM_CUDA(cudaStreamSynchronize(s));  // the closure's buffers are freed on return
+    return FEM_OK;
+}
+
+// Device buffers that hold one cached group's closure at a time (sized for the
+// largest group), reused from group to group without freeing in between.
+struct ClosureSlot {
+    DevBuf<int64_t> pep, pcp;
+    DevBuf<int32_t> gid, own, id;
+    DevBuf<uint8_t> col, pos;
+    DevBuf<uint16_t> ln;
+    DevBuf<uint32_t> aidx;
+    fem_status alloc(Arena &ar, const std::vector<HostClosure> &hs) {
+        size_t n[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
+        for (const HostClosure &h : hs) {
+            const size_t v[9] = {h.n_pep, h.n_pcp, h.n_gid, h.n_own, h.n_id, h.n_col, h.n_pos, h.n_ln, h.n_aidx};
+            for (int k = 0; k < 9; ++k) n[k] = std::max(n[k], v[k]);
+        }
+        FEM_TRY(pep.alloc(ar, n[0], "group slot"));
+        FEM_TRY(pcp.alloc(ar, n[1], "group slot"));
+        FEM_TRY(gid.alloc(ar, n[2], "group slot"));
+        FEM_TRY(own.alloc(ar, n[3], "group slot"));
+        FEM_TRY(id.alloc(ar, n[4], "group slot"));
+        FEM_TRY(col.alloc(ar, n[5], "group slot"));
+        FEM_TRY(pos.alloc(ar, n[6], "group slot"));
+        FEM_TRY(ln.alloc(ar, n[7], "group slot"));
+        FEM_TRY(aidx.alloc(ar, n[8], "group slot"));
+        return FEM_OK;
+    }
+    // copies host closure h into the slot on stream s
+    fem_status upload(const HostClosure &h, cudaStream_t s) {
+        auto up = [&](void *dst, size_t off, size_t bytes) -> fem_status {
+            if (bytes) FEM_CUDA(cudaMemcpyAsync(dst, h.host + off, bytes, cudaMemcpyHostToDevice, s));
+            return FEM_OK;
+        };
+        FEM_TRY(up(pep.ptr, h.o_pep, h.n_pep * 8));
+        FEM_TRY(up(pcp.ptr, h.o_pcp, h.n_pcp * 8));
+        FEM_TRY(up(gid.ptr, h.o_gid, h.n_gid * 4));
+        FEM_TRY(up(own.ptr, h.o_own, h.n_own * 4));
+        FEM_TRY(up(id.ptr, h.o_id, h.n_id * 4));
+        FEM_TRY(up(col.ptr, h.o_col, h.n_col));
+        FEM_TRY(up(pos.ptr, h.o_pos, h.n_pos));
+        FEM_TRY(up(ln.ptr, h.o_ln, h.n_ln * 2));
+        FEM_TRY(up(aidx.ptr, h.o_aidx, h.n_aidx * 4));
+        return FEM_OK;
+    }
+    // a closure that borrows the slot's buffers for host closure h (frees nothing)
+    void view(const HostClosure &h, Closure &cl) const {
+        cl.p0 = h.p0, cl.p1 = h.p1, cl.total_cnodes = h.total_cnodes, cl.total_celems = h.total_celems;
+        cl.max_cnodes = h.max_cnodes, cl.max_celems = h.max_celems, cl.n_colors = h.n_colors;
+        auto lend = [](auto &d, auto *ptr, size_t n) {
+            d.ptr = ptr;
+            d.n = n;
+            d.arena = nullptr;
+        };
+        lend(cl.patch_elem_ptr, pep.ptr, h.n_pep);
+        lend(cl.patch_cnode_ptr, pcp.ptr, h.n_pcp);
+        lend(cl.cnode_gid, gid.ptr, h.n_gid);
+        lend(cl.cnode_own, own.ptr, h.n_own);
+        lend(cl.celem_id, id.ptr, h.n_id);
+        lend(cl.celem_color, col.ptr, h.n_col);
+        lend(cl.celem_pos, h.has_pos ? pos.ptr : nullptr, h.n_pos);
+        lend(cl.celem_lnode, ln.ptr, h.n_ln);
+        lend(cl.celem_aidx, aidx.ptr, h.n_aidx);
+    }
+};
+
+// The cached groups, copied back one after the other into slots.  With two slots
+// (when the budget holds them) group i + 1 is copied in on a second stream while
+// group i runs; with one, copies and runs alternate on the caller's stream.
+static fem_status run_cached_groups(fem_mesh m, cudaStream_t s,
+                                    const std::function<fem_status(const Closure &)> &fn, bool *done) {
+    *done = false;
+    const std::vector<HostClosure> &hs = m->group_cache;
+    const int n = (int)hs.size();
+    ClosureSlot slot[2];
+    if (slot[0].alloc(m->arena, hs) != FEM_OK) {
+        cudaGetLastError();
+        return FEM_OK;  // not even one slot: the caller copies or builds group by group
+    }
+    int nslots = 2;
+    if (n < 2 || slot[1].alloc(m->arena, hs) != FEM_OK) {
+        cudaGetLastError();
+        nslots = 1;
+    }
+    if (nslots == 2 && !m->copy_stream) FEM_CUDA(cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking));
+    cudaEvent_t up[2] = {}, fin[2] = {};
+    auto cleanup = [&] {
+        for (int k = 0; k < 2; ++k) {
+            if (up[k]) cudaEventDestroy(up[k]);
+            if (fin[k]) cudaEventDestroy(fin[k]);
+        }
+    };
+    fem_status st = FEM_OK;
+    for (int k = 0; k < nslots && st == FEM_OK; ++k) {
+        if (cudaEventCreateWithFlags(&up[k], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&fin[k], cudaEventDisableTiming) != cudaSuccess)
+            st = cuda_status(cudaGetLastError(), "group slot events");
+    }
+    // the caller's stream may still be writing what the copies must not overtake
+    if (st == FEM_OK && nslots == 2 && cudaEventRecord(fin[1], s) != cudaSuccess)
+        st = cuda_status(cudaGetLastError(), "group slot events");
+    auto copy_in = [&](int i) -> fem_status {
+        const int k = i % nslots;
+        if (nslots == 1) return slot[0].upload(hs[i], s);
+        FEM_CUDA(cudaStreamWaitEvent(m->copy_stream, fin[k], 0));  // the slot's previous group has run
+        FEM_TRY(slot[k].upload(hs[i], m->copy_stream));
+        FEM_CUDA(cudaEventRecord(up[k], m->copy_stream));
+        return FEM_OK;
+    };
+    if (st == FEM_OK) {
+        if (nslots == 2) FEM_CUDA(cudaEventRecord(fin[0], s));
+        st = copy_in(0);
+    }
+    for (int i = 0; i < n && st == FEM_OK; ++i) {
+        const int k = i % nslots;
+        if (nslots == 2 && i + 1 < n) st = copy_in(i + 1);
+        if (st != FEM_OK) break;
+        if (nslots == 2 && cudaStreamWaitEvent(s, up[k], 0) != cudaSuccess) {
+            st = cuda_status(cudaGetLastError(), "group slot wait");
+            break;
+        }
+        Closure cl;
+        slot[k].view(hs[i], cl);
+        st = fn(cl);
+        if (st != FEM_OK) break;
+        if (nslots == 2 && cudaEventRecord(fin[k], s) != cudaSuccess) st = cuda_status(cudaGetLastError(), "group slot");
+        if (nslots == 1 && i + 1 < n && st == FEM_OK) st = copy_in(i + 1);
+    }
+    // the slots are freed on return: everything that reads them must be done
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (st == FEM_OK && e != cudaSuccess) st = cuda_status(e, "group slots");
+    if (nslots == 2) cudaStreamSynchronize(m->copy_stream);
+    cleanup();
+    if (st == FEM_OK) {
+        m->n_groups = n;
+        *done = true;
+    }
+    return st;
+}
+
+fem_status for_each_group(fem_mesh m, cudaStream_t s, const std::function<fem_status(const Closure &)> &fn) {
+    Plan &P = m->plan;
+    if (!P.chunked) return fn(P.full);
+    int groups = 0;
+    const bool use_cache = m->opt.group_cache != 0;
+    if (use_cache && !m->group_cache.empty() && m->group_cache_pos == m->want_pos) {
+        bool done = false;
+        FEM_TRY(run_cached_groups(m, s, fn, &done));
+        if (done) return FEM_OK;
+        // no slot fits beside what the call holds now: each group's copy in turn,
+        // or its closure built in smaller parts where even that copy does not fit
+        for (const HostClosure &h : m->group_cache) {
+            Closure cl;
+            fem_status st = closure_from_host(m, h, cl, s);
+            if (st == FEM_ERR_BUDGET) {
+                cl.reset();
+                cudaGetLastError();
+                FEM_CUDA(cudaStreamSynchronize(s));
+                FEM_TRY(closure_range(m, h.p0, h.p1, s, fn, &groups));
+                continue;
+            }
+            FEM_TRY(st);
+            ++groups;
+            FEM_TRY(fn(cl));
+            FEM_CUDA(cudaStreamSynchronize(s));  // the closure's buffers are freed on return
+        }
+        m->n_groups = groups;
+        return FEM_OK;
+    }
+    // Building the groups (and, with the cache, their host copies): with the cache,
+    // groups of half the size, so that two of them fit where one did and the
+    // copy of one can overlap the run of the other.
+    std::vector<HostClosure> rec;
+    bool rec_ok = use_cache;
+    const int64_t G = use_cache ? std::max<int64_t>(1, m->group_patches / 2) : m->group_patches;
+    for (int64_t p0 = 0; p0 < P.n_patches; p0 += G)
+        FEM_TRY(closure_range(m, p0, std::min(P.n_patches, p0 + G), s, fn, &groups, use_cache ? &rec : nullptr,
+                              &rec_ok));
+    m->n_groups = groups;
+    if (use_cache && rec_ok) {
+        m->group_cache = std::move(rec);
+        m->group_cache_pos = m->want_pos;
+    }
+    return FEM_OK;
+}
+
+fem_status for_each_group_in(fem_mesh m, int64_t pa, int64_t pb, cudaStream_t s,
+                             const std::function<fem_status(const Closure &)> &fn) {
+    Plan &P = m->plan;
+    if (!P.chunked) return fn(P.full);
+    int groups = 0;
+    for (int64_t p0 = pa; p0 < pb; p0 += m->group_patches)
+        FEM_TRY(closure_range(m, p0, std::min(pb, p0 + m->group_patches), s, fn, &groups));
+    return FEM_OK;
+}
+
+}  // namespace fem
