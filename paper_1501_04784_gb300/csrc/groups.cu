@@ -3,6 +3,11 @@
 // either built for the call (closure_range) or copied back from its page-locked
 // host copy (fem_options.group_cache) into one of two reusable device slots,
 // the next group's copy overlapping the current group's run.
+//
+// A host copy holds a closure's element ids, colours, closure-local node indices,
+// in-row positions and closure nodes; the accumulator targets (twice the bytes
+// of the positions) are derived from the positions on the device after the copy
+// (k_expand_targets), exactly as the closure fill derives them.
 #include <algorithm>
 #include <functional>
 #include <vector>
@@ -12,19 +17,91 @@
 
 namespace fem {
 
-// A page-locked host copy of a built closure (the group cache).  Returns false
-// (and leaves `h` empty) if the host memory cannot be had.
-static bool closure_to_host(fem_mesh m, const Closure &cl, HostClosure &h, cudaStream_t s) {
+// Accumulator targets of a closure's packed pairs from its in-row positions: the
+// targets k_celem_fill writes (see PlanView::celem_aidx).  One block per patch of
+// the closure.  The pair's row is its node with the larger global id, i.e. the
+// larger closure-local index (closure nodes ascend with the id); an owned row's
+// entry is its offset in the patch's accumulators plus the position; a pair whose
+// row the patch does not own goes to the scratch slot of the lane that will hold
+// the element; an FP64-accurate diagonal is AIDX_HV | owned-row index.
+template <int NPE>
+__global__ void __launch_bounds__(256) k_expand_targets(int64_t np_, const int64_t *__restrict__ pe_ptr,
+                                                        const int64_t *__restrict__ pc_ptr,
+                                                        const uint16_t *__restrict__ lnode,
+                                                        const uint8_t *__restrict__ pos, int pos_stride,
+                                                        const int32_t *__restrict__ cnode_own,
+                                                        const int64_t *__restrict__ patch_node_ptr,
+                                                        const int32_t *__restrict__ own_acc,
+                                                        const uint8_t *__restrict__ own_hv, int trash,
+                                                        int64_t nce, uint32_t *__restrict__ aidx) {
+    constexpr int NP = NPE * (NPE + 1) / 2;
+    for (int64_t pb = blockIdx.x; pb < np_; pb += gridDim.x) {
+        const int64_t e0 = pe_ptr[pb], e1 = pe_ptr[pb + 1], cb = pc_ptr[pb];
+        const int64_t nb = patch_node_ptr[pb];
+        for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
+            int ln[NPE], own[NPE], base[NPE];
+            bool hv[NPE];
+#pragma unroll
+            for (int a = 0; a < NPE; ++a) {
+                ln[a] = lnode[i * NPE + a];
+                own[a] = cnode_own[cb + ln[a]];
+                base[a] = own[a] >= 0 ? own_acc[nb + own[a]] : 0;
+                hv[a] = own[a] >= 0 && own_hv[nb + own[a]] != 0;
+            }
+            const uint8_t *pp = pos + i * pos_stride;
+            const uint32_t scratch = (uint32_t)(trash + ((i - e0) & 31));
+            uint32_t lo = 0;
+            int q = 0;
+#pragma unroll
+            for (int a = 0; a < NPE; ++a)
+#pragma unroll
+                for (int b = 0; b <= a; ++b, ++q) {
+                    const int r = ln[a] > ln[b] ? a : b;
+                    uint32_t t = scratch;
+                    if (own[r] >= 0) {
+                        if (a == b && hv[a]) t = AIDX_HV | (uint32_t)own[a];
+                        else t = (uint32_t)(base[r] + pp[q]);
+                    }
+                    if (q & 1) aidx[(int64_t)(q >> 1) * nce + i] = lo | ((t & 0xffffu) << 16);
+                    else lo = t & 0xffffu;
+                }
+            static_assert(NP % 2 == 0, "targets pair up into words");
+        }
+    }
+}
+
+// The targets of a closure whose positions (and everything else) are in place.
+static fem_status expand_targets(fem_mesh m, const Closure &cl, uint32_t *aidx, cudaStream_t s) {
+    const Plan &P = m->plan;
+    const int64_t np_ = cl.p1 - cl.p0;
+    if (np_ <= 0 || cl.total_celems == 0) return FEM_OK;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(np_, (int64_t)num_sms() * 8));
+#define FEM_EXPAND(NPE)                                                                                            \
+    k_expand_targets<NPE><<<grid, 256, 0, s>>>(np_, cl.patch_elem_ptr.ptr, cl.patch_cnode_ptr.ptr,                \
+                                               cl.celem_lnode.ptr, cl.celem_pos.ptr, P.pos_stride, cl.cnode_own.ptr, \
+                                               P.patch_node_ptr.ptr + cl.p0, P.own_acc.ptr, P.own_hv.ptr,          \
+                                               (int)P.max_acc, cl.total_celems, aidx)
+    if (m->npe == 8) FEM_EXPAND(8);
+    else FEM_EXPAND(4);
+#undef FEM_EXPAND
+    FEM_LAUNCHED("k_expand_targets");
+    return FEM_OK;
+}
+
+// A page-locked host copy of a built closure (which carries its positions).
+// Returns false (and leaves `h` empty) if the host memory cannot be had.
+static bool closure_to_host(const Closure &cl, HostClosure &h, cudaStream_t s) {
     const int64_t np_ = cl.p1 - cl.p0;
     h.p0 = cl.p0, h.p1 = cl.p1, h.total_cnodes = cl.total_cnodes, h.total_celems = cl.total_celems;
     h.max_cnodes = cl.max_cnodes, h.max_celems = cl.max_celems, h.n_colors = cl.n_colors;
-    h.has_pos = cl.celem_pos.ptr != nullptr;
     h.n_pep = h.n_pcp = (size_t)np_ + 1;
     h.n_gid = h.n_own = (size_t)cl.total_cnodes;
     h.n_id = h.n_col = (size_t)cl.total_celems;
-    h.n_pos = h.has_pos ? cl.celem_pos.n : 0;
+    h.n_pos = cl.celem_pos.n;
     h.n_ln = cl.celem_lnode.n;
-    h.n_aidx = cl.celem_aidx.n;
+    h.n_aidx = cl.celem_aidx.n;  // derived on the device, not copied
+    h.o_aidx = 0;
+    if (!cl.celem_pos.ptr) return false;
     size_t o = 0;
     auto take = [&](size_t &off, size_t bytes) { off = o; o += (bytes + 255) & ~(size_t)255; };
     take(h.o_pep, h.n_pep * 8);
@@ -35,7 +112,6 @@ static bool closure_to_host(fem_mesh m, const Closure &cl, HostClosure &h, cudaS
     take(h.o_col, h.n_col);
     take(h.o_pos, h.n_pos);
     take(h.o_ln, h.n_ln * 2);
-    take(h.o_aidx, h.n_aidx * 4);
     void *p = nullptr;
     if (cudaHostAlloc(&p, o, cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
@@ -49,72 +125,13 @@ static bool closure_to_host(fem_mesh m, const Closure &cl, HostClosure &h, cudaS
     bool ok = down(h.o_pep, cl.patch_elem_ptr.ptr, h.n_pep * 8) && down(h.o_pcp, cl.patch_cnode_ptr.ptr, h.n_pcp * 8) &&
               down(h.o_gid, cl.cnode_gid.ptr, h.n_gid * 4) && down(h.o_own, cl.cnode_own.ptr, h.n_own * 4) &&
               down(h.o_id, cl.celem_id.ptr, h.n_id * 4) && down(h.o_col, cl.celem_color.ptr, h.n_col) &&
-              down(h.o_pos, cl.celem_pos.ptr, h.n_pos) && down(h.o_ln, cl.celem_lnode.ptr, h.n_ln * 2) &&
-              down(h.o_aidx, cl.celem_aidx.ptr, h.n_aidx * 4);
+              down(h.o_pos, cl.celem_pos.ptr, h.n_pos) && down(h.o_ln, cl.celem_lnode.ptr, h.n_ln * 2);
     ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         h.release();
     }
-    (void)m;
     return ok;
-}
-
-// The closure of a host copy, back in device memory (under the budget).
-static fem_status closure_from_host(fem_mesh m, const HostClosure &h, Closure &cl, cudaStream_t s) {
-    Arena &ar = m->arena;
-    cl.p0 = h.p0, cl.p1 = h.p1, cl.total_cnodes = h.total_cnodes, cl.total_celems = h.total_celems;
-    cl.max_cnodes = h.max_cnodes, cl.max_celems = h.max_celems, cl.n_colors = h.n_colors;
-    FEM_TRY(cl.patch_elem_ptr.alloc(ar, h.n_pep, "patch elem ptr"));
-    FEM_TRY(cl.patch_cnode_ptr.alloc(ar, h.n_pcp, "patch cnode ptr"));
-    FEM_TRY(cl.cnode_gid.alloc(ar, h.n_gid, "cnode gid"));
-    FEM_TRY(cl.cnode_own.alloc(ar, h.n_own, "cnode own"));
-    FEM_TRY(cl.celem_id.alloc(ar, h.n_id, "celem id"));
-    FEM_TRY(cl.celem_color.alloc(ar, h.n_col, "celem colour"));
-    if (h.has_pos) FEM_TRY(cl.celem_pos.alloc(ar, h.n_pos, "celem positions"));
-    FEM_TRY(cl.celem_lnode.alloc(ar, h.n_ln, "celem local nodes"));
-    FEM_TRY(cl.celem_aidx.alloc(ar, h.n_aidx, "celem accumulator targets"));
-    auto up = [&](void *dst, size_t off, size_t bytes) -> fem_status {
-        if (bytes) FEM_CUDA(cudaMemcpyAsync(dst, h.host + off, bytes, cudaMemcpyHostToDevice, s));
-        return FEM_OK;
-    };
-    FEM_TRY(up(cl.patch_elem_ptr.ptr, h.o_pep, h.n_pep * 8));
-    FEM_TRY(up(cl.patch_cnode_ptr.ptr, h.o_pcp, h.n_pcp * 8));
-    FEM_TRY(up(cl.cnode_gid.ptr, h.o_gid, h.n_gid * 4));
-    FEM_TRY(up(cl.cnode_own.ptr, h.o_own, h.n_own * 4));
-    FEM_TRY(up(cl.celem_id.ptr, h.o_id, h.n_id * 4));
-    FEM_TRY(up(cl.celem_color.ptr, h.o_col, h.n_col));
-    if (h.has_pos) FEM_TRY(up(cl.celem_pos.ptr, h.o_pos, h.n_pos));
-    FEM_TRY(up(cl.celem_lnode.ptr, h.o_ln, h.n_ln * 2));
-    FEM_TRY(up(cl.celem_aidx.ptr, h.o_aidx, h.n_aidx * 4));
-    return FEM_OK;
-}
-
-// Builds the closure of patches [p0, p1) (halving the range while the budget
-// refuses it), runs fn on it and frees it; with `rec`, a host copy of every
-// closure built is appended to it (cleared if host memory runs out).
-static fem_status closure_range(fem_mesh m, int64_t p0, int64_t p1, cudaStream_t s,
-                                const std::function<fem_status(const Closure &)> &fn, int *groups,
-                                std::vector<HostClosure> *rec = nullptr, bool *rec_ok = nullptr) {
-    Closure cl;
-    fem_status st = build_closure(m, p0, p1, cl, s);
-    if (st == FEM_ERR_BUDGET && p1 - p0 > 1) {
-        cl.reset();
-        cudaGetLastError();
-        const int64_t mid = p0 + (p1 - p0) / 2;
-        FEM_TRY(closure_range(m, p0, mid, s, fn, groups, rec, rec_ok));
-        return closure_range(m, mid, p1, s, fn, groups, rec, rec_ok);
-    }
-    FEM_TRY(st);
-    ++*groups;
-    FEM_TRY(fn(cl));
-    if (rec && *rec_ok) {
-        HostClosure h;
-        if (closure_to_host(m, cl, h, s)) rec->push_back(std::move(h));
-        else *rec_ok = false;
-    }
-    FEM_CUDA(cudaStreamSynchronize(s));  // the closure's buffers are freed on return
-    return FEM_OK;
 }
 
 // Device buffers that hold one cached group's closure at a time (sized for the
@@ -142,23 +159,6 @@ struct ClosureSlot {
         FEM_TRY(aidx.alloc(ar, n[8], "group slot"));
         return FEM_OK;
     }
-    // copies host closure h into the slot on stream s
-    fem_status upload(const HostClosure &h, cudaStream_t s) {
-        auto up = [&](void *dst, size_t off, size_t bytes) -> fem_status {
-            if (bytes) FEM_CUDA(cudaMemcpyAsync(dst, h.host + off, bytes, cudaMemcpyHostToDevice, s));
-            return FEM_OK;
-        };
-        FEM_TRY(up(pep.ptr, h.o_pep, h.n_pep * 8));
-        FEM_TRY(up(pcp.ptr, h.o_pcp, h.n_pcp * 8));
-        FEM_TRY(up(gid.ptr, h.o_gid, h.n_gid * 4));
-        FEM_TRY(up(own.ptr, h.o_own, h.n_own * 4));
-        FEM_TRY(up(id.ptr, h.o_id, h.n_id * 4));
-        FEM_TRY(up(col.ptr, h.o_col, h.n_col));
-        FEM_TRY(up(pos.ptr, h.o_pos, h.n_pos));
-        FEM_TRY(up(ln.ptr, h.o_ln, h.n_ln * 2));
-        FEM_TRY(up(aidx.ptr, h.o_aidx, h.n_aidx * 4));
-        return FEM_OK;
-    }
     // a closure that borrows the slot's buffers for host closure h (frees nothing)
     void view(const HostClosure &h, Closure &cl) const {
         cl.p0 = h.p0, cl.p1 = h.p1, cl.total_cnodes = h.total_cnodes, cl.total_celems = h.total_celems;
@@ -174,15 +174,62 @@ struct ClosureSlot {
         lend(cl.cnode_own, own.ptr, h.n_own);
         lend(cl.celem_id, id.ptr, h.n_id);
         lend(cl.celem_color, col.ptr, h.n_col);
-        lend(cl.celem_pos, h.has_pos ? pos.ptr : nullptr, h.n_pos);
+        lend(cl.celem_pos, pos.ptr, h.n_pos);
         lend(cl.celem_lnode, ln.ptr, h.n_ln);
         lend(cl.celem_aidx, aidx.ptr, h.n_aidx);
     }
+    // copies host closure h into the slot on stream s, then derives its targets
+    fem_status upload(fem_mesh m, const HostClosure &h, cudaStream_t s) {
+        auto up = [&](void *dst, size_t off, size_t bytes) -> fem_status {
+            if (bytes) FEM_CUDA(cudaMemcpyAsync(dst, h.host + off, bytes, cudaMemcpyHostToDevice, s));
+            return FEM_OK;
+        };
+        FEM_TRY(up(pep.ptr, h.o_pep, h.n_pep * 8));
+        FEM_TRY(up(pcp.ptr, h.o_pcp, h.n_pcp * 8));
+        FEM_TRY(up(gid.ptr, h.o_gid, h.n_gid * 4));
+        FEM_TRY(up(own.ptr, h.o_own, h.n_own * 4));
+        FEM_TRY(up(id.ptr, h.o_id, h.n_id * 4));
+        FEM_TRY(up(col.ptr, h.o_col, h.n_col));
+        FEM_TRY(up(pos.ptr, h.o_pos, h.n_pos));
+        FEM_TRY(up(ln.ptr, h.o_ln, h.n_ln * 2));
+        Closure cl;
+        view(h, cl);
+        return expand_targets(m, cl, aidx.ptr, s);
+    }
 };
 
+// Builds the closure of patches [p0, p1) (halving the range while the budget
+// refuses it), runs fn on it and frees it; with `rec`, the closures are built
+// with their positions and a host copy of each is appended to rec (rec_ok is
+// cleared if host memory runs out).
+static fem_status closure_range(fem_mesh m, int64_t p0, int64_t p1, cudaStream_t s,
+                                const std::function<fem_status(const Closure &)> &fn, int *groups,
+                                std::vector<HostClosure> *rec = nullptr, bool *rec_ok = nullptr) {
+    Closure cl;
+    fem_status st = build_closure(m, p0, p1, cl, s, m->want_pos || rec != nullptr);
+    if (st == FEM_ERR_BUDGET && p1 - p0 > 1) {
+        cl.reset();
+        cudaGetLastError();
+        const int64_t mid = p0 + (p1 - p0) / 2;
+        FEM_TRY(closure_range(m, p0, mid, s, fn, groups, rec, rec_ok));
+        return closure_range(m, mid, p1, s, fn, groups, rec, rec_ok);
+    }
+    FEM_TRY(st);
+    ++*groups;
+    FEM_TRY(fn(cl));
+    if (rec && *rec_ok) {
+        HostClosure h;
+        if (closure_to_host(cl, h, s)) rec->push_back(std::move(h));
+        else *rec_ok = false;
+    }
+    FEM_CUDA(cudaStreamSynchronize(s));  // the closure's buffers are freed on return
+    return FEM_OK;
+}
+
 // The cached groups, copied back one after the other into slots.  With two slots
-// (when the budget holds them) group i + 1 is copied in on a second stream while
-// group i runs; with one, copies and runs alternate on the caller's stream.
+// (when the budget holds them) group i + 1 is copied in (and its targets
+// derived) on a second stream while group i runs; with one, copies and runs
+// alternate on the caller's stream.  *done stays false if not even one slot fits.
 static fem_status run_cached_groups(fem_mesh m, cudaStream_t s,
                                     const std::function<fem_status(const Closure &)> &fn, bool *done) {
     *done = false;
@@ -191,7 +238,7 @@ static fem_status run_cached_groups(fem_mesh m, cudaStream_t s,
     ClosureSlot slot[2];
     if (slot[0].alloc(m->arena, hs) != FEM_OK) {
         cudaGetLastError();
-        return FEM_OK;  // not even one slot: the caller copies or builds group by group
+        return FEM_OK;
     }
     int nslots = 2;
     if (n < 2 || slot[1].alloc(m->arena, hs) != FEM_OK) {
@@ -200,33 +247,25 @@ static fem_status run_cached_groups(fem_mesh m, cudaStream_t s,
     }
     if (nslots == 2 && !m->copy_stream) FEM_CUDA(cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking));
     cudaEvent_t up[2] = {}, fin[2] = {};
-    auto cleanup = [&] {
-        for (int k = 0; k < 2; ++k) {
-            if (up[k]) cudaEventDestroy(up[k]);
-            if (fin[k]) cudaEventDestroy(fin[k]);
-        }
-    };
     fem_status st = FEM_OK;
     for (int k = 0; k < nslots && st == FEM_OK; ++k) {
         if (cudaEventCreateWithFlags(&up[k], cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&fin[k], cudaEventDisableTiming) != cudaSuccess)
             st = cuda_status(cudaGetLastError(), "group slot events");
     }
-    // the caller's stream may still be writing what the copies must not overtake
-    if (st == FEM_OK && nslots == 2 && cudaEventRecord(fin[1], s) != cudaSuccess)
-        st = cuda_status(cudaGetLastError(), "group slot events");
+    // copies into a slot wait for the slot's previous group to have run (at the
+    // start: for whatever the caller's stream did with memory the slot reuses)
+    for (int k = 0; k < nslots && st == FEM_OK && nslots == 2; ++k)
+        if (cudaEventRecord(fin[k], s) != cudaSuccess) st = cuda_status(cudaGetLastError(), "group slot events");
     auto copy_in = [&](int i) -> fem_status {
         const int k = i % nslots;
-        if (nslots == 1) return slot[0].upload(hs[i], s);
-        FEM_CUDA(cudaStreamWaitEvent(m->copy_stream, fin[k], 0));  // the slot's previous group has run
-        FEM_TRY(slot[k].upload(hs[i], m->copy_stream));
+        if (nslots == 1) return slot[0].upload(m, hs[i], s);
+        FEM_CUDA(cudaStreamWaitEvent(m->copy_stream, fin[k], 0));
+        FEM_TRY(slot[k].upload(m, hs[i], m->copy_stream));
         FEM_CUDA(cudaEventRecord(up[k], m->copy_stream));
         return FEM_OK;
     };
-    if (st == FEM_OK) {
-        if (nslots == 2) FEM_CUDA(cudaEventRecord(fin[0], s));
-        st = copy_in(0);
-    }
+    if (st == FEM_OK) st = copy_in(0);
     for (int i = 0; i < n && st == FEM_OK; ++i) {
         const int k = i % nslots;
         if (nslots == 2 && i + 1 < n) st = copy_in(i + 1);
@@ -246,7 +285,10 @@ static fem_status run_cached_groups(fem_mesh m, cudaStream_t s,
     const cudaError_t e = cudaStreamSynchronize(s);
     if (st == FEM_OK && e != cudaSuccess) st = cuda_status(e, "group slots");
     if (nslots == 2) cudaStreamSynchronize(m->copy_stream);
-    cleanup();
+    for (int k = 0; k < 2; ++k) {
+        if (up[k]) cudaEventDestroy(up[k]);
+        if (fin[k]) cudaEventDestroy(fin[k]);
+    }
     if (st == FEM_OK) {
         m->n_groups = n;
         *done = true;
@@ -259,27 +301,13 @@ fem_status for_each_group(fem_mesh m, cudaStream_t s, const std::function<fem_st
     if (!P.chunked) return fn(P.full);
     int groups = 0;
     const bool use_cache = m->opt.group_cache != 0;
-    if (use_cache && !m->group_cache.empty() && m->group_cache_pos == m->want_pos) {
+    if (use_cache && !m->group_cache.empty()) {
         bool done = false;
         FEM_TRY(run_cached_groups(m, s, fn, &done));
         if (done) return FEM_OK;
-        // no slot fits beside what the call holds now: each group's copy in turn,
-        // or its closure built in smaller parts where even that copy does not fit
-        for (const HostClosure &h : m->group_cache) {
-            Closure cl;
-            fem_status st = closure_from_host(m, h, cl, s);
-            if (st == FEM_ERR_BUDGET) {
-                cl.reset();
-                cudaGetLastError();
-                FEM_CUDA(cudaStreamSynchronize(s));
-                FEM_TRY(closure_range(m, h.p0, h.p1, s, fn, &groups));
-                continue;
-            }
-            FEM_TRY(st);
-            ++groups;
-            FEM_TRY(fn(cl));
-            FEM_CUDA(cudaStreamSynchronize(s));  // the closure's buffers are freed on return
-        }
+        // no slot fits beside what the call holds now: each group's closure is
+        // built again, in smaller parts where it does not fit
+        for (const HostClosure &h : m->group_cache) FEM_TRY(closure_range(m, h.p0, h.p1, s, fn, &groups));
         m->n_groups = groups;
         return FEM_OK;
     }
@@ -293,10 +321,7 @@ fem_status for_each_group(fem_mesh m, cudaStream_t s, const std::function<fem_st
         FEM_TRY(closure_range(m, p0, std::min(P.n_patches, p0 + G), s, fn, &groups, use_cache ? &rec : nullptr,
                               &rec_ok));
     m->n_groups = groups;
-    if (use_cache && rec_ok) {
-        m->group_cache = std::move(rec);
-        m->group_cache_pos = m->want_pos;
-    }
+    if (use_cache && rec_ok) m->group_cache = std::move(rec);
     return FEM_OK;
 }
 

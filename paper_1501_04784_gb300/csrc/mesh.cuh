@@ -147,11 +147,12 @@ struct Plan {
 
 // A copy, in page-locked host memory, of one patch group's closure (plans built
 // per patch group under the memory budget): the numeric calls copy it back to the
-// device instead of building the closure again (fem_options.group_cache).
+// device instead of building the closure again (fem_options.group_cache).  The
+// copy holds the in-row positions instead of the accumulator targets (half their
+// bytes over the host link); the targets are derived from them on the device.
 struct HostClosure {
     int64_t p0 = 0, p1 = 0, total_cnodes = 0, total_celems = 0, max_cnodes = 0, max_celems = 0;
     int n_colors = 0;
-    bool has_pos = false;   // the in-row positions are part of the copy
     unsigned char *host = nullptr;
     size_t bytes = 0;
     // byte offsets of the arrays in `host` and their element counts
@@ -237,10 +238,8 @@ struct fem_mesh_s {
     cudaEvent_t chunk_built[2] = {}, slot_free[2] = {};
     int n_groups = 1;
     int64_t group_patches = 0;  // patches per group when the closures are built per group
-    // host copies of the patch groups' closures, in patch order (fem_options.group_cache);
-    // valid when non-empty and built with the current want_pos
+    // host copies of the patch groups' closures, in patch order (fem_options.group_cache)
     std::vector<fem::HostClosure> group_cache;
-    bool group_cache_pos = false;
 };
 
 namespace fem {
@@ -249,7 +248,8 @@ fem_status validate_connectivity(fem_mesh m, cudaStream_t s);
 void batch_forget(fem_mesh m);  // drops cached batched launches that use m's plan
 fem_status build_pattern(fem_mesh m, cudaStream_t s);
 fem_status build_plan(fem_mesh m, cudaStream_t s);
-fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaStream_t s);
+// with_pos: the closure carries the in-row positions (the backward pass, the host copies)
+fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaStream_t s, bool with_pos);
 // From now on the closures carry the in-row positions the backward pass reads.
 fem_status ensure_positions(fem_mesh m, cudaStream_t s);
 // Runs fn over the closure of every patch group (one group covering all patches

@@ -1180,7 +1180,7 @@ __global__ void __launch_bounds__(512) k_patch_color_order(const uint64_t *ckeys
     }
 }
 
-fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaStream_t s) {
+fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaStream_t s, bool with_pos) {
     Arena &ar = m->arena;
     Plan &P = m->plan;
     const int64_t npe = m->npe;
@@ -1425,7 +1425,7 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
     FEM_TRY(cl.celem_id.alloc(ar, nce, "celem id"));
     FEM_TRY(cl.celem_color.alloc(ar, nce, "celem colour"));
     FEM_TRY(cl.celem_lnode.alloc(ar, nce * npe, "celem local nodes"));
-    if (m->want_pos) FEM_TRY(cl.celem_pos.alloc(ar, nce * P.pos_stride, "celem positions"));
+    if (with_pos) FEM_TRY(cl.celem_pos.alloc(ar, nce * P.pos_stride, "celem positions"));
     FEM_TRY(cl.celem_aidx.alloc(ar, nce * (m->np / 2), "celem accumulator targets"));
     const OwnTables ot{P.node_patch.ptr,     P.own_idx.ptr, P.own_acc.ptr,          P.patch_node_ptr.ptr,
                        P.own_hv.ptr,         cl.patch_elem_ptr.ptr, p0, (int32_t)P.max_acc};
@@ -1445,13 +1445,13 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
             k_celem_fill<8><<<grid, TPB, smem, s>>>(ckeys.ptr, np_, m->E, cnkeys.ptr, cl.patch_cnode_ptr.ptr,
                                                     m->rowptr.ptr, m->col.ptr, P.pos_stride, ot, cl.celem_id.ptr,
                                                     cl.celem_color.ptr, cl.celem_lnode.ptr,
-                                                    m->want_pos ? cl.celem_pos.ptr : nullptr, aidx16);
+                                                    with_pos ? cl.celem_pos.ptr : nullptr, aidx16);
         } else {
             FEM_CUDA(cudaFuncSetAttribute(k_celem_fill<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_celem_fill<4><<<grid, TPB, smem, s>>>(ckeys.ptr, np_, m->E, cnkeys.ptr, cl.patch_cnode_ptr.ptr,
                                                     m->rowptr.ptr, m->col.ptr, P.pos_stride, ot, cl.celem_id.ptr,
                                                     cl.celem_color.ptr, cl.celem_lnode.ptr,
-                                                    m->want_pos ? cl.celem_pos.ptr : nullptr, aidx16);
+                                                    with_pos ? cl.celem_pos.ptr : nullptr, aidx16);
         }
         FEM_LAUNCHED("k_celem_fill");
     }
@@ -1466,8 +1466,7 @@ fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaSt
 fem_status ensure_positions(fem_mesh m, cudaStream_t s) {
     if (m->want_pos) return FEM_OK;
     m->want_pos = true;
-    m->group_cache.clear();  // copies without the positions
-    if (!m->plan_built || m->plan.chunked) return FEM_OK;
+    if (!m->plan_built || m->plan.chunked) return FEM_OK;  // group closures: built, or copied, with them
     Plan &P = m->plan;
     Closure &cl = P.full;
     const int64_t nce = cl.total_celems;
@@ -1507,7 +1506,8 @@ static fem_status plan_groups(fem_mesh m, cudaStream_t s) {
     int64_t G = std::max<int64_t>(1, P.n_patches / 2);
     for (;;) {
         Closure cl;
-        fem_status st = build_closure(m, 0, std::min(G, P.n_patches), cl, s);
+        // (with the host copies, the groups are recorded with their in-row positions)
+        fem_status st = build_closure(m, 0, std::min(G, P.n_patches), cl, s, m->want_pos || m->opt.group_cache);
         if (st == FEM_OK) break;
         cl.reset();
         cudaGetLastError();
@@ -1665,7 +1665,7 @@ static fem_status build_plan_cap(fem_mesh m, cudaStream_t s, int64_t cap_in) {
     }
 
     // closures of all patches, unless the budget refuses them
-    fem_status st = build_closure(m, 0, npatch, P.full, s);
+    fem_status st = build_closure(m, 0, npatch, P.full, s, m->want_pos);
     if (st == FEM_ERR_BUDGET) {
         P.full.reset();
         cudaGetLastError();
