@@ -153,12 +153,14 @@ typedef struct {
     int group_cache;             /* plans built per patch group (Eq. 10: the memory budget
                                     cannot hold every patch's closure at once): 1 (default) =
                                     each group's closure is built once and a copy kept in
-                                    page-locked host memory (about 93 bytes per closure
-                                    element, 129 once fem_vjp has run); later calls copy each
-                                    group back to the device, one at a time, instead of
-                                    building it again; 0 = build every group's closure at
-                                    every call (no host memory).  A group whose copy does not
-                                    fit beside the call's other buffers is built instead. */
+                                    page-locked host memory (about 57 bytes per closure
+                                    element); later calls copy the groups back to the device
+                                    in turn (the next group's copy overlapping the current
+                                    group's build when two fit the budget) instead of
+                                    building them again; 0 = build every group's closure at
+                                    every call (no host memory).  If not even one group's
+                                    copy fits beside the call's other buffers, the groups are
+                                    built instead. */
 } fem_options;
 
 /*
