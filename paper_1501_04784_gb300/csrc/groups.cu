@@ -100,7 +100,6 @@ static bool closure_to_host(const Closure &cl, HostClosure &h, cudaStream_t s) {
     h.n_pos = cl.celem_pos.n;
     h.n_ln = cl.celem_lnode.n;
     h.n_aidx = cl.celem_aidx.n;  // derived on the device, not copied
-    h.o_aidx = 0;
     if (!cl.celem_pos.ptr) return false;
     size_t o = 0;
     auto take = [&](size_t &off, size_t bytes) { off = o; o += (bytes + 255) & ~(size_t)255; };

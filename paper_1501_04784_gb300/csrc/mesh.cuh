@@ -155,8 +155,9 @@ struct HostClosure {
     int n_colors = 0;
     unsigned char *host = nullptr;
     size_t bytes = 0;
-    // byte offsets of the arrays in `host` and their element counts
-    size_t o_pep, o_pcp, o_gid, o_own, o_id, o_col, o_pos, o_ln, o_aidx;
+    // byte offsets of the arrays in `host` and their element counts (n_aidx: the
+    // target words the device derives, which the copy does not hold)
+    size_t o_pep, o_pcp, o_gid, o_own, o_id, o_col, o_pos, o_ln;
     size_t n_pep, n_pcp, n_gid, n_own, n_id, n_col, n_pos, n_ln, n_aidx;
     HostClosure() = default;
     HostClosure(const HostClosure &) = delete;
