@@ -133,69 +133,86 @@ static bool closure_to_host(const Closure &cl, HostClosure &h, cudaStream_t s) {
     return ok;
 }
 
-// Device buffers that hold one cached group's closure at a time (sized for the
-// largest group), reused from group to group without freeing in between.
-struct ClosureSlot {
-    DevBuf<int64_t> pep, pcp;
-    DevBuf<int32_t> gid, own, id;
-    DevBuf<uint8_t> col, pos;
-    DevBuf<uint16_t> ln;
-    DevBuf<uint32_t> aidx;
-    fem_status alloc(Arena &ar, const std::vector<HostClosure> &hs) {
-        size_t n[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
-        for (const HostClosure &h : hs) {
-            const size_t v[9] = {h.n_pep, h.n_pcp, h.n_gid, h.n_own, h.n_id, h.n_col, h.n_pos, h.n_ln, h.n_aidx};
-            for (int k = 0; k < 9; ++k) n[k] = std::max(n[k], v[k]);
-        }
-        FEM_TRY(pep.alloc(ar, n[0], "group slot"));
-        FEM_TRY(pcp.alloc(ar, n[1], "group slot"));
-        FEM_TRY(gid.alloc(ar, n[2], "group slot"));
-        FEM_TRY(own.alloc(ar, n[3], "group slot"));
-        FEM_TRY(id.alloc(ar, n[4], "group slot"));
-        FEM_TRY(col.alloc(ar, n[5], "group slot"));
-        FEM_TRY(pos.alloc(ar, n[6], "group slot"));
-        FEM_TRY(ln.alloc(ar, n[7], "group slot"));
-        FEM_TRY(aidx.alloc(ar, n[8], "group slot"));
+// ClosureSlot (mesh.cuh): device buffers that hold one cached group's closure at a
+// time, sized for the largest group, kept by the mesh between calls and reused
+// from group to group without freeing in between.
+static void group_sizes(const std::vector<HostClosure> &hs, size_t (&n)[9]) {
+    for (size_t &v : n) v = 1;
+    for (const HostClosure &h : hs) {
+        const size_t v[9] = {h.n_pep, h.n_pcp, h.n_gid, h.n_own, h.n_id, h.n_col, h.n_pos, h.n_ln, h.n_aidx};
+        for (int k = 0; k < 9; ++k) n[k] = std::max(n[k], v[k]);
+    }
+}
+
+bool ClosureSlot::fits(const std::vector<HostClosure> &hs) const {
+    size_t n[9];
+    group_sizes(hs, n);
+    return aidx.ptr && pep.n >= n[0] && pcp.n >= n[1] && gid.n >= n[2] && own.n >= n[3] && id.n >= n[4] &&
+           col.n >= n[5] && pos.n >= n[6] && ln.n >= n[7] && aidx.n >= n[8];
+}
+
+fem_status ClosureSlot::alloc(Arena &ar, const std::vector<HostClosure> &hs) {
+    release();
+    size_t n[9];
+    group_sizes(hs, n);
+    FEM_TRY(pep.alloc(ar, n[0], "group slot"));
+    FEM_TRY(pcp.alloc(ar, n[1], "group slot"));
+    FEM_TRY(gid.alloc(ar, n[2], "group slot"));
+    FEM_TRY(own.alloc(ar, n[3], "group slot"));
+    FEM_TRY(id.alloc(ar, n[4], "group slot"));
+    FEM_TRY(col.alloc(ar, n[5], "group slot"));
+    FEM_TRY(pos.alloc(ar, n[6], "group slot"));
+    FEM_TRY(ln.alloc(ar, n[7], "group slot"));
+    FEM_TRY(aidx.alloc(ar, n[8], "group slot"));
+    return FEM_OK;
+}
+
+void ClosureSlot::release() {
+    pep.free(); pcp.free(); gid.free(); own.free(); id.free(); col.free(); pos.free(); ln.free(); aidx.free();
+}
+
+void ClosureSlot::view(const HostClosure &h, Closure &cl) const {
+    cl.p0 = h.p0, cl.p1 = h.p1, cl.total_cnodes = h.total_cnodes, cl.total_celems = h.total_celems;
+    cl.max_cnodes = h.max_cnodes, cl.max_celems = h.max_celems, cl.n_colors = h.n_colors;
+    auto lend = [](auto &d, auto *ptr, size_t n) {
+        d.ptr = ptr;
+        d.n = n;
+        d.arena = nullptr;
+    };
+    lend(cl.patch_elem_ptr, pep.ptr, h.n_pep);
+    lend(cl.patch_cnode_ptr, pcp.ptr, h.n_pcp);
+    lend(cl.cnode_gid, gid.ptr, h.n_gid);
+    lend(cl.cnode_own, own.ptr, h.n_own);
+    lend(cl.celem_id, id.ptr, h.n_id);
+    lend(cl.celem_color, col.ptr, h.n_col);
+    lend(cl.celem_pos, pos.ptr, h.n_pos);
+    lend(cl.celem_lnode, ln.ptr, h.n_ln);
+    lend(cl.celem_aidx, aidx.ptr, h.n_aidx);
+}
+
+fem_status ClosureSlot::upload(fem_mesh m, const HostClosure &h, cudaStream_t s) {
+    auto up = [&](void *dst, size_t off, size_t bytes) -> fem_status {
+        if (bytes) FEM_CUDA(cudaMemcpyAsync(dst, h.host + off, bytes, cudaMemcpyHostToDevice, s));
         return FEM_OK;
-    }
-    // a closure that borrows the slot's buffers for host closure h (frees nothing)
-    void view(const HostClosure &h, Closure &cl) const {
-        cl.p0 = h.p0, cl.p1 = h.p1, cl.total_cnodes = h.total_cnodes, cl.total_celems = h.total_celems;
-        cl.max_cnodes = h.max_cnodes, cl.max_celems = h.max_celems, cl.n_colors = h.n_colors;
-        auto lend = [](auto &d, auto *ptr, size_t n) {
-            d.ptr = ptr;
-            d.n = n;
-            d.arena = nullptr;
-        };
-        lend(cl.patch_elem_ptr, pep.ptr, h.n_pep);
-        lend(cl.patch_cnode_ptr, pcp.ptr, h.n_pcp);
-        lend(cl.cnode_gid, gid.ptr, h.n_gid);
-        lend(cl.cnode_own, own.ptr, h.n_own);
-        lend(cl.celem_id, id.ptr, h.n_id);
-        lend(cl.celem_color, col.ptr, h.n_col);
-        lend(cl.celem_pos, pos.ptr, h.n_pos);
-        lend(cl.celem_lnode, ln.ptr, h.n_ln);
-        lend(cl.celem_aidx, aidx.ptr, h.n_aidx);
-    }
-    // copies host closure h into the slot on stream s, then derives its targets
-    fem_status upload(fem_mesh m, const HostClosure &h, cudaStream_t s) {
-        auto up = [&](void *dst, size_t off, size_t bytes) -> fem_status {
-            if (bytes) FEM_CUDA(cudaMemcpyAsync(dst, h.host + off, bytes, cudaMemcpyHostToDevice, s));
-            return FEM_OK;
-        };
-        FEM_TRY(up(pep.ptr, h.o_pep, h.n_pep * 8));
-        FEM_TRY(up(pcp.ptr, h.o_pcp, h.n_pcp * 8));
-        FEM_TRY(up(gid.ptr, h.o_gid, h.n_gid * 4));
-        FEM_TRY(up(own.ptr, h.o_own, h.n_own * 4));
-        FEM_TRY(up(id.ptr, h.o_id, h.n_id * 4));
-        FEM_TRY(up(col.ptr, h.o_col, h.n_col));
-        FEM_TRY(up(pos.ptr, h.o_pos, h.n_pos));
-        FEM_TRY(up(ln.ptr, h.o_ln, h.n_ln * 2));
-        Closure cl;
-        view(h, cl);
-        return expand_targets(m, cl, aidx.ptr, s);
-    }
-};
+    };
+    FEM_TRY(up(pep.ptr, h.o_pep, h.n_pep * 8));
+    FEM_TRY(up(pcp.ptr, h.o_pcp, h.n_pcp * 8));
+    FEM_TRY(up(gid.ptr, h.o_gid, h.n_gid * 4));
+    FEM_TRY(up(own.ptr, h.o_own, h.n_own * 4));
+    FEM_TRY(up(id.ptr, h.o_id, h.n_id * 4));
+    FEM_TRY(up(col.ptr, h.o_col, h.n_col));
+    FEM_TRY(up(pos.ptr, h.o_pos, h.n_pos));
+    FEM_TRY(up(ln.ptr, h.o_ln, h.n_ln * 2));
+    Closure cl;
+    view(h, cl);
+    return expand_targets(m, cl, aidx.ptr, s);
+}
+
+void drop_group_cache(fem_mesh m) {
+    m->group_cache.clear();
+    m->group_slot[0].release();
+    m->group_slot[1].release();
+}
 
 // Builds the closure of patches [p0, p1) (halving the range while the budget
 // refuses it), runs fn on it and frees it; with `rec`, the closures are built
@@ -234,14 +251,16 @@ static fem_status run_cached_groups(fem_mesh m, cudaStream_t s,
     *done = false;
     const std::vector<HostClosure> &hs = m->group_cache;
     const int n = (int)hs.size();
-    ClosureSlot slot[2];
-    if (slot[0].alloc(m->arena, hs) != FEM_OK) {
+    ClosureSlot *slot = m->group_slot;  // kept between calls (allocating them each call would cost more)
+    if (!slot[0].fits(hs) && slot[0].alloc(m->arena, hs) != FEM_OK) {
         cudaGetLastError();
+        slot[0].release();
         return FEM_OK;
     }
     int nslots = 2;
-    if (n < 2 || slot[1].alloc(m->arena, hs) != FEM_OK) {
+    if (n < 2 || (!slot[1].fits(hs) && slot[1].alloc(m->arena, hs) != FEM_OK)) {
         cudaGetLastError();
+        slot[1].release();
         nslots = 1;
     }
     if (nslots == 2 && !m->copy_stream) FEM_CUDA(cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking));
@@ -280,7 +299,7 @@ static fem_status run_cached_groups(fem_mesh m, cudaStream_t s,
         if (nslots == 2 && cudaEventRecord(fin[k], s) != cudaSuccess) st = cuda_status(cudaGetLastError(), "group slot");
         if (nslots == 1 && i + 1 < n && st == FEM_OK) st = copy_in(i + 1);
     }
-    // the slots are freed on return: everything that reads them must be done
+    // the slots are reused by the next call: everything that reads them must be done
     const cudaError_t e = cudaStreamSynchronize(s);
     if (st == FEM_OK && e != cudaSuccess) st = cuda_status(e, "group slots");
     if (nslots == 2) cudaStreamSynchronize(m->copy_stream);

@@ -180,6 +180,21 @@ struct HostClosure {
     ~HostClosure() { release(); }
 };
 
+// Device buffers that hold one patch group's closure copied back from its host
+// copy (groups.cu), sized for the largest group and reused from group to group.
+struct ClosureSlot {
+    DevBuf<int64_t> pep, pcp;
+    DevBuf<int32_t> gid, own, id;
+    DevBuf<uint8_t> col, pos;
+    DevBuf<uint16_t> ln;
+    DevBuf<uint32_t> aidx;
+    bool fits(const std::vector<HostClosure> &hs) const;
+    fem_status alloc(Arena &ar, const std::vector<HostClosure> &hs);
+    void release();
+    void view(const HostClosure &h, Closure &cl) const;  // borrows the buffers (frees nothing)
+    fem_status upload(fem_mesh m, const HostClosure &h, cudaStream_t s);  // copy in, derive the targets
+};
+
 }  // namespace fem
 
 struct fem_mesh_s {
@@ -239,8 +254,10 @@ struct fem_mesh_s {
     cudaEvent_t chunk_built[2] = {}, slot_free[2] = {};
     int n_groups = 1;
     int64_t group_patches = 0;  // patches per group when the closures are built per group
-    // host copies of the patch groups' closures, in patch order (fem_options.group_cache)
+    // host copies of the patch groups' closures, in patch order (fem_options.group_cache),
+    // and the two device slots the groups are copied back into (kept between calls)
     std::vector<fem::HostClosure> group_cache;
+    fem::ClosureSlot group_slot[2];
 };
 
 namespace fem {
@@ -249,6 +266,8 @@ fem_status validate_connectivity(fem_mesh m, cudaStream_t s);
 void batch_forget(fem_mesh m);  // drops cached batched launches that use m's plan
 fem_status build_pattern(fem_mesh m, cudaStream_t s);
 fem_status build_plan(fem_mesh m, cudaStream_t s);
+// Frees the host copies of the patch groups and their device slots (the plan changed).
+void drop_group_cache(fem_mesh m);
 // with_pos: the closure carries the in-row positions (the backward pass, the host copies)
 fem_status build_closure(fem_mesh m, int64_t p0, int64_t p1, Closure &cl, cudaStream_t s, bool with_pos);
 // From now on the closures carry the in-row positions the backward pass reads.

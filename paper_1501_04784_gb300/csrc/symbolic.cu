@@ -1540,7 +1540,7 @@ static fem_status build_plan_cap(fem_mesh m, cudaStream_t s, int64_t cap_in) {
     Plan &P = m->plan;
     batch_forget(m);  // cached batched launches were sized for the old plan
     P.reset();
-    m->group_cache.clear();
+    drop_group_cache(m);
     // the elasticity operator holds a 3x3 block per node pair: fewer pairs fit
     const bool elastic = m->opt.operator_kind == 2;
     // (defaults measured on the 1M-brick and 3.07M-tet workloads)
