@@ -156,8 +156,9 @@ typedef struct {
                                     page-locked host memory (about 57 bytes per closure
                                     element); later calls copy the groups back to the device
                                     in turn (the next group's copy overlapping the current
-                                    group's build when two fit the budget) instead of
-                                    building them again; 0 = build every group's closure at
+                                    group's build when two fit the budget; the two device
+                                    slots stay allocated between calls, within the budget)
+                                    instead of building them again; 0 = build every group's closure at
                                     every call (no host memory).  If not even one group's
                                     copy fits beside the call's other buffers, the groups are
                                     built instead. */
