@@ -109,13 +109,18 @@ def test_fp64_staged_and_fused_agree(fem):
     assert np.abs(staged - fused).max() <= 1e-14 * np.abs(ref["cs"]).max()
 
 
-def test_group_cache_equals_rebuilt_groups(fem):
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+def test_group_cache_equals_rebuilt_groups(fem, kind):
     """Patch groups copied back from the host copies of their closures (group_cache,
-    the default) give the values of groups built again at every call
+    the default; their accumulator targets derived on the device from the in-row
+    positions) give the values of groups built again at every call
     (group_cache = 0) and of the unbudgeted build, bitwise, on repeated calls; the
-    first backward pass (which adds the in-row positions and so renews the copies)
-    agrees too, and the builds after it still do.  Both match the oracle."""
-    m = meshgen.hex_grid(24, jitter=0.2, seed=78, permute_nodes=True, permute_elems=True)
+    backward pass agrees too, and the builds after it still do.  Both match the
+    oracle."""
+    if kind == "hex":
+        m = meshgen.hex_grid(24, jitter=0.2, seed=78, permute_nodes=True, permute_elems=True)
+    else:
+        m = meshgen.kuhn_tets(14, jitter=0.25, seed=79, permute_nodes=True, permute_elems=True)
     X, c = dev(m.X, torch.float32), dev(m.c, torch.float32)
     E, X64 = dev(m.E, torch.int32), dev(m.X, torch.float64)
     free = fem.Mesh(E, m.n_nodes, X=X64, patch_entries=1024, vjp_fused=1)
