@@ -132,7 +132,7 @@ __device__ __forceinline__ void elastic_brick_vjp(const S (*xc)[3], T lam, T mu,
         U = {T(0.5) * U.x, T(0.5) * U.y, T(0.5) * U.z};
         const Vec3<T> C0 = cross3(Sv, U), C1 = cross3(U, R), C2 = cross3(R, Sv);
         const T d = dot3(R, C0);
-        const T id = T(1) / d;
+        const T id = rcp_rn(d);
         const T A[3][3] = {{C0.x * id, C1.x * id, C2.x * id}, {C0.y * id, C1.y * id, C2.y * id},
                            {C0.z * id, C1.z * id, C2.z * id}};
         const T wd = d < T(0) ? -d : d;  // Gauss weights 1
@@ -203,7 +203,7 @@ __device__ __forceinline__ void elastic_tet_vjp(const S (*xc)[3], T lam, T mu, c
     const Vec3<T> R0 = tg.R0, R1 = tg.R1, R2 = tg.R2;
     const Vec3<T> C0 = cross3(R1, R2), C1 = cross3(R2, R0), C2 = cross3(R0, R1);
     const T d = dot3(R0, C0);
-    const T id = T(1) / d;
+    const T id = rcp_rn(d);
     const T A[3][3] = {{C0.x * id, C1.x * id, C2.x * id}, {C0.y * id, C1.y * id, C2.y * id},
                        {C0.z * id, C1.z * id, C2.z * id}};
     const T wd = (d < T(0) ? -d : d) * T(1.0 / 6.0);

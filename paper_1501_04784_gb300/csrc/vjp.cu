@@ -196,7 +196,7 @@ __device__ __forceinline__ void brick_vjp(const S (*xc)[3], T c, const T (&Sp)[3
                 const Vec3<T> &U = row[2][q1][q2];
                 const Vec3<T> C0 = cross3(Sv, U), C1 = cross3(U, R), C2 = cross3(R, Sv);
                 const T d = dot3(R, C0);
-                const T inv = T(1) / (d < T(0) ? -d : d);
+                const T inv = rcp_rn(d < T(0) ? -d : d);
                 const T m0 = Mb[q][0], m1 = Mb[q][1], m2 = Mb[q][2];
                 const T m3 = h * Mb[q][3], m4 = h * Mb[q][4], m5 = h * Mb[q][5];
                 const Vec3<T> Y0 = {m0 * C0.x + m3 * C1.x + m4 * C2.x, m0 * C0.y + m3 * C1.y + m4 * C2.y,
@@ -207,7 +207,7 @@ __device__ __forceinline__ void brick_vjp(const S (*xc)[3], T c, const T (&Sp)[3
                                     m4 * C0.z + m5 * C1.z + m2 * C2.z};
                 const T phi = dot3(C0, Y0) + dot3(C1, Y1) + dot3(C2, Y2);
                 dc += phi * inv;
-                // 1/d = sign(d) / |d|: one division per point, not two; phi is scaled by
+                // 1/d = sign(d) / |d|: one reciprocal per point, not two; phi is scaled by
                 // 1/|d| before the second factor, so no 1/d^2 is ever formed (it would
                 // overflow FP32 for |d| below ~1e-19 where phi/|d|^2 stays finite)
                 const T lam = ((d < T(0) ? -phi : phi) * inv) * inv, t = T(2) * inv;
@@ -254,10 +254,10 @@ __device__ __forceinline__ void tet_vjp(const S (*xc)[3], T c, const T (&Sp)[10]
     const Vec3<T> C0 = cross3(R1, R2), C1 = cross3(R2, R0), C2 = cross3(R0, R1);
     const T d = dot3(R0, C0);
     const T ad = d < T(0) ? -d : d;
-    const T id = T(1) / d;
+    const T id = rcp_rn(d);
     T A[3][3] = {{C0.x * id, C1.x * id, C2.x * id}, {C0.y * id, C1.y * id, C2.y * id},
                  {C0.z * id, C1.z * id, C2.z * id}};
-    const T w = T(1) / (T(6) * ad);
+    const T w = rcp_rn(T(6) * ad);
     T M[3][3];
     M[0][0] = dot3(C0, C0) * w; M[1][1] = dot3(C1, C1) * w; M[2][2] = dot3(C2, C2) * w;
     M[0][1] = M[1][0] = dot3(C0, C1) * w;
@@ -349,7 +349,7 @@ __device__ __forceinline__ void brick_mass_vjp(const S (*xc)[3], T c, const T (&
         const Vec3<T> C0 = cross3(Sv, U), C1 = cross3(U, R), C2 = cross3(R, Sv);
         const T d = dot3(R, C0);
         const T ad = d < T(0) ? -d : d;
-        const T id = T(1) / d;
+        const T id = rcp_rn(d);
         // A = J^{-1}: A[i][j] = C_j[i] / d
         const T A[3][3] = {{C0.x * id, C1.x * id, C2.x * id}, {C0.y * id, C1.y * id, C2.y * id},
                            {C0.z * id, C1.z * id, C2.z * id}};
@@ -391,7 +391,7 @@ __device__ __forceinline__ void tet_mass_vjp(const S (*xc)[3], T c, const T (&Sp
     const Vec3<T> C0 = cross3(R1, R2), C1 = cross3(R2, R0), C2 = cross3(R0, R1);
     const T d = dot3(R0, C0);
     const T ad = d < T(0) ? -d : d;
-    const T id = T(1) / d;
+    const T id = rcp_rn(d);
     const T A[3][3] = {{C0.x * id, C1.x * id, C2.x * id}, {C0.y * id, C1.y * id, C2.y * id},
                        {C0.z * id, C1.z * id, C2.z * id}};
     T Ss[4][4];
